@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark of the SISSO hot path on GB300.
+
+One step = one whole SISSO fit (§2.3 Eq. 8): for t = 1..4, SIS screening of every
+candidate of the rung-3 feature space (2.91e8 ids: 1000 samples x 10 lognormal primaries,
+one rung-3 operand from phi_1) plus the exhaustive l0 over all t-subsets of S_t
+(k = 100 per step, C(400, 4) = 1.05e9 subsets at t = 4).  Inputs are resident in HBM
+before the timed region; between timed steps L2 is flushed by writing 256 MB.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank fits its own seeded problem (independent replicas,
+weak scaling); the step time is the maximum over ranks.  ``--impl reference`` times the
+FP64 CPU oracle (the reference of this method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "features scored/s, ℓ0 subsets fit/s; time-to-descriptor vs plain at equal RMSE"
+UNIT = "features/s"
+FP32_FLOP_PER_CAND_SAMPLE = 6          # op, add, 2 FMA (sum, sum of squares, cross)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU work for the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running (clocks and throttle reasons)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline_sample(P, seconds: float, seed: int = 0):
+    """The FP64 oracle scoring a random sample of the workload's candidate ids on all host
+    cores; returns (features/s, ids scored, wall seconds, threads)."""
+    import numpy as np
+    import oracle
+    sp = oracle.Space(P.d, P.op_set, P.rung, P.grammar)
+    n = sp.n_features
+    rng = np.random.default_rng(seed)
+    th = cores()
+    probe = rng.integers(0, n, 2000)
+    t0 = time.perf_counter()
+    sp.scores(P.X, P.y, probe, nthreads=th)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    m = int(max(2000, min(5e7, 2000 * seconds / dt)))
+    ids = rng.integers(0, n, m)
+    t0 = time.perf_counter()
+    sp.scores(P.X, P.y, ids, nthreads=th)
+    dt = time.perf_counter() - t0
+    return m / dt, m, dt, th
+
+
+def top_binary_candidates(sizes, n_unary_ops):
+    """Candidates of the top level's binary sections (the pair kernel's work)."""
+    L = len(sizes) - 1
+    P, Q = sizes[L - 1], (sizes[L - 2] if L >= 2 else 0)
+    return sizes[L] - P - (P - Q) * n_unary_ops
+
+
+def run_reference(args, rank: int):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    from paper_2410_01752_gb300 import inputs
+    if rank != 0:
+        return
+    P = inputs.workload2(0)
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline_sample(P, per_step / 4, seed=1)
+    rates, dts, samples = [], [], []
+    for k in range(args.steps):
+        r, m, dt, th = cpu_baseline_sample(P, per_step, seed=100 + k)
+        rates.append(r)
+        dts.append(dt)
+        samples.append(m)
+    value = sum(samples) / sum(dts)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "grammar": "new_x_prev",
+                   "sis_size": P.sis_size, "max_dim": P.max_dim},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                         "sample": f"{samples[0]} random candidate ids per step scored in FP64 over all {P.N} samples"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        import oracle
+        oracle.build()
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import PREC_FP32, Sisso, build, inputs
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        build.build()
+    P = inputs.workload2(rank)
+    Xd = torch.from_numpy(P.X).cuda()
+    yd = torch.from_numpy(P.y).cuda()
+    stream = torch.cuda.current_stream()
+    s = Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=PREC_FP32, grammar=P.grammar,
+              stream=stream, device=local)
+    n_feat, sizes = s.feature_count()
+    sizes = sizes[: P.rung + 1]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    for _ in range(args.warmup):
+        s.fit()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    step_ms, stats = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            desc = s.fit()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            step_ms.append(e0.elapsed_time(e1))
+            stats.append(s.stats())
+    total_ms = sum(step_ms)
+    cand = sum(st["candidates_scored"] for st in stats)
+    subsets = sum(st["subsets_fit"] for st in stats)
+    launches = sum(st["launches"] for st in stats)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([cand, subsets, launches], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        total_ms, (cand, subsets, launches) = float(t.item()), [float(v) for v in c.tolist()]
+    value = cand / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(P.X).pin_memory()
+        yh = torch.from_numpy(P.y).pin_memory()
+        e2e_ms, e2e_cand, d2h = [], 0, 0
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            with Sisso(Xh.numpy(), yh.numpy(), P.op_set, P.rung, P.sis_size, P.max_dim, precision=PREC_FP32,
+                       grammar=P.grammar, device=local) as se:
+                dd = se.fit()
+                e2e_cand += se.stats()["candidates_scored"]
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            d2h = sum(8 * len(x.ids) + 8 * len(x.coef) + 16 for x in dd)
+        tot = sum(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([tot], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            c = torch.tensor([float(e2e_cand)], device="cuda", dtype=torch.float64)
+            dist.all_reduce(c)
+            tot, e2e_cand = float(t.item()), float(c.item())
+        e2e = {"value": e2e_cand / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the fused pair kernel), timed with CUDA events on
+    # its launch stream inside the library
+    pair_ms = sum(st["ms_screen_pair"] for st in stats)
+    pair_launches = sum(st["screen_pair_launches"] for st in stats)
+    n_unary = sum(1 for b in range(4, 12) if P.op_set >> b & 1)
+    cand_pair = top_binary_candidates(sizes, n_unary)
+    flop_launch = cand_pair * P.N * FP32_FLOP_PER_CAND_SAMPLE
+    avg_launch_s = (pair_ms / max(pair_launches, 1)) / 1e3
+    achieved = flop_launch / avg_launch_s / 1e12
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "kernel": "k_score_pairs<float>", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (measured max SM clock)",
+            "flop_per_launch": flop_launch, "launch_ms": avg_launch_s * 1e3,
+            "algorithmic_unit": f"{FP32_FLOP_PER_CAND_SAMPLE} flop per candidate-sample x {cand_pair} candidates x {P.N} samples"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, m, dt, th = cpu_baseline_sample(P, args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"{m} random candidate ids of the workload scored in FP64 over all {P.N} samples ({dt:.1f} s)"}
+
+    d_last = desc[-1] if desc else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "grammar": "new_x_prev",
+                   "sis_size": P.sis_size, "max_dim": P.max_dim, "n_features": n_feat,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "l0_subsets_fit_per_s": subsets / (total_ms / 1e3),
+        "time_to_descriptor_s": total_ms / args.steps / 1e3,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "phase_ms": {k: sum(st[k] for st in stats) / args.steps for k in
+                     ("ms_screen", "ms_screen_pair", "ms_select", "ms_gram", "ms_l0", "ms_refit", "ms_fit")},
+        "descriptor": {"ids": d_last.ids, "coef": d_last.coef, "rmse": d_last.rmse, "r2": d_last.r2,
+                       "expr": [s.expr(i) for i in d_last.ids]} if d_last else None,
+        "window_grown": sum(st["window_grown"] for st in stats),
+        "window_saturated": max(st["window_saturated"] for st in stats),
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

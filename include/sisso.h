@@ -1,0 +1,196 @@
+/*
+ * sisso.h — C ABI of the GB300 (sm_103a) SISSO hot path.
+ *
+ * SISSO (arXiv 2410.01752) fits y ~ c0 + sum_j c_j phi_j(x) where the phi_j are chosen
+ * from an operator-generated feature space (§2.1, Eq. 2) by sure independence screening
+ * (§2.2, Eqs. 5-6) and an exhaustive l0 search over the screened subspace (§2.3, Eqs. 7-8).
+ * This library runs that path on one GPU: a fused generate-and-score kernel screens
+ * every candidate without materialising the feature space, a device-wide selection and
+ * an FP64 re-score pick the subspace, and a persistent enumerator solves every D-subset
+ * by register Cholesky.
+ *
+ * Conventions for every entry point:
+ *  - Status codes, never aborts, traps or prints.  After an error on a context,
+ *    sisso_last_error(ctx) describes it (the string is owned by the context).
+ *  - Pointers passed in may be host or device memory unless stated otherwise; the
+ *    library copies what it keeps (unified addressing, cudaMemcpyDefault).
+ *    Output buffers are owned by the caller and are HOST memory.
+ *  - X is N x d, row-major (sample-major), FP64.  Feature ids are the canonical ids of
+ *    the expanded space: level, then operator in the order of the table below, then the
+ *    operand pair (i, j) in lexicographic order (see sisso_feature_expr for the meaning).
+ *  - A context owns all device memory it allocates and one CUDA stream (or the caller's,
+ *    see sisso_opts.cuda_stream).  Contexts are independent; one context must not be used
+ *    from two host threads at once.
+ */
+#ifndef SISSO_H
+#define SISSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sisso_ctx sisso_ctx;
+
+typedef enum {
+    SISSO_OK = 0,
+    SISSO_ERR_ARG = -1,        /* invalid argument (sizes, op mask, rung, non-finite input) */
+    SISSO_ERR_OOM = -2,        /* device allocation failed */
+    SISSO_ERR_CUDA = -3,       /* a CUDA call failed (message in sisso_last_error) */
+    SISSO_ERR_NUMERIC = -4,    /* no valid feature / every subset singular */
+    SISSO_ERR_TIMEOUT = -5,    /* a bounded device wait ran out */
+    SISSO_ERR_STATE = -6,      /* call out of order (e.g. get_descriptor before fit) */
+    SISSO_ERR_CAPACITY = -7    /* a fixed-capacity buffer would overflow */
+} sisso_status;
+
+/* Operator table, in canonical order (§2.1; the paper's operators plus those its
+ * examples use, §3.3 and Table 1).  Binary first: + and * are symmetric (i < j), - is
+ * taken for i < j only (a-b = -(b-a) scores and fits the same), / takes both orders. */
+enum {
+    SISSO_OP_ADD = 1u << 0,    /* z_i + z_j      */
+    SISSO_OP_SUB = 1u << 1,    /* z_i - z_j      */
+    SISSO_OP_MUL = 1u << 2,    /* z_i * z_j      */
+    SISSO_OP_DIV = 1u << 3,    /* z_i / z_j      */
+    SISSO_OP_EXP = 1u << 4,    /* exp(z)         */
+    SISSO_OP_LOG = 1u << 5,    /* log(z)         */
+    SISSO_OP_SQRT = 1u << 6,   /* sqrt(z)        */
+    SISSO_OP_SQ = 1u << 7,     /* z^2            */
+    SISSO_OP_INV = 1u << 8,    /* z^-1           */
+    SISSO_OP_SIN = 1u << 9,    /* sin(z)         */
+    SISSO_OP_CUBE = 1u << 10,  /* z^3            */
+    SISSO_OP_EXPNEG = 1u << 11 /* exp(-z)        */
+};
+#define SISSO_OP_ALL 0xFFFu
+
+enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1 };
+
+/* Expansion grammar (§2.1 Eq. 2).  EQ2: every pair of phi_{l-1} except pairs already
+ * in phi_{l-2}.  NEW_X_PREV: identical up to level 2; from level 3 one operand is new at
+ * level l-1 and the other comes from phi_{l-2}.  Unary operators always act on the
+ * features new at level l-1. */
+enum { SISSO_GRAMMAR_EQ2 = 0, SISSO_GRAMMAR_NEW_X_PREV = 1 };
+
+#define SISSO_MAX_RUNG 3
+#define SISSO_MAX_DIM 4
+#define SISSO_MAX_SIS 1024
+
+typedef struct {
+    int precision;          /* SISSO_PREC_*: arithmetic of the screening and l0 kernels;
+                               selection and refits are always FP64 (default FP32) */
+    int grammar;            /* SISSO_GRAMMAR_* (default EQ2) */
+    int survivors;          /* FP32 screening window: candidates re-scored in FP64 per
+                               step (0 = max(16384, 64 k)); grown x4 automatically when
+                               it cannot prove the selection exact */
+    double band_rel;        /* l0: FP32 RSS band, relative to SST, refit in FP64
+                               (0 = 1e-4) */
+    int64_t max_band;       /* l0: capacity of the FP64 refit list (0 = 1<<22) */
+    void* cuda_stream;      /* cudaStream_t to run on; NULL = a stream the context owns */
+    int device;             /* CUDA device ordinal (default 0) */
+} sisso_opts;
+
+/* Per-context counters and device timings (CUDA events on the context's stream). */
+typedef struct {
+    int64_t candidates_scored;   /* ids scored by the screening kernels, all steps */
+    int64_t subsets_fit;         /* l0 subsets solved in FP32/FP64, all steps */
+    int64_t subsets_refit;       /* subsets re-solved in FP64 */
+    int64_t survivors_rescored;  /* candidates re-scored in FP64 */
+    int window_grown;            /* times the screening window was enlarged */
+    int window_saturated;        /* 1 if the window hit its cap without proof */
+    int launches;                /* kernels launched by the last sisso_fit */
+    double ms_screen;            /* fused generate+score kernels */
+    double ms_screen_pair;       /* ... of which the top-level pair kernel */
+    int screen_pair_launches;    /* launches of the top-level pair kernel */
+    double ms_select;            /* device-wide selection, FP64 re-score, walk */
+    double ms_gram;              /* subspace Gram */
+    double ms_l0;                /* l0 enumeration (FP32 or FP64) */
+    double ms_refit;             /* FP64 refit, winner, residual */
+    double ms_fit;               /* whole sisso_fit, device time */
+} sisso_stats;
+
+void sisso_default_opts(sisso_opts* opts);
+
+/* Create a context: copies X (N x d row-major FP64) and y (N) to the device, plans the
+ * feature space phi_rung (§2.1) for the operator mask and grammar, and allocates every
+ * buffer sisso_fit needs.  sis_size is k of §2.2 (features added per step), max_dim the
+ * number of terms T of §2.3.  Errors: SISSO_ERR_ARG for N < max_dim+1, d < 1, rung not
+ * in 1..SISSO_MAX_RUNG, max_dim not in 1..SISSO_MAX_DIM, sis_size not in
+ * 1..SISSO_MAX_SIS, an empty op mask, or non-finite X/y; SISSO_ERR_OOM; SISSO_ERR_CUDA.
+ * On error *out is NULL. */
+sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32_t op_set,
+                          int rung, int sis_size, int max_dim, const sisso_opts* opts,
+                          sisso_ctx** out);
+
+/* Run SISSO (§2.3 Eq. 8): for t = 1..max_dim, screen phi against y (t = 1) or the best
+ * (t-1)-term residual, append the k accepted ids to S, solve every t-subset of S and
+ * keep the lowest-RSS model.  Stops early when a model is exact to FP64 rounding
+ * (RMSE <= 1e-10 std(y)) or S has fewer than t features.  Synchronous: returns when
+ * the results are on the host. */
+sisso_status sisso_fit(sisso_ctx* ctx);
+
+/* Number of descriptors produced by the last fit (<= max_dim). */
+sisso_status sisso_get_n_dims(const sisso_ctx* ctx, int* n_dims);
+
+/* Descriptor of dimension dim (1-based): ids[dim] ascending, coef[dim+1] with coef[0]
+ * the intercept and coef[j+1] the coefficient of ids[j] in the original units,
+ * rmse = sqrt(RSS/N), r2 = 1 - RSS/SST.  Any output pointer may be NULL. */
+sisso_status sisso_get_descriptor(const sisso_ctx* ctx, int dim, int64_t* ids, double* coef,
+                                  double* rmse, double* r2);
+
+/* Ids accepted by SIS at step `step` (1-based), in acceptance order; *n = count. */
+sisso_status sisso_get_sis(const sisso_ctx* ctx, int step, int64_t* ids, int cap, int* n);
+
+/* |phi_rung| and |phi_l| for l = 0..rung (sizes[rung+1]; may be NULL). */
+sisso_status sisso_feature_count(const sisso_ctx* ctx, int64_t* n_features, int64_t* sizes);
+
+/* Expression of feature id, e.g. "(x1*(x2/x3))": primaries are x1..xd; binary
+ * "(a+b)", "(a-b)", "(a*b)", "(a/b)"; unary "exp(a)", "log(a)", "sqrt(a)", "(a)^2",
+ * "(a)^-1", "sin(a)", "(a)^3", "exp(-a)". */
+sisso_status sisso_feature_expr(const sisso_ctx* ctx, int64_t id, char* buf, size_t len);
+
+sisso_status sisso_get_stats(const sisso_ctx* ctx, sisso_stats* out);
+const char* sisso_last_error(const sisso_ctx* ctx);
+void sisso_destroy(sisso_ctx* ctx);
+
+/* ---- feature space without a context (host only, no GPU needed) ------------------- */
+
+/* Sizes |phi_l|, l = 0..rung, of the space planned for (d, op_set, rung, grammar)
+ * (§2.1 Eq. 2 with the rule above).  sizes: HOST, rung+1 entries. */
+sisso_status sisso_space_sizes(int d, uint32_t op_set, int rung, int grammar, int64_t* sizes);
+
+/* Expression string of feature id in that space (same format as sisso_feature_expr). */
+sisso_status sisso_space_expr(int d, uint32_t op_set, int rung, int grammar, int64_t id, char* buf,
+                              size_t len);
+
+/* ---- kernel-level entry points (parity tests, benchmark) -------------------------- */
+
+/* Values of features ids[0..n) at every sample, evaluated on the device in `precision`
+ * from the primaries (§2.1).  out: HOST, n x N row-major, double (FP32 results are
+ * widened). */
+sisso_status sisso_eval_features(sisso_ctx* ctx, const int64_t* ids, int64_t n, int precision,
+                                 double* out);
+
+/* Screening scores of every id of phi_rung against `target` (N values; §2.2 Eqs. 5-6:
+ * Pearson |rho|) from the fused generate-and-score kernels in `precision`.  Invalid
+ * features score -1.  scores: HOST, |phi_rung| floats. */
+sisso_status sisso_score_all(sisso_ctx* ctx, const double* target, int precision, float* scores);
+
+/* One SIS step (§2.2) with the device-wide selection, FP64 re-score and walk: accepts up
+ * to k ids not in S_prev (n_prev ids) and not duplicates of S_prev or of each other.
+ * acc: HOST, k entries; *n_acc = number accepted. */
+sisso_status sisso_sis_step(sisso_ctx* ctx, const double* target, const int64_t* S_prev,
+                            int n_prev, int k, int64_t* acc, int* n_acc);
+
+/* Exhaustive l0 (§2.3) over every D-subset of n standardised features given their
+ * FP64 Gram G (n x n, Z^T Z / N), moments b (n, Z^T y~ / N) and syy = y~^T y~ / N:
+ * FP32 (or FP64) enumeration, FP64 refit of the band, tie rule on gid (n global ids).
+ * best_pos: HOST, D positions ascending; best_rss: RSS of the winner.  *examined: C(n,D). */
+sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, double syy,
+                             int n, int D, const int64_t* gid, int precision, int* best_pos,
+                             double* best_rss, int64_t* examined);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SISSO_H */

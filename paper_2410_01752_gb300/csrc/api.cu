@@ -1,0 +1,407 @@
+// api.cu — the C ABI declared in include/sisso.h: context lifetime, the SISSO iteration
+// of §2.3 (Eq. 8) driving the screening (sis.cu) and l0 (l0.cu) kernels, and the
+// kernel-level entry points used by the parity tests and the benchmark.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+using namespace sg;
+
+namespace {
+
+// X (N x d row-major, FP64) -> column-major FP64 and FP32 copies; flags non-finite input
+__global__ void k_ingest(const double* __restrict__ X, const double* __restrict__ y, int N, int d,
+                         double* __restrict__ Xc64, float* __restrict__ Xc32, double* __restrict__ y64,
+                         int* bad) {
+    const int64_t total = (int64_t)N * d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / d), c = (int)(e % d);
+        const double v = X[e];
+        if (!isfinite(v)) atomicOr(bad, 1);
+        Xc64[(size_t)c * N + s] = v;
+        Xc32[(size_t)c * N + s] = (float)v;
+    }
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+        const double v = y[s];
+        if (!isfinite(v)) atomicOr(bad, 2);
+        y64[s] = v;
+    }
+}
+
+__global__ void k_cast(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+template <typename T>
+sisso_status dalloc(sisso_ctx* c, T*& p, size_t count, const char* what) {
+    p = nullptr;
+    if (count == 0) count = 1;
+    return check_cuda(c, cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * count), what);
+}
+
+void free_all(sisso_ctx* c) {
+    void* bufs[] = {c->Xc64, c->Xc32, c->y64, c->yc64, c->scores, c->target64, c->tc64, c->tc32, c->tstats,
+                    c->hist, c->sel_state, c->surv_ids, c->surv_count, c->surv_score, c->surv_mean, c->surv_sd,
+                    c->surv_valid, c->sort_score, c->sort_id, c->sort_src, c->removed, c->walk, c->S_dev,
+                    c->S_sorted, c->Z, c->Zmean, c->Zsd, c->G64, c->b64, c->G32, c->b32, c->resid, c->ymom,
+                    c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (c->walk_h) cudaFreeHost(c->walk_h);
+    if (c->win_h) cudaFreeHost(c->win_h);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, const sisso_opts& o,
+                      std::string& why) {
+    if (d < 1) { why = "d < 1"; return SISSO_ERR_ARG; }
+    if (rung < 1 || rung > SISSO_MAX_RUNG) { why = "rung must be in 1..3"; return SISSO_ERR_ARG; }
+    if (max_dim < 1 || max_dim > SISSO_MAX_DIM) { why = "max_dim must be in 1..4"; return SISSO_ERR_ARG; }
+    if (k < 1 || k > SISSO_MAX_SIS) { why = "sis_size must be in 1..1024"; return SISSO_ERR_ARG; }
+    if (N < max_dim + 1 || N < 2) { why = "N must be at least max_dim + 1"; return SISSO_ERR_ARG; }
+    if ((ops & SISSO_OP_ALL) == 0 || (ops & ~SISSO_OP_ALL)) { why = "bad operator mask"; return SISSO_ERR_ARG; }
+    if (o.precision != SISSO_PREC_FP32 && o.precision != SISSO_PREC_FP64) { why = "bad precision"; return SISSO_ERR_ARG; }
+    if (o.grammar != SISSO_GRAMMAR_EQ2 && o.grammar != SISSO_GRAMMAR_NEW_X_PREV) { why = "bad grammar"; return SISSO_ERR_ARG; }
+    if ((int64_t)max_dim * k > 65535) { why = "subspace too large"; return SISSO_ERR_ARG; }
+    return SISSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sisso_default_opts(sisso_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = SISSO_PREC_FP32;
+    o->grammar = SISSO_GRAMMAR_EQ2;
+    o->survivors = 0;
+    o->band_rel = 0.0;
+    o->max_band = 0;
+    o->cuda_stream = nullptr;
+    o->device = 0;
+}
+
+sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32_t op_set, int rung,
+                          int sis_size, int max_dim, const sisso_opts* opts, sisso_ctx** out) {
+    if (!out) return SISSO_ERR_ARG;
+    *out = nullptr;
+    if (!X || !y) return SISSO_ERR_ARG;
+    sisso_opts o;
+    sisso_default_opts(&o);
+    if (opts) o = *opts;
+    std::string why;
+    sisso_status st = validate(N, d, op_set, rung, sis_size, max_dim, o, why);
+    if (st) return st;
+    sisso_ctx* c = new (std::nothrow) sisso_ctx();
+    if (!c) return SISSO_ERR_OOM;
+    c->N = N; c->d = d; c->rung = rung; c->k = sis_size; c->max_dim = max_dim; c->ops = op_set; c->opts = o;
+    if (!plan_space(d, op_set, rung, o.grammar, c->space)) { delete c; return SISSO_ERR_ARG; }
+    c->n_feat = c->space.phi[rung];
+    if (c->space.phi[rung - 1] >= (int64_t)1 << 31) { delete c; return SISSO_ERR_ARG; }
+    auto bail = [&](sisso_status s) { free_all(c); delete c; return s; };
+    if ((st = check_cuda(c, cudaSetDevice(o.device), "cudaSetDevice"))) return bail(st);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (o.cuda_stream) { c->stream = (cudaStream_t)o.cuda_stream; c->own_stream = false; }
+    else {
+        if ((st = check_cuda(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream"))) return bail(st);
+        c->own_stream = true;
+    }
+    const size_t Nn = (size_t)N;
+    c->n_cap = max_dim * sis_size;
+    const int64_t base_window = std::max<int64_t>(16384, 64LL * sis_size);
+    c->surv_cap = std::min<int64_t>(base_window * 64, c->n_feat) + c->n_cap;
+    int64_t sp = 1;
+    while (sp < c->surv_cap) sp <<= 1;
+    c->sort_cap = sp;
+    c->band_cap = o.max_band > 0 ? o.max_band : ((int64_t)1 << 22);
+    if ((st = dalloc(c, c->Xc64, Nn * d, "X")) || (st = dalloc(c, c->Xc32, Nn * d, "X32")) ||
+        (st = dalloc(c, c->y64, Nn, "y")) || (st = dalloc(c, c->yc64, Nn, "yc")) ||
+        (st = dalloc(c, c->scores, (size_t)c->n_feat, "scores")) || (st = dalloc(c, c->target64, Nn, "target")) ||
+        (st = dalloc(c, c->tc64, Nn, "tc64")) || (st = dalloc(c, c->tc32, Nn, "tc32")) ||
+        (st = dalloc(c, c->tstats, 1, "tstats")) || (st = dalloc(c, c->hist, 3 * 4096, "hist")) ||
+        (st = dalloc(c, c->sel_state, 4, "sel")) || (st = dalloc(c, c->surv_ids, (size_t)c->surv_cap, "surv")) ||
+        (st = dalloc(c, c->surv_count, 1, "surv_count")) ||
+        (st = dalloc(c, c->surv_score, (size_t)c->surv_cap, "surv_score")) ||
+        (st = dalloc(c, c->surv_mean, (size_t)c->surv_cap, "surv_mean")) ||
+        (st = dalloc(c, c->surv_sd, (size_t)c->surv_cap, "surv_sd")) ||
+        (st = dalloc(c, c->surv_valid, (size_t)c->surv_cap, "surv_valid")) ||
+        (st = dalloc(c, c->sort_score, (size_t)c->sort_cap, "sort")) ||
+        (st = dalloc(c, c->sort_id, (size_t)c->sort_cap, "sort_id")) ||
+        (st = dalloc(c, c->sort_src, (size_t)c->sort_cap, "sort_src")) ||
+        (st = dalloc(c, c->removed, (size_t)c->sort_cap, "removed")) || (st = dalloc(c, c->walk, 1, "walk")) ||
+        (st = dalloc(c, c->S_dev, (size_t)c->n_cap, "S")) || (st = dalloc(c, c->S_sorted, (size_t)c->n_cap, "S_sorted")) ||
+        (st = dalloc(c, c->Z, (size_t)c->n_cap * Nn, "Z")) || (st = dalloc(c, c->Zmean, (size_t)c->n_cap, "Zmean")) ||
+        (st = dalloc(c, c->Zsd, (size_t)c->n_cap, "Zsd")) ||
+        (st = dalloc(c, c->G64, (size_t)c->n_cap * c->n_cap, "G64")) || (st = dalloc(c, c->b64, (size_t)c->n_cap, "b64")) ||
+        (st = dalloc(c, c->G32, (size_t)c->n_cap * c->n_cap, "G32")) || (st = dalloc(c, c->b32, (size_t)c->n_cap, "b32")) ||
+        (st = dalloc(c, c->resid, Nn, "resid")) || (st = dalloc(c, c->ymom, 4, "ymom")) ||
+        (st = dalloc(c, c->band, (size_t)c->band_cap, "band")) ||
+        (st = dalloc(c, c->band_rss, (size_t)c->band_cap, "band_rss")) ||
+        (st = dalloc(c, c->band_count, 1, "band_count")) || (st = dalloc(c, c->work, 16, "work")) ||
+        (st = dalloc(c, c->win, 1, "win")))
+        return bail(st);
+    if ((st = check_cuda(c, cudaMallocHost(&c->walk_h, sizeof(WalkResult)), "walk_h")) ||
+        (st = check_cuda(c, cudaMallocHost(&c->win_h, sizeof(Winner)), "win_h")))
+        return bail(st);
+    // inputs: may be host or device memory (unified addressing)
+    double *Xraw = nullptr, *yraw = nullptr;
+    int* bad = nullptr;
+    if ((st = dalloc(c, Xraw, Nn * d, "Xraw")) || (st = dalloc(c, yraw, Nn, "yraw")) || (st = dalloc(c, bad, 1, "bad")))
+        return bail(st);
+    cudaMemcpyAsync(Xraw, X, sizeof(double) * Nn * d, cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(yraw, y, sizeof(double) * Nn, cudaMemcpyDefault, c->stream);
+    cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    k_ingest<<<std::max(1, std::min(c->sms * 8, (int)((Nn * d + 255) / 256))), 256, 0, c->stream>>>(
+        Xraw, yraw, N, d, c->Xc64, c->Xc32, c->y64, bad);
+    int h_bad = 0;
+    cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    // moments of y, and y~ = y - mean(y)
+    st = prepare_target(c, c->y64);
+    cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);
+    TargetStats ts{};
+    cudaMemcpyAsync(&ts, c->tstats, sizeof(ts), cudaMemcpyDeviceToHost, c->stream);
+    sisso_status st2 = check_cuda(c, cudaStreamSynchronize(c->stream), "create");
+    cudaFree(Xraw); cudaFree(yraw); cudaFree(bad);
+    if (st || st2) return bail(st ? st : st2);
+    if (h_bad) return bail(SISSO_ERR_ARG);
+    if (!(ts.sd > 0.0)) return bail(SISSO_ERR_ARG);     // constant target
+    c->ybar = ts.mean;
+    c->syy = ts.sd * ts.sd;
+    *out = c;
+    return SISSO_OK;
+}
+
+sisso_status sisso_fit(sisso_ctx* c) {
+    if (!c) return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    const int prec = c->opts.precision;
+    c->stats = sisso_stats{};
+    c->S.clear(); c->n_sis.clear(); c->res_ids.clear(); c->res_coef.clear(); c->res_rmse.clear(); c->res_r2.clear();
+    c->n_dims = 0;
+    c->fitted = false;
+    cudaEvent_t f0, f1;
+    cudaEventCreate(&f0); cudaEventCreate(&f1);
+    cudaEventRecord(f0, c->stream);
+    const double* target = c->y64;
+    sisso_status st = SISSO_OK;
+    for (int t = 1; t <= c->max_dim; ++t) {
+        if ((st = prepare_target(c, target))) break;
+        if ((st = score_all(c, prec))) break;
+        std::vector<int64_t> acc;
+        if ((st = sis_select(c, c->k, c->S.data(), (int)c->S.size(), acc))) break;
+        const int n_old = (int)c->S.size();
+        if (!acc.empty())
+            cudaMemcpyAsync(c->S_dev + n_old, acc.data(), sizeof(int64_t) * acc.size(), cudaMemcpyHostToDevice, c->stream);
+        c->S.insert(c->S.end(), acc.begin(), acc.end());
+        c->n_sis.push_back((int)acc.size());
+        const int n = (int)c->S.size();
+        if (n < t) {
+            if (t == 1) st = fail(c, SISSO_ERR_NUMERIC, "no valid feature");
+            break;
+        }
+        cudaEvent_t g0, g1;
+        cudaEventCreate(&g0); cudaEventCreate(&g1);
+        cudaEventRecord(g0, c->stream);
+        if ((st = append_subspace(c, n_old, (int)acc.size()))) break;
+        cudaEventRecord(g1, c->stream);
+        Winner w{};
+        if ((st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w))) break;
+        c->stats.ms_gram += event_ms(g0, g1);
+        cudaEventDestroy(g0); cudaEventDestroy(g1);
+        if ((st = winner_model(c, n, t, w))) break;
+        c->res_ids.emplace_back(w.ids, w.ids + t);
+        c->res_coef.emplace_back(w.coef, w.coef + t + 1);
+        c->res_rmse.push_back(w.rmse);
+        c->res_r2.push_back(w.r2);
+        c->n_dims = t;
+        target = c->resid;
+        if (w.rmse <= kStopRel * std::sqrt(c->syy)) break;   // exact fit
+    }
+    cudaEventRecord(f1, c->stream);
+    cudaEventSynchronize(f1);
+    c->stats.ms_fit = event_ms(f0, f1);
+    cudaEventDestroy(f0); cudaEventDestroy(f1);
+    if (st) return st;
+    c->fitted = true;
+    return SISSO_OK;
+}
+
+sisso_status sisso_get_n_dims(const sisso_ctx* c, int* n_dims) {
+    if (!c || !n_dims) return SISSO_ERR_ARG;
+    if (!c->fitted) return SISSO_ERR_STATE;
+    *n_dims = c->n_dims;
+    return SISSO_OK;
+}
+
+sisso_status sisso_get_descriptor(const sisso_ctx* c, int dim, int64_t* ids, double* coef, double* rmse, double* r2) {
+    if (!c) return SISSO_ERR_ARG;
+    if (!c->fitted) return SISSO_ERR_STATE;
+    if (dim < 1 || dim > c->n_dims) return SISSO_ERR_ARG;
+    const int q = dim - 1;
+    if (ids) std::copy(c->res_ids[q].begin(), c->res_ids[q].end(), ids);
+    if (coef) std::copy(c->res_coef[q].begin(), c->res_coef[q].end(), coef);
+    if (rmse) *rmse = c->res_rmse[q];
+    if (r2) *r2 = c->res_r2[q];
+    return SISSO_OK;
+}
+
+sisso_status sisso_get_sis(const sisso_ctx* c, int step, int64_t* ids, int cap, int* n) {
+    if (!c || !n) return SISSO_ERR_ARG;
+    if (!c->fitted) return SISSO_ERR_STATE;
+    if (step < 1 || step > (int)c->n_sis.size()) return SISSO_ERR_ARG;
+    int off = 0;
+    for (int s = 0; s < step - 1; ++s) off += c->n_sis[s];
+    const int cnt = c->n_sis[step - 1];
+    *n = cnt;
+    if (ids) for (int i = 0; i < cnt && i < cap; ++i) ids[i] = c->S[off + i];
+    return SISSO_OK;
+}
+
+sisso_status sisso_feature_count(const sisso_ctx* c, int64_t* n_features, int64_t* sizes) {
+    if (!c) return SISSO_ERR_ARG;
+    if (n_features) *n_features = c->n_feat;
+    if (sizes) for (int l = 0; l <= c->rung; ++l) sizes[l] = c->space.phi[l];
+    return SISSO_OK;
+}
+
+sisso_status sisso_feature_expr(const sisso_ctx* c, int64_t id, char* buf, size_t len) {
+    if (!c || !buf || len == 0) return SISSO_ERR_ARG;
+    if (id < 0 || id >= c->n_feat) return SISSO_ERR_ARG;
+    const std::string s = feature_expr(c->space, id);
+    if (s.size() + 1 > len) return SISSO_ERR_CAPACITY;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return SISSO_OK;
+}
+
+sisso_status sisso_get_stats(const sisso_ctx* c, sisso_stats* out) {
+    if (!c || !out) return SISSO_ERR_ARG;
+    *out = c->stats;
+    return SISSO_OK;
+}
+
+const char* sisso_last_error(const sisso_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void sisso_destroy(sisso_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->opts.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+// ---- feature space without a context -----------------------------------------------------
+
+sisso_status sisso_space_sizes(int d, uint32_t op_set, int rung, int grammar, int64_t* sizes) {
+    if (!sizes || rung < 1 || rung > SISSO_MAX_RUNG || (op_set & SISSO_OP_ALL) == 0 || (op_set & ~SISSO_OP_ALL))
+        return SISSO_ERR_ARG;
+    Space sp;
+    if (!plan_space(d, op_set, rung, grammar, sp)) return SISSO_ERR_ARG;
+    for (int l = 0; l <= rung; ++l) sizes[l] = sp.phi[l];
+    return SISSO_OK;
+}
+
+sisso_status sisso_space_expr(int d, uint32_t op_set, int rung, int grammar, int64_t id, char* buf, size_t len) {
+    if (!buf || len == 0 || rung < 1 || rung > SISSO_MAX_RUNG || (op_set & SISSO_OP_ALL) == 0) return SISSO_ERR_ARG;
+    Space sp;
+    if (!plan_space(d, op_set, rung, grammar, sp)) return SISSO_ERR_ARG;
+    if (id < 0 || id >= sp.phi[rung]) return SISSO_ERR_ARG;
+    const std::string s = feature_expr(sp, id);
+    if (s.size() + 1 > len) return SISSO_ERR_CAPACITY;
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+    return SISSO_OK;
+}
+
+// ---- kernel-level entry points --------------------------------------------------------
+
+sisso_status sisso_eval_features(sisso_ctx* c, const int64_t* ids, int64_t n, int precision, double* out) {
+    if (!c || !ids || !out || n < 0) return SISSO_ERR_ARG;
+    if (n == 0) return SISSO_OK;
+    cudaSetDevice(c->opts.device);
+    int64_t* d_ids = nullptr;
+    double* d_out = nullptr;
+    sisso_status st;
+    if ((st = dalloc(c, d_ids, (size_t)n, "ids")) || (st = dalloc(c, d_out, (size_t)n * c->N, "out"))) {
+        cudaFree(d_ids);
+        return st;
+    }
+    cudaMemcpyAsync(d_ids, ids, sizeof(int64_t) * n, cudaMemcpyDefault, c->stream);
+    st = eval_features(c, d_ids, n, precision, d_out);
+    if (!st) {
+        cudaMemcpyAsync(out, d_out, sizeof(double) * n * c->N, cudaMemcpyDefault, c->stream);
+        st = check_cuda(c, cudaStreamSynchronize(c->stream), "eval_features");
+    }
+    cudaFree(d_ids);
+    cudaFree(d_out);
+    return st;
+}
+
+sisso_status sisso_score_all(sisso_ctx* c, const double* target, int precision, float* scores) {
+    if (!c || !target || !scores) return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    cudaMemcpyAsync(c->target64, target, sizeof(double) * c->N, cudaMemcpyDefault, c->stream);
+    sisso_status st = prepare_target(c, c->target64);
+    if (!st) st = score_all(c, precision);
+    if (!st) {
+        cudaMemcpyAsync(scores, c->scores, sizeof(float) * c->n_feat, cudaMemcpyDefault, c->stream);
+        st = check_cuda(c, cudaStreamSynchronize(c->stream), "score_all");
+    }
+    return st;
+}
+
+sisso_status sisso_sis_step(sisso_ctx* c, const double* target, const int64_t* S_prev, int n_prev, int k,
+                            int64_t* acc, int* n_acc) {
+    if (!c || !target || !acc || !n_acc || k < 1 || k > SISSO_MAX_SIS || n_prev < 0 || n_prev > c->n_cap - k ||
+        (n_prev > 0 && !S_prev))
+        return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    std::vector<int64_t> prev(S_prev, S_prev + n_prev);
+    cudaMemcpyAsync(c->target64, target, sizeof(double) * c->N, cudaMemcpyDefault, c->stream);
+    sisso_status st = prepare_target(c, c->target64);
+    if (!st) st = score_all(c, c->opts.precision);
+    std::vector<int64_t> out;
+    if (!st) st = sis_select(c, k, prev.data(), n_prev, out);
+    if (st) return st;
+    *n_acc = (int)out.size();
+    std::copy(out.begin(), out.end(), acc);
+    return SISSO_OK;
+}
+
+sisso_status sisso_l0_search(sisso_ctx* c, const double* G, const double* b, double syy, int n, int D,
+                             const int64_t* gid, int precision, int* best_pos, double* best_rss, int64_t* examined) {
+    if (!c || !G || !b || !gid || !best_pos || n < 1 || D < 1 || D > SISSO_MAX_DIM || n < D || n > 65535)
+        return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    double *dG = nullptr, *db = nullptr;
+    float *dG32 = nullptr, *db32 = nullptr;
+    int64_t* dgid = nullptr;
+    sisso_status st;
+    const size_t nn = (size_t)n * n;
+    if ((st = dalloc(c, dG, nn, "G")) || (st = dalloc(c, db, (size_t)n, "b")) || (st = dalloc(c, dG32, nn, "G32")) ||
+        (st = dalloc(c, db32, (size_t)n, "b32")) || (st = dalloc(c, dgid, (size_t)n, "gid"))) {
+        cudaFree(dG); cudaFree(db); cudaFree(dG32); cudaFree(db32); cudaFree(dgid);
+        return st;
+    }
+    cudaMemcpyAsync(dG, G, sizeof(double) * nn, cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(dgid, gid, sizeof(int64_t) * n, cudaMemcpyDefault, c->stream);
+    k_cast<<<std::max(1, std::min(c->sms * 4, (int)((nn + 255) / 256))), 256, 0, c->stream>>>(dG, dG32, (int64_t)nn);
+    k_cast<<<1, 256, 0, c->stream>>>(db, db32, n);
+    Winner w{};
+    st = l0_solve(c, dG, db, dG32, db32, n, syy, n, D, dgid, precision, w);
+    if (!st) {
+        std::copy(w.pos, w.pos + D, best_pos);
+        if (best_rss) *best_rss = w.rss_gram;
+        if (examined) *examined = w.examined;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(dG); cudaFree(db); cudaFree(dG32); cudaFree(db32); cudaFree(dgid);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,365 @@
+// common.cuh — internal definitions shared by the library's translation units.
+//
+// The feature space of §2.1 (Eq. 2) is never materialised.  It is described by a small
+// plan: per level, one section per enabled operator with its first id and size, and for
+// binary sections the pair rule.  Ids map to (operator, operand pair) by closed-form
+// unranking (triangle rows by a square root and an integer fix-up), so any thread can
+// decode any id in O(1) and rebuild the feature as a postfix program over the primaries.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sisso.h"
+
+namespace sg {
+
+constexpr int kMaxRung = SISSO_MAX_RUNG;
+constexpr int kNumOps = 12;
+constexpr int kMaxSec = kMaxRung * kNumOps;
+constexpr int kMaxDim = SISSO_MAX_DIM;
+constexpr int kProgLen = 16;   // postfix nodes of a rung-3 tree: at most 15
+constexpr double kValueCap = 1e12;     // |v| above this makes a feature invalid
+constexpr double kConstRel = 1e-6;     // std <= 1e-6 max|v|: near-constant, invalid
+constexpr double kScoreTie = 1e-9;     // |rho| within this of the current maximum: tie
+constexpr double kDupTol = 1e-8;       // standardised vectors this close: duplicates
+constexpr double kPivotMin = 1e-12;    // FP64 Cholesky pivot: singular at or below
+constexpr float kPivotMin32 = 1e-5f;   // FP32 pivot at or below: refit in FP64
+constexpr double kRssTie = 1e-12;      // RSS within this * SST of the minimum: tie
+constexpr double kStopRel = 1e-10;     // RMSE <= this * std(y): exact fit, stop
+
+enum Op : int { ADD = 0, SUB, MUL, DIV, EXP, LOG, SQRT, SQ, INV, SIN, CUBE, EXPNEG };
+// kinds of sections: unary on new_{l-1}; symmetric or ordered pairs under either rule
+enum Kind : int { K_UNARY = 0, K_SYM_EQ2, K_DIV_EQ2, K_SYM_NXP, K_DIV_NXP };
+
+struct Section {
+    int64_t base, count;   // first id, number of ids
+    int64_t P, Q;          // |phi_{l-1}|, |phi_{l-2}| (Q = 0 at level 1)
+    int level, op, kind, pad;
+};
+
+struct Space {
+    int d, rung, grammar, nsec;
+    int64_t phi[kMaxRung + 1];   // cumulative sizes |phi_l|
+    Section sec[kMaxSec];
+};
+
+// Largest u with u*m - u(u-1)/2 <= r: the row of rank r in a triangle whose rows have
+// m, m-1, ..., 1 entries.
+__host__ __device__ inline int64_t tri_row(int64_t r, int64_t m) {
+    double b = 2.0 * (double)m + 1.0;
+    double disc = b * b - 8.0 * (double)r;
+    int64_t u = (int64_t)((b - sqrt(disc > 0 ? disc : 0.0)) * 0.5);
+    if (u < 0) u = 0;
+    auto S = [m](int64_t x) { return x * m - x * (x - 1) / 2; };
+    while (u > 0 && S(u) > r) --u;
+    while (S(u + 1) <= r) ++u;
+    return u;
+}
+
+__host__ __device__ inline int64_t tri_start(int64_t u, int64_t m) { return u * m - u * (u - 1) / 2; }
+
+// rank within a section -> operand pair (binary) or operand (unary, b = -1)
+__host__ __device__ inline void unrank(const Section& s, int64_t r, int64_t& a, int64_t& b) {
+    const int64_t P = s.P, Q = s.Q;
+    switch (s.kind) {
+        case K_UNARY: a = Q + r; b = -1; return;
+        case K_SYM_EQ2: {
+            const int64_t A = Q > 0 ? Q - 1 : 0, L0 = P - Q;
+            if (r < A * L0) { a = r / L0; b = Q + r % L0; return; }
+            r -= A * L0;
+            const int64_t m = P - 1 - A;
+            const int64_t u = tri_row(r, m);
+            a = A + u;
+            b = a + 1 + (r - tri_start(u, m));
+            return;
+        }
+        case K_DIV_EQ2: {
+            const int64_t B1 = Q * (P - Q);
+            if (r < B1) { a = r / (P - Q); b = Q + r % (P - Q); return; }
+            r -= B1;
+            a = Q + r / (P - 1);
+            const int64_t jj = r % (P - 1);
+            b = jj < a ? jj : jj + 1;
+            return;
+        }
+        case K_SYM_NXP: a = r / (P - Q); b = Q + r % (P - Q); return;
+        default: {  // K_DIV_NXP
+            const int64_t B1 = Q * (P - Q);
+            if (r < B1) { a = r / (P - Q); b = Q + r % (P - Q); return; }
+            r -= B1;
+            a = Q + r / Q;
+            b = r % Q;
+            return;
+        }
+    }
+}
+
+// operand pair -> rank within a binary section (inverse of unrank)
+__host__ __device__ inline int64_t rank_of(const Section& s, int64_t i, int64_t j) {
+    const int64_t P = s.P, Q = s.Q;
+    switch (s.kind) {
+        case K_SYM_EQ2: {
+            const int64_t A = Q > 0 ? Q - 1 : 0, L0 = P - Q;
+            if (i < A) return i * L0 + (j - Q);
+            const int64_t m = P - 1 - A;
+            return A * L0 + tri_start(i - A, m) + (j - i - 1);
+        }
+        case K_DIV_EQ2:
+            if (i < Q) return i * (P - Q) + (j - Q);
+            return Q * (P - Q) + (i - Q) * (P - 1) + (j < i ? j : j - 1);
+        case K_SYM_NXP: return i * (P - Q) + (j - Q);
+        case K_DIV_NXP:
+            if (i < Q) return i * (P - Q) + (j - Q);
+            return Q * (P - Q) + (i - Q) * Q + j;
+        default: return -1;
+    }
+}
+
+// id -> (level, op, a, b); op = -1 for a primary.  Returns false for an id out of range.
+__host__ __device__ inline bool decode(const Space& sp, int64_t id, int& level, int& op,
+                                       int64_t& a, int64_t& b) {
+    if (id < 0 || id >= sp.phi[sp.rung]) return false;
+    if (id < sp.d) { level = 0; op = -1; a = id; b = -1; return true; }
+    for (int k = 0; k < sp.nsec; ++k) {
+        const Section& s = sp.sec[k];
+        if (id >= s.base && id < s.base + s.count) {
+            level = s.level; op = s.op;
+            unrank(s, id - s.base, a, b);
+            return true;
+        }
+    }
+    return false;
+}
+
+// A feature as a postfix program over the primaries: code >= 0 pushes column `code`,
+// code < 0 applies operator (-code - 1).
+struct Prog {
+    int n;
+    int16_t code[kProgLen];
+};
+
+__host__ __device__ inline bool build_prog_rec(const Space& sp, int64_t id, Prog& p, int depth) {
+    int level, op; int64_t a, b;
+    if (depth > kMaxRung || !decode(sp, id, level, op, a, b)) return false;
+    if (level == 0) { p.code[p.n++] = (int16_t)a; return true; }
+    if (!build_prog_rec(sp, a, p, depth + 1)) return false;
+    if (b >= 0 && !build_prog_rec(sp, b, p, depth + 1)) return false;
+    p.code[p.n++] = (int16_t)(-op - 1);
+    return true;
+}
+
+__host__ __device__ inline bool build_prog(const Space& sp, int64_t id, Prog& p) {
+    p.n = 0;
+    return build_prog_rec(sp, id, p, 0);
+}
+
+template <typename T> __device__ __forceinline__ T op_unary(int op, T z);
+template <> __device__ __forceinline__ float op_unary<float>(int op, float z) {
+    switch (op) {
+        case EXP: return expf(z);
+        case LOG: return logf(z);
+        case SQRT: return sqrtf(z);
+        case SQ: return z * z;
+        case INV: return __frcp_rn(z);
+        case SIN: return sinf(z);
+        case CUBE: return z * z * z;
+        default: return expf(-z);
+    }
+}
+template <> __device__ __forceinline__ double op_unary<double>(int op, double z) {
+    switch (op) {
+        case EXP: return exp(z);
+        case LOG: return log(z);
+        case SQRT: return sqrt(z);
+        case SQ: return z * z;
+        case INV: return 1.0 / z;
+        case SIN: return sin(z);
+        case CUBE: return z * z * z;
+        default: return exp(-z);
+    }
+}
+
+template <typename T> __device__ __forceinline__ T op_binary(int op, T x, T y) {
+    switch (op) {
+        case ADD: return x + y;
+        case SUB: return x - y;
+        case MUL: return x * y;
+        default: return x / y;
+    }
+}
+
+// value of program p at one sample; x(c) returns primary c at that sample
+template <typename T, typename F>
+__device__ __forceinline__ T eval_prog(const Prog& p, F x) {
+    T st[kMaxRung + 2];
+    int top = 0;
+    for (int k = 0; k < p.n; ++k) {
+        const int c = p.code[k];
+        if (c >= 0) {
+            st[top++] = x(c);
+        } else {
+            const int op = -c - 1;
+            if (op >= EXP) {
+                st[top - 1] = op_unary<T>(op, st[top - 1]);
+            } else {
+                const T rhs = st[--top];
+                st[top - 1] = op_binary<T>(op, st[top - 1], rhs);
+            }
+        }
+    }
+    return st[0];
+}
+
+// ------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// moments of the current screening target, computed on the device
+struct TargetStats {
+    double mean, sd;        // FP64 mean and population std of the target
+    double sum32, srr32;    // sum and centred sum of squares of the FP32 copy
+    float sd32, pad;
+};
+
+// small result block of one SIS walk, copied back to the host
+struct WalkResult {
+    int n_acc;              // accepted ids
+    int exhausted;          // ran out of survivors before k were accepted
+    int visited;            // survivors visited
+    int pad;
+    double last_score;      // FP64 score of the last visited candidate
+    int64_t acc[SISSO_MAX_SIS];
+};
+
+struct Winner {
+    int found, pad;
+    int pos[kMaxDim];
+    double rss_gram, rss, rmse, r2;
+    double gamma[kMaxDim];
+    double coef[kMaxDim + 1];
+    int64_t ids[kMaxDim];
+    unsigned long long min_key;   // ordered key of the band minimum (FP32 or FP64 RSS)
+    double thr;                   // band threshold
+    int64_t examined;             // subsets enumerated
+};
+
+}  // namespace sg
+
+struct sisso_ctx {
+    int N, d, rung, k, max_dim;
+    uint32_t ops;
+    sisso_opts opts;
+    sg::Space space;
+    int64_t n_feat;
+    cudaStream_t stream;
+    bool own_stream;
+    std::string err;
+
+    // inputs
+    double* Xc64 = nullptr;    // d x N (column-major: feature c at Xc[c*N + s])
+    float* Xc32 = nullptr;     // d x N
+    double* y64 = nullptr;     // N
+    double* yc64 = nullptr;    // y - mean(y)
+    double ybar = 0, syy = 0;  // mean(y), y~^T y~ / N (computed on the device)
+
+    // screening
+    float* scores = nullptr;           // |phi| FP32 scores
+    double* target64 = nullptr;        // current screening target (N)
+    double* tc64 = nullptr;            // centred target FP64
+    float* tc32 = nullptr;             // centred target FP32
+    sg::TargetStats* tstats = nullptr;
+    unsigned int* hist = nullptr;      // radix-select histograms (3 x 4096)
+    unsigned int* sel_state = nullptr; // radix-select state
+    int64_t surv_cap = 0;              // capacity of the survivor buffers
+    int64_t* surv_ids = nullptr;
+    unsigned int* surv_count = nullptr;
+    double* surv_score = nullptr;      // FP64 re-score
+    double* surv_mean = nullptr;
+    double* surv_sd = nullptr;
+    int* surv_valid = nullptr;
+    int64_t sort_cap = 0;
+    double* sort_score = nullptr;      // sort buffers (power of two)
+    int64_t* sort_id = nullptr;
+    int* sort_src = nullptr;           // index into the survivor arrays
+    unsigned char* removed = nullptr;  // walk: visited flags (sort_cap)
+    sg::WalkResult* walk = nullptr;    // device
+    sg::WalkResult* walk_h = nullptr;  // pinned host
+    int64_t* S_dev = nullptr;          // S ids (device, acceptance order)
+    int64_t* S_sorted = nullptr;       // S ids ascending (device)
+
+    // subspace
+    int n_cap = 0;                     // max |S| = max_dim * k
+    double* Z = nullptr;               // standardised S features, n_cap x N
+    double* Zmean = nullptr;
+    double* Zsd = nullptr;
+    double* G64 = nullptr;             // n_cap x n_cap
+    double* b64 = nullptr;
+    float* G32 = nullptr;
+    float* b32 = nullptr;
+    double* resid = nullptr;           // residual of the best model (N)
+    double* ymom = nullptr;            // [mean(y), syy, sst] on device
+
+    // l0
+    int64_t band_cap = 0;
+    uint64_t* band = nullptr;          // packed positions
+    double* band_rss = nullptr;
+    unsigned int* band_count = nullptr;
+    uint64_t* prefixes = nullptr;
+    int64_t prefix_cap = 0;
+    int* work = nullptr;               // work counters
+    sg::Winner* win = nullptr;         // device
+    sg::Winner* win_h = nullptr;       // pinned host
+    unsigned long long* blk_best = nullptr;  // per-block tie-break winners
+    int blk_cap = 0;
+
+    // results
+    std::vector<int64_t> S;                       // acceptance order
+    std::vector<int> n_sis;                       // accepted per step
+    int n_dims = 0;
+    std::vector<std::vector<int64_t>> res_ids;
+    std::vector<std::vector<double>> res_coef;
+    std::vector<double> res_rmse, res_r2;
+    bool fitted = false;
+    sisso_stats stats{};
+    int sms = 0;
+};
+
+namespace sg {
+
+// host-side helpers implemented in the .cu files
+bool plan_space(int d, uint32_t ops, int rung, int grammar, Space& sp);
+std::string feature_expr(const Space& sp, int64_t id);
+sisso_status fail(sisso_ctx* c, sisso_status st, const std::string& msg);
+sisso_status check_cuda(sisso_ctx* c, cudaError_t e, const char* what);
+
+// screening (sis.cu)
+sisso_status prepare_target(sisso_ctx* c, const double* target_dev);
+sisso_status score_all(sisso_ctx* c, int precision);
+sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_prev,
+                        std::vector<int64_t>& acc);
+sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int precision,
+                           double* out_dev);
+
+// subspace and l0 (l0.cu)
+sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new);
+sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
+                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w);
+sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w);
+
+// timing
+struct PhaseTimer {
+    cudaEvent_t a, b;
+};
+double event_ms(cudaEvent_t a, cudaEvent_t b);
+
+}  // namespace sg

@@ -1,0 +1,662 @@
+// l0.cu — the sparsifying operator (§2.3, Eqs. 7-8) on the device.
+//
+//  Subspace: each new S member is evaluated in FP64 from the primaries and standardised
+//  (rows of Z); the FP64 Gram G = Z Z^T / N and b = Z y~ / N grow by the new rows only.
+//
+//  Enumeration (k_l0_enum): every D-subset {p_0 < ... < p_{D-3} < i1 < i2} is one FP32
+//  (or FP64) Cholesky solve.  A warp owns a prefix (p_0..p_{D-3}) and a run of i1 rows.
+//  It first tabulates, for every x > i1_start, the prefix-reduced row of x:
+//      R[m][x] = (G[x][p_m] - sum_{m'<m} R[m'][x] L[m][m']) / L[m][m],
+//      dpart[x] = G[x][x] - sum_m R[m][x]^2,   npart[x] = b[x] - sum_m R[m][x] w[m],
+//  so that for a pair (i1, i2) only
+//      r = (G[i1][i2] - sum_m R[m][i1] R[m][i2]) / sqrt(dpart[i1]),
+//      d = dpart[i2] - r^2,   num = npart[i2] - r * npart[i1] / sqrt(dpart[i1])
+//  remain, and RSS = N (syy - |w_prefix|^2 - w_i1^2 - num^2 / d).  Lanes own i2 (row i1
+//  of G is read coalesced), i1 is warp-uniform.
+//
+//  FP32 exactness: pass 1 finds UB = min_E (RSS32_E + err_E), pass 2 keeps every subset
+//  with RSS32_E - err_E <= UB (err_E = SST (rho + kappa / min pivot_E)) plus every
+//  subset with a pivot <= 1e-5; the kept band is re-solved in FP64 and the winner is the
+//  lowest FP64 RSS, ties (1e-12 SST) to the smallest ascending global-id tuple — the
+//  same rule as a full FP64 search.  In FP64 mode pass 1 gives the minimum and pass 2
+//  the tie window directly.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cfloat>
+#include <cstring>
+
+namespace sg {
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kRows = 16;                 // i1 rows per work item
+constexpr double kRho = 5e-5;             // FP32 RSS error floor, relative to SST
+constexpr double kKappa = 1e-6;           // FP32 RSS error per unit 1/pivot, rel. to SST
+constexpr float kPivotHi = 1e-2f;         // last pivot below this: exact error bound
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// order-preserving maps of floating values to unsigned integers (for atomicMin)
+__device__ __forceinline__ unsigned long long okey(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_inv(unsigned long long k) {
+    const unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+// ---------------------------------------------------------------------------------
+// subspace: standardised rows and Gram growth
+// ---------------------------------------------------------------------------------
+__global__ void k_standardise(Space sp, const double* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
+                              int row0, double* __restrict__ Z, double* __restrict__ mean_out,
+                              double* __restrict__ sd_out) {
+    __shared__ double red[32];
+    __shared__ double sh_mean, sh_sd;
+    const int row = row0 + blockIdx.x;
+    Prog p;
+    const bool ok = build_prog(sp, ids[row], p);
+    double* z = Z + (size_t)row * N;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = ok ? eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) : 0.0;
+        z[i] = v;
+        s += v;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        sh_mean = t / N;
+    }
+    __syncthreads();
+    const double m = sh_mean;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) { const double v = z[i] - m; ss += v * v; }
+    ss = warp_sum(ss);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        sh_sd = sqrt(t / N);
+        mean_out[row] = m;
+        sd_out[row] = sh_sd;
+    }
+    __syncthreads();
+    const double inv = sh_sd > 0.0 ? 1.0 / sh_sd : 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) z[i] = (z[i] - m) * inv;
+}
+
+// G[i][j] = G[j][i] = Z_i . Z_j / N for i in [n_old, n), j in [0, n); b[i] = Z_i . y~ / N
+__global__ void k_gram_rows(const double* __restrict__ Z, const double* __restrict__ yc, int N, int n_old,
+                            int n, int ld, double* __restrict__ G, double* __restrict__ b,
+                            float* __restrict__ G32, float* __restrict__ b32) {
+    const int i = n_old + blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* zi = Z + (size_t)i * N;
+    for (int j = blockIdx.y * kWarps + w; j <= n; j += gridDim.y * kWarps) {
+        // column n is the moment vector b
+        const double* zj = j < n ? Z + (size_t)j * N : yc;
+        if (j < n && j > i && j >= n_old) continue;   // computed by row j
+        double s = 0.0;
+        for (int t = lane; t < N; t += 32) s += zi[t] * zj[t];
+        s = warp_sum(s) / N;
+        if (lane == 0) {
+            if (j < n) {
+                G[(size_t)i * ld + j] = s;
+                G[(size_t)j * ld + i] = s;
+                G32[(size_t)i * ld + j] = (float)s;
+                G32[(size_t)j * ld + i] = (float)s;
+            } else {
+                b[i] = s;
+                b32[i] = (float)s;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// enumeration
+// ---------------------------------------------------------------------------------
+template <typename T>
+struct EnumArgs {
+    const T* G;                 // n x n (leading dimension ld)
+    const T* b;
+    int ld, n, N;
+    T syy;                      // y~^T y~ / N
+    double sst;                 // N * syy
+    const uint64_t* items;      // packed (prefix, i1 start)
+    int64_t n_items;
+    int* counter;               // work counter
+    float tau;                  // pivots at or below: FP32 -> refit list; FP64 -> singular
+    int fp32;                   // error-bounded FP32 mode
+    unsigned long long* ub_key; // pass 1 output (ordered key of the bound)
+    const Winner* win;          // pass 2 input: win->thr
+    uint64_t* band;
+    unsigned int* band_count;
+    int64_t band_cap;
+    unsigned long long* examined;
+};
+
+template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pre)[DP > 0 ? DP : 1], int i1, int i2) {
+    uint64_t k = 0;
+    int s = 0;
+#pragma unroll
+    for (int m = 0; m < DP; ++m) { k |= (uint64_t)pre[m] << s; s += 16; }
+    k |= (uint64_t)i1 << s; s += 16;
+    k |= (uint64_t)i2 << s;
+    return k;
+}
+
+// MODE 0: bound (min of RSS + err); MODE 1: band collection
+template <typename T, int DP, int MODE>
+__global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = A.n;
+    // per-warp tables: R[DP][n], dpart[n], npart[n]
+    T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)w * (DP + 2) * n;
+    T* Rt = tab;
+    T* dpart = tab + (size_t)DP * n;
+    T* npart = dpart + n;
+    const T N = T(A.N);
+    const T sstT = T(A.sst);
+    T best = T(INFINITY);                 // pass 1: this lane's bound
+    T thr = T(0);
+    if (MODE == 1) thr = T(A.win->thr);
+    unsigned long long my_examined = 0;
+
+    while (true) {
+        int item;
+        if (lane == 0) item = atomicAdd(A.counter, 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= A.n_items) break;
+        const uint64_t key = A.items[item];
+        int pre[DP > 0 ? DP : 1];
+#pragma unroll
+        for (int m = 0; m < DP; ++m) pre[m] = (int)((key >> (16 * m)) & 0xFFFF);
+        const int i1s = (int)((key >> 48) & 0xFFFF);
+        // prefix factor (warp-uniform, redundant in every lane)
+        T L[DP > 0 ? DP : 1][DP > 0 ? DP : 1], invd[DP > 0 ? DP : 1], wv[DP > 0 ? DP : 1];
+        T pw2 = T(0), minpiv = T(1e30);
+        bool pre_ok = true;
+#pragma unroll
+        for (int j = 0; j < DP; ++j) {
+            T dj = A.G[(size_t)pre[j] * A.ld + pre[j]];
+#pragma unroll
+            for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
+            pre_ok = pre_ok && dj > T(A.tau);
+            minpiv = dj < minpiv ? dj : minpiv;
+            const T ljj = sqrt(dj > T(0) ? dj : T(1));
+            L[j][j] = ljj;
+            invd[j] = T(1) / ljj;
+#pragma unroll
+            for (int i = j + 1; i < DP; ++i) {
+                T v = A.G[(size_t)pre[i] * A.ld + pre[j]];
+#pragma unroll
+                for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
+                L[i][j] = v * invd[j];
+            }
+            T v = A.b[pre[j]];
+#pragma unroll
+            for (int m = 0; m < j; ++m) v -= L[j][m] * wv[m];
+            wv[j] = v * invd[j];
+            pw2 += wv[j] * wv[j];
+        }
+        const int i1e = min(i1s + kRows, n - 1);
+        if (MODE == 0 && lane == 0)
+            for (int i1 = i1s; i1 < i1e; ++i1) my_examined += (unsigned long long)(n - 1 - i1);
+        if (!A.fp32 && !pre_ok) continue;      // FP64: singular prefix, every extension skipped
+        // tables for x in [i1s, n)
+        for (int x = i1s + lane; x < n; x += 32) {
+            T r[DP > 0 ? DP : 1];
+            T dp = A.G[(size_t)x * A.ld + x], np = A.b[x];
+#pragma unroll
+            for (int m = 0; m < DP; ++m) {
+                T v = A.G[(size_t)x * A.ld + pre[m]];
+#pragma unroll
+                for (int q = 0; q < m; ++q) v -= r[q] * L[m][q];
+                r[m] = v * invd[m];
+                Rt[(size_t)m * n + x] = r[m];
+                dp -= r[m] * r[m];
+                np -= r[m] * wv[m];
+            }
+            dpart[x] = dp;
+            npart[x] = np;
+        }
+        __syncwarp();
+        for (int i1 = i1s; i1 < i1e; ++i1) {
+            T r1[DP > 0 ? DP : 1];
+#pragma unroll
+            for (int m = 0; m < DP; ++m) r1[m] = Rt[(size_t)m * n + i1];
+            const T d1 = dpart[i1];
+            const bool ok1 = pre_ok && d1 > T(A.tau);
+            if (!A.fp32 && !ok1) continue;
+            const T isd1 = T(1) / sqrt(d1 > T(0) ? d1 : T(1));
+            const T w1 = npart[i1] * isd1;
+            const T pw = pw2 + w1 * w1;
+            const T mp1 = d1 < minpiv ? d1 : minpiv;          // smallest pivot so far
+            // error bound for subsets whose last pivot is >= kPivotHi (FP32 only)
+            T err_u = T(0);
+            if (A.fp32) {
+                const T mp = mp1 < T(kPivotHi) ? mp1 : T(kPivotHi);
+                err_u = sstT * (T(kRho) + T(kKappa) / (mp > T(0) ? mp : T(1e-30)));
+            }
+            const T base_c = A.syy - pw;
+            T c_fast;
+            if (MODE == 0) c_fast = base_c - (best - err_u) / N;
+            else c_fast = base_c - (thr + err_u) / N;
+            const T* Grow = A.G + (size_t)i1 * A.ld;
+            for (int i2 = i1 + 1 + lane; i2 < n; i2 += 32) {
+                T g = Grow[i2];
+#pragma unroll
+                for (int m = 0; m < DP; ++m) g -= r1[m] * Rt[(size_t)m * n + i2];
+                const T rr = g * isd1;
+                const T d2 = dpart[i2] - rr * rr;
+                const T num = npart[i2] - rr * w1;
+                const bool ill = !ok1 || !(d2 > T(A.tau));
+                if (ill) {
+                    if (MODE == 1 && A.fp32) {
+                        const unsigned slot = atomicAdd(A.band_count, 1u);
+                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                    }
+                    continue;
+                }
+                const bool slow = A.fp32 && d2 < T(kPivotHi);
+                if (!slow) {
+                    const T f = num * num - c_fast * d2;
+                    if (MODE == 0 ? !(f > T(0)) : !(f >= T(0))) continue;
+                    if (MODE == 0) {
+                        const T rss = N * (base_c - num * num / d2);
+                        best = rss + err_u;
+                        c_fast = base_c - (best - err_u) / N;
+                    } else {
+                        const unsigned slot = atomicAdd(A.band_count, 1u);
+                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                    }
+                } else {
+                    const T mp = d2 < mp1 ? d2 : mp1;
+                    const T err = sstT * (T(kRho) + T(kKappa) / mp);
+                    const T rss = N * (base_c - num * num / d2);
+                    if (MODE == 0) {
+                        if (rss + err < best) { best = rss + err; c_fast = base_c - (best - err_u) / N; }
+                    } else if (rss - err <= thr) {
+                        const unsigned slot = atomicAdd(A.band_count, 1u);
+                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (MODE == 0) {
+        // lane bounds -> global minimum
+        double bv = (double)best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+        if (lane == 0 && bv < INFINITY) atomicMin(A.ub_key, okey(bv));
+        unsigned long long ex = warp_sum(my_examined);
+        if (lane == 0) atomicAdd(A.examined, ex);
+    }
+}
+
+// D = 1: RSS_i = N (syy - b_i^2 / G_ii)
+template <typename T, int MODE>
+__global__ void k_l0_single(EnumArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    const T d = A.G[(size_t)i * A.ld + i];
+    const T bi = A.b[i];
+    if (MODE == 0) atomicAdd(A.examined, 1ull);
+    if (!(d > T(A.tau))) {
+        if (MODE == 1 && A.fp32) {
+            const unsigned slot = atomicAdd(A.band_count, 1u);
+            if (slot < A.band_cap) A.band[slot] = (uint64_t)i;
+        }
+        return;
+    }
+    const T rss = T(A.N) * (A.syy - bi * bi / d);
+    const T err = A.fp32 ? T(A.sst) * (T(kRho) + T(kKappa) / d) : T(0);
+    if (MODE == 0) {
+        atomicMin(A.ub_key, okey((double)(rss + err)));
+    } else if (rss - err <= T(A.win->thr)) {
+        const unsigned slot = atomicAdd(A.band_count, 1u);
+        if (slot < A.band_cap) A.band[slot] = (uint64_t)i;
+    }
+}
+
+// threshold of pass 2: the bound (+ the FP64 tie window)
+__global__ void k_set_thr(Winner* w, const unsigned long long* ub_key, double add) {
+    const double ub = okey_inv(*ub_key);
+    w->thr = ub + add;
+    w->min_key = *ub_key;
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 refit of the band and the tie-broken winner
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void unpack(uint64_t key, int D, int* pos) {
+    for (int j = 0; j < D; ++j) pos[j] = (int)((key >> (16 * j)) & 0xFFFF);
+}
+
+__device__ double rss64(const double* G, const double* b, int ld, double syy, int N, int D, const int* pos,
+                        double* gamma) {
+    double L[kMaxDim][kMaxDim], w[kMaxDim];
+    for (int j = 0; j < D; ++j) {
+        double dj = G[(size_t)pos[j] * ld + pos[j]];
+        for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
+        if (!(dj > kPivotMin)) return INFINITY;
+        L[j][j] = sqrt(dj);
+        for (int i = j + 1; i < D; ++i) {
+            double v = G[(size_t)pos[i] * ld + pos[j]];
+            for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
+            L[i][j] = v / L[j][j];
+        }
+    }
+    double q = 0.0;
+    for (int j = 0; j < D; ++j) {
+        double v = b[pos[j]];
+        for (int m = 0; m < j; ++m) v -= L[j][m] * w[m];
+        w[j] = v / L[j][j];
+        q += w[j] * w[j];
+    }
+    if (gamma) {   // back substitution L^T gamma = w
+        for (int j = D - 1; j >= 0; --j) {
+            double v = w[j];
+            for (int m = j + 1; m < D; ++m) v -= L[m][j] * gamma[m];
+            gamma[j] = v / L[j][j];
+        }
+    }
+    return (double)N * (syy - q);
+}
+
+__global__ void k_refit(const double* __restrict__ G, const double* __restrict__ b, int ld, double syy, int N,
+                        int D, const uint64_t* __restrict__ band, const unsigned* __restrict__ count, int64_t cap,
+                        double* __restrict__ rss, unsigned long long* min_key) {
+    const int64_t n = (int64_t)*count < cap ? (int64_t)*count : cap;
+    double local = INFINITY;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int pos[kMaxDim];
+        unpack(band[e], D, pos);
+        const double r = rss64(G, b, ld, syy, N, D, pos, nullptr);
+        rss[e] = r;
+        local = fmin(local, r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local = fmin(local, __shfl_xor_sync(0xffffffffu, local, o));
+    if ((threadIdx.x & 31) == 0 && local < INFINITY) atomicMin(min_key, okey(local));
+}
+
+__device__ __forceinline__ void gid_tuple(const int64_t* gid, const int* pos, int D, int64_t* t) {
+    for (int j = 0; j < D; ++j) t[j] = gid[pos[j]];
+    for (int a = 1; a < D; ++a)
+        for (int c = a; c > 0 && t[c - 1] > t[c]; --c) { const int64_t x = t[c]; t[c] = t[c - 1]; t[c - 1] = x; }
+}
+__device__ __forceinline__ bool tuple_less(const int64_t* a, const int64_t* b, int D) {
+    for (int j = 0; j < D; ++j) if (a[j] != b[j]) return a[j] < b[j];
+    return false;
+}
+
+// one block: among refit entries within the tie window of the minimum, the smallest
+// ascending global-id tuple (block-strided scan, then a shared-memory reduction)
+__global__ void k_winner(const uint64_t* __restrict__ band, const double* __restrict__ rss,
+                         const unsigned* __restrict__ count, int64_t cap, const unsigned long long* min_key,
+                         double tie, const int64_t* __restrict__ gid, int D, Winner* W) {
+    __shared__ int64_t best_e[1024];
+    const int64_t n = (int64_t)*count < cap ? (int64_t)*count : cap;
+    const double mn = okey_inv(*min_key);
+    int64_t be = -1;
+    int64_t bt[kMaxDim];
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        if (!(rss[e] <= mn + tie)) continue;
+        int pos[kMaxDim];
+        int64_t t[kMaxDim];
+        unpack(band[e], D, pos);
+        gid_tuple(gid, pos, D, t);
+        if (be < 0 || tuple_less(t, bt, D)) { be = e; for (int j = 0; j < D; ++j) bt[j] = t[j]; }
+    }
+    best_e[threadIdx.x] = be;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t w = -1;
+        int64_t wt[kMaxDim];
+        for (int q = 0; q < (int)blockDim.x; ++q) {
+            const int64_t e = best_e[q];
+            if (e < 0) continue;
+            int pos[kMaxDim];
+            int64_t t[kMaxDim];
+            unpack(band[e], D, pos);
+            gid_tuple(gid, pos, D, t);
+            if (w < 0 || tuple_less(t, wt, D)) { w = e; for (int j = 0; j < D; ++j) wt[j] = t[j]; }
+        }
+        W->found = w >= 0;
+        if (w >= 0) {
+            unpack(band[w], D, W->pos);
+            W->rss_gram = rss[w];
+        }
+    }
+}
+
+// winner's coefficients (original units), residual r* = y~ - Z_E gamma, RMSE, R^2
+__global__ void k_model(const double* __restrict__ G, const double* __restrict__ b, int ld, double syy, int N,
+                        int D, const double* __restrict__ Z, const double* __restrict__ Zmean,
+                        const double* __restrict__ Zsd, const double* __restrict__ yc, double ybar,
+                        const int64_t* __restrict__ gid, Winner* W, double* __restrict__ resid) {
+    __shared__ double gamma[kMaxDim];
+    __shared__ double red[32];
+    if (!W->found) return;
+    if (threadIdx.x == 0) rss64(G, b, ld, syy, N, D, W->pos, gamma);
+    __syncthreads();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double f = yc[i];
+        for (int j = 0; j < D; ++j) f -= gamma[j] * Z[(size_t)W->pos[j] * N + i];
+        resid[i] = f;
+        s += f * f;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rss = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rss += red[w];
+        // ids ascending with their coefficients
+        int order[kMaxDim];
+        for (int j = 0; j < D; ++j) order[j] = j;
+        for (int a = 1; a < D; ++a)
+            for (int c = a; c > 0 && gid[W->pos[order[c - 1]]] > gid[W->pos[order[c]]]; --c) {
+                const int t = order[c]; order[c] = order[c - 1]; order[c - 1] = t;
+            }
+        double c0 = ybar;
+        for (int j = 0; j < D; ++j) {
+            const int q = order[j], p = W->pos[q];
+            const double cj = gamma[q] / Zsd[p];
+            W->ids[j] = gid[p];
+            W->coef[j + 1] = cj;
+            W->gamma[j] = gamma[q];
+            c0 -= cj * Zmean[p];
+        }
+        W->coef[0] = c0;
+        W->rss = rss;
+        W->rmse = sqrt(rss / N);
+        W->r2 = 1.0 - rss / (syy * N);
+    }
+}
+
+}  // namespace
+
+// ===================================================================================
+// host side
+// ===================================================================================
+
+sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new) {
+    if (n_new <= 0) return SISSO_OK;
+    const int n = n_old + n_new;
+    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, c->S_dev, n_old, c->Z, c->Zmean, c->Zsd);
+    dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
+    k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,
+                                                      c->G32, c->b32);
+    c->stats.launches += 2;
+    return check_cuda(c, cudaGetLastError(), "append_subspace");
+}
+
+// work items: (prefix of D-2 positions, first i1 row), most work first
+static void build_items(int n, int D, std::vector<uint64_t>& items) {
+    items.clear();
+    const int DP = D - 2;
+    std::vector<int> pre(std::max(DP, 1));
+    std::vector<std::pair<int, uint64_t>> tmp;
+    auto emit = [&](int last) {
+        uint64_t key = 0;
+        for (int m = 0; m < DP; ++m) key |= (uint64_t)pre[m] << (16 * m);
+        for (int i1 = last + 1; i1 < n - 1; i1 += kRows)
+            tmp.push_back({i1, key | ((uint64_t)i1 << 48)});
+    };
+    if (DP == 0) {
+        emit(-1);
+    } else {
+        // all DP-combinations of [0, n-2)
+        for (int m = 0; m < DP; ++m) pre[m] = m;
+        while (true) {
+            if (pre[DP - 1] <= n - 3) emit(pre[DP - 1]);
+            int j = DP - 1;
+            while (j >= 0 && pre[j] == n - 3 - (DP - 1 - j)) --j;
+            if (j < 0) break;
+            ++pre[j];
+            for (int m = j + 1; m < DP; ++m) pre[m] = pre[m - 1] + 1;
+        }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](auto& a, auto& b) { return a.first < b.first; });
+    items.reserve(tmp.size());
+    for (auto& t : tmp) items.push_back(t.second);
+}
+
+template <typename T>
+static sisso_status run_enum(sisso_ctx* c, EnumArgs<T> A, int D, int mode) {
+    const int DP = D - 2;
+    const size_t smem = (size_t)kWarps * (DP + 2) * A.n * sizeof(T);
+    const int grid = c->sms * 2;
+    cudaMemsetAsync(A.counter, 0, sizeof(int), c->stream);
+#define SG_LAUNCH(DPV, MV)                                                                              \
+    do {                                                                                                \
+        cudaFuncSetAttribute(k_l0_enum<T, DPV, MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_l0_enum<T, DPV, MV><<<grid, kWarps * 32, smem, c->stream>>>(A);                               \
+    } while (0)
+    if (D == 1) {
+        if (mode == 0) k_l0_single<T, 0><<<(A.n + 255) / 256, 256, 0, c->stream>>>(A);
+        else k_l0_single<T, 1><<<(A.n + 255) / 256, 256, 0, c->stream>>>(A);
+    } else if (DP == 0) { if (mode == 0) SG_LAUNCH(0, 0); else SG_LAUNCH(0, 1); }
+    else if (DP == 1) { if (mode == 0) SG_LAUNCH(1, 0); else SG_LAUNCH(1, 1); }
+    else if (DP == 2) { if (mode == 0) SG_LAUNCH(2, 0); else SG_LAUNCH(2, 1); }
+    else return fail(c, SISSO_ERR_ARG, "descriptor dimension above SISSO_MAX_DIM");
+#undef SG_LAUNCH
+    c->stats.launches++;
+    return check_cuda(c, cudaGetLastError(), "l0_enum");
+}
+
+sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
+                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w) {
+    if (D < 1 || D > kMaxDim || n < D) return fail(c, SISSO_ERR_ARG, "l0: bad D or n");
+    if (n > 65535) return fail(c, SISSO_ERR_ARG, "l0: more than 65535 features");
+    const bool fp32 = precision != SISSO_PREC_FP64;
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+    cudaEventRecord(e0, c->stream);
+    // work items
+    std::vector<uint64_t> items;
+    if (D >= 2) build_items(n, D, items);
+    if ((int64_t)items.size() > c->prefix_cap) {
+        if (c->prefixes) cudaFreeAsync(c->prefixes, c->stream);
+        c->prefix_cap = (int64_t)items.size();
+        sisso_status st = check_cuda(c, cudaMallocAsync(&c->prefixes, sizeof(uint64_t) * c->prefix_cap, c->stream), "items");
+        if (st) return st;
+    }
+    if (!items.empty())
+        cudaMemcpyAsync(c->prefixes, items.data(), sizeof(uint64_t) * items.size(), cudaMemcpyHostToDevice, c->stream);
+    unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(c->work + 2);
+    unsigned long long* examined = ub_key + 1;
+    unsigned long long* min_key = ub_key + 2;
+    cudaMemsetAsync(ub_key, 0xFF, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(min_key, 0xFF, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(examined, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->band_count, 0, sizeof(unsigned), c->stream);
+    const double sst = syy * c->N;
+    sisso_status st;
+    if (fp32) {
+        EnumArgs<float> A{};
+        A.G = G32; A.b = b32; A.ld = ld; A.n = n; A.N = c->N; A.syy = (float)syy; A.sst = sst;
+        A.items = c->prefixes; A.n_items = (int64_t)items.size(); A.counter = c->work;
+        A.tau = kPivotMin32; A.fp32 = 1; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
+        A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
+        if ((st = run_enum(c, A, D, 0))) return st;
+        k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, 0.0);
+        cudaEventRecord(e1, c->stream);
+        if ((st = run_enum(c, A, D, 1))) return st;
+    } else {
+        EnumArgs<double> A{};
+        A.G = G; A.b = b; A.ld = ld; A.n = n; A.N = c->N; A.syy = syy; A.sst = sst;
+        A.items = c->prefixes; A.n_items = (int64_t)items.size(); A.counter = c->work;
+        A.tau = (float)kPivotMin; A.fp32 = 0; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
+        A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
+        if ((st = run_enum(c, A, D, 0))) return st;
+        // the FP64 tie window, widened so that rounding differences between this
+        // enumeration and the refit cannot drop a tied subset
+        k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, 2.0 * kRssTie * sst + 1e-14 * sst);
+        cudaEventRecord(e1, c->stream);
+        if ((st = run_enum(c, A, D, 1))) return st;
+    }
+    c->stats.launches++;
+    cudaEventRecord(e2, c->stream);
+    // FP64 refit of the band, minimum, tie-broken winner
+    k_refit<<<c->sms * 4, 256, 0, c->stream>>>(G, b, ld, syy, c->N, D, c->band, c->band_count, c->band_cap,
+                                              c->band_rss, min_key);
+    k_winner<<<1, 1024, 0, c->stream>>>(c->band, c->band_rss, c->band_count, c->band_cap, min_key, kRssTie * sst,
+                                        gid_dev, D, c->win);
+    c->stats.launches += 2;
+    if ((st = check_cuda(c, cudaGetLastError(), "l0_refit"))) return st;
+    unsigned cnt = 0;
+    unsigned long long ex = 0;
+    cudaMemcpyAsync(&cnt, c->band_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&ex, examined, sizeof(ex), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(c->win_h, c->win, sizeof(Winner), cudaMemcpyDeviceToHost, c->stream);
+    if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "l0"))) return st;
+    cudaEvent_t e3;
+    cudaEventCreate(&e3);
+    cudaEventRecord(e3, c->stream);
+    cudaEventSynchronize(e3);
+    c->stats.ms_l0 += event_ms(e0, e2);
+    c->stats.ms_refit += event_ms(e2, e3);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3);
+    if ((int64_t)cnt > c->band_cap)
+        return fail(c, SISSO_ERR_CAPACITY, "l0: FP64 refit band exceeds max_band (" + std::to_string(cnt) + ")");
+    c->stats.subsets_fit += (int64_t)ex;
+    c->stats.subsets_refit += cnt;
+    w = *c->win_h;
+    w.examined = (int64_t)ex;
+    if (!w.found) return fail(c, SISSO_ERR_NUMERIC, "l0: every subset is singular");
+    return SISSO_OK;
+}
+
+sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w) {
+    (void)n;
+    k_model<<<1, 1024, 0, c->stream>>>(c->G64, c->b64, c->n_cap, c->syy, c->N, D, c->Z, c->Zmean, c->Zsd, c->yc64,
+                                       c->ybar, c->S_dev, c->win, c->resid);
+    c->stats.launches++;
+    cudaMemcpyAsync(c->win_h, c->win, sizeof(Winner), cudaMemcpyDeviceToHost, c->stream);
+    sisso_status st = check_cuda(c, cudaStreamSynchronize(c->stream), "winner_model");
+    if (st) return st;
+    w = *c->win_h;
+    return SISSO_OK;
+}
+
+}  // namespace sg

@@ -1,0 +1,775 @@
+// sis.cu — sure independence screening (§2.2, Eqs. 5-6) on the device.
+//
+//  1. k_score_pairs: the fused generate-and-score kernel for the top level's binary
+//     sections (almost all of phi_L).  A CTA owns a 32 x 32 tile of operand pairs; for
+//     each 32-sample chunk it rebuilds the 64 operand features from the primaries
+//     (postfix programs, one warp per feature, lanes over samples) into shared memory,
+//     then every thread accumulates, for 4 pairs x 5 operators (+, -, *, a/b, b/a), the
+//     shifted sums S1 = sum v', S2 = sum v'^2, SR = sum v' r~ with v' = v - v(sample 0).
+//     Nothing but one FP32 score per candidate leaves the CTA.
+//  2. k_score_generic: every other id (lower levels, unary sections), thread per id.
+//  3. Selection: a 3-pass radix select finds the score of the M-th best candidate, the
+//     ids at or above it are compacted, re-scored in FP64 (k_rescore), sorted by
+//     (score desc, id asc) and walked by one CTA (k_walk) with the tie and duplicate
+//     rules.  The host checks that the k-th accepted FP64 score clears the FP32 cut-off
+//     by the FP32 error margin; if not, the window grows and selection repeats.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cfloat>
+#include <cstring>
+
+namespace sg {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_or(int v) { return __any_sync(0xffffffffu, v); }
+
+// sum over a block of blockDim.x threads (multiple of 32); result valid in all threads
+template <typename T> __device__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T r = 0;
+    for (int i = 0; i < nw; ++i) r += red[i];
+    __syncthreads();
+    return r;
+}
+template <typename T> __device__ T block_max(T v, T* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T r = red[0];
+    for (int i = 1; i < nw; ++i) r = max(r, red[i]);
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------
+// target moments: one block
+// ---------------------------------------------------------------------------------
+__global__ void k_prepare_target(const double* __restrict__ t, int N, double* __restrict__ tc64,
+                                 float* __restrict__ tc32, TargetStats* st) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += t[i];
+    const double mean = block_sum(s, red) / N;
+    double ss = 0.0, s32 = 0.0, ss32 = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double c = t[i] - mean;
+        const float f = (float)c;
+        tc64[i] = c;
+        tc32[i] = f;
+        ss += c * c;
+        s32 += (double)f;
+        ss32 += (double)f * (double)f;
+    }
+    ss = block_sum(ss, red);
+    s32 = block_sum(s32, red);
+    ss32 = block_sum(ss32, red);
+    if (threadIdx.x == 0) {
+        st->mean = mean;
+        st->sd = sqrt(ss / N);
+        st->sum32 = s32;
+        st->srr32 = ss32 - s32 * s32 / N;
+        st->sd32 = (float)sqrt(st->srr32 / N);
+    }
+}
+
+// score from shifted sums (v' = v - v0): Pearson |rho| with population moments, or -1
+// when the feature is certainly invalid.  The exact validity rule (every |v| <= 1e12,
+// std > 1e-6 max|v|) is applied by the FP64 re-score; here a feature is rejected only
+// if it must fail it (non-finite sums, |v0| > 1e12, std <= 1e-6 max(|v0|, |mean|)).
+template <typename T>
+__device__ __forceinline__ float finalize(T s1, T s2, T sr, T v0, int N, T sum_t, T sd_t) {
+    const T inv_n = T(1) / T(N);
+    const T ms = s1 * inv_n;
+    const T var = s2 * inv_n - ms * ms;
+    const T cov = sr * inv_n - ms * (sum_t * inv_n);
+    const T mean = v0 + ms;
+    const bool finite = isfinite(s1) && isfinite(s2) && isfinite(sr) && isfinite(v0);
+    if (!finite || !(fabs(v0) <= T(kValueCap)) || !(var > T(0))) return -1.f;
+    const T sd = sqrt(var);
+    const T mx = fabs(v0) > fabs(mean) ? fabs(v0) : fabs(mean);
+    if (!(sd > T(kConstRel) * mx)) return -1.f;
+    return (float)(fabs(cov) / (sd * sd_t));
+}
+
+template <typename T> struct TgtView;
+template <> struct TgtView<float> {
+    __device__ static const float* tc(const float* t32, const double*) { return t32; }
+    __device__ static float sum(const TargetStats* st) { return (float)st->sum32; }
+    __device__ static float sd(const TargetStats* st) { return st->sd32; }
+};
+template <> struct TgtView<double> {
+    __device__ static const double* tc(const float*, const double* t64) { return t64; }
+    __device__ static double sum(const TargetStats*) { return 0.0; }
+    __device__ static double sd(const TargetStats* st) { return st->sd; }
+};
+
+// ---------------------------------------------------------------------------------
+// generic scoring: one thread per id
+// ---------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_score_generic(Space sp, const T* __restrict__ Xc, int N, const float* tc32,
+                                const double* tc64, const TargetStats* st, int64_t id_lo,
+                                int64_t id_hi, float* __restrict__ scores) {
+    const int64_t id = id_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= id_hi) return;
+    Prog p;
+    if (!build_prog(sp, id, p)) { scores[id] = -1.f; return; }
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const T v0 = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; });
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s = 0; s < N; ++s) {
+        const T v = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) - v0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+        sr = fma(v, tc[s], sr);
+    }
+    scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
+// ---------------------------------------------------------------------------------
+// fused generate-and-score for the top level's binary sections
+// ---------------------------------------------------------------------------------
+constexpr int TJ = 32;          // j operands per tile (= lanes)
+constexpr int NG = 8;           // warps per CTA, one group of i operands each
+constexpr int RI = 4;           // i operands per thread
+constexpr int TI = NG * RI;     // i operands per tile
+constexpr int TS = 32;          // samples per chunk
+
+struct PairArgs {
+    Space sp;
+    int sec[4];                 // section index of +, -, *, / at the top level (-1: off)
+    int64_t P, Q;
+    int nxp;
+    int N;
+    const int2* tiles;
+    int n_tiles;
+    float* scores;
+};
+
+// four consecutive values from shared memory (16-byte aligned)
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    const double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+
+template <typename T> __device__ __forceinline__ T rcp(T x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+
+template <typename T>
+struct __align__(16) PairSmem {
+    T at[TS][TI], av[TS][TI], ar[TS][TI];   // i operands: shifted, raw, reciprocal
+    T bt[TS][TJ], bv[TS][TJ], br[TS][TJ];   // j operands
+    T r[TS];                                // centred target chunk
+    T a0[TI], b0[TJ];                       // sample-0 values
+    Prog prog[TI + TJ];
+};
+
+__device__ __forceinline__ bool pair_ok(int64_t i, int64_t j, int64_t P, int64_t Q, int nxp) {
+    if (!(i < j && j < P)) return false;
+    return nxp ? (i < Q && j >= Q) : (j >= Q);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NG * 32, 2)
+k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
+              const double* __restrict__ tc64, const TargetStats* __restrict__ st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    const int N = A.N;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const T sum_t = TgtView<T>::sum(st), sd_t = TgtView<T>::sd(st);
+
+    for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+        const int64_t i0 = A.tiles[tile].x, j0 = A.tiles[tile].y;
+        __syncthreads();
+        // operand programs: i operands first, then j operands
+        if (tid < TI + TJ) {
+            const int64_t f = tid < TI ? i0 + tid : j0 + (tid - TI);
+            Prog& p = S.prog[tid];
+            if (f >= A.P || !build_prog(A.sp, f, p)) p.n = 0;
+        }
+        __syncthreads();
+        // sample-0 values (shifts)
+        if (tid < TI + TJ) {
+            const Prog& p = S.prog[tid];
+            T v = T(0);
+            if (p.n) v = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; });
+            if (tid < TI) S.a0[tid] = v; else S.b0[tid - TI] = v;
+        }
+        __syncthreads();
+
+        const int64_t j = j0 + lane;
+        int64_t iq[RI];
+        bool ok[RI];
+        T Km[RI], Kd[RI], Ke[RI];
+        const T b0 = S.b0[lane];
+        const T rb0 = rcp<T>(b0);
+#pragma unroll
+        for (int q = 0; q < RI; ++q) {
+            iq[q] = i0 + g * RI + q;
+            ok[q] = pair_ok(iq[q], j, A.P, A.Q, A.nxp);
+            const T a0 = S.a0[g * RI + q];
+            Km[q] = a0 * b0;
+            Kd[q] = a0 * rb0;
+            Ke[q] = b0 * rcp<T>(a0);
+        }
+        T s1[5][RI], s2[5][RI], sr[5][RI];
+#pragma unroll
+        for (int o = 0; o < 5; ++o)
+#pragma unroll
+            for (int q = 0; q < RI; ++q) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
+
+        for (int s0 = 0; s0 < N; s0 += TS) {
+            const int ns = min(TS, N - s0);
+            __syncthreads();
+            // stage the chunk: warp g evaluates features g, g+8, ... for 32 samples
+            for (int f = g; f < TI + TJ; f += NG) {
+                const Prog& p = S.prog[f];
+                const int s = s0 + lane;
+                T v = T(0);
+                if (p.n && s < N) v = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; });
+                if (f < TI) {
+                    S.at[lane][f] = v - S.a0[f];
+                    S.av[lane][f] = v;
+                    S.ar[lane][f] = rcp<T>(v);
+                } else {
+                    const int jj = f - TI;
+                    S.bt[lane][jj] = v - S.b0[jj];
+                    S.bv[lane][jj] = v;
+                    S.br[lane][jj] = rcp<T>(v);
+                }
+            }
+            if (tid < TS) S.r[tid] = (s0 + tid < N) ? tc[s0 + tid] : T(0);
+            __syncthreads();
+
+#pragma unroll 2
+            for (int s = 0; s < ns; ++s) {
+                const T r = S.r[s];
+                const T bt = S.bt[s][lane], bv = S.bv[s][lane], br = S.br[s][lane];
+                T at[RI], av[RI], ar[RI];
+                load4(&S.at[s][g * RI], at);
+                load4(&S.av[s][g * RI], av);
+                load4(&S.ar[s][g * RI], ar);
+#pragma unroll
+                for (int q = 0; q < RI; ++q) {
+                    T v;
+                    v = at[q] + bt;            s1[0][q] += v; s2[0][q] = fma(v, v, s2[0][q]); sr[0][q] = fma(v, r, sr[0][q]);
+                    v = at[q] - bt;            s1[1][q] += v; s2[1][q] = fma(v, v, s2[1][q]); sr[1][q] = fma(v, r, sr[1][q]);
+                    v = fma(av[q], bv, -Km[q]); s1[2][q] += v; s2[2][q] = fma(v, v, s2[2][q]); sr[2][q] = fma(v, r, sr[2][q]);
+                    v = fma(av[q], br, -Kd[q]); s1[3][q] += v; s2[3][q] = fma(v, v, s2[3][q]); sr[3][q] = fma(v, r, sr[3][q]);
+                    v = fma(bv, ar[q], -Ke[q]); s1[4][q] += v; s2[4][q] = fma(v, v, s2[4][q]); sr[4][q] = fma(v, r, sr[4][q]);
+                }
+            }
+        }
+
+        // scores of the (up to) 20 candidates of this thread
+#pragma unroll
+        for (int q = 0; q < RI; ++q) {
+            if (!ok[q]) continue;
+            const T a0 = S.a0[g * RI + q];
+            const int64_t i = iq[q];
+            if (A.sec[0] >= 0) {
+                const Section& sc = A.sp.sec[A.sec[0]];
+                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[0][q], s2[0][q], sr[0][q], a0 + b0, N, sum_t, sd_t);
+            }
+            if (A.sec[1] >= 0) {
+                const Section& sc = A.sp.sec[A.sec[1]];
+                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[1][q], s2[1][q], sr[1][q], a0 - b0, N, sum_t, sd_t);
+            }
+            if (A.sec[2] >= 0) {
+                const Section& sc = A.sp.sec[A.sec[2]];
+                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[2][q], s2[2][q], sr[2][q], Km[q], N, sum_t, sd_t);
+            }
+            if (A.sec[3] >= 0) {
+                const Section& sc = A.sp.sec[A.sec[3]];
+                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[3][q], s2[3][q], sr[3][q], Kd[q], N, sum_t, sd_t);
+                A.scores[sc.base + rank_of(sc, j, i)] = finalize<T>(s1[4][q], s2[4][q], sr[4][q], Ke[q], N, sum_t, sd_t);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// radix select of the M-th largest score, then compaction
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned key_of(float s) { return s > 0.f ? __float_as_uint(s) : 0u; }
+
+// state: [0] prefix bits, [1] remaining count, [2] threshold key, [3] 1 if every
+// nonzero key is selected
+__global__ void k_hist(const float* __restrict__ scores, int64_t n, int pass,
+                       const unsigned* __restrict__ state, unsigned* __restrict__ hist) {
+    __shared__ unsigned h[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned prefix = pass ? state[0] : 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned k = key_of(scores[i]);
+        if (k == 0u) continue;
+        if (pass == 0) atomicAdd(&h[k >> 20], 1u);
+        else if (pass == 1) { if ((k >> 20) == prefix) atomicAdd(&h[(k >> 8) & 0xFFFu], 1u); }
+        else { if ((k >> 8) == prefix) atomicAdd(&h[k & 0xFFu], 1u); }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[pass * 4096 + i], h[i]);
+}
+
+__global__ void k_find(const unsigned* __restrict__ hist, int pass, unsigned* state, unsigned M) {
+    if (threadIdx.x != 0) return;
+    const int nb = pass == 2 ? 256 : 4096;
+    unsigned need = pass == 0 ? M : state[1];
+    if (pass > 0 && state[3]) return;
+    unsigned cum = 0;
+    for (int b = nb - 1; b >= 0; --b) {
+        const unsigned c = hist[pass * 4096 + b];
+        if (cum + c >= need) {
+            const unsigned prefix = pass == 0 ? (unsigned)b
+                                  : pass == 1 ? ((state[0] << 12) | (unsigned)b)
+                                              : ((state[0] << 8) | (unsigned)b);
+            state[0] = prefix;
+            state[1] = need - cum;
+            if (pass == 2) state[2] = prefix;
+            return;
+        }
+        cum += c;
+    }
+    // fewer than M nonzero keys: take them all
+    state[3] = 1u;
+    state[2] = 1u;
+}
+
+__global__ void k_compact(const float* __restrict__ scores, int64_t n, const unsigned* __restrict__ state,
+                          int64_t* __restrict__ out, unsigned* count, int64_t cap) {
+    const unsigned thr = state[2];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned k = key_of(scores[i]);
+        if (k != 0u && k >= thr) {
+            const unsigned slot = atomicAdd(count, 1u);
+            if (slot < cap) out[slot] = i;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 re-score: one warp per id, lanes over samples (two passes, as the definition)
+// ---------------------------------------------------------------------------------
+__global__ void k_rescore(Space sp, const double* __restrict__ Xc, int N, const double* __restrict__ tc,
+                          const TargetStats* __restrict__ st, const int64_t* __restrict__ ids, int n,
+                          double* score, double* mean_out, double* sd_out, int* valid_out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n) return;
+    Prog p;
+    const bool built = build_prog(sp, ids[w], p);
+    if (!built) {
+        if (lane == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
+        return;
+    }
+    double s = 0.0, mx = 0.0;
+    int bad = 0;
+    for (int i = lane; i < N; i += 32) {
+        const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; });
+        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
+        s += v;
+        mx = fmax(mx, fabs(v));
+    }
+    bad = warp_or(bad);
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    const double mean = s / N;
+    double ss = 0.0, sc = 0.0;
+    if (!bad) {
+        for (int i = lane; i < N; i += 32) {
+            const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean;
+            ss += v * v;
+            sc += v * tc[i];
+        }
+    }
+    ss = warp_sum(ss);
+    sc = warp_sum(sc);
+    if (lane == 0) {
+        const double sd = sqrt(ss / N);
+        const int ok = !bad && sd > kConstRel * mx;
+        valid_out[w] = ok;
+        mean_out[w] = mean;
+        sd_out[w] = sd;
+        score[w] = ok ? fabs(sc) / ((double)N * sd * st->sd) : -1.0;
+    }
+}
+
+// sort keys: valid survivors not in S get their FP64 score, others -1; padding -2
+__global__ void k_sort_keys(const int64_t* __restrict__ ids, const double* __restrict__ score,
+                            const int* __restrict__ valid, int n, const int64_t* __restrict__ S_sorted,
+                            int nS, int n_pad, double* sk, int64_t* sid, int* ssrc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    if (i >= n) { sk[i] = -2.0; sid[i] = INT64_MAX; ssrc[i] = -1; return; }
+    const int64_t id = ids[i];
+    int lo = 0, hi = nS;            // binary search in S (ascending)
+    while (lo < hi) { const int m = (lo + hi) >> 1; if (S_sorted[m] < id) lo = m + 1; else hi = m; }
+    const bool inS = lo < nS && S_sorted[lo] == id;
+    sk[i] = (valid[i] && !inS) ? score[i] : -1.0;
+    sid[i] = id;
+    ssrc[i] = i;
+}
+
+__device__ __forceinline__ bool before(double sa, int64_t ia, double sb, int64_t ib) {
+    return sa > sb || (sa == sb && ia < ib);
+}
+
+__global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int j) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = i ^ j;
+    if (l <= i) return;
+    const bool up = (i & k) == 0;
+    const double si = sk[i], sl = sk[l];
+    const int64_t ii = sid[i], il = sid[l];
+    const bool swap = up ? before(sl, il, si, ii) : before(si, ii, sl, il);
+    if (swap) {
+        sk[i] = sl; sk[l] = si;
+        sid[i] = il; sid[l] = ii;
+        const int t = ssrc[i]; ssrc[i] = ssrc[l]; ssrc[l] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// the walk: one CTA.  Thread 0 picks, among the remaining candidates whose score is
+// within kScoreTie of the current maximum, the lowest id; the whole CTA then checks it
+// against every S member and accepted id whose score is within kDupScore (a necessary
+// condition for standardised vectors within kDupTol: |rho_a - rho_b| <= |z_a - z_b|_inf)
+// by evaluating both features in FP64 over all samples.
+// ---------------------------------------------------------------------------------
+constexpr int kWalkThreads = 1024;
+constexpr double kDupScore = 2e-8;
+constexpr int kMaxPartners = SISSO_MAX_SIS * (SISSO_MAX_DIM + 1);
+
+__global__ void __launch_bounds__(kWalkThreads)
+k_walk(Space sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk,
+       const int64_t* __restrict__ sid, const int* __restrict__ ssrc, int n_sorted,
+       const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_score,
+       const double* __restrict__ sv_mean, const double* __restrict__ sv_sd, int s_off, int nS,
+       int k, unsigned char* __restrict__ removed, WalkResult* out) {
+    __shared__ int acc_src[SISSO_MAX_SIS];
+    __shared__ int partners[kMaxPartners];
+    __shared__ int n_part, cur, n_acc, done, exhausted, visited;
+    __shared__ double red[32];
+    __shared__ double cur_score, last_score;
+    const int tid = threadIdx.x;
+    if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; last_score = -1.0; }
+    int p = 0;   // thread 0's scan position
+    __syncthreads();
+    while (true) {
+        if (tid == 0) {
+            while (p < n_sorted && removed[p]) ++p;
+            if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
+                done = 1;
+                exhausted = n_acc < k;
+            } else {
+                const double m = sk[p];
+                int best = p;
+                for (int q = p; q < n_sorted && sk[q] >= m - kScoreTie; ++q)
+                    if (!removed[q] && sid[q] < sid[best]) best = q;
+                removed[best] = 1;
+                cur = best;
+                cur_score = sk[best];
+                last_score = sk[best];
+                ++visited;
+            }
+            n_part = 0;
+        }
+        __syncthreads();
+        if (done) break;
+        const int c = cur;
+        const double cs = cur_score;
+        const int csrc = ssrc[c];
+        const int64_t cid = sid[c];
+        for (int q = tid; q < nS + n_acc; q += blockDim.x) {
+            const int src = q < nS ? s_off + q : acc_src[q - nS];
+            if (sv_sd[src] > 0.0 && fabs(sv_score[src] - cs) <= kDupScore) {
+                const int slot = atomicAdd(&n_part, 1);
+                if (slot < kMaxPartners) partners[slot] = src;
+            }
+        }
+        __syncthreads();
+        Prog pc;
+        build_prog(sp, cid, pc);
+        const double mc = sv_mean[csrc], dc = sv_sd[csrc];
+        int dupf = 0;
+        const int np = min(n_part, kMaxPartners);
+        for (int q = 0; q < np; ++q) {
+            const int src = partners[q];
+            Prog pm;
+            build_prog(sp, sv_ids[src], pm);
+            const double mm = sv_mean[src], dm = sv_sd[src];
+            double e1 = 0.0, e2 = 0.0;
+            for (int s = tid; s < N; s += blockDim.x) {
+                const double zc = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + s]; }) - mc) / dc;
+                const double zm = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + s]; }) - mm) / dm;
+                e1 = fmax(e1, fabs(zc - zm));
+                e2 = fmax(e2, fabs(zc + zm));
+            }
+            e1 = block_max(e1, red);
+            e2 = block_max(e2, red);
+            if (e1 <= kDupTol || e2 <= kDupTol) { dupf = 1; break; }
+        }
+        if (tid == 0 && !dupf) {
+            acc_src[n_acc] = csrc;
+            out->acc[n_acc] = cid;
+            ++n_acc;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        out->n_acc = n_acc;
+        out->exhausted = exhausted;
+        out->visited = visited;
+        out->last_score = last_score;
+    }
+}
+
+// features' values (n ids) in FP32 or FP64, one warp per id; out is n x N (FP64)
+template <typename T>
+__global__ void k_eval(Space sp, const T* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
+                       int64_t n, double* __restrict__ out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    Prog p;
+    const bool ok = build_prog(sp, ids[w], p);
+    for (int s = lane; s < N; s += 32)
+        out[w * N + s] = ok ? (double)eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : NAN;
+}
+
+int grid_for(int64_t n, int block, int cap) {
+    const int64_t g = (n + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+}  // namespace
+
+// ===================================================================================
+// host side
+// ===================================================================================
+
+sisso_status prepare_target(sisso_ctx* c, const double* target_dev) {
+    k_prepare_target<<<1, 1024, 0, c->stream>>>(target_dev, c->N, c->tc64, c->tc32, c->tstats);
+    c->stats.launches++;
+    return check_cuda(c, cudaGetLastError(), "prepare_target");
+}
+
+// tiles of the top level's pair set (i tile origin, j tile origin)
+static void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
+    tiles.clear();
+    for (int64_t i0 = 0; i0 < P; i0 += TI) {
+        if (nxp && i0 >= Q) break;
+        int64_t jstart = nxp ? (Q / TJ) * TJ : (i0 / TJ) * TJ;
+        if (!nxp && Q > 0) jstart = std::max<int64_t>(jstart, (Q / TJ) * TJ);
+        for (int64_t j0 = jstart; j0 < P; j0 += TJ) {
+            if (j0 + TJ - 1 <= i0) continue;         // no i < j in the tile
+            if (j0 + TJ <= Q) continue;              // no j >= Q
+            tiles.push_back(make_int2((int)i0, (int)j0));
+        }
+    }
+}
+
+sisso_status score_all(sisso_ctx* c, int precision) {
+    const Space& sp = c->space;
+    const int L = sp.rung;
+    const bool fp64 = precision == SISSO_PREC_FP64;
+    PairArgs A{};
+    A.sp = sp;
+    for (int o = 0; o < 4; ++o) A.sec[o] = -1;
+    A.P = sp.phi[L - 1];
+    A.Q = L >= 2 ? sp.phi[L - 2] : 0;
+    A.nxp = sp.grammar == SISSO_GRAMMAR_NEW_X_PREV && L >= 3;
+    A.N = c->N;
+    A.scores = c->scores;
+    // id ranges outside the top level's binary sections go to the generic kernel
+    std::vector<std::pair<int64_t, int64_t>> ranges;
+    ranges.push_back({0, sp.phi[L - 1]});
+    for (int s = 0; s < sp.nsec; ++s) {
+        const Section& sc = sp.sec[s];
+        if (sc.level == L && sc.op <= DIV) A.sec[sc.op] = s;
+        else if (sc.level == L) ranges.push_back({sc.base, sc.base + sc.count});
+    }
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+    cudaEventRecord(e0, c->stream);
+    for (auto& r : ranges) {
+        const int64_t n = r.second - r.first;
+        if (n <= 0) continue;
+        const int grid = (int)((n + 127) / 128);
+        if (fp64)
+            k_score_generic<double><<<grid, 128, 0, c->stream>>>(sp, c->Xc64, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->scores);
+        else
+            k_score_generic<float><<<grid, 128, 0, c->stream>>>(sp, c->Xc32, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->scores);
+        c->stats.launches++;
+    }
+    sisso_status st = check_cuda(c, cudaGetLastError(), "score_generic");
+    if (st) return st;
+    cudaEventRecord(e1, c->stream);
+    bool any = false;
+    for (int o = 0; o < 4; ++o) any |= A.sec[o] >= 0;
+    if (any) {
+        std::vector<int2> tiles;
+        pair_tiles(A.P, A.Q, A.nxp, tiles);
+        int2* d_tiles = nullptr;
+        st = check_cuda(c, cudaMallocAsync(&d_tiles, sizeof(int2) * tiles.size(), c->stream), "tiles");
+        if (st) return st;
+        cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream);
+        A.tiles = d_tiles;
+        A.n_tiles = (int)tiles.size();
+        const int grid = std::min<int>(A.n_tiles, c->sms * 16);
+        if (fp64) {
+            const size_t sm = sizeof(PairSmem<double>);
+            cudaFuncSetAttribute(k_score_pairs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_score_pairs<double><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc64, c->tc32, c->tc64, c->tstats);
+        } else {
+            const size_t sm = sizeof(PairSmem<float>);
+            cudaFuncSetAttribute(k_score_pairs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_score_pairs<float><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc32, c->tc32, c->tc64, c->tstats);
+        }
+        c->stats.launches++;
+        c->stats.screen_pair_launches++;
+        st = check_cuda(c, cudaGetLastError(), "score_pairs");
+        cudaFreeAsync(d_tiles, c->stream);
+        if (st) return st;
+    }
+    cudaEventRecord(e2, c->stream);
+    cudaEventSynchronize(e2);
+    c->stats.ms_screen += event_ms(e0, e2);
+    c->stats.ms_screen_pair += event_ms(e1, e2);
+    c->stats.candidates_scored += c->n_feat;
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+    return SISSO_OK;
+}
+
+sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int precision, double* out_dev) {
+    const int grid = (int)((n * 32 + 255) / 256);
+    if (precision == SISSO_PREC_FP64)
+        k_eval<double><<<grid, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, ids_dev, n, out_dev);
+    else
+        k_eval<float><<<grid, 256, 0, c->stream>>>(c->space, c->Xc32, c->N, ids_dev, n, out_dev);
+    c->stats.launches++;
+    return check_cuda(c, cudaGetLastError(), "eval_features");
+}
+
+// One SIS step on the scores already in c->scores (against the target prepared by
+// prepare_target).  S_prev_host: S_{t-1} in acceptance order.
+sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_prev,
+                        std::vector<int64_t>& acc) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    sisso_status st = SISSO_OK;
+    // S, ascending, for membership tests; S in order after the survivors for re-scoring
+    std::vector<int64_t> Ss(S_prev_host, S_prev_host + n_prev);
+    std::sort(Ss.begin(), Ss.end());
+    if (n_prev > 0)
+        cudaMemcpyAsync(c->S_sorted, Ss.data(), sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
+    const bool fp_kernel64 = c->opts.precision == SISSO_PREC_FP64;
+    const double eps = fp_kernel64 ? 1e-6 : 2e-4;   // bound on |score_kernel - score_FP64|
+    int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(16384, 64LL * k);
+    const int64_t n = c->n_feat;
+    const int gridS = std::max(1, c->sms * 8);
+    while (true) {
+        M = std::min<int64_t>(M, c->surv_cap - n_prev);
+        cudaMemsetAsync(c->hist, 0, sizeof(unsigned) * 3 * 4096, c->stream);
+        cudaMemsetAsync(c->sel_state, 0, sizeof(unsigned) * 4, c->stream);
+        cudaMemsetAsync(c->surv_count, 0, sizeof(unsigned), c->stream);
+        for (int pass = 0; pass < 3; ++pass) {
+            k_hist<<<gridS, kBlock, 0, c->stream>>>(c->scores, n, pass, c->sel_state, c->hist);
+            k_find<<<1, 32, 0, c->stream>>>(c->hist, pass, c->sel_state, (unsigned)M);
+            c->stats.launches += 2;
+        }
+        k_compact<<<gridS, kBlock, 0, c->stream>>>(c->scores, n, c->sel_state, c->surv_ids, c->surv_count,
+                                                   c->surv_cap - n_prev);
+        c->stats.launches++;
+        unsigned h_state[4], h_count = 0;
+        cudaMemcpyAsync(h_state, c->sel_state, sizeof(h_state), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(&h_count, c->surv_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+        if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "select"))) break;
+        if ((int64_t)h_count > c->surv_cap - n_prev) {
+            st = fail(c, SISSO_ERR_CAPACITY, "screening window overflow (tied scores)");
+            break;
+        }
+        const int ns = (int)h_count;
+        const bool all = h_state[3] != 0;
+        float t32 = 0.f;
+        if (!all) std::memcpy(&t32, &h_state[2], sizeof(float));
+        // re-score survivors and S members in FP64
+        if (n_prev > 0)
+            cudaMemcpyAsync(c->surv_ids + ns, S_prev_host, sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
+        const int nr = ns + n_prev;
+        k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, c->tc64, c->tstats,
+                                                                 c->surv_ids, nr, c->surv_score, c->surv_mean,
+                                                                 c->surv_sd, c->surv_valid);
+        int n_pad = 1;
+        while (n_pad < std::max(ns, 1)) n_pad <<= 1;
+        k_sort_keys<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->surv_ids, c->surv_score, c->surv_valid, ns,
+                                                                 c->S_sorted, n_prev, n_pad, c->sort_score,
+                                                                 c->sort_id, c->sort_src);
+        c->stats.launches += 2;
+        for (int kk = 2; kk <= n_pad; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                k_bitonic<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_id, c->sort_src, n_pad, kk, j);
+                c->stats.launches++;
+            }
+        cudaMemsetAsync(c->removed, 0, (size_t)n_pad, c->stream);
+        k_walk<<<1, kWalkThreads, 0, c->stream>>>(c->space, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
+                                                  n_pad, c->surv_ids, c->surv_score, c->surv_mean, c->surv_sd,
+                                                  ns, n_prev, k, c->removed, c->walk);
+        c->stats.launches++;
+        cudaMemcpyAsync(c->walk_h, c->walk, sizeof(WalkResult), cudaMemcpyDeviceToHost, c->stream);
+        if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "walk"))) break;
+        c->stats.survivors_rescored += nr;
+        const WalkResult& w = *c->walk_h;
+        // exact iff every candidate outside the window scores (FP64) below the last
+        // accepted one by more than the tie tolerance
+        const bool safe = all || (w.n_acc == k && w.last_score - kScoreTie > (double)t32 + eps);
+        const bool can_grow = M < c->surv_cap - n_prev;
+        if (safe || !can_grow) {
+            if (!safe) c->stats.window_saturated = 1;
+            acc.assign(w.acc, w.acc + w.n_acc);
+            break;
+        }
+        M *= 4;
+        c->stats.window_grown++;
+    }
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    c->stats.ms_select += event_ms(e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace sg

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of the C ABI in ``include/sisso.h`` (argument marshalling only).
+
+Every computation happens in the CUDA library; this module only converts arguments.
+Arrays may be numpy arrays (host memory) or CUDA tensors (device memory, passed by
+pointer).  If the shared library is missing, loading it raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsisso_gb300.so")
+
+# operator bits and enums of include/sisso.h
+OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_EXP, OP_LOG, OP_SQRT, OP_SQ, OP_INV, OP_SIN, OP_CUBE, OP_EXPNEG = (
+    1 << i for i in range(12))
+PREC_FP64, PREC_FP32 = 0, 1
+GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
+MAX_DIM, MAX_SIS, MAX_RUNG = 4, 1024, 3
+STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
+          -4: "SISSO_ERR_NUMERIC", -5: "SISSO_ERR_TIMEOUT", -6: "SISSO_ERR_STATE",
+          -7: "SISSO_ERR_CAPACITY"}
+
+# every entry point the header declares (checked by the tests)
+EXPORTS = [
+    "sisso_default_opts", "sisso_create", "sisso_fit", "sisso_get_n_dims", "sisso_get_descriptor",
+    "sisso_get_sis", "sisso_feature_count", "sisso_feature_expr", "sisso_get_stats",
+    "sisso_last_error", "sisso_destroy", "sisso_eval_features", "sisso_score_all",
+    "sisso_sis_step", "sisso_l0_search", "sisso_space_sizes", "sisso_space_expr",
+]
+
+
+class SissoError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("grammar", C.c_int), ("survivors", C.c_int),
+                ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("device", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("candidates_scored", C.c_int64), ("subsets_fit", C.c_int64),
+                ("subsets_refit", C.c_int64), ("survivors_rescored", C.c_int64),
+                ("window_grown", C.c_int), ("window_saturated", C.c_int), ("launches", C.c_int),
+                ("ms_screen", C.c_double), ("ms_screen_pair", C.c_double),
+                ("screen_pair_launches", C.c_int), ("ms_select", C.c_double),
+                ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
+                ("ms_fit", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2410_01752_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64p, dp = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    L.sisso_default_opts.argtypes = [C.POINTER(Opts)]
+    L.sisso_default_opts.restype = None
+    L.sisso_create.argtypes = [vp, vp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                               C.POINTER(Opts), C.POINTER(vp)]
+    L.sisso_fit.argtypes = [vp]
+    L.sisso_get_n_dims.argtypes = [vp, C.POINTER(C.c_int)]
+    L.sisso_get_descriptor.argtypes = [vp, C.c_int, i64p, dp, dp, dp]
+    L.sisso_get_sis.argtypes = [vp, C.c_int, i64p, C.c_int, C.POINTER(C.c_int)]
+    L.sisso_feature_count.argtypes = [vp, i64p, i64p]
+    L.sisso_feature_expr.argtypes = [vp, C.c_int64, C.c_char_p, C.c_size_t]
+    L.sisso_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.sisso_last_error.argtypes = [vp]
+    L.sisso_last_error.restype = C.c_char_p
+    L.sisso_destroy.argtypes = [vp]
+    L.sisso_destroy.restype = None
+    L.sisso_eval_features.argtypes = [vp, vp, C.c_int64, C.c_int, vp]
+    L.sisso_score_all.argtypes = [vp, vp, C.c_int, vp]
+    L.sisso_sis_step.argtypes = [vp, vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int)]
+    L.sisso_l0_search.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, C.c_int,
+                                  C.POINTER(C.c_int), dp, i64p]
+    L.sisso_space_sizes.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, i64p]
+    L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
+    for name in EXPORTS:
+        if name not in ("sisso_default_opts", "sisso_last_error", "sisso_destroy"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive) for a numpy array or a CUDA tensor of the given dtype."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        want = {np.float64: torch.float64, np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            a = a.to(want).contiguous()
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def space_sizes(d: int, op_set: int, rung: int, grammar: int = GRAMMAR_EQ2) -> list[int]:
+    """|phi_l| for l = 0..rung (host only)."""
+    out = np.zeros(rung + 1, dtype=np.int64)
+    st = load().sisso_space_sizes(d, op_set, rung, grammar, out.ctypes.data_as(C.POINTER(C.c_int64)))
+    if st:
+        raise SissoError(st, "space_sizes")
+    return [int(v) for v in out]
+
+
+def space_expr(d: int, op_set: int, rung: int, grammar: int, fid: int) -> str:
+    """Expression of feature ``fid`` (host only)."""
+    buf = C.create_string_buffer(8192)
+    st = load().sisso_space_expr(d, op_set, rung, grammar, fid, buf, 8192)
+    if st:
+        raise SissoError(st, "space_expr")
+    return buf.value.decode()
+
+
+@dataclass
+class Descriptor:
+    ids: list[int]
+    coef: list[float]        # [intercept, c_1, ..., c_t] aligned with ids
+    rmse: float
+    r2: float
+
+
+class Sisso:
+    """One SISSO problem on one GPU: ``Sisso(X, y, ...).fit()``."""
+
+    def __init__(self, X, y, op_set: int, rung: int, sis_size: int, max_dim: int,
+                 precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
+                 max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0):
+        L = load()
+        self._ctx = C.c_void_p()
+        N, d = int(X.shape[0]), int(X.shape[1])
+        xp, self._x = _ptr(X, np.float64)
+        yp, self._y = _ptr(y, np.float64)
+        o = Opts()
+        L.sisso_default_opts(C.byref(o))
+        o.precision, o.grammar, o.survivors = precision, grammar, survivors
+        o.max_band, o.band_rel, o.device = max_band, band_rel, device
+        if stream is not None:
+            o.cuda_stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
+        st = L.sisso_create(xp, yp, N, d, op_set, rung, sis_size, max_dim, C.byref(o), C.byref(self._ctx))
+        if st != 0:
+            raise SissoError(st, "sisso_create")
+        self.N, self.d, self.max_dim = N, d, max_dim
+        self._x = self._y = None
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise SissoError(st, f"{what}: {load().sisso_last_error(self._ctx).decode()}")
+
+    def fit(self) -> list[Descriptor]:
+        self._check(load().sisso_fit(self._ctx), "sisso_fit")
+        return self.descriptors()
+
+    def descriptors(self) -> list[Descriptor]:
+        L = load()
+        n = C.c_int()
+        self._check(L.sisso_get_n_dims(self._ctx, C.byref(n)), "get_n_dims")
+        out = []
+        for t in range(1, n.value + 1):
+            ids = np.zeros(t, dtype=np.int64)
+            coef = np.zeros(t + 1, dtype=np.float64)
+            rmse, r2 = C.c_double(), C.c_double()
+            self._check(L.sisso_get_descriptor(self._ctx, t, ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                               coef.ctypes.data_as(C.POINTER(C.c_double)),
+                                               C.byref(rmse), C.byref(r2)), "get_descriptor")
+            out.append(Descriptor([int(v) for v in ids], [float(v) for v in coef], rmse.value, r2.value))
+        return out
+
+    def sis(self, step: int) -> list[int]:
+        buf = np.zeros(MAX_SIS, dtype=np.int64)
+        n = C.c_int()
+        self._check(load().sisso_get_sis(self._ctx, step, buf.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         MAX_SIS, C.byref(n)), "get_sis")
+        return [int(v) for v in buf[: n.value]]
+
+    def feature_count(self) -> tuple[int, list[int]]:
+        n = C.c_int64()
+        sizes = np.zeros(MAX_RUNG + 1, dtype=np.int64)
+        self._check(load().sisso_feature_count(self._ctx, C.byref(n), sizes.ctypes.data_as(C.POINTER(C.c_int64))),
+                    "feature_count")
+        return n.value, [int(v) for v in sizes]
+
+    def expr(self, fid: int) -> str:
+        buf = C.create_string_buffer(8192)
+        self._check(load().sisso_feature_expr(self._ctx, fid, buf, 8192), "feature_expr")
+        return buf.value.decode()
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(load().sisso_get_stats(self._ctx, C.byref(s)), "get_stats")
+        return s.as_dict()
+
+    # ---- kernel-level entry points ----
+    def eval_features(self, ids, precision: int = PREC_FP64) -> np.ndarray:
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        out = np.zeros((ids.size, self.N), dtype=np.float64)
+        self._check(load().sisso_eval_features(self._ctx, C.c_void_p(ids.ctypes.data), ids.size, precision,
+                                               C.c_void_p(out.ctypes.data)), "eval_features")
+        return out
+
+    def score_all(self, target, precision: int = PREC_FP32) -> np.ndarray:
+        n, _ = self.feature_count()
+        out = np.zeros(n, dtype=np.float32)
+        tp, keep = _ptr(target, np.float64)
+        self._check(load().sisso_score_all(self._ctx, tp, precision, C.c_void_p(out.ctypes.data)), "score_all")
+        del keep
+        return out
+
+    def sis_step(self, target, S_prev, k: int) -> list[int]:
+        tp, keep = _ptr(target, np.float64)
+        Sp = np.ascontiguousarray(np.asarray(S_prev, dtype=np.int64).reshape(-1))
+        acc = np.zeros(k, dtype=np.int64)
+        n = C.c_int()
+        self._check(load().sisso_sis_step(self._ctx, tp, C.c_void_p(Sp.ctypes.data) if Sp.size else None,
+                                          Sp.size, k, acc.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(n)),
+                    "sis_step")
+        del keep
+        return [int(v) for v in acc[: n.value]]
+
+    def l0_search(self, G, b, syy: float, D: int, gid, precision: int = PREC_FP32):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        gid = np.ascontiguousarray(gid, dtype=np.int64)
+        pos = np.zeros(D, dtype=np.int32)
+        rss, ex = C.c_double(), C.c_int64()
+        self._check(load().sisso_l0_search(self._ctx, C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data),
+                                           float(syy), b.size, D, C.c_void_p(gid.ctypes.data), precision,
+                                           pos.ctypes.data_as(C.POINTER(C.c_int)), C.byref(rss), C.byref(ex)),
+                    "l0_search")
+        return [int(p) for p in pos], rss.value, ex.value
+
+    def close(self):
+        if self._ctx:
+            load().sisso_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
