@@ -15,7 +15,9 @@
  *    partner set by one operand in new_{l-1} and the other in phi_{l-2}.
  *  - Canonical id order: level, then operator in table order, then (i, j) lexicographic.
  *  - Validity: a feature is invalid if any value is non-finite or |v| > 1e12, or if its
- *    population std <= 1e-6 * max|v| (near-constant).
+ *    population std <= 1e-6 * max|v| (near-constant), or if it is identically zero: its
+ *    root operator is + or - and max|v| <= 1e-9 * max(|a| + |b|) over the samples (the
+ *    operands cancel to rounding noise, e.g. x1 - (x3 + (x1 - x3))).
  *  - SIS score (§2.2 Eqs. 5-6): Pearson |rho| with population moments; this ranks the
  *    same as |Phi^T y| on standardised columns.  Walk: repeatedly take, among the
  *    remaining candidates whose score is within 1e-9 of the current maximum, the lowest
@@ -48,6 +50,7 @@
 #define PIVOT_MIN 1e-12
 #define RSS_TIE 1e-12
 #define STOP_REL 1e-10
+#define CANCEL_REL 1e-9
 
 /* ------------------------------------------------------------------------------------ */
 /* feature space (§2.1)                                                                  */
@@ -254,6 +257,27 @@ static int eval_rec(const space_t* s, const double* X, int N, int64_t id, double
     return 0;
 }
 
+/* values of feature id and, when its root operator is + or -, whether the operands cancel
+   to rounding noise at every sample (an identically zero feature) */
+static int eval_checked(const space_t* s, const double* X, int N, int64_t id, double* out, int* cancelled) {
+    int level, op; int64_t a, b;
+    *cancelled = 0;
+    if (decode(s, id, &level, &op, &a, &b)) return -1;
+    if (level == 0 || (op != ORC_ADD && op != ORC_SUB)) return eval_rec(s, X, N, id, out);
+    double* va = (double*)malloc(sizeof(double) * (size_t)N);
+    double* vb = (double*)malloc(sizeof(double) * (size_t)N);
+    int rc = eval_rec(s, X, N, a, va) || eval_rec(s, X, N, b, vb);
+    double mv = 0.0, mo = 0.0;
+    for (int i = 0; i < N && !rc; i++) {
+        out[i] = apply_binary(op, va[i], vb[i]);
+        if (fabs(out[i]) > mv) mv = fabs(out[i]);
+        if (fabs(va[i]) + fabs(vb[i]) > mo) mo = fabs(va[i]) + fabs(vb[i]);
+    }
+    *cancelled = !rc && mv <= CANCEL_REL * mo;
+    free(va); free(vb);
+    return rc ? -1 : 0;
+}
+
 int oracle_eval(int d, uint32_t ops, int rung, int grammar, const double* X, int N, int64_t id, double* out) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar)) return -1;
@@ -300,7 +324,9 @@ static void* score_worker(void* p) {
     for (int64_t q = j->begin; q < j->end; q++) {
         int64_t id = j->ids ? j->ids[q] : q;
         double m, sd;
-        int ok = (eval_rec(j->s, j->X, j->N, id, v) == 0) && moments(v, j->N, &m, &sd);
+        int cancelled;
+        int ok = (eval_checked(j->s, j->X, j->N, id, v, &cancelled) == 0) && !cancelled &&
+                 moments(v, j->N, &m, &sd);
         j->valid[q] = ok;
         j->score[q] = ok ? pearson(v, j->N, m, sd, j->tc, j->tsd) : 0.0;
     }
@@ -355,7 +381,8 @@ int oracle_scores(int d, uint32_t ops, int rung, int grammar, const double* X, i
 /* standardised vector z = (v - mean)/sd of a valid feature; returns 0 if valid */
 static int standardised(const space_t* s, const double* X, int N, int64_t id, double* z) {
     double m, sd;
-    if (eval_rec(s, X, N, id, z) || !moments(z, N, &m, &sd)) return -1;
+    int cancelled;
+    if (eval_checked(s, X, N, id, z, &cancelled) || cancelled || !moments(z, N, &m, &sd)) return -1;
     for (int i = 0; i < N; i++) z[i] = (z[i] - m) / sd;
     return 0;
 }

@@ -74,9 +74,15 @@ def to_str(f) -> str:
             "^-1": f"({a})^-1", "sin": f"sin({a})", "^3": f"({a})^3", "exp-": f"exp(-{a})"}[op]
 
 
-def valid(v: np.ndarray) -> bool:
+def valid(v: np.ndarray, f=None, X=None) -> bool:
+    """Validity; with the feature tree f and X given, also the identically-zero rule
+    (root + or - whose operands cancel to rounding noise)."""
     if not np.all(np.isfinite(v)) or np.max(np.abs(v)) > 1e12:
         return False
+    if f is not None and f[0] in ("+", "-"):
+        mag = np.abs(evaluate(f[1], X)) + np.abs(evaluate(f[2], X))
+        if np.max(np.abs(v)) <= 1e-9 * np.max(mag):
+            return False
     return float(np.std(v)) > 1e-6 * float(np.max(np.abs(v)))
 
 
@@ -88,12 +94,16 @@ def standardise(v: np.ndarray) -> np.ndarray:
     return (v - v.mean()) / v.std()
 
 
-def sis(values: list[np.ndarray], target: np.ndarray, S_prev: list[int], k: int) -> list[int]:
+def sis(values: list[np.ndarray], target: np.ndarray, S_prev: list[int], k: int,
+        ok: list[bool] | None = None) -> list[int]:
     """SIS step (§2.2 Eqs. 5-6) by brute force, with the tie-tolerant walk and the
-    duplicate rule (standardised vectors equal up to sign within 1e-8)."""
+    duplicate rule (standardised vectors equal up to sign within 1e-8).  ok[i]: validity
+    of feature i (default: the value rules only)."""
+    if ok is None:
+        ok = [valid(v) for v in values]
     cand = [(abs_corr(v, target), i) for i, v in enumerate(values)
-            if valid(v) and i not in S_prev]
-    refs = [standardise(values[i]) for i in S_prev if valid(values[i])]
+            if ok[i] and i not in S_prev]
+    refs = [standardise(values[i]) for i in S_prev if ok[i]]
     remaining = sorted(cand, key=lambda c: (-c[0], c[1]))
     acc = []
     while remaining and len(acc) < k:
@@ -134,11 +144,12 @@ def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: in
     of the best t-term lstsq fit; l0 over all t-subsets of S_t."""
     feats, _ = space(d, ops, rung, new_x_prev)
     values = [evaluate(f, X) for f in feats]
+    ok = [valid(v, f, X) for v, f in zip(values, feats)]
     S: list[int] = []
     out = []
     target = y.copy()
     for t in range(1, T + 1):
-        S = S + sis(values, target, S, k)
+        S = S + sis(values, target, S, k, ok)
         if len(S) < t:
             break
         cols = np.column_stack([values[i] for i in S])

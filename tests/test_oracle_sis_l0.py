@@ -25,7 +25,7 @@ def test_scores_match_numpy_corrcoef(orc):
     n_invalid = 0
     for i, f in enumerate(feats):
         v = brute.evaluate(f, X)
-        assert va[i] == brute.valid(v), brute.to_str(f)
+        assert va[i] == brute.valid(v, f, X), brute.to_str(f)
         if va[i]:
             assert sc[i] == pytest.approx(brute.abs_corr(v, y), abs=1e-12)
         else:
@@ -54,13 +54,36 @@ def test_sis_matches_brute_force(orc, seed, k):
     names = ["+", "-", "*", "/", "sqrt", "^2"]
     feats, _ = brute.space(3, names, 2)
     values = [brute.evaluate(f, X) for f in feats]
+    ok = [brute.valid(v, f, X) for v, f in zip(values, feats)]
     sp = orc.Space(3, _mask(orc, names), 2)
     acc1 = sp.sis(X, y, [], k)
-    assert acc1 == brute.sis(values, y, [], k)
+    assert acc1 == brute.sis(values, y, [], k, ok)
     r = y - np.polyval(np.polyfit(values[acc1[0]], y, 1), values[acc1[0]])
     acc2 = sp.sis(X, r, acc1, k)
-    assert acc2 == brute.sis(values, r, acc1, k)
+    assert acc2 == brute.sis(values, r, acc1, k, ok)
     assert not set(acc1) & set(acc2)
+
+
+def test_identically_zero_features_are_invalid(orc):
+    """Features whose root + or - cancels exactly (x1-(x3+(x1-x3)), x1*x2-(x2*x4)/(x4/x1))
+    are invalid, whatever score their rounding noise would get; a small but genuine
+    difference of nearly collinear primaries stays valid."""
+    rng = np.random.default_rng(6)
+    X = rng.lognormal(0, 0.5, size=(60, 4))
+    y = rng.normal(size=60)
+    names = ["+", "-", "*", "/"]
+    sp = orc.Space(4, _mask(orc, names), 3, orc.GRAMMAR_NEW_X_PREV)
+    ids = {sp.expr(i): i for i in range(sp.n_features)}
+    zero = ["(x1-(x3+(x1-x3)))", "((x1*x2)-((x2*x4)/(x4/x1)))"]
+    sc, va = sp.scores(X, y, [ids[e] for e in zero])
+    assert not va.any()
+    for e in zero:                          # their values really are rounding noise
+        v = sp.eval(X, ids[e])
+        assert np.abs(v).max() < 1e-13
+    Xc = X.copy()
+    Xc[:, 1] = Xc[:, 0] + 1e-4 * rng.normal(size=60)   # corr ~ 0.99999
+    sc, va = sp.scores(Xc, y, [ids["(x1-x2)"]])
+    assert va.all()
 
 
 def test_sis_duplicates_are_skipped(orc):
