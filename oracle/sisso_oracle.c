@@ -17,7 +17,10 @@
  *  - Validity: a feature is invalid if any value is non-finite or |v| > 1e12, or if its
  *    population std <= 1e-6 * max|v| (near-constant), or if it is identically zero: its
  *    root operator is + or - and max|v| <= 1e-9 * max(|a| + |b|) over the samples (the
- *    operands cancel to rounding noise, e.g. x1 - (x3 + (x1 - x3))).
+ *    operands cancel to rounding noise, e.g. x1 - (x3 + (x1 - x3))).  Validity is
+ *    recursive: a feature built from an invalid feature is invalid (§2.1 builds level l
+ *    from the features of level l-1; log(x2 * x2^-1), the log of a constant, is not a
+ *    feature).  Ids do not depend on validity: the enumeration stays data independent.
  *  - SIS score (§2.2 Eqs. 5-6): Pearson |rho| with population moments; this ranks the
  *    same as |Phi^T y| on standardised columns.  Walk: repeatedly take, among the
  *    remaining candidates whose score is within 1e-9 of the current maximum, the lowest
@@ -310,6 +313,21 @@ static double pearson(const double* v, int N, double mean, double sd, const doub
     return fabs(c) / ((double)N * sd * tsd);
 }
 
+/* own rules on the values of feature id (finite, |v| <= 1e12, not identically zero, not
+   near-constant), then recursively the same for its operands */
+static int valid_rec(const space_t* s, const double* X, int N, int64_t id) {
+    int level, op; int64_t a, b;
+    if (decode(s, id, &level, &op, &a, &b)) return 0;
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    double m, sd;
+    int cancelled;
+    int ok = eval_checked(s, X, N, id, v, &cancelled) == 0 && !cancelled && moments(v, N, &m, &sd);
+    free(v);
+    if (!ok) return 0;
+    if (level == 0) return 1;
+    return valid_rec(s, X, N, a) && (b < 0 || valid_rec(s, X, N, b));
+}
+
 typedef struct {
     const space_t* s; const double* X; int N;
     const double* tc; double tsd;
@@ -324,9 +342,12 @@ static void* score_worker(void* p) {
     for (int64_t q = j->begin; q < j->end; q++) {
         int64_t id = j->ids ? j->ids[q] : q;
         double m, sd;
-        int cancelled;
+        int cancelled, level, op;
+        int64_t a, b;
         int ok = (eval_checked(j->s, j->X, j->N, id, v, &cancelled) == 0) && !cancelled &&
                  moments(v, j->N, &m, &sd);
+        if (ok && decode(j->s, id, &level, &op, &a, &b) == 0 && level > 0)
+            ok = valid_rec(j->s, j->X, j->N, a) && (b < 0 || valid_rec(j->s, j->X, j->N, b));
         j->valid[q] = ok;
         j->score[q] = ok ? pearson(v, j->N, m, sd, j->tc, j->tsd) : 0.0;
     }

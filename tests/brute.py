@@ -76,14 +76,19 @@ def to_str(f) -> str:
 
 def valid(v: np.ndarray, f=None, X=None) -> bool:
     """Validity; with the feature tree f and X given, also the identically-zero rule
-    (root + or - whose operands cancel to rounding noise)."""
+    (root + or - whose operands cancel to rounding noise) and, recursively, the validity
+    of every operand."""
     if not np.all(np.isfinite(v)) or np.max(np.abs(v)) > 1e12:
         return False
     if f is not None and f[0] in ("+", "-"):
         mag = np.abs(evaluate(f[1], X)) + np.abs(evaluate(f[2], X))
         if np.max(np.abs(v)) <= 1e-9 * np.max(mag):
             return False
-    return float(np.std(v)) > 1e-6 * float(np.max(np.abs(v)))
+    if not float(np.std(v)) > 1e-6 * float(np.max(np.abs(v))):
+        return False
+    if f is not None and f[0] != "x":
+        return all(valid(evaluate(ch, X), ch, X) for ch in f[1:])
+    return True
 
 
 def abs_corr(v: np.ndarray, t: np.ndarray) -> float:

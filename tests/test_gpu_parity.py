@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Bars: feature ids (SIS selections, descriptors, l0 winners) bit-exact; FP64 kernel
-values/scores within 1e-9; FP32 screening scores within the 2e-4 margin the selection's
+values within 1e-12 relative, their scores within 1e-7 (the score buffer is FP32); FP32
+screening scores within the 2e-4 margin the selection's
 exactness proof assumes; coefficients and RMSE within 1e-6 relative (RMSE of an exact fit
 within 1e-9 std(y) absolute).
 """
@@ -87,7 +88,7 @@ def test_score_all(S, orc, name, make, names, rung, g, prec):
     # a kernel may only reject what the oracle rejects
     rejected = got < 0
     assert not np.any(rejected & valid), [sp.expr(int(i)) for i in np.where(rejected & valid)[0][:5]]
-    tol = 1e-9 if prec == 0 else FP32_SCORE_TOL
+    tol = 1e-7 if prec == 0 else FP32_SCORE_TOL       # scores are stored as FP32
     err = np.abs(got[valid].astype(np.float64) - ref[valid])
     assert err.max() <= tol, (err.max(), sp.expr(int(np.where(valid)[0][np.argmax(err)])))
 

@@ -86,6 +86,20 @@ def test_identically_zero_features_are_invalid(orc):
     assert va.all()
 
 
+def test_validity_is_recursive(orc):
+    """A feature built from an invalid feature is invalid: log(x2*x2^-1) (log of a
+    constant) and (exp(x1))^-1 where exp(x1) exceeds 1e12 although 1/exp(x1) does not."""
+    rng = np.random.default_rng(12)
+    X = rng.uniform(1, 5, size=(40, 2))
+    X[7, 0] = 30.0                                   # exp(30) = 1.07e13 > 1e12
+    sp = orc.Space(2, _mask(orc, ["*", "exp", "log", "^-1"]), 3)
+    ids = {sp.expr(i): i for i in range(sp.n_features)}
+    sc, va = sp.scores(X, rng.normal(size=40), [ids[e] for e in ("log((x2*(x2)^-1))", "(exp(x1))^-1",
+                                                                  "exp(x1)", "(x2)^-1", "log((x1*x2))")])
+    assert list(va) == [False, False, False, True, True]
+    assert np.abs(1.0 / np.exp(X[:, 0])).max() < 1e12     # its own values are fine
+
+
 def test_sis_duplicates_are_skipped(orc):
     """Value-identical features (x1*(x2/x3), (x1*x2)/x3, ...) enter S once, as the
     lowest id; sign-flipped duplicates too."""
