@@ -41,6 +41,8 @@ def parse():
                     help="CPU work for the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--d", type=int, default=10, help="primary features (smaller cases for profiling)")
+    ap.add_argument("--N", type=int, default=1000, help="samples (smaller cases for profiling)")
     return ap.parse_args()
 
 
@@ -183,7 +185,7 @@ def main():
     torch.cuda.set_device(local)
     if rank == 0 or world > 1:
         build.build()
-    P = inputs.workload2(rank)
+    P = inputs.workload2(rank, N=args.N, d=args.d)
     Xd = torch.from_numpy(P.X).cuda()
     yd = torch.from_numpy(P.y).cuda()
     stream = torch.cuda.current_stream()
@@ -302,7 +304,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "phase_ms": {k: sum(st[k] for st in stats) / args.steps for k in
-                     ("ms_screen", "ms_screen_pair", "ms_select", "ms_gram", "ms_l0", "ms_refit", "ms_fit")},
+                     ("ms_screen", "ms_screen_pair", "ms_select", "ms_radix", "ms_rescore", "ms_sort", "ms_walk",
+                      "ms_gram", "ms_l0", "ms_refit", "ms_fit", "walk_visited", "walk_dup_checks")},
         "descriptor": {"ids": d_last.ids, "coef": d_last.coef, "rmse": d_last.rmse, "r2": d_last.r2,
                        "expr": [s.expr(i) for i in d_last.ids]} if d_last else None,
         "window_grown": sum(st["window_grown"] for st in stats),

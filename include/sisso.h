@@ -103,6 +103,12 @@ typedef struct {
     double ms_screen_pair;       /* ... of which the top-level pair kernel */
     int screen_pair_launches;    /* launches of the top-level pair kernel */
     double ms_select;            /* device-wide selection, FP64 re-score, walk */
+    double ms_radix;             /* ... radix select and compaction */
+    double ms_rescore;           /* ... FP64 re-score of the window */
+    double ms_sort;              /* ... sort of the window */
+    double ms_walk;              /* ... tie/duplicate walk */
+    int64_t walk_visited;        /* candidates visited by the walks */
+    int64_t walk_dup_checks;     /* duplicate checks (vector comparisons) made */
     double ms_gram;              /* subspace Gram */
     double ms_l0;                /* l0 enumeration (FP32 or FP64) */
     double ms_refit;             /* FP64 refit, winner, residual */

@@ -47,7 +47,9 @@ void free_all(sisso_ctx* c) {
                     c->hist, c->sel_state, c->surv_ids, c->surv_count, c->surv_score, c->surv_mean, c->surv_sd,
                     c->surv_valid, c->sort_score, c->sort_id, c->sort_src, c->removed, c->walk, c->S_dev,
                     c->S_sorted, c->Z, c->Zmean, c->Zsd, c->G64, c->b64, c->G32, c->b32, c->resid, c->ymom,
-                    c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best};
+                    c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
+                    c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
+                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -131,6 +133,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         (st = dalloc(c, c->surv_mean, (size_t)c->surv_cap, "surv_mean")) ||
         (st = dalloc(c, c->surv_sd, (size_t)c->surv_cap, "surv_sd")) ||
         (st = dalloc(c, c->surv_valid, (size_t)c->surv_cap, "surv_valid")) ||
+        (st = dalloc(c, c->surv_probe, (size_t)c->surv_cap * kProbes, "surv_probe")) ||
         (st = dalloc(c, c->sort_score, (size_t)c->sort_cap, "sort")) ||
         (st = dalloc(c, c->sort_id, (size_t)c->sort_cap, "sort_id")) ||
         (st = dalloc(c, c->sort_src, (size_t)c->sort_cap, "sort_src")) ||
@@ -144,8 +147,30 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         (st = dalloc(c, c->band, (size_t)c->band_cap, "band")) ||
         (st = dalloc(c, c->band_rss, (size_t)c->band_cap, "band_rss")) ||
         (st = dalloc(c, c->band_count, 1, "band_count")) || (st = dalloc(c, c->work, 16, "work")) ||
-        (st = dalloc(c, c->win, 1, "win")))
+        (st = dalloc(c, c->win, 1, "win")) || (st = dalloc(c, c->space_dev, 1, "space")))
         return bail(st);
+    cudaMemcpyAsync(c->space_dev, &c->space, sizeof(Space), cudaMemcpyHostToDevice, c->stream);
+    // standardised FP64 vectors of the screening window, for the duplicate rule: up to
+    // 4 GB (the walk evaluates on the fly when a window does not fit)
+    c->zcap = std::min<int64_t>(c->surv_cap, ((int64_t)4 << 30) / ((int64_t)8 * N));
+    if ((st = dalloc(c, c->zcache, (size_t)c->zcap * Nn, "zcache")) ||
+        (st = dalloc(c, c->subvalid, (size_t)c->space.phi[rung - 1], "subvalid")) ||
+        (st = dalloc(c, c->dup_list, (size_t)c->sort_cap * kDupSlots, "dup_list")) ||
+        (st = dalloc(c, c->dup_ok, (size_t)c->sort_cap * kDupSlots, "dup_ok")) ||
+        (st = dalloc(c, c->dup_cnt, (size_t)c->sort_cap, "dup_cnt")) ||
+        (st = dalloc(c, c->accepted, (size_t)c->surv_cap, "accepted")))
+        return bail(st);
+    // operand cache (phi_{L-1} values): kept when it fits 8 GB, otherwise the screening
+    // kernels rebuild operands from the primaries on the fly
+    {
+        const size_t elt = o.precision == SISSO_PREC_FP64 ? sizeof(double) : sizeof(float);
+        const size_t bytes = (size_t)c->space.phi[rung - 1] * Nn * elt;
+        if (bytes <= ((size_t)8 << 30)) {
+            if (o.precision == SISSO_PREC_FP64) st = dalloc(c, c->opcache64, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
+            else st = dalloc(c, c->opcache32, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
+            if (st) return bail(st);
+        }
+    }
     if ((st = check_cuda(c, cudaMallocHost(&c->walk_h, sizeof(WalkResult)), "walk_h")) ||
         (st = check_cuda(c, cudaMallocHost(&c->win_h, sizeof(Winner)), "win_h")))
         return bail(st);
@@ -161,8 +186,10 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         Xraw, yraw, N, d, c->Xc64, c->Xc32, c->y64, bad);
     int h_bad = 0;
     cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    // moments of y, and y~ = y - mean(y)
-    st = prepare_target(c, c->y64);
+    // validity of the operand features (depends on X only), moments of y, y~ = y - mean(y)
+    st = compute_subvalid(c);
+    if (!st) st = fill_opcache(c);
+    if (!st) st = prepare_target(c, c->y64);
     cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);
     TargetStats ts{};
     cudaMemcpyAsync(&ts, c->tstats, sizeof(ts), cudaMemcpyDeviceToHost, c->stream);

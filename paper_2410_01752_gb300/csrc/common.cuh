@@ -143,19 +143,35 @@ struct Prog {
     int16_t code[kProgLen];
 };
 
-__host__ __device__ inline bool build_prog_rec(const Space& sp, int64_t id, Prog& p, int depth) {
-    int level, op; int64_t a, b;
-    if (depth > kMaxRung || !decode(sp, id, level, op, a, b)) return false;
-    if (level == 0) { p.code[p.n++] = (int16_t)a; return true; }
-    if (!build_prog_rec(sp, a, p, depth + 1)) return false;
-    if (b >= 0 && !build_prog_rec(sp, b, p, depth + 1)) return false;
-    p.code[p.n++] = (int16_t)(-op - 1);
-    return true;
-}
-
+// Postfix program of feature id: children first (a, then b), then the operator.
+// Iterative depth-first walk with an explicit stack (a rung-3 tree has at most 7
+// pending entries); no recursion, so the per-thread stack stays small and static.
 __host__ __device__ inline bool build_prog(const Space& sp, int64_t id, Prog& p) {
     p.n = 0;
-    return build_prog_rec(sp, id, p, 0);
+    int64_t st_id[12];
+    int st_op[12];            // >= 0: emit operator; -1: expand st_id
+    int top = 0;
+    st_id[top] = id; st_op[top] = -1; ++top;
+    while (top > 0) {
+        --top;
+        if (st_op[top] >= 0) {
+            if (p.n >= kProgLen) return false;
+            p.code[p.n++] = (int16_t)(-st_op[top] - 1);
+            continue;
+        }
+        int level, op; int64_t a, b;
+        if (!decode(sp, st_id[top], level, op, a, b)) return false;
+        if (level == 0) {
+            if (p.n >= kProgLen) return false;
+            p.code[p.n++] = (int16_t)a;
+            continue;
+        }
+        if (top + 3 > 12) return false;
+        st_op[top] = op; st_id[top] = 0; ++top;                    // operator after children
+        if (b >= 0) { st_id[top] = b; st_op[top] = -1; ++top; }   // b after a
+        st_id[top] = a; st_op[top] = -1; ++top;                    // a first
+    }
+    return true;
 }
 
 template <typename T> __device__ __forceinline__ T op_unary(int op, T z);
@@ -192,6 +208,41 @@ template <typename T> __device__ __forceinline__ T op_binary(int op, T x, T y) {
         default: return x / y;
     }
 }
+
+// value of program p at one sample, and in mag the magnitude |a| + |b| of the root's
+// operands when the root is + or - (|v| otherwise)
+template <typename T, typename F>
+__device__ __forceinline__ T eval_prog_mag(const Prog& p, F x, T& mag) {
+    T st[kMaxRung + 2];
+    int top = 0;
+    mag = T(0);
+    for (int k = 0; k < p.n; ++k) {
+        const int c = p.code[k];
+        if (c >= 0) {
+            st[top++] = x(c);
+        } else {
+            const int op = -c - 1;
+            if (op >= EXP) {
+                st[top - 1] = op_unary<T>(op, st[top - 1]);
+            } else {
+                const T rhs = st[--top];
+                if (k == p.n - 1 && (op == ADD || op == SUB)) mag = fabs(st[top - 1]) + fabs(rhs);
+                st[top - 1] = op_binary<T>(op, st[top - 1], rhs);
+            }
+        }
+    }
+    return st[0];
+}
+
+__host__ __device__ inline bool root_is_addsub(const Prog& p) {
+    if (p.n == 0) return false;
+    const int c = p.code[p.n - 1];
+    return c < 0 && (-c - 1 == ADD || -c - 1 == SUB);
+}
+
+constexpr double kCancelRel = 1e-9;    // root +/- with max|v| <= this * max(|a|+|b|): zero
+constexpr int kProbes = 8;             // standardised values kept per candidate for dedup
+constexpr int kDupSlots = 16;          // partner candidates kept per screened candidate
 
 // value of program p at one sample; x(c) returns primary c at that sample
 template <typename T, typename F>
@@ -236,7 +287,7 @@ struct WalkResult {
     int n_acc;              // accepted ids
     int exhausted;          // ran out of survivors before k were accepted
     int visited;            // survivors visited
-    int pad;
+    int dup_checks;         // vector comparisons made
     double last_score;      // FP64 score of the last visited candidate
     int64_t acc[SISSO_MAX_SIS];
 };
@@ -260,6 +311,7 @@ struct sisso_ctx {
     uint32_t ops;
     sisso_opts opts;
     sg::Space space;
+    sg::Space* space_dev = nullptr;   // the same plan in device memory (kernels read it there)
     int64_t n_feat;
     cudaStream_t stream;
     bool own_stream;
@@ -287,6 +339,16 @@ struct sisso_ctx {
     double* surv_mean = nullptr;
     double* surv_sd = nullptr;
     int* surv_valid = nullptr;
+    double* surv_probe = nullptr;      // kProbes standardised values per entry
+    double* zcache = nullptr;          // standardised FP64 vectors of the window (zcap x N)
+    int64_t zcap = 0;
+    unsigned char* subvalid = nullptr; // FP64 validity (recursive) of every id of phi_{L-1}
+    float* opcache32 = nullptr;        // values of phi_{L-1}, feature-major (id x N), or null
+    double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
+    int* dup_list = nullptr;           // per sorted entry: partner candidates (kDupSlots)
+    unsigned char* dup_ok = nullptr;   // ... confirmed duplicates
+    int* dup_cnt = nullptr;            // ... number of partner candidates (-1: overflow)
+    unsigned char* accepted = nullptr; // per window entry: accepted by the walk
     int64_t sort_cap = 0;
     double* sort_score = nullptr;      // sort buffers (power of two)
     int64_t* sort_id = nullptr;
@@ -343,6 +405,8 @@ sisso_status fail(sisso_ctx* c, sisso_status st, const std::string& msg);
 sisso_status check_cuda(sisso_ctx* c, cudaError_t e, const char* what);
 
 // screening (sis.cu)
+sisso_status compute_subvalid(sisso_ctx* c);
+sisso_status fill_opcache(sisso_ctx* c);
 sisso_status prepare_target(sisso_ctx* c, const double* target_dev);
 sisso_status score_all(sisso_ctx* c, int precision);
 sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_prev,

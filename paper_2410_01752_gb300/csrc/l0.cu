@@ -54,14 +54,14 @@ __device__ __forceinline__ double okey_inv(unsigned long long k) {
 // ---------------------------------------------------------------------------------
 // subspace: standardised rows and Gram growth
 // ---------------------------------------------------------------------------------
-__global__ void k_standardise(Space sp, const double* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
+__global__ void k_standardise(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
                               int row0, double* __restrict__ Z, double* __restrict__ mean_out,
                               double* __restrict__ sd_out) {
     __shared__ double red[32];
     __shared__ double sh_mean, sh_sd;
     const int row = row0 + blockIdx.x;
     Prog p;
-    const bool ok = build_prog(sp, ids[row], p);
+    const bool ok = build_prog(*sp, ids[row], p);
     double* z = Z + (size_t)row * N;
     double s = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -502,7 +502,7 @@ __global__ void k_model(const double* __restrict__ G, const double* __restrict__
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new) {
     if (n_new <= 0) return SISSO_OK;
     const int n = n_old + n_new;
-    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, c->S_dev, n_old, c->Z, c->Zmean, c->Zsd);
+    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->Z, c->Zmean, c->Zsd);
     dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
     k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,
                                                       c->G32, c->b32);

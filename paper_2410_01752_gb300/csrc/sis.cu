@@ -94,6 +94,46 @@ __global__ void k_prepare_target(const double* __restrict__ t, int N, double* __
     }
 }
 
+// FP64 validity of ids [lo, hi) (one level), one warp per id: the value rules (finite,
+// |v| <= 1e12, not identically zero, std > 1e-6 max|v|) and the operands' validity
+// (lower levels, already computed)
+__global__ void k_subvalid(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t lo,
+                           int64_t hi, unsigned char* __restrict__ valid) {
+    const int64_t id = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (id >= hi) return;
+    int level, op; int64_t a, b;
+    Prog p;
+    if (!decode(*sp, id, level, op, a, b) || !build_prog(*sp, id, p)) { if (lane == 0) valid[id] = 0; return; }
+    if (level > 0 && (!valid[a] || (b >= 0 && !valid[b]))) { if (lane == 0) valid[id] = 0; return; }
+    double s = 0.0, mx = 0.0, mo = 0.0;
+    int bad = 0;
+    for (int i = lane; i < N; i += 32) {
+        double mag;
+        const double v = eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
+        s += v;
+        mx = fmax(mx, fabs(v));
+        mo = fmax(mo, mag);
+    }
+    bad = warp_or(bad);
+    s = warp_sum(s);
+    mx = warp_max(mx);
+    mo = warp_max(mo);
+    const double mean = s / N;
+    double ss = 0.0;
+    if (!bad)
+        for (int i = lane; i < N; i += 32) {
+            const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean;
+            ss += v * v;
+        }
+    ss = warp_sum(ss);
+    if (lane == 0) {
+        const bool cancelled = root_is_addsub(p) && mx <= kCancelRel * mo;
+        valid[id] = !bad && !cancelled && sqrt(ss / N) > kConstRel * mx;
+    }
+}
+
 // score from shifted sums (v' = v - v0): Pearson |rho| with population moments, or -1
 // when the feature is certainly invalid.  The exact validity rule (every |v| <= 1e12,
 // std > 1e-6 max|v|) is applied by the FP64 re-score; here a feature is rejected only
@@ -129,13 +169,19 @@ template <> struct TgtView<double> {
 // generic scoring: one thread per id
 // ---------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_score_generic(Space sp, const T* __restrict__ Xc, int N, const float* tc32,
+__global__ void k_score_generic(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, const float* tc32,
                                 const double* tc64, const TargetStats* st, int64_t id_lo,
-                                int64_t id_hi, float* __restrict__ scores) {
+                                int64_t id_hi, const unsigned char* __restrict__ subvalid,
+                                float* __restrict__ scores) {
     const int64_t id = id_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= id_hi) return;
     Prog p;
-    if (!build_prog(sp, id, p)) { scores[id] = -1.f; return; }
+    int level, op; int64_t a, b;
+    if (!decode(*sp, id, level, op, a, b) || !build_prog(*sp, id, p)) { scores[id] = -1.f; return; }
+    // invalid for certain: ids below the top level carry their exact validity; top-level
+    // ids are invalid when an operand is
+    const int64_t top0 = sp->phi[sp->rung - 1];
+    if (id < top0 ? !subvalid[id] : (!subvalid[a] || (b >= 0 && !subvalid[b]))) { scores[id] = -1.f; return; }
     const T* tc = TgtView<T>::tc(tc32, tc64);
     const T v0 = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; });
     T s1 = 0, s2 = 0, sr = 0;
@@ -149,6 +195,92 @@ __global__ void k_score_generic(Space sp, const T* __restrict__ Xc, int N, const
 }
 
 // ---------------------------------------------------------------------------------
+// operand cache: values of every feature of phi_{L-1} (they do not depend on the target),
+// feature-major rows of N samples.  With it, lower-level ids and the top level's unary
+// sections score from cached rows, and the pair kernel stages operands by plain loads.
+// ---------------------------------------------------------------------------------
+// sample-major layout: cache[s * P + id], so that a warp reads 32 consecutive features of
+// one sample with one coalesced access
+template <typename T>
+__global__ void k_fill_cache(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, int64_t n_ids,
+                             T* __restrict__ cache) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_ids) return;
+    Prog p;
+    const bool ok = build_prog(*sp, id, p);
+    for (int s = 0; s < N; ++s)
+        cache[(size_t)s * n_ids + id] = ok ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
+}
+
+// ids [lo, hi) below the top level (P = |phi_{L-1}| of them) scored from the cache: one
+// thread per id, coalesced across the warp for each sample
+template <typename T>
+__global__ void k_score_cached(const T* __restrict__ cache, int N, int64_t P, const float* tc32,
+                               const double* tc64, const TargetStats* st, int64_t lo, int64_t hi,
+                               const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
+    const int64_t id = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= hi) return;
+    if (!subvalid[id]) { scores[id] = -1.f; return; }
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const T v0 = cache[id];
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s = 0; s < N; ++s) {
+        const T v = cache[(size_t)s * P + id] - v0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+        sr = fma(v, tc[s], sr);
+    }
+    scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
+// the top level's unary sections from cached operand rows: a CTA takes 32 operands and
+// every enabled unary operator (warp w = operator w, lane = operand), 32-sample chunks
+// staged in shared memory
+constexpr int kUnaryMax = 8;
+struct UnaryArgs {
+    int n_ops;
+    int op[kUnaryMax];
+    int64_t base[kUnaryMax];   // first id of each operator's section
+    int64_t Q, P;              // operands: new_{L-1} = [Q, P)
+    int N;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kUnaryMax * 32)
+k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
+              const TargetStats* st, const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
+    __shared__ T xs[32][33];
+    __shared__ T r[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t z0 = U.Q + (int64_t)blockIdx.x * 32;
+    const int64_t z = z0 + lane;
+    const int N = U.N;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const bool active = w < U.n_ops && z < U.P;
+    const int op = w < U.n_ops ? U.op[w] : EXP;
+    const T v0 = active ? op_unary<T>(op, cache[z]) : T(0);
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s0 = 0; s0 < N; s0 += 32) {
+        __syncthreads();
+        // warp w stages samples w, w+8, ...: 32 consecutive operands each (coalesced)
+        for (int q = w; q < 32; q += kUnaryMax)
+            xs[q][lane] = (z < U.P && s0 + q < N) ? cache[(size_t)(s0 + q) * U.P + z] : T(1);
+        if (w == 0) r[lane] = s0 + lane < N ? tc[s0 + lane] : T(0);
+        __syncthreads();
+        const int ns = min(32, N - s0);
+        if (active)
+            for (int s = 0; s < ns; ++s) {
+                const T v = op_unary<T>(op, xs[s][lane]) - v0;
+                s1 += v;
+                s2 = fma(v, v, s2);
+                sr = fma(v, r[s], sr);
+            }
+    }
+    if (active)
+        scores[U.base[w] + (z - U.Q)] = subvalid[z] ? finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st)) : -1.f;
+}
+
+// ---------------------------------------------------------------------------------
 // fused generate-and-score for the top level's binary sections
 // ---------------------------------------------------------------------------------
 constexpr int TJ = 32;          // j operands per tile (= lanes)
@@ -158,7 +290,7 @@ constexpr int TI = NG * RI;     // i operands per tile
 constexpr int TS = 32;          // samples per chunk
 
 struct PairArgs {
-    Space sp;
+    const Space* sp;            // plan in device memory
     int sec[4];                 // section index of +, -, *, / at the top level (-1: off)
     int64_t P, Q;
     int nxp;
@@ -184,12 +316,18 @@ template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 template <typename T>
-struct __align__(16) PairSmem {
+struct __align__(16) PairBuf {
     T at[TS][TI], av[TS][TI], ar[TS][TI];   // i operands: shifted, raw, reciprocal
     T bt[TS][TJ], bv[TS][TJ], br[TS][TJ];   // j operands
     T r[TS];                                // centred target chunk
+};
+
+template <typename T>
+struct __align__(16) PairSmem {
+    PairBuf<T> buf[2];                      // double buffer: stage chunk c+1 while computing c
     T a0[TI], b0[TJ];                       // sample-0 values
-    Prog prog[TI + TJ];
+    unsigned char ok[TI + TJ];              // operand validity (FP64, recursive)
+    Prog prog[TI + TJ];                     // operand programs (on-the-fly staging only)
 };
 
 __device__ __forceinline__ bool pair_ok(int64_t i, int64_t j, int64_t P, int64_t Q, int nxp) {
@@ -197,10 +335,57 @@ __device__ __forceinline__ bool pair_ok(int64_t i, int64_t j, int64_t P, int64_t
     return nxp ? (i < Q && j >= Q) : (j >= Q);
 }
 
+// Staging: warp g owns samples g, g+8, g+16, g+24 of a chunk for both operand sides; lane
+// = operand.  With the operand cache (sample-major) every access is one coalesced load
+// and a conflict-free row of shared memory; without it the lane evaluates its operand's
+// program from the primaries.
+constexpr int kStageSlots = 2 * TS / NG;    // (sample, side) slots per warp and chunk
+
 template <typename T>
-__global__ void __launch_bounds__(NG * 32, 2)
+__device__ __forceinline__ void stage_load(const PairArgs& A, const T* __restrict__ Xc, const T* __restrict__ cache,
+                                           const PairSmem<T>& S, int64_t i0, int64_t j0, int s0, int g, int lane,
+                                           T (&v)[kStageSlots]) {
+    const int N = A.N;
+#pragma unroll
+    for (int q = 0; q < kStageSlots; ++q) {
+        const int s = s0 + g + NG * (q >> 1);
+        const int side = q & 1;
+        const int64_t f = (side ? j0 : i0) + lane;
+        T x = T(0);
+        if (s < N && f < A.P) {
+            if (cache) x = cache[(size_t)s * A.P + f];
+            else {
+                const Prog& p = S.prog[side ? TI + lane : lane];
+                if (p.n) x = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; });
+            }
+        }
+        v[q] = x;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[kStageSlots], int g, int lane) {
+    PairBuf<T>& B = S.buf[b];
+#pragma unroll
+    for (int q = 0; q < kStageSlots; ++q) {
+        const int s = g + NG * (q >> 1);
+        if (q & 1) {
+            B.bt[s][lane] = v[q] - S.b0[lane];
+            B.bv[s][lane] = v[q];
+            B.br[s][lane] = rcp<T>(v[q]);
+        } else {
+            B.at[s][lane] = v[q] - S.a0[lane];
+            B.av[s][lane] = v[q];
+            B.ar[s][lane] = rcp<T>(v[q]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NG * 32, sizeof(T) == 4 ? 2 : 1)
 k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
-              const double* __restrict__ tc64, const TargetStats* __restrict__ st) {
+              const double* __restrict__ tc64, const TargetStats* __restrict__ st,
+              const unsigned char* __restrict__ subvalid, const T* __restrict__ cache) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
@@ -211,18 +396,15 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
     for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
         const int64_t i0 = A.tiles[tile].x, j0 = A.tiles[tile].y;
         __syncthreads();
-        // operand programs: i operands first, then j operands
+        // operand programs (on-the-fly only), validity and sample-0 values
         if (tid < TI + TJ) {
             const int64_t f = tid < TI ? i0 + tid : j0 + (tid - TI);
             Prog& p = S.prog[tid];
-            if (f >= A.P || !build_prog(A.sp, f, p)) p.n = 0;
-        }
-        __syncthreads();
-        // sample-0 values (shifts)
-        if (tid < TI + TJ) {
-            const Prog& p = S.prog[tid];
+            p.n = 0;
+            if (f < A.P && !cache && !build_prog(*A.sp, f, p)) p.n = 0;
+            S.ok[tid] = f < A.P && subvalid[f];
             T v = T(0);
-            if (p.n) v = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; });
+            if (f < A.P) v = cache ? cache[f] : (p.n ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; }) : T(0));
             if (tid < TI) S.a0[tid] = v; else S.b0[tid - TI] = v;
         }
         __syncthreads();
@@ -248,37 +430,26 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
 #pragma unroll
             for (int q = 0; q < RI; ++q) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
 
-        for (int s0 = 0; s0 < N; s0 += TS) {
+        T pf[kStageSlots];
+        stage_load<T>(A, Xc, cache, S, i0, j0, 0, g, lane, pf);
+        stage_store<T>(S, 0, pf, g, lane);
+        if (tid < TS) S.buf[0].r[tid] = tid < N ? tc[tid] : T(0);
+        __syncthreads();
+        int b = 0;
+        for (int s0 = 0; s0 < N; s0 += TS, b ^= 1) {
+            const bool more = s0 + TS < N;
+            if (more) stage_load<T>(A, Xc, cache, S, i0, j0, s0 + TS, g, lane, pf);   // in flight during compute
+            const T rnext = (more && tid < TS && s0 + TS + tid < N) ? tc[s0 + TS + tid] : T(0);
+            const PairBuf<T>& B = S.buf[b];
             const int ns = min(TS, N - s0);
-            __syncthreads();
-            // stage the chunk: warp g evaluates features g, g+8, ... for 32 samples
-            for (int f = g; f < TI + TJ; f += NG) {
-                const Prog& p = S.prog[f];
-                const int s = s0 + lane;
-                T v = T(0);
-                if (p.n && s < N) v = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; });
-                if (f < TI) {
-                    S.at[lane][f] = v - S.a0[f];
-                    S.av[lane][f] = v;
-                    S.ar[lane][f] = rcp<T>(v);
-                } else {
-                    const int jj = f - TI;
-                    S.bt[lane][jj] = v - S.b0[jj];
-                    S.bv[lane][jj] = v;
-                    S.br[lane][jj] = rcp<T>(v);
-                }
-            }
-            if (tid < TS) S.r[tid] = (s0 + tid < N) ? tc[s0 + tid] : T(0);
-            __syncthreads();
-
 #pragma unroll 2
             for (int s = 0; s < ns; ++s) {
-                const T r = S.r[s];
-                const T bt = S.bt[s][lane], bv = S.bv[s][lane], br = S.br[s][lane];
+                const T r = B.r[s];
+                const T bt = B.bt[s][lane], bv = B.bv[s][lane], br = B.br[s][lane];
                 T at[RI], av[RI], ar[RI];
-                load4(&S.at[s][g * RI], at);
-                load4(&S.av[s][g * RI], av);
-                load4(&S.ar[s][g * RI], ar);
+                load4(&B.at[s][g * RI], at);
+                load4(&B.av[s][g * RI], av);
+                load4(&B.ar[s][g * RI], ar);
 #pragma unroll
                 for (int q = 0; q < RI; ++q) {
                     T v;
@@ -289,30 +460,37 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
                     v = fma(bv, ar[q], -Ke[q]); s1[4][q] += v; s2[4][q] = fma(v, v, s2[4][q]); sr[4][q] = fma(v, r, sr[4][q]);
                 }
             }
+            if (more) {
+                stage_store<T>(S, b ^ 1, pf, g, lane);
+                if (tid < TS) S.buf[b ^ 1].r[tid] = rnext;
+            }
+            __syncthreads();
         }
 
         // scores of the (up to) 20 candidates of this thread
+        const bool okj = S.ok[TI + lane];
 #pragma unroll
         for (int q = 0; q < RI; ++q) {
             if (!ok[q]) continue;
             const T a0 = S.a0[g * RI + q];
             const int64_t i = iq[q];
+            const bool opv = okj && S.ok[g * RI + q];   // both operands valid
             if (A.sec[0] >= 0) {
-                const Section& sc = A.sp.sec[A.sec[0]];
-                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[0][q], s2[0][q], sr[0][q], a0 + b0, N, sum_t, sd_t);
+                const Section& sc = A.sp->sec[A.sec[0]];
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], a0 + b0, N, sum_t, sd_t) : -1.f;
             }
             if (A.sec[1] >= 0) {
-                const Section& sc = A.sp.sec[A.sec[1]];
-                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[1][q], s2[1][q], sr[1][q], a0 - b0, N, sum_t, sd_t);
+                const Section& sc = A.sp->sec[A.sec[1]];
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], a0 - b0, N, sum_t, sd_t) : -1.f;
             }
             if (A.sec[2] >= 0) {
-                const Section& sc = A.sp.sec[A.sec[2]];
-                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[2][q], s2[2][q], sr[2][q], Km[q], N, sum_t, sd_t);
+                const Section& sc = A.sp->sec[A.sec[2]];
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], Km[q], N, sum_t, sd_t) : -1.f;
             }
             if (A.sec[3] >= 0) {
-                const Section& sc = A.sp.sec[A.sec[3]];
-                A.scores[sc.base + rank_of(sc, i, j)] = finalize<T>(s1[3][q], s2[3][q], sr[3][q], Kd[q], N, sum_t, sd_t);
-                A.scores[sc.base + rank_of(sc, j, i)] = finalize<T>(s1[4][q], s2[4][q], sr[4][q], Ke[q], N, sum_t, sd_t);
+                const Section& sc = A.sp->sec[A.sec[3]];
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[3][q], s2[3][q], sr[3][q], Kd[q], N, sum_t, sd_t) : -1.f;
+                A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[4][q], s2[4][q], sr[4][q], Ke[q], N, sum_t, sd_t) : -1.f;
             }
         }
     }
@@ -380,44 +558,67 @@ __global__ void k_compact(const float* __restrict__ scores, int64_t n, const uns
 }
 
 // ---------------------------------------------------------------------------------
-// FP64 re-score: one warp per id, lanes over samples (two passes, as the definition)
+// FP64 re-score: one warp per id, lanes over samples.  Applies the exact validity rules
+// (every |v| <= 1e12 and finite, not identically zero, std > 1e-6 max|v|), computes the
+// Pearson score with two passes as the definition does, and keeps the standardised
+// vector (zc, when given) and kProbes of its values for the duplicate rule.
 // ---------------------------------------------------------------------------------
-__global__ void k_rescore(Space sp, const double* __restrict__ Xc, int N, const double* __restrict__ tc,
-                          const TargetStats* __restrict__ st, const int64_t* __restrict__ ids, int n,
-                          double* score, double* mean_out, double* sd_out, int* valid_out) {
+__global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict__ Xc, int N,
+                          const double* __restrict__ tc, const TargetStats* __restrict__ st,
+                          const int64_t* __restrict__ ids, int n, const unsigned char* __restrict__ subvalid,
+                          double* score, double* mean_out, double* sd_out, int* valid_out,
+                          double* __restrict__ probe, double* __restrict__ zc) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n) return;
     Prog p;
-    const bool built = build_prog(sp, ids[w], p);
+    int level, op; int64_t a, b;
+    const int64_t id = ids[w];
+    bool built = decode(*sp, id, level, op, a, b) && build_prog(*sp, id, p);
+    if (built && level > 0 && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
     if (!built) {
         if (lane == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
+        if (lane < kProbes) probe[(size_t)w * kProbes + lane] = 0.0;
         return;
     }
-    double s = 0.0, mx = 0.0;
+    double* z = zc ? zc + (size_t)w * N : nullptr;
+    double s = 0.0, mx = 0.0, mo = 0.0;
     int bad = 0;
     for (int i = lane; i < N; i += 32) {
-        const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; });
+        double mag;
+        const double v = eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
         if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
         s += v;
         mx = fmax(mx, fabs(v));
+        mo = fmax(mo, mag);
+        if (z) z[i] = v;
     }
     bad = warp_or(bad);
     s = warp_sum(s);
     mx = warp_max(mx);
+    mo = warp_max(mo);
+    const bool cancelled = root_is_addsub(p) && mx <= kCancelRel * mo;
     const double mean = s / N;
     double ss = 0.0, sc = 0.0;
     if (!bad) {
         for (int i = lane; i < N; i += 32) {
-            const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean;
+            const double v = (z ? z[i] : eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; })) - mean;
             ss += v * v;
             sc += v * tc[i];
         }
     }
     ss = warp_sum(ss);
     sc = warp_sum(sc);
+    const double sd = sqrt(ss / N);
+    const int ok = !bad && !cancelled && sd > kConstRel * mx;
+    const double inv = ok ? 1.0 / sd : 0.0;
+    if (z)
+        for (int i = lane; i < N; i += 32) z[i] = (z[i] - mean) * inv;
+    if (lane < kProbes) {
+        const int i = (int)(((int64_t)lane * N) / kProbes);
+        const double v = z ? z[i] : (eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean) * inv;
+        probe[(size_t)w * kProbes + lane] = v;
+    }
     if (lane == 0) {
-        const double sd = sqrt(ss / N);
-        const int ok = !bad && sd > kConstRel * mx;
         valid_out[w] = ok;
         mean_out[w] = mean;
         sd_out[w] = sd;
@@ -462,86 +663,266 @@ __global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int
 }
 
 // ---------------------------------------------------------------------------------
+// duplicate rule.  Two features are duplicates when their standardised vectors agree up
+// to sign within kDupTol (max norm).  Necessary conditions, checked first: their scores
+// differ by at most kDupScore (|rho_a - rho_b| <= |z_a -/+ z_b|_inf) and their kProbes
+// probe values agree.  k_dup_find lists, per screened entry, the window entries and S
+// members passing both; k_dup_confirm checks every listed pair on all samples; the walk
+// then only reads the confirmed pairs.
+// ---------------------------------------------------------------------------------
+constexpr double kDupScore = 2e-8;
+constexpr int kMaxRefs = 2048;          // slow path: S members / accepted ids gathered per round
+
+__device__ __forceinline__ bool probes_match(const double* a, const double* b) {
+    bool same = true, flip = true;
+#pragma unroll
+    for (int r = 0; r < kProbes; ++r) {
+        same = same && fabs(a[r] - b[r]) <= kDupTol;
+        flip = flip && fabs(a[r] + b[r]) <= kDupTol;
+    }
+    return same || flip;
+}
+
+__global__ void k_dup_find(const double* __restrict__ sk, const int* __restrict__ ssrc,
+                           const int64_t* __restrict__ sid, int n_sorted,
+                           const double* __restrict__ sv_score, const double* __restrict__ sv_sd,
+                           const double* __restrict__ probe, int s_off, int nS, int* __restrict__ dup_list,
+                           int* __restrict__ dup_cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_sorted) return;
+    const double s = sk[i];
+    if (s < 0.0) { dup_cnt[i] = 0; return; }
+    const int src = ssrc[i];
+    double pc[kProbes];
+#pragma unroll
+    for (int r = 0; r < kProbes; ++r) pc[r] = probe[(size_t)src * kProbes + r];
+    // keep the kDupSlots partners with the smallest keys: S members first (key -1), then
+    // window entries by id (a cluster's earliest-visited member is its smallest id)
+    int64_t key[kDupSlots];
+    int val[kDupSlots];
+    int n = 0, total = 0;
+    auto consider = [&](int m, int64_t k) {
+        if (!probes_match(pc, probe + (size_t)m * kProbes)) return;
+        ++total;
+        if (n == kDupSlots && k >= key[n - 1]) return;
+        int q = n < kDupSlots ? n++ : n - 1;
+        while (q > 0 && key[q - 1] > k) { key[q] = key[q - 1]; val[q] = val[q - 1]; --q; }
+        key[q] = k;
+        val[q] = m;
+    };
+    for (int q = 0; q < nS; ++q) {
+        const int m = s_off + q;
+        if (sv_sd[m] > 0.0 && fabs(sv_score[m] - s) <= kDupScore) consider(m, -1);
+    }
+    for (int j = i - 1; j >= 0 && sk[j] - s <= kDupScore; --j) consider(ssrc[j], sid[j]);
+    for (int j = i + 1; j < n_sorted && sk[j] >= 0.0 && s - sk[j] <= kDupScore; ++j) consider(ssrc[j], sid[j]);
+    for (int q = 0; q < n; ++q) dup_list[(size_t)i * kDupSlots + q] = val[q];
+    // overflow: n partners kept, more exist (the walk falls back to a full check)
+    dup_cnt[i] = total > kDupSlots ? -n - 1 : n;
+}
+
+// one warp per sorted entry: every listed partner compared on all samples
+__global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __restrict__ Xc, int N,
+                              const int* __restrict__ ssrc, const int64_t* __restrict__ sid, int n_sorted,
+                              const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_mean,
+                              const double* __restrict__ sv_sd, const double* __restrict__ zc,
+                              const int* __restrict__ dup_list, const int* __restrict__ dup_cnt,
+                              unsigned char* __restrict__ dup_ok) {
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_sorted; i += (gridDim.x * blockDim.x) >> 5) {
+        const int raw = dup_cnt[i];
+        const int cnt = raw < 0 ? -raw - 1 : raw;
+        if (cnt <= 0) continue;
+        const int src = ssrc[i];
+        Prog pc;
+        if (!zc) build_prog(*sp, sid[i], pc);
+        const double mc = sv_mean[src], dc = sv_sd[src];
+        for (int q = 0; q < cnt; ++q) {
+            const int m = dup_list[(size_t)i * kDupSlots + q];
+            Prog pm;
+            if (!zc) build_prog(*sp, sv_ids[m], pm);
+            const double mm = sv_mean[m], dm = sv_sd[m];
+            double e1 = 0.0, e2 = 0.0;
+            for (int t = lane; t < N; t += 32) {
+                double za, zb;
+                if (zc) {
+                    za = zc[(size_t)src * N + t];
+                    zb = zc[(size_t)m * N + t];
+                } else {
+                    za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
+                    zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+                }
+                e1 = fmax(e1, fabs(za - zb));
+                e2 = fmax(e2, fabs(za + zb));
+            }
+            e1 = warp_max(e1);
+            e2 = warp_max(e2);
+            if (lane == 0) dup_ok[(size_t)i * kDupSlots + q] = (e1 <= kDupTol || e2 <= kDupTol);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // the walk: one CTA.  Thread 0 picks, among the remaining candidates whose score is
-// within kScoreTie of the current maximum, the lowest id; the whole CTA then checks it
-// against every S member and accepted id whose score is within kDupScore (a necessary
-// condition for standardised vectors within kDupTol: |rho_a - rho_b| <= |z_a - z_b|_inf)
-// by evaluating both features in FP64 over all samples.
+// within kScoreTie of the current maximum, the lowest id, and accepts it unless a
+// confirmed duplicate of it is an S member or an id accepted before it.  Entries whose
+// partner list overflowed are checked by the whole CTA against every S member and
+// accepted id.
 // ---------------------------------------------------------------------------------
 constexpr int kWalkThreads = 1024;
-constexpr double kDupScore = 2e-8;
-constexpr int kMaxPartners = SISSO_MAX_SIS * (SISSO_MAX_DIM + 1);
+constexpr int kHeapCap = 2048;          // tie-window entries held in the shared-memory heap
 
 __global__ void __launch_bounds__(kWalkThreads)
-k_walk(Space sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk,
+k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk,
        const int64_t* __restrict__ sid, const int* __restrict__ ssrc, int n_sorted,
        const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_score,
-       const double* __restrict__ sv_mean, const double* __restrict__ sv_sd, int s_off, int nS,
-       int k, unsigned char* __restrict__ removed, WalkResult* out) {
+       const double* __restrict__ sv_mean, const double* __restrict__ sv_sd,
+       const double* __restrict__ probe, const double* __restrict__ zc, const int* __restrict__ dup_list,
+       const int* __restrict__ dup_cnt, const unsigned char* __restrict__ dup_ok, int s_off, int nS,
+       int k, unsigned char* __restrict__ removed, unsigned char* __restrict__ accepted, WalkResult* out) {
     __shared__ int acc_src[SISSO_MAX_SIS];
-    __shared__ int partners[kMaxPartners];
-    __shared__ int n_part, cur, n_acc, done, exhausted, visited;
+    __shared__ int64_t heap_id[kHeapCap];
+    __shared__ int heap_ix[kHeapCap];
+    __shared__ int refs[kMaxRefs];
+    __shared__ int cur, n_acc, done, exhausted, visited, checks, slow, n_refs;
     __shared__ double red[32];
     __shared__ double cur_score, last_score;
     const int tid = threadIdx.x;
-    if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; last_score = -1.0; }
-    int p = 0;   // thread 0's scan position
+    if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0; }
+    // thread 0's state: first remaining entry p, window end e, heap of the window's
+    // remaining entries keyed by id (the window only grows as the maximum falls)
+    int p = 0, e = 0, hn = 0;
     __syncthreads();
     while (true) {
         if (tid == 0) {
-            while (p < n_sorted && removed[p]) ++p;
-            if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
-                done = 1;
-                exhausted = n_acc < k;
-            } else {
+            slow = 0;
+            while (!done && !slow) {
+                while (p < n_sorted && removed[p]) ++p;
+                if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
+                    done = 1;
+                    exhausted = n_acc < k;
+                    break;
+                }
                 const double m = sk[p];
-                int best = p;
-                for (int q = p; q < n_sorted && sk[q] >= m - kScoreTie; ++q)
-                    if (!removed[q] && sid[q] < sid[best]) best = q;
+                if (e < p) e = p;
+                int best = -1;
+                while (e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
+                    if (hn == kHeapCap) break;
+                    int q = hn++;                                  // push (sift up)
+                    const int64_t xid = sid[e];
+                    while (q > 0 && heap_id[(q - 1) >> 1] > xid) {
+                        heap_id[q] = heap_id[(q - 1) >> 1];
+                        heap_ix[q] = heap_ix[(q - 1) >> 1];
+                        q = (q - 1) >> 1;
+                    }
+                    heap_id[q] = xid;
+                    heap_ix[q] = e;
+                    ++e;
+                }
+                if (hn == kHeapCap && e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
+                    // window larger than the heap: plain scan (still exact)
+                    best = p;
+                    for (int q = p; q < n_sorted && sk[q] >= m - kScoreTie; ++q)
+                        if (!removed[q] && sid[q] < sid[best]) best = q;
+                    // the heap may hold best: drop it lazily (skipped when popped)
+                } else {
+                    while (hn > 0) {                               // pop min id (lazy deletion)
+                        const int top = heap_ix[0];
+                        const int64_t last_id = heap_id[hn - 1];
+                        const int last_ix = heap_ix[hn - 1];
+                        --hn;
+                        int q = 0;
+                        while (true) {
+                            int ch = 2 * q + 1;
+                            if (ch >= hn) break;
+                            if (ch + 1 < hn && heap_id[ch + 1] < heap_id[ch]) ++ch;
+                            if (heap_id[ch] >= last_id) break;
+                            heap_id[q] = heap_id[ch];
+                            heap_ix[q] = heap_ix[ch];
+                            q = ch;
+                        }
+                        if (hn > 0) { heap_id[q] = last_id; heap_ix[q] = last_ix; }
+                        if (!removed[top]) { best = top; break; }
+                    }
+                }
+                if (best < 0) { best = p; }
                 removed[best] = 1;
                 cur = best;
                 cur_score = sk[best];
                 last_score = sk[best];
                 ++visited;
+                const int raw = dup_cnt[best];
+                const int cnt = raw < 0 ? -raw - 1 : raw;
+                bool dup = false;
+                for (int q = 0; q < cnt && !dup; ++q) {
+                    if (!dup_ok[(size_t)best * kDupSlots + q]) continue;
+                    const int mm = dup_list[(size_t)best * kDupSlots + q];
+                    dup = mm >= s_off || accepted[mm];
+                }
+                checks += cnt;
+                if (!dup && raw < 0) { slow = 1; break; }          // partners beyond the list
+                if (!dup) {
+                    const int src = ssrc[best];
+                    accepted[src] = 1;
+                    acc_src[n_acc] = src;
+                    out->acc[n_acc] = sid[best];
+                    ++n_acc;
+                }
             }
-            n_part = 0;
+            n_refs = 0;
         }
         __syncthreads();
         if (done) break;
+        // slow path: every S member and accepted id that passes the score and probe tests
+        // (gathered in parallel), compared on all samples by the whole CTA
         const int c = cur;
-        const double cs = cur_score;
         const int csrc = ssrc[c];
         const int64_t cid = sid[c];
-        for (int q = tid; q < nS + n_acc; q += blockDim.x) {
+        Prog pc;
+        if (!zc) build_prog(*sp, cid, pc);
+        const double mc = sv_mean[csrc], dc = sv_sd[csrc];
+        int dupf = 0;
+        const int nall = nS + n_acc;
+        for (int r0 = 0; r0 < nall && !dupf; r0 += kMaxRefs) {
+        if (tid == 0) n_refs = 0;
+        __syncthreads();
+        for (int q = r0 + tid; q < nall && q < r0 + kMaxRefs; q += blockDim.x) {
             const int src = q < nS ? s_off + q : acc_src[q - nS];
-            if (sv_sd[src] > 0.0 && fabs(sv_score[src] - cs) <= kDupScore) {
-                const int slot = atomicAdd(&n_part, 1);
-                if (slot < kMaxPartners) partners[slot] = src;
+            if (sv_sd[src] > 0.0 && fabs(sv_score[src] - cur_score) <= kDupScore &&
+                probes_match(probe + (size_t)csrc * kProbes, probe + (size_t)src * kProbes)) {
+                const int slot = atomicAdd(&n_refs, 1);
+                refs[slot] = src;
             }
         }
         __syncthreads();
-        Prog pc;
-        build_prog(sp, cid, pc);
-        const double mc = sv_mean[csrc], dc = sv_sd[csrc];
-        int dupf = 0;
-        const int np = min(n_part, kMaxPartners);
-        for (int q = 0; q < np; ++q) {
-            const int src = partners[q];
+        const int nr = n_refs;
+        for (int q = 0; q < nr; ++q) {
+            const int src = refs[q];
             Prog pm;
-            build_prog(sp, sv_ids[src], pm);
+            if (!zc) build_prog(*sp, sv_ids[src], pm);
             const double mm = sv_mean[src], dm = sv_sd[src];
             double e1 = 0.0, e2 = 0.0;
-            for (int s = tid; s < N; s += blockDim.x) {
-                const double zc = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + s]; }) - mc) / dc;
-                const double zm = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + s]; }) - mm) / dm;
-                e1 = fmax(e1, fabs(zc - zm));
-                e2 = fmax(e2, fabs(zc + zm));
+            for (int t = tid; t < N; t += blockDim.x) {
+                double za, zb;
+                if (zc) {
+                    za = zc[(size_t)csrc * N + t];
+                    zb = zc[(size_t)src * N + t];
+                } else {
+                    za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
+                    zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+                }
+                e1 = fmax(e1, fabs(za - zb));
+                e2 = fmax(e2, fabs(za + zb));
             }
             e1 = block_max(e1, red);
             e2 = block_max(e2, red);
+            if (tid == 0) ++checks;
             if (e1 <= kDupTol || e2 <= kDupTol) { dupf = 1; break; }
         }
+        __syncthreads();
+        }
         if (tid == 0 && !dupf) {
+            accepted[csrc] = 1;
             acc_src[n_acc] = csrc;
             out->acc[n_acc] = cid;
             ++n_acc;
@@ -552,26 +933,22 @@ k_walk(Space sp, const double* __restrict__ Xc, int N, const double* __restrict_
         out->n_acc = n_acc;
         out->exhausted = exhausted;
         out->visited = visited;
+        out->dup_checks = checks;
         out->last_score = last_score;
     }
 }
 
 // features' values (n ids) in FP32 or FP64, one warp per id; out is n x N (FP64)
 template <typename T>
-__global__ void k_eval(Space sp, const T* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
+__global__ void k_eval(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
                        int64_t n, double* __restrict__ out) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
     Prog p;
-    const bool ok = build_prog(sp, ids[w], p);
+    const bool ok = build_prog(*sp, ids[w], p);
     for (int s = lane; s < N; s += 32)
         out[w * N + s] = ok ? (double)eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : NAN;
-}
-
-int grid_for(int64_t n, int block, int cap) {
-    const int64_t g = (n + block - 1) / block;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
 }
 
 }  // namespace
@@ -579,6 +956,33 @@ int grid_for(int64_t n, int block, int cap) {
 // ===================================================================================
 // host side
 // ===================================================================================
+
+// validity of every id of phi_{L-1}, level by level (operands before their features)
+sisso_status compute_subvalid(sisso_ctx* c) {
+    const Space& sp = c->space;
+    for (int l = 0; l < sp.rung; ++l) {
+        const int64_t lo = l == 0 ? 0 : sp.phi[l - 1], hi = sp.phi[l];
+        const int64_t n = hi - lo;
+        if (n <= 0) continue;
+        k_subvalid<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, lo, hi, c->subvalid);
+        c->stats.launches++;
+    }
+    return check_cuda(c, cudaGetLastError(), "subvalid");
+}
+
+sisso_status fill_opcache(sisso_ctx* c) {
+    const int64_t n = c->space.phi[c->rung - 1];
+    const int grid = (int)((n + 127) / 128);
+    if (c->opcache32) {
+        k_fill_cache<float><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
+        c->stats.launches++;
+    }
+    if (c->opcache64) {
+        k_fill_cache<double><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache64);
+        c->stats.launches++;
+    }
+    return check_cuda(c, cudaGetLastError(), "fill_opcache");
+}
 
 sisso_status prepare_target(sisso_ctx* c, const double* target_dev) {
     k_prepare_target<<<1, 1024, 0, c->stream>>>(target_dev, c->N, c->tc64, c->tc32, c->tstats);
@@ -606,7 +1010,7 @@ sisso_status score_all(sisso_ctx* c, int precision) {
     const int L = sp.rung;
     const bool fp64 = precision == SISSO_PREC_FP64;
     PairArgs A{};
-    A.sp = sp;
+    A.sp = c->space_dev;
     for (int o = 0; o < 4; ++o) A.sec[o] = -1;
     A.P = sp.phi[L - 1];
     A.Q = L >= 2 ? sp.phi[L - 2] : 0;
@@ -624,15 +1028,35 @@ sisso_status score_all(sisso_ctx* c, int precision) {
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
     cudaEventRecord(e0, c->stream);
-    for (auto& r : ranges) {
-        const int64_t n = r.second - r.first;
-        if (n <= 0) continue;
-        const int grid = (int)((n + 127) / 128);
-        if (fp64)
-            k_score_generic<double><<<grid, 128, 0, c->stream>>>(sp, c->Xc64, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->scores);
-        else
-            k_score_generic<float><<<grid, 128, 0, c->stream>>>(sp, c->Xc32, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->scores);
+    const bool cached = fp64 ? c->opcache64 != nullptr : c->opcache32 != nullptr;
+    if (cached) {
+        // lower levels from cached rows; the top level's unary sections from cached operands
+        const int64_t nlow = sp.phi[L - 1];
+        const int gl = (int)((nlow + 255) / 256);
+        if (fp64) k_score_cached<double><<<gl, 256, 0, c->stream>>>(c->opcache64, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+        else k_score_cached<float><<<gl, 256, 0, c->stream>>>(c->opcache32, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
         c->stats.launches++;
+        UnaryArgs U{};
+        U.Q = A.Q; U.P = A.P; U.N = c->N;
+        for (int q = 0; q < sp.nsec; ++q)
+            if (sp.sec[q].level == L && sp.sec[q].op > DIV) { U.op[U.n_ops] = sp.sec[q].op; U.base[U.n_ops] = sp.sec[q].base; ++U.n_ops; }
+        if (U.n_ops > 0) {
+            const int gu = (int)((A.P - A.Q + 31) / 32);
+            if (fp64) k_score_unary<double><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            else k_score_unary<float><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            c->stats.launches++;
+        }
+    } else {
+        for (auto& r : ranges) {
+            const int64_t n = r.second - r.first;
+            if (n <= 0) continue;
+            const int grid = (int)((n + 127) / 128);
+            if (fp64)
+                k_score_generic<double><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->subvalid, c->scores);
+            else
+                k_score_generic<float><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, c->tc32, c->tc64, c->tstats, r.first, r.second, c->subvalid, c->scores);
+            c->stats.launches++;
+        }
     }
     sisso_status st = check_cuda(c, cudaGetLastError(), "score_generic");
     if (st) return st;
@@ -652,11 +1076,11 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         if (fp64) {
             const size_t sm = sizeof(PairSmem<double>);
             cudaFuncSetAttribute(k_score_pairs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_score_pairs<double><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc64, c->tc32, c->tc64, c->tstats);
+            k_score_pairs<double><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc64, c->tc32, c->tc64, c->tstats, c->subvalid, c->opcache64);
         } else {
             const size_t sm = sizeof(PairSmem<float>);
             cudaFuncSetAttribute(k_score_pairs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_score_pairs<float><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc32, c->tc32, c->tc64, c->tstats);
+            k_score_pairs<float><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc32, c->tc32, c->tc64, c->tstats, c->subvalid, c->opcache32);
         }
         c->stats.launches++;
         c->stats.screen_pair_launches++;
@@ -676,9 +1100,9 @@ sisso_status score_all(sisso_ctx* c, int precision) {
 sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int precision, double* out_dev) {
     const int grid = (int)((n * 32 + 255) / 256);
     if (precision == SISSO_PREC_FP64)
-        k_eval<double><<<grid, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, ids_dev, n, out_dev);
+        k_eval<double><<<grid, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, ids_dev, n, out_dev);
     else
-        k_eval<float><<<grid, 256, 0, c->stream>>>(c->space, c->Xc32, c->N, ids_dev, n, out_dev);
+        k_eval<float><<<grid, 256, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, ids_dev, n, out_dev);
     c->stats.launches++;
     return check_cuda(c, cudaGetLastError(), "eval_features");
 }
@@ -701,8 +1125,11 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
     int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(16384, 64LL * k);
     const int64_t n = c->n_feat;
     const int gridS = std::max(1, c->sms * 8);
+    cudaEvent_t q[5];
+    for (auto& e : q) cudaEventCreate(&e);
     while (true) {
         M = std::min<int64_t>(M, c->surv_cap - n_prev);
+        cudaEventRecord(q[0], c->stream);
         cudaMemsetAsync(c->hist, 0, sizeof(unsigned) * 3 * 4096, c->stream);
         cudaMemsetAsync(c->sel_state, 0, sizeof(unsigned) * 4, c->stream);
         cudaMemsetAsync(c->surv_count, 0, sizeof(unsigned), c->stream);
@@ -730,27 +1157,47 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         if (n_prev > 0)
             cudaMemcpyAsync(c->surv_ids + ns, S_prev_host, sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
         const int nr = ns + n_prev;
-        k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space, c->Xc64, c->N, c->tc64, c->tstats,
-                                                                 c->surv_ids, nr, c->surv_score, c->surv_mean,
-                                                                 c->surv_sd, c->surv_valid);
+        cudaEventRecord(q[1], c->stream);
+        double* zc = (int64_t)nr <= c->zcap ? c->zcache : nullptr;   // cache the vectors if they fit
+        k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->tc64, c->tstats,
+                                                                 c->surv_ids, nr, c->subvalid, c->surv_score,
+                                                                 c->surv_mean, c->surv_sd, c->surv_valid,
+                                                                 c->surv_probe, zc);
         int n_pad = 1;
         while (n_pad < std::max(ns, 1)) n_pad <<= 1;
         k_sort_keys<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->surv_ids, c->surv_score, c->surv_valid, ns,
                                                                  c->S_sorted, n_prev, n_pad, c->sort_score,
                                                                  c->sort_id, c->sort_src);
         c->stats.launches += 2;
+        cudaEventRecord(q[2], c->stream);
         for (int kk = 2; kk <= n_pad; kk <<= 1)
             for (int j = kk >> 1; j > 0; j >>= 1) {
                 k_bitonic<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_id, c->sort_src, n_pad, kk, j);
                 c->stats.launches++;
             }
+        cudaEventRecord(q[3], c->stream);
         cudaMemsetAsync(c->removed, 0, (size_t)n_pad, c->stream);
-        k_walk<<<1, kWalkThreads, 0, c->stream>>>(c->space, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
+        cudaMemsetAsync(c->accepted, 0, (size_t)ns, c->stream);
+        k_dup_find<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_src, c->sort_id, n_pad, c->surv_score,
+                                                               c->surv_sd, c->surv_probe, ns, n_prev, c->dup_list,
+                                                               c->dup_cnt);
+        k_dup_confirm<<<std::max(1, std::min(c->sms * 16, (n_pad * 32 + 255) / 256)), 256, 0, c->stream>>>(
+            c->space_dev, c->Xc64, c->N, c->sort_src, c->sort_id, n_pad, c->surv_ids, c->surv_mean, c->surv_sd, zc,
+            c->dup_list, c->dup_cnt, c->dup_ok);
+        k_walk<<<1, kWalkThreads, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
                                                   n_pad, c->surv_ids, c->surv_score, c->surv_mean, c->surv_sd,
-                                                  ns, n_prev, k, c->removed, c->walk);
-        c->stats.launches++;
+                                                  c->surv_probe, zc, c->dup_list, c->dup_cnt, c->dup_ok, ns, n_prev,
+                                                  k, c->removed, c->accepted, c->walk);
+        c->stats.launches += 3;
+        cudaEventRecord(q[4], c->stream);
         cudaMemcpyAsync(c->walk_h, c->walk, sizeof(WalkResult), cudaMemcpyDeviceToHost, c->stream);
         if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "walk"))) break;
+        c->stats.ms_radix += event_ms(q[0], q[1]);
+        c->stats.ms_rescore += event_ms(q[1], q[2]);
+        c->stats.ms_sort += event_ms(q[2], q[3]);
+        c->stats.ms_walk += event_ms(q[3], q[4]);
+        c->stats.walk_visited += c->walk_h->visited;
+        c->stats.walk_dup_checks += c->walk_h->dup_checks;
         c->stats.survivors_rescored += nr;
         const WalkResult& w = *c->walk_h;
         // exact iff every candidate outside the window scores (FP64) below the last
@@ -765,6 +1212,7 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         M *= 4;
         c->stats.window_grown++;
     }
+    for (auto& e : q) cudaEventDestroy(e);
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
     c->stats.ms_select += event_ms(e0, e1);

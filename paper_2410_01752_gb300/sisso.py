@@ -52,6 +52,8 @@ class Stats(C.Structure):
                 ("window_grown", C.c_int), ("window_saturated", C.c_int), ("launches", C.c_int),
                 ("ms_screen", C.c_double), ("ms_screen_pair", C.c_double),
                 ("screen_pair_launches", C.c_int), ("ms_select", C.c_double),
+                ("ms_radix", C.c_double), ("ms_rescore", C.c_double), ("ms_sort", C.c_double),
+                ("ms_walk", C.c_double), ("walk_visited", C.c_int64), ("walk_dup_checks", C.c_int64),
                 ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
                 ("ms_fit", C.c_double)]
 
