@@ -49,7 +49,7 @@ void free_all(sisso_ctx* c) {
                     c->S_sorted, c->Z, c->Zmean, c->Zsd, c->G64, c->b64, c->G32, c->b32, c->resid, c->ymom,
                     c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
-                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64};
+                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -168,6 +168,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         if (bytes <= ((size_t)8 << 30)) {
             if (o.precision == SISSO_PREC_FP64) st = dalloc(c, c->opcache64, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
             else st = dalloc(c, c->opcache32, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
+            if (!st) st = dalloc(c, c->opsum, 2 * (size_t)c->space.phi[rung - 1], "opsum");
             if (st) return bail(st);
         }
     }

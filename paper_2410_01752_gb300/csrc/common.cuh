@@ -343,8 +343,9 @@ struct sisso_ctx {
     double* zcache = nullptr;          // standardised FP64 vectors of the window (zcap x N)
     int64_t zcap = 0;
     unsigned char* subvalid = nullptr; // FP64 validity (recursive) of every id of phi_{L-1}
-    float* opcache32 = nullptr;        // values of phi_{L-1}, feature-major (id x N), or null
+    float* opcache32 = nullptr;        // values of phi_{L-1}, sample-major (N x id), or null
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
+    double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r (2 x |phi_{L-1}|)
     int* dup_list = nullptr;           // per sorted entry: partner candidates (kDupSlots)
     unsigned char* dup_ok = nullptr;   // ... confirmed duplicates
     int* dup_cnt = nullptr;            // ... number of partner candidates (-1: overflow)

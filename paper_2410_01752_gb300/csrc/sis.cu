@@ -153,6 +153,14 @@ __device__ __forceinline__ float finalize(T s1, T s2, T sr, T v0, int N, T sum_t
     return (float)(fabs(cov) / (sd * sd_t));
 }
 
+// the same, for + and -: the sums of v' and v' r come from per-operand FP64 sums; only
+// their combination is done in FP64 (where a and b nearly cancel), the rest in T (FP64
+// throughput is a small fraction of FP32 on this part)
+template <typename T>
+__device__ __forceinline__ float finalize_lin(double s1, T s2, double sr, T v0, int N, T sum_t, T sd_t) {
+    return finalize<T>((T)s1, s2, (T)sr, v0, N, sum_t, sd_t);
+}
+
 template <typename T> struct TgtView;
 template <> struct TgtView<float> {
     __device__ static const float* tc(const float* t32, const double*) { return t32; }
@@ -231,6 +239,26 @@ __global__ void k_score_cached(const T* __restrict__ cache, int N, int64_t P, co
         sr = fma(v, tc[s], sr);
     }
     scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
+// per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) and AR[f] = sum_s (x_fs - x_f0) r_s
+// in FP64, with r the centred target the pair kernel uses.  For + and - the pair kernel's
+// sums of v' = (a - a0) +/- (b - b0) and of v' r follow from these exactly.
+template <typename T>
+__global__ void k_opsums(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
+                         double* __restrict__ A1, double* __restrict__ AR) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= P) return;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const double x0 = (double)cache[f];
+    double a = 0.0, ar = 0.0;
+    for (int s = 0; s < N; ++s) {
+        const double v = (double)cache[(size_t)s * P + f] - x0;
+        a += v;
+        ar += v * (double)tc[s];
+    }
+    A1[f] = a;
+    AR[f] = ar;
 }
 
 // the top level's unary sections from cached operand rows: a CTA takes 32 operands and
@@ -315,15 +343,20 @@ template <typename T> __device__ __forceinline__ T rcp(T x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
+// one j operand at one sample: shifted value, raw value, reciprocal, and the target's
+// value at that sample, read with one vector load
+template <typename T> struct Quad;
+template <> struct __align__(16) Quad<float> { float t, v, r, y; };
+template <> struct __align__(32) Quad<double> { double t, v, r, y; };
+
 template <typename T>
-struct __align__(16) PairBuf {
+struct __align__(32) PairBuf {
     T at[TS][TI], av[TS][TI], ar[TS][TI];   // i operands: shifted, raw, reciprocal
-    T bt[TS][TJ], bv[TS][TJ], br[TS][TJ];   // j operands
-    T r[TS];                                // centred target chunk
+    Quad<T> bq[TS][TJ];                     // j operands and the target
 };
 
 template <typename T>
-struct __align__(16) PairSmem {
+struct __align__(32) PairSmem {
     PairBuf<T> buf[2];                      // double buffer: stage chunk c+1 while computing c
     T a0[TI], b0[TJ];                       // sample-0 values
     unsigned char ok[TI + TJ];              // operand validity (FP64, recursive)
@@ -343,8 +376,8 @@ constexpr int kStageSlots = 2 * TS / NG;    // (sample, side) slots per warp and
 
 template <typename T>
 __device__ __forceinline__ void stage_load(const PairArgs& A, const T* __restrict__ Xc, const T* __restrict__ cache,
-                                           const PairSmem<T>& S, int64_t i0, int64_t j0, int s0, int g, int lane,
-                                           T (&v)[kStageSlots]) {
+                                           const T* __restrict__ tc, const PairSmem<T>& S, int64_t i0, int64_t j0,
+                                           int s0, int g, int lane, T (&v)[kStageSlots], T (&y)[kStageSlots / 2]) {
     const int N = A.N;
 #pragma unroll
     for (int q = 0; q < kStageSlots; ++q) {
@@ -360,19 +393,24 @@ __device__ __forceinline__ void stage_load(const PairArgs& A, const T* __restric
             }
         }
         v[q] = x;
+        if (side) y[q >> 1] = s < N ? tc[s] : T(0);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[kStageSlots], int g, int lane) {
+__device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[kStageSlots],
+                                            const T (&y)[kStageSlots / 2], int g, int lane) {
     PairBuf<T>& B = S.buf[b];
 #pragma unroll
     for (int q = 0; q < kStageSlots; ++q) {
         const int s = g + NG * (q >> 1);
         if (q & 1) {
-            B.bt[s][lane] = v[q] - S.b0[lane];
-            B.bv[s][lane] = v[q];
-            B.br[s][lane] = rcp<T>(v[q]);
+            Quad<T> e;
+            e.t = v[q] - S.b0[lane];
+            e.v = v[q];
+            e.r = rcp<T>(v[q]);
+            e.y = y[q >> 1];
+            B.bq[s][lane] = e;
         } else {
             B.at[s][lane] = v[q] - S.a0[lane];
             B.av[s][lane] = v[q];
@@ -381,11 +419,12 @@ __device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[
     }
 }
 
-template <typename T>
+template <typename T, bool LIN>
 __global__ void __launch_bounds__(NG * 32, sizeof(T) == 4 ? 2 : 1)
 k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
               const double* __restrict__ tc64, const TargetStats* __restrict__ st,
-              const unsigned char* __restrict__ subvalid, const T* __restrict__ cache) {
+              const unsigned char* __restrict__ subvalid, const T* __restrict__ cache,
+              const double* __restrict__ A1, const double* __restrict__ AR) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
@@ -424,28 +463,32 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
             Kd[q] = a0 * rb0;
             Ke[q] = b0 * rcp<T>(a0);
         }
-        T s1[5][RI], s2[5][RI], sr[5][RI];
+        // + and -: only the sum of squares per pair (first sums from per-operand sums when
+        // available); *, a/b, b/a: all three sums.  Without per-operand sums (no operand
+        // cache) + and - accumulate all three as well.
+        constexpr bool lin = LIN;
+        T q2[2][RI], l1[2][RI], lr[2][RI];
+        T s1[3][RI], s2[3][RI], sr[3][RI];
 #pragma unroll
-        for (int o = 0; o < 5; ++o)
+        for (int q = 0; q < RI; ++q) {
+            q2[0][q] = q2[1][q] = l1[0][q] = l1[1][q] = lr[0][q] = lr[1][q] = T(0);
 #pragma unroll
-            for (int q = 0; q < RI; ++q) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
+            for (int o = 0; o < 3; ++o) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
+        }
 
-        T pf[kStageSlots];
-        stage_load<T>(A, Xc, cache, S, i0, j0, 0, g, lane, pf);
-        stage_store<T>(S, 0, pf, g, lane);
-        if (tid < TS) S.buf[0].r[tid] = tid < N ? tc[tid] : T(0);
+        T pf[kStageSlots], py[kStageSlots / 2];
+        stage_load<T>(A, Xc, cache, tc, S, i0, j0, 0, g, lane, pf, py);
+        stage_store<T>(S, 0, pf, py, g, lane);
         __syncthreads();
         int b = 0;
         for (int s0 = 0; s0 < N; s0 += TS, b ^= 1) {
             const bool more = s0 + TS < N;
-            if (more) stage_load<T>(A, Xc, cache, S, i0, j0, s0 + TS, g, lane, pf);   // in flight during compute
-            const T rnext = (more && tid < TS && s0 + TS + tid < N) ? tc[s0 + TS + tid] : T(0);
+            if (more) stage_load<T>(A, Xc, cache, tc, S, i0, j0, s0 + TS, g, lane, pf, py);   // in flight during compute
             const PairBuf<T>& B = S.buf[b];
             const int ns = min(TS, N - s0);
-#pragma unroll 2
-            for (int s = 0; s < ns; ++s) {
-                const T r = B.r[s];
-                const T bt = B.bt[s][lane], bv = B.bv[s][lane], br = B.br[s][lane];
+            auto step = [&](int s) {
+                const Quad<T> bq = B.bq[s][lane];
+                const T r = bq.y, bt = bq.t, bv = bq.v, br = bq.r;
                 T at[RI], av[RI], ar[RI];
                 load4(&B.at[s][g * RI], at);
                 load4(&B.av[s][g * RI], av);
@@ -453,44 +496,57 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
 #pragma unroll
                 for (int q = 0; q < RI; ++q) {
                     T v;
-                    v = at[q] + bt;            s1[0][q] += v; s2[0][q] = fma(v, v, s2[0][q]); sr[0][q] = fma(v, r, sr[0][q]);
-                    v = at[q] - bt;            s1[1][q] += v; s2[1][q] = fma(v, v, s2[1][q]); sr[1][q] = fma(v, r, sr[1][q]);
-                    v = fma(av[q], bv, -Km[q]); s1[2][q] += v; s2[2][q] = fma(v, v, s2[2][q]); sr[2][q] = fma(v, r, sr[2][q]);
-                    v = fma(av[q], br, -Kd[q]); s1[3][q] += v; s2[3][q] = fma(v, v, s2[3][q]); sr[3][q] = fma(v, r, sr[3][q]);
-                    v = fma(bv, ar[q], -Ke[q]); s1[4][q] += v; s2[4][q] = fma(v, v, s2[4][q]); sr[4][q] = fma(v, r, sr[4][q]);
+                    v = at[q] + bt;             q2[0][q] = fma(v, v, q2[0][q]);
+                    if constexpr (!LIN) { l1[0][q] += v; lr[0][q] = fma(v, r, lr[0][q]); }
+                    v = at[q] - bt;             q2[1][q] = fma(v, v, q2[1][q]);
+                    if constexpr (!LIN) { l1[1][q] += v; lr[1][q] = fma(v, r, lr[1][q]); }
+                    v = fma(av[q], bv, -Km[q]); s1[0][q] += v; s2[0][q] = fma(v, v, s2[0][q]); sr[0][q] = fma(v, r, sr[0][q]);
+                    v = fma(av[q], br, -Kd[q]); s1[1][q] += v; s2[1][q] = fma(v, v, s2[1][q]); sr[1][q] = fma(v, r, sr[1][q]);
+                    v = fma(bv, ar[q], -Ke[q]); s1[2][q] += v; s2[2][q] = fma(v, v, s2[2][q]); sr[2][q] = fma(v, r, sr[2][q]);
                 }
+            };
+            if (ns == TS) {
+#pragma unroll 4
+                for (int s = 0; s < TS; ++s) step(s);
+            } else {
+                for (int s = 0; s < ns; ++s) step(s);
             }
-            if (more) {
-                stage_store<T>(S, b ^ 1, pf, g, lane);
-                if (tid < TS) S.buf[b ^ 1].r[tid] = rnext;
-            }
+            if (more) stage_store<T>(S, b ^ 1, pf, py, g, lane);
             __syncthreads();
         }
 
         // scores of the (up to) 20 candidates of this thread
         const bool okj = S.ok[TI + lane];
+        const double a1j = lin && j < A.P ? A1[j] : 0.0, arj = lin && j < A.P ? AR[j] : 0.0;
 #pragma unroll
         for (int q = 0; q < RI; ++q) {
             if (!ok[q]) continue;
             const T a0 = S.a0[g * RI + q];
             const int64_t i = iq[q];
             const bool opv = okj && S.ok[g * RI + q];   // both operands valid
+            const double a1i = lin ? A1[i] : 0.0, ari = lin ? AR[i] : 0.0;
             if (A.sec[0] >= 0) {
                 const Section& sc = A.sp->sec[A.sec[0]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], a0 + b0, N, sum_t, sd_t) : -1.f;
+                float v = -1.f;
+                if (opv) v = lin ? finalize_lin<T>(a1i + a1j, q2[0][q], ari + arj, a0 + b0, N, sum_t, sd_t)
+                                 : finalize<T>(l1[0][q], q2[0][q], lr[0][q], a0 + b0, N, sum_t, sd_t);
+                A.scores[sc.base + rank_of(sc, i, j)] = v;
             }
             if (A.sec[1] >= 0) {
                 const Section& sc = A.sp->sec[A.sec[1]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], a0 - b0, N, sum_t, sd_t) : -1.f;
+                float v = -1.f;
+                if (opv) v = lin ? finalize_lin<T>(a1i - a1j, q2[1][q], ari - arj, a0 - b0, N, sum_t, sd_t)
+                                 : finalize<T>(l1[1][q], q2[1][q], lr[1][q], a0 - b0, N, sum_t, sd_t);
+                A.scores[sc.base + rank_of(sc, i, j)] = v;
             }
             if (A.sec[2] >= 0) {
                 const Section& sc = A.sp->sec[A.sec[2]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], Km[q], N, sum_t, sd_t) : -1.f;
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], Km[q], N, sum_t, sd_t) : -1.f;
             }
             if (A.sec[3] >= 0) {
                 const Section& sc = A.sp->sec[A.sec[3]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[3][q], s2[3][q], sr[3][q], Kd[q], N, sum_t, sd_t) : -1.f;
-                A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[4][q], s2[4][q], sr[4][q], Ke[q], N, sum_t, sd_t) : -1.f;
+                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], Kd[q], N, sum_t, sd_t) : -1.f;
+                A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], Ke[q], N, sum_t, sd_t) : -1.f;
             }
         }
     }
@@ -1072,16 +1128,28 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream);
         A.tiles = d_tiles;
         A.n_tiles = (int)tiles.size();
-        const int grid = std::min<int>(A.n_tiles, c->sms * 16);
-        if (fp64) {
-            const size_t sm = sizeof(PairSmem<double>);
-            cudaFuncSetAttribute(k_score_pairs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_score_pairs<double><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc64, c->tc32, c->tc64, c->tstats, c->subvalid, c->opcache64);
-        } else {
-            const size_t sm = sizeof(PairSmem<float>);
-            cudaFuncSetAttribute(k_score_pairs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_score_pairs<float><<<grid, NG * 32, sm, c->stream>>>(A, c->Xc32, c->tc32, c->tc64, c->tstats, c->subvalid, c->opcache32);
+        const double* A1 = nullptr;
+        const double* AR = nullptr;
+        if (cached) {
+            const int go = (int)((A.P + 255) / 256);
+            if (fp64) k_opsums<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+            else k_opsums<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+            c->stats.launches++;
+            A1 = c->opsum;
+            AR = c->opsum + A.P;
         }
+        cudaEventRecord(e1, c->stream);
+        const int grid = std::min<int>(A.n_tiles, c->sms * 16);
+#define SG_PAIRS(TT, LINV, XC, CACHE)                                                                  \
+    do {                                                                                                \
+        const size_t sm = sizeof(PairSmem<TT>);                                                         \
+        cudaFuncSetAttribute(k_score_pairs<TT, LINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_score_pairs<TT, LINV><<<grid, NG * 32, sm, c->stream>>>(A, XC, c->tc32, c->tc64, c->tstats,        \
+                                                                  c->subvalid, CACHE, A1, AR);          \
+    } while (0)
+        if (fp64) { if (cached) SG_PAIRS(double, true, c->Xc64, c->opcache64); else SG_PAIRS(double, false, c->Xc64, c->opcache64); }
+        else { if (cached) SG_PAIRS(float, true, c->Xc32, c->opcache32); else SG_PAIRS(float, false, c->Xc32, c->opcache32); }
+#undef SG_PAIRS
         c->stats.launches++;
         c->stats.screen_pair_launches++;
         st = check_cuda(c, cudaGetLastError(), "score_pairs");
