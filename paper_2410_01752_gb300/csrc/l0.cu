@@ -135,8 +135,8 @@ struct EnumArgs {
     int ld, n, N;
     T syy;                      // y~^T y~ / N
     double sst;                 // N * syy
-    const uint64_t* items;      // packed (prefix, i1 start)
-    int64_t n_items;
+    int cpp;                    // work items per prefix (chunks of kRows i1 rows)
+    int64_t n_items;            // C(n - 2, D - 2) prefixes x cpp
     int* counter;               // work counter
     float tau;                  // pivots at or below: FP32 -> refit list; FP64 -> singular
     int fp32;                   // error-bounded FP32 mode
@@ -156,6 +156,36 @@ template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pr
     k |= (uint64_t)i1 << s; s += 16;
     k |= (uint64_t)i2 << s;
     return k;
+}
+
+// r-th DP-combination in colex order (largest element first): p[DP-1] is the largest m
+// with C(m, DP) <= r, then the rest recursively
+__device__ __forceinline__ int64_t binom2(int64_t m) { return m * (m - 1) / 2; }
+__device__ __forceinline__ int64_t binom3(int64_t m) { return m * (m - 1) * (m - 2) / 6; }
+
+template <int DP> __device__ __forceinline__ void colex_unrank(int64_t r, int (&p)[DP > 0 ? DP : 1]) {
+    if (DP == 0) return;
+    if (DP == 1) { p[0] = (int)r; return; }
+    if (DP == 2) {
+        int64_t m = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
+        while (m > 1 && binom2(m) > r) --m;
+        while (binom2(m + 1) <= r) ++m;
+        p[1] = (int)m;
+        p[0] = (int)(r - binom2(m));
+        return;
+    }
+    if (DP == 3) {
+        int64_t m = (int64_t)cbrt(6.0 * (double)r) + 1;
+        while (m > 2 && binom3(m) > r) --m;
+        while (binom3(m + 1) <= r) ++m;
+        p[DP > 2 ? 2 : 0] = (int)m;
+        r -= binom3(m);
+        int64_t q = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
+        while (q > 1 && binom2(q) > r) --q;
+        while (binom2(q + 1) <= r) ++q;
+        p[1] = (int)q;
+        p[0] = (int)(r - binom2(q));
+    }
 }
 
 // MODE 0: bound (min of RSS + err); MODE 1: band collection
@@ -181,11 +211,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
         if (lane == 0) item = atomicAdd(A.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= A.n_items) break;
-        const uint64_t key = A.items[item];
+        // item -> (prefix in colex order, chunk): prefixes are the (D-2)-combinations of
+        // [0, n-2) ordered by their largest element, so the longest sweeps come first
         int pre[DP > 0 ? DP : 1];
-#pragma unroll
-        for (int m = 0; m < DP; ++m) pre[m] = (int)((key >> (16 * m)) & 0xFFFF);
-        const int i1s = (int)((key >> 48) & 0xFFFF);
+        const int64_t prank = (int64_t)item / A.cpp;
+        const int chunk = item % A.cpp;
+        colex_unrank<DP>(prank, pre);
+        const int i1s = (DP > 0 ? pre[DP - 1] + 1 : 0) + chunk * kRows;
+        if (i1s >= n - 1) continue;
         // prefix factor (warp-uniform, redundant in every lane)
         T L[DP > 0 ? DP : 1][DP > 0 ? DP : 1], invd[DP > 0 ? DP : 1], wv[DP > 0 ? DP : 1];
         T pw2 = T(0), minpiv = T(1e30);
@@ -510,35 +543,11 @@ sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new) {
     return check_cuda(c, cudaGetLastError(), "append_subspace");
 }
 
-// work items: (prefix of D-2 positions, first i1 row), most work first
-static void build_items(int n, int D, std::vector<uint64_t>& items) {
-    items.clear();
-    const int DP = D - 2;
-    std::vector<int> pre(std::max(DP, 1));
-    std::vector<std::pair<int, uint64_t>> tmp;
-    auto emit = [&](int last) {
-        uint64_t key = 0;
-        for (int m = 0; m < DP; ++m) key |= (uint64_t)pre[m] << (16 * m);
-        for (int i1 = last + 1; i1 < n - 1; i1 += kRows)
-            tmp.push_back({i1, key | ((uint64_t)i1 << 48)});
-    };
-    if (DP == 0) {
-        emit(-1);
-    } else {
-        // all DP-combinations of [0, n-2)
-        for (int m = 0; m < DP; ++m) pre[m] = m;
-        while (true) {
-            if (pre[DP - 1] <= n - 3) emit(pre[DP - 1]);
-            int j = DP - 1;
-            while (j >= 0 && pre[j] == n - 3 - (DP - 1 - j)) --j;
-            if (j < 0) break;
-            ++pre[j];
-            for (int m = j + 1; m < DP; ++m) pre[m] = pre[m - 1] + 1;
-        }
-    }
-    std::stable_sort(tmp.begin(), tmp.end(), [](auto& a, auto& b) { return a.first < b.first; });
-    items.reserve(tmp.size());
-    for (auto& t : tmp) items.push_back(t.second);
+static int64_t binom_host(int64_t n, int k) {
+    if (k < 0 || n < k) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
 }
 
 template <typename T>
@@ -572,17 +581,11 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
     cudaEventRecord(e0, c->stream);
-    // work items
-    std::vector<uint64_t> items;
-    if (D >= 2) build_items(n, D, items);
-    if ((int64_t)items.size() > c->prefix_cap) {
-        if (c->prefixes) cudaFreeAsync(c->prefixes, c->stream);
-        c->prefix_cap = (int64_t)items.size();
-        sisso_status st = check_cuda(c, cudaMallocAsync(&c->prefixes, sizeof(uint64_t) * c->prefix_cap, c->stream), "items");
-        if (st) return st;
-    }
-    if (!items.empty())
-        cudaMemcpyAsync(c->prefixes, items.data(), sizeof(uint64_t) * items.size(), cudaMemcpyHostToDevice, c->stream);
+    // work items: (D-2)-prefixes of [0, n-2) in colex order x chunks of kRows i1 rows,
+    // decoded in the kernel
+    const int DPh = D - 2;
+    const int cpp = D >= 2 ? std::max(1, (n - 1 - DPh + kRows - 1) / kRows) : 1;
+    const int64_t n_items = D >= 2 ? binom_host(n - 2, DPh) * cpp : 0;
     unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(c->work + 2);
     unsigned long long* examined = ub_key + 1;
     unsigned long long* min_key = ub_key + 2;
@@ -595,7 +598,7 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     if (fp32) {
         EnumArgs<float> A{};
         A.G = G32; A.b = b32; A.ld = ld; A.n = n; A.N = c->N; A.syy = (float)syy; A.sst = sst;
-        A.items = c->prefixes; A.n_items = (int64_t)items.size(); A.counter = c->work;
+        A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
         A.tau = kPivotMin32; A.fp32 = 1; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;
@@ -605,7 +608,7 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     } else {
         EnumArgs<double> A{};
         A.G = G; A.b = b; A.ld = ld; A.n = n; A.N = c->N; A.syy = syy; A.sst = sst;
-        A.items = c->prefixes; A.n_items = (int64_t)items.size(); A.counter = c->work;
+        A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
         A.tau = (float)kPivotMin; A.fp32 = 0; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;

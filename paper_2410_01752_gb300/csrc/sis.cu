@@ -754,8 +754,8 @@ __global__ void k_dup_find(const double* __restrict__ sk, const int* __restrict_
     for (int r = 0; r < kProbes; ++r) pc[r] = probe[(size_t)src * kProbes + r];
     // keep the kDupSlots partners with the smallest keys: S members first (key -1), then
     // window entries by id (a cluster's earliest-visited member is its smallest id)
-    int64_t key[kDupSlots];
-    int val[kDupSlots];
+    int64_t key[kDupSlots] = {};
+    int val[kDupSlots] = {};
     int n = 0, total = 0;
     auto consider = [&](int m, int64_t k) {
         if (!probes_match(pc, probe + (size_t)m * kProbes)) return;
