@@ -196,6 +196,42 @@ sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, d
                              int n, int D, const int64_t* gid, int precision, int* best_pos,
                              double* best_rss, int64_t* examined);
 
+/* ---- allocation-free l0 search --------------------------------------------------------
+ *
+ * sisso_l0_search_noalloc: the same search as sisso_l0_search, for callers that cannot
+ * allocate device memory — for example a plug-in that may only use the memory its host
+ * hands to it, a framework that routes every device allocation through its own pool and
+ * forbids raw cudaMalloc, or a latency-critical loop that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It needs no context and allocates nothing:
+ * its working memory (about 1.8 MB) is one array inside the library, reserved on every
+ * device that loads the library until the process exits.  The paper has no counterpart;
+ * this is an interface convenience.
+ *
+ * G (n x n, row-major, FP64), b (n) and gid (n) may be host or device memory; N is the
+ * number of samples behind G and b (RSS = N (syy - b_E^T G_E^-1 b_E)).  precision is
+ * SISSO_PREC_FP32 (error-bounded FP32 enumeration and FP64 refit) or SISSO_PREC_FP64.
+ * stream: a cudaStream_t, or NULL for the legacy default stream.  Outputs are HOST memory:
+ * best_pos (D positions, ascending), *best_rss, *examined (C(n, D)); the call returns
+ * once they are written.
+ *
+ * Limits: n <= SISSO_NOALLOC_MAX_N; the FP64 refit band holds at most
+ * SISSO_NOALLOC_MAX_BAND subsets.  Larger problems return SISSO_ERR_CAPACITY (use
+ * sisso_l0_search).  Other errors: SISSO_ERR_ARG (bad sizes, NULL pointers),
+ * SISSO_ERR_NUMERIC (every subset singular), SISSO_ERR_CUDA.
+ *
+ * The first call on each device looks up the device address of the working array
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call on a device shares the one array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that overlap on the
+ * GPU — from two host threads or two streams — race and must be serialised by the caller.
+ */
+#define SISSO_NOALLOC_MAX_N 256
+#define SISSO_NOALLOC_MAX_BAND 65536
+
+sisso_status sisso_l0_search_noalloc(const double* G, const double* b, double syy, int N, int n, int D,
+                                     const int64_t* gid, int precision, void* stream, int* best_pos,
+                                     double* best_rss, int64_t* examined);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstring>
+#include <mutex>
 
 namespace sg {
 namespace {
@@ -663,3 +664,154 @@ sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w) {
 }
 
 }  // namespace sg
+
+// =====================================================================================
+// allocation-free l0 search: the kernels above, with their working memory in one
+// file-scope device array instead of context buffers
+// =====================================================================================
+namespace sg {
+namespace {
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaN = SISSO_NOALLOC_MAX_N;
+constexpr size_t kNaBand = SISSO_NOALLOC_MAX_BAND;
+constexpr size_t kNaG64 = 0;                                              // n x n FP64
+constexpr size_t kNaG32 = na_align(kNaG64 + kNaN * kNaN * sizeof(double)); // n x n FP32
+constexpr size_t kNaB64 = na_align(kNaG32 + kNaN * kNaN * sizeof(float));
+constexpr size_t kNaB32 = na_align(kNaB64 + kNaN * sizeof(double));
+constexpr size_t kNaGid = na_align(kNaB32 + kNaN * sizeof(float));
+constexpr size_t kNaBandOff = na_align(kNaGid + kNaN * sizeof(int64_t));
+constexpr size_t kNaRss = na_align(kNaBandOff + kNaBand * sizeof(uint64_t));
+constexpr size_t kNaCtr = na_align(kNaRss + kNaBand * sizeof(double));    // counters (64 B)
+constexpr size_t kNaWin = na_align(kNaCtr + 64);
+constexpr size_t kNaTotal = na_align(kNaWin + sizeof(Winner));
+
+// the working array: reserved on every device that loads the library
+static __device__ __align__(256) unsigned char g_l0_scratch[kNaTotal];
+
+std::mutex g_na_mu;
+unsigned char* g_na_addr[256] = {};    // device address of g_l0_scratch, per device ordinal
+
+__global__ void k_na_cast(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+template <typename T>
+cudaError_t na_enum(const EnumArgs<T>& A, int D, int mode, int sms, cudaStream_t st) {
+    const int DP = D - 2;
+    const size_t smem = (size_t)kWarps * (DP + 2) * A.n * sizeof(T);
+    const int grid = sms * 2;
+#define SG_NA(DPV, MV)                                                                                   \
+    do {                                                                                                 \
+        cudaFuncSetAttribute(k_l0_enum<T, DPV, MV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_l0_enum<T, DPV, MV><<<grid, kWarps * 32, smem, st>>>(A);                                       \
+    } while (0)
+    if (D == 1) {
+        if (mode == 0) k_l0_single<T, 0><<<(A.n + 255) / 256, 256, 0, st>>>(A);
+        else k_l0_single<T, 1><<<(A.n + 255) / 256, 256, 0, st>>>(A);
+    } else if (DP == 0) { if (mode == 0) SG_NA(0, 0); else SG_NA(0, 1); }
+    else if (DP == 1) { if (mode == 0) SG_NA(1, 0); else SG_NA(1, 1); }
+    else { if (mode == 0) SG_NA(2, 0); else SG_NA(2, 1); }
+#undef SG_NA
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" sisso_status sisso_l0_search_noalloc(const double* G, const double* b, double syy, int N, int n, int D,
+                                                const int64_t* gid, int precision, void* stream, int* best_pos,
+                                                double* best_rss, int64_t* examined) {
+    using namespace sg;
+    if (!G || !b || !gid || !best_pos || N < 1 || n < 1 || D < 1 || D > SISSO_MAX_DIM || n < D ||
+        (precision != SISSO_PREC_FP32 && precision != SISSO_PREC_FP64) || !(syy > 0.0))
+        return SISSO_ERR_ARG;
+    if (n > SISSO_NOALLOC_MAX_N) return SISSO_ERR_CAPACITY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SISSO_ERR_CUDA;
+    unsigned char* base = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lock(g_na_mu);
+        if (!g_na_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_l0_scratch) != cudaSuccess || !p) return SISSO_ERR_CUDA;
+            g_na_addr[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_na_addr[dev];
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SISSO_ERR_CUDA;
+    double* dG = reinterpret_cast<double*>(base + kNaG64);
+    float* dG32 = reinterpret_cast<float*>(base + kNaG32);
+    double* db = reinterpret_cast<double*>(base + kNaB64);
+    float* db32 = reinterpret_cast<float*>(base + kNaB32);
+    int64_t* dgid = reinterpret_cast<int64_t*>(base + kNaGid);
+    uint64_t* band = reinterpret_cast<uint64_t*>(base + kNaBandOff);
+    double* band_rss = reinterpret_cast<double*>(base + kNaRss);
+    int* counter = reinterpret_cast<int*>(base + kNaCtr);
+    unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(base + kNaCtr + 8);
+    unsigned long long* ex_key = ub_key + 1;
+    unsigned long long* min_key = ub_key + 2;
+    unsigned int* band_count = reinterpret_cast<unsigned int*>(base + kNaCtr + 32);
+    Winner* win = reinterpret_cast<Winner*>(base + kNaWin);
+
+    const size_t nn = (size_t)n * n;
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    ok(cudaMemcpyAsync(dG, G, sizeof(double) * nn, cudaMemcpyDefault, st));
+    ok(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyDefault, st));
+    ok(cudaMemcpyAsync(dgid, gid, sizeof(int64_t) * n, cudaMemcpyDefault, st));
+    // what must start at zero (or at the maximum key) for this call
+    ok(cudaMemsetAsync(base + kNaCtr, 0, 64, st));
+    ok(cudaMemsetAsync(ub_key, 0xFF, sizeof(unsigned long long), st));
+    ok(cudaMemsetAsync(min_key, 0xFF, sizeof(unsigned long long), st));
+    if (e != cudaSuccess) return SISSO_ERR_CUDA;
+    k_na_cast<<<std::max(1, std::min(sms * 4, (int)((nn + 255) / 256))), 256, 0, st>>>(dG, dG32, (int64_t)nn);
+    k_na_cast<<<1, 256, 0, st>>>(db, db32, n);
+    const bool fp32 = precision != SISSO_PREC_FP64;
+    const double sst = syy * N;
+    const int DPh = D - 2;
+    const int cpp = D >= 2 ? std::max(1, (n - 1 - DPh + kRows - 1) / kRows) : 1;
+    const int64_t n_items = D >= 2 ? binom_host(n - 2, DPh) * cpp : 0;
+    if (fp32) {
+        EnumArgs<float> A{};
+        A.G = dG32; A.b = db32; A.ld = n; A.n = n; A.N = N; A.syy = (float)syy; A.sst = sst;
+        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = kPivotMin32; A.fp32 = 1;
+        A.ub_key = ub_key; A.win = win; A.band = band; A.band_count = band_count;
+        A.band_cap = (int64_t)kNaBand; A.examined = ex_key;
+        ok(na_enum(A, D, 0, sms, st));
+        k_set_thr<<<1, 1, 0, st>>>(win, ub_key, 0.0);
+        ok(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        ok(na_enum(A, D, 1, sms, st));
+    } else {
+        EnumArgs<double> A{};
+        A.G = dG; A.b = db; A.ld = n; A.n = n; A.N = N; A.syy = syy; A.sst = sst;
+        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = (float)kPivotMin; A.fp32 = 0;
+        A.ub_key = ub_key; A.win = win; A.band = band; A.band_count = band_count;
+        A.band_cap = (int64_t)kNaBand; A.examined = ex_key;
+        ok(na_enum(A, D, 0, sms, st));
+        k_set_thr<<<1, 1, 0, st>>>(win, ub_key, 2.0 * kRssTie * sst + 1e-14 * sst);
+        ok(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        ok(na_enum(A, D, 1, sms, st));
+    }
+    k_refit<<<sms * 4, 256, 0, st>>>(dG, db, n, syy, N, D, band, band_count, (int64_t)kNaBand, band_rss, min_key);
+    k_winner<<<1, 1024, 0, st>>>(band, band_rss, band_count, (int64_t)kNaBand, min_key, kRssTie * sst, dgid, D, win);
+    ok(cudaGetLastError());
+    unsigned cnt = 0;
+    unsigned long long ex = 0;
+    Winner w{};
+    ok(cudaMemcpyAsync(&cnt, band_count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(&ex, ex_key, sizeof(ex), cudaMemcpyDeviceToHost, st));
+    ok(cudaMemcpyAsync(&w, win, sizeof(Winner), cudaMemcpyDeviceToHost, st));
+    ok(cudaStreamSynchronize(st));
+    if (e != cudaSuccess) return SISSO_ERR_CUDA;
+    if ((size_t)cnt > kNaBand) return SISSO_ERR_CAPACITY;
+    if (!w.found) return SISSO_ERR_NUMERIC;
+    for (int j = 0; j < D; ++j) best_pos[j] = w.pos[j];
+    if (best_rss) *best_rss = w.rss_gram;
+    if (examined) *examined = (int64_t)ex;
+    return SISSO_OK;
+}

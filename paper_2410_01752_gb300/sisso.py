@@ -31,7 +31,10 @@ EXPORTS = [
     "sisso_get_sis", "sisso_feature_count", "sisso_feature_expr", "sisso_get_stats",
     "sisso_last_error", "sisso_destroy", "sisso_eval_features", "sisso_score_all",
     "sisso_sis_step", "sisso_l0_search", "sisso_space_sizes", "sisso_space_expr",
+    "sisso_l0_search_noalloc",
 ]
+NOALLOC_MAX_N = 256
+NOALLOC_MAX_BAND = 65536
 
 
 class SissoError(RuntimeError):
@@ -94,6 +97,8 @@ def load() -> C.CDLL:
     L.sisso_l0_search.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, C.c_int,
                                   C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_sizes.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, i64p]
+    L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
+                                          C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
     for name in EXPORTS:
         if name not in ("sisso_default_opts", "sisso_last_error", "sisso_destroy"):
@@ -130,6 +135,24 @@ def space_expr(d: int, op_set: int, rung: int, grammar: int, fid: int) -> str:
     if st:
         raise SissoError(st, "space_expr")
     return buf.value.decode()
+
+
+def l0_search_noalloc(G, b, syy: float, N: int, D: int, gid, precision: int = PREC_FP32, stream=None):
+    """Exhaustive l0 over every D-subset of len(b) standardised features without a context
+    and without allocating device memory (sisso_l0_search_noalloc): for callers that may
+    not allocate.  Returns (positions, RSS, subsets examined)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    gid = np.ascontiguousarray(gid, dtype=np.int64)
+    pos = np.zeros(D, dtype=np.int32)
+    rss, ex = C.c_double(), C.c_int64()
+    st = load().sisso_l0_search_noalloc(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), int(N),
+                                        b.size, D, C.c_void_p(gid.ctypes.data), precision,
+                                        C.c_void_p(getattr(stream, "cuda_stream", stream)) if stream else None,
+                                        pos.ctypes.data_as(C.POINTER(C.c_int)), C.byref(rss), C.byref(ex))
+    if st:
+        raise SissoError(st, "l0_search_noalloc")
+    return [int(p) for p in pos], rss.value, ex.value
 
 
 @dataclass
