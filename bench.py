@@ -126,6 +126,26 @@ def cpu_baseline_sample(P, seconds: float, seed: int = 0):
     return m / dt, m, dt, th
 
 
+def captured_traffic():
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary, or None
+    when the kernel's source has changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_score_pairs_rung3_N1000_d10_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha256")))
+    h = hashlib.sha256()
+    for f in ("sis.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2410_01752_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    sha = next((v.strip() for k, v in vals.items() if k.startswith("source_sha256")), "")
+    if sha != h.hexdigest():
+        return None
+    return int(vals["traffic_bytes_per_launch"].strip())
+
+
 def top_binary_candidates(sizes, n_unary_ops):
     """Candidates of the top level's binary sections (the pair kernel's work)."""
     L = len(sizes) - 1
@@ -276,8 +296,9 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    full_size = (P.N, P.d) == (1000, 10)
     roof = {"bound": "alu", "kernel": "k_score_pairs<float>", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic() if full_size else None,
             "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (measured max SM clock)",
             "flop_per_launch": flop_launch, "launch_ms": avg_launch_s * 1e3,
             "algorithmic_unit": f"{FP32_FLOP_PER_CAND_SAMPLE} flop per candidate-sample x {cand_pair} candidates x {P.N} samples"}
