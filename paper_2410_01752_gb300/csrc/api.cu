@@ -49,7 +49,7 @@ void free_all(sisso_ctx* c) {
                     c->S_sorted, c->Z, c->Zmean, c->Zsd, c->G64, c->b64, c->G32, c->b32, c->resid, c->ymom,
                     c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
-                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum};
+                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -152,7 +152,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     cudaMemcpyAsync(c->space_dev, &c->space, sizeof(Space), cudaMemcpyHostToDevice, c->stream);
     // standardised FP64 vectors of the screening window, for the duplicate rule: up to
     // 4 GB (the walk evaluates on the fly when a window does not fit)
-    c->zcap = std::min<int64_t>(c->surv_cap, ((int64_t)4 << 30) / ((int64_t)8 * N));
+    c->zcap = std::min<int64_t>(c->surv_cap, ((int64_t)16 << 30) / ((int64_t)8 * N));
     if ((st = dalloc(c, c->zcache, (size_t)c->zcap * Nn, "zcache")) ||
         (st = dalloc(c, c->subvalid, (size_t)c->space.phi[rung - 1], "subvalid")) ||
         (st = dalloc(c, c->dup_list, (size_t)c->sort_cap * kDupSlots, "dup_list")) ||
@@ -171,6 +171,10 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
             if (!st) st = dalloc(c, c->opsum, 2 * (size_t)c->space.phi[rung - 1], "opsum");
             if (st) return bail(st);
         }
+        // FP64 operand values (feature-major) for the exact re-score and duplicate checks
+        if ((size_t)c->space.phi[rung - 1] * Nn * sizeof(double) <= ((size_t)16 << 30)) {
+            if ((st = dalloc(c, c->opval64, (size_t)c->space.phi[rung - 1] * Nn, "opval64"))) return bail(st);
+        }
     }
     if ((st = check_cuda(c, cudaMallocHost(&c->walk_h, sizeof(WalkResult)), "walk_h")) ||
         (st = check_cuda(c, cudaMallocHost(&c->win_h, sizeof(Winner)), "win_h")))
@@ -188,7 +192,8 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     int h_bad = 0;
     cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     // validity of the operand features (depends on X only), moments of y, y~ = y - mean(y)
-    st = compute_subvalid(c);
+    st = fill_val64(c);
+    if (!st) st = compute_subvalid(c);
     if (!st) st = fill_opcache(c);
     if (!st) st = prepare_target(c, c->y64);
     cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);

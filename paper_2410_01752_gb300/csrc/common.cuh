@@ -241,6 +241,35 @@ __host__ __device__ inline bool root_is_addsub(const Prog& p) {
 }
 
 constexpr double kCancelRel = 1e-9;    // root +/- with max|v| <= this * max(|a|+|b|): zero
+
+// A feature written over the FP64 operand values V (feature-major rows of N samples, one
+// row per id of phi_{L-1}): ids below P are rows; top-level ids are one operator on one
+// or two rows.
+struct OpRef {
+    int64_t a, b;   // rows (b = -1: unary or direct)
+    int op;         // -1: row a itself
+};
+
+__host__ __device__ inline bool make_opref(const Space& sp, int64_t id, OpRef& r) {
+    const int64_t P = sp.phi[sp.rung - 1];
+    if (id >= 0 && id < P) { r.a = id; r.b = -1; r.op = -1; return true; }
+    int level, op; int64_t a, b;
+    if (!decode(sp, id, level, op, a, b)) return false;
+    r.a = a; r.b = b; r.op = op;
+    return true;
+}
+
+// value at sample s; mag = |a| + |b| for a root + or -, |v| otherwise
+__device__ __forceinline__ double opref_val(const OpRef& r, const double* __restrict__ V, int N, int s,
+                                            double& mag) {
+    const double x = V[(size_t)r.a * N + s];
+    if (r.op < 0) { mag = fabs(x); return x; }
+    if (r.b < 0) { const double v = op_unary<double>(r.op, x); mag = fabs(v); return v; }
+    const double y = V[(size_t)r.b * N + s];
+    const double v = op_binary<double>(r.op, x, y);
+    mag = (r.op == ADD || r.op == SUB) ? fabs(x) + fabs(y) : fabs(v);
+    return v;
+}
 constexpr int kProbes = 8;             // standardised values kept per candidate for dedup
 constexpr int kDupSlots = 16;          // partner candidates kept per screened candidate
 
@@ -346,6 +375,7 @@ struct sisso_ctx {
     float* opcache32 = nullptr;        // values of phi_{L-1}, sample-major (N x id), or null
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
     double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r (2 x |phi_{L-1}|)
+    double* opval64 = nullptr;         // FP64 values of phi_{L-1}, feature-major (id x N), or null
     int* dup_list = nullptr;           // per sorted entry: partner candidates (kDupSlots)
     unsigned char* dup_ok = nullptr;   // ... confirmed duplicates
     int* dup_cnt = nullptr;            // ... number of partner candidates (-1: overflow)
@@ -408,6 +438,7 @@ sisso_status check_cuda(sisso_ctx* c, cudaError_t e, const char* what);
 // screening (sis.cu)
 sisso_status compute_subvalid(sisso_ctx* c);
 sisso_status fill_opcache(sisso_ctx* c);
+sisso_status fill_val64(sisso_ctx* c);
 sisso_status prepare_target(sisso_ctx* c, const double* target_dev);
 sisso_status score_all(sisso_ctx* c, int precision);
 sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_prev,

@@ -56,17 +56,19 @@ __device__ __forceinline__ double okey_inv(unsigned long long k) {
 // subspace: standardised rows and Gram growth
 // ---------------------------------------------------------------------------------
 __global__ void k_standardise(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const int64_t* __restrict__ ids,
-                              int row0, double* __restrict__ Z, double* __restrict__ mean_out,
-                              double* __restrict__ sd_out) {
+                              int row0, const double* __restrict__ V, double* __restrict__ Z,
+                              double* __restrict__ mean_out, double* __restrict__ sd_out) {
     __shared__ double red[32];
     __shared__ double sh_mean, sh_sd;
     const int row = row0 + blockIdx.x;
     Prog p;
-    const bool ok = build_prog(*sp, ids[row], p);
+    OpRef ref{};
+    const bool ok = V ? make_opref(*sp, ids[row], ref) : build_prog(*sp, ids[row], p);
     double* z = Z + (size_t)row * N;
     double s = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double v = ok ? eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) : 0.0;
+        double mg;
+        const double v = !ok ? 0.0 : V ? opref_val(ref, V, N, i, mg) : eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; });
         z[i] = v;
         s += v;
     }
@@ -536,7 +538,8 @@ __global__ void k_model(const double* __restrict__ G, const double* __restrict__
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new) {
     if (n_new <= 0) return SISSO_OK;
     const int n = n_old + n_new;
-    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->Z, c->Zmean, c->Zsd);
+    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->opval64, c->Z,
+                                                 c->Zmean, c->Zsd);
     dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
     k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,
                                                       c->G32, c->b32);

@@ -97,8 +97,20 @@ __global__ void k_prepare_target(const double* __restrict__ t, int N, double* __
 // FP64 validity of ids [lo, hi) (one level), one warp per id: the value rules (finite,
 // |v| <= 1e12, not identically zero, std > 1e-6 max|v|) and the operands' validity
 // (lower levels, already computed)
+// FP64 values of every id of phi_{L-1}, feature-major (one warp per id, lanes over samples)
+__global__ void k_fill_val64(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t n_ids,
+                             double* __restrict__ V) {
+    const int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (id >= n_ids) return;
+    Prog p;
+    const bool ok = build_prog(*sp, id, p);
+    for (int s = lane; s < N; s += 32)
+        V[(size_t)id * N + s] = ok ? eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : NAN;
+}
+
 __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t lo,
-                           int64_t hi, unsigned char* __restrict__ valid) {
+                           int64_t hi, const double* __restrict__ V, unsigned char* __restrict__ valid) {
     const int64_t id = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (id >= hi) return;
@@ -108,9 +120,16 @@ __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restric
     if (level > 0 && (!valid[a] || (b >= 0 && !valid[b]))) { if (lane == 0) valid[id] = 0; return; }
     double s = 0.0, mx = 0.0, mo = 0.0;
     int bad = 0;
+    const bool addsub = level > 0 && (op == ADD || op == SUB);
     for (int i = lane; i < N; i += 32) {
         double mag;
-        const double v = eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+        double v;
+        if (V) {
+            v = V[(size_t)id * N + i];
+            mag = addsub ? fabs(V[(size_t)a * N + i]) + fabs(V[(size_t)b * N + i]) : fabs(v);
+        } else {
+            v = eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+        }
         if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
         s += v;
         mx = fmax(mx, fabs(v));
@@ -124,7 +143,7 @@ __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restric
     double ss = 0.0;
     if (!bad)
         for (int i = lane; i < N; i += 32) {
-            const double v = eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean;
+            const double v = (V ? V[(size_t)id * N + i] : eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; })) - mean;
             ss += v * v;
         }
     ss = warp_sum(ss);
@@ -241,6 +260,37 @@ __global__ void k_score_cached(const T* __restrict__ cache, int N, int64_t P, co
     scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
 }
 
+constexpr int kUnaryMax = 8;
+struct UnaryArgs {
+    int n_ops;
+    int op[kUnaryMax];
+    int64_t base[kUnaryMax];   // first id of each operator's section
+    int64_t Q, P;              // operands: new_{L-1} = [Q, P)
+    int N;
+};
+
+// the same with one warp per id (few ids, many samples): lanes split the samples
+template <typename T>
+__global__ void k_score_cached_w(const T* __restrict__ cache, int N, int64_t P, const float* tc32,
+                                 const double* tc64, const TargetStats* st, int64_t lo, int64_t hi,
+                                 const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
+    const int64_t id = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (id >= hi) return;
+    if (!subvalid[id]) { if (lane == 0) scores[id] = -1.f; return; }
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const T v0 = cache[id];
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s = lane; s < N; s += 32) {
+        const T v = cache[(size_t)s * P + id] - v0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+        sr = fma(v, tc[s], sr);
+    }
+    s1 = warp_sum(s1); s2 = warp_sum(s2); sr = warp_sum(sr);
+    if (lane == 0) scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
 // per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) and AR[f] = sum_s (x_fs - x_f0) r_s
 // in FP64, with r the centred target the pair kernel uses.  For + and - the pair kernel's
 // sums of v' = (a - a0) +/- (b - b0) and of v' r follow from these exactly.
@@ -261,17 +311,58 @@ __global__ void k_opsums(const T* __restrict__ cache, int N, int64_t P, const fl
     AR[f] = ar;
 }
 
+// the same with one warp per operand
+template <typename T>
+__global__ void k_opsums_w(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
+                           double* __restrict__ A1, double* __restrict__ AR) {
+    const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (f >= P) return;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const double x0 = (double)cache[f];
+    double a = 0.0, ar = 0.0;
+    for (int s = lane; s < N; s += 32) {
+        const double v = (double)cache[(size_t)s * P + f] - x0;
+        a += v;
+        ar += v * (double)tc[s];
+    }
+    a = warp_sum(a);
+    ar = warp_sum(ar);
+    if (lane == 0) { A1[f] = a; AR[f] = ar; }
+}
+
+// the top level's unary sections with one warp per candidate (few operands, many samples)
+template <typename T>
+__global__ void k_score_unary_w(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
+                                const TargetStats* st, const unsigned char* __restrict__ subvalid,
+                                float* __restrict__ scores) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nz = U.P - U.Q;
+    if (w >= nz * U.n_ops) return;
+    const int k = (int)(w / nz);
+    const int64_t z = U.Q + w % nz;
+    const int op = U.op[k];
+    const int N = U.N;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    if (!subvalid[z]) { if (lane == 0) scores[U.base[k] + (z - U.Q)] = -1.f; return; }
+    const T v0 = op_unary<T>(op, cache[z]);
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s = lane; s < N; s += 32) {
+        const T v = op_unary<T>(op, cache[(size_t)s * U.P + z]) - v0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+        sr = fma(v, tc[s], sr);
+    }
+    s1 = warp_sum(s1); s2 = warp_sum(s2); sr = warp_sum(sr);
+    if (lane == 0)
+        scores[U.base[k] + (z - U.Q)] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
 // the top level's unary sections from cached operand rows: a CTA takes 32 operands and
 // every enabled unary operator (warp w = operator w, lane = operand), 32-sample chunks
 // staged in shared memory
-constexpr int kUnaryMax = 8;
-struct UnaryArgs {
-    int n_ops;
-    int op[kUnaryMax];
-    int64_t base[kUnaryMax];   // first id of each operator's section
-    int64_t Q, P;              // operands: new_{L-1} = [Q, P)
-    int N;
-};
+
 
 template <typename T>
 __global__ void __launch_bounds__(kUnaryMax * 32)
@@ -622,15 +713,18 @@ __global__ void k_compact(const float* __restrict__ scores, int64_t n, const uns
 __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict__ Xc, int N,
                           const double* __restrict__ tc, const TargetStats* __restrict__ st,
                           const int64_t* __restrict__ ids, int n, const unsigned char* __restrict__ subvalid,
-                          double* score, double* mean_out, double* sd_out, int* valid_out,
-                          double* __restrict__ probe, double* __restrict__ zc) {
+                          const double* __restrict__ V, double* score, double* mean_out, double* sd_out,
+                          int* valid_out, double* __restrict__ probe, double* __restrict__ zc) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n) return;
     Prog p;
     int level, op; int64_t a, b;
     const int64_t id = ids[w];
-    bool built = decode(*sp, id, level, op, a, b) && build_prog(*sp, id, p);
-    if (built && level > 0 && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
+    const int64_t Pbot = sp->phi[sp->rung - 1];
+    OpRef ref{};
+    bool built = decode(*sp, id, level, op, a, b) && (V ? make_opref(*sp, id, ref) : build_prog(*sp, id, p));
+    if (built && id < Pbot && !subvalid[id]) built = false;                                  // exact, recursive
+    if (built && id >= Pbot && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
     if (!built) {
         if (lane == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
         if (lane < kProbes) probe[(size_t)w * kProbes + lane] = 0.0;
@@ -639,9 +733,12 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
     double* z = zc ? zc + (size_t)w * N : nullptr;
     double s = 0.0, mx = 0.0, mo = 0.0;
     int bad = 0;
+    auto value = [&](int i, double& mag) -> double {
+        return V ? opref_val(ref, V, N, i, mag) : eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+    };
     for (int i = lane; i < N; i += 32) {
         double mag;
-        const double v = eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+        const double v = value(i, mag);
         if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
         s += v;
         mx = fmax(mx, fabs(v));
@@ -652,12 +749,15 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
     s = warp_sum(s);
     mx = warp_max(mx);
     mo = warp_max(mo);
-    const bool cancelled = root_is_addsub(p) && mx <= kCancelRel * mo;
+    // identically zero: a top-level + or - whose operands cancel (lower ids: in subvalid)
+    const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
+    const bool cancelled = top_addsub && mx <= kCancelRel * mo;
     const double mean = s / N;
     double ss = 0.0, sc = 0.0;
     if (!bad) {
         for (int i = lane; i < N; i += 32) {
-            const double v = (z ? z[i] : eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; })) - mean;
+            double mag;
+            const double v = (z ? z[i] : value(i, mag)) - mean;
             ss += v * v;
             sc += v * tc[i];
         }
@@ -671,7 +771,8 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
         for (int i = lane; i < N; i += 32) z[i] = (z[i] - mean) * inv;
     if (lane < kProbes) {
         const int i = (int)(((int64_t)lane * N) / kProbes);
-        const double v = z ? z[i] : (eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }) - mean) * inv;
+        double mag;
+        const double v = z ? z[i] : (value(i, mag) - mean) * inv;
         probe[(size_t)w * kProbes + lane] = v;
     }
     if (lane == 0) {
@@ -782,8 +883,8 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
                               const int* __restrict__ ssrc, const int64_t* __restrict__ sid, int n_sorted,
                               const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_mean,
                               const double* __restrict__ sv_sd, const double* __restrict__ zc,
-                              const int* __restrict__ dup_list, const int* __restrict__ dup_cnt,
-                              unsigned char* __restrict__ dup_ok) {
+                              const double* __restrict__ V, const int* __restrict__ dup_list,
+                              const int* __restrict__ dup_cnt, unsigned char* __restrict__ dup_ok) {
     const int lane = threadIdx.x & 31;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_sorted; i += (gridDim.x * blockDim.x) >> 5) {
         const int raw = dup_cnt[i];
@@ -791,19 +892,24 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
         if (cnt <= 0) continue;
         const int src = ssrc[i];
         Prog pc;
-        if (!zc) build_prog(*sp, sid[i], pc);
+        OpRef rc{};
+        if (!zc) { if (V) make_opref(*sp, sid[i], rc); else build_prog(*sp, sid[i], pc); }
         const double mc = sv_mean[src], dc = sv_sd[src];
         for (int q = 0; q < cnt; ++q) {
             const int m = dup_list[(size_t)i * kDupSlots + q];
             Prog pm;
-            if (!zc) build_prog(*sp, sv_ids[m], pm);
+            OpRef rm{};
+            if (!zc) { if (V) make_opref(*sp, sv_ids[m], rm); else build_prog(*sp, sv_ids[m], pm); }
             const double mm = sv_mean[m], dm = sv_sd[m];
             double e1 = 0.0, e2 = 0.0;
             for (int t = lane; t < N; t += 32) {
-                double za, zb;
+                double za, zb, mg;
                 if (zc) {
                     za = zc[(size_t)src * N + t];
                     zb = zc[(size_t)m * N + t];
+                } else if (V) {
+                    za = (opref_val(rc, V, N, t, mg) - mc) / dc;
+                    zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
                 } else {
                     za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
                     zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
@@ -833,9 +939,10 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
        const int64_t* __restrict__ sid, const int* __restrict__ ssrc, int n_sorted,
        const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_score,
        const double* __restrict__ sv_mean, const double* __restrict__ sv_sd,
-       const double* __restrict__ probe, const double* __restrict__ zc, const int* __restrict__ dup_list,
-       const int* __restrict__ dup_cnt, const unsigned char* __restrict__ dup_ok, int s_off, int nS,
-       int k, unsigned char* __restrict__ removed, unsigned char* __restrict__ accepted, WalkResult* out) {
+       const double* __restrict__ probe, const double* __restrict__ zc, const double* __restrict__ V,
+       const int* __restrict__ dup_list, const int* __restrict__ dup_cnt, const unsigned char* __restrict__ dup_ok,
+       int s_off, int nS, int k, unsigned char* __restrict__ removed, unsigned char* __restrict__ accepted,
+       WalkResult* out) {
     __shared__ int acc_src[SISSO_MAX_SIS];
     __shared__ int64_t heap_id[kHeapCap];
     __shared__ int heap_ix[kHeapCap];
@@ -935,7 +1042,8 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
         const int csrc = ssrc[c];
         const int64_t cid = sid[c];
         Prog pc;
-        if (!zc) build_prog(*sp, cid, pc);
+        OpRef rc{};
+        if (!zc) { if (V) make_opref(*sp, cid, rc); else build_prog(*sp, cid, pc); }
         const double mc = sv_mean[csrc], dc = sv_sd[csrc];
         int dupf = 0;
         const int nall = nS + n_acc;
@@ -955,14 +1063,18 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
         for (int q = 0; q < nr; ++q) {
             const int src = refs[q];
             Prog pm;
-            if (!zc) build_prog(*sp, sv_ids[src], pm);
+            OpRef rm{};
+            if (!zc) { if (V) make_opref(*sp, sv_ids[src], rm); else build_prog(*sp, sv_ids[src], pm); }
             const double mm = sv_mean[src], dm = sv_sd[src];
             double e1 = 0.0, e2 = 0.0;
             for (int t = tid; t < N; t += blockDim.x) {
-                double za, zb;
+                double za, zb, mg;
                 if (zc) {
                     za = zc[(size_t)csrc * N + t];
                     zb = zc[(size_t)src * N + t];
+                } else if (V) {
+                    za = (opref_val(rc, V, N, t, mg) - mc) / dc;
+                    zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
                 } else {
                     za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
                     zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
@@ -1020,10 +1132,19 @@ sisso_status compute_subvalid(sisso_ctx* c) {
         const int64_t lo = l == 0 ? 0 : sp.phi[l - 1], hi = sp.phi[l];
         const int64_t n = hi - lo;
         if (n <= 0) continue;
-        k_subvalid<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, lo, hi, c->subvalid);
+        k_subvalid<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, lo, hi,
+                                                                       c->opval64, c->subvalid);
         c->stats.launches++;
     }
     return check_cuda(c, cudaGetLastError(), "subvalid");
+}
+
+sisso_status fill_val64(sisso_ctx* c) {
+    if (!c->opval64) return SISSO_OK;
+    const int64_t n = c->space.phi[c->rung - 1];
+    k_fill_val64<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opval64);
+    c->stats.launches++;
+    return check_cuda(c, cudaGetLastError(), "fill_val64");
 }
 
 sisso_status fill_opcache(sisso_ctx* c) {
@@ -1088,9 +1209,15 @@ sisso_status score_all(sisso_ctx* c, int precision) {
     if (cached) {
         // lower levels from cached rows; the top level's unary sections from cached operands
         const int64_t nlow = sp.phi[L - 1];
-        const int gl = (int)((nlow + 255) / 256);
-        if (fp64) k_score_cached<double><<<gl, 256, 0, c->stream>>>(c->opcache64, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
-        else k_score_cached<float><<<gl, 256, 0, c->stream>>>(c->opcache32, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+        const bool few = nlow < 65536;      // few ids: a warp per id splits the samples
+        const int gl = few ? (int)((nlow * 32 + 255) / 256) : (int)((nlow + 255) / 256);
+        if (fp64) {
+            if (few) k_score_cached_w<double><<<gl, 256, 0, c->stream>>>(c->opcache64, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+            else k_score_cached<double><<<gl, 256, 0, c->stream>>>(c->opcache64, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+        } else {
+            if (few) k_score_cached_w<float><<<gl, 256, 0, c->stream>>>(c->opcache32, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+            else k_score_cached<float><<<gl, 256, 0, c->stream>>>(c->opcache32, c->N, nlow, c->tc32, c->tc64, c->tstats, 0, nlow, c->subvalid, c->scores);
+        }
         c->stats.launches++;
         UnaryArgs U{};
         U.Q = A.Q; U.P = A.P; U.N = c->N;
@@ -1098,8 +1225,14 @@ sisso_status score_all(sisso_ctx* c, int precision) {
             if (sp.sec[q].level == L && sp.sec[q].op > DIV) { U.op[U.n_ops] = sp.sec[q].op; U.base[U.n_ops] = sp.sec[q].base; ++U.n_ops; }
         if (U.n_ops > 0) {
             const int gu = (int)((A.P - A.Q + 31) / 32);
-            if (fp64) k_score_unary<double><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
-            else k_score_unary<float><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            if (gu >= 2 * c->sms) {
+                if (fp64) k_score_unary<double><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                else k_score_unary<float><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            } else {      // few operands: a warp per candidate splits the samples
+                const int gw = (int)(((A.P - A.Q) * U.n_ops * 32 + 255) / 256);
+                if (fp64) k_score_unary_w<double><<<gw, 256, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                else k_score_unary_w<float><<<gw, 256, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            }
             c->stats.launches++;
         }
     } else {
@@ -1131,9 +1264,15 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         const double* A1 = nullptr;
         const double* AR = nullptr;
         if (cached) {
-            const int go = (int)((A.P + 255) / 256);
-            if (fp64) k_opsums<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
-            else k_opsums<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+            const bool few = A.P < 65536;
+            const int go = few ? (int)((A.P * 32 + 255) / 256) : (int)((A.P + 255) / 256);
+            if (fp64) {
+                if (few) k_opsums_w<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+                else k_opsums<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+            } else {
+                if (few) k_opsums_w<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+                else k_opsums<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
+            }
             c->stats.launches++;
             A1 = c->opsum;
             AR = c->opsum + A.P;
@@ -1190,7 +1329,7 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         cudaMemcpyAsync(c->S_sorted, Ss.data(), sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
     const bool fp_kernel64 = c->opts.precision == SISSO_PREC_FP64;
     const double eps = fp_kernel64 ? 1e-6 : 2e-4;   // bound on |score_kernel - score_FP64|
-    int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(16384, 64LL * k);
+    int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(4096, 32LL * k);
     const int64_t n = c->n_feat;
     const int gridS = std::max(1, c->sms * 8);
     cudaEvent_t q[5];
@@ -1228,9 +1367,9 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         cudaEventRecord(q[1], c->stream);
         double* zc = (int64_t)nr <= c->zcap ? c->zcache : nullptr;   // cache the vectors if they fit
         k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->tc64, c->tstats,
-                                                                 c->surv_ids, nr, c->subvalid, c->surv_score,
-                                                                 c->surv_mean, c->surv_sd, c->surv_valid,
-                                                                 c->surv_probe, zc);
+                                                                 c->surv_ids, nr, c->subvalid, c->opval64,
+                                                                 c->surv_score, c->surv_mean, c->surv_sd,
+                                                                 c->surv_valid, c->surv_probe, zc);
         int n_pad = 1;
         while (n_pad < std::max(ns, 1)) n_pad <<= 1;
         k_sort_keys<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->surv_ids, c->surv_score, c->surv_valid, ns,
@@ -1251,11 +1390,11 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
                                                                c->dup_cnt);
         k_dup_confirm<<<std::max(1, std::min(c->sms * 16, (n_pad * 32 + 255) / 256)), 256, 0, c->stream>>>(
             c->space_dev, c->Xc64, c->N, c->sort_src, c->sort_id, n_pad, c->surv_ids, c->surv_mean, c->surv_sd, zc,
-            c->dup_list, c->dup_cnt, c->dup_ok);
+            c->opval64, c->dup_list, c->dup_cnt, c->dup_ok);
         k_walk<<<1, kWalkThreads, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
                                                   n_pad, c->surv_ids, c->surv_score, c->surv_mean, c->surv_sd,
-                                                  c->surv_probe, zc, c->dup_list, c->dup_cnt, c->dup_ok, ns, n_prev,
-                                                  k, c->removed, c->accepted, c->walk);
+                                                  c->surv_probe, zc, c->opval64, c->dup_list, c->dup_cnt, c->dup_ok,
+                                                  ns, n_prev, k, c->removed, c->accepted, c->walk);
         c->stats.launches += 3;
         cudaEventRecord(q[4], c->stream);
         cudaMemcpyAsync(c->walk_h, c->walk, sizeof(WalkResult), cudaMemcpyDeviceToHost, c->stream);
