@@ -64,7 +64,12 @@ enum {
 };
 #define SISSO_OP_ALL 0xFFFu
 
-enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1 };
+/* Arithmetic of the screening and l0 kernels.  FP64 and FP32 give the exact FP64 result
+ * (section 4 of the design notes: error-bounded FP32 plus FP64 re-score / refit).  The
+ * mixed forms compute the subspace Gram on the tensor cores from BF16 or FP16 operands
+ * (FP32 accumulation) and refit in FP64 the 100 best subsets and every subset whose
+ * condition estimate exceeds 1e6. */
+enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1, SISSO_PREC_MIXED_BF16 = 2, SISSO_PREC_MIXED_FP16 = 3 };
 
 /* Expansion grammar (§2.1 Eq. 2).  EQ2: every pair of phi_{l-1} except pairs already
  * in phi_{l-2}.  NEW_X_PREV: identical up to level 2; from level 3 one operand is new at
@@ -195,6 +200,15 @@ sisso_status sisso_sis_step(sisso_ctx* ctx, const double* target, const int64_t*
 sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, double syy,
                              int n, int D, const int64_t* gid, int precision, int* best_pos,
                              double* best_rss, int64_t* examined);
+
+/* Subspace Gram on the tcgen05 tensor cores (the mixed-precision forms' a4 step): with Z
+ * n standardised rows of N samples (FP64, row-major) and yc the centred target with
+ * population std sdy, returns G = Z Z^T / N (n x n) and b = Z yc / N (n), computed from
+ * BF16 (kind = SISSO_PREC_MIXED_BF16) or FP16 (SISSO_PREC_MIXED_FP16) operands with FP32
+ * accumulation.  Inputs host or device; G and b HOST.  Uses the current device and the
+ * legacy default stream.  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT. */
+sisso_status sisso_gram_tc(const double* Z, const double* yc, double sdy, int n, int N, int kind, float* G,
+                           float* b);
 
 /* ---- allocation-free l0 search --------------------------------------------------------
  *

@@ -452,6 +452,10 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w);
 sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w);
 
+// tensor-core Gram (gram_tc.cu)
+sisso_status gram_tc(sisso_ctx* c, const double* Z, const double* yc, double sdy, int n, int N, int kind,
+                     float* G32, int ldg, float* b32);
+
 // timing
 struct PhaseTimer {
     cudaEvent_t a, b;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsisso_gb300.so")
 # operator bits and enums of include/sisso.h
 OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_EXP, OP_LOG, OP_SQRT, OP_SQ, OP_INV, OP_SIN, OP_CUBE, OP_EXPNEG = (
     1 << i for i in range(12))
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
 MAX_DIM, MAX_SIS, MAX_RUNG = 4, 1024, 3
 STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
@@ -31,7 +31,7 @@ EXPORTS = [
     "sisso_get_sis", "sisso_feature_count", "sisso_feature_expr", "sisso_get_stats",
     "sisso_last_error", "sisso_destroy", "sisso_eval_features", "sisso_score_all",
     "sisso_sis_step", "sisso_l0_search", "sisso_space_sizes", "sisso_space_expr",
-    "sisso_l0_search_noalloc",
+    "sisso_l0_search_noalloc", "sisso_gram_tc",
 ]
 NOALLOC_MAX_N = 256
 NOALLOC_MAX_BAND = 65536
@@ -97,6 +97,7 @@ def load() -> C.CDLL:
     L.sisso_l0_search.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, C.c_int,
                                   C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_sizes.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, i64p]
+    L.sisso_gram_tc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp]
     L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
                                           C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
@@ -135,6 +136,20 @@ def space_expr(d: int, op_set: int, rung: int, grammar: int, fid: int) -> str:
     if st:
         raise SissoError(st, "space_expr")
     return buf.value.decode()
+
+
+def gram_tc(Z, yc, sdy: float, kind: int = PREC_MIXED_BF16):
+    """Z Z^T / N and Z yc / N on the tensor cores from 16-bit operands (sisso_gram_tc)."""
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    yc = np.ascontiguousarray(yc, dtype=np.float64)
+    n, N = Z.shape
+    G = np.zeros((n, n), dtype=np.float32)
+    b = np.zeros(n, dtype=np.float32)
+    st = load().sisso_gram_tc(C.c_void_p(Z.ctypes.data), C.c_void_p(yc.ctypes.data), float(sdy), n, N, kind,
+                              C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data))
+    if st:
+        raise SissoError(st, "gram_tc")
+    return G, b
 
 
 def l0_search_noalloc(G, b, syy: float, N: int, D: int, gid, precision: int = PREC_FP32, stream=None):
