@@ -49,7 +49,8 @@ void free_all(sisso_ctx* c) {
                     c->S_sorted, c->Z, c->Zmean, c->Zsd, c->G64, c->b64, c->G32, c->b32, c->resid, c->ymom,
                     c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
-                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64};
+                    c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
+                    c->band_r32, c->band_sel};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -65,7 +66,7 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if (k < 1 || k > SISSO_MAX_SIS) { why = "sis_size must be in 1..1024"; return SISSO_ERR_ARG; }
     if (N < max_dim + 1 || N < 2) { why = "N must be at least max_dim + 1"; return SISSO_ERR_ARG; }
     if ((ops & SISSO_OP_ALL) == 0 || (ops & ~SISSO_OP_ALL)) { why = "bad operator mask"; return SISSO_ERR_ARG; }
-    if (o.precision != SISSO_PREC_FP32 && o.precision != SISSO_PREC_FP64) { why = "bad precision"; return SISSO_ERR_ARG; }
+    if (o.precision < SISSO_PREC_FP64 || o.precision > SISSO_PREC_MIXED_FP16) { why = "bad precision"; return SISSO_ERR_ARG; }
     if (o.grammar != SISSO_GRAMMAR_EQ2 && o.grammar != SISSO_GRAMMAR_NEW_X_PREV) { why = "bad grammar"; return SISSO_ERR_ARG; }
     if ((int64_t)max_dim * k > 65535) { why = "subspace too large"; return SISSO_ERR_ARG; }
     return SISSO_OK;
@@ -147,6 +148,8 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         (st = dalloc(c, c->band, (size_t)c->band_cap, "band")) ||
         (st = dalloc(c, c->band_rss, (size_t)c->band_cap, "band_rss")) ||
         (st = dalloc(c, c->band_count, 1, "band_count")) || (st = dalloc(c, c->work, 16, "work")) ||
+        (st = dalloc(c, c->band_r32, (size_t)c->band_cap, "band_r32")) ||
+        (st = dalloc(c, c->band_sel, (size_t)c->band_cap, "band_sel")) ||
         (st = dalloc(c, c->win, 1, "win")) || (st = dalloc(c, c->space_dev, 1, "space")))
         return bail(st);
     cudaMemcpyAsync(c->space_dev, &c->space, sizeof(Space), cudaMemcpyHostToDevice, c->stream);
@@ -214,6 +217,8 @@ sisso_status sisso_fit(sisso_ctx* c) {
     if (!c) return SISSO_ERR_ARG;
     cudaSetDevice(c->opts.device);
     const int prec = c->opts.precision;
+    const bool mixed = prec == SISSO_PREC_MIXED_BF16 || prec == SISSO_PREC_MIXED_FP16;
+    const int screen_prec = mixed ? SISSO_PREC_FP32 : prec;
     c->stats = sisso_stats{};
     c->S.clear(); c->n_sis.clear(); c->res_ids.clear(); c->res_coef.clear(); c->res_rmse.clear(); c->res_r2.clear();
     c->n_dims = 0;
@@ -225,7 +230,7 @@ sisso_status sisso_fit(sisso_ctx* c) {
     sisso_status st = SISSO_OK;
     for (int t = 1; t <= c->max_dim; ++t) {
         if ((st = prepare_target(c, target))) break;
-        if ((st = score_all(c, prec))) break;
+        if ((st = score_all(c, screen_prec))) break;
         std::vector<int64_t> acc;
         if ((st = sis_select(c, c->k, c->S.data(), (int)c->S.size(), acc))) break;
         const int n_old = (int)c->S.size();
@@ -241,13 +246,16 @@ sisso_status sisso_fit(sisso_ctx* c) {
         cudaEvent_t g0, g1;
         cudaEventCreate(&g0); cudaEventCreate(&g1);
         cudaEventRecord(g0, c->stream);
-        if ((st = append_subspace(c, n_old, (int)acc.size()))) break;
+        if ((st = append_subspace(c, n_old, (int)acc.size(), !mixed))) break;
+        if (mixed && (st = gram_tc(c, c->Z, c->yc64, std::sqrt(c->syy), n, c->N, prec, c->G32, c->n_cap, c->b32))) break;
         cudaEventRecord(g1, c->stream);
         Winner w{};
-        if ((st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w))) break;
+        if (mixed) st = l0_solve_mixed(c, n, t, w);
+        else st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
+        if (st) break;
         c->stats.ms_gram += event_ms(g0, g1);
         cudaEventDestroy(g0); cudaEventDestroy(g1);
-        if ((st = winner_model(c, n, t, w))) break;
+        if ((st = mixed ? winner_model_z(c, n, t, w) : winner_model(c, n, t, w))) break;
         c->res_ids.emplace_back(w.ids, w.ids + t);
         c->res_coef.emplace_back(w.coef, w.coef + t + 1);
         c->res_rmse.push_back(w.rmse);

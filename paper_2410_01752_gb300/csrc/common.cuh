@@ -407,6 +407,8 @@ struct sisso_ctx {
     uint64_t* band = nullptr;          // packed positions
     double* band_rss = nullptr;
     unsigned int* band_count = nullptr;
+    float* band_r32 = nullptr;         // mixed precision: FP32 RSS of each band entry
+    unsigned char* band_sel = nullptr; // mixed precision: entries refit in FP64
     uint64_t* prefixes = nullptr;
     int64_t prefix_cap = 0;
     int* work = nullptr;               // work counters
@@ -447,7 +449,9 @@ sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int 
                            double* out_dev);
 
 // subspace and l0 (l0.cu)
-sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new);
+sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
+sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
+sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w);
 sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w);

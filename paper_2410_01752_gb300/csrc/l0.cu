@@ -149,6 +149,8 @@ struct EnumArgs {
     unsigned int* band_count;
     int64_t band_cap;
     unsigned long long* examined;
+    double rho, kappa;          // FP32 RSS error model: SST (rho + kappa / min pivot)
+    float* band_r32;            // optional: the FP32 RSS of each band entry (NaN: flagged by a pivot)
 };
 
 template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pre)[DP > 0 ? DP : 1], int i1, int i2) {
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
             T err_u = T(0);
             if (A.fp32) {
                 const T mp = mp1 < T(kPivotHi) ? mp1 : T(kPivotHi);
-                err_u = sstT * (T(kRho) + T(kKappa) / (mp > T(0) ? mp : T(1e-30)));
+                err_u = sstT * (T(A.rho) + T(A.kappa) / (mp > T(0) ? mp : T(1e-30)));
             }
             const T base_c = A.syy - pw;
             T c_fast;
@@ -304,7 +306,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
                 if (ill) {
                     if (MODE == 1 && A.fp32) {
                         const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                        if (slot < A.band_cap) {
+                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                            if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
+                        }
                     }
                     continue;
                 }
@@ -318,17 +323,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
                         c_fast = base_c - (best - err_u) / N;
                     } else {
                         const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                        if (slot < A.band_cap) {
+                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                            if (A.band_r32) A.band_r32[slot] = (float)(N * (base_c - num * num / d2));
+                        }
                     }
                 } else {
                     const T mp = d2 < mp1 ? d2 : mp1;
-                    const T err = sstT * (T(kRho) + T(kKappa) / mp);
+                    const T err = sstT * (T(A.rho) + T(A.kappa) / mp);
                     const T rss = N * (base_c - num * num / d2);
                     if (MODE == 0) {
                         if (rss + err < best) { best = rss + err; c_fast = base_c - (best - err_u) / N; }
                     } else if (rss - err <= thr) {
                         const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                        if (slot < A.band_cap) {
+                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                            if (A.band_r32) A.band_r32[slot] = (float)rss;
+                        }
                     }
                 }
             }
@@ -357,17 +368,23 @@ __global__ void k_l0_single(EnumArgs<T> A) {
     if (!(d > T(A.tau))) {
         if (MODE == 1 && A.fp32) {
             const unsigned slot = atomicAdd(A.band_count, 1u);
-            if (slot < A.band_cap) A.band[slot] = (uint64_t)i;
+            if (slot < A.band_cap) {
+                A.band[slot] = (uint64_t)i;
+                if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
+            }
         }
         return;
     }
     const T rss = T(A.N) * (A.syy - bi * bi / d);
-    const T err = A.fp32 ? T(A.sst) * (T(kRho) + T(kKappa) / d) : T(0);
+    const T err = A.fp32 ? T(A.sst) * (T(A.rho) + T(A.kappa) / d) : T(0);
     if (MODE == 0) {
         atomicMin(A.ub_key, okey((double)(rss + err)));
     } else if (rss - err <= T(A.win->thr)) {
         const unsigned slot = atomicAdd(A.band_count, 1u);
-        if (slot < A.band_cap) A.band[slot] = (uint64_t)i;
+        if (slot < A.band_cap) {
+            A.band[slot] = (uint64_t)i;
+            if (A.band_r32) A.band_r32[slot] = (float)rss;
+        }
     }
 }
 
@@ -529,23 +546,209 @@ __global__ void k_model(const double* __restrict__ G, const double* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------------
+// mixed precision: the band's K best FP32 RSS (plus every entry flagged by a pivot) are
+// re-solved in FP64 from the standardised FP64 rows, without an FP64 Gram
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned fkey(float v) {
+    const unsigned u = __float_as_uint(v);
+    return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+
+// one block: the K-th smallest key among finite band RSS32 (binary search on the key), then
+// the selection flags (key <= threshold, or flagged)
+__global__ void k_select_top(const float* __restrict__ r32, const unsigned* __restrict__ count, int64_t cap, int K,
+                             unsigned char* __restrict__ sel) {
+    __shared__ unsigned red[32];
+    __shared__ unsigned thr_s;
+    const int64_t n = (int64_t)*count < cap ? (int64_t)*count : cap;
+    auto count_le = [&](unsigned t) -> unsigned {
+        unsigned c = 0;
+        for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const float v = r32[e];
+            if (v == v && fkey(v) <= t) ++c;
+        }
+        c = warp_sum(c);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        unsigned tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        __syncthreads();
+        return tot;
+    };
+    // smallest threshold t with count(key <= t) >= K (all finite entries if fewer than K)
+    unsigned lo = 0, hi = 0xFFFFFFFFu;
+    if (count_le(hi) < (unsigned)K) lo = hi;
+    while (lo < hi) {
+        const unsigned mid = lo + ((hi - lo) >> 1);
+        if (count_le(mid) >= (unsigned)K) hi = mid; else lo = mid + 1;
+    }
+    if (threadIdx.x == 0) thr_s = lo;
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const float v = r32[e];
+        sel[e] = (v != v) || fkey(v) <= thr_s;
+    }
+}
+
+// one warp per band entry: FP64 sub-Gram and moments from Z rows, Cholesky, RSS
+__global__ void k_refit_z(const double* __restrict__ Z, const double* __restrict__ yc, int N, double syy, int D,
+                          const uint64_t* __restrict__ band, const unsigned* __restrict__ count, int64_t cap,
+                          const unsigned char* __restrict__ sel, double* __restrict__ rss_out,
+                          unsigned long long* min_key) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n = (int64_t)*count < cap ? (int64_t)*count : cap;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n;
+         e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        if (!sel[e]) { if (lane == 0) rss_out[e] = INFINITY; continue; }
+        int pos[kMaxDim];
+        unpack(band[e], D, pos);
+        double g[kMaxDim][kMaxDim], bv[kMaxDim];
+        for (int i = 0; i < D; ++i) {
+            const double* zi = Z + (size_t)pos[i] * N;
+            for (int j = 0; j <= i; ++j) {
+                const double* zj = Z + (size_t)pos[j] * N;
+                double acc = 0.0;
+                for (int t = lane; t < N; t += 32) acc += zi[t] * zj[t];
+                g[i][j] = g[j][i] = warp_sum(acc) / N;
+            }
+            double acc = 0.0;
+            for (int t = lane; t < N; t += 32) acc += zi[t] * yc[t];
+            bv[i] = warp_sum(acc) / N;
+        }
+        if (lane == 0) {
+            double L[kMaxDim][kMaxDim], w[kMaxDim], q = 0.0;
+            bool ok = true;
+            for (int j = 0; j < D && ok; ++j) {
+                double dj = g[j][j];
+                for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
+                if (!(dj > kPivotMin)) { ok = false; break; }
+                L[j][j] = sqrt(dj);
+                for (int i = j + 1; i < D; ++i) {
+                    double v = g[i][j];
+                    for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
+                    L[i][j] = v / L[j][j];
+                }
+                double v = bv[j];
+                for (int m = 0; m < j; ++m) v -= L[j][m] * w[m];
+                w[j] = v / L[j][j];
+                q += w[j] * w[j];
+            }
+            const double r = ok ? (double)N * (syy - q) : INFINITY;
+            rss_out[e] = r;
+            if (r < INFINITY) atomicMin(min_key, okey(r));
+        }
+    }
+}
+
+// the winner's model from Z rows (one block): coefficients in original units, residual
+__global__ void k_model_z(const double* __restrict__ Z, const double* __restrict__ Zmean,
+                          const double* __restrict__ Zsd, const double* __restrict__ yc, double ybar, int N, double syy,
+                          int D, const int64_t* __restrict__ gid, Winner* W, double* __restrict__ resid) {
+    __shared__ double g[kMaxDim][kMaxDim], bv[kMaxDim], gamma[kMaxDim];
+    __shared__ double red[32];
+    if (!W->found) return;
+    // lower triangle of the sub-Gram, then the moments with the target (column D)
+    for (int i = 0; i < D; ++i) {
+        const double* zi = Z + (size_t)W->pos[i] * N;
+        for (int j = 0; j <= D; ++j) {
+            if (j < D && j > i) continue;
+            const double* zj = j < D ? Z + (size_t)W->pos[j] * N : yc;
+            double acc = 0.0;
+            for (int t = threadIdx.x; t < N; t += blockDim.x) acc += zi[t] * zj[t];
+            acc = warp_sum(acc);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+                if (j < D) g[i][j] = g[j][i] = tot / N;
+                else bv[i] = tot / N;
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {   // Cholesky solve G gamma = b
+        double L[kMaxDim][kMaxDim], w[kMaxDim];
+        for (int j = 0; j < D; ++j) {
+            double dj = g[j][j];
+            for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
+            L[j][j] = sqrt(dj > 0 ? dj : 1e-300);
+            for (int i = j + 1; i < D; ++i) {
+                double v = g[i][j];
+                for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
+                L[i][j] = v / L[j][j];
+            }
+            double v = bv[j];
+            for (int m = 0; m < j; ++m) v -= L[j][m] * w[m];
+            w[j] = v / L[j][j];
+        }
+        for (int j = D - 1; j >= 0; --j) {
+            double v = w[j];
+            for (int m = j + 1; m < D; ++m) v -= L[m][j] * gamma[m];
+            gamma[j] = v / L[j][j];
+        }
+    }
+    __syncthreads();
+    double ssr = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double f = yc[i];
+        for (int j = 0; j < D; ++j) f -= gamma[j] * Z[(size_t)W->pos[j] * N + i];
+        resid[i] = f;
+        ssr += f * f;
+    }
+    ssr = warp_sum(ssr);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ssr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rss = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rss += red[w];
+        int order[kMaxDim];
+        for (int j = 0; j < D; ++j) order[j] = j;
+        for (int a = 1; a < D; ++a)
+            for (int c = a; c > 0 && gid[W->pos[order[c - 1]]] > gid[W->pos[order[c]]]; --c) {
+                const int t = order[c]; order[c] = order[c - 1]; order[c - 1] = t;
+            }
+        double c0 = ybar;
+        for (int j = 0; j < D; ++j) {
+            const int q = order[j], p = W->pos[q];
+            const double cj = gamma[q] / Zsd[p];
+            W->ids[j] = gid[p];
+            W->coef[j + 1] = cj;
+            W->gamma[j] = gamma[q];
+            c0 -= cj * Zmean[p];
+        }
+        W->coef[0] = c0;
+        W->rss = rss;
+        W->rmse = sqrt(rss / N);
+        W->r2 = 1.0 - rss / (syy * N);
+    }
+}
+
 }  // namespace
 
 // ===================================================================================
 // host side
 // ===================================================================================
 
-sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new) {
+sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64) {
     if (n_new <= 0) return SISSO_OK;
     const int n = n_old + n_new;
     k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->opval64, c->Z,
                                                  c->Zmean, c->Zsd);
-    dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
-    k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,
-                                                      c->G32, c->b32);
-    c->stats.launches += 2;
+    c->stats.launches++;
+    if (gram64) {
+        dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
+        k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,
+                                                          c->G32, c->b32);
+        c->stats.launches++;
+    }
     return check_cuda(c, cudaGetLastError(), "append_subspace");
 }
+
 
 static int64_t binom_host(int64_t n, int k) {
     if (k < 0 || n < k) return 0;
@@ -603,7 +806,7 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
         EnumArgs<float> A{};
         A.G = G32; A.b = b32; A.ld = ld; A.n = n; A.N = c->N; A.syy = (float)syy; A.sst = sst;
         A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
-        A.tau = kPivotMin32; A.fp32 = 1; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
+        A.tau = kPivotMin32; A.fp32 = 1; A.rho = kRho; A.kappa = kKappa; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;
         k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, 0.0);
@@ -651,6 +854,80 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     w = *c->win_h;
     w.examined = (int64_t)ex;
     if (!w.found) return fail(c, SISSO_ERR_NUMERIC, "l0: every subset is singular");
+    return SISSO_OK;
+}
+
+// Mixed precision l0: FP32 enumeration on the tensor-core Gram (G32, b32), then the K = 100
+// best subsets by FP32 RSS and every subset with a pivot <= 1e-6 (condition estimate above
+// 1e6) re-solved in FP64 from the standardised rows; the winner is the lowest FP64 RSS
+// with the same tie rule as the exact forms.
+sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w) {
+    constexpr int kTop = 100;
+    if (D < 1 || D > kMaxDim || n < D) return fail(c, SISSO_ERR_ARG, "l0: bad D or n");
+    cudaEvent_t e0, e2, e3;
+    cudaEventCreate(&e0); cudaEventCreate(&e2); cudaEventCreate(&e3);
+    cudaEventRecord(e0, c->stream);
+    const int DPh = D - 2;
+    const int cpp = D >= 2 ? std::max(1, (n - 1 - DPh + kRows - 1) / kRows) : 1;
+    const int64_t n_items = D >= 2 ? binom_host(n - 2, DPh) * cpp : 0;
+    unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(c->work + 2);
+    unsigned long long* examined = ub_key + 1;
+    unsigned long long* min_key = ub_key + 2;
+    cudaMemsetAsync(ub_key, 0xFF, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(examined, 0, sizeof(unsigned long long), c->stream);
+    const double sst = c->syy * c->N;
+    EnumArgs<float> A{};
+    A.G = c->G32; A.b = c->b32; A.ld = c->n_cap; A.n = n; A.N = c->N; A.syy = (float)c->syy; A.sst = sst;
+    A.cpp = cpp; A.n_items = n_items; A.counter = c->work; A.tau = 1e-6f; A.fp32 = 1; A.rho = 0.0; A.kappa = 0.0;
+    A.ub_key = ub_key; A.win = c->win; A.band = c->band; A.band_count = c->band_count; A.band_cap = c->band_cap;
+    A.examined = examined; A.band_r32 = c->band_r32;
+    sisso_status st;
+    if ((st = run_enum(c, A, D, 0))) return st;
+    // widen the band until it holds at least kTop subsets (or everything)
+    unsigned cnt = 0;
+    for (double delta = 1e-4 * sst;; delta *= 10.0) {
+        cudaMemsetAsync(c->band_count, 0, sizeof(unsigned), c->stream);
+        k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, delta);
+        if ((st = run_enum(c, A, D, 1))) return st;
+        cudaMemcpyAsync(&cnt, c->band_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+        if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "l0 mixed band"))) return st;
+        if ((int64_t)cnt > c->band_cap)
+            return fail(c, SISSO_ERR_CAPACITY, "l0: mixed-precision band exceeds max_band");
+        if (cnt >= (unsigned)kTop || delta > 2.0 * sst) break;
+    }
+    cudaEventRecord(e2, c->stream);
+    cudaMemsetAsync(min_key, 0xFF, sizeof(unsigned long long), c->stream);
+    k_select_top<<<1, 1024, 0, c->stream>>>(c->band_r32, c->band_count, c->band_cap, kTop, c->band_sel);
+    k_refit_z<<<c->sms * 8, 256, 0, c->stream>>>(c->Z, c->yc64, c->N, c->syy, D, c->band, c->band_count, c->band_cap,
+                                                 c->band_sel, c->band_rss, min_key);
+    k_winner<<<1, 1024, 0, c->stream>>>(c->band, c->band_rss, c->band_count, c->band_cap, min_key, kRssTie * sst,
+                                        c->S_dev, D, c->win);
+    c->stats.launches += 3;
+    unsigned long long ex = 0;
+    cudaMemcpyAsync(&ex, examined, sizeof(ex), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(c->win_h, c->win, sizeof(Winner), cudaMemcpyDeviceToHost, c->stream);
+    cudaEventRecord(e3, c->stream);
+    if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "l0 mixed"))) return st;
+    c->stats.ms_l0 += event_ms(e0, e2);
+    c->stats.ms_refit += event_ms(e2, e3);
+    cudaEventDestroy(e0); cudaEventDestroy(e2); cudaEventDestroy(e3);
+    c->stats.subsets_fit += (int64_t)ex;
+    c->stats.subsets_refit += std::min<int64_t>(cnt, kTop);
+    w = *c->win_h;
+    w.examined = (int64_t)ex;
+    if (!w.found) return fail(c, SISSO_ERR_NUMERIC, "l0: every refit subset is singular");
+    return SISSO_OK;
+}
+
+sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w) {
+    (void)n;
+    k_model_z<<<1, 1024, 0, c->stream>>>(c->Z, c->Zmean, c->Zsd, c->yc64, c->ybar, c->N, c->syy, D, c->S_dev, c->win,
+                                         c->resid);
+    c->stats.launches++;
+    cudaMemcpyAsync(c->win_h, c->win, sizeof(Winner), cudaMemcpyDeviceToHost, c->stream);
+    sisso_status st = check_cuda(c, cudaStreamSynchronize(c->stream), "winner_model_z");
+    if (st) return st;
+    w = *c->win_h;
     return SISSO_OK;
 }
 
@@ -782,7 +1059,7 @@ extern "C" sisso_status sisso_l0_search_noalloc(const double* G, const double* b
     if (fp32) {
         EnumArgs<float> A{};
         A.G = dG32; A.b = db32; A.ld = n; A.n = n; A.N = N; A.syy = (float)syy; A.sst = sst;
-        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = kPivotMin32; A.fp32 = 1;
+        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = kPivotMin32; A.fp32 = 1; A.rho = kRho; A.kappa = kKappa;
         A.ub_key = ub_key; A.win = win; A.band = band; A.band_count = band_count;
         A.band_cap = (int64_t)kNaBand; A.examined = ex_key;
         ok(na_enum(A, D, 0, sms, st));
