@@ -41,6 +41,8 @@ def parse():
                     help="CPU work for the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3],
+                    help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples")
     ap.add_argument("--d", type=int, default=10, help="primary features (smaller cases for profiling)")
     ap.add_argument("--N", type=int, default=1000, help="samples (smaller cases for profiling)")
     return ap.parse_args()
@@ -183,8 +185,88 @@ def run_reference(args, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def oracle_reference(P, S_ids, D):
+    """FP64 reference for the final descriptor, on the GPU's subspace: the oracle evaluates
+    the features, l0 over every D-subset of them, QR refit of the winner."""
+    import numpy as np
+    import oracle
+    sp = oracle.Space(P.d, P.op_set, P.rung, P.grammar)
+    F = np.array([sp.eval(P.X, i) for i in S_ids])
+    Z = (F - F.mean(1, keepdims=True)) / F.std(1, keepdims=True)
+    yc = P.y - P.y.mean()
+    N = P.N
+    pos, _, _ = oracle.l0(Z @ Z.T / N, Z @ yc / N, float(yc @ yc) / N, N, D, S_ids)
+    ids = sorted(S_ids[p] for p in pos)
+    A = np.column_stack([np.ones(N)] + [F[list(S_ids).index(i)] for i in ids])
+    coef, *_ = np.linalg.lstsq(A, P.y, rcond=None)
+    r = P.y - A @ coef
+    return ids, coef, float(np.sqrt(r @ r / N))
+
+
+def run_mixed(args):
+    """Mixed-precision forms vs the plain FP32 form: time to the final descriptor, equal
+    descriptor and RMSE, errors against the FP64 reference."""
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16, Sisso, build, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    P = inputs.workload3(0)
+    Xd, yd = torch.from_numpy(P.X).cuda(), torch.from_numpy(P.y).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, prec in (("plain_fp32", PREC_FP32), ("mixed_bf16", PREC_MIXED_BF16), ("mixed_fp16", PREC_MIXED_FP16)):
+        s = Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar, stream=stream)
+        for _ in range(args.warmup):
+            s.fit()
+        ms, st = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d = s.fit()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            st = s.stats()
+        S_all = sum((s.sis(t) for t in range(1, len(d) + 1)), [])
+        res[name] = {"ms": sum(ms) / len(ms), "desc": d[-1], "S": S_all, "stats": st}
+        s.close()
+    plain = res["plain_fp32"]
+    ref_ids, ref_coef, ref_rmse = oracle_reference(P, plain["S"], len(plain["desc"].ids))
+    out = {}
+    for name, r in res.items():
+        d = r["desc"]
+        same = d.ids == ref_ids
+        out[name] = {
+            "time_to_descriptor_ms": r["ms"], "descriptor": d.ids, "rmse": d.rmse,
+            "same_descriptor_as_fp64": same, "same_subspace_as_plain": r["S"] == plain["S"],
+            "coef_rel_err_vs_fp64": [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(d.coef, ref_coef)] if same else None,
+            "rmse_rel_err_vs_fp64": abs(d.rmse - ref_rmse) / ref_rmse,
+            "rmse_rel_diff_vs_plain": abs(d.rmse - plain["desc"].rmse) / plain["desc"].rmse,
+            "ms_gram": r["stats"]["ms_gram"], "ms_l0": r["stats"]["ms_l0"], "ms_refit": r["stats"]["ms_refit"],
+            "subsets_refit": r["stats"]["subsets_refit"]}
+    m = out["mixed_bf16"]
+    line = {
+        "metric": "time-to-descriptor vs plain at equal RMSE", "value": m["time_to_descriptor_ms"] / 1e3, "unit": "s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["time_to_descriptor_ms"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "sis_size": P.sis_size,
+                   "max_dim": P.max_dim, "l2": "flushed between steps (256 MB write)"},
+        "speedup_vs_plain": {k: out["plain_fp32"]["time_to_descriptor_ms"] / v["time_to_descriptor_ms"]
+                             for k, v in out.items() if k != "plain_fp32"},
+        "forms": out, "fp64_reference": {"ids": ref_ids, "coef": list(map(float, ref_coef)), "rmse": ref_rmse},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == 3:
+        run_mixed(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -307,6 +307,7 @@ struct DevBuf {
 // moments of the current screening target, computed on the device
 struct TargetStats {
     double mean, sd;        // FP64 mean and population std of the target
+    double tsum;            // FP64 sum of the centred target (rounding-level, kept exact)
     double sum32, srr32;    // sum and centred sum of squares of the FP32 copy
     float sd32, pad;
 };

@@ -83,11 +83,15 @@ __global__ void k_prepare_target(const double* __restrict__ t, int N, double* __
         ss32 += (double)f * (double)f;
     }
     ss = block_sum(ss, red);
+    double tsum = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tsum += tc64[i];
+    tsum = block_sum(tsum, red);
     s32 = block_sum(s32, red);
     ss32 = block_sum(ss32, red);
     if (threadIdx.x == 0) {
         st->mean = mean;
         st->sd = sqrt(ss / N);
+        st->tsum = tsum;
         st->sum32 = s32;
         st->srr32 = ss32 - s32 * s32 / N;
         st->sd32 = (float)sqrt(st->srr32 / N);
@@ -228,6 +232,18 @@ __global__ void k_score_generic(const Space* __restrict__ sp, const T* __restric
 // ---------------------------------------------------------------------------------
 // sample-major layout: cache[s * P + id], so that a warp reads 32 consecutive features of
 // one sample with one coalesced access
+template <typename T>
+__global__ void k_fill_cache_w(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, int64_t n_ids,
+                               T* __restrict__ cache) {
+    const int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (id >= n_ids) return;
+    Prog p;
+    const bool ok = build_prog(*sp, id, p);
+    for (int s = lane; s < N; s += 32)
+        cache[(size_t)s * n_ids + id] = ok ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
+}
+
 template <typename T>
 __global__ void k_fill_cache(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, int64_t n_ids,
                              T* __restrict__ cache) {
@@ -731,40 +747,39 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
         return;
     }
     double* z = zc ? zc + (size_t)w * N : nullptr;
-    double s = 0.0, mx = 0.0, mo = 0.0;
-    int bad = 0;
     auto value = [&](int i, double& mag) -> double {
         return V ? opref_val(ref, V, N, i, mag) : eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
     };
+    // one pass of sums shifted by the sample-0 value (FP64: relative error ~1e-14, far
+    // inside the 1e-9 tie window of the walk)
+    double mag0;
+    const double v0 = value(0, mag0);
+    double s1 = 0.0, s2 = 0.0, sc = 0.0, mx = 0.0, mo = 0.0;
+    int bad = 0;
     for (int i = lane; i < N; i += 32) {
         double mag;
         const double v = value(i, mag);
         if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
-        s += v;
+        const double u = v - v0;
+        s1 += u;
+        s2 += u * u;
+        sc += u * tc[i];
         mx = fmax(mx, fabs(v));
         mo = fmax(mo, mag);
         if (z) z[i] = v;
     }
     bad = warp_or(bad);
-    s = warp_sum(s);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    sc = warp_sum(sc);
     mx = warp_max(mx);
     mo = warp_max(mo);
     // identically zero: a top-level + or - whose operands cancel (lower ids: in subvalid)
     const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
     const bool cancelled = top_addsub && mx <= kCancelRel * mo;
-    const double mean = s / N;
-    double ss = 0.0, sc = 0.0;
-    if (!bad) {
-        for (int i = lane; i < N; i += 32) {
-            double mag;
-            const double v = (z ? z[i] : value(i, mag)) - mean;
-            ss += v * v;
-            sc += v * tc[i];
-        }
-    }
-    ss = warp_sum(ss);
-    sc = warp_sum(sc);
-    const double sd = sqrt(ss / N);
+    const double mean = v0 + s1 / N;
+    const double var = s2 / N - (s1 / N) * (s1 / N);
+    const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
     const int ok = !bad && !cancelled && sd > kConstRel * mx;
     const double inv = ok ? 1.0 / sd : 0.0;
     if (z)
@@ -779,7 +794,7 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
         valid_out[w] = ok;
         mean_out[w] = mean;
         sd_out[w] = sd;
-        score[w] = ok ? fabs(sc) / ((double)N * sd * st->sd) : -1.0;
+        score[w] = ok ? fabs(sc - (s1 / N) * st->tsum) / ((double)N * sd * st->sd) : -1.0;
     }
 }
 
@@ -828,6 +843,7 @@ __global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int
 // then only reads the confirmed pairs.
 // ---------------------------------------------------------------------------------
 constexpr double kDupScore = 2e-8;
+constexpr int kConfirm = 2;             // partner slots confirmed ahead of the walk
 constexpr int kMaxRefs = 2048;          // slow path: S members / accepted ids gathered per round
 
 __device__ __forceinline__ bool probes_match(const double* a, const double* b) {
@@ -888,7 +904,7 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
     const int lane = threadIdx.x & 31;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_sorted; i += (gridDim.x * blockDim.x) >> 5) {
         const int raw = dup_cnt[i];
-        const int cnt = raw < 0 ? -raw - 1 : raw;
+        const int cnt = min(raw < 0 ? -raw - 1 : raw, kConfirm);
         if (cnt <= 0) continue;
         const int src = ssrc[i];
         Prog pc;
@@ -1016,14 +1032,15 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
                 ++visited;
                 const int raw = dup_cnt[best];
                 const int cnt = raw < 0 ? -raw - 1 : raw;
-                bool dup = false;
+                bool dup = false, unknown = raw < 0;              // partners beyond the list
                 for (int q = 0; q < cnt && !dup; ++q) {
-                    if (!dup_ok[(size_t)best * kDupSlots + q]) continue;
                     const int mm = dup_list[(size_t)best * kDupSlots + q];
-                    dup = mm >= s_off || accepted[mm];
+                    if (!(mm >= s_off || accepted[mm])) continue;  // not a reference (yet)
+                    if (q >= kConfirm) { unknown = true; break; }  // reference, not confirmed ahead
+                    dup = dup_ok[(size_t)best * kDupSlots + q];
                 }
                 checks += cnt;
-                if (!dup && raw < 0) { slow = 1; break; }          // partners beyond the list
+                if (!dup && unknown) { slow = 1; break; }
                 if (!dup) {
                     const int src = ssrc[best];
                     accepted[src] = 1;
@@ -1149,13 +1166,17 @@ sisso_status fill_val64(sisso_ctx* c) {
 
 sisso_status fill_opcache(sisso_ctx* c) {
     const int64_t n = c->space.phi[c->rung - 1];
-    const int grid = (int)((n + 127) / 128);
+    const bool few = n < 65536;     // few features: a warp per feature splits the samples
+    const int grid = few ? (int)((n * 32 + 255) / 256) : (int)((n + 127) / 128);
+    const int block = few ? 256 : 128;
     if (c->opcache32) {
-        k_fill_cache<float><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
+        if (few) k_fill_cache_w<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
+        else k_fill_cache<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
         c->stats.launches++;
     }
     if (c->opcache64) {
-        k_fill_cache<double><<<grid, 128, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache64);
+        if (few) k_fill_cache_w<double><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache64);
+        else k_fill_cache<double><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache64);
         c->stats.launches++;
     }
     return check_cuda(c, cudaGetLastError(), "fill_opcache");
