@@ -13,7 +13,7 @@
 //     (score desc, id asc) and walked by one CTA (k_walk) with the tie and duplicate
 //     rules.  The host checks that the k-th accepted FP64 score clears the FP32 cut-off
 //     by the FP32 error margin; if not, the window grows and selection repeats.
-#include "common.cuh"
+#include "sis_device.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -21,47 +21,6 @@
 
 namespace sg {
 namespace {
-
-constexpr int kBlock = 256;
-
-// ---------------------------------------------------------------------------------
-// reductions
-// ---------------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <typename T> __device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ int warp_or(int v) { return __any_sync(0xffffffffu, v); }
-
-// sum over a block of blockDim.x threads (multiple of 32); result valid in all threads
-template <typename T> __device__ T block_sum(T v, T* red) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    T r = 0;
-    for (int i = 0; i < nw; ++i) r += red[i];
-    __syncthreads();
-    return r;
-}
-template <typename T> __device__ T block_max(T v, T* red) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_max(v);
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    T r = red[0];
-    for (int i = 1; i < nw; ++i) r = max(r, red[i]);
-    __syncthreads();
-    return r;
-}
 
 // ---------------------------------------------------------------------------------
 // target moments: one block
@@ -156,45 +115,6 @@ __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restric
         valid[id] = !bad && !cancelled && sqrt(ss / N) > kConstRel * mx;
     }
 }
-
-// score from shifted sums (v' = v - v0): Pearson |rho| with population moments, or -1
-// when the feature is certainly invalid.  The exact validity rule (every |v| <= 1e12,
-// std > 1e-6 max|v|) is applied by the FP64 re-score; here a feature is rejected only
-// if it must fail it (non-finite sums, |v0| > 1e12, std <= 1e-6 max(|v0|, |mean|)).
-template <typename T>
-__device__ __forceinline__ float finalize(T s1, T s2, T sr, T v0, int N, T sum_t, T sd_t) {
-    const T inv_n = T(1) / T(N);
-    const T ms = s1 * inv_n;
-    const T var = s2 * inv_n - ms * ms;
-    const T cov = sr * inv_n - ms * (sum_t * inv_n);
-    const T mean = v0 + ms;
-    const bool finite = isfinite(s1) && isfinite(s2) && isfinite(sr) && isfinite(v0);
-    if (!finite || !(fabs(v0) <= T(kValueCap)) || !(var > T(0))) return -1.f;
-    const T sd = sqrt(var);
-    const T mx = fabs(v0) > fabs(mean) ? fabs(v0) : fabs(mean);
-    if (!(sd > T(kConstRel) * mx)) return -1.f;
-    return (float)(fabs(cov) / (sd * sd_t));
-}
-
-// the same, for + and -: the sums of v' and v' r come from per-operand FP64 sums; only
-// their combination is done in FP64 (where a and b nearly cancel), the rest in T (FP64
-// throughput is a small fraction of FP32 on this part)
-template <typename T>
-__device__ __forceinline__ float finalize_lin(double s1, T s2, double sr, T v0, int N, T sum_t, T sd_t) {
-    return finalize<T>((T)s1, s2, (T)sr, v0, N, sum_t, sd_t);
-}
-
-template <typename T> struct TgtView;
-template <> struct TgtView<float> {
-    __device__ static const float* tc(const float* t32, const double*) { return t32; }
-    __device__ static float sum(const TargetStats* st) { return (float)st->sum32; }
-    __device__ static float sd(const TargetStats* st) { return st->sd32; }
-};
-template <> struct TgtView<double> {
-    __device__ static const double* tc(const float*, const double* t64) { return t64; }
-    __device__ static double sum(const TargetStats*) { return 0.0; }
-    __device__ static double sd(const TargetStats* st) { return st->sd; }
-};
 
 // ---------------------------------------------------------------------------------
 // generic scoring: one thread per id
@@ -418,114 +338,6 @@ k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const
 // ---------------------------------------------------------------------------------
 // fused generate-and-score for the top level's binary sections
 // ---------------------------------------------------------------------------------
-constexpr int TJ = 32;          // j operands per tile (= lanes)
-constexpr int NG = 8;           // warps per CTA, one group of i operands each
-constexpr int RI = 4;           // i operands per thread
-constexpr int TI = NG * RI;     // i operands per tile
-constexpr int TS = 32;          // samples per chunk
-
-struct PairArgs {
-    const Space* sp;            // plan in device memory
-    int sec[4];                 // section index of +, -, *, / at the top level (-1: off)
-    int64_t P, Q;
-    int nxp;
-    int N;
-    const int2* tiles;
-    int n_tiles;
-    float* scores;
-};
-
-// four consecutive values from shared memory (16-byte aligned)
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-    const float4 x = *reinterpret_cast<const float4*>(p);
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
-    const double2 x = *reinterpret_cast<const double2*>(p);
-    const double2 y = *reinterpret_cast<const double2*>(p + 2);
-    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
-}
-
-template <typename T> __device__ __forceinline__ T rcp(T x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
-
-// one j operand at one sample: shifted value, raw value, reciprocal, and the target's
-// value at that sample, read with one vector load
-template <typename T> struct Quad;
-template <> struct __align__(16) Quad<float> { float t, v, r, y; };
-template <> struct __align__(32) Quad<double> { double t, v, r, y; };
-
-template <typename T>
-struct __align__(32) PairBuf {
-    T at[TS][TI], av[TS][TI], ar[TS][TI];   // i operands: shifted, raw, reciprocal
-    Quad<T> bq[TS][TJ];                     // j operands and the target
-};
-
-template <typename T>
-struct __align__(32) PairSmem {
-    PairBuf<T> buf[2];                      // double buffer: stage chunk c+1 while computing c
-    T a0[TI], b0[TJ];                       // sample-0 values
-    unsigned char ok[TI + TJ];              // operand validity (FP64, recursive)
-    Prog prog[TI + TJ];                     // operand programs (on-the-fly staging only)
-};
-
-__device__ __forceinline__ bool pair_ok(int64_t i, int64_t j, int64_t P, int64_t Q, int nxp) {
-    if (!(i < j && j < P)) return false;
-    return nxp ? (i < Q && j >= Q) : (j >= Q);
-}
-
-// Staging: warp g owns samples g, g+8, g+16, g+24 of a chunk for both operand sides; lane
-// = operand.  With the operand cache (sample-major) every access is one coalesced load
-// and a conflict-free row of shared memory; without it the lane evaluates its operand's
-// program from the primaries.
-constexpr int kStageSlots = 2 * TS / NG;    // (sample, side) slots per warp and chunk
-
-template <typename T>
-__device__ __forceinline__ void stage_load(const PairArgs& A, const T* __restrict__ Xc, const T* __restrict__ cache,
-                                           const T* __restrict__ tc, const PairSmem<T>& S, int64_t i0, int64_t j0,
-                                           int s0, int g, int lane, T (&v)[kStageSlots], T (&y)[kStageSlots / 2]) {
-    const int N = A.N;
-#pragma unroll
-    for (int q = 0; q < kStageSlots; ++q) {
-        const int s = s0 + g + NG * (q >> 1);
-        const int side = q & 1;
-        const int64_t f = (side ? j0 : i0) + lane;
-        T x = T(0);
-        if (s < N && f < A.P) {
-            if (cache) x = cache[(size_t)s * A.P + f];
-            else {
-                const Prog& p = S.prog[side ? TI + lane : lane];
-                if (p.n) x = eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; });
-            }
-        }
-        v[q] = x;
-        if (side) y[q >> 1] = s < N ? tc[s] : T(0);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[kStageSlots],
-                                            const T (&y)[kStageSlots / 2], int g, int lane) {
-    PairBuf<T>& B = S.buf[b];
-#pragma unroll
-    for (int q = 0; q < kStageSlots; ++q) {
-        const int s = g + NG * (q >> 1);
-        if (q & 1) {
-            Quad<T> e;
-            e.t = v[q] - S.b0[lane];
-            e.v = v[q];
-            e.r = rcp<T>(v[q]);
-            e.y = y[q >> 1];
-            B.bq[s][lane] = e;
-        } else {
-            B.at[s][lane] = v[q] - S.a0[lane];
-            B.av[s][lane] = v[q];
-            B.ar[s][lane] = rcp<T>(v[q]);
-        }
-    }
-}
-
 template <typename T, bool LIN>
 __global__ void __launch_bounds__(NG * 32, sizeof(T) == 4 ? 2 : 1)
 k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
@@ -534,129 +346,8 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
               const double* __restrict__ A1, const double* __restrict__ AR) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int N = A.N;
-    const T* tc = TgtView<T>::tc(tc32, tc64);
-    const T sum_t = TgtView<T>::sum(st), sd_t = TgtView<T>::sd(st);
-
-    for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-        const int64_t i0 = A.tiles[tile].x, j0 = A.tiles[tile].y;
-        __syncthreads();
-        // operand programs (on-the-fly only), validity and sample-0 values
-        if (tid < TI + TJ) {
-            const int64_t f = tid < TI ? i0 + tid : j0 + (tid - TI);
-            Prog& p = S.prog[tid];
-            p.n = 0;
-            if (f < A.P && !cache && !build_prog(*A.sp, f, p)) p.n = 0;
-            S.ok[tid] = f < A.P && subvalid[f];
-            T v = T(0);
-            if (f < A.P) v = cache ? cache[f] : (p.n ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N]; }) : T(0));
-            if (tid < TI) S.a0[tid] = v; else S.b0[tid - TI] = v;
-        }
-        __syncthreads();
-
-        const int64_t j = j0 + lane;
-        int64_t iq[RI];
-        bool ok[RI];
-        T Km[RI], Kd[RI], Ke[RI];
-        const T b0 = S.b0[lane];
-        const T rb0 = rcp<T>(b0);
-#pragma unroll
-        for (int q = 0; q < RI; ++q) {
-            iq[q] = i0 + g * RI + q;
-            ok[q] = pair_ok(iq[q], j, A.P, A.Q, A.nxp);
-            const T a0 = S.a0[g * RI + q];
-            Km[q] = a0 * b0;
-            Kd[q] = a0 * rb0;
-            Ke[q] = b0 * rcp<T>(a0);
-        }
-        // + and -: only the sum of squares per pair (first sums from per-operand sums when
-        // available); *, a/b, b/a: all three sums.  Without per-operand sums (no operand
-        // cache) + and - accumulate all three as well.
-        constexpr bool lin = LIN;
-        T q2[2][RI], l1[2][RI], lr[2][RI];
-        T s1[3][RI], s2[3][RI], sr[3][RI];
-#pragma unroll
-        for (int q = 0; q < RI; ++q) {
-            q2[0][q] = q2[1][q] = l1[0][q] = l1[1][q] = lr[0][q] = lr[1][q] = T(0);
-#pragma unroll
-            for (int o = 0; o < 3; ++o) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
-        }
-
-        T pf[kStageSlots], py[kStageSlots / 2];
-        stage_load<T>(A, Xc, cache, tc, S, i0, j0, 0, g, lane, pf, py);
-        stage_store<T>(S, 0, pf, py, g, lane);
-        __syncthreads();
-        int b = 0;
-        for (int s0 = 0; s0 < N; s0 += TS, b ^= 1) {
-            const bool more = s0 + TS < N;
-            if (more) stage_load<T>(A, Xc, cache, tc, S, i0, j0, s0 + TS, g, lane, pf, py);   // in flight during compute
-            const PairBuf<T>& B = S.buf[b];
-            const int ns = min(TS, N - s0);
-            auto step = [&](int s) {
-                const Quad<T> bq = B.bq[s][lane];
-                const T r = bq.y, bt = bq.t, bv = bq.v, br = bq.r;
-                T at[RI], av[RI], ar[RI];
-                load4(&B.at[s][g * RI], at);
-                load4(&B.av[s][g * RI], av);
-                load4(&B.ar[s][g * RI], ar);
-#pragma unroll
-                for (int q = 0; q < RI; ++q) {
-                    T v;
-                    v = at[q] + bt;             q2[0][q] = fma(v, v, q2[0][q]);
-                    if constexpr (!LIN) { l1[0][q] += v; lr[0][q] = fma(v, r, lr[0][q]); }
-                    v = at[q] - bt;             q2[1][q] = fma(v, v, q2[1][q]);
-                    if constexpr (!LIN) { l1[1][q] += v; lr[1][q] = fma(v, r, lr[1][q]); }
-                    v = fma(av[q], bv, -Km[q]); s1[0][q] += v; s2[0][q] = fma(v, v, s2[0][q]); sr[0][q] = fma(v, r, sr[0][q]);
-                    v = fma(av[q], br, -Kd[q]); s1[1][q] += v; s2[1][q] = fma(v, v, s2[1][q]); sr[1][q] = fma(v, r, sr[1][q]);
-                    v = fma(bv, ar[q], -Ke[q]); s1[2][q] += v; s2[2][q] = fma(v, v, s2[2][q]); sr[2][q] = fma(v, r, sr[2][q]);
-                }
-            };
-            if (ns == TS) {
-#pragma unroll 4
-                for (int s = 0; s < TS; ++s) step(s);
-            } else {
-                for (int s = 0; s < ns; ++s) step(s);
-            }
-            if (more) stage_store<T>(S, b ^ 1, pf, py, g, lane);
-            __syncthreads();
-        }
-
-        // scores of the (up to) 20 candidates of this thread
-        const bool okj = S.ok[TI + lane];
-        const double a1j = lin && j < A.P ? A1[j] : 0.0, arj = lin && j < A.P ? AR[j] : 0.0;
-#pragma unroll
-        for (int q = 0; q < RI; ++q) {
-            if (!ok[q]) continue;
-            const T a0 = S.a0[g * RI + q];
-            const int64_t i = iq[q];
-            const bool opv = okj && S.ok[g * RI + q];   // both operands valid
-            const double a1i = lin ? A1[i] : 0.0, ari = lin ? AR[i] : 0.0;
-            if (A.sec[0] >= 0) {
-                const Section& sc = A.sp->sec[A.sec[0]];
-                float v = -1.f;
-                if (opv) v = lin ? finalize_lin<T>(a1i + a1j, q2[0][q], ari + arj, a0 + b0, N, sum_t, sd_t)
-                                 : finalize<T>(l1[0][q], q2[0][q], lr[0][q], a0 + b0, N, sum_t, sd_t);
-                A.scores[sc.base + rank_of(sc, i, j)] = v;
-            }
-            if (A.sec[1] >= 0) {
-                const Section& sc = A.sp->sec[A.sec[1]];
-                float v = -1.f;
-                if (opv) v = lin ? finalize_lin<T>(a1i - a1j, q2[1][q], ari - arj, a0 - b0, N, sum_t, sd_t)
-                                 : finalize<T>(l1[1][q], q2[1][q], lr[1][q], a0 - b0, N, sum_t, sd_t);
-                A.scores[sc.base + rank_of(sc, i, j)] = v;
-            }
-            if (A.sec[2] >= 0) {
-                const Section& sc = A.sp->sec[A.sec[2]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], Km[q], N, sum_t, sd_t) : -1.f;
-            }
-            if (A.sec[3] >= 0) {
-                const Section& sc = A.sp->sec[A.sec[3]];
-                A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], Kd[q], N, sum_t, sd_t) : -1.f;
-                A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], Ke[q], N, sum_t, sd_t) : -1.f;
-            }
-        }
-    }
+    for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x)
+        pair_tile<T, LIN>(A, Xc, tc32, tc64, st, subvalid, cache, A1, AR, S, A.tiles[tile].x, A.tiles[tile].y);
 }
 
 // ---------------------------------------------------------------------------------
