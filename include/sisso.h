@@ -65,7 +65,8 @@ enum {
 #define SISSO_OP_ALL 0xFFFu
 
 /* Arithmetic of the screening and l0 kernels.  FP64 and FP32 give the exact FP64 result
- * (section 4 of the design notes: error-bounded FP32 plus FP64 re-score / refit).  The
+ * (FP32 work is error-bounded and whatever it cannot decide is re-scored or refit in
+ * FP64).  The
  * mixed forms compute the subspace Gram on the tensor cores from BF16 or FP16 operands
  * (FP32 accumulation) and refit in FP64 the 100 best subsets and every subset whose
  * condition estimate exceeds 1e6. */
@@ -86,7 +87,7 @@ typedef struct {
                                selection and refits are always FP64 (default FP32) */
     int grammar;            /* SISSO_GRAMMAR_* (default EQ2) */
     int survivors;          /* FP32 screening window: candidates re-scored in FP64 per
-                               step (0 = max(16384, 64 k)); grown x4 automatically when
+                               step (0 = max(4096, 32 k)); grown x4 automatically when
                                it cannot prove the selection exact */
     double band_rel;        /* l0: FP32 RSS band, relative to SST, refit in FP64
                                (0 = 1e-4) */
@@ -209,6 +210,117 @@ sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, d
  * legacy default stream.  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT. */
 sisso_status sisso_gram_tc(const double* Z, const double* yc, double sdy, int n, int N, int kind, float* G,
                            float* b);
+
+/* ---- batched multi-task form ----------------------------------------------------------
+ *
+ * Many independent SISSO problems (each §2.1-2.3: feature space Eq. 2, SIS Eqs. 5-6, l0
+ * Eqs. 7-8), possibly of different sizes, solved by one persistent kernel launch captured
+ * in a CUDA graph.  Every task shares the operator set, rung, grammar, sis_size and
+ * max_dim; each has its own N and d.  Each task computes what sisso_create + sisso_fit
+ * with precision SISSO_PREC_FP32 computes (FP32 screening and l0 enumeration, FP64
+ * re-score, refit and model), so its descriptors equal the per-problem path's.
+ *
+ * The paper solves one problem at a time; this form serves many small ones at once.
+ */
+typedef struct sisso_batch sisso_batch;
+
+typedef struct {
+    const double* X;    /* N x d row-major, HOST memory */
+    const double* y;    /* N, HOST memory */
+    int N, d;
+} sisso_task;
+
+/* One task's result.  status: SISSO_OK or the task's own error (SISSO_ERR_NUMERIC: no
+ * valid feature or every subset singular; SISSO_ERR_CAPACITY: a window or band
+ * overflowed).  Dimension t = 1..n_dims is row t-1: ids ascending, coef[0] the intercept
+ * and coef[j] the coefficient of ids[j-1], in original units. */
+typedef struct {
+    int status;
+    int n_dims;
+    int64_t ids[SISSO_MAX_DIM][SISSO_MAX_DIM];
+    double coef[SISSO_MAX_DIM][SISSO_MAX_DIM + 1];
+    double rmse[SISSO_MAX_DIM];
+    double r2[SISSO_MAX_DIM];
+} sisso_task_result;
+
+/* Launch shape of the persistent kernel (0 = keep the current value). */
+typedef struct {
+    int score_units;    /* screening units (32 x 32 pair tiles, 32-operand unary blocks,
+                           256-id blocks) per work item */
+    int enum_items;     /* l0 work units (a (D-2)-prefix x 16 rows of subsets) per work item */
+    int gram_rows;      /* new subspace rows per Gram work item */
+    int ctas_per_sm;    /* resident CTAs per SM: 1 or 2 */
+    int window;         /* first screening window (candidates re-scored in FP64) */
+} sisso_batch_tune;
+
+/* Per-batch counters of the last run. */
+typedef struct {
+    double ms_run;              /* device time of the last sisso_batch_run (CUDA events) */
+    int64_t candidates_scored;  /* all tasks, all steps */
+    int64_t subsets_fit;        /* l0 subsets enumerated, all tasks and steps */
+    int64_t subsets_refit;      /* band entries re-solved in FP64 */
+    int windows_grown;
+    int windows_saturated;      /* tasks whose window hit its cap without proof */
+    int tasks_failed;           /* tasks with status != SISSO_OK */
+    int grid;                   /* CTAs launched */
+    /* device-clock profile of the last run, per stage: 0 unused, 1 start, 2 level, 3 score,
+       4 gram, 5 bound, 6 band, 7 validity flattening, 8 select, 9 refit, 10 waiting for
+       work, 11 unused.  stage_ms sums the CTAs' time, stage_max_ms is the longest single
+       occurrence, stage_count the occurrences. */
+    double stage_ms[12];
+    double stage_max_ms[12];
+    int64_t stage_count[12];
+} sisso_batch_stats;
+
+/* Plan every task (feature space, work units, memory), copy the inputs to pinned host
+ * and device memory, and allocate all device memory the runs need (one arena).  opts:
+ * grammar, max_band (band capacity per task and step, default 16384), cuda_stream and
+ * device are used; precision must be SISSO_PREC_FP32 (or default).  Limits: n_tasks <=
+ * 2^20, max_dim * sis_size <= 512, every task N >= max_dim + 1 and d >= 1, finite inputs,
+ * non-constant y, and at most 2^18 screening units per task.  Errors: SISSO_ERR_ARG
+ * (message names the task), SISSO_ERR_OOM, SISSO_ERR_CUDA.  On error *out is NULL and
+ * the message is in sisso_batch_create_error(). */
+sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t op_set, int rung, int sis_size,
+                                int max_dim, const sisso_opts* opts, sisso_batch** out);
+const char* sisso_batch_create_error(void);
+
+/* Replace the launch shape (fields 0 keep their value); the graphs are re-captured. */
+sisso_status sisso_batch_set_tune(sisso_batch* b, const sisso_batch_tune* tune);
+sisso_status sisso_batch_get_tune(const sisso_batch* b, sisso_batch_tune* tune);
+
+/* Autotuner: times candidate launch shapes on this batch (each a full run, reps times,
+ * CUDA events) one parameter at a time and keeps the fastest.  cache_path (may be NULL):
+ * a text file of earlier choices keyed by the batch's shape signature; a hit skips the
+ * timing, a miss appends the choice.  chosen (may be NULL) receives it. */
+sisso_status sisso_batch_autotune(sisso_batch* b, int reps, const char* cache_path, sisso_batch_tune* chosen);
+
+/* Replace task inputs with new values of the same shapes (HOST memory, copied to the
+ * pinned staging buffer; the device copy happens in the next run with copies = 1). */
+sisso_status sisso_batch_load(sisso_batch* b, const sisso_task* tasks, int n_tasks);
+
+/* One run of every task: a CUDA graph launch on the batch's stream, waited for.  copies =
+ * 1: the graph also copies the inputs host -> device before the kernel and the results
+ * device -> host after it; copies = 0: inputs already on the device (from an earlier
+ * copying run or create), results fetched by sisso_batch_results.  Errors:
+ * SISSO_ERR_TIMEOUT (a bounded device wait ran out), SISSO_ERR_CAPACITY (work queue),
+ * SISSO_ERR_CUDA.  Per-task errors are in the results, not here. */
+sisso_status sisso_batch_run(sisso_batch* b, int copies);
+
+/* Results of the last run for tasks [0, n): out HOST, n entries. */
+sisso_status sisso_batch_results(sisso_batch* b, sisso_task_result* out, int n);
+
+/* Per-task device timestamps of the last run, in ms from the launch's first CTA start:
+ * start[i] when task i began, end[i] when its last result was written.  HOST, n each
+ * (either may be NULL). */
+sisso_status sisso_batch_timing(sisso_batch* b, double* start, double* end, int n);
+
+sisso_status sisso_batch_get_stats(sisso_batch* b, sisso_batch_stats* out);
+const char* sisso_batch_last_error(const sisso_batch* b);
+void sisso_batch_destroy(sisso_batch* b);
+
+/* Convenience: create, one copying run, results, destroy.  results: HOST, n_tasks. */
+sisso_status sisso_fit_batch(const sisso_task* tasks, int n_tasks, uint32_t op_set, int rung, int sis_size,
+                             int max_dim, const sisso_opts* opts, sisso_task_result* results);
 
 /* ---- allocation-free l0 search --------------------------------------------------------
  *

@@ -31,6 +31,8 @@ constexpr double kPivotMin = 1e-12;    // FP64 Cholesky pivot: singular at or be
 constexpr float kPivotMin32 = 1e-5f;   // FP32 pivot at or below: refit in FP64
 constexpr double kRssTie = 1e-12;      // RSS within this * SST of the minimum: tie
 constexpr double kStopRel = 1e-10;     // RMSE <= this * std(y): exact fit, stop
+constexpr double kScoreErr32 = 2e-4;   // bound on |FP32 kernel score - FP64 score|
+constexpr double kScoreErr64 = 1e-6;   // ... FP64 kernel (FP32 score buffer)
 
 enum Op : int { ADD = 0, SUB, MUL, DIV, EXP, LOG, SQRT, SQ, INV, SIN, CUBE, EXPNEG };
 // kinds of sections: unary on new_{l-1}; symmetric or ordered pairs under either rule
@@ -448,6 +450,8 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
                         std::vector<int64_t>& acc);
 sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int precision,
                            double* out_dev);
+// 32 x 32 operand-pair tiles of the top level's binary sections (upper left corners)
+void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles);
 
 // subspace and l0 (l0.cu)
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);

@@ -14,13 +14,14 @@
 //  remain, and RSS = N (syy - |w_prefix|^2 - w_i1^2 - num^2 / d).  Lanes own i2 (row i1
 //  of G is read coalesced), i1 is warp-uniform.
 //
-//  FP32 exactness: pass 1 finds UB = min_E (RSS32_E + err_E), pass 2 keeps every subset
-//  with RSS32_E - err_E <= UB (err_E = SST (rho + kappa / min pivot_E)) plus every
-//  subset with a pivot <= 1e-5; the kept band is re-solved in FP64 and the winner is the
-//  lowest FP64 RSS, ties (1e-12 SST) to the smallest ascending global-id tuple — the
-//  same rule as a full FP64 search.  In FP64 mode pass 1 gives the minimum and pass 2
-//  the tie window directly.
-#include "common.cuh"
+//  FP32 exactness: pass 1 finds UB = the FP64 RSS of the best FP32 subset (an upper bound
+//  of the minimum); pass 2 takes every subset with RSS32_E - err_E <= UB + tie (err_E an a
+//  posteriori bound from the subset's coefficients) and every subset with an FP32 pivot
+//  <= 1e-5, solves each in FP64 and keeps it when its FP64 RSS is within UB + tie.  The
+//  winner is the lowest FP64 RSS of the band, ties (1e-12 SST) to the smallest ascending
+//  global-id tuple — the same rule as a full FP64 search.  In FP64 mode pass 1 gives the
+//  minimum and pass 2 the tie window directly.
+#include "l0_device.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -30,27 +31,8 @@
 namespace sg {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kRows = 16;                 // i1 rows per work item
-constexpr double kRho = 5e-5;             // FP32 RSS error floor, relative to SST
-constexpr double kKappa = 1e-6;           // FP32 RSS error per unit 1/pivot, rel. to SST
-constexpr float kPivotHi = 1e-2f;         // last pivot below this: exact error bound
+template <typename T> __device__ __forceinline__ T warp_sum(T v) { return l0_warp_sum(v); }
 
-template <typename T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// order-preserving maps of floating values to unsigned integers (for atomicMin)
-__device__ __forceinline__ unsigned long long okey(double v) {
-    unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double okey_inv(unsigned long long k) {
-    const unsigned long long u = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
-    return __longlong_as_double((long long)u);
-}
 
 // ---------------------------------------------------------------------------------
 // subspace: standardised rows and Gram growth
@@ -128,233 +110,23 @@ __global__ void k_gram_rows(const double* __restrict__ Z, const double* __restri
     }
 }
 
-// ---------------------------------------------------------------------------------
-// enumeration
-// ---------------------------------------------------------------------------------
-template <typename T>
-struct EnumArgs {
-    const T* G;                 // n x n (leading dimension ld)
-    const T* b;
-    int ld, n, N;
-    T syy;                      // y~^T y~ / N
-    double sst;                 // N * syy
-    int cpp;                    // work items per prefix (chunks of kRows i1 rows)
-    int64_t n_items;            // C(n - 2, D - 2) prefixes x cpp
-    int* counter;               // work counter
-    float tau;                  // pivots at or below: FP32 -> refit list; FP64 -> singular
-    int fp32;                   // error-bounded FP32 mode
-    unsigned long long* ub_key; // pass 1 output (ordered key of the bound)
-    const Winner* win;          // pass 2 input: win->thr
-    uint64_t* band;
-    unsigned int* band_count;
-    int64_t band_cap;
-    unsigned long long* examined;
-    double rho, kappa;          // FP32 RSS error model: SST (rho + kappa / min pivot)
-    float* band_r32;            // optional: the FP32 RSS of each band entry (NaN: flagged by a pivot)
-};
-
-template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pre)[DP > 0 ? DP : 1], int i1, int i2) {
-    uint64_t k = 0;
-    int s = 0;
-#pragma unroll
-    for (int m = 0; m < DP; ++m) { k |= (uint64_t)pre[m] << s; s += 16; }
-    k |= (uint64_t)i1 << s; s += 16;
-    k |= (uint64_t)i2 << s;
-    return k;
-}
-
-// r-th DP-combination in colex order (largest element first): p[DP-1] is the largest m
-// with C(m, DP) <= r, then the rest recursively
-__device__ __forceinline__ int64_t binom2(int64_t m) { return m * (m - 1) / 2; }
-__device__ __forceinline__ int64_t binom3(int64_t m) { return m * (m - 1) * (m - 2) / 6; }
-
-template <int DP> __device__ __forceinline__ void colex_unrank(int64_t r, int (&p)[DP > 0 ? DP : 1]) {
-    if (DP == 0) return;
-    if (DP == 1) { p[0] = (int)r; return; }
-    if (DP == 2) {
-        int64_t m = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
-        while (m > 1 && binom2(m) > r) --m;
-        while (binom2(m + 1) <= r) ++m;
-        p[1] = (int)m;
-        p[0] = (int)(r - binom2(m));
-        return;
-    }
-    if (DP == 3) {
-        int64_t m = (int64_t)cbrt(6.0 * (double)r) + 1;
-        while (m > 2 && binom3(m) > r) --m;
-        while (binom3(m + 1) <= r) ++m;
-        p[DP > 2 ? 2 : 0] = (int)m;
-        r -= binom3(m);
-        int64_t q = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
-        while (q > 1 && binom2(q) > r) --q;
-        while (binom2(q + 1) <= r) ++q;
-        p[1] = (int)q;
-        p[0] = (int)(r - binom2(q));
-    }
-}
-
-// MODE 0: bound (min of RSS + err); MODE 1: band collection
 template <typename T, int DP, int MODE>
 __global__ void __launch_bounds__(kWarps * 32) k_l0_enum(EnumArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = A.n;
-    // per-warp tables: R[DP][n], dpart[n], npart[n]
-    T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)w * (DP + 2) * n;
-    T* Rt = tab;
-    T* dpart = tab + (size_t)DP * n;
-    T* npart = dpart + n;
-    const T N = T(A.N);
-    const T sstT = T(A.sst);
-    T best = T(INFINITY);                 // pass 1: this lane's bound
-    T thr = T(0);
-    if (MODE == 1) thr = T(A.win->thr);
+    T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)w * (DP + 2) * A.n;
+    T best = T(INFINITY);                 // pass 1: this lane's best subset
+    unsigned long long best_key = 0;
+    const double thr = MODE == 1 ? A.win->thr : 0.0;
     unsigned long long my_examined = 0;
-
     while (true) {
         int item;
         if (lane == 0) item = atomicAdd(A.counter, 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= A.n_items) break;
-        // item -> (prefix in colex order, chunk): prefixes are the (D-2)-combinations of
-        // [0, n-2) ordered by their largest element, so the longest sweeps come first
-        int pre[DP > 0 ? DP : 1];
-        const int64_t prank = (int64_t)item / A.cpp;
-        const int chunk = item % A.cpp;
-        colex_unrank<DP>(prank, pre);
-        const int i1s = (DP > 0 ? pre[DP - 1] + 1 : 0) + chunk * kRows;
-        if (i1s >= n - 1) continue;
-        // prefix factor (warp-uniform, redundant in every lane)
-        T L[DP > 0 ? DP : 1][DP > 0 ? DP : 1], invd[DP > 0 ? DP : 1], wv[DP > 0 ? DP : 1];
-        T pw2 = T(0), minpiv = T(1e30);
-        bool pre_ok = true;
-#pragma unroll
-        for (int j = 0; j < DP; ++j) {
-            T dj = A.G[(size_t)pre[j] * A.ld + pre[j]];
-#pragma unroll
-            for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
-            pre_ok = pre_ok && dj > T(A.tau);
-            minpiv = dj < minpiv ? dj : minpiv;
-            const T ljj = sqrt(dj > T(0) ? dj : T(1));
-            L[j][j] = ljj;
-            invd[j] = T(1) / ljj;
-#pragma unroll
-            for (int i = j + 1; i < DP; ++i) {
-                T v = A.G[(size_t)pre[i] * A.ld + pre[j]];
-#pragma unroll
-                for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
-                L[i][j] = v * invd[j];
-            }
-            T v = A.b[pre[j]];
-#pragma unroll
-            for (int m = 0; m < j; ++m) v -= L[j][m] * wv[m];
-            wv[j] = v * invd[j];
-            pw2 += wv[j] * wv[j];
-        }
-        const int i1e = min(i1s + kRows, n - 1);
-        if (MODE == 0 && lane == 0)
-            for (int i1 = i1s; i1 < i1e; ++i1) my_examined += (unsigned long long)(n - 1 - i1);
-        if (!A.fp32 && !pre_ok) continue;      // FP64: singular prefix, every extension skipped
-        // tables for x in [i1s, n)
-        for (int x = i1s + lane; x < n; x += 32) {
-            T r[DP > 0 ? DP : 1];
-            T dp = A.G[(size_t)x * A.ld + x], np = A.b[x];
-#pragma unroll
-            for (int m = 0; m < DP; ++m) {
-                T v = A.G[(size_t)x * A.ld + pre[m]];
-#pragma unroll
-                for (int q = 0; q < m; ++q) v -= r[q] * L[m][q];
-                r[m] = v * invd[m];
-                Rt[(size_t)m * n + x] = r[m];
-                dp -= r[m] * r[m];
-                np -= r[m] * wv[m];
-            }
-            dpart[x] = dp;
-            npart[x] = np;
-        }
-        __syncwarp();
-        for (int i1 = i1s; i1 < i1e; ++i1) {
-            T r1[DP > 0 ? DP : 1];
-#pragma unroll
-            for (int m = 0; m < DP; ++m) r1[m] = Rt[(size_t)m * n + i1];
-            const T d1 = dpart[i1];
-            const bool ok1 = pre_ok && d1 > T(A.tau);
-            if (!A.fp32 && !ok1) continue;
-            const T isd1 = T(1) / sqrt(d1 > T(0) ? d1 : T(1));
-            const T w1 = npart[i1] * isd1;
-            const T pw = pw2 + w1 * w1;
-            const T mp1 = d1 < minpiv ? d1 : minpiv;          // smallest pivot so far
-            // error bound for subsets whose last pivot is >= kPivotHi (FP32 only)
-            T err_u = T(0);
-            if (A.fp32) {
-                const T mp = mp1 < T(kPivotHi) ? mp1 : T(kPivotHi);
-                err_u = sstT * (T(A.rho) + T(A.kappa) / (mp > T(0) ? mp : T(1e-30)));
-            }
-            const T base_c = A.syy - pw;
-            T c_fast;
-            if (MODE == 0) c_fast = base_c - (best - err_u) / N;
-            else c_fast = base_c - (thr + err_u) / N;
-            const T* Grow = A.G + (size_t)i1 * A.ld;
-            for (int i2 = i1 + 1 + lane; i2 < n; i2 += 32) {
-                T g = Grow[i2];
-#pragma unroll
-                for (int m = 0; m < DP; ++m) g -= r1[m] * Rt[(size_t)m * n + i2];
-                const T rr = g * isd1;
-                const T d2 = dpart[i2] - rr * rr;
-                const T num = npart[i2] - rr * w1;
-                const bool ill = !ok1 || !(d2 > T(A.tau));
-                if (ill) {
-                    if (MODE == 1 && A.fp32) {
-                        const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) {
-                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
-                            if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
-                        }
-                    }
-                    continue;
-                }
-                const bool slow = A.fp32 && d2 < T(kPivotHi);
-                if (!slow) {
-                    const T f = num * num - c_fast * d2;
-                    if (MODE == 0 ? !(f > T(0)) : !(f >= T(0))) continue;
-                    if (MODE == 0) {
-                        const T rss = N * (base_c - num * num / d2);
-                        best = rss + err_u;
-                        c_fast = base_c - (best - err_u) / N;
-                    } else {
-                        const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) {
-                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
-                            if (A.band_r32) A.band_r32[slot] = (float)(N * (base_c - num * num / d2));
-                        }
-                    }
-                } else {
-                    const T mp = d2 < mp1 ? d2 : mp1;
-                    const T err = sstT * (T(A.rho) + T(A.kappa) / mp);
-                    const T rss = N * (base_c - num * num / d2);
-                    if (MODE == 0) {
-                        if (rss + err < best) { best = rss + err; c_fast = base_c - (best - err_u) / N; }
-                    } else if (rss - err <= thr) {
-                        const unsigned slot = atomicAdd(A.band_count, 1u);
-                        if (slot < A.band_cap) {
-                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
-                            if (A.band_r32) A.band_r32[slot] = (float)rss;
-                        }
-                    }
-                }
-            }
-        }
-        __syncwarp();
+        enum_item<T, DP, MODE>(A, tab, item, best, best_key, thr, my_examined);
     }
-    if (MODE == 0) {
-        // lane bounds -> global minimum
-        double bv = (double)best;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, o));
-        if (lane == 0 && bv < INFINITY) atomicMin(A.ub_key, okey(bv));
-        unsigned long long ex = warp_sum(my_examined);
-        if (lane == 0) atomicAdd(A.examined, ex);
-    }
+    if (MODE == 0) enum_flush(A, DP + 2, best, best_key, my_examined);
 }
 
 // D = 1: RSS_i = N (syy - b_i^2 / G_ii)
@@ -362,30 +134,7 @@ template <typename T, int MODE>
 __global__ void k_l0_single(EnumArgs<T> A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const T d = A.G[(size_t)i * A.ld + i];
-    const T bi = A.b[i];
-    if (MODE == 0) atomicAdd(A.examined, 1ull);
-    if (!(d > T(A.tau))) {
-        if (MODE == 1 && A.fp32) {
-            const unsigned slot = atomicAdd(A.band_count, 1u);
-            if (slot < A.band_cap) {
-                A.band[slot] = (uint64_t)i;
-                if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
-            }
-        }
-        return;
-    }
-    const T rss = T(A.N) * (A.syy - bi * bi / d);
-    const T err = A.fp32 ? T(A.sst) * (T(A.rho) + T(A.kappa) / d) : T(0);
-    if (MODE == 0) {
-        atomicMin(A.ub_key, okey((double)(rss + err)));
-    } else if (rss - err <= T(A.win->thr)) {
-        const unsigned slot = atomicAdd(A.band_count, 1u);
-        if (slot < A.band_cap) {
-            A.band[slot] = (uint64_t)i;
-            if (A.band_r32) A.band_r32[slot] = (float)rss;
-        }
-    }
+    single_subset<T, MODE>(A, i, MODE == 1 ? A.win->thr : 0.0);
 }
 
 // threshold of pass 2: the bound (+ the FP64 tie window)
@@ -398,41 +147,6 @@ __global__ void k_set_thr(Winner* w, const unsigned long long* ub_key, double ad
 // ---------------------------------------------------------------------------------
 // FP64 refit of the band and the tie-broken winner
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void unpack(uint64_t key, int D, int* pos) {
-    for (int j = 0; j < D; ++j) pos[j] = (int)((key >> (16 * j)) & 0xFFFF);
-}
-
-__device__ double rss64(const double* G, const double* b, int ld, double syy, int N, int D, const int* pos,
-                        double* gamma) {
-    double L[kMaxDim][kMaxDim], w[kMaxDim];
-    for (int j = 0; j < D; ++j) {
-        double dj = G[(size_t)pos[j] * ld + pos[j]];
-        for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
-        if (!(dj > kPivotMin)) return INFINITY;
-        L[j][j] = sqrt(dj);
-        for (int i = j + 1; i < D; ++i) {
-            double v = G[(size_t)pos[i] * ld + pos[j]];
-            for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
-            L[i][j] = v / L[j][j];
-        }
-    }
-    double q = 0.0;
-    for (int j = 0; j < D; ++j) {
-        double v = b[pos[j]];
-        for (int m = 0; m < j; ++m) v -= L[j][m] * w[m];
-        w[j] = v / L[j][j];
-        q += w[j] * w[j];
-    }
-    if (gamma) {   // back substitution L^T gamma = w
-        for (int j = D - 1; j >= 0; --j) {
-            double v = w[j];
-            for (int m = j + 1; m < D; ++m) v -= L[m][j] * gamma[m];
-            gamma[j] = v / L[j][j];
-        }
-    }
-    return (double)N * (syy - q);
-}
-
 __global__ void k_refit(const double* __restrict__ G, const double* __restrict__ b, int ld, double syy, int N,
                         int D, const uint64_t* __restrict__ band, const unsigned* __restrict__ count, int64_t cap,
                         double* __restrict__ rss, unsigned long long* min_key) {
@@ -448,16 +162,6 @@ __global__ void k_refit(const double* __restrict__ G, const double* __restrict__
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local = fmin(local, __shfl_xor_sync(0xffffffffu, local, o));
     if ((threadIdx.x & 31) == 0 && local < INFINITY) atomicMin(min_key, okey(local));
-}
-
-__device__ __forceinline__ void gid_tuple(const int64_t* gid, const int* pos, int D, int64_t* t) {
-    for (int j = 0; j < D; ++j) t[j] = gid[pos[j]];
-    for (int a = 1; a < D; ++a)
-        for (int c = a; c > 0 && t[c - 1] > t[c]; --c) { const int64_t x = t[c]; t[c] = t[c - 1]; t[c - 1] = x; }
-}
-__device__ __forceinline__ bool tuple_less(const int64_t* a, const int64_t* b, int D) {
-    for (int j = 0; j < D; ++j) if (a[j] != b[j]) return a[j] < b[j];
-    return false;
 }
 
 // one block: among refit entries within the tie window of the minimum, the smallest
@@ -806,7 +510,8 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
         EnumArgs<float> A{};
         A.G = G32; A.b = b32; A.ld = ld; A.n = n; A.N = c->N; A.syy = (float)syy; A.sst = sst;
         A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
-        A.tau = kPivotMin32; A.fp32 = 1; A.rho = kRho; A.kappa = kKappa; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
+        A.tau = kPivotMin32; A.fp32 = 1; A.sqrt_syy = std::sqrt(syy); A.ub_key = ub_key; A.win = c->win; A.band = c->band;
+        A.G64 = G; A.b64 = b; A.syy64 = syy; A.tie64 = 2.0 * kRssTie * sst;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;
         k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, 0.0);
@@ -878,7 +583,7 @@ sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w) {
     const double sst = c->syy * c->N;
     EnumArgs<float> A{};
     A.G = c->G32; A.b = c->b32; A.ld = c->n_cap; A.n = n; A.N = c->N; A.syy = (float)c->syy; A.sst = sst;
-    A.cpp = cpp; A.n_items = n_items; A.counter = c->work; A.tau = 1e-6f; A.fp32 = 1; A.rho = 0.0; A.kappa = 0.0;
+    A.cpp = cpp; A.n_items = n_items; A.counter = c->work; A.tau = 1e-6f; A.fp32 = 1; A.sqrt_syy = 0.0;
     A.ub_key = ub_key; A.win = c->win; A.band = c->band; A.band_count = c->band_count; A.band_cap = c->band_cap;
     A.examined = examined; A.band_r32 = c->band_r32;
     sisso_status st;
@@ -1059,7 +764,8 @@ extern "C" sisso_status sisso_l0_search_noalloc(const double* G, const double* b
     if (fp32) {
         EnumArgs<float> A{};
         A.G = dG32; A.b = db32; A.ld = n; A.n = n; A.N = N; A.syy = (float)syy; A.sst = sst;
-        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = kPivotMin32; A.fp32 = 1; A.rho = kRho; A.kappa = kKappa;
+        A.cpp = cpp; A.n_items = n_items; A.counter = counter; A.tau = kPivotMin32; A.fp32 = 1; A.sqrt_syy = std::sqrt(syy);
+        A.G64 = dG; A.b64 = db; A.syy64 = syy; A.tie64 = 2.0 * kRssTie * sst;
         A.ub_key = ub_key; A.win = win; A.band = band; A.band_count = band_count;
         A.band_cap = (int64_t)kNaBand; A.examined = ex_key;
         ok(na_enum(A, D, 0, sms, st));

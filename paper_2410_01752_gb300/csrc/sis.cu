@@ -28,33 +28,7 @@ namespace {
 __global__ void k_prepare_target(const double* __restrict__ t, int N, double* __restrict__ tc64,
                                  float* __restrict__ tc32, TargetStats* st) {
     __shared__ double red[32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) s += t[i];
-    const double mean = block_sum(s, red) / N;
-    double ss = 0.0, s32 = 0.0, ss32 = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double c = t[i] - mean;
-        const float f = (float)c;
-        tc64[i] = c;
-        tc32[i] = f;
-        ss += c * c;
-        s32 += (double)f;
-        ss32 += (double)f * (double)f;
-    }
-    ss = block_sum(ss, red);
-    double tsum = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tsum += tc64[i];
-    tsum = block_sum(tsum, red);
-    s32 = block_sum(s32, red);
-    ss32 = block_sum(ss32, red);
-    if (threadIdx.x == 0) {
-        st->mean = mean;
-        st->sd = sqrt(ss / N);
-        st->tsum = tsum;
-        st->sum32 = s32;
-        st->srr32 = ss32 - s32 * s32 / N;
-        st->sd32 = (float)sqrt(st->srr32 / N);
-    }
+    prepare_target_block(t, N, tc64, tc32, st, red);
 }
 
 // FP64 validity of ids [lo, hi) (one level), one warp per id: the value rules (finite,
@@ -177,33 +151,16 @@ __global__ void k_fill_cache(const Space* __restrict__ sp, const T* __restrict__
 
 // ids [lo, hi) below the top level (P = |phi_{L-1}| of them) scored from the cache: one
 // thread per id, coalesced across the warp for each sample
+
 template <typename T>
 __global__ void k_score_cached(const T* __restrict__ cache, int N, int64_t P, const float* tc32,
                                const double* tc64, const TargetStats* st, int64_t lo, int64_t hi,
                                const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
     const int64_t id = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= hi) return;
-    if (!subvalid[id]) { scores[id] = -1.f; return; }
-    const T* tc = TgtView<T>::tc(tc32, tc64);
-    const T v0 = cache[id];
-    T s1 = 0, s2 = 0, sr = 0;
-    for (int s = 0; s < N; ++s) {
-        const T v = cache[(size_t)s * P + id] - v0;
-        s1 += v;
-        s2 = fma(v, v, s2);
-        sr = fma(v, tc[s], sr);
-    }
-    scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+    score_cached_id<T>(cache, N, P, tc32, tc64, st, id, subvalid, scores);
 }
 
-constexpr int kUnaryMax = 8;
-struct UnaryArgs {
-    int n_ops;
-    int op[kUnaryMax];
-    int64_t base[kUnaryMax];   // first id of each operator's section
-    int64_t Q, P;              // operands: new_{L-1} = [Q, P)
-    int N;
-};
 
 // the same with one warp per id (few ids, many samples): lanes split the samples
 template <typename T>
@@ -300,39 +257,14 @@ __global__ void k_score_unary_w(UnaryArgs U, const T* __restrict__ cache, const 
 // staged in shared memory
 
 
+
 template <typename T>
 __global__ void __launch_bounds__(kUnaryMax * 32)
 k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
               const TargetStats* st, const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
     __shared__ T xs[32][33];
     __shared__ T r[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t z0 = U.Q + (int64_t)blockIdx.x * 32;
-    const int64_t z = z0 + lane;
-    const int N = U.N;
-    const T* tc = TgtView<T>::tc(tc32, tc64);
-    const bool active = w < U.n_ops && z < U.P;
-    const int op = w < U.n_ops ? U.op[w] : EXP;
-    const T v0 = active ? op_unary<T>(op, cache[z]) : T(0);
-    T s1 = 0, s2 = 0, sr = 0;
-    for (int s0 = 0; s0 < N; s0 += 32) {
-        __syncthreads();
-        // warp w stages samples w, w+8, ...: 32 consecutive operands each (coalesced)
-        for (int q = w; q < 32; q += kUnaryMax)
-            xs[q][lane] = (z < U.P && s0 + q < N) ? cache[(size_t)(s0 + q) * U.P + z] : T(1);
-        if (w == 0) r[lane] = s0 + lane < N ? tc[s0 + lane] : T(0);
-        __syncthreads();
-        const int ns = min(32, N - s0);
-        if (active)
-            for (int s = 0; s < ns; ++s) {
-                const T v = op_unary<T>(op, xs[s][lane]) - v0;
-                s1 += v;
-                s2 = fma(v, v, s2);
-                sr = fma(v, r[s], sr);
-            }
-    }
-    if (active)
-        scores[U.base[w] + (z - U.Q)] = subvalid[z] ? finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st)) : -1.f;
+    unary_block<T>(U, cache, tc32, tc64, st, subvalid, scores, blockIdx.x, xs, r);
 }
 
 // ---------------------------------------------------------------------------------
@@ -417,76 +349,15 @@ __global__ void k_compact(const float* __restrict__ scores, int64_t n, const uns
 // Pearson score with two passes as the definition does, and keeps the standardised
 // vector (zc, when given) and kProbes of its values for the duplicate rule.
 // ---------------------------------------------------------------------------------
+
 __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict__ Xc, int N,
                           const double* __restrict__ tc, const TargetStats* __restrict__ st,
                           const int64_t* __restrict__ ids, int n, const unsigned char* __restrict__ subvalid,
                           const double* __restrict__ V, double* score, double* mean_out, double* sd_out,
                           int* valid_out, double* __restrict__ probe, double* __restrict__ zc) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n) return;
-    Prog p;
-    int level, op; int64_t a, b;
-    const int64_t id = ids[w];
-    const int64_t Pbot = sp->phi[sp->rung - 1];
-    OpRef ref{};
-    bool built = decode(*sp, id, level, op, a, b) && (V ? make_opref(*sp, id, ref) : build_prog(*sp, id, p));
-    if (built && id < Pbot && !subvalid[id]) built = false;                                  // exact, recursive
-    if (built && id >= Pbot && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
-    if (!built) {
-        if (lane == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
-        if (lane < kProbes) probe[(size_t)w * kProbes + lane] = 0.0;
-        return;
-    }
-    double* z = zc ? zc + (size_t)w * N : nullptr;
-    auto value = [&](int i, double& mag) -> double {
-        return V ? opref_val(ref, V, N, i, mag) : eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
-    };
-    // one pass of sums shifted by the sample-0 value (FP64: relative error ~1e-14, far
-    // inside the 1e-9 tie window of the walk)
-    double mag0;
-    const double v0 = value(0, mag0);
-    double s1 = 0.0, s2 = 0.0, sc = 0.0, mx = 0.0, mo = 0.0;
-    int bad = 0;
-    for (int i = lane; i < N; i += 32) {
-        double mag;
-        const double v = value(i, mag);
-        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
-        const double u = v - v0;
-        s1 += u;
-        s2 += u * u;
-        sc += u * tc[i];
-        mx = fmax(mx, fabs(v));
-        mo = fmax(mo, mag);
-        if (z) z[i] = v;
-    }
-    bad = warp_or(bad);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    sc = warp_sum(sc);
-    mx = warp_max(mx);
-    mo = warp_max(mo);
-    // identically zero: a top-level + or - whose operands cancel (lower ids: in subvalid)
-    const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
-    const bool cancelled = top_addsub && mx <= kCancelRel * mo;
-    const double mean = v0 + s1 / N;
-    const double var = s2 / N - (s1 / N) * (s1 / N);
-    const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
-    const int ok = !bad && !cancelled && sd > kConstRel * mx;
-    const double inv = ok ? 1.0 / sd : 0.0;
-    if (z)
-        for (int i = lane; i < N; i += 32) z[i] = (z[i] - mean) * inv;
-    if (lane < kProbes) {
-        const int i = (int)(((int64_t)lane * N) / kProbes);
-        double mag;
-        const double v = z ? z[i] : (value(i, mag) - mean) * inv;
-        probe[(size_t)w * kProbes + lane] = v;
-    }
-    if (lane == 0) {
-        valid_out[w] = ok;
-        mean_out[w] = mean;
-        sd_out[w] = sd;
-        score[w] = ok ? fabs(sc - (s1 / N) * st->tsum) / ((double)N * sd * st->sd) : -1.0;
-    }
+    rescore_one(sp, Xc, N, N, tc, st, ids[w], w, subvalid, V, score, mean_out, sd_out, valid_out, probe, zc);
 }
 
 // sort keys: valid survivors not in S get their FP64 score, others -1; padding -2
@@ -880,7 +751,7 @@ sisso_status prepare_target(sisso_ctx* c, const double* target_dev) {
 }
 
 // tiles of the top level's pair set (i tile origin, j tile origin)
-static void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
+void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
     tiles.clear();
     for (int64_t i0 = 0; i0 < P; i0 += TI) {
         if (nxp && i0 >= Q) break;
@@ -1040,7 +911,7 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
     if (n_prev > 0)
         cudaMemcpyAsync(c->S_sorted, Ss.data(), sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
     const bool fp_kernel64 = c->opts.precision == SISSO_PREC_FP64;
-    const double eps = fp_kernel64 ? 1e-6 : 2e-4;   // bound on |score_kernel - score_FP64|
+    const double eps = fp_kernel64 ? kScoreErr64 : kScoreErr32;   // bound on |score_kernel - score_FP64|
     int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(4096, 32LL * k);
     const int64_t n = c->n_feat;
     const int gridS = std::max(1, c->sms * 8);

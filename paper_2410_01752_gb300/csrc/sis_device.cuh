@@ -196,6 +196,178 @@ __device__ __forceinline__ void stage_store(PairSmem<T>& S, int b, const T (&v)[
 }
 
 
+// moments of a screening target t (one block of any multiple of 32 threads): the centred
+// copies in FP64 and FP32 and their sums
+__device__ void prepare_target_block(const double* t, int N, double* tc64, float* tc32, TargetStats* st,
+                                     double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += t[i];
+    const double mean = block_sum(s, red) / N;
+    double ss = 0.0, s32 = 0.0, ss32 = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double c = t[i] - mean;
+        const float f = (float)c;
+        tc64[i] = c;
+        tc32[i] = f;
+        ss += c * c;
+        s32 += (double)f;
+        ss32 += (double)f * (double)f;
+    }
+    ss = block_sum(ss, red);
+    double tsum = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tsum += tc64[i];
+    tsum = block_sum(tsum, red);
+    s32 = block_sum(s32, red);
+    ss32 = block_sum(ss32, red);
+    if (threadIdx.x == 0) {
+        st->mean = mean;
+        st->sd = sqrt(ss / N);
+        st->tsum = tsum;
+        st->sum32 = s32;
+        st->srr32 = ss32 - s32 * s32 / N;
+        st->sd32 = (float)sqrt(st->srr32 / N);
+    }
+}
+
+// one id below the top level scored from the sample-major cache (row stride P)
+template <typename T>
+__device__ __forceinline__ void score_cached_id(const T* cache, int N, int64_t P, const float* tc32, const double* tc64,
+                                                const TargetStats* st, int64_t id, const unsigned char* subvalid,
+                                                float* scores) {
+    if (!subvalid[id]) { scores[id] = -1.f; return; }
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const T v0 = cache[id];
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s = 0; s < N; ++s) {
+        const T v = cache[(size_t)s * P + id] - v0;
+        s1 += v;
+        s2 = fma(v, v, s2);
+        sr = fma(v, tc[s], sr);
+    }
+    scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+}
+
+constexpr int kUnaryMax = 8;
+struct UnaryArgs {
+    int n_ops;
+    int op[kUnaryMax];
+    int64_t base[kUnaryMax];   // first id of each operator's section
+    int64_t Q, P;              // operands: new_{L-1} = [Q, P)
+    int N;
+};
+
+// the top level's unary sections from cached operand rows: a block of kUnaryMax warps takes
+// 32 operands (from U.Q + 32 blk) and every enabled unary operator (warp w = operator w,
+// lane = operand), 32-sample chunks staged in shared memory (xs, r)
+template <typename T>
+__device__ __forceinline__ void unary_block(const UnaryArgs& U, const T* cache, const float* tc32, const double* tc64,
+                                            const TargetStats* st, const unsigned char* subvalid, float* scores,
+                                            int64_t blk, T (*xs)[33], T* r) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t z0 = U.Q + blk * 32;
+    const int64_t z = z0 + lane;
+    const int N = U.N;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const bool active = w < U.n_ops && z < U.P;
+    const int op = w < U.n_ops ? U.op[w] : EXP;
+    const T v0 = active ? op_unary<T>(op, cache[z]) : T(0);
+    T s1 = 0, s2 = 0, sr = 0;
+    for (int s0 = 0; s0 < N; s0 += 32) {
+        __syncthreads();
+        // warp w stages samples w, w+8, ...: 32 consecutive operands each (coalesced)
+        for (int q = w; q < 32; q += kUnaryMax)
+            xs[q][lane] = (z < U.P && s0 + q < N) ? cache[(size_t)(s0 + q) * U.P + z] : T(1);
+        if (w == 0) r[lane] = s0 + lane < N ? tc[s0 + lane] : T(0);
+        __syncthreads();
+        const int ns = min(32, N - s0);
+        if (active)
+            for (int s = 0; s < ns; ++s) {
+                const T v = op_unary<T>(op, xs[s][lane]) - v0;
+                s1 += v;
+                s2 = fma(v, v, s2);
+                sr = fma(v, r[s], sr);
+            }
+    }
+    if (active)
+        scores[U.base[w] + (z - U.Q)] = subvalid[z] ? finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st)) : -1.f;
+}
+
+// FP64 re-score of one id by one warp (lanes over samples), written to entry w of the
+// output arrays: the exact validity rules (every |v| <= 1e12 and finite, not identically
+// zero, std > 1e-6 max|v|), the Pearson score, kProbes standardised values for the
+// duplicate rule, and the standardised vector (zc, when given, row stride N).  Operand
+// values come from V (row stride ldv) when given, else from the primaries Xc.
+__device__ __forceinline__ void rescore_one(const Space* sp, const double* Xc, int N, int ldv, const double* tc,
+                                            const TargetStats* st, int64_t id, int w,
+                                            const unsigned char* subvalid, const double* V, double* score,
+                                            double* mean_out, double* sd_out, int* valid_out, double* probe,
+                                            double* zc) {
+    const int lane = threadIdx.x & 31;
+    Prog p;
+    int level, op; int64_t a, b;
+    const int64_t Pbot = sp->phi[sp->rung - 1];
+    OpRef ref{};
+    bool built = decode(*sp, id, level, op, a, b) && (V ? make_opref(*sp, id, ref) : build_prog(*sp, id, p));
+    if (built && id < Pbot && !subvalid[id]) built = false;                                  // exact, recursive
+    if (built && id >= Pbot && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
+    if (!built) {
+        if (lane == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
+        if (lane < kProbes) probe[(size_t)w * kProbes + lane] = 0.0;
+        return;
+    }
+    double* z = zc ? zc + (size_t)w * N : nullptr;
+    auto value = [&](int i, double& mag) -> double {
+        return V ? opref_val(ref, V, ldv, i, mag) : eval_prog_mag<double>(p, [&](int c) { return Xc[(size_t)c * N + i]; }, mag);
+    };
+    // one pass of sums shifted by the sample-0 value (FP64: relative error ~1e-14, far
+    // inside the 1e-9 tie window of the walk)
+    double mag0;
+    const double v0 = value(0, mag0);
+    double s1 = 0.0, s2 = 0.0, sc = 0.0, mx = 0.0, mo = 0.0;
+    int bad = 0;
+    for (int i = lane; i < N; i += 32) {
+        double mag;
+        const double v = value(i, mag);
+        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
+        const double u = v - v0;
+        s1 += u;
+        s2 += u * u;
+        sc += u * tc[i];
+        mx = fmax(mx, fabs(v));
+        mo = fmax(mo, mag);
+        if (z) z[i] = v;
+    }
+    bad = warp_or(bad);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    sc = warp_sum(sc);
+    mx = warp_max(mx);
+    mo = warp_max(mo);
+    // identically zero: a top-level + or - whose operands cancel (lower ids: in subvalid)
+    const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
+    const bool cancelled = top_addsub && mx <= kCancelRel * mo;
+    const double mean = v0 + s1 / N;
+    const double var = s2 / N - (s1 / N) * (s1 / N);
+    const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
+    const int ok = !bad && !cancelled && sd > kConstRel * mx;
+    const double inv = ok ? 1.0 / sd : 0.0;
+    if (z)
+        for (int i = lane; i < N; i += 32) z[i] = (z[i] - mean) * inv;
+    if (lane < kProbes) {
+        const int i = (int)(((int64_t)lane * N) / kProbes);
+        double mag;
+        const double v = z ? z[i] : (value(i, mag) - mean) * inv;
+        probe[(size_t)w * kProbes + lane] = v;
+    }
+    if (lane == 0) {
+        valid_out[w] = ok;
+        mean_out[w] = mean;
+        sd_out[w] = sd;
+        score[w] = ok ? fabs(sc - (s1 / N) * st->tsum) / ((double)N * sd * st->sd) : -1.0;
+    }
+}
+
+
 // One 32 x 32 tile of operand pairs (i0.., j0..): stage operands chunk by chunk, accumulate
 // the shifted sums of + - * a/b b/a for 4 pairs per thread, write the scores.  Called by
 // every thread of an 8-warp CTA; S is that CTA's shared memory.

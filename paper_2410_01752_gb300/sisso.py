@@ -32,6 +32,10 @@ EXPORTS = [
     "sisso_last_error", "sisso_destroy", "sisso_eval_features", "sisso_score_all",
     "sisso_sis_step", "sisso_l0_search", "sisso_space_sizes", "sisso_space_expr",
     "sisso_l0_search_noalloc", "sisso_gram_tc",
+    "sisso_batch_create", "sisso_batch_create_error", "sisso_batch_set_tune", "sisso_batch_get_tune",
+    "sisso_batch_autotune", "sisso_batch_load", "sisso_batch_run", "sisso_batch_results",
+    "sisso_batch_timing", "sisso_batch_get_stats", "sisso_batch_last_error", "sisso_batch_destroy",
+    "sisso_fit_batch",
 ]
 NOALLOC_MAX_N = 256
 NOALLOC_MAX_BAND = 65536
@@ -62,6 +66,35 @@ class Stats(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Task(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("y", C.c_void_p), ("N", C.c_int), ("d", C.c_int)]
+
+
+class TaskResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_dims", C.c_int),
+                ("ids", (C.c_int64 * MAX_DIM) * MAX_DIM),
+                ("coef", (C.c_double * (MAX_DIM + 1)) * MAX_DIM),
+                ("rmse", C.c_double * MAX_DIM), ("r2", C.c_double * MAX_DIM)]
+
+
+class BatchTune(C.Structure):
+    _fields_ = [("score_units", C.c_int), ("enum_items", C.c_int), ("gram_rows", C.c_int),
+                ("ctas_per_sm", C.c_int), ("window", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("ms_run", C.c_double), ("candidates_scored", C.c_int64), ("subsets_fit", C.c_int64),
+                ("subsets_refit", C.c_int64), ("windows_grown", C.c_int), ("windows_saturated", C.c_int),
+                ("tasks_failed", C.c_int), ("grid", C.c_int), ("stage_ms", C.c_double * 12),
+                ("stage_max_ms", C.c_double * 12), ("stage_count", C.c_int64 * 12)]
+
+    def as_dict(self) -> dict:
+        return {f: (list(getattr(self, f)) if f.startswith("stage_") else getattr(self, f)) for f, _ in self._fields_}
 
 
 _lib = None
@@ -101,8 +134,26 @@ def load() -> C.CDLL:
     L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
                                           C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
+    L.sisso_batch_create.argtypes = [vp, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int, C.POINTER(Opts),
+                                     C.POINTER(vp)]
+    L.sisso_batch_create_error.argtypes = []
+    L.sisso_batch_create_error.restype = C.c_char_p
+    L.sisso_batch_set_tune.argtypes = [vp, C.POINTER(BatchTune)]
+    L.sisso_batch_get_tune.argtypes = [vp, C.POINTER(BatchTune)]
+    L.sisso_batch_autotune.argtypes = [vp, C.c_int, C.c_char_p, C.POINTER(BatchTune)]
+    L.sisso_batch_load.argtypes = [vp, vp, C.c_int]
+    L.sisso_batch_run.argtypes = [vp, C.c_int]
+    L.sisso_batch_results.argtypes = [vp, vp, C.c_int]
+    L.sisso_batch_timing.argtypes = [vp, dp, dp, C.c_int]
+    L.sisso_batch_get_stats.argtypes = [vp, C.POINTER(BatchStats)]
+    L.sisso_batch_last_error.argtypes = [vp]
+    L.sisso_batch_last_error.restype = C.c_char_p
+    L.sisso_batch_destroy.argtypes = [vp]
+    L.sisso_batch_destroy.restype = None
+    L.sisso_fit_batch.argtypes = [vp, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), vp]
     for name in EXPORTS:
-        if name not in ("sisso_default_opts", "sisso_last_error", "sisso_destroy"):
+        if name not in ("sisso_default_opts", "sisso_last_error", "sisso_destroy", "sisso_batch_create_error",
+                        "sisso_batch_last_error", "sisso_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -303,3 +354,131 @@ class Sisso:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _task_array(problems):
+    """ctypes array of sisso_task over host float64 copies (kept alive by the caller)."""
+    keep = []
+    arr = (Task * len(problems))()
+    for i, (X, y) in enumerate(problems):
+        Xa = np.ascontiguousarray(X, dtype=np.float64)
+        ya = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
+        keep += [Xa, ya]
+        arr[i].X, arr[i].y = Xa.ctypes.data, ya.ctypes.data
+        arr[i].N, arr[i].d = int(Xa.shape[0]), int(Xa.shape[1])
+    return arr, keep
+
+
+def _results(res, n: int) -> list:
+    out = []
+    for i in range(n):
+        r = res[i]
+        dims = []
+        for t in range(1, r.n_dims + 1):
+            dims.append(Descriptor([int(r.ids[t - 1][j]) for j in range(t)],
+                                   [float(r.coef[t - 1][j]) for j in range(t + 1)],
+                                   float(r.rmse[t - 1]), float(r.r2[t - 1])))
+        out.append((int(r.status), dims))
+    return out
+
+
+class Batch:
+    """Many independent problems in one persistent launch (CUDA graph): ``Batch(problems, ...).run()``.
+
+    problems: list of (X, y) host arrays; every task shares op_set, rung, sis_size, max_dim.
+    """
+
+    def __init__(self, problems, op_set: int, rung: int, sis_size: int, max_dim: int,
+                 grammar: int = GRAMMAR_EQ2, max_band: int = 0, stream=None, device: int = 0):
+        L = load()
+        self._b = C.c_void_p()
+        self.n = len(problems)
+        arr, keep = _task_array(problems)
+        o = Opts()
+        L.sisso_default_opts(C.byref(o))
+        o.precision, o.grammar, o.max_band, o.device = PREC_FP32, grammar, max_band, device
+        if stream is not None:
+            o.cuda_stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
+        st = L.sisso_batch_create(arr, self.n, op_set, rung, sis_size, max_dim, C.byref(o), C.byref(self._b))
+        del keep
+        if st != 0:
+            raise SissoError(st, "sisso_batch_create: " + L.sisso_batch_create_error().decode())
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise SissoError(st, f"{what}: {load().sisso_batch_last_error(self._b).decode()}")
+
+    def load(self, problems):
+        arr, keep = _task_array(problems)
+        self._check(load().sisso_batch_load(self._b, arr, len(problems)), "batch_load")
+        del keep
+
+    def tune(self, **kw) -> dict:
+        t = BatchTune(**kw)
+        self._check(load().sisso_batch_set_tune(self._b, C.byref(t)), "batch_set_tune")
+        return self.get_tune()
+
+    def get_tune(self) -> dict:
+        t = BatchTune()
+        self._check(load().sisso_batch_get_tune(self._b, C.byref(t)), "batch_get_tune")
+        return t.as_dict()
+
+    def autotune(self, reps: int = 2, cache_path: str | None = None) -> dict:
+        t = BatchTune()
+        self._check(load().sisso_batch_autotune(self._b, reps, cache_path.encode() if cache_path else None,
+                                                C.byref(t)), "batch_autotune")
+        return t.as_dict()
+
+    def run(self, copies: bool = True):
+        self._check(load().sisso_batch_run(self._b, 1 if copies else 0), "batch_run")
+
+    def results(self) -> list:
+        """Per task: (status, [Descriptor for t = 1..n_dims])."""
+        res = (TaskResult * self.n)()
+        self._check(load().sisso_batch_results(self._b, res, self.n), "batch_results")
+        return _results(res, self.n)
+
+    def timing(self) -> tuple[np.ndarray, np.ndarray]:
+        """Per-task start and end (ms from the launch's first CTA)."""
+        a = np.zeros(self.n, dtype=np.float64)
+        e = np.zeros(self.n, dtype=np.float64)
+        self._check(load().sisso_batch_timing(self._b, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                              e.ctypes.data_as(C.POINTER(C.c_double)), self.n), "batch_timing")
+        return a, e
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        self._check(load().sisso_batch_get_stats(self._b, C.byref(s)), "batch_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self._b:
+            load().sisso_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fit_batch(problems, op_set: int, rung: int, sis_size: int, max_dim: int, grammar: int = GRAMMAR_EQ2) -> list:
+    """One-shot sisso_fit_batch: per task (status, [Descriptor ...])."""
+    L = load()
+    arr, keep = _task_array(problems)
+    o = Opts()
+    L.sisso_default_opts(C.byref(o))
+    o.precision, o.grammar = PREC_FP32, grammar
+    res = (TaskResult * len(problems))()
+    st = L.sisso_fit_batch(arr, len(problems), op_set, rung, sis_size, max_dim, C.byref(o), res)
+    del keep
+    if st != 0:
+        raise SissoError(st, "sisso_fit_batch: " + L.sisso_batch_create_error().decode())
+    return _results(res, len(problems))

@@ -108,3 +108,48 @@ def test_null_and_state_errors(lib):
     assert L.sisso_get_n_dims(None, C.byref(n)) == -1
     assert L.sisso_space_sizes(3, 0, 2, 0, None) == -1
     L.sisso_destroy(None)
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("nan_x", "non-finite X"), ("nan_y", "non-finite y"), ("const_y", "constant y"),
+    ("small_n", "N >= max_dim + 1"), ("k_dim", "max_dim * sis_size"), ("prec", "FP32"),
+])
+def test_batch_argument_errors(lib, case, msg):
+    """The batched form validates every task on the host before touching a GPU."""
+    rng = np.random.default_rng(0)
+    probs = [(rng.uniform(1, 2, size=(30, 3)), rng.normal(size=30)) for _ in range(3)]
+    k, D, prec = 10, 3, lib.PREC_FP32
+    if case == "nan_x":
+        probs[1][0][4, 2] = np.nan
+    elif case == "nan_y":
+        probs[2][1][7] = np.inf
+    elif case == "const_y":
+        probs[1] = (probs[1][0], np.full(30, 2.5))
+    elif case == "small_n":
+        probs[2] = (probs[2][0][:3], probs[2][1][:3])
+    elif case == "k_dim":
+        k = 200
+    L = lib.load()
+    arr, keep = lib._task_array(probs)
+    o = lib.Opts()
+    L.sisso_default_opts(C.byref(o))
+    if case == "prec":
+        o.precision = lib.PREC_FP64
+    b = C.c_void_p()
+    st = L.sisso_batch_create(arr, len(probs), lib.OP_ADD | lib.OP_MUL, 2, k, D, C.byref(o), C.byref(b))
+    assert st == -1
+    assert not b.value
+    err = L.sisso_batch_create_error().decode()
+    assert msg in err
+    if case in ("nan_x", "const_y"):
+        assert err.startswith("task 1:")
+
+
+def test_batch_null_arguments(lib):
+    L = lib.load()
+    assert L.sisso_batch_run(None, 1) == -1
+    assert L.sisso_batch_results(None, None, 0) == -1
+    assert L.sisso_batch_set_tune(None, None) == -1
+    L.sisso_batch_destroy(None)
+    b = C.c_void_p()
+    assert L.sisso_batch_create(None, 0, 1, 2, 5, 2, None, C.byref(b)) == -1
