@@ -263,13 +263,16 @@ typedef struct {
     int windows_saturated;      /* tasks whose window hit its cap without proof */
     int tasks_failed;           /* tasks with status != SISSO_OK */
     int grid;                   /* CTAs launched */
+    int64_t walk_visits;        /* screening walks: candidates visited, all tasks and steps */
+    int64_t walk_checks;        /* ... full duplicate comparisons */
     /* device-clock profile of the last run, per stage: 0 unused, 1 start, 2 level, 3 score,
        4 gram, 5 bound, 6 band, 7 validity flattening, 8 select, 9 refit, 10 waiting for
-       work, 11 unused.  stage_ms sums the CTAs' time, stage_max_ms is the longest single
+       work, 11 unused, and the parts of select: 12 radix select, 13 FP64 re-score, 14 sort,
+       15 walk.  stage_ms sums the CTAs' time, stage_max_ms is the longest single
        occurrence, stage_count the occurrences. */
-    double stage_ms[12];
-    double stage_max_ms[12];
-    int64_t stage_count[12];
+    double stage_ms[16];
+    double stage_max_ms[16];
+    int64_t stage_count[16];
 } sisso_batch_stats;
 
 /* Plan every task (feature space, work units, memory), copy the inputs to pinned host

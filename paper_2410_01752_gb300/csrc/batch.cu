@@ -45,12 +45,14 @@ constexpr int kWinMax = 4096;                    // screening window cap (sorted
 constexpr int kInitIds = 32;                     // ids per LEVEL unit
 constexpr int kLowIds = kBT;                     // lower-level ids per SCORE unit
 constexpr int kMaxSub = 1024;                    // subspace size cap (max_dim * k)
+constexpr int kZRaw = 512;                       // window entries whose FP64 values are kept
 constexpr unsigned long long kIdleNs = 10000000000ull;  // 10 s with no progress anywhere: give up
 constexpr unsigned long long kExit = ~0ull;
 
 enum : int { WK_NONE = 0, WK_START, WK_LEVEL, WK_SCORE, WK_GRAM, WK_BOUND, WK_BAND };
 // stage ids of the profile counters (parallel items by kind; serial stages after them)
-enum : int { PS_FLAT = 7, PS_SELECT = 8, PS_REFIT = 9, PS_IDLE = 10, PS_PUSH = 11 };
+enum : int { PS_FLAT = 7, PS_SELECT = 8, PS_REFIT = 9, PS_IDLE = 10, PS_PUSH = 11,
+             PS_SEL_RADIX = 12, PS_SEL_RESCORE = 13, PS_SEL_SORT = 14, PS_SEL_WALK = 15 };
 
 __device__ __forceinline__ void prof_add(const unsigned long long* prof_c, int s, unsigned long long dt) {
     unsigned long long* prof = const_cast<unsigned long long*>(prof_c);
@@ -119,6 +121,7 @@ struct BTask {
     unsigned char* valid;       // validity of ids [0, P), one array
     double* yc;                 // y - mean(y)
     double* Z;                  // standardised subspace members (kMaxSub rows, stride ldv)
+    double* zraw;               // FP64 values of the first kZRaw window entries (stride N)
     BDim dim[kMaxDim + 1];      // index t = 1..max_dim
 };
 
@@ -129,6 +132,8 @@ struct BState {
     int n_dims;
     int saturated;              // a screening window could not grow to exactness
     int grown;                  // screening windows grown
+    int visits;                 // walk: candidates visited
+    int checks;                 // walk: full duplicate comparisons
     int n_S[kMaxDim + 1];       // subspace size after step t
     unsigned band_count[kMaxDim + 1];
     unsigned long long ub_key[kMaxDim + 1];
@@ -159,15 +164,18 @@ struct BatchArgs {
 
 // shared memory of one CTA: one layout per stage
 struct SelectSmem {
-    unsigned hist[4096];
+    union {
+        unsigned hist[8 * 1024];            // radix select: one histogram per warp
+        struct {
+            double sk[kWinMax];             // sorted window: FP64 score (or -1/-2), id, entry
+            int64_t sid[kWinMax];
+            int ssrc[kWinMax];
+        } srt;
+    } u;
     unsigned part[kBT];
-    double sk[kWinMax];
-    int64_t sid[kWinMax];
-    int ssrc[kWinMax];
     unsigned char removed[kWinMax];
     int64_t S_sorted[kMaxSub];
-};
-struct UnarySmem {
+};struct UnarySmem {
     float xs[32][33];
     float r[32];
 };
@@ -429,7 +437,6 @@ __device__ __forceinline__ void run_score(const BatchArgs& B, int task, int t, l
 // ---------------------------------------------------------------------------------
 // SELECT: window, FP64 re-score, sort, walk (one CTA)
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned skey(float s) { return s > 0.f ? __float_as_uint(s) : 0u; }
 
 // the bin holding the need-th largest key of a 4096- (or 256-) bin histogram: returns
 // the bin and the rank still needed inside it; bin -1 when fewer keys exist
@@ -438,7 +445,7 @@ __device__ void hist_find(SelectSmem& M, Ctl& C, int nb, unsigned need) {
     const int tid = threadIdx.x;
     unsigned p = 0;
     if (tid * per < nb)
-        for (int b = 0; b < per; ++b) p += M.hist[tid * per + b];
+        for (int b = 0; b < per; ++b) p += M.u.hist[tid * per + b];
     M.part[tid] = p;
     __syncthreads();
     if (tid == 0) {
@@ -450,7 +457,7 @@ __device__ void hist_find(SelectSmem& M, Ctl& C, int nb, unsigned need) {
             const unsigned c = M.part[g];
             if (cum + c >= need) {
                 for (int b = g * per + per - 1; b >= g * per; --b) {
-                    const unsigned cb = M.hist[b];
+                    const unsigned cb = M.u.hist[b];
                     if (cum + cb >= need) { bin = b; rest = need - cum; break; }
                     cum += cb;
                 }
@@ -465,26 +472,57 @@ __device__ void hist_find(SelectSmem& M, Ctl& C, int nb, unsigned need) {
 }
 
 // radix select over the step's scores: C.ukey = key of the M-th best; C.flag = 1 when fewer
-// than M keys are nonzero (then every nonzero key is taken)
+// than M keys are nonzero (then every nonzero key is taken).  Keys are the float bits of
+// positive scores, capped below 2.0, so bits 31-30 are zero: three passes of 10 bits, with
+// per-warp histograms and vector loads (the scan is one CTA's, so it must keep many loads
+// in flight).
+__device__ __forceinline__ unsigned rkey(float s) {
+    const unsigned k = s > 0.f ? __float_as_uint(s) : 0u;
+    return k < 0x3FFFFFFFu ? k : 0x3FFFFFFFu;
+}
+
+template <typename F>
+__device__ __forceinline__ void scan_keys(const float* scores, int64_t n, F f) {
+    const int64_t n4 = n >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(scores);
+    int64_t v = threadIdx.x;
+    for (; v + kBT < n4; v += 2 * kBT) {
+        const float4 a = __ldcg(s4 + v), b = __ldcg(s4 + v + kBT);
+        f(rkey(a.x)); f(rkey(a.y)); f(rkey(a.z)); f(rkey(a.w));
+        f(rkey(b.x)); f(rkey(b.y)); f(rkey(b.z)); f(rkey(b.w));
+    }
+    for (; v < n4; v += kBT) {
+        const float4 a = __ldcg(s4 + v);
+        f(rkey(a.x)); f(rkey(a.y)); f(rkey(a.z)); f(rkey(a.w));
+    }
+    for (int64_t i = (n4 << 2) + threadIdx.x; i < n; i += kBT) f(rkey(__ldcg(scores + i)));
+}
+
 __device__ void radix_select(SelectSmem& M, Ctl& C, const float* scores, int64_t n, unsigned Mw) {
     unsigned prefix = 0, need = Mw;
     int all = 0;
+    const int w = threadIdx.x >> 5;
+    unsigned* hw = M.u.hist + w * 1024;               // this warp's histogram
     for (int pass = 0; pass < 3 && !all; ++pass) {
-        const int nb = pass == 2 ? 256 : 4096;
-        for (int i = threadIdx.x; i < 4096; i += kBT) M.hist[i] = 0;
+        for (int i = threadIdx.x; i < 8 * 1024; i += kBT) M.u.hist[i] = 0;
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < n; i += kBT) {
-            const unsigned k = skey(__ldcg(scores + i));
-            if (k == 0u) continue;
-            if (pass == 0) atomicAdd(&M.hist[k >> 20], 1u);
-            else if (pass == 1) { if ((k >> 20) == prefix) atomicAdd(&M.hist[(k >> 8) & 0xFFFu], 1u); }
-            else { if ((k >> 8) == prefix) atomicAdd(&M.hist[k & 0xFFu], 1u); }
+        const int sh = 20 - 10 * pass;
+        const unsigned pre = prefix;
+        scan_keys(scores, n, [&](unsigned k) {
+            if (k != 0u && (pass == 0 || (k >> (sh + 10)) == pre)) atomicAdd(&hw[(k >> sh) & 0x3FFu], 1u);
+        });
+        __syncthreads();
+        for (int b = threadIdx.x; b < 1024; b += kBT) {
+            unsigned t = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) t += M.u.hist[q * 1024 + b];
+            M.u.hist[b] = t;
         }
         __syncthreads();
-        hist_find(M, C, nb, need);
+        hist_find(M, C, 1024, need);
         const int bin = C.ival[0];
         if (bin < 0) { all = 1; break; }
-        prefix = pass == 0 ? (unsigned)bin : pass == 1 ? ((prefix << 12) | (unsigned)bin) : ((prefix << 8) | (unsigned)bin);
+        prefix = (prefix << 10) | (unsigned)bin;
         need = (unsigned)C.ival[1];
         __syncthreads();
     }
@@ -504,12 +542,12 @@ __device__ void block_sort(SelectSmem& M, int n_pad) {
                 const int l = i ^ j;
                 if (l <= i) continue;
                 const bool up = (i & kk) == 0;
-                const double si = M.sk[i], sl = M.sk[l];
-                const int64_t ii = M.sid[i], il = M.sid[l];
+                const double si = M.u.srt.sk[i], sl = M.u.srt.sk[l];
+                const int64_t ii = M.u.srt.sid[i], il = M.u.srt.sid[l];
                 if (up ? before(sl, il, si, ii) : before(si, ii, sl, il)) {
-                    M.sk[i] = sl; M.sk[l] = si;
-                    M.sid[i] = il; M.sid[l] = ii;
-                    const int x = M.ssrc[i]; M.ssrc[i] = M.ssrc[l]; M.ssrc[l] = x;
+                    M.u.srt.sk[i] = sl; M.u.srt.sk[l] = si;
+                    M.u.srt.sid[i] = il; M.u.srt.sid[l] = ii;
+                    const int x = M.u.srt.ssrc[i]; M.u.srt.ssrc[i] = M.u.srt.ssrc[l]; M.u.srt.ssrc[l] = x;
                 }
             }
             __syncthreads();
@@ -532,6 +570,22 @@ __device__ void standardise_into(const BTask& T, Ctl& C, const OpRef& ref, doubl
     const double sdv = sqrt(block_sum(ss, C.red) / N);
     const double inv = sdv > 0.0 ? 1.0 / sdv : 0.0;
     for (int i = threadIdx.x; i < N; i += kBT) z[i] = (z[i] - m) * inv;
+    mean = m;
+    sd = sdv;
+    __syncthreads();
+}
+
+// the same from a row of values already computed (two passes, as the per-problem path)
+__device__ void standardise_from(const BTask& T, Ctl& C, const double* raw, double* z, double& mean, double& sd) {
+    const int N = T.N;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += kBT) s += raw[i];
+    const double m = block_sum(s, C.red) / N;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < N; i += kBT) { const double u = raw[i] - m; ss += u * u; }
+    const double sdv = sqrt(block_sum(ss, C.red) / N);
+    const double inv = sdv > 0.0 ? 1.0 / sdv : 0.0;
+    for (int i = threadIdx.x; i < N; i += kBT) z[i] = (raw[i] - m) * inv;
     mean = m;
     sd = sdv;
     __syncthreads();
@@ -565,6 +619,7 @@ __device__ __noinline__ int run_select(const BatchArgs& B, Ctl& C, int task, int
     if (Mw > kWinMax) Mw = kWinMax;
     int n_acc = 0;
     while (true) {
+        unsigned long long ts0 = gtimer();
         radix_select(M, C, D.scores, T.n_feat, (unsigned)Mw);
         const unsigned thr = (unsigned)C.ukey;
         const int all = C.flag;
@@ -574,7 +629,7 @@ __device__ __noinline__ int run_select(const BatchArgs& B, Ctl& C, int task, int
         if (tid == 0) C.n = 0;
         __syncthreads();
         for (int64_t i = tid; i < T.n_feat; i += kBT) {
-            const unsigned kk = skey(__ldcg(D.scores + i));
+            const unsigned kk = rkey(__ldcg(D.scores + i));
             if (kk != 0u && kk >= thr) {
                 const int slot = atomicAdd(&C.n, 1);
                 if (slot < kWinMax) D.w_ids[slot] = i;
@@ -583,28 +638,34 @@ __device__ __noinline__ int run_select(const BatchArgs& B, Ctl& C, int task, int
         __syncthreads();
         const int ns = C.n;
         if (ns > kWinMax) return SISSO_ERR_CAPACITY;    // tied scores overflow the window
+        unsigned long long ts1 = gtimer();
+        if (tid == 0) prof_add(B.prof, PS_SEL_RADIX, ts1 - ts0);
         // FP64 re-score, one warp per entry
         for (int e = w; e < ns; e += kBT / 32)
             rescore_one(T.sp, nullptr, N, T.ldv, D.tc64, D.ts, D.w_ids[e], e, T.valid, T.V, D.w_score, D.w_mean,
-                        D.w_sd, D.w_valid, D.w_probe, nullptr);
+                        D.w_sd, D.w_valid, D.w_probe, e < kZRaw ? T.zraw : nullptr, true);
         __syncthreads();
+        ts0 = gtimer();
+        if (tid == 0) prof_add(B.prof, PS_SEL_RESCORE, ts0 - ts1);
         int n_pad = 1;
         while (n_pad < (ns > 0 ? ns : 1)) n_pad <<= 1;
         for (int i = tid; i < n_pad; i += kBT) {
-            if (i >= ns) { M.sk[i] = -2.0; M.sid[i] = INT64_MAX; M.ssrc[i] = -1; }
+            if (i >= ns) { M.u.srt.sk[i] = -2.0; M.u.srt.sid[i] = INT64_MAX; M.u.srt.ssrc[i] = -1; }
             else {
                 const int64_t id = D.w_ids[i];
                 int lo = 0, hi = n_prev;
                 while (lo < hi) { const int m = (lo + hi) >> 1; if (M.S_sorted[m] < id) lo = m + 1; else hi = m; }
                 const bool inS = lo < n_prev && M.S_sorted[lo] == id;
-                M.sk[i] = (D.w_valid[i] && !inS) ? D.w_score[i] : -1.0;
-                M.sid[i] = id;
-                M.ssrc[i] = i;
+                M.u.srt.sk[i] = (D.w_valid[i] && !inS) ? D.w_score[i] : -1.0;
+                M.u.srt.sid[i] = id;
+                M.u.srt.ssrc[i] = i;
             }
             M.removed[i] = 0;
         }
         __syncthreads();
         block_sort(M, n_pad);
+        ts1 = gtimer();
+        if (tid == 0) prof_add(B.prof, PS_SEL_SORT, ts1 - ts0);
         // the walk
         if (tid == 0) { C.n_acc = 0; C.done = 0; C.visited = 0; C.dval[0] = -1.0; C.ival[2] = 0; }
         __syncthreads();
@@ -612,17 +673,17 @@ __device__ __noinline__ int run_select(const BatchArgs& B, Ctl& C, int task, int
         while (true) {
             if (tid == 0) {
                 while (p < n_pad && M.removed[p]) ++p;
-                if (C.n_acc >= k || p >= n_pad || M.sk[p] < 0.0) {
+                if (C.n_acc >= k || p >= n_pad || M.u.srt.sk[p] < 0.0) {
                     C.done = 1;
                 } else {
                     // among the entries within kScoreTie of the maximum, the lowest id
-                    const double mxs = M.sk[p];
+                    const double mxs = M.u.srt.sk[p];
                     int best = p;
-                    for (int e = p + 1; e < n_pad && M.sk[e] >= 0.0 && M.sk[e] >= mxs - kScoreTie; ++e)
-                        if (!M.removed[e] && M.sid[e] < M.sid[best]) best = e;
+                    for (int e = p + 1; e < n_pad && M.u.srt.sk[e] >= 0.0 && M.u.srt.sk[e] >= mxs - kScoreTie; ++e)
+                        if (!M.removed[e] && M.u.srt.sid[e] < M.u.srt.sid[best]) best = e;
                     M.removed[best] = 1;
                     C.cur = best;
-                    C.dval[0] = M.sk[best];
+                    C.dval[0] = M.u.srt.sk[best];
                     ++C.visited;
                 }
                 C.n_match = 0;
@@ -630,46 +691,60 @@ __device__ __noinline__ int run_select(const BatchArgs& B, Ctl& C, int task, int
             __syncthreads();
             if (C.done) break;
             const int row = n_prev + C.n_acc;         // Z row the candidate takes if accepted
-            OpRef ref{};
-            make_opref(*T.sp, M.sid[C.cur], ref);
-            double* z = T.Z + (size_t)row * T.ldv;
-            double zm, zs;
-            standardise_into(T, C, ref, z, zm, zs);
-            // probe test (a necessary condition) against every S member and every id
-            // accepted in this step
+            const int src = M.u.srt.ssrc[C.cur];
+            // probe test (a necessary condition) against every S member and every id accepted
+            // in this step, with the candidate's probes from the re-score
+            const double* pc = D.w_probe + (size_t)src * kProbes;
             for (int r = tid; r < row; r += kBT) {
                 const double* zr = T.Z + (size_t)r * T.ldv;
                 bool same = true, flip = true;
 #pragma unroll
                 for (int q = 0; q < kProbes; ++q) {
-                    const int i = (int)(((int64_t)q * N) / kProbes);
-                    same = same && fabs(z[i] - zr[i]) <= kDupTol;
-                    flip = flip && fabs(z[i] + zr[i]) <= kDupTol;
+                    const double zq = zr[(int)(((int64_t)q * N) / kProbes)];
+                    same = same && fabs(pc[q] - zq) <= kDupTol;
+                    flip = flip && fabs(pc[q] + zq) <= kDupTol;
                 }
                 if (same || flip) C.match[atomicAdd(&C.n_match, 1)] = r;
             }
             __syncthreads();
             const int nm = C.n_match;
+            const double* raw = src < kZRaw ? T.zraw + (size_t)src * N : nullptr;
+            OpRef ref{};
+            if (!raw) make_opref(*T.sp, M.u.srt.sid[C.cur], ref);
             bool dup = false;
-            for (int q = 0; q < nm && !dup; ++q) {
-                const double* zr = T.Z + (size_t)C.match[q] * T.ldv;
-                double e1 = 0.0, e2 = 0.0;
-                for (int i = tid; i < N; i += kBT) {
-                    e1 = fmax(e1, fabs(z[i] - zr[i]));
-                    e2 = fmax(e2, fabs(z[i] + zr[i]));
+            if (tid == 0) { St.visits += 1; St.checks += nm; }
+            if (nm > 0) {
+                // full comparison on every sample, the candidate standardised by its re-score moments
+                const double mc = D.w_mean[src], dc = D.w_sd[src];
+                for (int q = 0; q < nm && !dup; ++q) {
+                    const double* zr = T.Z + (size_t)C.match[q] * T.ldv;
+                    double e1 = 0.0, e2 = 0.0;
+                    for (int i = tid; i < N; i += kBT) {
+                        double mg;
+                        const double zc = ((raw ? raw[i] : opref_val(ref, T.V, T.ldv, i, mg)) - mc) / dc;
+                        e1 = fmax(e1, fabs(zc - zr[i]));
+                        e2 = fmax(e2, fabs(zc + zr[i]));
+                    }
+                    e1 = block_max(e1, C.red);
+                    e2 = block_max(e2, C.red);
+                    dup = e1 <= kDupTol || e2 <= kDupTol;
                 }
-                e1 = block_max(e1, C.red);
-                e2 = block_max(e2, C.red);
-                dup = e1 <= kDupTol || e2 <= kDupTol;
+            }
+            double zm = 0.0, zs = 0.0;
+            if (!dup) {
+                double* z = T.Z + (size_t)row * T.ldv;
+                if (raw) standardise_from(T, C, raw, z, zm, zs);
+                else standardise_into(T, C, ref, z, zm, zs);
             }
             if (tid == 0 && !dup) {
-                D.gid[row] = M.sid[C.cur];
+                D.gid[row] = M.u.srt.sid[C.cur];
                 D.zmean[row] = zm;
                 D.zsd[row] = zs;
                 ++C.n_acc;
             }
             __syncthreads();
         }
+        if (tid == 0) prof_add(B.prof, PS_SEL_WALK, gtimer() - ts1);
         n_acc = C.n_acc;
         const double last = C.dval[0];
         // exact iff every candidate outside the window scores below the last visited one by
@@ -1176,6 +1251,12 @@ long long queue_items(const TaskPlan& T, int rung, int k, int max_dim, const sis
 
 sisso_status capture(sisso_batch* b, bool copies, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
+    // a persistent grid: never more CTAs than can be resident at once
+    int resident = 0;
+    if (b->tune.ctas_per_sm == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch<1>, kBT, kBatchSmem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch<2>, kBT, kBatchSmem);
+    const int grid = b->sms * std::max(1, std::min(resident, b->tune.ctas_per_sm));
+
     sisso_status st = bcuda(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "capture");
     if (st) return st;
     if (copies) cudaMemcpyAsync(b->in_dev, b->in_host, sizeof(double) * b->in_count, cudaMemcpyHostToDevice, b->stream);
@@ -1191,7 +1272,6 @@ sisso_status capture(sisso_batch* b, bool copies, cudaGraphExec_t* out) {
     A.k = b->k; A.max_dim = b->max_dim;
     A.score_units = b->tune.score_units; A.enum_items = b->tune.enum_items; A.gram_rows = b->tune.gram_rows;
     A.win0 = b->tune.window; A.band_cap = b->band_cap;
-    const int grid = b->sms * b->tune.ctas_per_sm;
     if (b->tune.ctas_per_sm == 1) k_batch<1><<<grid, kBT, kBatchSmem, b->stream>>>(A);
     else k_batch<2><<<grid, kBT, kBatchSmem, b->stream>>>(A);
     cudaMemcpyAsync(b->ctr_host, b->ctr, sizeof(int) * 8, cudaMemcpyDeviceToHost, b->stream);
@@ -1313,7 +1393,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
     size_t total = 0;
     auto region = [&](size_t bytes) { const size_t at = total; total += align256(bytes); return at; };
     struct Off {
-        size_t V, cache, vlvl[kMaxRung], valid, yc, Z;
+        size_t V, cache, vlvl[kMaxRung], valid, yc, Z, zraw;
         size_t scores[kMaxDim + 1], tc64[kMaxDim + 1], tc32[kMaxDim + 1], ts[kMaxDim + 1], w_ids[kMaxDim + 1],
             w_score[kMaxDim + 1], w_mean[kMaxDim + 1], w_sd[kMaxDim + 1], w_valid[kMaxDim + 1], w_probe[kMaxDim + 1],
             gid[kMaxDim + 1], zmean[kMaxDim + 1], zsd[kMaxDim + 1], G64[kMaxDim + 1], b64[kMaxDim + 1],
@@ -1334,6 +1414,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         f.valid = region((size_t)P.P);
         f.yc = region(sizeof(double) * N);
         f.Z = region(sizeof(double) * ldv * ncap);
+        f.zraw = region(sizeof(double) * (size_t)N * kZRaw);
         for (int t = 1; t <= max_dim; ++t) {
             const size_t nt = (size_t)t * sis_size;
             f.scores[t] = region(sizeof(float) * P.n_feat);
@@ -1423,6 +1504,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         T.valid = reinterpret_cast<unsigned char*>(A + f.valid);
         T.yc = reinterpret_cast<double*>(A + f.yc);
         T.Z = reinterpret_cast<double*>(A + f.Z);
+        T.zraw = reinterpret_cast<double*>(A + f.zraw);
         for (int t = 1; t <= max_dim; ++t) {
             BDim& D = T.dim[t];
             D.scores = reinterpret_cast<float*>(A + f.scores[t]);
@@ -1567,7 +1649,7 @@ sisso_status sisso_batch_get_stats(sisso_batch* b, sisso_batch_stats* out) {
     if (st) return st;
     sisso_batch_stats s = b->stats;
     s.candidates_scored = 0; s.subsets_fit = 0; s.subsets_refit = 0;
-    s.windows_grown = 0; s.windows_saturated = 0; s.tasks_failed = 0;
+    s.windows_grown = 0; s.windows_saturated = 0; s.tasks_failed = 0; s.walk_visits = 0; s.walk_checks = 0;
     for (int i = 0; i < b->n_tasks; ++i) {
         const BState& x = b->state_host[i];
         const int nd = b->res_host[i].n_dims;
@@ -1577,10 +1659,12 @@ sisso_status sisso_batch_get_stats(sisso_batch* b, sisso_batch_stats* out) {
             s.subsets_refit += x.band_count[t];
         }
         s.windows_grown += x.grown;
+        s.walk_visits += x.visits;
+        s.walk_checks += x.checks;
         s.windows_saturated += x.saturated;
         s.tasks_failed += b->res_host[i].status != SISSO_OK;
     }
-    for (int q = 0; q < 12; ++q) {
+    for (int q = 0; q < 16; ++q) {
         s.stage_ms[q] = (double)b->prof_host[q] * 1e-6;
         s.stage_count[q] = (int64_t)b->prof_host[16 + q];
         s.stage_max_ms[q] = (double)b->prof_host[32 + q] * 1e-6;

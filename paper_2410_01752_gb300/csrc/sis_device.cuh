@@ -295,13 +295,14 @@ __device__ __forceinline__ void unary_block(const UnaryArgs& U, const T* cache, 
 // FP64 re-score of one id by one warp (lanes over samples), written to entry w of the
 // output arrays: the exact validity rules (every |v| <= 1e12 and finite, not identically
 // zero, std > 1e-6 max|v|), the Pearson score, kProbes standardised values for the
-// duplicate rule, and the standardised vector (zc, when given, row stride N).  Operand
+// duplicate rule, and the standardised vector (zc, when given, row stride N; the raw
+// values instead with zc_raw).  Operand
 // values come from V (row stride ldv) when given, else from the primaries Xc.
 __device__ __forceinline__ void rescore_one(const Space* sp, const double* Xc, int N, int ldv, const double* tc,
                                             const TargetStats* st, int64_t id, int w,
                                             const unsigned char* subvalid, const double* V, double* score,
                                             double* mean_out, double* sd_out, int* valid_out, double* probe,
-                                            double* zc) {
+                                            double* zc, bool zc_raw = false) {
     const int lane = threadIdx.x & 31;
     Prog p;
     int level, op; int64_t a, b;
@@ -351,12 +352,12 @@ __device__ __forceinline__ void rescore_one(const Space* sp, const double* Xc, i
     const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
     const int ok = !bad && !cancelled && sd > kConstRel * mx;
     const double inv = ok ? 1.0 / sd : 0.0;
-    if (z)
+    if (z && !zc_raw)
         for (int i = lane; i < N; i += 32) z[i] = (z[i] - mean) * inv;
     if (lane < kProbes) {
         const int i = (int)(((int64_t)lane * N) / kProbes);
         double mag;
-        const double v = z ? z[i] : (value(i, mag) - mean) * inv;
+        const double v = z ? (zc_raw ? (z[i] - mean) * inv : z[i]) : (value(i, mag) - mean) * inv;
         probe[(size_t)w * kProbes + lane] = v;
     }
     if (lane == 0) {

@@ -90,8 +90,9 @@ class BatchTune(C.Structure):
 class BatchStats(C.Structure):
     _fields_ = [("ms_run", C.c_double), ("candidates_scored", C.c_int64), ("subsets_fit", C.c_int64),
                 ("subsets_refit", C.c_int64), ("windows_grown", C.c_int), ("windows_saturated", C.c_int),
-                ("tasks_failed", C.c_int), ("grid", C.c_int), ("stage_ms", C.c_double * 12),
-                ("stage_max_ms", C.c_double * 12), ("stage_count", C.c_int64 * 12)]
+                ("tasks_failed", C.c_int), ("grid", C.c_int), ("walk_visits", C.c_int64),
+                ("walk_checks", C.c_int64), ("stage_ms", C.c_double * 16),
+                ("stage_max_ms", C.c_double * 16), ("stage_count", C.c_int64 * 16)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f.startswith("stage_") else getattr(self, f)) for f, _ in self._fields_}
