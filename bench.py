@@ -41,8 +41,11 @@ def parse():
                     help="CPU work for the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3],
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5],
                     help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples")
+    ap.add_argument("--tasks", type=int, default=512, help="batched workload: number of tasks")
+    ap.add_argument("--tune-cache", default=None, help="batched workload: autotuner cache file")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch shape")
     ap.add_argument("--d", type=int, default=10, help="primary features (smaller cases for profiling)")
     ap.add_argument("--N", type=int, default=1000, help="samples (smaller cases for profiling)")
     return ap.parse_args()
@@ -139,11 +142,33 @@ def captured_traffic():
         return None
     vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha256")))
     h = hashlib.sha256()
-    for f in ("sis.cu", "common.cuh"):
+    for f in ("sis.cu", "sis_device.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2410_01752_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     sha = next((v.strip() for k, v in vals.items() if k.startswith("source_sha256")), "")
     if sha != h.hexdigest():
+        return None
+    return int(vals["traffic_bytes_per_launch"].strip())
+
+
+def captured_batch_traffic(tune: dict):
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary, or None
+    when its source or the launch shape differs from that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_batch_workload5_512tasks_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = dict(l.split(":", 1) for l in txt.splitlines()
+                if l.startswith(("traffic_bytes", "source_sha256", "tune")))
+    h = hashlib.sha256()
+    for f in ("batch.cu", "sis_device.cuh", "l0_device.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2410_01752_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    sha = next((v.strip() for k, v in vals.items() if k.startswith("source_sha256")), "")
+    shape = [tune[k] for k in ("score_units", "enum_items", "gram_rows", "ctas_per_sm", "window")]
+    if sha != h.hexdigest() or [int(x) for x in vals.get("tune", "").split()] != shape:
         return None
     return int(vals["traffic_bytes_per_launch"].strip())
 
@@ -262,10 +287,161 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_flops(probs, res) -> float:
+    """Algorithmic FP32 flops of the batched workload's screening: FP32_FLOP_PER_CAND_SAMPLE
+    per candidate and sample of each task's space, for every screening step it ran."""
+    import oracle
+    tot = 0.0
+    for P, (_, dims) in zip(probs, res):
+        tot += oracle.Space(P.d, P.op_set, P.rung, P.grammar).n_features * P.X.shape[0] * max(len(dims), 1)
+    return tot * FP32_FLOP_PER_CAND_SAMPLE
+
+
+def oracle_tasks_sample(probs, seconds: float, seed: int = 0):
+    """The FP64 oracle fitting randomly drawn tasks of the batch on all host cores for about
+    `seconds`; returns (tasks/s, tasks fitted, wall seconds, threads)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    th = cores()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        P = probs[int(rng.integers(0, len(probs)))]
+        oracle.fit(P.X, P.y, oracle.Space(P.d, P.op_set, P.rung, P.grammar), P.sis_size, P.max_dim, nthreads=th)
+        done += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            return done / dt, done, dt, th
+
+
+BATCH_NAME = "batched multi-task: {n} tasks, N~U{{20..2000}}, d~U{{4..12}}, x~U[0.5,5], rung 2, 9 ops, k=50, D<=3"
+
+
+def run_batch(args, rank: int):
+    """Batched multi-task workload: every task in one persistent launch (CUDA graph)."""
+    import numpy as np
+    from paper_2410_01752_gb300 import inputs
+    probs = [inputs.workload5_task(p) for p in range(args.tasks)]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        for k in range(args.warmup):
+            oracle_tasks_sample(probs, per_step / 4, seed=k)
+        done, dts = 0, 0.0
+        th = cores()
+        for k in range(args.steps):
+            _, n, dt, th = oracle_tasks_sample(probs, per_step, seed=100 + k)
+            done += n
+            dts += dt
+        value = done / dts
+        line = {"impl": "reference", "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dts / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": BATCH_NAME.format(n=args.tasks), "tasks": args.tasks},
+                "cpu_baseline": {"value": value, "unit": "tasks/s", "cores": th, "kind": "oracle",
+                                 "sample": f"{done} randomly drawn tasks fitted by the FP64 oracle"},
+                "e2e": {"value": value, "unit": "tasks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+    from paper_2410_01752_gb300 import build, sisso
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    b = sisso.Batch([(P.X, P.y) for P in probs], probs[0].op_set, 2, 50, 3, stream=stream)
+    tune = b.get_tune() if args.no_autotune else b.autotune(reps=2, cache_path=args.tune_cache)
+    for _ in range(args.warmup):
+        b.run(copies=False)
+    ms, stats = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(copies=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(b.stats())
+    res = b.results()
+    start, end = b.timing()
+    failed = sum(1 for st_, _ in res if st_ != 0)
+    mean_ms = sum(ms) / len(ms)
+    value = args.tasks / (mean_ms / 1e3)
+    # end to end through the C ABI: new host inputs into the pinned staging buffer, one graph
+    # launch with the copies, results read back
+    e2e = None
+    if not args.no_e2e:
+        host = [(P.X.copy(), P.y.copy()) for P in probs]
+        in_bytes = sum(X.nbytes + y.nbytes for X, y in host)
+        tms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.load(host)
+            b.run(copies=True)
+            r2 = b.results()
+            tms.append(time.perf_counter() - t0)
+        assert [d.ids for _, dd in r2 for d in dd] == [d.ids for _, dd in res for d in dd]
+        e2e = {"value": args.tasks / (sum(tms) / len(tms)), "unit": "tasks/s", "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": int(args.tasks * sisso.C.sizeof(sisso.TaskResult))}
+    flop = batch_flops(probs, res)
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = flop / (mean_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_batch (persistent, all stages)", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_batch_traffic(tune),
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (measured max SM clock)",
+            "flop_per_launch": flop, "launch_ms": mean_ms,
+            "algorithmic_unit": f"{FP32_FLOP_PER_CAND_SAMPLE} flop per candidate-sample of screening, every task and step run",
+            "score_stage_frac": None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, n, dt, th = oracle_tasks_sample(probs, args.cpu_seconds)
+        cpu = {"value": r, "unit": "tasks/s", "cores": th, "kind": "oracle",
+               "sample": f"{n} randomly drawn tasks of the batch fitted by the FP64 oracle ({dt:.1f} s)"}
+    st = stats[-1]
+    # the screening stage alone: its flops over its share of the SMs' time (CTA-time / CTAs per SM)
+    score_sm_s = st["stage_ms"][3] / 1e3 / (st["grid"] / sms)
+    roof["score_stage_frac"] = flop / (score_sm_s / sms) / 1e12 / peak if score_sm_s > 0 else None
+    names = ["-", "start", "level", "score", "gram", "bound", "band", "flat", "select", "refit", "idle", "-",
+             "select.radix", "select.rescore", "select.sort", "select.walk"]
+    line = {
+        "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH_NAME.format(n=args.tasks), "tasks": args.tasks, "tune": tune,
+                   "l2": "flushed between steps (256 MB write)", "graph": "one persistent launch per step"},
+        "latency_ms": {"p50": float(np.percentile(end, 50)), "p99": float(np.percentile(end, 99)),
+                       "max": float(end.max()), "note": "per task, from the launch's first CTA to its last result"},
+        "service_ms": {"p50": float(np.percentile(end - start, 50)), "p99": float(np.percentile(end - start, 99))},
+        "tasks_failed": failed,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 1,
+        "clocks": clk.summary(),
+        "stage_cta_ms": {names[q]: st["stage_ms"][q] for q in range(16) if names[q] != "-"},
+        "subsets_fit": st["subsets_fit"], "subsets_refit": st["subsets_refit"],
+        "windows_grown": st["windows_grown"], "windows_saturated": st["windows_saturated"],
+        "walk_visits": st["walk_visits"], "grid": st["grid"],
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     if args.workload == 3:
         run_mixed(args)
+        return
+    if args.workload == 5:
+        run_batch(args, int(os.environ.get("RANK", "0")))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
