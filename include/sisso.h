@@ -79,7 +79,7 @@ enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1, SISSO_PREC_MIXED_BF16 = 2, SISS
 enum { SISSO_GRAMMAR_EQ2 = 0, SISSO_GRAMMAR_NEW_X_PREV = 1 };
 
 #define SISSO_MAX_RUNG 3
-#define SISSO_MAX_DIM 4
+#define SISSO_MAX_DIM 5
 #define SISSO_MAX_SIS 1024
 
 typedef struct {
@@ -197,10 +197,16 @@ sisso_status sisso_sis_step(sisso_ctx* ctx, const double* target, const int64_t*
 /* Exhaustive l0 (§2.3) over every D-subset of n standardised features given their
  * FP64 Gram G (n x n, Z^T Z / N), moments b (n, Z^T y~ / N) and syy = y~^T y~ / N:
  * FP32 (or FP64) enumeration, FP64 refit of the band, tie rule on gid (n global ids).
- * best_pos: HOST, D positions ascending; best_rss: RSS of the winner.  *examined: C(n,D). */
+ * best_pos: HOST, D positions ascending; best_rss: RSS of the winner.  *examined: C(n,D).
+ * n <= 65535 for D <= 4, n <= 4095 for D = 5. */
 sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, double syy,
                              int n, int D, const int64_t* gid, int precision, int* best_pos,
                              double* best_rss, int64_t* examined);
+
+/* FP64 subspace Gram of the n features ids (n <= max_dim x sis_size of the context): the
+ * features evaluated and standardised on the device (§2.3), G = Z Z^T / N (n x n) and
+ * b = Z y~ / N (n), HOST; *syy (may be NULL) = y~^T y~ / N. */
+sisso_status sisso_subspace_gram(sisso_ctx* ctx, const int64_t* ids, int n, double* G, double* b, double* syy);
 
 /* Subspace Gram on the tcgen05 tensor cores (the mixed-precision forms' a4 step): with Z
  * n standardised rows of N samples (FP64, row-major) and yc the centred target with
@@ -279,7 +285,7 @@ typedef struct {
  * and device memory, and allocate all device memory the runs need (one arena).  opts:
  * grammar, max_band (band capacity per task and step, default 16384), cuda_stream and
  * device are used; precision must be SISSO_PREC_FP32 (or default).  Limits: n_tasks <=
- * 2^20, max_dim * sis_size <= 512, every task N >= max_dim + 1 and d >= 1, finite inputs,
+ * 2^20, max_dim <= 4, max_dim * sis_size <= 512, every task N >= max_dim + 1 and d >= 1, finite inputs,
  * non-constant y, and at most 2^18 screening units per task.  Errors: SISSO_ERR_ARG
  * (message names the task), SISSO_ERR_OOM, SISSO_ERR_CUDA.  On error *out is NULL and
  * the message is in sisso_batch_create_error(). */
@@ -324,6 +330,66 @@ void sisso_batch_destroy(sisso_batch* b);
 /* Convenience: create, one copying run, results, destroy.  results: HOST, n_tasks. */
 sisso_status sisso_fit_batch(const sisso_task* tasks, int n_tasks, uint32_t op_set, int rung, int sis_size,
                              int max_dim, const sisso_opts* opts, sisso_task_result* results);
+
+/* ---- learned subset proposal ----------------------------------------------------------
+ *
+ * For the l0 search at D = 5 (§2.3, Eq. 7) a small network ranks the search's 3-prefixes
+ * {p0 < p1 < p2} (p = positions in the screened subspace) by its prediction of the lowest
+ * RSS/SST (log10) among the 5-subsets that extend them with higher positions; the best
+ * prefixes are taken until their extensions make up a fraction of C(n, 5), and only those
+ * are solved, exactly.  The network: SISSO_MLP_IN inputs (the upper triangle of the 5 x 5
+ * standardised sub-Gram in row order, then the 5 correlations with the target; entries of
+ * features a prefix lacks are 0), two hidden layers of SISSO_MLP_HIDDEN with ReLU, one
+ * output; BF16 weights, activations and gradients with FP32 accumulation on the tensor
+ * cores, FP32 master weights, MSE loss, Adam.  The paper has no counterpart; exhaustive
+ * search (sisso_l0_search) remains the fallback and the judge.
+ *
+ * Parameter layout (FP32, SISSO_MLP_PARAMS values): W1 [256 x 20] row-major (output x input),
+ * b1 [256], W2 [256 x 256], b2 [256], w3 [256], b3 [1].
+ */
+#define SISSO_MLP_IN 20
+#define SISSO_MLP_HIDDEN 256
+#define SISSO_MLP_PARAMS (256 * 20 + 256 + 256 * 256 + 256 + 256 + 1)
+
+typedef struct sisso_mlp sisso_mlp;
+
+/* A network on the current device, He-uniform weights from the seed, zero biases. */
+sisso_status sisso_mlp_create(uint64_t seed, sisso_mlp** out);
+void sisso_mlp_destroy(sisso_mlp* mlp);
+/* params: HOST (get) / host or device (set), SISSO_MLP_PARAMS floats in the layout above. */
+sisso_status sisso_mlp_get_params(sisso_mlp* mlp, float* params);
+sisso_status sisso_mlp_set_params(sisso_mlp* mlp, const float* params);
+/* out[i] = network(X[i]) for M rows X (M x SISSO_MLP_IN, host or device); out HOST. */
+sisso_status sisso_mlp_forward(sisso_mlp* mlp, const float* X, int64_t M, float* out);
+/* Mean squared error of one batch (B a multiple of 128) and its gradient (HOST,
+ * SISSO_MLP_PARAMS floats, the parameter layout); loss may be NULL. */
+sisso_status sisso_mlp_gradients(sisso_mlp* mlp, const float* X, const float* t, int B, float* loss, float* grad);
+/* Adam (lr, betas 0.9 / 0.999) on the MSE over M examples for `epochs` epochs of batches of
+ * `batch` rows (a multiple of 128) in a seeded order; *final_loss: the last epoch's mean. */
+sisso_status sisso_mlp_train(sisso_mlp* mlp, const float* X, const float* t, int64_t M, int epochs, int batch,
+                             float lr, uint64_t seed, float* final_loss);
+
+/* Network inputs of every 3-prefix of n standardised features (G n x n, b, syy as for
+ * sisso_l0_search), prefixes in colex order (rank C(p2,3) + C(p1,2) + p0): out HOST,
+ * C(n,3) x SISSO_MLP_IN floats; prefixes (may be NULL) HOST, C(n,3) x 3 positions. */
+sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes);
+/* Training labels: per 3-prefix (same order), the lowest FP32 RSS / SST over the 5-subsets
+ * extending it with higher positions (exhaustive; +inf when it has none).  n in 5..1400.
+ * out HOST. */
+sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, int N, int n, float* out);
+
+/* The learned l0 search at D = 5 on the context's device: network scores of every 3-prefix,
+ * prefixes best first up to frac x C(n,5) subsets, their extensions solved exactly (same
+ * FP32 enumeration, FP64 confirmation and tie rule as sisso_l0_search).  Outputs as
+ * sisso_l0_search; *examined the subsets solved, *n_prefixes (may be NULL) those taken.
+ * n in 5..1400. */
+sisso_status sisso_l0_learned(sisso_ctx* ctx, const double* G, const double* b, double syy, int n,
+                              const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos, double* best_rss,
+                              int64_t* examined, int64_t* n_prefixes);
+
+/* Make sisso_fit use the learned search for its D = 5 step (mlp NULL: exhaustive again).
+ * The context does not own the network. */
+sisso_status sisso_set_proposal(sisso_ctx* ctx, sisso_mlp* mlp, double frac);
 
 /* ---- allocation-free l0 search --------------------------------------------------------
  *

@@ -62,13 +62,13 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
                       std::string& why) {
     if (d < 1) { why = "d < 1"; return SISSO_ERR_ARG; }
     if (rung < 1 || rung > SISSO_MAX_RUNG) { why = "rung must be in 1..3"; return SISSO_ERR_ARG; }
-    if (max_dim < 1 || max_dim > SISSO_MAX_DIM) { why = "max_dim must be in 1..4"; return SISSO_ERR_ARG; }
+    if (max_dim < 1 || max_dim > SISSO_MAX_DIM) { why = "max_dim must be in 1..5"; return SISSO_ERR_ARG; }
     if (k < 1 || k > SISSO_MAX_SIS) { why = "sis_size must be in 1..1024"; return SISSO_ERR_ARG; }
     if (N < max_dim + 1 || N < 2) { why = "N must be at least max_dim + 1"; return SISSO_ERR_ARG; }
     if ((ops & SISSO_OP_ALL) == 0 || (ops & ~SISSO_OP_ALL)) { why = "bad operator mask"; return SISSO_ERR_ARG; }
     if (o.precision < SISSO_PREC_FP64 || o.precision > SISSO_PREC_MIXED_FP16) { why = "bad precision"; return SISSO_ERR_ARG; }
     if (o.grammar != SISSO_GRAMMAR_EQ2 && o.grammar != SISSO_GRAMMAR_NEW_X_PREV) { why = "bad grammar"; return SISSO_ERR_ARG; }
-    if ((int64_t)max_dim * k > 65535) { why = "subspace too large"; return SISSO_ERR_ARG; }
+    if ((int64_t)max_dim * k > (max_dim <= 4 ? 65535 : 4095)) { why = "subspace too large"; return SISSO_ERR_ARG; }
     return SISSO_OK;
 }
 
@@ -251,6 +251,9 @@ sisso_status sisso_fit(sisso_ctx* c) {
         cudaEventRecord(g1, c->stream);
         Winner w{};
         if (mixed) st = l0_solve_mixed(c, n, t, w);
+        else if (c->proposal && t == 5 && n >= 5)
+            st = l0_learned(c, c->proposal, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, c->S_dev,
+                            c->prune_frac, w, &c->learned_prefixes);
         else st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
         if (st) break;
         c->stats.ms_gram += event_ms(g0, g1);
@@ -415,7 +418,8 @@ sisso_status sisso_sis_step(sisso_ctx* c, const double* target, const int64_t* S
 
 sisso_status sisso_l0_search(sisso_ctx* c, const double* G, const double* b, double syy, int n, int D,
                              const int64_t* gid, int precision, int* best_pos, double* best_rss, int64_t* examined) {
-    if (!c || !G || !b || !gid || !best_pos || n < 1 || D < 1 || D > SISSO_MAX_DIM || n < D || n > 65535)
+    if (!c || !G || !b || !gid || !best_pos || n < 1 || D < 1 || D > SISSO_MAX_DIM || n < D ||
+        n > (D <= 4 ? 65535 : 4095))
         return SISSO_ERR_ARG;
     cudaSetDevice(c->opts.device);
     double *dG = nullptr, *db = nullptr;
@@ -446,3 +450,62 @@ sisso_status sisso_l0_search(sisso_ctx* c, const double* G, const double* b, dou
 }
 
 }  // extern "C"
+
+extern "C" sisso_status sisso_set_proposal(sisso_ctx* c, sisso_mlp* mlp, double frac) {
+    if (!c || (mlp && !(frac > 0.0 && frac <= 1.0))) return SISSO_ERR_ARG;
+    c->proposal = mlp;
+    if (mlp) c->prune_frac = frac;
+    return SISSO_OK;
+}
+
+extern "C" sisso_status sisso_l0_learned(sisso_ctx* c, const double* G, const double* b, double syy, int n,
+                                         const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos,
+                                         double* best_rss, int64_t* examined, int64_t* n_prefixes) {
+    using namespace sg;
+    if (!c || !G || !b || !gid || !mlp || !best_pos || n < 5 || n > 1400 || !(frac > 0.0 && frac <= 1.0) ||
+        !(syy > 0.0))
+        return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    double *dG = nullptr, *db = nullptr;
+    float *dG32 = nullptr, *db32 = nullptr;
+    int64_t* dgid = nullptr;
+    sisso_status st;
+    const size_t nn = (size_t)n * n;
+    if ((st = dalloc(c, dG, nn, "G")) || (st = dalloc(c, db, (size_t)n, "b")) || (st = dalloc(c, dG32, nn, "G32")) ||
+        (st = dalloc(c, db32, (size_t)n, "b32")) || (st = dalloc(c, dgid, (size_t)n, "gid"))) {
+        cudaFree(dG); cudaFree(db); cudaFree(dG32); cudaFree(db32); cudaFree(dgid);
+        return st;
+    }
+    cudaMemcpyAsync(dG, G, sizeof(double) * nn, cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyDefault, c->stream);
+    cudaMemcpyAsync(dgid, gid, sizeof(int64_t) * n, cudaMemcpyDefault, c->stream);
+    k_cast<<<std::max(1, std::min(c->sms * 4, (int)((nn + 255) / 256))), 256, 0, c->stream>>>(dG, dG32, (int64_t)nn);
+    k_cast<<<1, 256, 0, c->stream>>>(db, db32, n);
+    Winner w{};
+    int64_t sel = 0;
+    st = l0_learned(c, mlp, dG, db, dG32, db32, n, syy, n, dgid, frac, w, &sel);
+    if (!st) {
+        std::copy(w.pos, w.pos + 5, best_pos);
+        if (best_rss) *best_rss = w.rss_gram;
+        if (examined) *examined = w.examined;
+        if (n_prefixes) *n_prefixes = sel;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(dG); cudaFree(db); cudaFree(dG32); cudaFree(db32); cudaFree(dgid);
+    return st;
+}
+
+extern "C" sisso_status sisso_subspace_gram(sisso_ctx* c, const int64_t* ids, int n, double* G, double* b, double* syy) {
+    using namespace sg;
+    if (!c || !ids || !G || !b || n < 1 || n > c->n_cap) return SISSO_ERR_ARG;
+    cudaSetDevice(c->opts.device);
+    cudaMemcpyAsync(c->S_dev, ids, sizeof(int64_t) * n, cudaMemcpyDefault, c->stream);
+    sisso_status st = append_subspace(c, 0, n, true);
+    if (st) return st;
+    cudaMemcpy2DAsync(G, sizeof(double) * n, c->G64, sizeof(double) * c->n_cap, sizeof(double) * n, n,
+                      cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(b, c->b64, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    st = check_cuda(c, cudaStreamSynchronize(c->stream), "subspace_gram");
+    if (!st && syy) *syy = c->syy;
+    return st;
+}

@@ -180,7 +180,7 @@ struct SelectSmem {
     float r[32];
 };
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kL0Smem = (size_t)8 * (kMaxDim) * 512 * sizeof(float);   // per-warp tables, n <= 512
+constexpr size_t kL0Smem = (size_t)8 * 4 * 512 * sizeof(float);   // per-warp tables: D <= 4, n <= 512
 constexpr size_t kBatchSmem = cmax(cmax(sizeof(PairSmem<float>), sizeof(SelectSmem)), cmax(sizeof(UnarySmem), kL0Smem));
 
 struct Ctl {                    // small per-CTA control block (static shared memory)
@@ -1333,9 +1333,9 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
     sisso_default_opts(&o);
     if (opts) o = *opts;
     if (!tasks || n_tasks < 1 || n_tasks > (1 << 20)) { set_err("n_tasks must be 1..2^20"); return SISSO_ERR_ARG; }
-    if (rung < 1 || rung > kMaxRung || max_dim < 1 || max_dim > kMaxDim || sis_size < 1 ||
+    if (rung < 1 || rung > kMaxRung || max_dim < 1 || max_dim > 4 || sis_size < 1 ||
         (op_set & SISSO_OP_ALL) == 0 || max_dim * sis_size > 512) {
-        set_err("bad rung, max_dim, sis_size (max_dim * sis_size <= 512) or op_set");
+        set_err("bad rung, max_dim (1..4), sis_size (max_dim * sis_size <= 512) or op_set");
         return SISSO_ERR_ARG;
     }
     if (o.precision != SISSO_PREC_FP32) { set_err("the batched form computes in FP32 (SISSO_PREC_FP32)"); return SISSO_ERR_ARG; }

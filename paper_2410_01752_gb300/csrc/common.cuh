@@ -430,6 +430,11 @@ struct sisso_ctx {
     bool fitted = false;
     sisso_stats stats{};
     int sms = 0;
+
+    // learned proposal for the D = 5 step (not owned)
+    sisso_mlp* proposal = nullptr;
+    double prune_frac = 0.01;
+    int64_t learned_prefixes = 0;
 };
 
 namespace sg {
@@ -458,8 +463,14 @@ sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
 sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
-                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w);
+                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,
+                      const int* prefix_list = nullptr, int64_t n_prefixes = 0);
 sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w);
+
+// learned proposal (learn.cu)
+sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const double* b, const float* G32,
+                        const float* b32, int ld, double syy, int n, const int64_t* gid_dev, double frac, Winner& w,
+                        int64_t* n_selected);
 
 // tensor-core Gram (gram_tc.cu)
 sisso_status gram_tc(sisso_ctx* c, const double* Z, const double* yc, double sdy, int n, int N, int kind,

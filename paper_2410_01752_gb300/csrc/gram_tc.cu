@@ -14,7 +14,7 @@
 //     32w..32w+31, i.e. output rows) and add it into the FP32 result.
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag, waits
 // (bounded) for its own copies, frees its TMEM and returns.
-#include "common.cuh"
+#include "tc_device.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -32,7 +32,6 @@ constexpr int STAGES = 4;
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTileBytes = TMT * BK * 2;        // 16 KB per operand tile
 constexpr uint32_t kTmemCols = 128;                  // FP32 accumulator: 128 lanes x 128 columns
-constexpr long long kWaitLimit = 1ll << 24;          // polls before a wait is declared lost
 
 struct TcSmem {
     uint8_t a[STAGES][kTileBytes];
@@ -40,81 +39,6 @@ struct TcSmem {
     uint64_t full[STAGES], empty[STAGES], done;
     uint32_t tmem_base;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// bounded wait on the phase of the given parity
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// K-major operand tile of 128 rows x 64 16-bit values, 128-byte swizzle: rows of 128 B,
-// 8-row groups 1024 B apart (stride byte offset), descriptor version 1, layout 2 (128B)
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B of the same
-// 16-bit type (0 FP16, 1 BF16), both K-major, N = 128, M = 128
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type) {
-    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(TNT >> 3) << 17) | ((uint32_t)(TMT >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                        uint32_t accumulate) {
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 struct TcArgs {
     int rows;          // real rows (features + target row)
@@ -246,23 +170,6 @@ __global__ void k_unpack_gram(const float* __restrict__ C, int ld, int n, float 
     }
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static std::once_flag once;
-    static EncodeTiledFn fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    return fn;
-}
-
 }  // namespace
 
 // G32 (n x n, leading dimension ldg) and b32 (n) of the n standardised rows of Z and the
@@ -304,7 +211,7 @@ sisso_status gram_tc(sisso_ctx* c, const double* Z, const double* yc, double sdy
     }
     TcArgs A{};
     A.rows = rows; A.tiles = tiles; A.nk = nk; A.scale = 1.0f / (float)N; A.C = C; A.ld = Rpad; A.err = err;
-    A.idesc = idesc_f16(bf16 ? 1u : 0u);
+    A.idesc = idesc_f16(bf16 ? 1u : 0u, TMT, TNT);
     const int out_tiles = tiles * tiles;
     A.splits = std::max(1, std::min(nk, (c->sms + out_tiles - 1) / out_tiles));
     const size_t smem = sizeof(TcSmem) + 1024;

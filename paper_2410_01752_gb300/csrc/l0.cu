@@ -478,6 +478,7 @@ static sisso_status run_enum(sisso_ctx* c, EnumArgs<T> A, int D, int mode) {
     } else if (DP == 0) { if (mode == 0) SG_LAUNCH(0, 0); else SG_LAUNCH(0, 1); }
     else if (DP == 1) { if (mode == 0) SG_LAUNCH(1, 0); else SG_LAUNCH(1, 1); }
     else if (DP == 2) { if (mode == 0) SG_LAUNCH(2, 0); else SG_LAUNCH(2, 1); }
+    else if (DP == 3) { if (mode == 0) SG_LAUNCH(3, 0); else SG_LAUNCH(3, 1); }
     else return fail(c, SISSO_ERR_ARG, "descriptor dimension above SISSO_MAX_DIM");
 #undef SG_LAUNCH
     c->stats.launches++;
@@ -485,9 +486,10 @@ static sisso_status run_enum(sisso_ctx* c, EnumArgs<T> A, int D, int mode) {
 }
 
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
-                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w) {
+                      int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,
+                      const int* prefix_list, int64_t n_prefixes) {
     if (D < 1 || D > kMaxDim || n < D) return fail(c, SISSO_ERR_ARG, "l0: bad D or n");
-    if (n > 65535) return fail(c, SISSO_ERR_ARG, "l0: more than 65535 features");
+    if (n > (D <= 4 ? 65535 : 4095)) return fail(c, SISSO_ERR_ARG, "l0: too many features for D");
     const bool fp32 = precision != SISSO_PREC_FP64;
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
@@ -496,7 +498,8 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     // decoded in the kernel
     const int DPh = D - 2;
     const int cpp = D >= 2 ? std::max(1, (n - 1 - DPh + kRows - 1) / kRows) : 1;
-    const int64_t n_items = D >= 2 ? binom_host(n - 2, DPh) * cpp : 0;
+    if (prefix_list && D < 3) return fail(c, SISSO_ERR_ARG, "l0: a prefix list needs D >= 3");
+    const int64_t n_items = D >= 2 ? (prefix_list ? n_prefixes : binom_host(n - 2, DPh)) * cpp : 0;
     unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(c->work + 2);
     unsigned long long* examined = ub_key + 1;
     unsigned long long* min_key = ub_key + 2;
@@ -511,7 +514,7 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
         A.G = G32; A.b = b32; A.ld = ld; A.n = n; A.N = c->N; A.syy = (float)syy; A.sst = sst;
         A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
         A.tau = kPivotMin32; A.fp32 = 1; A.sqrt_syy = std::sqrt(syy); A.ub_key = ub_key; A.win = c->win; A.band = c->band;
-        A.G64 = G; A.b64 = b; A.syy64 = syy; A.tie64 = 2.0 * kRssTie * sst;
+        A.G64 = G; A.b64 = b; A.syy64 = syy; A.tie64 = 2.0 * kRssTie * sst; A.prefix_list = prefix_list;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;
         k_set_thr<<<1, 1, 0, c->stream>>>(c->win, ub_key, 0.0);
@@ -520,7 +523,7 @@ sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const floa
     } else {
         EnumArgs<double> A{};
         A.G = G; A.b = b; A.ld = ld; A.n = n; A.N = c->N; A.syy = syy; A.sst = sst;
-        A.cpp = cpp; A.n_items = n_items; A.counter = c->work;
+        A.cpp = cpp; A.n_items = n_items; A.counter = c->work; A.prefix_list = prefix_list;
         A.tau = (float)kPivotMin; A.fp32 = 0; A.ub_key = ub_key; A.win = c->win; A.band = c->band;
         A.band_count = c->band_count; A.band_cap = c->band_cap; A.examined = examined;
         if ((st = run_enum(c, A, D, 0))) return st;
@@ -697,7 +700,8 @@ cudaError_t na_enum(const EnumArgs<T>& A, int D, int mode, int sms, cudaStream_t
         else k_l0_single<T, 1><<<(A.n + 255) / 256, 256, 0, st>>>(A);
     } else if (DP == 0) { if (mode == 0) SG_NA(0, 0); else SG_NA(0, 1); }
     else if (DP == 1) { if (mode == 0) SG_NA(1, 0); else SG_NA(1, 1); }
-    else { if (mode == 0) SG_NA(2, 0); else SG_NA(2, 1); }
+    else if (DP == 2) { if (mode == 0) SG_NA(2, 0); else SG_NA(2, 1); }
+    else { if (mode == 0) SG_NA(3, 0); else SG_NA(3, 1); }
 #undef SG_NA
     return cudaGetLastError();
 }

@@ -53,15 +53,22 @@ struct EnumArgs {
     const double* b64;          //   pivot is solved in FP64 on the spot and kept in the band only
     double syy64;               //   when its RSS is within tie64 of the pass-2 threshold
     double tie64;
+    const int* prefix_list;     // optional: the prefixes to enumerate (D-2 positions each, ascending),
+                                //   item = list index x chunk; otherwise every prefix in colex order
 };
 
 
+// subset positions packed into 64 bits: 16 bits each for D <= 4 (n <= 65535), 12 bits each
+// for D = 5 (n <= 4095)
+__host__ __device__ constexpr int pos_bits(int D) { return D <= 4 ? 16 : 12; }
+
 template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pre)[DP > 0 ? DP : 1], int i1, int i2) {
+    constexpr int W = pos_bits(DP + 2);
     uint64_t k = 0;
     int s = 0;
 #pragma unroll
-    for (int m = 0; m < DP; ++m) { k |= (uint64_t)pre[m] << s; s += 16; }
-    k |= (uint64_t)i1 << s; s += 16;
+    for (int m = 0; m < DP; ++m) { k |= (uint64_t)pre[m] << s; s += W; }
+    k |= (uint64_t)i1 << s; s += W;
     k |= (uint64_t)i2 << s;
     return k;
 }
@@ -71,29 +78,37 @@ template <int DP> __device__ __forceinline__ uint64_t pack_subset(const int (&pr
 __device__ __forceinline__ int64_t binom2(int64_t m) { return m * (m - 1) / 2; }
 __device__ __forceinline__ int64_t binom3(int64_t m) { return m * (m - 1) * (m - 2) / 6; }
 
+__device__ __forceinline__ int64_t binom4(int64_t m) { return m * (m - 1) * (m - 2) * (m - 3) / 24; }
+
+// largest m with C(m, 2) <= r
+__device__ __forceinline__ int64_t colex_top2(int64_t r) {
+    int64_t m = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
+    while (m > 1 && binom2(m) > r) --m;
+    while (binom2(m + 1) <= r) ++m;
+    return m;
+}
+__device__ __forceinline__ int64_t colex_top3(int64_t r) {
+    int64_t m = (int64_t)cbrt(6.0 * (double)r) + 1;
+    while (m > 2 && binom3(m) > r) --m;
+    while (binom3(m + 1) <= r) ++m;
+    return m;
+}
+__device__ __forceinline__ int64_t colex_top4(int64_t r) {
+    int64_t m = (int64_t)sqrt(sqrt(24.0 * (double)r)) + 2;
+    while (m > 3 && binom4(m) > r) --m;
+    while (binom4(m + 1) <= r) ++m;
+    return m;
+}
+
 template <int DP> __device__ __forceinline__ void colex_unrank(int64_t r, int (&p)[DP > 0 ? DP : 1]) {
     if (DP == 0) return;
     if (DP == 1) { p[0] = (int)r; return; }
-    if (DP == 2) {
-        int64_t m = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
-        while (m > 1 && binom2(m) > r) --m;
-        while (binom2(m + 1) <= r) ++m;
-        p[1] = (int)m;
-        p[0] = (int)(r - binom2(m));
-        return;
-    }
-    if (DP == 3) {
-        int64_t m = (int64_t)cbrt(6.0 * (double)r) + 1;
-        while (m > 2 && binom3(m) > r) --m;
-        while (binom3(m + 1) <= r) ++m;
-        p[DP > 2 ? 2 : 0] = (int)m;
-        r -= binom3(m);
-        int64_t q = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
-        while (q > 1 && binom2(q) > r) --q;
-        while (binom2(q + 1) <= r) ++q;
-        p[1] = (int)q;
-        p[0] = (int)(r - binom2(q));
-    }
+    int64_t m;
+    if (DP >= 4) { m = colex_top4(r); p[DP > 3 ? 3 : 0] = (int)m; r -= binom4(m); }
+    if (DP >= 3) { m = colex_top3(r); p[DP > 2 ? 2 : 0] = (int)m; r -= binom3(m); }
+    m = colex_top2(r);
+    p[1] = (int)m;
+    p[0] = (int)(r - binom2(m));
 }
 
 // MODE 0: bound (min of RSS + err); MODE 1: band collection
@@ -130,7 +145,9 @@ __device__ double rss64(const double* G, const double* b, int ld, double syy, in
 }
 
 __device__ __forceinline__ void unpack(uint64_t key, int D, int* pos) {
-    for (int j = 0; j < D; ++j) pos[j] = (int)((key >> (16 * j)) & 0xFFFF);
+    const int W = pos_bits(D);
+    const uint64_t mask = (1ull << W) - 1;
+    for (int j = 0; j < D; ++j) pos[j] = (int)((key >> (W * j)) & mask);
 }
 
 // pass 2, a subset flagged by an FP32 pivot: keep it for the FP64 refit?  With the FP64
@@ -219,7 +236,12 @@ __device__ __forceinline__ void enum_item(const EnumArgs<T>& A, T* tab, int64_t 
     int pre[DP > 0 ? DP : 1];
     const int64_t prank = item / A.cpp;
     const int chunk = (int)(item % A.cpp);
-    colex_unrank<DP>(prank, pre);
+    if (A.prefix_list) {
+#pragma unroll
+        for (int m = 0; m < DP; ++m) pre[m] = A.prefix_list[prank * (DP > 0 ? DP : 1) + m];
+    } else {
+        colex_unrank<DP>(prank, pre);
+    }
     const int i1s = (DP > 0 ? pre[DP - 1] + 1 : 0) + chunk * kRows;
     if (i1s >= n - 1) return;
     // prefix factor (warp-uniform, redundant in every lane)

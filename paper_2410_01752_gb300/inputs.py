@@ -12,6 +12,10 @@ Workloads (x: primary features, N samples x d; y: target):
   3  N=65536, d=12; x7..x12 ~ U[1,5]; x1..x6 = 3 + 0.5 (sqrt(.999) g + sqrt(.001) e_j)
      (pairwise correlation 0.999); y = c1 x1 x7^2 + c2 x2 / sqrt(x8) + c3 log(x3) x9
      + 1% noise                                                                 (rung 2, k=200, D<=3)
+  4  learned proposal: problem p of the training set (seeds 4000 + p) or of the held-out
+     evaluation set (seeds 40000 + p): N ~ U{500..2000}, d ~ U{8..12}, x ~ U[1,5],
+     3-5 distinct planted rung-2 terms from the menu below, c ~ U(-5, 5), 1% noise
+                                                                                (rung 2, k=60, D<=5)
   5  one of 512 tasks: N ~ U{20..2000}, d ~ U{4..12}, x ~ U[0.5, 5], 1-3 planted rung-2
      terms from a fixed menu, c ~ U(-5, 5), 0.5% noise                          (rung 2, k=50, D<=3)
   The paper's own workloads are of the same kind: x in [1,5], small N, 3-4 term targets
@@ -117,5 +121,20 @@ def workload5_task(p: int) -> Problem:
     return Problem(X, y, OPS9, 2, 50, 3, GRAMMAR_EQ2, f"task{p} N={N} d={d}")
 
 
+def workload4(p: int, held_out: bool = True, sis_size: int = 60, max_dim: int = 5) -> Problem:
+    r = np.random.default_rng((40000 if held_out else 4000) + p)
+    N = int(r.integers(500, 2001))
+    d = int(r.integers(8, 13))
+    X = r.uniform(1.0, 5.0, size=(N, d))
+    perm = r.permutation(d)
+    x = [X[:, perm[j]] for j in range(4)]
+    terms = r.choice(len(_MENU), size=int(r.integers(3, 6)), replace=False)
+    c = r.uniform(-5.0, 5.0, size=len(terms))
+    clean = sum(ci * _MENU[t](x) for ci, t in zip(c, terms))
+    y = clean + r.normal(0.0, 0.01 * max(clean.std(), 1e-12), size=N)
+    return Problem(X, y, OPS9, 2, sis_size, max_dim, GRAMMAR_EQ2,
+                   f"learned-{'eval' if held_out else 'train'}{p} N={N} d={d} rung2 k={sis_size} D<={max_dim}")
+
+
 def workload(config: int, p: int = 0, **kw) -> Problem:
-    return {1: workload1, 2: workload2, 3: workload3, 5: workload5_task}[config](p, **kw)
+    return {1: workload1, 2: workload2, 3: workload3, 4: workload4, 5: workload5_task}[config](p, **kw)

@@ -20,7 +20,7 @@ OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_EXP, OP_LOG, OP_SQRT, OP_SQ, OP_INV, OP_SIN, 
     1 << i for i in range(12))
 PREC_FP64, PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
-MAX_DIM, MAX_SIS, MAX_RUNG = 4, 1024, 3
+MAX_DIM, MAX_SIS, MAX_RUNG = 5, 1024, 3
 STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
           -4: "SISSO_ERR_NUMERIC", -5: "SISSO_ERR_TIMEOUT", -6: "SISSO_ERR_STATE",
           -7: "SISSO_ERR_CAPACITY"}
@@ -35,8 +35,13 @@ EXPORTS = [
     "sisso_batch_create", "sisso_batch_create_error", "sisso_batch_set_tune", "sisso_batch_get_tune",
     "sisso_batch_autotune", "sisso_batch_load", "sisso_batch_run", "sisso_batch_results",
     "sisso_batch_timing", "sisso_batch_get_stats", "sisso_batch_last_error", "sisso_batch_destroy",
-    "sisso_fit_batch",
+    "sisso_fit_batch", "sisso_subspace_gram",
+    "sisso_mlp_create", "sisso_mlp_destroy", "sisso_mlp_get_params", "sisso_mlp_set_params", "sisso_mlp_forward",
+    "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
+    "sisso_set_proposal",
 ]
+MLP_IN, MLP_HIDDEN = 20, 256
+MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 NOALLOC_MAX_N = 256
 NOALLOC_MAX_BAND = 65536
 
@@ -152,9 +157,24 @@ def load() -> C.CDLL:
     L.sisso_batch_destroy.argtypes = [vp]
     L.sisso_batch_destroy.restype = None
     L.sisso_fit_batch.argtypes = [vp, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int, C.POINTER(Opts), vp]
+    L.sisso_subspace_gram.argtypes = [vp, vp, C.c_int, vp, vp, dp]
+    L.sisso_mlp_create.argtypes = [C.c_uint64, C.POINTER(vp)]
+    L.sisso_mlp_destroy.argtypes = [vp]
+    L.sisso_mlp_destroy.restype = None
+    L.sisso_mlp_get_params.argtypes = [vp, vp]
+    L.sisso_mlp_set_params.argtypes = [vp, vp]
+    L.sisso_mlp_forward.argtypes = [vp, vp, C.c_int64, vp]
+    L.sisso_mlp_gradients.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_float), vp]
+    L.sisso_mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_uint64,
+                                  C.POINTER(C.c_float)]
+    L.sisso_prefix_features.argtypes = [vp, vp, C.c_double, C.c_int, vp, vp]
+    L.sisso_prefix_labels.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp]
+    L.sisso_l0_learned.argtypes = [vp, vp, vp, C.c_double, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_int), dp,
+                                   i64p, i64p]
+    L.sisso_set_proposal.argtypes = [vp, vp, C.c_double]
     for name in EXPORTS:
         if name not in ("sisso_default_opts", "sisso_last_error", "sisso_destroy", "sisso_batch_create_error",
-                        "sisso_batch_last_error", "sisso_batch_destroy"):
+                        "sisso_batch_last_error", "sisso_batch_destroy", "sisso_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -339,6 +359,35 @@ class Sisso:
                     "l0_search")
         return [int(p) for p in pos], rss.value, ex.value
 
+    def subspace_gram(self, ids):
+        """FP64 (G, b, syy) of the standardised features ids against y."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        n = ids.size
+        G = np.zeros((n, n), dtype=np.float64)
+        b = np.zeros(n, dtype=np.float64)
+        syy = C.c_double()
+        self._check(load().sisso_subspace_gram(self._ctx, C.c_void_p(ids.ctypes.data), n, C.c_void_p(G.ctypes.data),
+                                               C.c_void_p(b.ctypes.data), C.byref(syy)), "subspace_gram")
+        return G, b, syy.value
+
+    def l0_learned(self, G, b, syy: float, gid, mlp: "MLP", frac: float):
+        """D = 5 search over the prefixes the network ranks best (frac of all subsets)."""
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        gid = np.ascontiguousarray(gid, dtype=np.int64)
+        pos = np.zeros(5, dtype=np.int32)
+        rss, ex, npre = C.c_double(), C.c_int64(), C.c_int64()
+        self._check(load().sisso_l0_learned(self._ctx, C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data),
+                                            float(syy), b.size, C.c_void_p(gid.ctypes.data), mlp._m, float(frac),
+                                            pos.ctypes.data_as(C.POINTER(C.c_int)), C.byref(rss), C.byref(ex),
+                                            C.byref(npre)), "l0_learned")
+        return [int(p) for p in pos], rss.value, ex.value, npre.value
+
+    def set_proposal(self, mlp, frac: float = 0.01):
+        self._proposal = mlp
+        self._check(load().sisso_set_proposal(self._ctx, mlp._m if mlp is not None else None, float(frac)),
+                    "set_proposal")
+
     def close(self):
         if self._ctx:
             load().sisso_destroy(self._ctx)
@@ -483,3 +532,91 @@ def fit_batch(problems, op_set: int, rung: int, sis_size: int, max_dim: int, gra
     if st != 0:
         raise SissoError(st, "sisso_fit_batch: " + L.sisso_batch_create_error().decode())
     return _results(res, len(problems))
+
+
+class MLP:
+    """The proposal network (20 -> 256 -> 256 -> 1, BF16 on the tensor cores) on the current device."""
+
+    def __init__(self, seed: int = 0):
+        self._m = C.c_void_p()
+        st = load().sisso_mlp_create(int(seed), C.byref(self._m))
+        if st != 0:
+            raise SissoError(st, "sisso_mlp_create")
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise SissoError(st, what)
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(load().sisso_mlp_get_params(self._m, C.c_void_p(p.ctypes.data)), "mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == MLP_PARAMS
+        self._check(load().sisso_mlp_set_params(self._m, C.c_void_p(p.ctypes.data)), "mlp_set_params")
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+        out = np.zeros(X.shape[0], dtype=np.float32)
+        self._check(load().sisso_mlp_forward(self._m, C.c_void_p(X.ctypes.data), X.shape[0],
+                                             C.c_void_p(out.ctypes.data)), "mlp_forward")
+        return out
+
+    def gradients(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = C.c_float()
+        self._check(load().sisso_mlp_gradients(self._m, C.c_void_p(X.ctypes.data), C.c_void_p(t.ctypes.data),
+                                               X.shape[0], C.byref(loss), C.c_void_p(g.ctypes.data)), "mlp_gradients")
+        return loss.value, g
+
+    def train(self, X, t, epochs: int = 5, batch: int = 2048, lr: float = 1e-3, seed: int = 0) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1)
+        loss = C.c_float()
+        self._check(load().sisso_mlp_train(self._m, C.c_void_p(X.ctypes.data), C.c_void_p(t.ctypes.data),
+                                           X.shape[0], epochs, batch, float(lr), int(seed), C.byref(loss)),
+                    "mlp_train")
+        return loss.value
+
+    def close(self):
+        if self._m:
+            load().sisso_mlp_destroy(self._m)
+            self._m = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prefix_features(G, b, syy: float):
+    """(inputs C(n,3) x 20, prefixes C(n,3) x 3) of every 3-prefix, colex order."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = b.size
+    npre = n * (n - 1) * (n - 2) // 6
+    X = np.zeros((npre, MLP_IN), dtype=np.float32)
+    P = np.zeros((npre, 3), dtype=np.int32)
+    st = load().sisso_prefix_features(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), n,
+                                      C.c_void_p(X.ctypes.data), C.c_void_p(P.ctypes.data))
+    if st != 0:
+        raise SissoError(st, "prefix_features")
+    return X, P
+
+
+def prefix_labels(G, b, syy: float, N: int) -> np.ndarray:
+    """Per 3-prefix: the lowest RSS/SST over its 5-subset extensions (+inf: none)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = b.size
+    out = np.zeros(n * (n - 1) * (n - 2) // 6, dtype=np.float32)
+    st = load().sisso_prefix_labels(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), int(N), n,
+                                    C.c_void_p(out.ctypes.data))
+    if st != 0:
+        raise SissoError(st, "prefix_labels")
+    return out

@@ -82,7 +82,7 @@ def test_eq2_rung3_triangle_unranking(orc, lib):
 
 @pytest.mark.parametrize("kw,bad", [
     (dict(op_set=0), "empty op mask"), (dict(rung=4), "rung > 3"), (dict(rung=0), "rung 0"),
-    (dict(max_dim=5), "max_dim > 4"), (dict(sis_size=0), "k = 0"), (dict(sis_size=2000), "k > 1024"),
+    (dict(max_dim=6), "max_dim > 5"), (dict(sis_size=0), "k = 0"), (dict(sis_size=2000), "k > 1024"),
     (dict(N=3), "N < max_dim + 1"), (dict(precision=7), "precision"), (dict(grammar=3), "grammar")])
 def test_argument_errors(lib, kw, bad):
     args = dict(N=20, d=3, op_set=lib.OP_ADD | lib.OP_MUL, rung=2, sis_size=5, max_dim=3, precision=1, grammar=0)

@@ -1,0 +1,184 @@
+"""Learned subset proposal (GPU): the network's forward pass and gradients against the
+numpy reference, the prefix inputs and labels against their definitions, the pruned search
+against the exhaustive one, and what training gains over an untrained network."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2410_01752_gb300 import sisso
+    sisso.load()
+    return sisso
+
+
+def _random_net(seed, scale=0.08):
+    r = np.random.default_rng(seed)
+    p = np.zeros(ref.N_PARAMS)
+    o = 0
+    for name, shape in ref.SIZES:
+        k = int(np.prod(shape))
+        fan = shape[1] if len(shape) == 2 else ref.N_HID
+        p[o:o + k] = r.uniform(-1, 1, k) * np.sqrt(6.0 / fan) if name != "b3" else 0.1
+        if name in ("b1", "b2"):
+            p[o:o + k] = r.normal(0, 0.05, k)
+        o += k
+    return p.astype(np.float32)
+
+
+def _batch(seed, B=256):
+    r = np.random.default_rng(seed)
+    X = r.normal(0, 0.6, size=(B, ref.N_IN)).astype(np.float32)
+    t = r.normal(-2, 1, size=B).astype(np.float32)
+    return X, t
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _blocks(g):
+    out, o = {}, 0
+    for name, shape in ref.SIZES:
+        k = int(np.prod(shape))
+        out[name] = g[o:o + k]
+        o += k
+    return out
+
+
+def test_forward_matches_reference(S):
+    p = _random_net(1)
+    X, _ = _batch(2, 1000)
+    net = S.MLP(0)
+    net.set_params(p)
+    got = net.forward(X)
+    want16, _ = ref.forward(p.astype(np.float64), X, bf16_points=True)
+    want64, _ = ref.forward(p.astype(np.float64), X)
+    assert _rel(got, want16) < 2e-3          # same rounding points, FP32 vs FP64 accumulation
+    assert _rel(got, want64) < 3e-2          # BF16 against exact arithmetic
+    net.close()
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_gradients_match_reference(S, seed):
+    p = _random_net(seed)
+    X, t = _batch(seed + 10, 256)
+    net = S.MLP(0)
+    net.set_params(p)
+    loss, g = net.gradients(X, t)
+    loss16, g16 = ref.loss_and_grad(p.astype(np.float64), X, t, bf16_points=True)
+    loss64, g64 = ref.loss_and_grad(p.astype(np.float64), X, t)
+    assert loss == pytest.approx(loss16, rel=2e-3)
+    assert loss == pytest.approx(loss64, rel=5e-2)
+    G, G16, G64 = _blocks(g), _blocks(g16), _blocks(g64)
+    for name in G:
+        assert _rel(G[name], G16[name]) < 1e-2, name
+        assert _rel(G[name], G64[name]) < 6e-2, name
+    net.close()
+
+
+def test_training_lowers_the_loss(S):
+    r = np.random.default_rng(7)
+    X = r.normal(0, 0.6, size=(8192, ref.N_IN)).astype(np.float32)
+    t = (np.sin(X[:, 0]) + X[:, 1] * X[:, 2] - 0.5 * X[:, 3] ** 2).astype(np.float32)
+    net = S.MLP(1)
+    p0 = net.params()
+    l0, _ = ref.loss_and_grad(p0.astype(np.float64), X, t)
+    lt = net.train(X, t, epochs=20, batch=1024, lr=2e-3, seed=0)
+    y = net.forward(X)
+    assert float(np.mean((y - t) ** 2)) < 0.2 * l0
+    assert lt < 0.3 * l0
+    net.close()
+
+
+def _gram_case(seed, n, N=300):
+    r = np.random.default_rng(seed)
+    cols = r.normal(size=(N, n)) + 0.5 * r.normal(size=(N, 1))
+    y = cols[:, :4] @ r.uniform(-2, 2, 4) + 0.4 * r.normal(size=N)
+    Z = (cols - cols.mean(0)) / cols.std(0)
+    yc = y - y.mean()
+    return Z.T @ Z / N, Z.T @ yc / N, float(yc @ yc) / N, N
+
+
+def test_prefix_features_and_order(S):
+    G, b, syy, N = _gram_case(0, 9)
+    X, P = S.prefix_features(G, b, syy)
+    combos = sorted(itertools.combinations(range(9), 3), key=lambda c: (c[2], c[1], c[0]))   # colex
+    assert [tuple(q) for q in P] == combos
+    for row, (p0, p1, p2) in zip(X, combos):
+        p = [p0, p1, p2]
+        tri = [G[p[i], p[j]] if i < 3 and j < 3 else 0.0 for i in range(5) for j in range(i, 5)]
+        cor = [b[p[i]] / np.sqrt(syy) if i < 3 else 0.0 for i in range(5)]
+        np.testing.assert_allclose(row, np.array(tri + cor, dtype=np.float32), rtol=1e-6, atol=1e-7)
+
+
+def test_prefix_labels_match_brute_force(S):
+    G, b, syy, N = _gram_case(1, 11)
+    lab = S.prefix_labels(G, b, syy, N)
+    _, P = S.prefix_features(G, b, syy)
+    sst = syy * N
+    for (p0, p1, p2), got in zip(P, lab):
+        rest = [x for x in range(p2 + 1, 11)]
+        if len(rest) < 2:
+            assert np.isinf(got)
+            continue
+        best = np.inf
+        for i1, i2 in itertools.combinations(rest, 2):
+            E = [p0, p1, p2, i1, i2]
+            w = np.linalg.solve(G[np.ix_(E, E)], b[E])
+            best = min(best, N * (syy - b[E] @ w))
+        assert got == pytest.approx(best / sst, rel=1e-3, abs=1e-5)
+
+
+@pytest.mark.parametrize("n,seed", [(24, 2), (31, 3)])
+def test_learned_search_at_full_fraction_is_exhaustive(S, orc, n, seed):
+    """Taking every prefix, the pruned search is the exhaustive search, whatever the network."""
+    G, b, syy, N = _gram_case(seed, n)
+    gid = np.random.default_rng(seed).permutation(10 * n)[:n]
+    pos_ref, rss_ref, _ = orc.l0(G, b, syy, N, 5, gid)
+    net = S.MLP(seed)
+    X = np.random.default_rng(0).uniform(1, 2, size=(N, 2))
+    with S.Sisso(X, np.arange(N, dtype=float), S.OP_ADD, 1, 2, 1) as c:
+        pos, rss, ex, npre = c.l0_learned(G, b, syy, gid, net, 1.0)
+    assert sorted(pos) == sorted(pos_ref)
+    assert rss == pytest.approx(rss_ref, rel=1e-9, abs=1e-9 * syy * N)
+    assert ex == math.comb(n, 5)
+    net.close()
+
+
+def test_training_gains_over_untrained_network(S):
+    """A network trained on the method's own exhaustive results ranks prefixes better than
+    the same network untrained: at 1% of the subsets it finds the exhaustive optimum more
+    often on held-out problems."""
+    from paper_2410_01752_gb300 import inputs, proposal
+    X, t = proposal.training_set(120, k=30, per_problem=512, top=64, seed=0)
+    trained, loss = proposal.train(X, t, seed=0, epochs=10, batch=1024, lr=2e-3)
+    untrained = S.MLP(0)
+    probs = [inputs.workload4(p, held_out=True) for p in range(8)]
+    hits_t = hits_u = 0
+    for P in probs:
+        with S.Sisso(P.X, P.y, P.op_set, P.rung, 24, 5, precision=S.PREC_FP32) as c:
+            d = c.fit()
+            if len(d) < 5:
+                continue
+            Sids = sum((c.sis(q) for q in range(1, 6)), [])
+            G, b, syy = c.subspace_gram(Sids)
+            pos_ex, _, _ = c.l0_search(G, b, syy, 5, Sids, S.PREC_FP32)
+            pt = c.l0_learned(G, b, syy, Sids, trained, 0.01)[0]
+            pu = c.l0_learned(G, b, syy, Sids, untrained, 0.01)[0]
+            hits_t += sorted(pt) == sorted(pos_ex)
+            hits_u += sorted(pu) == sorted(pos_ex)
+    assert hits_t >= hits_u
+    assert hits_t >= 4
+    trained.close()
+    untrained.close()

@@ -144,7 +144,8 @@ def _gram_case(seed, n, N=200, collinear=False):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n,D,seed,col", [(20, 1, 0, False), (40, 2, 1, False), (60, 3, 2, False),
                                           (45, 4, 3, False), (33, 3, 4, True), (30, 4, 5, True),
-                                          (4, 4, 6, False), (97, 2, 7, True)])
+                                          (4, 4, 6, False), (97, 2, 7, True), (24, 5, 8, False),
+                                          (31, 5, 9, True), (5, 5, 10, False)])
 def test_l0_search(S, orc, n, D, seed, col, prec):
     G, b, syy, N = _gram_case(seed, n, collinear=col)
     gid = np.random.default_rng(seed + 50).permutation(10 * n)[:n]
