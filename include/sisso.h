@@ -337,10 +337,11 @@ sisso_status sisso_fit_batch(const sisso_task* tasks, int n_tasks, uint32_t op_s
  * {p0 < p1 < p2} (p = positions in the screened subspace) by its prediction of the lowest
  * RSS/SST (log10) among the 5-subsets that extend them with higher positions; the best
  * prefixes are taken until their extensions make up a fraction of C(n, 5), and only those
- * are solved, exactly.  The network: SISSO_MLP_IN inputs (the upper triangle of the 5 x 5
- * standardised sub-Gram in row order, then the 5 correlations with the target; entries of
- * features a prefix lacks are 0), two hidden layers of SISSO_MLP_HIDDEN with ReLU, one
- * output; BF16 weights, activations and gradients with FP32 accumulation on the tensor
+ * are solved, exactly.  The network: SISSO_MLP_IN inputs describing a candidate 5-subset
+ * (the upper triangle of its 5 x 5 standardised sub-Gram in row order, then its 5
+ * correlations with the target); a prefix is described by its greedy completion (the
+ * feature above p2 that lowers its RSS most, then the next such feature; slots of features
+ * that do not exist are 0).  Two hidden layers of SISSO_MLP_HIDDEN with ReLU, one output; BF16 weights, activations and gradients with FP32 accumulation on the tensor
  * cores, FP32 master weights, MSE loss, Adam.  The paper has no counterpart; exhaustive
  * search (sisso_l0_search) remains the fallback and the judge.
  *
@@ -370,7 +371,8 @@ sisso_status sisso_mlp_train(sisso_mlp* mlp, const float* X, const float* t, int
                              float lr, uint64_t seed, float* final_loss);
 
 /* Network inputs of every 3-prefix of n standardised features (G n x n, b, syy as for
- * sisso_l0_search), prefixes in colex order (rank C(p2,3) + C(p1,2) + p0): out HOST,
+ * sisso_l0_search), prefixes in colex order (rank C(p2,3) + C(p1,2) + p0), each described by
+ * its greedy completion (computed in FP32): out HOST,
  * C(n,3) x SISSO_MLP_IN floats; prefixes (may be NULL) HOST, C(n,3) x 3 positions. */
 sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes);
 /* Training labels: per 3-prefix (same order), the lowest FP32 RSS / SST over the 5-subsets

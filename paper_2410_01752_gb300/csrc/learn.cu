@@ -8,9 +8,10 @@
 // enumeration with FP64 confirmation as the full search).  The full search stays the
 // fallback and the judge.
 //
-// The network: 20 inputs (the upper triangle of the 5 x 5 standardised sub-Gram in row
-// order and the 5 correlations with the target; for a prefix, the entries of the missing
-// features are 0), two hidden layers of 256 with ReLU, one output.  Weights are FP32 masters
+// The network: 20 inputs describing a candidate 5-subset (the upper triangle of its 5 x 5
+// standardised sub-Gram in row order and its 5 correlations with the target); for a prefix
+// the candidate is the prefix completed greedily by the two features that lower its RSS
+// most.  Two hidden layers of 256 with ReLU, one output.  Weights are FP32 masters
 // with BF16 copies; activations and gradients are BF16; products accumulate in FP32.  The
 // three 256-wide contractions of a step (forward H1 W2^T, backward dZ2 W2 and dZ2^T H1) and
 // the input layer (K padded to 64) run on the tcgen05 tensor cores: C = A B^T with A and B
@@ -217,8 +218,7 @@ __global__ void k_head_bwd(const __nv_bfloat16* __restrict__ H2, const float* __
     for (int r = blockIdx.x * nw + w; r < B; r += gridDim.x * nw) {
         const float e = out[r] - t[r];
         const float d = 2.f * e / (float)B;
-        gb += d;
-        ls += e * e;
+        if (lane == 0) { gb += d; ls += e * e; }    // once per row
         for (int j = lane; j < kHid; j += 32) {
             const float h = __bfloat162float(H2[(size_t)r * kHid + j]);
             atomicAdd(&gw[j], d * h);
@@ -338,20 +338,83 @@ __device__ __forceinline__ void prefix_of(int64_t r, int& p0, int& p1, int& p2) 
     p0 = (int)(r - c2(q));
 }
 
-// network inputs of every 3-prefix (colex rank r): the upper triangle of the 5 x 5 sub-Gram
-// in row order with rows/columns 3, 4 empty, then the correlations b_i / sqrt(syy) (i < 3)
+// Greedy completion of a prefix: with E the current positions (m of them) and L, w its
+// Cholesky factor and forward solution, adding feature j lowers RSS / N by c_j^2 / d_j with
+// v = L^-1 G[E][j], d_j = G[j][j] - |v|^2, c_j = b[j] - v . w.  Returns the j > lo that
+// lowers it most (-1 if none) and extends L, w by it.
+template <int M>
+__device__ __forceinline__ int greedy_next(const double* __restrict__ G, const double* __restrict__ b, int n,
+                                           const int (&E)[5], float (&L)[5][5], float (&w)[5], int lo, int skip) {
+    int best = -1;
+    float best_gain = -1.f, bv[5] = {0, 0, 0, 0, 0}, bd = 1.f, bc = 0.f;
+    for (int j = lo + 1; j < n; ++j) {
+        if (j == skip) continue;
+        float v[5];
+        float d = (float)G[(size_t)j * n + j], c = (float)b[j];
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            float x = (float)G[(size_t)E[q] * n + j];
+#pragma unroll
+            for (int r = 0; r < q; ++r) x -= L[q][r] * v[r];
+            v[q] = x / L[q][q];
+            d -= v[q] * v[q];
+            c -= v[q] * w[q];
+        }
+        if (!(d > 1e-6f)) continue;
+        const float gain = c * c / d;
+        if (gain > best_gain) {
+            best_gain = gain; best = j; bd = d; bc = c;
+#pragma unroll
+            for (int q = 0; q < M; ++q) bv[q] = v[q];
+        }
+    }
+    if (best >= 0) {
+#pragma unroll
+        for (int q = 0; q < M; ++q) L[M][q] = bv[q];
+        L[M][M] = sqrtf(bd);
+        w[M] = bc / L[M][M];
+    }
+    return best;
+}
+
+// network inputs of every 3-prefix (colex rank r): the prefix completed greedily by the two
+// features that lower its RSS most (positions above p2), as a candidate 5-subset
+// E = (p0, p1, p2, j1, j2): the upper triangle of its standardised sub-Gram in row order,
+// then its correlations b_i / sqrt(syy).  A prefix without two such features keeps zeros
+// in the missing slots (it has no extension either).
 __global__ void k_prefix_features(const double* __restrict__ G, const double* __restrict__ b, double inv_sy, int n,
                                   int64_t n_pre, float* __restrict__ X, int* __restrict__ plist) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_pre; r += (int64_t)gridDim.x * blockDim.x) {
-        int p[3];
-        prefix_of(r, p[0], p[1], p[2]);
+        int E[5] = {0, 0, 0, -1, -1};
+        prefix_of(r, E[0], E[1], E[2]);
+        // Cholesky of the prefix (FP32; a singular prefix gets no completion)
+        float L[5][5] = {}, w[5] = {};
+        bool ok = true;
+        for (int q = 0; q < 3 && ok; ++q) {
+            float d = (float)G[(size_t)E[q] * n + E[q]];
+            for (int m = 0; m < q; ++m) d -= L[q][m] * L[q][m];
+            if (!(d > 1e-6f)) { ok = false; break; }
+            L[q][q] = sqrtf(d);
+            for (int i = q + 1; i < 3; ++i) {
+                float x = (float)G[(size_t)E[i] * n + E[q]];
+                for (int m = 0; m < q; ++m) x -= L[i][m] * L[q][m];
+                L[i][q] = x / L[q][q];
+            }
+            float v = (float)b[E[q]];
+            for (int m = 0; m < q; ++m) v -= L[q][m] * w[m];
+            w[q] = v / L[q][q];
+        }
+        if (ok) {
+            E[3] = greedy_next<3>(G, b, n, E, L, w, E[2], -1);
+            if (E[3] >= 0) E[4] = greedy_next<4>(G, b, n, E, L, w, E[2], E[3]);
+        }
         float* x = X + r * kIn;
         int q = 0;
         for (int i = 0; i < 5; ++i)
             for (int j = i; j < 5; ++j, ++q)
-                x[q] = (i < 3 && j < 3) ? (float)G[(size_t)p[i] * n + p[j]] : 0.f;
-        for (int i = 0; i < 5; ++i) x[15 + i] = i < 3 ? (float)(b[p[i]] * inv_sy) : 0.f;
-        if (plist) { plist[3 * r] = p[0]; plist[3 * r + 1] = p[1]; plist[3 * r + 2] = p[2]; }
+                x[q] = (E[i] >= 0 && E[j] >= 0) ? (float)G[(size_t)E[i] * n + E[j]] : 0.f;
+        for (int i = 0; i < 5; ++i) x[15 + i] = E[i] >= 0 ? (float)(b[E[i]] * inv_sy) : 0.f;
+        if (plist) { plist[3 * r] = E[0]; plist[3 * r + 1] = E[1]; plist[3 * r + 2] = E[2]; }
     }
 }
 
@@ -408,12 +471,14 @@ __global__ void k_wsel_hist(const float* __restrict__ score, const int* __restri
         if (h[i]) atomicAdd(&hist[pass * 2048 + i], h[i]);
 }
 
-// state: [0] prefix bits, [1..2] weight still to take (uint64), [3] threshold key
+// state (32-bit words): [0] prefix bits, [1] threshold key, [2..3] weight still to take
+// (one 64-bit value, 8-byte aligned), [4] compacted count
 __global__ void k_wsel_find(const unsigned long long* __restrict__ hist, int pass, unsigned* state,
                             unsigned long long budget) {
     if (threadIdx.x != 0) return;
+    unsigned long long* rest = reinterpret_cast<unsigned long long*>(state + 2);
     const int nb = pass == 2 ? 1024 : 2048;
-    unsigned long long need = pass == 0 ? budget : *reinterpret_cast<unsigned long long*>(state + 1);
+    const unsigned long long need = pass == 0 ? budget : *rest;
     unsigned long long cum = 0;
     int bin = nb - 1;
     for (int q = 0; q < nb; ++q) {
@@ -424,14 +489,14 @@ __global__ void k_wsel_find(const unsigned long long* __restrict__ hist, int pas
     const unsigned pre = pass == 0 ? (unsigned)bin : pass == 1 ? ((state[0] << 11) | (unsigned)bin)
                                                                : ((state[0] << 10) | (unsigned)bin);
     state[0] = pre;
-    *reinterpret_cast<unsigned long long*>(state + 1) = need > cum ? need - cum : 0;
-    if (pass == 2) state[3] = pre;
+    *rest = need > cum ? need - cum : 0;
+    if (pass == 2) state[1] = pre;
 }
 
 __global__ void k_wsel_compact(const float* __restrict__ score, const int* __restrict__ plist, int64_t n_pre,
                                const unsigned* __restrict__ state, int* __restrict__ out, unsigned* __restrict__ count,
                                int64_t cap, unsigned long long* __restrict__ taken) {
-    const unsigned thr = state[3];
+    const unsigned thr = state[1];
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_pre; r += (int64_t)gridDim.x * blockDim.x) {
         if (fkey32(score[r]) <= thr) {
             const unsigned slot = atomicAdd(count, 1u);

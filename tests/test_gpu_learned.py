@@ -110,15 +110,40 @@ def _gram_case(seed, n, N=300):
     return Z.T @ Z / N, Z.T @ yc / N, float(yc @ yc) / N, N
 
 
+def _q(G, b, E):
+    E = list(E)
+    return float(b[E] @ np.linalg.solve(G[np.ix_(E, E)], b[E]))
+
+
+def _greedy(G, b, E, lo, skip=-1):
+    """The feature above lo that raises b_E^T G_E^-1 b_E most (lowers the RSS most)."""
+    best, gain = -1, -1.0
+    for j in range(lo + 1, len(b)):
+        if j == skip:
+            continue
+        g = _q(G, b, list(E) + [j]) - _q(G, b, E)
+        if g > gain:
+            best, gain = j, g
+    return best
+
+
 def test_prefix_features_and_order(S):
-    G, b, syy, N = _gram_case(0, 9)
+    n = 11
+    G, b, syy, N = _gram_case(0, n)
     X, P = S.prefix_features(G, b, syy)
-    combos = sorted(itertools.combinations(range(9), 3), key=lambda c: (c[2], c[1], c[0]))   # colex
+    combos = sorted(itertools.combinations(range(n), 3), key=lambda c: (c[2], c[1], c[0]))   # colex
     assert [tuple(q) for q in P] == combos
     for row, (p0, p1, p2) in zip(X, combos):
-        p = [p0, p1, p2]
-        tri = [G[p[i], p[j]] if i < 3 and j < 3 else 0.0 for i in range(5) for j in range(i, 5)]
-        cor = [b[p[i]] / np.sqrt(syy) if i < 3 else 0.0 for i in range(5)]
+        E = [p0, p1, p2]
+        j1 = _greedy(G, b, E, p2)
+        if j1 >= 0:
+            E.append(j1)
+            j2 = _greedy(G, b, E, p2, skip=j1)
+            if j2 >= 0:
+                E.append(j2)
+        E += [-1] * (5 - len(E))
+        tri = [G[E[i], E[j]] if E[i] >= 0 and E[j] >= 0 else 0.0 for i in range(5) for j in range(i, 5)]
+        cor = [b[E[i]] / np.sqrt(syy) if E[i] >= 0 else 0.0 for i in range(5)]
         np.testing.assert_allclose(row, np.array(tri + cor, dtype=np.float32), rtol=1e-6, atol=1e-7)
 
 
