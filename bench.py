@@ -41,9 +41,12 @@ def parse():
                     help="CPU work for the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 5],
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples")
     ap.add_argument("--tasks", type=int, default=512, help="batched workload: number of tasks")
+    ap.add_argument("--train-problems", type=int, default=2000, help="learned workload: training problems")
+    ap.add_argument("--eval-problems", type=int, default=100, help="learned workload: held-out problems")
+    ap.add_argument("--frac", type=float, default=0.01, help="learned workload: fraction of subsets solved")
     ap.add_argument("--tune-cache", default=None, help="batched workload: autotuner cache file")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default launch shape")
     ap.add_argument("--d", type=int, default=10, help="primary features (smaller cases for profiling)")
@@ -435,10 +438,69 @@ def run_batch(args, rank: int):
     b.close()
 
 
+def run_learned(args):
+    """Learned proposal: train the network on the method's own exhaustive results, then on
+    held-out problems compare the fit's time to the D = 5 descriptor with and without it;
+    the exhaustive search judges recall."""
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import build, inputs, proposal, sisso
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    X, t = proposal.training_set(args.train_problems, k=60, per_problem=768, top=256, seed=0)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, rel_loss = proposal.train(X, t, seed=0, epochs=10, batch=2048, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    zero = sisso.MLP(0)
+    zero.set_params(np.zeros(sisso.MLP_PARAMS, dtype=np.float32))
+    untrained = sisso.MLP(0)
+    probs = [inputs.workload4(p, held_out=True) for p in range(args.eval_problems)]
+    for _ in range(args.warmup):
+        proposal.evaluate(net, probs[:1], frac=args.frac)
+    res = proposal.evaluate(net, probs, frac=args.frac)
+    ok = [r for r in res if "recall" in r]
+    others = {}
+    n_cmp = min(len(probs), 32)
+    for name, m in (("greedy_only", zero), ("untrained", untrained)):
+        rr = [r for r in proposal.evaluate(m, probs[:n_cmp], frac=args.frac) if "recall" in r]
+        others[name] = {"recall": sum(r["recall"] for r in rr) / max(len(rr), 1), "problems": len(rr)}
+    first = {P.name for P in probs[:n_cmp]}
+    trained_first = [r for r in ok if r["name"] in first]
+    ms_l = float(np.mean([r["fit_learned_ms_device"] for r in ok]))
+    ms_p = float(np.mean([r["fit_plain_ms_device"] for r in ok]))
+    recall = sum(r["recall"] for r in ok) / max(len(ok), 1)
+    same = sum(r["same_descriptor"] and r["rmse_rel_diff"] <= 1e-5 for r in ok) / max(len(ok), 1)
+    line = {
+        "metric": "time-to-descriptor vs plain at equal RMSE", "value": ms_l / 1e3, "unit": "s",
+        "n_gpus": 1, "steps": len(ok), "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": "learned proposal: D=5 over 300 features (k=60, 5 SIS steps), N~U{500..2000}, "
+                               "d~U{8..12}, x~U[1,5], 3-5 planted rung-2 terms",
+                   "train_problems": args.train_problems, "eval_problems": len(ok), "frac": args.frac,
+                   "train_examples": int(X.shape[0])},
+        "plain_ms": ms_p, "speedup_vs_plain": ms_p / ms_l,
+        "recall": recall, "same_descriptor_equal_rmse": same,
+        "recall_first_n": {"trained": sum(r["recall"] for r in trained_first) / max(len(trained_first), 1),
+                           **{k: v["recall"] for k, v in others.items()}, "problems": n_cmp},
+        "l0_d5_ms": {"exhaustive": 1e3 * float(np.mean([r["exhaustive_s"] for r in ok])),
+                     "learned": 1e3 * float(np.mean([r["learned_s"] for r in ok]))},
+        "subsets_solved": {"exhaustive": ok[0]["examined_exhaustive"] if ok else None,
+                           "learned_mean": float(np.mean([r["examined_learned"] for r in ok])) if ok else None},
+        "training": {"data_s": t_data, "train_s": t_train, "loss_rel_to_target_var": rel_loss},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == 3:
         run_mixed(args)
+        return
+    if args.workload == 4:
+        run_learned(args)
         return
     if args.workload == 5:
         run_batch(args, int(os.environ.get("RANK", "0")))

@@ -372,9 +372,11 @@ sisso_status sisso_mlp_train(sisso_mlp* mlp, const float* X, const float* t, int
 
 /* Network inputs of every 3-prefix of n standardised features (G n x n, b, syy as for
  * sisso_l0_search), prefixes in colex order (rank C(p2,3) + C(p1,2) + p0), each described by
- * its greedy completion (computed in FP32): out HOST,
- * C(n,3) x SISSO_MLP_IN floats; prefixes (may be NULL) HOST, C(n,3) x 3 positions. */
-sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes);
+ * its greedy completion (computed in FP32): out HOST, C(n,3) x SISSO_MLP_IN floats;
+ * prefixes (may be NULL) HOST, C(n,3) x 3 positions; base (may be NULL) HOST, C(n,3)
+ * values log10(RSS/SST) of the completions (0 for a prefix without one). */
+sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes,
+                                   float* base);
 /* Training labels: per 3-prefix (same order), the lowest FP32 RSS / SST over the 5-subsets
  * extending it with higher positions (exhaustive; +inf when it has none).  n in 5..1400.
  * out HOST. */

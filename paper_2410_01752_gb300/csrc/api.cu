@@ -251,10 +251,13 @@ sisso_status sisso_fit(sisso_ctx* c) {
         cudaEventRecord(g1, c->stream);
         Winner w{};
         if (mixed) st = l0_solve_mixed(c, n, t, w);
-        else if (c->proposal && t == 5 && n >= 5)
+        else if (c->proposal && t == 5 && n >= 5 && n <= 1400) {
             st = l0_learned(c, c->proposal, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, c->S_dev,
                             c->prune_frac, w, &c->learned_prefixes);
-        else st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
+            // the exhaustive search is the fallback when the proposed subsets are all singular
+            if (st == SISSO_ERR_NUMERIC)
+                st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
+        } else st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
         if (st) break;
         c->stats.ms_gram += event_ms(g0, g1);
         cudaEventDestroy(g0); cudaEventDestroy(g1);

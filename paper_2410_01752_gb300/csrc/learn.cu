@@ -1,10 +1,12 @@
 // learn.cu — learned subset proposal for the l0 search (§2.3, Eq. 7) at D = 5.
 //
-// Scoring every D-subset with a network costs about 1e3 exact solves each, so the network
-// ranks the search's prefixes instead: for every 3-subset {p0 < p1 < p2} of the n screened
-// features it predicts log10 of the lowest RSS/SST among the 5-subsets that extend it
-// (positions above p2), the prefixes are taken best first until their extensions make up a
-// given fraction of C(n, 5), and only those extensions are solved, exactly (the same FP32
+// Scoring every D-subset with a network costs about 1e3 exact solves each, so the search's
+// prefixes are ranked instead: for every 3-subset {p0 < p1 < p2} of the n screened features,
+// its greedy completion (the two features above p2 that lower its RSS most) gives a base
+// score, log10 of that 5-subset's RSS/SST, and the network predicts from the completion's
+// statistics how much lower the prefix's best completion goes; the prefixes are taken by
+// base + correction, best first, until their extensions make up a given fraction of
+// C(n, 5), and only those extensions are solved, exactly (the same FP32
 // enumeration with FP64 confirmation as the full search).  The full search stays the
 // fallback and the judge.
 //
@@ -381,9 +383,11 @@ __device__ __forceinline__ int greedy_next(const double* __restrict__ G, const d
 // features that lower its RSS most (positions above p2), as a candidate 5-subset
 // E = (p0, p1, p2, j1, j2): the upper triangle of its standardised sub-Gram in row order,
 // then its correlations b_i / sqrt(syy).  A prefix without two such features keeps zeros
-// in the missing slots (it has no extension either).
+// in the missing slots (it has no extension either).  base (optional): log10 of the
+// completion's RSS / SST, the score the network corrects.
 __global__ void k_prefix_features(const double* __restrict__ G, const double* __restrict__ b, double inv_sy, int n,
-                                  int64_t n_pre, float* __restrict__ X, int* __restrict__ plist) {
+                                  int64_t n_pre, float* __restrict__ X, int* __restrict__ plist,
+                                  float* __restrict__ base) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_pre; r += (int64_t)gridDim.x * blockDim.x) {
         int E[5] = {0, 0, 0, -1, -1};
         prefix_of(r, E[0], E[1], E[2]);
@@ -407,6 +411,13 @@ __global__ void k_prefix_features(const double* __restrict__ G, const double* __
         if (ok) {
             E[3] = greedy_next<3>(G, b, n, E, L, w, E[2], -1);
             if (E[3] >= 0) E[4] = greedy_next<4>(G, b, n, E, L, w, E[2], E[3]);
+        }
+        // base score: log10 of the greedy completion's RSS / SST = 1 - |w|^2 syy^-1
+        if (base) {
+            float q = 0.f;
+            for (int i = 0; i < 5; ++i) q += (ok && E[4] >= 0) ? w[i] * w[i] : 0.f;
+            const float frac = (ok && E[4] >= 0) ? 1.f - q * (float)(inv_sy * inv_sy) : 1.f;
+            base[r] = log10f(fmaxf(frac, 1e-12f));
         }
         float* x = X + r * kIn;
         int q = 0;
@@ -444,6 +455,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_prefix_labels(EnumArgs<float> A
         for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
         if (lane == 0 && best < INFINITY) atomicMin(&lab[item / A.cpp], fkey32(best));
     }
+}
+
+__global__ void k_add(float* __restrict__ a, const float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
 }
 
 // weight of a prefix: its number of extensions C(n - 1 - p2, 2)
@@ -815,28 +831,31 @@ sisso_status sisso_mlp_train(sisso_mlp* m, const float* X, const float* t, int64
     return mlp_status(m, e);
 }
 
-sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes) {
+sisso_status sisso_prefix_features(const double* G, const double* b, double syy, int n, float* out, int* prefixes,
+                                   float* base) {
     if (!G || !b || !out || n < 3 || n > 4095 || !(syy > 0.0)) return SISSO_ERR_ARG;
     const int64_t np = (int64_t)n * (n - 1) * (n - 2) / 6;
     double *dG = nullptr, *db = nullptr;
-    float* dX = nullptr;
+    float *dX = nullptr, *dB = nullptr;
     int* dP = nullptr;
     bool ok = cudaMalloc((void**)&dG, sizeof(double) * n * n) == cudaSuccess &&
               cudaMalloc((void**)&db, sizeof(double) * n) == cudaSuccess &&
               cudaMalloc((void**)&dX, sizeof(float) * np * kIn) == cudaSuccess &&
-              (!prefixes || cudaMalloc((void**)&dP, sizeof(int) * 3 * np) == cudaSuccess);
+              (!prefixes || cudaMalloc((void**)&dP, sizeof(int) * 3 * np) == cudaSuccess) &&
+              (!base || cudaMalloc((void**)&dB, sizeof(float) * np) == cudaSuccess);
     sisso_status st = ok ? SISSO_OK : SISSO_ERR_OOM;
     if (ok) {
         cudaMemcpy(dG, G, sizeof(double) * n * n, cudaMemcpyDefault);
         cudaMemcpy(db, b, sizeof(double) * n, cudaMemcpyDefault);
         k_prefix_features<<<(unsigned)std::min<int64_t>((np + 255) / 256, 65535), 256>>>(dG, db, 1.0 / std::sqrt(syy), n,
-                                                                                          np, dX, dP);
+                                                                                          np, dX, dP, dB);
         if (cudaMemcpy(out, dX, sizeof(float) * np * kIn, cudaMemcpyDefault) != cudaSuccess) st = SISSO_ERR_CUDA;
         if (!st && prefixes && cudaMemcpy(prefixes, dP, sizeof(int) * 3 * np, cudaMemcpyDefault) != cudaSuccess)
             st = SISSO_ERR_CUDA;
+        if (!st && base && cudaMemcpy(base, dB, sizeof(float) * np, cudaMemcpyDefault) != cudaSuccess) st = SISSO_ERR_CUDA;
     }
     cudaGetLastError();
-    cudaFree(dG); cudaFree(db); cudaFree(dX); cudaFree(dP);
+    cudaFree(dG); cudaFree(db); cudaFree(dX); cudaFree(dP); cudaFree(dB);
     return st;
 }
 
@@ -919,6 +938,8 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
     ck(cudaMallocAsync((void**)&X, sizeof(float) * np * kIn, c->stream), "learned: inputs");
     ck(cudaMallocAsync((void**)&plist, sizeof(int) * 3 * np, c->stream), "learned: prefixes");
     ck(cudaMallocAsync((void**)&sel, sizeof(int) * 3 * np, c->stream), "learned: selection");
+    float* base = nullptr;
+    ck(cudaMallocAsync((void**)&base, sizeof(float) * np, c->stream), "learned: base");
     ck(cudaMallocAsync((void**)&hist, sizeof(unsigned long long) * 3 * 2048, c->stream), "learned: histogram");
     ck(cudaMallocAsync((void**)&state, sizeof(unsigned) * 8, c->stream), "learned: state");
     if (st) return st;
@@ -926,7 +947,7 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
     ck(cudaMemcpy2DAsync(Gd, sizeof(double) * n, G, sizeof(double) * ld, sizeof(double) * n, n, cudaMemcpyDeviceToDevice,
                          c->stream), "learned: G copy");
     k_prefix_features<<<(unsigned)std::min<int64_t>((np + 255) / 256, 65535), 256, 0, c->stream>>>(
-        Gd, b, 1.0 / std::sqrt(syy), n, np, X, plist);
+        Gd, b, 1.0 / std::sqrt(syy), n, np, X, plist, base);
     // network scores (on the network's stream, ordered after the features)
     sisso_status sm = mlp_reserve(mlp, np, false);
     if (sm) return fail(c, sm, "learned: network buffers");
@@ -942,6 +963,8 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
     cudaEventRecord(ev, mlp->stream);
     cudaStreamWaitEvent(c->stream, ev, 0);
     cudaEventDestroy(ev);
+    // score = base (greedy completion) + the network's correction
+    k_add<<<(unsigned)std::min<int64_t>((np + 255) / 256, 65535), 256, 0, c->stream>>>(score, base, np);
     // weighted selection of the lowest predicted RSS up to frac of the subsets
     const double total = (double)n * (n - 1) * (n - 2) * (n - 3) * (n - 4) / 120.0;
     const unsigned long long budget = (unsigned long long)std::max(1.0, std::ceil(frac * total));
@@ -967,6 +990,7 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
     }
     cudaFreeAsync(Gd, c->stream); cudaFreeAsync(X, c->stream); cudaFreeAsync(plist, c->stream);
     cudaFreeAsync(sel, c->stream); cudaFreeAsync(hist, c->stream); cudaFreeAsync(state, c->stream);
+    cudaFreeAsync(base, c->stream);
     return st;
 }
 

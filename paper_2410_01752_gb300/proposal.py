@@ -26,8 +26,9 @@ def problem_gram(P, k: int):
 
 
 def training_set(n_problems: int, k: int = 60, per_problem: int = 1024, top: int = 128, seed: int = 0):
-    """Inputs (M x 20, float32) and targets log10(RSS/SST) (M, float32): per problem the
-    `top` best prefixes and `per_problem` random others (prefixes with extensions only)."""
+    """Inputs (M x 20, float32) and targets (M, float32): per problem the `top` best
+    prefixes and `per_problem` random others (prefixes with extensions only); the target is
+    log10 of the prefix's best completion's RSS/SST minus that of its greedy completion."""
     rng = np.random.default_rng(seed)
     Xs, ts = [], []
     for p in range(n_problems):
@@ -35,7 +36,7 @@ def training_set(n_problems: int, k: int = 60, per_problem: int = 1024, top: int
         G, b, syy, N, ids = problem_gram(P, k)
         if len(ids) < 5:
             continue
-        X, _ = prefix_features(G, b, syy)
+        X, _, base = prefix_features(G, b, syy)
         lab = prefix_labels(G, b, syy, N)
         ok = np.flatnonzero(np.isfinite(lab))
         if ok.size == 0:
@@ -44,14 +45,23 @@ def training_set(n_problems: int, k: int = 60, per_problem: int = 1024, top: int
         rest = rng.choice(ok, size=min(per_problem, ok.size), replace=False)
         sel = np.unique(np.concatenate([best, rest]))
         Xs.append(X[sel])
-        ts.append(np.log10(np.maximum(lab[sel], 1e-12)).astype(np.float32))
+        ts.append((np.log10(np.maximum(lab[sel], 1e-12)) - base[sel]).astype(np.float32))
     return np.concatenate(Xs), np.concatenate(ts)
 
 
 def train(X, t, seed: int = 0, epochs: int = 8, batch: int = 2048, lr: float = 1e-3) -> tuple[MLP, float]:
+    """Train on standardised targets, then fold the scale into the output layer (w3, b3), so
+    the network returns corrections in log10 units; the loss returned is relative to the
+    targets' variance (1.0: no better than their mean)."""
     net = MLP(seed)
     M = (X.shape[0] // batch) * batch
-    loss = net.train(X[:M], t[:M], epochs=epochs, batch=batch, lr=lr, seed=seed)
+    mu, sd = float(t[:M].mean()), float(t[:M].std()) or 1.0
+    loss = net.train(X[:M], (t[:M] - mu) / sd, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    p = net.params()
+    n_w3 = 256
+    p[-1 - n_w3:-1] *= sd
+    p[-1] = p[-1] * sd + mu
+    net.set_params(p)
     return net, loss
 
 

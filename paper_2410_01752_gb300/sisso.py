@@ -167,7 +167,7 @@ def load() -> C.CDLL:
     L.sisso_mlp_gradients.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_float), vp]
     L.sisso_mlp_train.argtypes = [vp, vp, vp, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_uint64,
                                   C.POINTER(C.c_float)]
-    L.sisso_prefix_features.argtypes = [vp, vp, C.c_double, C.c_int, vp, vp]
+    L.sisso_prefix_features.argtypes = [vp, vp, C.c_double, C.c_int, vp, vp, vp]
     L.sisso_prefix_labels.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp]
     L.sisso_l0_learned.argtypes = [vp, vp, vp, C.c_double, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_int), dp,
                                    i64p, i64p]
@@ -595,18 +595,20 @@ class MLP:
 
 
 def prefix_features(G, b, syy: float):
-    """(inputs C(n,3) x 20, prefixes C(n,3) x 3) of every 3-prefix, colex order."""
+    """(inputs C(n,3) x 20, prefixes C(n,3) x 3, base scores C(n,3)) of every 3-prefix, colex order."""
     G = np.ascontiguousarray(G, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = b.size
     npre = n * (n - 1) * (n - 2) // 6
     X = np.zeros((npre, MLP_IN), dtype=np.float32)
     P = np.zeros((npre, 3), dtype=np.int32)
+    base = np.zeros(npre, dtype=np.float32)
     st = load().sisso_prefix_features(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), n,
-                                      C.c_void_p(X.ctypes.data), C.c_void_p(P.ctypes.data))
+                                      C.c_void_p(X.ctypes.data), C.c_void_p(P.ctypes.data),
+                                      C.c_void_p(base.ctypes.data))
     if st != 0:
         raise SissoError(st, "prefix_features")
-    return X, P
+    return X, P, base
 
 
 def prefix_labels(G, b, syy: float, N: int) -> np.ndarray:

@@ -130,7 +130,7 @@ def _greedy(G, b, E, lo, skip=-1):
 def test_prefix_features_and_order(S):
     n = 11
     G, b, syy, N = _gram_case(0, n)
-    X, P = S.prefix_features(G, b, syy)
+    X, P, base = S.prefix_features(G, b, syy)
     combos = sorted(itertools.combinations(range(n), 3), key=lambda c: (c[2], c[1], c[0]))   # colex
     assert [tuple(q) for q in P] == combos
     for row, (p0, p1, p2) in zip(X, combos):
@@ -141,6 +141,8 @@ def test_prefix_features_and_order(S):
             j2 = _greedy(G, b, E, p2, skip=j1)
             if j2 >= 0:
                 E.append(j2)
+        want_base = np.log10(max(1.0 - _q(G, b, E) / syy, 1e-12)) if len(E) == 5 else 0.0
+        assert base[combos.index((p0, p1, p2))] == pytest.approx(want_base, abs=2e-4)
         E += [-1] * (5 - len(E))
         tri = [G[E[i], E[j]] if E[i] >= 0 and E[j] >= 0 else 0.0 for i in range(5) for j in range(i, 5)]
         cor = [b[E[i]] / np.sqrt(syy) if E[i] >= 0 else 0.0 for i in range(5)]
@@ -150,7 +152,7 @@ def test_prefix_features_and_order(S):
 def test_prefix_labels_match_brute_force(S):
     G, b, syy, N = _gram_case(1, 11)
     lab = S.prefix_labels(G, b, syy, N)
-    _, P = S.prefix_features(G, b, syy)
+    _, P, _ = S.prefix_features(G, b, syy)
     sst = syy * N
     for (p0, p1, p2), got in zip(P, lab):
         rest = [x for x in range(p2 + 1, 11)]
@@ -182,15 +184,15 @@ def test_learned_search_at_full_fraction_is_exhaustive(S, orc, n, seed):
 
 
 def test_training_gains_over_untrained_network(S):
-    """A network trained on the method's own exhaustive results ranks prefixes better than
-    the same network untrained: at 1% of the subsets it finds the exhaustive optimum more
-    often on held-out problems."""
+    """A network trained on the method's own exhaustive results ranks prefixes at least as
+    well as the same network untrained, and the pruned search (1% of the subsets) finds the
+    exhaustive optimum on almost every held-out problem."""
     from paper_2410_01752_gb300 import inputs, proposal
     X, t = proposal.training_set(120, k=30, per_problem=512, top=64, seed=0)
-    trained, loss = proposal.train(X, t, seed=0, epochs=10, batch=1024, lr=2e-3)
+    trained, loss = proposal.train(X, t, seed=0, epochs=10, batch=1024, lr=1e-3)
     untrained = S.MLP(0)
     probs = [inputs.workload4(p, held_out=True) for p in range(8)]
-    hits_t = hits_u = 0
+    hits_t = hits_u = evaluated = 0
     for P in probs:
         with S.Sisso(P.X, P.y, P.op_set, P.rung, 24, 5, precision=S.PREC_FP32) as c:
             d = c.fit()
@@ -203,7 +205,9 @@ def test_training_gains_over_untrained_network(S):
             pu = c.l0_learned(G, b, syy, Sids, untrained, 0.01)[0]
             hits_t += sorted(pt) == sorted(pos_ex)
             hits_u += sorted(pu) == sorted(pos_ex)
+            evaluated += 1
+    assert evaluated >= 6
     assert hits_t >= hits_u
-    assert hits_t >= 4
+    assert hits_t >= evaluated - 1
     trained.close()
     untrained.close()
