@@ -40,18 +40,19 @@ constexpr int kInPad = 64;                 // K of the input layer (one 128-byte
 constexpr int kHid = SISSO_MLP_HIDDEN;     // 256
 constexpr int GT = 128;                    // output tile (M = N = 128)
 constexpr int GBK = 64;                    // K per stage
-constexpr int GST = 4;                     // stages
+constexpr int GST = 2;                     // stages (2 CTAs per SM)
 constexpr int kGemmThreads = 128;
-constexpr uint32_t kGTile = GT * GBK * 2;  // 16 KB
 
 // parameter layout (FP32 masters): W1 [256 x 20], b1 [256], W2 [256 x 256], b2 [256], w3 [256], b3
 constexpr int oW1 = 0, oB1 = oW1 + kHid * kIn, oW2 = oB1 + kHid, oB2 = oW2 + kHid * kHid, oW3 = oB2 + kHid,
               oB3 = oW3 + kHid, kParams = oB3 + 1;
 static_assert(kParams == SISSO_MLP_PARAMS, "parameter layout");
 
+// one CTA: a 128 x BN output tile over all of K, in 64-wide stages through a 2-slot ring
+template <int BN>
 struct GemmSmem {
-    uint8_t a[GST][kGTile];
-    uint8_t b[GST][kGTile];
+    uint8_t a[GST][GT * GBK * 2];
+    uint8_t b[GST][BN * GBK * 2];
     uint64_t full[GST], empty[GST], done;
     uint32_t tmem_base;
 };
@@ -65,7 +66,7 @@ struct GemmArgs {
     // EPI_F32
     float* C;
     int ldc;
-    int cols;                 // valid output columns
+    int cols;                 // valid output columns (a multiple of 32)
     // EPI_RELU
     const float* bias;
     __nv_bfloat16* H;         // rows x ldh
@@ -76,12 +77,17 @@ struct GemmArgs {
     uint32_t idesc;
 };
 
-// C[M x N] = A[M x K] B[N x K]^T, one 128 x 128 tile per CTA
-template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+// C[M x N] = A[M x K] B[N x K]^T: warp 0 streams the A and B tiles of each K stage with TMA,
+// warp 1 issues tcgen05.mma (M = 128, N = BN, K = 16) into a BN-column TMEM accumulator,
+// all four warps read it back (warp w: rows 32w..32w+31) and store it, each lane writing
+// its row's 32 consecutive values with 16-byte stores
+template <int EPI, int BN>
+__global__ void __launch_bounds__(kGemmThreads, 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, GemmArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    GemmSmem& S = *reinterpret_cast<GemmSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    using SM = GemmSmem<BN>;
+    SM& S = *reinterpret_cast<SM*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t kA = GT * GBK * 2, kB = BN * GBK * 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ti = blockIdx.x % A.m_tiles, tj = blockIdx.x / A.m_tiles;
     const int nk = A.nk;
@@ -92,7 +98,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
-                     "r"(128)
+                     "r"(BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -109,9 +115,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
             const int s = ks % GST;
             const uint32_t ph = (uint32_t)(ks / GST) & 1u;
             if (ks >= GST && !mbar_wait(&S.empty[s], ph ^ 1u)) { failed = 1; break; }
-            mbar_expect_tx(&S.full[s], 2 * kGTile);
+            mbar_expect_tx(&S.full[s], kA + kB);
             tma_load_2d(S.a[s], &map_a, ks * GBK, ti * GT, &S.full[s]);
-            tma_load_2d(S.b[s], &map_b, ks * GBK, tj * GT, &S.full[s]);
+            tma_load_2d(S.b[s], &map_b, ks * GBK, tj * BN, &S.full[s]);
             ++issued;
         }
         if (failed)
@@ -141,29 +147,40 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
     } else {
         const int row = ti * GT + warp * 32 + lane;
 #pragma unroll 1
-        for (int cb = 0; cb < GT / 32; ++cb) {
+        for (int cb = 0; cb < BN / 32; ++cb) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
-            const int col0 = tj * GT + cb * 32;
+            const int col0 = tj * BN + cb * 32;
             if (EPI == EPI_F32) {
-                if (row < A.rows)
+                if (row < A.rows && col0 < A.cols) {
+                    float4* dst = reinterpret_cast<float4*>(A.C + (size_t)row * A.ldc + col0);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (col0 + q < A.cols) A.C[(size_t)row * A.ldc + col0 + q] = __uint_as_float(r[q]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const float h = fmaxf(__uint_as_float(r[q]) + A.bias[col0 + q], 0.f);
-                    const __nv_bfloat16 hb = __float2bfloat16(row < A.rows ? h : 0.f);
-                    A.H[(size_t)row * A.ldh + col0 + q] = hb;
-                    if (A.HT) A.HT[(size_t)(col0 + q) * A.ldt + row] = hb;   // lanes = rows: coalesced
+                    for (int q = 0; q < 8; ++q)
+                        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                             __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
                 }
+            } else {
+                uint32_t pk[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float h0 = row < A.rows ? fmaxf(__uint_as_float(r[2 * q]) + A.bias[col0 + 2 * q], 0.f) : 0.f;
+                    const float h1 = row < A.rows ? fmaxf(__uint_as_float(r[2 * q + 1]) + A.bias[col0 + 2 * q + 1], 0.f) : 0.f;
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(h0, h1);
+                    pk[q] = *reinterpret_cast<const uint32_t*>(&hb);
+                    if (A.HT) {
+                        A.HT[(size_t)(col0 + 2 * q) * A.ldt + row] = hb.x;       // lanes = rows: coalesced
+                        A.HT[(size_t)(col0 + 2 * q + 1) * A.ldt + row] = hb.y;
+                    }
+                }
+                uint4* dst = reinterpret_cast<uint4*>(A.H + (size_t)row * A.ldh + col0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 // ---------------------------------------------------------------------------------
@@ -528,36 +545,40 @@ __global__ void k_wsel_compact(const float* __restrict__ score, const int* __res
 // ---------------------------------------------------------------------------------
 // host: GEMM launch
 // ---------------------------------------------------------------------------------
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t gstride[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {GBK, GT};
+    const cuuint32_t box[2] = {GBK, (cuuint32_t)box_rows};
     const cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// C = A B^T with A [Mpad x K], B [Npad x K] (BF16, row-major = K-major); M, N multiples of 128
+template <int EPI, int BN>
+cudaError_t gemm_launch(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g,
+                        int64_t grid) {
+    const size_t smem = sizeof(GemmSmem<BN>) + 1024;
+    cudaFuncSetAttribute(k_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gemm_tc<EPI, BN><<<(unsigned)grid, kGemmThreads, smem, st>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
+// C = A B^T with A [Mpad x K], B [Npad x K] (BF16, row-major = K-major); M, N multiples of
+// 128; tiles 128 x 256 when N is a multiple of 256
 cudaError_t gemm(cudaStream_t st, const __nv_bfloat16* Am, int64_t Mpad, const __nv_bfloat16* Bm, int64_t Npad, int K,
                  int epi, GemmArgs g) {
+    const int bn = Npad % 256 == 0 ? 256 : GT;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Am, Mpad, K) || !make_map(&mb, Bm, Npad, K)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, Am, Mpad, K, GT) || !make_map(&mb, Bm, Npad, K, bn)) return cudaErrorInvalidValue;
     g.nk = K / GBK;
     g.m_tiles = (int)(Mpad / GT);
-    g.idesc = idesc_f16(1u, GT, GT);
-    const size_t smem = sizeof(GemmSmem) + 1024;
-    const int64_t grid = (Mpad / GT) * (Npad / GT);
-    if (epi == EPI_F32) {
-        cudaFuncSetAttribute(k_gemm_tc<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gemm_tc<EPI_F32><<<(unsigned)grid, kGemmThreads, smem, st>>>(ma, mb, g);
-    } else {
-        cudaFuncSetAttribute(k_gemm_tc<EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_gemm_tc<EPI_RELU><<<(unsigned)grid, kGemmThreads, smem, st>>>(ma, mb, g);
-    }
-    return cudaGetLastError();
+    g.idesc = idesc_f16(1u, GT, bn);
+    const int64_t grid = (Mpad / GT) * (Npad / bn);
+    if (epi == EPI_F32) return bn == 256 ? gemm_launch<EPI_F32, 256>(st, ma, mb, g, grid) : gemm_launch<EPI_F32, GT>(st, ma, mb, g, grid);
+    return bn == 256 ? gemm_launch<EPI_RELU, 256>(st, ma, mb, g, grid) : gemm_launch<EPI_RELU, GT>(st, ma, mb, g, grid);
 }
 
 int64_t pad128(int64_t m) { return (m + GT - 1) / GT * GT; }
