@@ -184,44 +184,51 @@ __global__ void k_score_cached_w(const T* __restrict__ cache, int N, int64_t P, 
     if (lane == 0) scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
 }
 
-// per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) and AR[f] = sum_s (x_fs - x_f0) r_s
-// in FP64, with r the centred target the pair kernel uses.  For + and - the pair kernel's
-// sums of v' = (a - a0) +/- (b - b0) and of v' r follow from these exactly.
-template <typename T>
+// per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) (when A1ON) and AR[f] =
+// sum_s (x_fs - x_f0) r_s, with r the centred target the pair kernel uses.  For + and - the
+// pair kernel's sums of v' = (a - a0) +/- (b - b0) and of v' r follow from these.  Products
+// and runs of 32 samples are summed in T (FP32 for the FP32 screening: the FP32 pipe, not the
+// 64x slower FP64 one), the runs in FP64.  A1 does not depend on the target: computed once.
+template <typename T, bool A1ON>
 __global__ void k_opsums(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
                          double* __restrict__ A1, double* __restrict__ AR) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= P) return;
     const T* tc = TgtView<T>::tc(tc32, tc64);
-    const double x0 = (double)cache[f];
+    const T x0 = cache[f];
     double a = 0.0, ar = 0.0;
-    for (int s = 0; s < N; ++s) {
-        const double v = (double)cache[(size_t)s * P + f] - x0;
-        a += v;
-        ar += v * (double)tc[s];
+    for (int s0 = 0; s0 < N; s0 += 32) {
+        const int e = s0 + 32 < N ? s0 + 32 : N;
+        T pa = T(0), pr = T(0);
+        for (int s = s0; s < e; ++s) {
+            const T v = cache[(size_t)s * P + f] - x0;
+            if (A1ON) pa += v;
+            pr = fma(v, tc[s], pr);
+        }
+        a += (double)pa;
+        ar += (double)pr;
     }
-    A1[f] = a;
+    if (A1ON) A1[f] = a;
     AR[f] = ar;
 }
 
 // the same with one warp per operand
-template <typename T>
+template <typename T, bool A1ON>
 __global__ void k_opsums_w(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
                            double* __restrict__ A1, double* __restrict__ AR) {
     const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (f >= P) return;
     const T* tc = TgtView<T>::tc(tc32, tc64);
-    const double x0 = (double)cache[f];
-    double a = 0.0, ar = 0.0;
+    const T x0 = cache[f];
+    T pa = T(0), pr = T(0);
     for (int s = lane; s < N; s += 32) {
-        const double v = (double)cache[(size_t)s * P + f] - x0;
-        a += v;
-        ar += v * (double)tc[s];
+        const T v = cache[(size_t)s * P + f] - x0;
+        if (A1ON) pa += v;
+        pr = fma(v, tc[s], pr);
     }
-    a = warp_sum(a);
-    ar = warp_sum(ar);
-    if (lane == 0) { A1[f] = a; AR[f] = ar; }
+    const double a = warp_sum((double)pa), ar = warp_sum((double)pr);
+    if (lane == 0) { if (A1ON) A1[f] = a; AR[f] = ar; }
 }
 
 // the top level's unary sections with one warp per candidate (few operands, many samples)
@@ -405,7 +412,7 @@ __global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int
 // then only reads the confirmed pairs.
 // ---------------------------------------------------------------------------------
 constexpr double kDupScore = 2e-8;
-constexpr int kConfirm = 2;             // partner slots confirmed ahead of the walk
+constexpr int kConfirm = 8;             // partner slots confirmed ahead of the walk
 constexpr int kMaxRefs = 2048;          // slow path: S members / accepted ids gathered per round
 
 __device__ __forceinline__ bool probes_match(const double* a, const double* b) {
@@ -849,13 +856,21 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         if (cached) {
             const bool few = A.P < 65536;
             const int go = few ? (int)((A.P * 32 + 255) / 256) : (int)((A.P + 255) / 256);
-            if (fp64) {
-                if (few) k_opsums_w<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
-                else k_opsums<double><<<go, 256, 0, c->stream>>>(c->opcache64, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
-            } else {
-                if (few) k_opsums_w<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
-                else k_opsums<float><<<go, 256, 0, c->stream>>>(c->opcache32, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P);
-            }
+            const bool a1 = c->opsum_prec != (fp64 ? 0 : 1);   // A1 of this cache not yet computed
+#define SG_OPSUMS(TT, CACHE)                                                                                   \
+    do {                                                                                                       \
+        if (few) {                                                                                             \
+            if (a1) k_opsums_w<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+            else k_opsums_w<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+        } else {                                                                                               \
+            if (a1) k_opsums<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+            else k_opsums<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+        }                                                                                                      \
+    } while (0)
+            if (fp64) SG_OPSUMS(double, c->opcache64);
+            else SG_OPSUMS(float, c->opcache32);
+#undef SG_OPSUMS
+            c->opsum_prec = fp64 ? 0 : 1;
             c->stats.launches++;
             A1 = c->opsum;
             AR = c->opsum + A.P;

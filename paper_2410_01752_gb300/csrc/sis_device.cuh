@@ -4,6 +4,8 @@
 
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace sg {
 namespace {
 
@@ -369,6 +371,30 @@ __device__ __forceinline__ void rescore_one(const Space* sp, const double* Xc, i
 }
 
 
+// paired FP32 arithmetic (two lanes of FP32 in one 64-bit register, one instruction for both)
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 f2pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2up(f2 x, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x)); }
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // One 32 x 32 tile of operand pairs (i0.., j0..): stage operands chunk by chunk, accumulate
 // the shifted sums of + - * a/b b/a for 4 pairs per thread, write the scores.  Called by
 // every thread of an 8-warp CTA; S is that CTA's shared memory.
@@ -424,6 +450,24 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         for (int o = 0; o < 3; ++o) { s1[o][q] = T(0); s2[o][q] = T(0); sr[o][q] = T(0); }
     }
 
+    // FP32 with per-operand sums: the same sums kept in pairs of i operands (q, q + 1), two FP32
+    // lanes per register (fma/add/sub.f32x2: half the FP32 instructions to issue)
+    constexpr bool kPair = std::is_same<T, float>::value && LIN;
+    constexpr int RH = RI / 2;
+    f2 Q2[2][RH], L1[2][RH], LR[2][RH], S1[3][RH], S2[3][RH], SR[3][RH], NKM[RH], NKD[RH], NKE[RH];
+    if constexpr (kPair) {
+#pragma unroll
+        for (int h = 0; h < RH; ++h) {
+            const f2 z = f2pk(0.f, 0.f);
+            Q2[0][h] = Q2[1][h] = L1[0][h] = L1[1][h] = LR[0][h] = LR[1][h] = z;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) { S1[o][h] = z; S2[o][h] = z; SR[o][h] = z; }
+            NKM[h] = f2pk(-(float)Km[2 * h], -(float)Km[2 * h + 1]);
+            NKD[h] = f2pk(-(float)Kd[2 * h], -(float)Kd[2 * h + 1]);
+            NKE[h] = f2pk(-(float)Ke[2 * h], -(float)Ke[2 * h + 1]);
+        }
+    }
+
     T pf[kStageSlots], py[kStageSlots / 2];
     stage_load<T>(A, Xc, cache, tc, S, i0, j0, 0, g, lane, pf, py);
     stage_store<T>(S, 0, pf, py, g, lane);
@@ -435,6 +479,26 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         const PairBuf<T>& B = S.buf[b];
         const int ns = min(TS, N - s0);
         auto step = [&](int s) {
+            if constexpr (kPair) {
+                const Quad<T> bq = B.bq[s][lane];
+                const f2 r2 = f2pk((float)bq.y, (float)bq.y), bt2 = f2pk((float)bq.t, (float)bq.t);
+                const f2 bv2 = f2pk((float)bq.v, (float)bq.v), br2 = f2pk((float)bq.r, (float)bq.r);
+                const ulonglong2 at = *reinterpret_cast<const ulonglong2*>(&B.at[s][g * RI]);
+                const ulonglong2 av = *reinterpret_cast<const ulonglong2*>(&B.av[s][g * RI]);
+                const ulonglong2 ar = *reinterpret_cast<const ulonglong2*>(&B.ar[s][g * RI]);
+                const f2 atp[RH] = {at.x, at.y}, avp[RH] = {av.x, av.y}, arp[RH] = {ar.x, ar.y};
+#pragma unroll
+                for (int h = 0; h < RH; ++h) {
+                    f2 v;
+                    v = f2add(atp[h], bt2);           Q2[0][h] = f2fma(v, v, Q2[0][h]);
+                    if constexpr (!LIN) { L1[0][h] = f2add(L1[0][h], v); LR[0][h] = f2fma(v, r2, LR[0][h]); }
+                    v = f2sub(atp[h], bt2);           Q2[1][h] = f2fma(v, v, Q2[1][h]);
+                    if constexpr (!LIN) { L1[1][h] = f2add(L1[1][h], v); LR[1][h] = f2fma(v, r2, LR[1][h]); }
+                    v = f2fma(avp[h], bv2, NKM[h]);   S1[0][h] = f2add(S1[0][h], v); S2[0][h] = f2fma(v, v, S2[0][h]); SR[0][h] = f2fma(v, r2, SR[0][h]);
+                    v = f2fma(avp[h], br2, NKD[h]);   S1[1][h] = f2add(S1[1][h], v); S2[1][h] = f2fma(v, v, S2[1][h]); SR[1][h] = f2fma(v, r2, SR[1][h]);
+                    v = f2fma(bv2, arp[h], NKE[h]);   S1[2][h] = f2add(S1[2][h], v); S2[2][h] = f2fma(v, v, S2[2][h]); SR[2][h] = f2fma(v, r2, SR[2][h]);
+                }
+            } else {
             const Quad<T> bq = B.bq[s][lane];
             const T r = bq.y, bt = bq.t, bv = bq.v, br = bq.r;
             T at[RI], av[RI], ar[RI];
@@ -452,6 +516,7 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
                 v = fma(av[q], br, -Kd[q]); s1[1][q] += v; s2[1][q] = fma(v, v, s2[1][q]); sr[1][q] = fma(v, r, sr[1][q]);
                 v = fma(bv, ar[q], -Ke[q]); s1[2][q] += v; s2[2][q] = fma(v, v, s2[2][q]); sr[2][q] = fma(v, r, sr[2][q]);
             }
+            }
         };
         if (ns == TS) {
 #pragma unroll 4
@@ -461,6 +526,25 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         }
         if (more) stage_store<T>(S, b ^ 1, pf, py, g, lane);
         __syncthreads();
+    }
+
+    if constexpr (kPair) {
+#pragma unroll
+        for (int h = 0; h < RH; ++h) {
+            float a, b;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                f2up(Q2[o][h], a, b); q2[o][2 * h] = a; q2[o][2 * h + 1] = b;
+                f2up(L1[o][h], a, b); l1[o][2 * h] = a; l1[o][2 * h + 1] = b;
+                f2up(LR[o][h], a, b); lr[o][2 * h] = a; lr[o][2 * h + 1] = b;
+            }
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                f2up(S1[o][h], a, b); s1[o][2 * h] = a; s1[o][2 * h + 1] = b;
+                f2up(S2[o][h], a, b); s2[o][2 * h] = a; s2[o][2 * h + 1] = b;
+                f2up(SR[o][h], a, b); sr[o][2 * h] = a; sr[o][2 * h + 1] = b;
+            }
+        }
     }
 
     // scores of the (up to) 20 candidates of this thread
