@@ -280,7 +280,7 @@ __device__ __forceinline__ void enum_item(const EnumArgs<T>& A, T* tab, int64_t 
         T dp = A.G[(size_t)x * A.ld + x], np = A.b[x];
 #pragma unroll
         for (int m = 0; m < DP; ++m) {
-            T v = A.G[(size_t)x * A.ld + pre[m]];
+            T v = A.G[(size_t)pre[m] * A.ld + x];        // G symmetric: row pre[m], lanes coalesced
 #pragma unroll
             for (int q = 0; q < m; ++q) v -= r[q] * L[m][q];
             r[m] = v * invd[m];
@@ -292,82 +292,104 @@ __device__ __forceinline__ void enum_item(const EnumArgs<T>& A, T* tab, int64_t 
         npart[x] = np;
     }
     __syncwarp();
-    for (int i1 = i1s; i1 < i1e; ++i1) {
-        T r1[DP > 0 ? DP : 1];
+    // RB rows i1 per pass over i2: the i2 tables are read once for RB subsets and RB
+    // independent loads of G are in flight
+    constexpr int RB = 4;
+    for (int i1b = i1s; i1b < i1e; i1b += RB) {
+        T r1[RB][DP > 0 ? DP : 1], isd1[RB], w1[RB], base_c[RB], c_cmp[RB];
+        bool ok1[RB], live[RB];
 #pragma unroll
-        for (int m = 0; m < DP; ++m) r1[m] = Rt[(size_t)m * n + i1];
-        const T d1 = dpart[i1];
-        const bool ok1 = pre_ok && d1 > T(A.tau);
-        if (!A.fp32 && !ok1) continue;
-        const T isd1 = T(1) / sqrt(d1 > T(0) ? d1 : T(1));
-        const T w1 = npart[i1] * isd1;
-        const T base_c = A.syy - (pw2 + w1 * w1);
-        // rss < best (MODE 0) or rss <= thr_eff (MODE 1)  <=>  num^2 - c d2 > 0 (>= 0)
-        T c_cmp = MODE == 0 ? base_c - best / N : base_c - thr_eff / N;
-        const T* Grow = A.G + (size_t)i1 * A.ld;
-        for (int i2 = i1 + 1 + lane; i2 < n; i2 += 32) {
+        for (int k = 0; k < RB; ++k) {
+            const int i1 = i1b + k;
+            live[k] = i1 < i1e;
+            const int ic = live[k] ? i1 : i1s;
+#pragma unroll
+            for (int m = 0; m < DP; ++m) r1[k][m] = Rt[(size_t)m * n + ic];
+            const T d1 = dpart[ic];
+            ok1[k] = pre_ok && d1 > T(A.tau);
+            if (!A.fp32 && !ok1[k]) live[k] = false;          // FP64: singular, every extension skipped
+            isd1[k] = T(1) / sqrt(d1 > T(0) ? d1 : T(1));
+            w1[k] = npart[ic] * isd1[k];
+            base_c[k] = A.syy - (pw2 + w1[k] * w1[k]);
+            // rss < best (MODE 0) or rss <= thr_eff (MODE 1)  <=>  num^2 - c d2 > 0 (>= 0)
+            c_cmp[k] = MODE == 0 ? base_c[k] - best / N : base_c[k] - thr_eff / N;
+        }
+        for (int i2 = i1b + 1 + lane; i2 < n; i2 += 32) {
             T rt[DP > 0 ? DP : 1];
-            T g = Grow[i2];
 #pragma unroll
-            for (int m = 0; m < DP; ++m) { rt[m] = Rt[(size_t)m * n + i2]; g -= r1[m] * rt[m]; }
-            const T rr = g * isd1;
-            const T d2 = dpart[i2] - rr * rr;
-            const T num = npart[i2] - rr * w1;
-            if (!ok1 || !(d2 > T(A.tau))) {
-                // flagged by a pivot: the FP32 factor says nothing; FP64 decides (pass 2)
-                if (MODE == 1 && A.fp32) {
+            for (int m = 0; m < DP; ++m) rt[m] = Rt[(size_t)m * n + i2];
+            const T dp2 = dpart[i2], np2 = npart[i2];
+            T gk[RB];
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                gk[k] = (live[k] && i2 > i1b + k) ? A.G[(size_t)(i1b + k) * A.ld + i2] : T(0);
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                if (!live[k] || i2 <= i1b + k) continue;
+                const int i1 = i1b + k;
+                T g = gk[k];
+#pragma unroll
+                for (int m = 0; m < DP; ++m) g -= r1[k][m] * rt[m];
+                const T rr = g * isd1[k];
+                const T d2 = dp2 - rr * rr;
+                const T num = np2 - rr * w1[k];
+                if (!ok1[k] || !(d2 > T(A.tau))) {
+                    // flagged by a pivot: the FP32 factor says nothing; FP64 decides (pass 2)
+                    if (MODE == 1 && A.fp32) {
+                        int pos[DP + 2];
+#pragma unroll
+                        for (int m = 0; m < DP; ++m) pos[m] = pre[m];
+                        pos[DP] = i1;
+                        pos[DP + 1] = i2;
+                        if (!keep_flagged(A, pos, DP + 2, thr)) continue;
+                        const unsigned slot = atomicAdd(A.band_count, 1u);
+                        if (slot < A.band_cap) {
+                            A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                            if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
+                        }
+                    }
+                    continue;
+                }
+                const T f = num * num - c_cmp[k] * d2;
+                if (MODE == 0) {
+                    if (!(f > T(0))) continue;
+                    best = N * (base_c[k] - num * num / d2);
+                    best_key = pack_subset<DP>(pre, i1, i2);
+#pragma unroll
+                    for (int kk = 0; kk < RB; ++kk) c_cmp[kk] = base_c[kk] - best / N;
+                    continue;
+                }
+                const T rss = N * (base_c[k] - num * num / d2);
+                if (!(f >= T(0))) {
+                    if (!apost) continue;
+                    // back substitution L^T gamma = w, then the a posteriori bound
+                    const T g2 = num / d2;
+                    const T g1 = (w1[k] - rr * g2) * isd1[k];
+                    T sg = fabs(g2) + fabs(g1);
+                    T gp[DP > 0 ? DP : 1];
+#pragma unroll
+                    for (int j = DP - 1; j >= 0; --j) {
+                        T v = wv[j] - r1[k][j] * g1 - rt[j] * g2;
+#pragma unroll
+                        for (int m = j + 1; m < DP; ++m) v -= L[m][j] * gp[m];
+                        gp[j] = v * invd[j];
+                        sg += fabs(gp[j]);
+                    }
+                    if (!(rss - apost_err(A, DP + 2, sg, rss) <= thr_eff)) continue;
+                }
+                if (apost) {
                     int pos[DP + 2];
 #pragma unroll
                     for (int m = 0; m < DP; ++m) pos[m] = pre[m];
                     pos[DP] = i1;
                     pos[DP + 1] = i2;
                     if (!keep_flagged(A, pos, DP + 2, thr)) continue;
-                    const unsigned slot = atomicAdd(A.band_count, 1u);
-                    if (slot < A.band_cap) {
-                        A.band[slot] = pack_subset<DP>(pre, i1, i2);
-                        if (A.band_r32) A.band_r32[slot] = __int_as_float(0x7fc00000);
-                    }
                 }
-                continue;
-            }
-            const T f = num * num - c_cmp * d2;
-            if (MODE == 0) {
-                if (!(f > T(0))) continue;
-                best = N * (base_c - num * num / d2);
-                best_key = pack_subset<DP>(pre, i1, i2);
-                c_cmp = base_c - best / N;
-                continue;
-            }
-            const T rss = N * (base_c - num * num / d2);
-            if (!(f >= T(0))) {
-                if (!apost) continue;
-                // back substitution L^T gamma = w, then the a posteriori bound
-                const T g2 = num / d2;
-                const T g1 = (w1 - rr * g2) * isd1;
-                T s = fabs(g2) + fabs(g1);
-                T gp[DP > 0 ? DP : 1];
-#pragma unroll
-                for (int j = DP - 1; j >= 0; --j) {
-                    T v = wv[j] - r1[j] * g1 - rt[j] * g2;
-#pragma unroll
-                    for (int m = j + 1; m < DP; ++m) v -= L[m][j] * gp[m];
-                    gp[j] = v * invd[j];
-                    s += fabs(gp[j]);
+                const unsigned slot = atomicAdd(A.band_count, 1u);
+                if (slot < A.band_cap) {
+                    A.band[slot] = pack_subset<DP>(pre, i1, i2);
+                    if (A.band_r32) A.band_r32[slot] = (float)rss;
                 }
-                if (!(rss - apost_err(A, DP + 2, s, rss) <= thr_eff)) continue;
-            }
-            if (apost) {
-                int pos[DP + 2];
-#pragma unroll
-                for (int m = 0; m < DP; ++m) pos[m] = pre[m];
-                pos[DP] = i1;
-                pos[DP + 1] = i2;
-                if (!keep_flagged(A, pos, DP + 2, thr)) continue;
-            }
-            const unsigned slot = atomicAdd(A.band_count, 1u);
-            if (slot < A.band_cap) {
-                A.band[slot] = pack_subset<DP>(pre, i1, i2);
-                if (A.band_r32) A.band_r32[slot] = (float)rss;
             }
         }
     }
