@@ -415,7 +415,7 @@ def run_batch(args, rank: int):
     # the screening stage alone: its flops over its share of the SMs' time (CTA-time / CTAs per SM)
     score_sm_s = st["stage_ms"][3] / 1e3 / (st["grid"] / sms)
     roof["score_stage_frac"] = flop / (score_sm_s / sms) / 1e12 / peak if score_sm_s > 0 else None
-    names = ["-", "start", "level", "score", "gram", "bound", "band", "flat", "select", "refit", "idle", "-",
+    names = ["-", "start", "level", "score", "gram", "bound", "band", "flat", "select", "refit", "idle", "opsum",
              "select.radix", "select.rescore", "select.sort", "select.walk"]
     line = {
         "metric": "tasks/s", "value": value, "unit": "tasks/s", "n_gpus": 1, "steps": args.steps,

@@ -273,7 +273,7 @@ typedef struct {
     int64_t walk_checks;        /* ... full duplicate comparisons */
     /* device-clock profile of the last run, per stage: 0 unused, 1 start, 2 level, 3 score,
        4 gram, 5 bound, 6 band, 7 validity flattening, 8 select, 9 refit, 10 waiting for
-       work, 11 unused, and the parts of select: 12 radix select, 13 FP64 re-score, 14 sort,
+       work, 11 per-operand sums, and the parts of select: 12 radix select, 13 FP64 re-score, 14 sort,
        15 walk.  stage_ms sums the CTAs' time, stage_max_ms is the longest single
        occurrence, stage_count the occurrences. */
     double stage_ms[16];

@@ -49,9 +49,9 @@ constexpr int kZRaw = 512;                       // window entries whose FP64 va
 constexpr unsigned long long kIdleNs = 10000000000ull;  // 10 s with no progress anywhere: give up
 constexpr unsigned long long kExit = ~0ull;
 
-enum : int { WK_NONE = 0, WK_START, WK_LEVEL, WK_SCORE, WK_GRAM, WK_BOUND, WK_BAND };
+enum : int { WK_NONE = 0, WK_START, WK_LEVEL, WK_SCORE, WK_GRAM, WK_BOUND, WK_BAND, WK_OPSUM = 11 };
 // stage ids of the profile counters (parallel items by kind; serial stages after them)
-enum : int { PS_FLAT = 7, PS_SELECT = 8, PS_REFIT = 9, PS_IDLE = 10, PS_PUSH = 11,
+enum : int { PS_FLAT = 7, PS_SELECT = 8, PS_REFIT = 9, PS_IDLE = 10,
              PS_SEL_RADIX = 12, PS_SEL_RESCORE = 13, PS_SEL_SORT = 14, PS_SEL_WALK = 15 };
 
 __device__ __forceinline__ void prof_add(const unsigned long long* prof_c, int s, unsigned long long dt) {
@@ -99,6 +99,7 @@ struct BDim {
     uint64_t* band;             // l0 band (band_cap)
     double* band_rss;
     double* resid;              // residual of the step-t model (N)
+    double* AR;                 // per operand: sum_s (x_s - x_0) r_s with r the step-t target (P)
 };
 
 // per task, written by the host at creation
@@ -122,6 +123,7 @@ struct BTask {
     double* yc;                 // y - mean(y)
     double* Z;                  // standardised subspace members (kMaxSub rows, stride ldv)
     double* zraw;               // FP64 values of the first kZRaw window entries (stride N)
+    double* A1;                 // per operand: sum_s (x_s - x_0) (P), written with the step-1 sums
     BDim dim[kMaxDim + 1];      // index t = 1..max_dim
 };
 
@@ -407,6 +409,33 @@ __device__ __noinline__ void run_flat(const BTask& T) {
 }
 
 // ---------------------------------------------------------------------------------
+// OPSUM: per-operand sums for the pair tiles' + and - (256 operands per item), FP32 runs of
+// 32 samples accumulated in FP64
+// ---------------------------------------------------------------------------------
+__device__ __noinline__ void run_opsum(const BatchArgs& B, int task, int t, long long q) {
+    const BTask& T = B.tasks[task];
+    const BDim& D = T.dim[t];
+    const int64_t f = q * kBT + threadIdx.x;
+    if (f >= T.P) return;
+    const float x0 = T.cache[f];
+    const int N = T.N;
+    double a = 0.0, ar = 0.0;
+    for (int s0 = 0; s0 < N; s0 += 32) {
+        const int e = s0 + 32 < N ? s0 + 32 : N;
+        float pa = 0.f, pr = 0.f;
+        for (int sidx = s0; sidx < e; ++sidx) {
+            const float v = T.cache[(size_t)sidx * T.P + f] - x0;
+            pa += v;
+            pr = fmaf(v, D.tc32[sidx], pr);
+        }
+        a += (double)pa;
+        ar += (double)pr;
+    }
+    if (t == 1) T.A1[f] = a;
+    D.AR[f] = ar;
+}
+
+// ---------------------------------------------------------------------------------
 // SCORE: units [u0, u1) of step t
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ void run_score(const BatchArgs& B, int task, int t, long long q, unsigned char* smem) {
@@ -427,7 +456,7 @@ __device__ __forceinline__ void run_score(const BatchArgs& B, int task, int t, l
             PairArgs A = T.pa;
             A.scores = D.scores;
             const int2 tl = T.tiles[u - T.n_low - T.n_un];
-            pair_tile<float, false>(A, nullptr, D.tc32, D.tc64, D.ts, T.valid, T.cache, nullptr, nullptr,
+            pair_tile<float, true>(A, nullptr, D.tc32, D.tc64, D.ts, T.valid, T.cache, T.A1, D.AR,
                                     *reinterpret_cast<PairSmem<float>*>(smem), tl.x, tl.y);
             __syncthreads();
         }
@@ -1001,7 +1030,7 @@ __device__ __noinline__ int run_refit(const BatchArgs& B, Ctl& C, int task, int 
 // ---------------------------------------------------------------------------------
 // stage transitions
 // ---------------------------------------------------------------------------------
-enum : int { NX_LEVEL = 0, NX_SCORE, NX_SELECT, NX_BOUND, NX_BAND, NX_REFIT };
+enum : int { NX_LEVEL = 0, NX_SCORE, NX_SELECT, NX_BOUND, NX_BAND, NX_REFIT, NX_OPSUM };
 
 // Run serial stages from `next` on and queue the next parallel stage (or finish the task).
 __device__ void advance(const BatchArgs& B, Ctl& C, int task, int next, int t, unsigned char* smem) {
@@ -1018,8 +1047,13 @@ __device__ void advance(const BatchArgs& B, Ctl& C, int task, int next, int t, u
             const unsigned long long f0 = gtimer();
             run_flat(T);
             if (threadIdx.x == 0) prof_add(B.prof, PS_FLAT, gtimer() - f0);
-            next = NX_SCORE;
+            next = NX_OPSUM;
             t = 1;
+            continue;
+        }
+        if (next == NX_OPSUM) {
+            if (T.n_tiles > 0) { push(B, C, task, WK_OPSUM, t, (T.P + kBT - 1) / kBT); return; }
+            next = NX_SCORE;
             continue;
         }
         if (next == NX_SCORE) {
@@ -1063,7 +1097,7 @@ __device__ void advance(const BatchArgs& B, Ctl& C, int task, int next, int t, u
         const BDim& Dn = T.dim[t + 1];
         prepare_target_block(T.dim[t].resid, T.N, Dn.tc64, Dn.tc32, Dn.ts, C.red);
         __syncthreads();
-        next = NX_SCORE;
+        next = NX_OPSUM;
         ++t;
     }
 }
@@ -1096,6 +1130,7 @@ __global__ void __launch_bounds__(kBT, MINB) k_batch(BatchArgs B) {
         if (ldcg_i(&B.state[task].status) == SISSO_OK) {
             if (kind == WK_LEVEL) run_level(B, C, task, t, q, reinterpret_cast<float (*)[33]>(smem));
             else if (kind == WK_SCORE) run_score(B, task, t, q, smem);
+            else if (kind == WK_OPSUM) run_opsum(B, task, t, q);
             else if (kind == WK_GRAM) run_gram(B, task, t, q);
             else run_enum(B, C, task, t, q, kind == WK_BAND, smem);
         }
@@ -1112,6 +1147,7 @@ __global__ void __launch_bounds__(kBT, MINB) k_batch(BatchArgs B) {
         if (!C.flag) continue;
         if (kind == WK_LEVEL) advance(B, C, task, NX_LEVEL, t + 1, smem);
         else if (kind == WK_SCORE) advance(B, C, task, NX_SELECT, t, smem);
+        else if (kind == WK_OPSUM) advance(B, C, task, NX_SCORE, t, smem);
         else if (kind == WK_GRAM) advance(B, C, task, NX_BOUND, t, smem);
         else if (kind == WK_BOUND) advance(B, C, task, NX_BAND, t, smem);
         else advance(B, C, task, NX_REFIT, t, smem);
@@ -1242,6 +1278,7 @@ long long queue_items(const TaskPlan& T, int rung, int k, int max_dim, const sis
     for (int l = 1; l < rung; ++l) n += T.lvl_units[l];
     const int units = T.n_low + T.n_un + T.n_tiles;
     for (int t = 1; t <= max_dim; ++t) {
+        n += (T.P + kBT - 1) / kBT;
         n += (units + tu.score_units - 1) / tu.score_units;
         n += std::max(1, (k + tu.gram_rows - 1) / tu.gram_rows);
         n += 2 * ((enum_total_host(t * k, t) + tu.enum_items - 1) / tu.enum_items);
@@ -1393,11 +1430,12 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
     size_t total = 0;
     auto region = [&](size_t bytes) { const size_t at = total; total += align256(bytes); return at; };
     struct Off {
-        size_t V, cache, vlvl[kMaxRung], valid, yc, Z, zraw;
+        size_t V, cache, vlvl[kMaxRung], valid, yc, Z, zraw, A1;
         size_t scores[kMaxDim + 1], tc64[kMaxDim + 1], tc32[kMaxDim + 1], ts[kMaxDim + 1], w_ids[kMaxDim + 1],
             w_score[kMaxDim + 1], w_mean[kMaxDim + 1], w_sd[kMaxDim + 1], w_valid[kMaxDim + 1], w_probe[kMaxDim + 1],
             gid[kMaxDim + 1], zmean[kMaxDim + 1], zsd[kMaxDim + 1], G64[kMaxDim + 1], b64[kMaxDim + 1],
-            G32[kMaxDim + 1], b32[kMaxDim + 1], band[kMaxDim + 1], band_rss[kMaxDim + 1], resid[kMaxDim + 1];
+            G32[kMaxDim + 1], b32[kMaxDim + 1], band[kMaxDim + 1], band_rss[kMaxDim + 1], resid[kMaxDim + 1],
+            AR[kMaxDim + 1];
     };
     std::vector<Off> off(n_tasks);
     for (int i = 0; i < n_tasks; ++i) {
@@ -1415,6 +1453,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         f.yc = region(sizeof(double) * N);
         f.Z = region(sizeof(double) * ldv * ncap);
         f.zraw = region(sizeof(double) * (size_t)N * kZRaw);
+        f.A1 = region(sizeof(double) * P.P);
         for (int t = 1; t <= max_dim; ++t) {
             const size_t nt = (size_t)t * sis_size;
             f.scores[t] = region(sizeof(float) * P.n_feat);
@@ -1437,6 +1476,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
             f.band[t] = region(sizeof(uint64_t) * b->band_cap);
             f.band_rss[t] = region(sizeof(double) * b->band_cap);
             f.resid[t] = region(sizeof(double) * N);
+            f.AR[t] = region(sizeof(double) * P.P);
         }
     }
     b->arena_bytes = total;
@@ -1505,6 +1545,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         T.yc = reinterpret_cast<double*>(A + f.yc);
         T.Z = reinterpret_cast<double*>(A + f.Z);
         T.zraw = reinterpret_cast<double*>(A + f.zraw);
+        T.A1 = reinterpret_cast<double*>(A + f.A1);
         for (int t = 1; t <= max_dim; ++t) {
             BDim& D = T.dim[t];
             D.scores = reinterpret_cast<float*>(A + f.scores[t]);
@@ -1527,6 +1568,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
             D.band = reinterpret_cast<uint64_t*>(A + f.band[t]);
             D.band_rss = reinterpret_cast<double*>(A + f.band_rss[t]);
             D.resid = reinterpret_cast<double*>(A + f.resid[t]);
+            D.AR = reinterpret_cast<double*>(A + f.AR[t]);
         }
     }
     // longest first: estimated screening work |phi_L| x N
