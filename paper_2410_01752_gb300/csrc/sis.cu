@@ -425,42 +425,76 @@ __device__ __forceinline__ bool probes_match(const double* a, const double* b) {
     return same || flip;
 }
 
+// one warp per sorted entry: the lanes test 32 candidates at a time; matches enter the
+// partner list in the order the serial rule takes them (S members by position, then window
+// entries, whose keys are distinct ids), so the list is the same whatever the lane count
 __global__ void k_dup_find(const double* __restrict__ sk, const int* __restrict__ ssrc,
                            const int64_t* __restrict__ sid, int n_sorted,
                            const double* __restrict__ sv_score, const double* __restrict__ sv_sd,
                            const double* __restrict__ probe, int s_off, int nS, int* __restrict__ dup_list,
                            int* __restrict__ dup_cnt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int64_t s_key[8][kDupSlots];
+    __shared__ int s_val[8][kDupSlots];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (i >= n_sorted) return;
     const double s = sk[i];
-    if (s < 0.0) { dup_cnt[i] = 0; return; }
+    if (s < 0.0) { if (lane == 0) dup_cnt[i] = 0; return; }
     const int src = ssrc[i];
     double pc[kProbes];
 #pragma unroll
     for (int r = 0; r < kProbes; ++r) pc[r] = probe[(size_t)src * kProbes + r];
+    int64_t* key = s_key[wb];
+    int* val = s_val[wb];
     // keep the kDupSlots partners with the smallest keys: S members first (key -1), then
     // window entries by id (a cluster's earliest-visited member is its smallest id)
-    int64_t key[kDupSlots] = {};
-    int val[kDupSlots] = {};
     int n = 0, total = 0;
-    auto consider = [&](int m, int64_t k) {
-        if (!probes_match(pc, probe + (size_t)m * kProbes)) return;
-        ++total;
-        if (n == kDupSlots && k >= key[n - 1]) return;
-        int q = n < kDupSlots ? n++ : n - 1;
-        while (q > 0 && key[q - 1] > k) { key[q] = key[q - 1]; val[q] = val[q - 1]; --q; }
-        key[q] = k;
-        val[q] = m;
+    int64_t last = 0;                                    // key[n - 1] once the list is full
+    auto offer = [&](bool match, int m, int64_t k) {
+        const unsigned all = __ballot_sync(0xffffffffu, match);
+        total += __popc(all);
+        unsigned b = __ballot_sync(0xffffffffu, match && (n < kDupSlots || k < last));
+        while (b) {
+            const int l = __ffs(b) - 1;
+            b &= b - 1;
+            const int64_t kk = __shfl_sync(0xffffffffu, k, l);
+            const int mm = __shfl_sync(0xffffffffu, m, l);
+            if (n == kDupSlots && kk >= last) continue;
+            if (lane == 0) {
+                int q = n < kDupSlots ? n : n - 1;
+                while (q > 0 && key[q - 1] > kk) { key[q] = key[q - 1]; val[q] = val[q - 1]; --q; }
+                key[q] = kk;
+                val[q] = mm;
+            }
+            __syncwarp();
+            if (n < kDupSlots) ++n;
+            last = key[n - 1];
+            __syncwarp();
+        }
     };
-    for (int q = 0; q < nS; ++q) {
-        const int m = s_off + q;
-        if (sv_sd[m] > 0.0 && fabs(sv_score[m] - s) <= kDupScore) consider(m, -1);
+    for (int q0 = 0; q0 < nS; q0 += 32) {
+        const int q = q0 + lane, m = s_off + q;
+        const bool c = q < nS && sv_sd[m] > 0.0 && fabs(sv_score[m] - s) <= kDupScore &&
+                       probes_match(pc, probe + (size_t)m * kProbes);
+        offer(c, m, -1);
     }
-    for (int j = i - 1; j >= 0 && sk[j] - s <= kDupScore; --j) consider(ssrc[j], sid[j]);
-    for (int j = i + 1; j < n_sorted && sk[j] >= 0.0 && s - sk[j] <= kDupScore; ++j) consider(ssrc[j], sid[j]);
-    for (int q = 0; q < n; ++q) dup_list[(size_t)i * kDupSlots + q] = val[q];
+    for (int b0 = 0;; b0 += 32) {                        // higher scores (sorted descending)
+        const int j = i - 1 - b0 - lane;
+        const bool in = j >= 0 && sk[j] - s <= kDupScore;
+        const int mj = in ? ssrc[j] : 0;
+        offer(in && probes_match(pc, probe + (size_t)mj * kProbes), mj, in ? sid[j] : 0);
+        if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;
+    }
+    for (int b0 = 0;; b0 += 32) {                        // lower scores
+        const int j = i + 1 + b0 + lane;
+        const bool in = j < n_sorted && sk[j] >= 0.0 && s - sk[j] <= kDupScore;
+        const int mj = in ? ssrc[j] : 0;
+        offer(in && probes_match(pc, probe + (size_t)mj * kProbes), mj, in ? sid[j] : 0);
+        if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;
+    }
+    if (lane < n) dup_list[(size_t)i * kDupSlots + lane] = val[lane];
     // overflow: n partners kept, more exist (the walk falls back to a full check)
-    dup_cnt[i] = total > kDupSlots ? -n - 1 : n;
+    if (lane == 0) dup_cnt[i] = total > kDupSlots ? -n - 1 : n;
 }
 
 // one warp per sorted entry: every listed partner compared on all samples
@@ -510,24 +544,29 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
 }
 
 // ---------------------------------------------------------------------------------
-// the walk: one CTA.  Thread 0 picks, among the remaining candidates whose score is
-// within kScoreTie of the current maximum, the lowest id, and accepts it unless a
-// confirmed duplicate of it is an S member or an id accepted before it.  Entries whose
-// partner list overflowed are checked by the whole CTA against every S member and
-// accepted id.
+// the walk: one CTA.  Lane 0 of warp 0 picks, among the remaining candidates whose score
+// is within kScoreTie of the current maximum, the lowest id; warp 0 then checks the pick's
+// listed partners in parallel and accepts it unless a confirmed duplicate of it is an S
+// member or an id accepted before it.  Entries whose partner list overflowed are checked by
+// the whole CTA against every S member and accepted id.  When the sorted window fits
+// (kWalkStage entries), its scores, ids, partner counts and the walk's flags are held in
+// shared memory for the walk's dependent reads.
 // ---------------------------------------------------------------------------------
 constexpr int kWalkThreads = 1024;
 constexpr int kHeapCap = 2048;          // tie-window entries held in the shared-memory heap
+constexpr int kWalkStage = 4096;        // sorted entries staged in shared memory
+constexpr size_t kWalkSmem = (size_t)kWalkStage * (sizeof(double) + sizeof(int64_t) + sizeof(int) + 2);
 
 __global__ void __launch_bounds__(kWalkThreads)
-k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk,
-       const int64_t* __restrict__ sid, const int* __restrict__ ssrc, int n_sorted,
+k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk_g,
+       const int64_t* __restrict__ sid_g, const int* __restrict__ ssrc, int n_sorted,
        const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_score,
        const double* __restrict__ sv_mean, const double* __restrict__ sv_sd,
        const double* __restrict__ probe, const double* __restrict__ zc, const double* __restrict__ V,
-       const int* __restrict__ dup_list, const int* __restrict__ dup_cnt, const unsigned char* __restrict__ dup_ok,
-       int s_off, int nS, int k, unsigned char* __restrict__ removed, unsigned char* __restrict__ accepted,
+       const int* __restrict__ dup_list, const int* __restrict__ cnt_g, const unsigned char* __restrict__ dup_ok,
+       int s_off, int nS, int k, unsigned char* __restrict__ removed_g, unsigned char* __restrict__ accepted_g,
        WalkResult* out) {
+    extern __shared__ __align__(16) unsigned char wsm[];
     __shared__ int acc_src[SISSO_MAX_SIS];
     __shared__ int64_t heap_id[kHeapCap];
     __shared__ int heap_ix[kHeapCap];
@@ -536,89 +575,127 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
     __shared__ double red[32];
     __shared__ double cur_score, last_score;
     const int tid = threadIdx.x;
+    // staged copies (the flags start cleared) or the global arrays
+    const bool staged = n_sorted <= kWalkStage && s_off <= kWalkStage;
+    const double* sk = sk_g;
+    const int64_t* sid = sid_g;
+    const int* dup_cnt = cnt_g;
+    unsigned char* removed = removed_g;
+    unsigned char* accepted = accepted_g;
+    if (staged) {
+        double* s_sk = reinterpret_cast<double*>(wsm);
+        int64_t* s_sid = reinterpret_cast<int64_t*>(s_sk + kWalkStage);
+        int* s_cnt = reinterpret_cast<int*>(s_sid + kWalkStage);
+        unsigned char* s_rem = reinterpret_cast<unsigned char*>(s_cnt + kWalkStage);
+        unsigned char* s_acc = s_rem + kWalkStage;
+        for (int q = tid; q < n_sorted; q += blockDim.x) {
+            s_sk[q] = sk_g[q];
+            s_sid[q] = sid_g[q];
+            s_cnt[q] = cnt_g[q];
+            s_rem[q] = 0;
+        }
+        for (int q = tid; q < s_off; q += blockDim.x) s_acc[q] = 0;
+        sk = s_sk; sid = s_sid; dup_cnt = s_cnt; removed = s_rem; accepted = s_acc;
+    }
     if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0; }
-    // thread 0's state: first remaining entry p, window end e, heap of the window's
+    // lane 0's state: first remaining entry p, window end e, heap of the window's
     // remaining entries keyed by id (the window only grows as the maximum falls)
     int p = 0, e = 0, hn = 0;
     __syncthreads();
     while (true) {
-        if (tid == 0) {
-            slow = 0;
-            while (!done && !slow) {
-                while (p < n_sorted && removed[p]) ++p;
-                if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
-                    done = 1;
-                    exhausted = n_acc < k;
-                    break;
-                }
-                const double m = sk[p];
-                if (e < p) e = p;
-                int best = -1;
-                while (e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
-                    if (hn == kHeapCap) break;
-                    int q = hn++;                                  // push (sift up)
-                    const int64_t xid = sid[e];
-                    while (q > 0 && heap_id[(q - 1) >> 1] > xid) {
-                        heap_id[q] = heap_id[(q - 1) >> 1];
-                        heap_ix[q] = heap_ix[(q - 1) >> 1];
-                        q = (q - 1) >> 1;
-                    }
-                    heap_id[q] = xid;
-                    heap_ix[q] = e;
-                    ++e;
-                }
-                if (hn == kHeapCap && e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
-                    // window larger than the heap: plain scan (still exact)
-                    best = p;
-                    for (int q = p; q < n_sorted && sk[q] >= m - kScoreTie; ++q)
-                        if (!removed[q] && sid[q] < sid[best]) best = q;
-                    // the heap may hold best: drop it lazily (skipped when popped)
-                } else {
-                    while (hn > 0) {                               // pop min id (lazy deletion)
-                        const int top = heap_ix[0];
-                        const int64_t last_id = heap_id[hn - 1];
-                        const int last_ix = heap_ix[hn - 1];
-                        --hn;
-                        int q = 0;
-                        while (true) {
-                            int ch = 2 * q + 1;
-                            if (ch >= hn) break;
-                            if (ch + 1 < hn && heap_id[ch + 1] < heap_id[ch]) ++ch;
-                            if (heap_id[ch] >= last_id) break;
-                            heap_id[q] = heap_id[ch];
-                            heap_ix[q] = heap_ix[ch];
-                            q = ch;
+        if (tid < 32) {
+            const int lane = tid;
+            if (lane == 0) slow = 0;
+            while (true) {
+                int best = -1, stop = 0;
+                if (lane == 0) {
+                    while (p < n_sorted && removed[p]) ++p;
+                    if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
+                        done = 1;
+                        exhausted = n_acc < k;
+                        stop = 1;
+                    } else {
+                        const double m = sk[p];
+                        if (e < p) e = p;
+                        while (e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
+                            if (hn == kHeapCap) break;
+                            int q = hn++;                          // push (sift up)
+                            const int64_t xid = sid[e];
+                            while (q > 0 && heap_id[(q - 1) >> 1] > xid) {
+                                heap_id[q] = heap_id[(q - 1) >> 1];
+                                heap_ix[q] = heap_ix[(q - 1) >> 1];
+                                q = (q - 1) >> 1;
+                            }
+                            heap_id[q] = xid;
+                            heap_ix[q] = e;
+                            ++e;
                         }
-                        if (hn > 0) { heap_id[q] = last_id; heap_ix[q] = last_ix; }
-                        if (!removed[top]) { best = top; break; }
+                        if (hn == kHeapCap && e < n_sorted && sk[e] >= 0.0 && sk[e] >= m - kScoreTie) {
+                            // window larger than the heap: plain scan (still exact)
+                            best = p;
+                            for (int q = p; q < n_sorted && sk[q] >= m - kScoreTie; ++q)
+                                if (!removed[q] && sid[q] < sid[best]) best = q;
+                            // the heap may hold best: drop it lazily (skipped when popped)
+                        } else {
+                            while (hn > 0) {                       // pop min id (lazy deletion)
+                                const int top = heap_ix[0];
+                                const int64_t last_id = heap_id[hn - 1];
+                                const int last_ix = heap_ix[hn - 1];
+                                --hn;
+                                int q = 0;
+                                while (true) {
+                                    int ch = 2 * q + 1;
+                                    if (ch >= hn) break;
+                                    if (ch + 1 < hn && heap_id[ch + 1] < heap_id[ch]) ++ch;
+                                    if (heap_id[ch] >= last_id) break;
+                                    heap_id[q] = heap_id[ch];
+                                    heap_ix[q] = heap_ix[ch];
+                                    q = ch;
+                                }
+                                if (hn > 0) { heap_id[q] = last_id; heap_ix[q] = last_ix; }
+                                if (!removed[top]) { best = top; break; }
+                            }
+                        }
+                        if (best < 0) best = p;
+                        removed[best] = 1;
+                        cur = best;
+                        cur_score = sk[best];
+                        last_score = sk[best];
+                        ++visited;
                     }
                 }
-                if (best < 0) { best = p; }
-                removed[best] = 1;
-                cur = best;
-                cur_score = sk[best];
-                last_score = sk[best];
-                ++visited;
+                stop = __shfl_sync(0xffffffffu, stop, 0);
+                if (stop) break;
+                best = __shfl_sync(0xffffffffu, best, 0);
+                __syncwarp();
+                // the first reference among the listed partners decides: a confirmed
+                // duplicate rejects; a reference beyond the confirmed slots, or partners
+                // beyond the list, leave the pick to the full check
                 const int raw = dup_cnt[best];
                 const int cnt = raw < 0 ? -raw - 1 : raw;
-                bool dup = false, unknown = raw < 0;              // partners beyond the list
-                for (int q = 0; q < cnt && !dup; ++q) {
-                    const int mm = dup_list[(size_t)best * kDupSlots + q];
-                    if (!(mm >= s_off || accepted[mm])) continue;  // not a reference (yet)
-                    if (q >= kConfirm) { unknown = true; break; }  // reference, not confirmed ahead
-                    dup = dup_ok[(size_t)best * kDupSlots + q];
+                bool ref = false;
+                if (lane < cnt) {
+                    const int mm = dup_list[(size_t)best * kDupSlots + lane];
+                    ref = mm >= s_off || accepted[mm];
                 }
-                checks += cnt;
-                if (!dup && unknown) { slow = 1; break; }
-                if (!dup) {
-                    const int src = ssrc[best];
-                    accepted[src] = 1;
-                    acc_src[n_acc] = src;
-                    out->acc[n_acc] = sid[best];
-                    ++n_acc;
+                const bool dup = __ballot_sync(0xffffffffu, ref && lane < kConfirm &&
+                                                            dup_ok[(size_t)best * kDupSlots + lane] != 0) != 0;
+                const bool unknown = raw < 0 || __ballot_sync(0xffffffffu, ref && lane >= kConfirm) != 0;
+                if (lane == 0) {
+                    checks += cnt;
+                    if (!dup && unknown) slow = 1;
+                    else if (!dup) {
+                        const int src = ssrc[best];
+                        accepted[src] = 1;
+                        acc_src[n_acc] = src;
+                        out->acc[n_acc] = sid[best];
+                        ++n_acc;
+                    }
                 }
+                __syncwarp();
+                if (!dup && unknown) break;
             }
-            n_refs = 0;
+            if (lane == 0) n_refs = 0;
         }
         __syncthreads();
         if (done) break;
@@ -983,13 +1060,15 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         cudaEventRecord(q[3], c->stream);
         cudaMemsetAsync(c->removed, 0, (size_t)n_pad, c->stream);
         cudaMemsetAsync(c->accepted, 0, (size_t)ns, c->stream);
-        k_dup_find<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_src, c->sort_id, n_pad, c->surv_score,
+        k_dup_find<<<(int)(((int64_t)n_pad * 32 + 255) / 256), 256, 0, c->stream>>>(c->sort_score, c->sort_src, c->sort_id, n_pad, c->surv_score,
                                                                c->surv_sd, c->surv_probe, ns, n_prev, c->dup_list,
                                                                c->dup_cnt);
         k_dup_confirm<<<std::max(1, std::min(c->sms * 16, (n_pad * 32 + 255) / 256)), 256, 0, c->stream>>>(
             c->space_dev, c->Xc64, c->N, c->sort_src, c->sort_id, n_pad, c->surv_ids, c->surv_mean, c->surv_sd, zc,
             c->opval64, c->dup_list, c->dup_cnt, c->dup_ok);
-        k_walk<<<1, kWalkThreads, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
+        cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmem);
+        const size_t wsm = n_pad <= kWalkStage && ns <= kWalkStage ? kWalkSmem : 0;
+        k_walk<<<1, kWalkThreads, wsm, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
                                                   n_pad, c->surv_ids, c->surv_score, c->surv_mean, c->surv_sd,
                                                   c->surv_probe, zc, c->opval64, c->dup_list, c->dup_cnt, c->dup_ok,
                                                   ns, n_prev, k, c->removed, c->accepted, c->walk);
