@@ -489,7 +489,8 @@ def run_learned(args):
         "subsets_solved": {"exhaustive": ok[0]["examined_exhaustive"] if ok else None,
                            "learned_mean": float(np.mean([r["examined_learned"] for r in ok])) if ok else None},
         "training": {"data_s": t_data, "train_s": t_train, "loss_rel_to_target_var": rel_loss},
-        "gpu_launches": None,
+        "gpu_launches": int(round(float(np.mean([r["fit_learned_launches"] for r in ok])))) if ok else None,
+        "gpu_launches_note": "kernel launches of one learned fit (mean over the held-out problems)",
     }
     print(json.dumps(line), flush=True)
 

@@ -997,6 +997,7 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
         k_wsel_find<<<1, 32, 0, c->stream>>>(hist, pass, state, budget);
     }
     k_wsel_compact<<<gs, 256, 0, c->stream>>>(score, plist, np, state, sel, count, np, nullptr);
+    c->stats.launches += 13;   // features, pack, 2 layers + head, add, 3 x (histogram, find), compact
     unsigned h_count = 0;
     cudaMemcpyAsync(&h_count, count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     ck(cudaStreamSynchronize(c->stream), "learned: selection");

@@ -412,7 +412,10 @@ __global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int
 // then only reads the confirmed pairs.
 // ---------------------------------------------------------------------------------
 constexpr double kDupScore = 2e-8;
-constexpr int kConfirm = 8;             // partner slots confirmed ahead of the walk
+// partner slots confirmed ahead of the walk: a cluster's accepted representative is its
+// smallest id, so later members find it in the first slots; with few samples a full check
+// costs little and more slots spare the walk its CTA-wide path, with many samples fewer
+__host__ __device__ __forceinline__ int n_confirm(int N) { return N <= 8192 ? 8 : 2; }
 constexpr int kMaxRefs = 2048;          // slow path: S members / accepted ids gathered per round
 
 __device__ __forceinline__ bool probes_match(const double* a, const double* b) {
@@ -507,7 +510,7 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
     const int lane = threadIdx.x & 31;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_sorted; i += (gridDim.x * blockDim.x) >> 5) {
         const int raw = dup_cnt[i];
-        const int cnt = min(raw < 0 ? -raw - 1 : raw, kConfirm);
+        const int cnt = min(raw < 0 ? -raw - 1 : raw, n_confirm(N));
         if (cnt <= 0) continue;
         const int src = ssrc[i];
         Prog pc;
@@ -555,11 +558,11 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
 constexpr int kWalkThreads = 1024;
 constexpr int kHeapCap = 2048;          // tie-window entries held in the shared-memory heap
 constexpr int kWalkStage = 4096;        // sorted entries staged in shared memory
-constexpr size_t kWalkSmem = (size_t)kWalkStage * (sizeof(double) + sizeof(int64_t) + sizeof(int) + 2);
+constexpr size_t kWalkSmem = (size_t)kWalkStage * (sizeof(double) + sizeof(int64_t) + 2 * sizeof(int) + 2);
 
 __global__ void __launch_bounds__(kWalkThreads)
 k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const double* __restrict__ sk_g,
-       const int64_t* __restrict__ sid_g, const int* __restrict__ ssrc, int n_sorted,
+       const int64_t* __restrict__ sid_g, const int* __restrict__ ssrc_g, int n_sorted,
        const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_score,
        const double* __restrict__ sv_mean, const double* __restrict__ sv_sd,
        const double* __restrict__ probe, const double* __restrict__ zc, const double* __restrict__ V,
@@ -580,22 +583,25 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
     const double* sk = sk_g;
     const int64_t* sid = sid_g;
     const int* dup_cnt = cnt_g;
+    const int* ssrc = ssrc_g;
     unsigned char* removed = removed_g;
     unsigned char* accepted = accepted_g;
     if (staged) {
         double* s_sk = reinterpret_cast<double*>(wsm);
         int64_t* s_sid = reinterpret_cast<int64_t*>(s_sk + kWalkStage);
         int* s_cnt = reinterpret_cast<int*>(s_sid + kWalkStage);
-        unsigned char* s_rem = reinterpret_cast<unsigned char*>(s_cnt + kWalkStage);
+        int* s_src = s_cnt + kWalkStage;
+        unsigned char* s_rem = reinterpret_cast<unsigned char*>(s_src + kWalkStage);
         unsigned char* s_acc = s_rem + kWalkStage;
         for (int q = tid; q < n_sorted; q += blockDim.x) {
             s_sk[q] = sk_g[q];
             s_sid[q] = sid_g[q];
             s_cnt[q] = cnt_g[q];
+            s_src[q] = ssrc_g[q];
             s_rem[q] = 0;
         }
         for (int q = tid; q < s_off; q += blockDim.x) s_acc[q] = 0;
-        sk = s_sk; sid = s_sid; dup_cnt = s_cnt; removed = s_rem; accepted = s_acc;
+        sk = s_sk; sid = s_sid; dup_cnt = s_cnt; ssrc = s_src; removed = s_rem; accepted = s_acc;
     }
     if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0; }
     // lane 0's state: first remaining entry p, window end e, heap of the window's
@@ -673,14 +679,14 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
                 // beyond the list, leave the pick to the full check
                 const int raw = dup_cnt[best];
                 const int cnt = raw < 0 ? -raw - 1 : raw;
-                bool ref = false;
-                if (lane < cnt) {
+                bool ref = false, okq = false;
+                if (lane < cnt) {                          // both reads issued together
                     const int mm = dup_list[(size_t)best * kDupSlots + lane];
+                    okq = lane < n_confirm(N) && dup_ok[(size_t)best * kDupSlots + lane] != 0;
                     ref = mm >= s_off || accepted[mm];
                 }
-                const bool dup = __ballot_sync(0xffffffffu, ref && lane < kConfirm &&
-                                                            dup_ok[(size_t)best * kDupSlots + lane] != 0) != 0;
-                const bool unknown = raw < 0 || __ballot_sync(0xffffffffu, ref && lane >= kConfirm) != 0;
+                const bool dup = __ballot_sync(0xffffffffu, ref && okq) != 0;
+                const bool unknown = raw < 0 || __ballot_sync(0xffffffffu, ref && lane >= n_confirm(N)) != 0;
                 if (lane == 0) {
                     checks += cnt;
                     if (!dup && unknown) slow = 1;

@@ -102,14 +102,23 @@ def _c3_small(N=600):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("case", ["c1", "rung3", "collinear"])
+@pytest.mark.parametrize("case", ["c1", "rung3", "collinear", "wide", "long"])
 def test_sis_step(S, orc, case, prec):
+    """One SIS step and a second one on a residual.  "wide": k = 150 makes the re-scored
+    window 8192 entries (walk on the global arrays, not the shared-memory copy); "long":
+    9000 samples (two partner slots confirmed ahead of the walk instead of eight)."""
     if case == "c1":
         P = inputs.workload1(1)
         X, y, m, rung, g, k = P.X, P.y, P.op_set, 2, 0, 20
     elif case == "rung3":
         X, y = _lognormal_problem(11, 150, 4)
         m, rung, g, k = _mask(orc, ALL9), 3, 1, 30
+    elif case == "wide":
+        X, y = _lognormal_problem(13, 150, 4)
+        m, rung, g, k = _mask(orc, ALL9), 3, 1, 150
+    elif case == "long":
+        X, y = _lognormal_problem(14, 9000, 4)
+        m, rung, g, k = _mask(orc, ALL9), 2, 0, 20
     else:
         X, y = _c3_small()
         m, rung, g, k = _mask(orc, ALL9), 2, 0, 40
