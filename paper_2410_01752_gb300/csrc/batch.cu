@@ -7,6 +7,8 @@
 //
 //   START    (serial)   primaries: values, validity; moments of y (target of step 1)
 //   LEVEL l  (parallel) phi_l for 0 < l < L: FP64 rows, FP32 sample-major cache, validity
+//   OPSUM t  (parallel) per-operand sums for the + and - pairs: sum(x - x0) once per task,
+//                       sum((x - x0) r) against the step-t target
 //   SCORE t  (parallel) every candidate of phi_L scored against the step-t target (FP32)
 //   SELECT t (serial)   the best FP32 scores re-scored in FP64, sorted, walked with the tie
 //                       and duplicate rules; accepted features standardised into Z

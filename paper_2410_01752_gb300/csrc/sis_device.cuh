@@ -282,13 +282,27 @@ __device__ __forceinline__ void unary_block(const UnaryArgs& U, const T* cache, 
         if (w == 0) r[lane] = s0 + lane < N ? tc[s0 + lane] : T(0);
         __syncthreads();
         const int ns = min(32, N - s0);
-        if (active)
+        // the operator is fixed per warp: one loop per operator, no branch per sample
+        auto run = [&](auto opc) {
             for (int s = 0; s < ns; ++s) {
-                const T v = op_unary<T>(op, xs[s][lane]) - v0;
+                const T v = op_unary<T>(decltype(opc)::value, xs[s][lane]) - v0;
                 s1 += v;
                 s2 = fma(v, v, s2);
                 sr = fma(v, r[s], sr);
             }
+        };
+        if (active) {
+            switch (op) {
+                case EXP: run(std::integral_constant<int, EXP>{}); break;
+                case LOG: run(std::integral_constant<int, LOG>{}); break;
+                case SQRT: run(std::integral_constant<int, SQRT>{}); break;
+                case SQ: run(std::integral_constant<int, SQ>{}); break;
+                case INV: run(std::integral_constant<int, INV>{}); break;
+                case SIN: run(std::integral_constant<int, SIN>{}); break;
+                case CUBE: run(std::integral_constant<int, CUBE>{}); break;
+                default: run(std::integral_constant<int, EXPNEG>{}); break;
+            }
+        }
     }
     if (active)
         scores[U.base[w] + (z - U.Q)] = subvalid[z] ? finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st)) : -1.f;
@@ -423,15 +437,11 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
     __syncthreads();
 
     const int64_t j = j0 + lane;
-    int64_t iq[RI];
-    bool ok[RI];
     T Km[RI], Kd[RI], Ke[RI];
     const T b0 = S.b0[lane];
     const T rb0 = rcp<T>(b0);
 #pragma unroll
     for (int q = 0; q < RI; ++q) {
-        iq[q] = i0 + g * RI + q;
-        ok[q] = pair_ok(iq[q], j, A.P, A.Q, A.nxp);
         const T a0 = S.a0[g * RI + q];
         Km[q] = a0 * b0;
         Kd[q] = a0 * rb0;
@@ -552,9 +562,14 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
     const double a1j = lin && j < A.P ? A1[j] : 0.0, arj = lin && j < A.P ? AR[j] : 0.0;
 #pragma unroll
     for (int q = 0; q < RI; ++q) {
-        if (!ok[q]) continue;
+        // indices, validity and shifts recomputed here (same values): in the paired form they
+        // are not live across the sample loop, which leaves the registers to the accumulators
+        const int64_t i = i0 + g * RI + q;
+        if (!pair_ok(i, j, A.P, A.Q, A.nxp)) continue;
         const T a0 = S.a0[g * RI + q];
-        const int64_t i = iq[q];
+        const T kmq = kPair ? a0 * b0 : Km[q];
+        const T kdq = kPair ? a0 * rb0 : Kd[q];
+        const T keq = kPair ? b0 * rcp<T>(a0) : Ke[q];
         const bool opv = okj && S.ok[g * RI + q];   // both operands valid
         const double a1i = lin ? A1[i] : 0.0, ari = lin ? AR[i] : 0.0;
         if (A.sec[0] >= 0) {
@@ -573,12 +588,12 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         }
         if (A.sec[2] >= 0) {
             const Section& sc = A.sp->sec[A.sec[2]];
-            A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], Km[q], N, sum_t, sd_t) : -1.f;
+            A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[0][q], s2[0][q], sr[0][q], kmq, N, sum_t, sd_t) : -1.f;
         }
         if (A.sec[3] >= 0) {
             const Section& sc = A.sp->sec[A.sec[3]];
-            A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], Kd[q], N, sum_t, sd_t) : -1.f;
-            A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], Ke[q], N, sum_t, sd_t) : -1.f;
+            A.scores[sc.base + rank_of(sc, i, j)] = opv ? finalize<T>(s1[1][q], s2[1][q], sr[1][q], kdq, N, sum_t, sd_t) : -1.f;
+            A.scores[sc.base + rank_of(sc, j, i)] = opv ? finalize<T>(s1[2][q], s2[2][q], sr[2][q], keq, N, sum_t, sd_t) : -1.f;
         }
     }
 }
