@@ -403,6 +403,37 @@ __global__ void k_bitonic(double* sk, int64_t* sid, int* ssrc, int n, int k, int
     }
 }
 
+// the same network in one CTA's shared memory (windows of up to kSortBlock entries):
+// one launch instead of one per stage
+constexpr int kSortBlock = 8192;
+constexpr size_t kSortSmem = (size_t)kSortBlock * (sizeof(double) + sizeof(int64_t) + sizeof(int));
+
+__global__ void __launch_bounds__(1024) k_sort_block(double* sk, int64_t* sid, int* ssrc, int n) {
+    extern __shared__ __align__(16) unsigned char ssm[];
+    double* k_ = reinterpret_cast<double*>(ssm);
+    int64_t* id_ = reinterpret_cast<int64_t*>(k_ + n);
+    int* src_ = reinterpret_cast<int*>(id_ + n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { k_[i] = sk[i]; id_[i] = sid[i]; src_[i] = ssrc[i]; }
+    __syncthreads();
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l <= i) continue;
+                const bool up = (i & k) == 0;
+                const double si = k_[i], sl = k_[l];
+                const int64_t ii = id_[i], il = id_[l];
+                if (up ? before(sl, il, si, ii) : before(si, ii, sl, il)) {
+                    k_[i] = sl; k_[l] = si;
+                    id_[i] = il; id_[l] = ii;
+                    const int t = src_[i]; src_[i] = src_[l]; src_[l] = t;
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { sk[i] = k_[i]; sid[i] = id_[i]; ssrc[i] = src_[i]; }
+}
+
 // ---------------------------------------------------------------------------------
 // duplicate rule.  Two features are duplicates when their standardised vectors agree up
 // to sign within kDupTol (max norm).  Necessary conditions, checked first: their scores
@@ -1058,11 +1089,19 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
                                                                  c->sort_id, c->sort_src);
         c->stats.launches += 2;
         cudaEventRecord(q[2], c->stream);
-        for (int kk = 2; kk <= n_pad; kk <<= 1)
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                k_bitonic<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_id, c->sort_src, n_pad, kk, j);
-                c->stats.launches++;
-            }
+        if (n_pad <= kSortBlock) {
+            const size_t sm = (size_t)n_pad * (sizeof(double) + sizeof(int64_t) + sizeof(int));
+            cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem);
+            k_sort_block<<<1, 1024, sm, c->stream>>>(c->sort_score, c->sort_id, c->sort_src, n_pad);
+            c->stats.launches++;
+        } else {
+            for (int kk = 2; kk <= n_pad; kk <<= 1)
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    k_bitonic<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->sort_score, c->sort_id, c->sort_src, n_pad, kk,
+                                                                          j);
+                    c->stats.launches++;
+                }
+        }
         cudaEventRecord(q[3], c->stream);
         cudaMemsetAsync(c->removed, 0, (size_t)n_pad, c->stream);
         cudaMemsetAsync(c->accepted, 0, (size_t)ns, c->stream);
