@@ -347,6 +347,13 @@ sisso_status sisso_fit_batch(const sisso_task* tasks, int n_tasks, uint32_t op_s
  *
  * Parameter layout (FP32, SISSO_MLP_PARAMS values): W1 [256 x 20] row-major (output x input),
  * b1 [256], W2 [256 x 256], b2 [256], w3 [256], b3 [1].
+ *
+ * Ownership: the caller owns every buffer it passes and the sisso_mlp it creates (destroy it
+ * after the last context that uses it as a proposal).  Errors, for every entry point below:
+ * SISSO_ERR_ARG for a NULL required pointer or an out-of-range size (n, M, B, batch, frac in
+ * (0, 1], lr > 0), checked before the device is touched; SISSO_ERR_OOM / SISSO_ERR_CUDA for
+ * device failures; SISSO_ERR_TIMEOUT when a bounded wait in the network's tensor-core
+ * kernels ran out (the network is then in an undefined state: destroy it).
  */
 #define SISSO_MLP_IN 20
 #define SISSO_MLP_HIDDEN 256

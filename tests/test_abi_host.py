@@ -153,3 +153,41 @@ def test_batch_null_arguments(lib):
     L.sisso_batch_destroy(None)
     b = C.c_void_p()
     assert L.sisso_batch_create(None, 0, 1, 2, 5, 2, None, C.byref(b)) == -1
+
+
+def test_learned_api_argument_errors(lib):
+    """The learned-proposal entry points reject NULL pointers and out-of-range sizes with
+    SISSO_ERR_ARG before they touch a device."""
+    L = lib.load()
+    f = np.zeros(lib.MLP_PARAMS, dtype=np.float32)
+    X = np.zeros((256, lib.MLP_IN), dtype=np.float32)
+    fp = C.c_void_p(f.ctypes.data)
+    xp = C.c_void_p(X.ctypes.data)
+    assert L.sisso_mlp_create(7, None) == -1
+    assert L.sisso_mlp_get_params(None, fp) == -1
+    assert L.sisso_mlp_set_params(None, fp) == -1
+    assert L.sisso_mlp_forward(None, xp, 256, fp) == -1
+    assert L.sisso_mlp_gradients(None, xp, fp, 256, None, fp) == -1
+    assert L.sisso_mlp_train(None, xp, fp, 256, 1, 128, 1e-3, 0, None) == -1
+    L.sisso_mlp_destroy(None)
+    n = 12
+    G = np.eye(n)
+    b = np.full(n, 0.1)
+    out = np.zeros(n ** 3, dtype=np.float32)
+    Gp, bp, op = (C.c_void_p(a.ctypes.data) for a in (G, b, out))
+    assert L.sisso_prefix_features(None, bp, 1.0, n, op, None, None) == -1
+    assert L.sisso_prefix_features(Gp, bp, 1.0, 2, op, None, None) == -1       # fewer than 3 features
+    assert L.sisso_prefix_features(Gp, bp, 1.0, 4096, op, None, None) == -1    # above 4095
+    assert L.sisso_prefix_features(Gp, bp, 0.0, n, op, None, None) == -1       # syy must be > 0
+    assert L.sisso_prefix_labels(Gp, bp, 1.0, 100, 4, op) == -1                # fewer than 5 features
+    assert L.sisso_prefix_labels(Gp, bp, 1.0, 100, 1401, op) == -1             # above 1400
+    assert L.sisso_prefix_labels(Gp, bp, 1.0, 0, n, op) == -1                  # N >= 1
+    assert L.sisso_prefix_labels(Gp, None, 1.0, 100, n, op) == -1
+    gid = np.arange(n, dtype=np.int64)
+    pos = (C.c_int * 5)()
+    rss = C.c_double()
+    ex, npre = C.c_int64(), C.c_int64()
+    assert L.sisso_l0_learned(None, Gp, bp, 1.0, n, C.c_void_p(gid.ctypes.data), None, 0.01, pos, C.byref(rss),
+                              C.byref(ex), C.byref(npre)) == -1
+    assert L.sisso_set_proposal(None, None, 0.01) == -1
+    assert L.sisso_subspace_gram(None, C.c_void_p(gid.ctypes.data), n, Gp, bp, C.byref(rss)) == -1
