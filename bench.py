@@ -176,6 +176,19 @@ def captured_batch_traffic(tune: dict):
     return int(vals["traffic_bytes_per_launch"].strip())
 
 
+def job_totals(total_ms, counts, dist, device):
+    """Whole-job figures of a replicated run: the slowest rank's time (the job ends when it
+    does) and every rank's units summed.  dist None: a single process."""
+    if dist is None:
+        return float(total_ms), [float(v) for v in counts]
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(v) for v in counts], device=device, dtype=torch.float64)
+    dist.all_reduce(c)
+    return float(t.item()), [float(v) for v in c.tolist()]
+
+
 def top_binary_candidates(sizes, n_unary_ops):
     """Candidates of the top level's binary sections (the pair kernel's work)."""
     L = len(sizes) - 1
@@ -563,12 +576,7 @@ def main():
     cand = sum(st["candidates_scored"] for st in stats)
     subsets = sum(st["subsets_fit"] for st in stats)
     launches = sum(st["launches"] for st in stats)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([cand, subsets, launches], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        total_ms, (cand, subsets, launches) = float(t.item()), [float(v) for v in c.tolist()]
+    total_ms, (cand, subsets, launches) = job_totals(total_ms, [cand, subsets, launches], dist, "cuda")
     value = cand / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -589,13 +597,7 @@ def main():
             torch.cuda.synchronize()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
             d2h = sum(8 * len(x.ids) + 8 * len(x.coef) + 16 for x in dd)
-        tot = sum(e2e_ms)
-        if dist is not None:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            c = torch.tensor([float(e2e_cand)], device="cuda", dtype=torch.float64)
-            dist.all_reduce(c)
-            tot, e2e_cand = float(t.item()), float(c.item())
+        tot, (e2e_cand,) = job_totals(sum(e2e_ms), [e2e_cand], dist, "cuda")
         e2e = {"value": e2e_cand / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
                "d2h_bytes_per_step": int(d2h)}
 
