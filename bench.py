@@ -113,15 +113,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_baseline_sample(P, seconds: float, seed: int = 0):
+def cpu_baseline_sample(P, seconds: float, seed: int = 0, threads: int = 0):
     """The FP64 oracle scoring a random sample of the workload's candidate ids on all host
-    cores; returns (features/s, ids scored, wall seconds, threads)."""
+    cores (or `threads`); returns (features/s, ids scored, wall seconds, threads)."""
     import numpy as np
     import oracle
     sp = oracle.Space(P.d, P.op_set, P.rung, P.grammar)
     n = sp.n_features
     rng = np.random.default_rng(seed)
-    th = cores()
+    th = threads if threads > 0 else cores()
     probe = rng.integers(0, n, 2000)
     t0 = time.perf_counter()
     sp.scores(P.X, P.y, probe, nthreads=th)
@@ -629,8 +629,10 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         r, m, dt, th = cpu_baseline_sample(P, args.cpu_seconds)
+        r1, m1, dt1, _ = cpu_baseline_sample(P, max(1.0, args.cpu_seconds / 4), seed=1, threads=1)
         cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
-               "sample": f"{m} random candidate ids of the workload scored in FP64 over all {P.N} samples ({dt:.1f} s)"}
+               "sample": f"{m} random candidate ids of the workload scored in FP64 over all {P.N} samples ({dt:.1f} s)",
+               "value_1thread": r1, "sample_1thread": f"{m1} random candidate ids on one thread ({dt1:.1f} s)"}
 
     d_last = desc[-1] if desc else None
     line = {
