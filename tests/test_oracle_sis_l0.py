@@ -124,7 +124,8 @@ def _gram(cols, y):
     return Z.T @ Z / N, Z.T @ yc / N, float(yc @ yc) / N
 
 
-@pytest.mark.parametrize("n,D,seed", [(8, 1, 0), (10, 2, 1), (12, 3, 2), (9, 4, 3), (16, 3, 4)])
+@pytest.mark.parametrize("n,D,seed", [(8, 1, 0), (10, 2, 1), (12, 3, 2), (9, 4, 3), (16, 3, 4), (11, 5, 5),
+                                      (14, 5, 6)])
 def test_l0_matches_lstsq_brute_force(orc, n, D, seed):
     """Exhaustive l0 equals numpy.linalg.lstsq over every D-subset (with intercept):
     the same winner, the same RSS, C(n, D) subsets examined."""
