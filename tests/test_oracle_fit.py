@@ -11,20 +11,22 @@ def _mask(orc, names):
     return orc.opmask(*[orc.OP_NAMES.index(n) for n in names])
 
 
-@pytest.mark.parametrize("seed,names,rung,k,T", [
-    (0, ["+", "-", "*", "/", "sqrt"], 2, 4, 3),
-    (1, ["+", "*", "/", "log", "^2"], 2, 3, 3),
-    (2, ["+", "*", "exp-"], 3, 3, 2),
+@pytest.mark.parametrize("seed,names,rung,k,T,nxp", [
+    (0, ["+", "-", "*", "/", "sqrt"], 2, 4, 3, False),
+    (1, ["+", "*", "/", "log", "^2"], 2, 3, 3, False),
+    (2, ["+", "*", "exp-"], 3, 3, 2, False),
+    (3, ["+", "-", "*", "/", "log"], 3, 4, 3, True),      # the restricted rung-3 grammar
 ])
-def test_fit_matches_brute_force_pipeline(orc, seed, names, rung, k, T):
+def test_fit_matches_brute_force_pipeline(orc, seed, names, rung, k, T, nxp):
     """Every step (S_t, descriptor, coefficients, RMSE) equals the numpy brute-force
     iteration: SIS on y, then on the residual of the best lstsq fit."""
     rng = np.random.default_rng(seed)
     X = rng.uniform(1, 5, size=(20, 2 if rung == 3 else 3))
     d = X.shape[1]
     y = 2 * X[:, 0] / X[:, 1] + np.sqrt(X[:, -1]) + 0.05 * rng.normal(size=20)
-    ref = brute.sisso(X, y, d, names, rung, k, T)
-    res = orc.fit(X, y, orc.Space(d, _mask(orc, names), rung), k, T)
+    ref = brute.sisso(X, y, d, names, rung, k, T, new_x_prev=nxp)
+    res = orc.fit(X, y, orc.Space(d, _mask(orc, names), rung, orc.GRAMMAR_NEW_X_PREV if nxp else orc.GRAMMAR_EQ2),
+                  k, T)
     assert len(res.dims) == len(ref)
     for t, (tup, c, rmse, S) in enumerate(ref):
         assert res.dims[t].ids == tup
