@@ -79,6 +79,8 @@ def lib():
         L.oracle_eval.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, C.c_int64, dp]
         L.oracle_scores.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p,
                                     C.c_int64, dp, ip, C.c_int]
+        L.oracle_scores_all.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, dp, ip,
+                                        C.c_int]
         L.oracle_sis.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p, C.c_int,
                                  C.c_int, i64p, C.c_int]
         L.oracle_l0.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, i64p, ip, dp, C.c_int]
@@ -154,6 +156,20 @@ class Space:
                                  _dp(sc), va.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
         if rc:
             raise ValueError(f"oracle_scores failed ({rc})")
+        return sc, va.astype(bool)
+
+    def scores_all(self, X, target, nthreads: int = 0):
+        """(|rho|, valid) for every id, the features of phi_{rung-1} evaluated once and kept
+        (the whole-space form the SIS step uses; equal to ``scores`` bit for bit)."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        target = np.ascontiguousarray(target, dtype=np.float64)
+        n = self.n_features
+        sc = np.zeros(n, dtype=np.float64)
+        va = np.zeros(n, dtype=np.int32)
+        rc = lib().oracle_scores_all(*self.args, _dp(X), X.shape[0], _dp(target), _dp(sc),
+                                     va.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
+        if rc:
+            raise ValueError(f"oracle_scores_all failed ({rc})")
         return sc, va.astype(bool)
 
     def sis(self, X, target, S_prev, k: int, nthreads: int = 0) -> list[int]:

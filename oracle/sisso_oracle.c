@@ -386,6 +386,139 @@ static void scores_threaded(const space_t* s, const double* X, int N, const doub
     free(th); free(jobs);
 }
 
+/* ---- every id at once, level by level ------------------------------------------------
+ *
+ * Scoring the whole of phi_rung one id at a time re-derives each operand from the
+ * primaries.  Here the features of phi_{rung-1} are evaluated once (eval_rec) with their
+ * recursive validity (valid_rec) and kept; each feature new at level `rung` is then built
+ * from its operands' stored values, walking the sections in canonical id order (operator
+ * in table order, then row i, then partner j), the way §2.1 builds level l from level
+ * l-1.  Every FP64 operation is the one eval_checked, moments and pearson perform, so the
+ * scores and validity flags equal those of the per-id path bit for bit. */
+
+#define LEVEL_TABLE_MAX_BYTES ((size_t)24 << 30)
+
+typedef struct {
+    const space_t* s; int N;
+    const double* X;
+    const double* vals;   /* phi_{rung-1} values, id-major (P x N) */
+    int* vok;             /* recursive validity of phi_{rung-1} */
+    const double* tc; double tsd;
+    double* score; int* valid;
+    int tid, nthreads;
+} level_job;
+
+/* values and recursive validity of the ids tid, tid + nthreads, ... of phi_{rung-1} */
+static void* level_table_worker(void* p) {
+    level_job* j = (level_job*)p;
+    int64_t P = j->s->phi[j->s->rung - 1];
+    for (int64_t id = j->tid; id < P; id += j->nthreads) {
+        double* v = (double*)j->vals + (size_t)id * (size_t)j->N;
+        j->vok[id] = eval_rec(j->s, j->X, j->N, id, v) == 0 && valid_rec(j->s, j->X, j->N, id);
+    }
+    return NULL;
+}
+
+/* score of the stored feature v (valid flag ok) */
+static void score_values(const level_job* j, const double* v, int ok, int64_t id) {
+    double m, sd;
+    ok = ok && moments(v, j->N, &m, &sd);
+    j->valid[id] = ok;
+    j->score[id] = ok ? pearson(v, j->N, m, sd, j->tc, j->tsd) : 0.0;
+}
+
+static void* level_score_worker(void* p) {
+    level_job* j = (level_job*)p;
+    const space_t* s = j->s;
+    int l = s->rung, N = j->N;
+    int64_t P = sz_P(s, l), Q = sz_Q(s, l);
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    /* features of phi_{rung-1}: their stored values */
+    for (int64_t id = j->tid; id < P; id += j->nthreads)
+        score_values(j, j->vals + (size_t)id * (size_t)N, j->vok[id], id);
+    /* features new at level rung: rows (op, i) of binary sections, one row per feature
+       of new_{rung-1} for unary sections; row r of the whole level goes to thread r mod n */
+    int64_t id0 = P, row = 0;
+    for (int op = 0; op < ORC_NOPS; op++) {
+        if (s->sec[l][op] == 0) continue;
+        if (!op_is_binary(op)) {
+            for (int64_t r = 0; r < P - Q; r++, row++) {
+                int64_t id = id0 + r, a = Q + r;
+                if (row % j->nthreads != j->tid) continue;
+                const double* va = j->vals + (size_t)a * (size_t)N;
+                for (int q = 0; q < N; q++) v[q] = apply_unary(op, va[q]);
+                score_values(j, v, j->vok[a], id);
+            }
+            id0 += P - Q;
+            continue;
+        }
+        for (int64_t i = 0; i < P; i++, row++) {
+            int64_t lo[2], hi[2];
+            int nr = row_ranges(s, l, op, i, lo, hi);
+            int64_t w = 0;
+            for (int q = 0; q < nr; q++) w += hi[q] - lo[q];
+            if (row % j->nthreads == j->tid) {
+                int64_t id = id0;
+                const double* va = j->vals + (size_t)i * (size_t)N;
+                for (int q = 0; q < nr; q++) {
+                    for (int64_t b = lo[q]; b < hi[q]; b++, id++) {
+                        const double* vb = j->vals + (size_t)b * (size_t)N;
+                        double mv = 0.0, mo = 0.0;
+                        for (int e = 0; e < N; e++) {
+                            v[e] = apply_binary(op, va[e], vb[e]);
+                            if (fabs(v[e]) > mv) mv = fabs(v[e]);
+                            if (fabs(va[e]) + fabs(vb[e]) > mo) mo = fabs(va[e]) + fabs(vb[e]);
+                        }
+                        int cancelled = (op == ORC_ADD || op == ORC_SUB) && mv <= CANCEL_REL * mo;
+                        score_values(j, v, !cancelled && j->vok[i] && j->vok[b], id);
+                    }
+                }
+            }
+            id0 += w;
+        }
+    }
+    free(v);
+    return NULL;
+}
+
+/* scores and validity of every id of phi_rung by the level table; returns -1 (nothing
+   written) when the table would not fit in LEVEL_TABLE_MAX_BYTES or rung < 1 */
+static int scores_all_levelwise(const space_t* s, const double* X, int N, const double* tc, double tsd,
+                                double* score, int* valid, int nthreads) {
+    if (s->rung < 1) return -1;
+    int64_t P = s->phi[s->rung - 1];
+    if ((size_t)P * (size_t)N > LEVEL_TABLE_MAX_BYTES / sizeof(double)) return -1;
+    double* vals = (double*)malloc(sizeof(double) * (size_t)P * (size_t)N);
+    int* vok = (int*)malloc(sizeof(int) * (size_t)P);
+    if (!vals || !vok) { free(vals); free(vok); return -1; }
+    nthreads = default_threads(nthreads);
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    level_job* jobs = (level_job*)malloc(sizeof(level_job) * (size_t)nthreads);
+    for (int phase = 0; phase < 2; phase++) {
+        for (int t = 0; t < nthreads; t++) {
+            level_job jb = { s, N, X, vals, vok, tc, tsd, score, valid, t, nthreads };
+            jobs[t] = jb;
+            pthread_create(&th[t], NULL, phase == 0 ? level_table_worker : level_score_worker, &jobs[t]);
+        }
+        for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    }
+    free(th); free(jobs); free(vals); free(vok);
+    return 0;
+}
+
+int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+                      const double* target, double* score_out, int* valid_out, int nthreads) {
+    space_t s;
+    if (space_init(&s, d, ops, rung, grammar) || N < 2) return -1;
+    double* tc = (double*)malloc(sizeof(double) * (size_t)N);
+    double tsd = centre(target, N, tc);
+    if (!(tsd > 0.0)) { free(tc); return -2; }
+    if (scores_all_levelwise(&s, X, N, tc, tsd, score_out, valid_out, nthreads))
+        scores_threaded(&s, X, N, tc, tsd, NULL, s.phi[rung], score_out, valid_out, nthreads);
+    free(tc);
+    return 0;
+}
+
 int oracle_scores(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                   const double* target, const int64_t* ids, int64_t n_ids,
                   double* score_out, int* valid_out, int nthreads) {
@@ -436,7 +569,8 @@ static int sis_step(const space_t* s, const double* X, int N, const double* targ
     if (!(tsd > 0.0)) { free(tc); return -2; }
     double* score = (double*)malloc(sizeof(double) * (size_t)n_all);
     int* valid = (int*)malloc(sizeof(int) * (size_t)n_all);
-    scores_threaded(s, X, N, tc, tsd, NULL, n_all, score, valid, nthreads);
+    if (scores_all_levelwise(s, X, N, tc, tsd, score, valid, nthreads))
+        scores_threaded(s, X, N, tc, tsd, NULL, n_all, score, valid, nthreads);
 
     /* candidates: valid and not already in S */
     cand_t* c = (cand_t*)malloc(sizeof(cand_t) * (size_t)n_all);

@@ -52,6 +52,9 @@ int oracle_eval(int d, uint32_t ops, int rung, int grammar, const double* X, int
 int oracle_scores(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                   const double* target, const int64_t* ids, int64_t n_ids,
                   double* score_out, int* valid_out, int nthreads);
+/* the same for every id of phi_rung, evaluated level by level (bit-identical results) */
+int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+                      const double* target, double* score_out, int* valid_out, int nthreads);
 /* one SIS step: accept up to k ids (written to acc_out); returns number accepted or <0 */
 int oracle_sis(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                const double* target, const int64_t* S_prev, int n_prev, int k,

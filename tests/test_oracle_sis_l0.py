@@ -173,3 +173,20 @@ def test_l0_singular_subsets_skipped_and_ties(orc):
     assert rss == pytest.approx(0.0, abs=1e-9)
     # {0,2}, {1,2} and {3,2} all fit exactly; global ids (40,20), (30,20), (10,20): (10,20) wins
     assert sorted(pos) == [2, 3]
+
+
+@pytest.mark.parametrize("d,rung,grammar,N", [(3, 1, 0, 40), (4, 2, 0, 30), (2, 3, 0, 20), (3, 3, 1, 25)])
+def test_levelwise_scores_equal_per_id_scores(orc, d, rung, grammar, N):
+    """The whole-space scoring the SIS step uses (phi_{rung-1} evaluated once, new features
+    built from stored operands in canonical id order) gives the per-id path's scores and
+    validity bit for bit, with every operator of the table enabled and domain errors in
+    the data.  The per-id path is itself pinned against numpy above."""
+    rng = np.random.default_rng(100 * d + rung)
+    X = rng.uniform(-0.5, 3.0, size=(N, d))
+    y = rng.normal(size=N)
+    sp = orc.Space(d, (1 << 12) - 1, rung, grammar)
+    a, va = sp.scores(X, y)
+    b, vb = sp.scores_all(X, y)
+    assert np.array_equal(va, vb)
+    assert np.array_equal(a, b)
+    assert 0 < va.sum() < va.size
