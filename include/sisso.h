@@ -119,6 +119,9 @@ typedef struct {
     double ms_l0;                /* l0 enumeration (FP32 or FP64) */
     double ms_refit;             /* FP64 refit, winner, residual */
     double ms_fit;               /* whole sisso_fit, device time */
+    double ms_l0_enum;           /* ... of ms_l0: the tiled FP32 enumeration kernel alone */
+    int l0_enum_launches;        /* launches of the tiled FP32 enumeration kernel */
+    int64_t l0_candidates;       /* subsets its filter sent to the exact FP32/FP64 test */
 } sisso_stats;
 
 void sisso_default_opts(sisso_opts* opts);

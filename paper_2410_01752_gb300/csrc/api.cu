@@ -50,7 +50,7 @@ void free_all(sisso_ctx* c) {
                     c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
                     c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
-                    c->band_r32, c->band_sel};
+                    c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -153,6 +153,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         (st = dalloc(c, c->win, 1, "win")) || (st = dalloc(c, c->space_dev, 1, "space")))
         return bail(st);
     cudaMemcpyAsync(c->space_dev, &c->space, sizeof(Space), cudaMemcpyHostToDevice, c->stream);
+    if ((st = ensure_tile_buffers(c, c->n_cap))) return bail(st);
     // standardised FP64 vectors of the screening window, for the duplicate rule: up to
     // 4 GB (the walk evaluates on the fly when a window does not fit)
     c->zcap = std::min<int64_t>(c->surv_cap, ((int64_t)16 << 30) / ((int64_t)8 * N));

@@ -420,6 +420,13 @@ struct sisso_ctx {
     sg::Winner* win_h = nullptr;       // pinned host
     unsigned long long* blk_best = nullptr;  // per-block tie-break winners
     int blk_cap = 0;
+    // tiled FP32 enumeration: padded FP32 Gram, moments and diagonal (rows x tile_ld), tile list
+    float* tile_G = nullptr;
+    float* tile_b = nullptr;
+    float* tile_diag = nullptr;
+    int tile_rows = 0, tile_ld = 0;
+    void* tile_info = nullptr;
+    int tile_info_cap = 0;
 
     // results
     std::vector<int64_t> S;                       // acceptance order
@@ -462,6 +469,7 @@ void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles);
 // subspace and l0 (l0.cu)
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
 sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
+sisso_status ensure_tile_buffers(sisso_ctx* c, int n);
 sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,

@@ -22,11 +22,14 @@
 //  global-id tuple — the same rule as a full FP64 search.  In FP64 mode pass 1 gives the
 //  minimum and pass 2 the tie window directly.
 #include "l0_device.cuh"
+#include "l0_tile.cuh"
 
 #include <algorithm>
 #include <cfloat>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <vector>
 
 namespace sg {
 namespace {
@@ -485,12 +488,134 @@ static sisso_status run_enum(sisso_ctx* c, EnumArgs<T> A, int D, int mode) {
     return check_cuda(c, cudaGetLastError(), "l0_enum");
 }
 
+// padded FP32 copies and the tile list of the tiled enumeration, for up to n features
+sisso_status ensure_tile_buffers(sisso_ctx* c, int n) {
+    const int ld = kTC + (n + 31) / 32 * 32;                  // kTC zero columns, then the row
+    const int n_tiles = ((n + kTR - 1) / kTR) * ((n + kTC - 1) / kTC);
+    if (n <= c->tile_rows && ld <= c->tile_ld && n_tiles <= c->tile_info_cap) return SISSO_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->tile_G); cudaFree(c->tile_b); cudaFree(c->tile_diag); cudaFree(c->tile_info);
+    c->tile_G = c->tile_b = c->tile_diag = nullptr;
+    c->tile_info = nullptr;
+    c->tile_rows = c->tile_ld = c->tile_info_cap = 0;
+    sisso_status st;
+    if ((st = check_cuda(c, cudaMalloc(&c->tile_G, sizeof(float) * (size_t)n * ld), "tile_G")) ||
+        (st = check_cuda(c, cudaMalloc(&c->tile_b, sizeof(float) * (size_t)ld), "tile_b")) ||
+        (st = check_cuda(c, cudaMalloc(&c->tile_diag, sizeof(float) * (size_t)ld), "tile_diag")) ||
+        (st = check_cuda(c, cudaMalloc(&c->tile_info, sizeof(TileInfo) * (size_t)n_tiles), "tile_info")))
+        return st;
+    c->tile_rows = n; c->tile_ld = ld; c->tile_info_cap = n_tiles;
+    return SISSO_OK;
+}
+
+// Exhaustive FP32 l0 (D >= 2) by the single-pass tiled enumeration (l0_tile.cuh): padded
+// FP32 copies, a greedy FP64 bound, one enumeration launch, FP64 refit of the band and the
+// tie-broken winner.
+static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* b, int ld, double syy, int n, int D,
+                                   const int64_t* gid_dev, Winner& w) {
+    sisso_status st;
+    if ((st = ensure_tile_buffers(c, n))) return st;
+    const int DP = D - 2;
+    const int ldp = kTC + (n + 31) / 32 * 32;
+    // tiles (a, c): a row block [a, a + kTR) and a column block [c, c + kTC) starting at the
+    // row block (columns left of it hold no subsets); a tile's prefixes are the colex ranks
+    // below C(m, DP), m the largest row of the tile with a column to its right; one work
+    // unit per (tile, prefix)
+    std::vector<TileInfo> tiles;
+    int64_t items = 0;
+    for (int a = 0; a < n - 1; a += kTR)
+        for (int cc = a; cc < n; cc += kTC) {
+            const int m = std::min({a + kTR - 1, n - 2, cc + kTC - 2});
+            if (m < a || m < DP) continue;
+            const int64_t np = binom_host(m, DP);
+            if (np <= 0) continue;
+            tiles.push_back(TileInfo{a, cc, np, items});
+            items += np;
+        }
+    if ((int)tiles.size() > c->tile_info_cap) return fail(c, SISSO_ERR_CAPACITY, "l0: tile list");
+    cudaMemcpyAsync(c->tile_info, tiles.data(), sizeof(TileInfo) * tiles.size(), cudaMemcpyHostToDevice, c->stream);
+    const double sst = syy * c->N;
+    unsigned long long* ub_key = reinterpret_cast<unsigned long long*>(c->work + 2);
+    unsigned long long* examined = ub_key + 1;
+    unsigned long long* min_key = ub_key + 2;
+    unsigned long long* cand = ub_key + 3;
+    cudaEvent_t e0, e1, e2, e3, e4;
+    cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); cudaEventCreate(&e3); cudaEventCreate(&e4);
+    cudaEventRecord(e0, c->stream);
+    cudaMemsetAsync(c->work, 0, sizeof(unsigned long long), c->stream);   // 64-bit unit counter
+    cudaMemsetAsync(ub_key, 0xFF, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(min_key, 0xFF, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(examined, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(cand, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->band_count, 0, sizeof(unsigned), c->stream);
+    const int64_t tot = (int64_t)n * ldp;
+    k_pad_gram<<<std::max(1, (int)std::min<int64_t>(c->sms * 8, (tot + 255) / 256)), 256, 0, c->stream>>>(
+        G, b, ld, n, ldp, c->tile_G, c->tile_b, c->tile_diag);
+    k_greedy_bound<<<1, 256, 0, c->stream>>>(G, b, ld, syy, c->N, n, D, ub_key);
+    TileArgs A{};
+    A.G = c->tile_G + kTC; A.b = c->tile_b; A.diag = c->tile_diag; A.ldp = ldp; A.n = n; A.N = c->N; A.D = D;
+    A.syy = (float)syy; A.tau = kPivotMin32; A.sst = sst; A.sqrt_syy = std::sqrt(syy);
+    // filter: coefficient 1-norm bound Smax = 16 sqrt(syy); E1 = twice the a posteriori bound
+    // at Smax (|RSS| <= 2 SST) plus the rounding of the filter's own comparison
+    {
+        const double u = 5.9604644775390625e-8, c1 = 1.0 + 3.1 * (D + 1);
+        const double smax = 16.0 * std::sqrt(syy);
+        const double err = 2.0 * u * (c->N * (2.0 * std::sqrt(syy) * smax + c1 * smax * smax) + (D + 3) * 4.0 * sst);
+        A.Smax = (float)smax;
+        A.E1 = (float)(2.0 * err + 64.0 * u * sst);
+    }
+    A.tiles = reinterpret_cast<const TileInfo*>(c->tile_info); A.n_tiles = (int)tiles.size(); A.n_items = items;
+    A.counter = c->work; A.ub_key = ub_key; A.tie64 = 2.0 * kRssTie * sst;
+    A.G64 = G; A.b64 = b; A.ld64 = ld; A.syy64 = syy;
+    A.band = c->band; A.band_count = c->band_count; A.band_cap = c->band_cap; A.band_r32 = nullptr;
+    A.examined = examined; A.candidates = cand;
+    cudaEventRecord(e1, c->stream);
+    const int grid = c->sms * 2;
+    switch (DP) {
+        case 0: k_l0_tile<0><<<grid, kTW * 32, 0, c->stream>>>(A); break;
+        case 1: k_l0_tile<1><<<grid, kTW * 32, 0, c->stream>>>(A); break;
+        case 2: k_l0_tile<2><<<grid, kTW * 32, 0, c->stream>>>(A); break;
+        default: k_l0_tile<3><<<grid, kTW * 32, 0, c->stream>>>(A); break;
+    }
+    cudaEventRecord(e2, c->stream);
+    k_refit<<<c->sms * 4, 256, 0, c->stream>>>(G, b, ld, syy, c->N, D, c->band, c->band_count, c->band_cap,
+                                              c->band_rss, min_key);
+    k_winner<<<1, 1024, 0, c->stream>>>(c->band, c->band_rss, c->band_count, c->band_cap, min_key, kRssTie * sst,
+                                        gid_dev, D, c->win);
+    c->stats.launches += 5;
+    c->stats.l0_enum_launches++;
+    cudaEventRecord(e3, c->stream);
+    if ((st = check_cuda(c, cudaGetLastError(), "l0_tile"))) return st;
+    unsigned cnt = 0;
+    unsigned long long ex[2] = {0, 0};
+    cudaMemcpyAsync(&cnt, c->band_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&ex[0], examined, sizeof(ex[0]), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&ex[1], cand, sizeof(ex[1]), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(c->win_h, c->win, sizeof(Winner), cudaMemcpyDeviceToHost, c->stream);
+    cudaEventRecord(e4, c->stream);
+    if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "l0 tiled"))) return st;
+    c->stats.ms_l0 += event_ms(e0, e2);
+    c->stats.ms_l0_enum += event_ms(e1, e2);
+    c->stats.ms_refit += event_ms(e2, e3);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); cudaEventDestroy(e3); cudaEventDestroy(e4);
+    if ((int64_t)cnt > c->band_cap)
+        return fail(c, SISSO_ERR_CAPACITY, "l0: FP64 refit band exceeds max_band (" + std::to_string(cnt) + ")");
+    c->stats.subsets_fit += (int64_t)ex[0];
+    c->stats.l0_candidates += (int64_t)ex[1];
+    c->stats.subsets_refit += cnt;
+    w = *c->win_h;
+    w.examined = (int64_t)ex[0];
+    if (!w.found) return fail(c, SISSO_ERR_NUMERIC, "l0: every subset is singular");
+    return SISSO_OK;
+}
+
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,
                       const int* prefix_list, int64_t n_prefixes) {
     if (D < 1 || D > kMaxDim || n < D) return fail(c, SISSO_ERR_ARG, "l0: bad D or n");
     if (n > (D <= 4 ? 65535 : 4095)) return fail(c, SISSO_ERR_ARG, "l0: too many features for D");
     const bool fp32 = precision != SISSO_PREC_FP64;
+    if (fp32 && !prefix_list && D >= 2) return l0_solve_tiled(c, G, b, ld, syy, n, D, gid_dev, w);
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
     cudaEventRecord(e0, c->stream);

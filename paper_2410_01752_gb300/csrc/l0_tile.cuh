@@ -1,0 +1,537 @@
+// l0_tile.cuh — single-pass tiled enumeration of the exhaustive l0 search (§2.3, Eqs. 7-8)
+// in FP32 with an FP64 Gram at hand: every D-subset {p_0 < .. < p_{D-3} < i1 < i2} is
+// examined once, and the result is the exact FP64 optimum.
+//
+// Work decomposition.  The (i1, i2) plane is cut into tiles of kTR rows (i1) x kTC columns
+// (i2), column tiles starting at their row block; a work unit is one tile and one
+// (D-2)-prefix in colex order, taken by one warp from a global counter.  The warp factors
+// the prefix block, tabulates the prefix-reduced values of the tile's rows (shared memory,
+// per warp) and of the 8 columns each lane owns, cb + lane + 32 j (registers; the window
+// [cb, cb + kTC) ends at n for the last tile), and sweeps the rows in segments of equal
+// first live column group, so that no per-group bound is tested inside the sweep.  Per
+// subset, with 1/d1 and w1/sqrt(d1) precomputed per row:
+//     g = G[i1][i2] - sum_m R[m][i1] R[m][i2],   d2 = dp[i2] - g^2 / d1,
+//     num = np[i2] - g w1 / sqrt(d1),   RSS = N (c - num^2 / d2),  c = syy - |w_prefix|^2 - w1^2
+// as in the two-pass enumerator, but the decision is a division-free filter:
+//     candidate  <=>  not ( num^2 - cB d2 < 0   and   S1 |num| - Rk d2 <= 0   and  d2 > tau )
+// cB puts the FP32 RSS above B + tie + E1 (B the running bound, below), and the second
+// test bounds the subset's coefficient 1-norm s = |gamma|_1 by Smax: with a = L_P^-T w_P,
+// a1 = L_P^-T R[.][i1], a2 = L_P^-T R[.][i2] (prefix back substitutions),
+//     s <= |a|_1 + (1 + |a1|_1) |w1| / sqrt(d1)
+//            + ((1 + |a1|_1) |r| / sqrt(d1) + 1 + |a2|_1) |num| / d2,   |r| <= 1,
+// i.e. s <= S0 + S1' |num| / d2, and s <= Smax keeps the a posteriori FP32 error below E1/2.
+// So a subset that is not a candidate has RSS_FP32 - err > B + tie: it cannot be the
+// minimum nor tie with it.  Candidates (a fraction of a percent on screened subspaces)
+// go through a per-warp queue to the exact test of the two-pass form: the FP32 RSS and
+// its a posteriori bound from the back-substituted coefficients, then an FP64 solve from
+// the FP64 Gram; a subset whose FP64 RSS is within B + tie enters the band and lowers B.
+//
+// Running bound.  B starts at the FP64 RSS of a greedy forward selection (an upper bound
+// of the minimum M) and only decreases, to FP64 RSS values of visited subsets, so B >= M
+// at every moment.  The optimum E* has RSS_FP32 - err <= M <= B, and every tie E of it
+// RSS_FP64(E) <= M + tie <= B + tie: both are candidates whenever visited and enter the
+// band.  The band (records and ties) is then refit in FP64 and the tie rule picks the
+// winner, exactly as after the two-pass form.
+#pragma once
+
+#include "l0_device.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int kTR = 64;                  // i1 rows per tile
+constexpr int kTC = 256;                 // i2 columns per tile: 8 per lane
+constexpr int kTW = 8;                   // warps per CTA = prefixes per work item
+constexpr int kTQ = kTC + 64;            // per-warp candidate queue (entries)
+
+struct TileInfo {
+    int a, c;                            // first row, first column
+    int64_t n_pre;                       // prefixes (colex ranks 0 .. n_pre-1)
+    int64_t item0;                       // first work item of this tile
+};
+
+struct TileArgs {
+    const float* G;                      // FP32 Gram, padded: row stride ldp (multiple of kTC), 16-byte rows
+    const float* b;                      // FP32 moments, padded to ldp with zeros
+    const float* diag;                   // G[x][x], padded to ldp with ones
+    int ldp, n, N, D;
+    float syy, tau;
+    double sst, sqrt_syy;
+    float E1, Smax;                      // filter window and coefficient bound (FP32 RSS units / sqrt(syy) units)
+    const TileInfo* tiles;
+    int n_tiles;
+    int64_t n_items;
+    int* counter;
+    unsigned long long* ub_key;          // running bound B (ordered FP64 key)
+    double tie64;
+    const double* G64;                   // FP64 Gram (ld64) and moments for the confirmations
+    const double* b64;
+    int ld64;
+    double syy64;
+    uint64_t* band;
+    unsigned* band_count;
+    int64_t band_cap;
+    float* band_r32;
+    unsigned long long* examined;
+    unsigned long long* candidates;      // subsets sent to the exact test
+};
+
+// a posteriori bound on |RSS_FP32 - RSS| (the same formula as the two-pass form)
+__device__ __forceinline__ float tile_apost_err(const TileArgs& A, float s, float rss) {
+    const float u = 5.9604644775390625e-8f;
+    const float c1 = 1.f + 3.1f * (float)(A.D + 1);
+    return 2.f * u * ((float)A.N * (2.f * (float)A.sqrt_syy * s + c1 * s * s) +
+                      (float)(A.D + 3) * (2.f * (float)A.sst + fabsf(rss)));
+}
+
+// r-th DP-combination in colex order, as colex_unrank but from FP32 estimates of the
+// largest element (sqrt / cbrt of the rank) corrected by exact 64-bit integer steps: the
+// GB300 FP64 pipe runs at a small fraction of the FP32 rate
+__device__ __forceinline__ int64_t top2_fast(int64_t r) {
+    int64_t m = (int64_t)((1.f + sqrtf(1.f + 8.f * (float)r)) * 0.5f);
+    if (m < 1) m = 1;
+    while (m > 1 && binom2(m) > r) --m;
+    while (binom2(m + 1) <= r) ++m;
+    return m;
+}
+__device__ __forceinline__ int64_t top3_fast(int64_t r) {
+    int64_t m = (int64_t)cbrtf(6.f * (float)r) + 1;
+    if (m < 2) m = 2;
+    while (m > 2 && binom3(m) > r) --m;
+    while (binom3(m + 1) <= r) ++m;
+    return m;
+}
+template <int DP> __device__ __forceinline__ void colex_unrank_fast(int64_t r, int (&p)[DP > 0 ? DP : 1]) {
+    if (DP == 0) return;
+    if (DP == 1) { p[0] = (int)r; return; }
+    int64_t m;
+    if (DP >= 3) { m = top3_fast(r); p[DP > 2 ? 2 : 0] = (int)m; r -= binom3(m); }
+    m = top2_fast(r);
+    p[1] = (int)m;
+    p[0] = (int)(r - binom2(m));
+}
+
+// prefix factor of one warp's current prefix, in shared memory (read by the exact test)
+struct PrefixSm {
+    int pre[4];
+    float L[3][3], invd[3], wv[3];
+};
+
+// prefix-reduced values of feature x: R[m][x], dp = G[x][x] - sum R^2, np = b[x] - sum R w
+template <int DP>
+__device__ __forceinline__ void prefix_reduce(const TileArgs& A, const int (&pre)[DP > 0 ? DP : 1],
+                                              const float (&L)[DP > 0 ? DP : 1][DP > 0 ? DP : 1],
+                                              const float (&invd)[DP > 0 ? DP : 1], const float (&wv)[DP > 0 ? DP : 1],
+                                              int x, float (&r)[DP > 0 ? DP : 1], float& dp, float& np) {
+    dp = A.diag[x];
+    np = A.b[x];
+#pragma unroll
+    for (int m = 0; m < DP; ++m) {
+        float v = A.G[(size_t)pre[m] * A.ldp + x];
+#pragma unroll
+        for (int q = 0; q < m; ++q) v -= r[q] * L[m][q];
+        r[m] = v * invd[m];
+        dp -= r[m] * r[m];
+        np -= r[m] * wv[m];
+    }
+}
+
+// |L_P^-T v|_1
+template <int DP>
+__device__ __forceinline__ float back_l1(const float (&L)[DP > 0 ? DP : 1][DP > 0 ? DP : 1],
+                                         const float (&invd)[DP > 0 ? DP : 1], const float (&v)[DP > 0 ? DP : 1]) {
+    float g[DP > 0 ? DP : 1];
+    float s = 0.f;
+#pragma unroll
+    for (int j = DP - 1; j >= 0; --j) {
+        float t = v[j];
+#pragma unroll
+        for (int m = j + 1; m < DP; ++m) t -= L[m][j] * g[m];
+        g[j] = t * invd[j];
+        s += fabsf(g[j]);
+    }
+    return s;
+}
+
+// per-warp row record: R[.][i1], 1/sqrt(d1), w1, c, S1, Rk, flags (bit 1: pivots of the
+// prefix and of i1 are above tau), padded to a multiple of 4 words
+__host__ __device__ constexpr int row_words(int DP) { return ((DP + 6) + 3) & ~3; }
+
+template <int DP>
+__device__ __forceinline__ void add_band(const TileArgs& A, const int (&pos)[DP + 2], float r32) {
+    const unsigned slot = atomicAdd(A.band_count, 1u);
+    if (slot < A.band_cap) {
+        uint64_t k = 0;
+        int s = 0;
+        const int W = pos_bits(DP + 2);
+#pragma unroll
+        for (int m = 0; m < DP + 2; ++m) { k |= (uint64_t)pos[m] << s; s += W; }
+        A.band[slot] = k;
+        if (A.band_r32) A.band_r32[slot] = r32;
+    }
+}
+
+// the exact decision for one candidate (i1 = a + k, column x); returns the lane's new bound
+template <int DP>
+__device__ __noinline__ double tile_exact(const TileArgs& A, const PrefixSm* Ps, const float* rowrec, int a, int k,
+                                          int x, double B, double thr, float thr32) {
+    const int i1 = a + k;
+    if (!(x > i1 && x < A.n)) return B;
+    constexpr int RW = row_words(DP);
+    int pre[DP > 0 ? DP : 1];
+    float L[DP > 0 ? DP : 1][DP > 0 ? DP : 1], invd[DP > 0 ? DP : 1], wv[DP > 0 ? DP : 1];
+#pragma unroll
+    for (int m = 0; m < DP; ++m) {
+        pre[m] = Ps->pre[m];
+        invd[m] = Ps->invd[m];
+        wv[m] = Ps->wv[m];
+#pragma unroll
+        for (int q = 0; q < DP; ++q) L[m][q] = Ps->L[m][q];
+    }
+    const float* rr_ = rowrec + k * RW;
+    float r1[DP > 0 ? DP : 1];
+#pragma unroll
+    for (int m = 0; m < DP; ++m) r1[m] = rr_[m];
+    const float isd1 = rr_[DP], w1 = rr_[DP + 1], base_c = rr_[DP + 2];
+    const int flags = __float_as_int(rr_[DP + 5]);
+    float rt[DP > 0 ? DP : 1], dp2, np2;
+    prefix_reduce<DP>(A, pre, L, invd, wv, x, rt, dp2, np2);
+    float g = A.G[(size_t)i1 * A.ldp + x];
+#pragma unroll
+    for (int m = 0; m < DP; ++m) g -= r1[m] * rt[m];
+    const float rr = g * isd1;
+    const float d2 = dp2 - rr * rr;
+    const float num = np2 - rr * w1;
+    int pos[DP + 2];
+#pragma unroll
+    for (int m = 0; m < DP; ++m) pos[m] = pre[m];
+    pos[DP] = i1;
+    pos[DP + 1] = x;
+    float r32 = __int_as_float(0x7fc00000);
+    if ((flags & 2) && d2 > A.tau) {
+        const float rss = (float)A.N * (base_c - num * num / d2);
+        r32 = rss;
+        if (!(rss <= thr32)) {
+            // coefficients gamma = L^-T w and the a posteriori bound
+            const float g2 = num / d2;
+            const float g1 = (w1 - rr * g2) * isd1;
+            float sg = fabsf(g2) + fabsf(g1);
+            float gp[DP > 0 ? DP : 1];
+#pragma unroll
+            for (int j = DP - 1; j >= 0; --j) {
+                float v = wv[j] - r1[j] * g1 - rt[j] * g2;
+#pragma unroll
+                for (int m = j + 1; m < DP; ++m) v -= L[m][j] * gp[m];
+                gp[j] = v * invd[j];
+                sg += fabsf(gp[j]);
+            }
+            if (!(rss - tile_apost_err(A, sg, rss) <= thr32)) return B;
+        }
+    }
+    // FP64 confirmation from the FP64 Gram
+    const double r64 = rss64(A.G64, A.b64, A.ld64, A.syy64, A.N, DP + 2, pos, nullptr);
+    if (!(r64 <= thr)) return B;
+    add_band<DP>(A, pos, r32);
+    if (r64 < B) {
+        atomicMin(A.ub_key, okey(r64));
+        return r64;
+    }
+    return B;
+}
+
+// the warp's queued candidates (row k, column cb + offset) through the exact test;
+// returns the warp's bound
+template <int DP>
+__device__ __forceinline__ double tile_flush(const TileArgs& A, const PrefixSm* Ps, const float* rowrec,
+                                             const unsigned short* q, int qn, int a, int cb, int lane, double B) {
+    // the threshold of the whole flush: B + tie (a lane's own B only decreases meanwhile,
+    // so the flush keeps a superset of what the lane-current threshold would keep)
+    const double thr = B + A.tie64;
+    const float thr32 = __double2float_ru(thr);
+    for (int e = lane; e < qn; e += 32) {
+        const unsigned v = q[e];
+        B = tile_exact<DP>(A, Ps, rowrec, a, (int)(v >> 8), cb + (int)(v & 255u), B, thr, thr32);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) B = fmin(B, __shfl_xor_sync(0xffffffffu, B, o));
+    return fmin(B, okey_inv(*(volatile unsigned long long*)A.ub_key));
+}
+
+template <int DP>
+__global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
+    constexpr int DPa = DP > 0 ? DP : 1;
+    constexpr int RW = row_words(DP);
+    __shared__ __align__(16) float s_row[kTW][kTR * RW];
+    __shared__ unsigned short s_q[kTW][kTQ];
+    __shared__ PrefixSm s_pf[kTW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* rowrec = s_row[w];
+    unsigned short* q = s_q[w];
+    PrefixSm* Ps = &s_pf[w];
+    const float N = (float)A.N;
+    double B = INFINITY;                            // fmin ignores an unset (NaN) key
+    B = fmin(B, okey_inv(*(volatile unsigned long long*)A.ub_key));
+    unsigned long long my_examined = 0, my_cand = 0;
+
+    while (true) {
+        // one work unit per warp: (tile, prefix)
+        int64_t item = 0;
+        if (lane == 0) item = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(A.counter), 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= A.n_items) break;
+        int lo = 0, hi = A.n_tiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.tiles[mid].item0 <= item) lo = mid; else hi = mid - 1;
+        }
+        const int a = A.tiles[lo].a, c = A.tiles[lo].c;
+        const int64_t prank = item - A.tiles[lo].item0;
+
+        // column groups j (columns c + 32 j + lane) and rows of this unit
+        int pm = -1;
+        int row_lo, row_hi, j_lo, jc, cb;
+        float q2 = 0.f, pw2 = 0.f;
+        float rt[8][DPa], dp2[8], np2[8];
+        {
+            // ---- prefix factor (warp-uniform, redundant in every lane) ---------------
+            int pre[DPa];
+            float L[DPa][DPa], invd[DPa], wv[DPa];
+            colex_unrank_fast<DP>(prank, pre);
+            bool ok = true;
+#pragma unroll
+            for (int j = 0; j < DP; ++j) {
+                float dj = A.diag[pre[j]];
+#pragma unroll
+                for (int m = 0; m < j; ++m) dj -= L[j][m] * L[j][m];
+                ok = ok && dj > A.tau;
+                const float ljj = sqrtf(dj > 0.f ? dj : 1.f);
+                L[j][j] = ljj;
+                invd[j] = 1.f / ljj;
+#pragma unroll
+                for (int i = j + 1; i < DP; ++i) {
+                    float v = A.G[(size_t)pre[i] * A.ldp + pre[j]];
+#pragma unroll
+                    for (int m = 0; m < j; ++m) v -= L[i][m] * L[j][m];
+                    L[i][j] = v * invd[j];
+                }
+                float v = A.b[pre[j]];
+#pragma unroll
+                for (int m = 0; m < j; ++m) v -= L[j][m] * wv[m];
+                wv[j] = v * invd[j];
+                pw2 += wv[j] * wv[j];
+            }
+#pragma unroll
+            for (int i = 0; i < DP; ++i)
+#pragma unroll
+                for (int j = i + 1; j < DP; ++j) L[i][j] = 0.f;
+            if (lane == 0) {
+#pragma unroll
+                for (int m = 0; m < DP; ++m) {
+                    Ps->pre[m] = pre[m];
+                    Ps->invd[m] = invd[m];
+                    Ps->wv[m] = wv[m];
+#pragma unroll
+                    for (int qq = 0; qq < DP; ++qq) Ps->L[m][qq] = L[m][qq];
+                }
+            }
+            const float A0 = back_l1<DP>(L, invd, wv);
+            if (DP > 0) pm = pre[DP > 0 ? DP - 1 : 0];
+            row_lo = max(a, pm + 1);                                       // first row with subsets
+            row_hi = min(a + kTR - 1, min(A.n - 2, c + kTC - 2));          // last
+            // the lanes' columns cb + lane + 32 j: the window [cb, cb + kTC) holds the tile's
+            // columns [c, min(c + kTC, n)) and ends at n for the last tile (cb may be < 0:
+            // the padded copy has kTC zero columns on the left)
+            cb = min(c, A.n - kTC);
+            jc = (c - cb) >> 5;                                            // group of column c
+            j_lo = max(jc, (row_lo + 1 - cb) >> 5);                        // first group right of row_lo
+
+            // ---- columns: this lane's columns c + lane + 32 j in registers -----------
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int x = cb + lane + 32 * j;
+                if (j >= j_lo && x >= c && x < A.n) {
+                    prefix_reduce<DP>(A, pre, L, invd, wv, x, rt[j], dp2[j], np2[j]);
+                    q2 = fmaxf(q2, back_l1<DP>(L, invd, rt[j]));
+                } else {
+#pragma unroll
+                    for (int m = 0; m < DP; ++m) rt[j][m] = 0.f;
+                    dp2[j] = 1.f;
+                    np2[j] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q2 = fmaxf(q2, __shfl_xor_sync(0xffffffffu, q2, o));
+
+            // ---- rows: record per row in shared memory --------------------------------
+            for (int i1 = row_lo + lane; i1 <= row_hi; i1 += 32) {
+                float* rr_ = rowrec + (i1 - a) * RW;
+                float r1[DPa], d1, n1;
+                prefix_reduce<DP>(A, pre, L, invd, wv, i1, r1, d1, n1);
+                const bool piv = ok && d1 > A.tau;
+                const float isd1 = 1.f / sqrtf(d1 > 0.f ? d1 : 1.f);
+                const float w1 = n1 * isd1;
+                const float a1 = back_l1<DP>(L, invd, r1);
+                const float S0 = A0 + (1.f + a1) * fabsf(w1) * isd1;
+                const float S1 = 1.02f * ((1.f + a1) * isd1 * 1.0001f + 1.f + q2);
+#pragma unroll
+                for (int m = 0; m < DP; ++m) rr_[m] = r1[m];
+                rr_[DP] = isd1;
+                rr_[DP + 1] = w1;
+                rr_[DP + 2] = A.syy - (pw2 + w1 * w1);
+                rr_[DP + 3] = S1;
+                rr_[DP + 4] = piv ? A.Smax - 1.02f * S0 : -INFINITY;
+                rr_[DP + 5] = __int_as_float(piv ? 2 : 0);
+                const int lo_c = max(c, i1 + 1), hi_c = min(c + kTC, A.n);
+                if (hi_c > lo_c) my_examined += (unsigned long long)(hi_c - lo_c);
+            }
+        }
+        __syncwarp();
+
+        // ---- sweep -------------------------------------------------------------------
+        // this lane's columns that belong to the tile: bits j with c <= cb + lane + 32 j < n
+        unsigned nmask = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int x = cb + lane + 32 * j;
+            nmask |= (x >= c && x < A.n) ? (1u << j) : 0u;
+        }
+        int qn = 0;                                     // queue length (warp-uniform)
+        float thrN = (float)((B + A.tie64) / (double)A.N) + A.E1 / N;
+        int i1 = row_lo;
+        // rows in segments of equal first live group J (the groups holding a column right
+        // of i1 are J .. 7), so that every segment's group range is fixed at compile time
+#pragma unroll
+        for (int J = 0; J < 8; ++J) {
+            const int seg_end = J < j_lo ? row_lo - 1 : (J == 7 ? row_hi : min(row_hi, cb + 32 * J + 30));
+            for (; i1 <= seg_end; ++i1) {
+                const int k = i1 - a;
+                const float4* rv = reinterpret_cast<const float4*>(rowrec + k * RW);
+                float rec[RW];
+#pragma unroll
+                for (int v4 = 0; v4 < RW / 4; ++v4) {
+                    const float4 t = rv[v4];
+                    rec[4 * v4] = t.x; rec[4 * v4 + 1] = t.y; rec[4 * v4 + 2] = t.z; rec[4 * v4 + 3] = t.w;
+                }
+                // per row: 1/d1 and w1/sqrt(d1), so that r = g/sqrt(d1) is never formed:
+                // d2 = dp2 - g^2/d1, num = np2 - g w1/sqrt(d1)
+                const float isd1 = rec[DP], w1 = rec[DP + 1];
+                const float id1 = isd1 * isd1, w1s = w1 * isd1;
+                const float S1 = rec[DP + 3], Rk = rec[DP + 4];
+                const float cB = rec[DP + 2] - thrN;
+                // columns right of i1: j >= js, js the smallest j with cb + lane + 32 j > i1
+                const int dj = i1 - cb - lane;
+                const int js = dj < 0 ? 0 : (dj >> 5) + 1;
+                const unsigned vmask = nmask & (js >= 8 ? 0u : (0xFFu << js));
+                const float* grow = A.G + (size_t)i1 * A.ldp + cb + lane;
+                float gv[8];
+#pragma unroll
+                for (int j = J; j < 8; ++j) gv[j] = grow[32 * j];
+                unsigned mask = 0;
+#pragma unroll
+                for (int j = J; j < 8; ++j) {
+                    float g = gv[j];
+#pragma unroll
+                    for (int m = 0; m < DP; ++m) g -= rec[m] * rt[j][m];
+                    const float d2 = dp2[j] - g * g * id1;
+                    const float num = np2[j] - g * w1s;
+                    const float f = num * num - cB * d2;
+                    const float e = S1 * fabsf(num) - Rk * d2;
+                    mask |= (f < 0.f && e <= 0.f && d2 > A.tau) ? 0u : (1u << j);
+                }
+                mask &= vmask;
+                if (__any_sync(0xffffffffu, mask != 0)) {
+                    const int cnt = __popc(mask);
+                    int off = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(0xffffffffu, off, o);
+                        if (lane >= o) off += t;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, off, 31);
+                    off -= cnt;
+                    while (mask) {
+                        const int j = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        q[qn + off++] = (unsigned short)((k << 8) | (lane + 32 * j));
+                    }
+                    qn += total;
+                    __syncwarp();
+                    if (qn > kTQ - kTC) {
+                        B = tile_flush<DP>(A, Ps, rowrec, q, qn, a, cb, lane, B);
+                        my_cand += qn;
+                        qn = 0;
+                        thrN = (float)((B + A.tie64) / (double)A.N) + A.E1 / N;
+                    }
+                }
+            }
+        }
+        if (qn > 0) {
+            B = tile_flush<DP>(A, Ps, rowrec, q, qn, a, cb, lane, B);
+            my_cand += qn;
+        }
+        __syncwarp();
+    }
+    my_examined = l0_warp_sum(my_examined);
+    if (lane == 0) {
+        atomicAdd(A.examined, my_examined);
+        atomicAdd(A.candidates, my_cand);
+    }
+}
+
+// greedy forward selection in FP64: its D-subset's RSS is an upper bound of the minimum
+__global__ void k_greedy_bound(const double* __restrict__ G, const double* __restrict__ b, int ld, double syy, int N,
+                               int n, int D, unsigned long long* ub_key) {
+    __shared__ double s_val[256];
+    __shared__ int s_idx[256];
+    __shared__ int sel[kMaxDim];
+    int pos[kMaxDim];
+    for (int t = 0; t < D; ++t) {
+        double best = INFINITY;
+        int bi = -1;
+        for (int x = threadIdx.x; x < n; x += blockDim.x) {
+            bool used = false;
+            for (int j = 0; j < t; ++j) used |= sel[j] == x;
+            if (used) continue;
+            for (int j = 0; j < t; ++j) pos[j] = sel[j];
+            pos[t] = x;
+            const double r = rss64(G, b, ld, syy, N, t + 1, pos, nullptr);
+            if (r < best) { best = r; bi = x; }
+        }
+        s_val[threadIdx.x] = best;
+        s_idx[threadIdx.x] = bi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = INFINITY;
+            int bx = -1;
+            for (int q = 0; q < (int)blockDim.x; ++q)
+                if (s_idx[q] >= 0 && s_val[q] < bv) { bv = s_val[q]; bx = s_idx[q]; }
+            if (bx < 0) {                       // every extension singular: give up (bound stays)
+                sel[t] = -1;
+            } else {
+                sel[t] = bx;
+                if (t == D - 1) atomicMin(ub_key, okey(bv));
+            }
+        }
+        __syncthreads();
+        if (sel[t] < 0) return;
+    }
+}
+
+// padded FP32 copies for the tiled enumeration: row i of Gp holds kTC zero columns, then
+// (float)G[i][0..n), then zeros up to the stride ldp; bp, diag: (float)b, G[x][x] (padding 0, 1)
+__global__ void k_pad_gram(const double* __restrict__ G, const double* __restrict__ b, int ld, int n, int ldp,
+                           float* __restrict__ Gp, float* __restrict__ bp, float* __restrict__ dg) {
+    const int64_t total = (int64_t)n * ldp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldp), x = (int)(e % ldp) - kTC;
+        Gp[e] = x >= 0 && x < n ? (float)G[(size_t)i * ld + x] : 0.f;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ldp; j += gridDim.x * blockDim.x) {
+        bp[j] = j < n ? (float)b[j] : 0.f;
+        dg[j] = j < n ? (float)G[(size_t)j * ld + j] : 1.f;
+    }
+}
+
+}  // namespace
+}  // namespace sg

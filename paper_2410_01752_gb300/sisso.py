@@ -67,7 +67,8 @@ class Stats(C.Structure):
                 ("ms_radix", C.c_double), ("ms_rescore", C.c_double), ("ms_sort", C.c_double),
                 ("ms_walk", C.c_double), ("walk_visited", C.c_int64), ("walk_dup_checks", C.c_int64),
                 ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
-                ("ms_fit", C.c_double)]
+                ("ms_fit", C.c_double), ("ms_l0_enum", C.c_double), ("l0_enum_launches", C.c_int),
+                ("l0_candidates", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -154,9 +154,16 @@ def _gram_case(seed, n, N=200, collinear=False):
 @pytest.mark.parametrize("n,D,seed,col", [(20, 1, 0, False), (40, 2, 1, False), (60, 3, 2, False),
                                           (45, 4, 3, False), (33, 3, 4, True), (30, 4, 5, True),
                                           (4, 4, 6, False), (97, 2, 7, True), (24, 5, 8, False),
-                                          (31, 5, 9, True), (5, 5, 10, False)])
+                                          (31, 5, 9, True), (5, 5, 10, False),
+                                          # several 64-row x 256-column tiles and ragged edges
+                                          (300, 2, 11, False), (517, 2, 12, True), (260, 3, 13, False),
+                                          (301, 3, 14, True), (130, 4, 15, False), (150, 4, 16, True),
+                                          (66, 5, 17, False), (70, 5, 18, True)])
 def test_l0_search(S, orc, n, D, seed, col, prec):
     G, b, syy, N = _gram_case(seed, n, collinear=col)
+    if n > 64:          # move the planted features (and the collinear pairs) into later tiles
+        perm = np.random.default_rng(seed + 90).permutation(n)
+        G, b = G[np.ix_(perm, perm)], b[perm]
     gid = np.random.default_rng(seed + 50).permutation(10 * n)[:n]
     pos_ref, rss_ref, ex_ref = orc.l0(G, b, syy, N, D, gid)
     X = np.random.default_rng(0).uniform(1, 2, size=(N, 2))
