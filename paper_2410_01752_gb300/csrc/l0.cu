@@ -571,12 +571,19 @@ static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* 
     A.examined = examined; A.candidates = cand;
     cudaEventRecord(e1, c->stream);
     const int grid = c->sms * 2;
+#define SG_TILE(DPV)                                                                                   \
+    do {                                                                                               \
+        const size_t sm = tile_smem_bytes(DPV);                                                        \
+        cudaFuncSetAttribute(k_l0_tile<DPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+        k_l0_tile<DPV><<<grid, kTW * 32, sm, c->stream>>>(A);                                          \
+    } while (0)
     switch (DP) {
-        case 0: k_l0_tile<0><<<grid, kTW * 32, 0, c->stream>>>(A); break;
-        case 1: k_l0_tile<1><<<grid, kTW * 32, 0, c->stream>>>(A); break;
-        case 2: k_l0_tile<2><<<grid, kTW * 32, 0, c->stream>>>(A); break;
-        default: k_l0_tile<3><<<grid, kTW * 32, 0, c->stream>>>(A); break;
+        case 0: SG_TILE(0); break;
+        case 1: SG_TILE(1); break;
+        case 2: SG_TILE(2); break;
+        default: SG_TILE(3); break;
     }
+#undef SG_TILE
     cudaEventRecord(e2, c->stream);
     k_refit<<<c->sms * 4, 256, 0, c->stream>>>(G, b, ld, syy, c->N, D, c->band, c->band_count, c->band_cap,
                                               c->band_rss, min_key);

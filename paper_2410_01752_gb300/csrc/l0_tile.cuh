@@ -173,9 +173,9 @@ __device__ __forceinline__ void add_band(const TileArgs& A, const int (&pos)[DP 
 
 // the exact decision for one candidate (i1 = a + k, column x); returns the lane's new bound
 template <int DP>
-__device__ __noinline__ double tile_exact(const TileArgs& A, const PrefixSm* Ps, const float* rowrec, int a, int k,
-                                          int x, double B, double thr, float thr32) {
-    const int i1 = a + k;
+__device__ __noinline__ double tile_exact(const TileArgs& A, const PrefixSm* Ps, const float* rowrec, const float* colv,
+                                          int a, int k, int off, int cb, float g, double B, double thr, float thr32) {
+    const int i1 = a + k, x = cb + off;
     if (!(x > i1 && x < A.n)) return B;
     constexpr int RW = row_words(DP);
     int pre[DP > 0 ? DP : 1];
@@ -194,11 +194,10 @@ __device__ __noinline__ double tile_exact(const TileArgs& A, const PrefixSm* Ps,
     for (int m = 0; m < DP; ++m) r1[m] = rr_[m];
     const float isd1 = rr_[DP], w1 = rr_[DP + 1], base_c = rr_[DP + 2];
     const int flags = __float_as_int(rr_[DP + 5]);
-    float rt[DP > 0 ? DP : 1], dp2, np2;
-    prefix_reduce<DP>(A, pre, L, invd, wv, x, rt, dp2, np2);
-    float g = A.G[(size_t)i1 * A.ldp + x];
+    float rt[DP > 0 ? DP : 1];
 #pragma unroll
-    for (int m = 0; m < DP; ++m) g -= r1[m] * rt[m];
+    for (int m = 0; m < DP; ++m) rt[m] = colv[m * kTC + off];
+    const float dp2 = colv[DP * kTC + off], np2 = colv[(DP + 1) * kTC + off];
     const float rr = g * isd1;
     const float d2 = dp2 - rr * rr;
     const float num = np2 - rr * w1;
@@ -243,14 +242,15 @@ __device__ __noinline__ double tile_exact(const TileArgs& A, const PrefixSm* Ps,
 // returns the warp's bound
 template <int DP>
 __device__ __forceinline__ double tile_flush(const TileArgs& A, const PrefixSm* Ps, const float* rowrec,
-                                             const unsigned short* q, int qn, int a, int cb, int lane, double B) {
+                                             const float* colv, const unsigned short* q, const float* qg, int qn,
+                                             int a, int cb, int lane, double B) {
     // the threshold of the whole flush: B + tie (a lane's own B only decreases meanwhile,
     // so the flush keeps a superset of what the lane-current threshold would keep)
     const double thr = B + A.tie64;
     const float thr32 = __double2float_ru(thr);
     for (int e = lane; e < qn; e += 32) {
         const unsigned v = q[e];
-        B = tile_exact<DP>(A, Ps, rowrec, a, (int)(v >> 8), cb + (int)(v & 255u), B, thr, thr32);
+        B = tile_exact<DP>(A, Ps, rowrec, colv, a, (int)(v >> 8), (int)(v & 255u), cb, qg[e], B, thr, thr32);
     }
     __syncwarp();
 #pragma unroll
@@ -262,13 +262,18 @@ template <int DP>
 __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
     constexpr int DPa = DP > 0 ? DP : 1;
     constexpr int RW = row_words(DP);
-    __shared__ __align__(16) float s_row[kTW][kTR * RW];
-    __shared__ unsigned short s_q[kTW][kTQ];
-    __shared__ PrefixSm s_pf[kTW];
+    extern __shared__ __align__(16) unsigned char tile_smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* rowrec = s_row[w];
-    unsigned short* q = s_q[w];
-    PrefixSm* Ps = &s_pf[w];
+    // per warp: row records, column table (DP + 2 rows of kTC values), candidate queue
+    // (packed row / column and the candidate's g), prefix factor
+    float* rowrec = reinterpret_cast<float*>(tile_smem) + (size_t)w * kTR * RW;
+    float* colv = reinterpret_cast<float*>(tile_smem) + (size_t)kTW * kTR * RW + (size_t)w * (DP + 2) * kTC;
+    float* qg = reinterpret_cast<float*>(tile_smem) + (size_t)kTW * (kTR * RW + (DP + 2) * kTC) + (size_t)w * kTQ;
+    PrefixSm* Ps = reinterpret_cast<PrefixSm*>(reinterpret_cast<float*>(tile_smem) +
+                                               (size_t)kTW * (kTR * RW + (DP + 2) * kTC + kTQ)) + w;
+    unsigned short* q = reinterpret_cast<unsigned short*>(reinterpret_cast<PrefixSm*>(
+                            reinterpret_cast<float*>(tile_smem) + (size_t)kTW * (kTR * RW + (DP + 2) * kTC + kTQ)) +
+                        kTW) + (size_t)w * kTQ;
     const float N = (float)A.N;
     double B = INFINITY;                            // fmin ignores an unset (NaN) key
     B = fmin(B, okey_inv(*(volatile unsigned long long*)A.ub_key));
@@ -359,6 +364,10 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
                     dp2[j] = 1.f;
                     np2[j] = 0.f;
                 }
+#pragma unroll
+                for (int m = 0; m < DP; ++m) colv[m * kTC + lane + 32 * j] = rt[j][m];
+                colv[DP * kTC + lane + 32 * j] = dp2[j];
+                colv[(DP + 1) * kTC + lane + 32 * j] = np2[j];
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) q2 = fmaxf(q2, __shfl_xor_sync(0xffffffffu, q2, o));
@@ -433,6 +442,7 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
                     float g = gv[j];
 #pragma unroll
                     for (int m = 0; m < DP; ++m) g -= rec[m] * rt[j][m];
+                    gv[j] = g;
                     const float d2 = dp2[j] - g * g * id1;
                     const float num = np2[j] - g * w1s;
                     const float f = num * num - cB * d2;
@@ -450,15 +460,17 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
                     }
                     const int total = __shfl_sync(0xffffffffu, off, 31);
                     off -= cnt;
-                    while (mask) {
-                        const int j = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        q[qn + off++] = (unsigned short)((k << 8) | (lane + 32 * j));
+#pragma unroll
+                    for (int j = J; j < 8; ++j) {
+                        if (!((mask >> j) & 1u)) continue;
+                        q[qn + off] = (unsigned short)((k << 8) | (lane + 32 * j));
+                        qg[qn + off] = gv[j];
+                        ++off;
                     }
                     qn += total;
                     __syncwarp();
                     if (qn > kTQ - kTC) {
-                        B = tile_flush<DP>(A, Ps, rowrec, q, qn, a, cb, lane, B);
+                        B = tile_flush<DP>(A, Ps, rowrec, colv, q, qg, qn, a, cb, lane, B);
                         my_cand += qn;
                         qn = 0;
                         thrN = (float)((B + A.tie64) / (double)A.N) + A.E1 / N;
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
             }
         }
         if (qn > 0) {
-            B = tile_flush<DP>(A, Ps, rowrec, q, qn, a, cb, lane, B);
+            B = tile_flush<DP>(A, Ps, rowrec, colv, q, qg, qn, a, cb, lane, B);
             my_cand += qn;
         }
         __syncwarp();
@@ -477,6 +489,12 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
         atomicAdd(A.examined, my_examined);
         atomicAdd(A.candidates, my_cand);
     }
+}
+
+// dynamic shared memory of k_l0_tile<DP>
+__host__ __device__ constexpr size_t tile_smem_bytes(int DP) {
+    return sizeof(float) * (size_t)kTW * (kTR * row_words(DP) + (DP + 2) * kTC + kTQ) + sizeof(PrefixSm) * kTW +
+           sizeof(unsigned short) * (size_t)kTW * kTQ;
 }
 
 // greedy forward selection in FP64: its D-subset's RSS is an upper bound of the minimum
