@@ -41,6 +41,8 @@ def parse():
                     help="CPU work for the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default line: skip the bounded runs of the mixed, batched and learned forms")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples")
     ap.add_argument("--tasks", type=int, default=512, help="batched workload: number of tasks")
@@ -196,8 +198,235 @@ def top_binary_candidates(sizes, n_unary_ops):
     return sizes[L] - P - (P - Q) * n_unary_ops
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_fit(name):
+    """The oracle's stored fits of a workload (tests/golden/<name>_oracle.json), or None."""
+    try:
+        with open(os.path.join(GOLDEN, f"{name}_oracle.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def compare_fit(sis_steps, desc, rec, rtol):
+    """Parity of one fit against the oracle's stored fit: SIS selections and descriptors
+    bit-exact, coefficients and RMSE within rtol relative."""
+    out = {"sis_steps_equal": [list(a) for a in sis_steps] == rec["sis"],
+           "descriptors_equal": [d.ids for d in desc] == [r["ids"] for r in rec["dims"]],
+           "coef_max_rel_err": None, "rmse_max_rel_err": None}
+    if out["descriptors_equal"]:
+        ce = [abs(a - b) / max(abs(b), 1e-300) for d, r in zip(desc, rec["dims"]) for a, b in zip(d.coef, r["coef"])]
+        re = [abs(d.rmse - r["rmse"]) / r["rmse"] for d, r in zip(desc, rec["dims"]) if r["rmse"] > 0]
+        out["coef_max_rel_err"], out["rmse_max_rel_err"] = max(ce), max(re) if re else 0.0
+    out["ok"] = bool(out["sis_steps_equal"] and out["descriptors_equal"] and out["coef_max_rel_err"] <= rtol
+                     and out["rmse_max_rel_err"] <= rtol)
+    out["tolerance_rel"] = rtol
+    return out
+
+
+L0_FLOP_PER_SUBSET = {1: 3, 2: 11, 3: 26, 4: 50, 5: 85}   # full Cholesky solve + RSS per D-subset (FMA = 2)
+L0_FP32_OPS_PER_SUBSET = {3: 8, 4: 9, 5: 10}              # tiled enumeration: FP32 arithmetic per subset (filter included)
+
+
+def l0_roofline(s, D, peak, sms, mhz, reps=3):
+    """The tiled l0 enumeration alone, one launch over every D-subset of the fit's final
+    subspace (the fit's own last step), timed with CUDA events inside the library."""
+    import math
+    import numpy as np
+    S = sum((s.sis(t) for t in range(1, D + 1)), [])
+    G, b, syy = s.subspace_gram(S)
+    ms = []
+    for _ in range(reps):
+        st0 = s.stats()
+        s.l0_search(G, b, syy, D, np.array(S))
+        st1 = s.stats()
+        ms.append(st1["ms_l0_enum"] - st0["ms_l0_enum"])
+        cand = st1["l0_candidates"] - st0["l0_candidates"]
+    t = sorted(ms)[len(ms) // 2] / 1e3
+    n_sub = math.comb(len(S), D)
+    achieved = L0_FLOP_PER_SUBSET[D] * n_sub / t / 1e12
+    return {"bound": "alu", "kernel": f"k_l0_tile<{D - 2}>", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "launch_ms": t * 1e3, "subsets": n_sub,
+            "subsets_per_s": n_sub / t, "candidates_exact_test": int(cand),
+            "algorithmic_unit": f"{L0_FLOP_PER_SUBSET[D]} flop per {D}-subset (full Cholesky solve and RSS, FMA = 2) "
+                                f"x C({len(S)},{D}) subsets per launch",
+            "fp32_issue_frac": L0_FP32_OPS_PER_SUBSET.get(D, 0) * n_sub / t / (sms * 128 * mhz * 1e6),
+            "fp32_issue_note": f"{L0_FP32_OPS_PER_SUBSET.get(D, 0)} FP32 arithmetic instructions per subset in the "
+                               "prefix-reduced form, against SMs x 128 lanes x clock",
+            "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x measured max SM clock"}
+
+
+def form_mixed(args):
+    """Mixed-precision forms vs the plain FP32 form at full size (65 536 samples, six
+    primaries correlated 0.999, rung 2, k = 200, D <= 3): time to the final descriptor and
+    parity of every form with the oracle's stored fit."""
+    import torch
+    from paper_2410_01752_gb300 import PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16, Sisso, inputs
+    P = inputs.workload3(0)
+    rec = (golden_fit("workload3") or [None])[0]
+    Xd, yd = torch.from_numpy(P.X).cuda(), torch.from_numpy(P.y).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec, tol in (("plain_fp32", PREC_FP32, 1e-6), ("mixed_bf16", PREC_MIXED_BF16, 1e-4),
+                            ("mixed_fp16", PREC_MIXED_FP16, 1e-4)):
+        with Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar,
+                   stream=stream) as s:
+            s.fit()
+            ms = []
+            for _ in range(2):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                d = s.fit()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            st = s.stats()
+            out[name] = {"time_to_descriptor_ms": sum(ms) / len(ms), "descriptor": d[-1].ids, "rmse": d[-1].rmse,
+                         "ms_gram": st["ms_gram"], "ms_screen": st["ms_screen"], "ms_l0": st["ms_l0"],
+                         "gpu_launches": st["launches"],
+                         "parity": compare_fit([s.sis(t) for t in range(1, len(d) + 1)], d, rec, tol) if rec else None}
+    for k in ("mixed_bf16", "mixed_fp16"):
+        out[k]["speedup_vs_plain"] = out["plain_fp32"]["time_to_descriptor_ms"] / out[k]["time_to_descriptor_ms"]
+        out[k]["rmse_rel_diff_vs_plain"] = abs(out[k]["rmse"] - out["plain_fp32"]["rmse"]) / out["plain_fp32"]["rmse"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, m, dt, th = cpu_baseline_sample(P, 5.0, seed=3)
+        cpu = {"value": r, "unit": "features/s", "cores": th, "kind": "oracle",
+               "sample": f"{m} random candidate ids scored in FP64 over all {P.N} samples ({dt:.1f} s)"}
+    return {"workload": P.name, "forms": out, "cpu_baseline": cpu,
+            "metric": "time-to-descriptor vs plain at equal RMSE", "unit": "ms",
+            "parity_ok": all(v["parity"] and v["parity"]["ok"] for v in out.values())}
+
+
+def form_batched(args):
+    """The batched multi-task form: 512 tasks in one persistent launch (CUDA graph), launch
+    shape from the autotuner; every task's descriptors against the oracle's stored fits."""
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import inputs, sisso
+    probs = [inputs.workload5_task(p) for p in range(512)]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    with sisso.Batch([(P.X, P.y) for P in probs], probs[0].op_set, 2, 50, 3, stream=stream) as b:
+        tune = b.autotune(reps=1, cache_path=args.tune_cache)
+        b.run(copies=False)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(copies=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res = b.results()
+        start, end = b.timing()
+        tms = []
+        host = [(P.X, P.y) for P in probs]
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.load(host)
+            b.run(copies=True)
+            b.results()
+            tms.append(time.perf_counter() - t0)
+        in_bytes = sum(P.X.nbytes + P.y.nbytes for P in probs)
+    gold = []
+    try:
+        with open(os.path.join(GOLDEN, "workload5_oracle.jsonl")) as f:
+            gold = [json.loads(l) for l in f]
+    except OSError:
+        pass
+    ok_ids, cerr = 0, 0.0
+    for (st_, dims), g in zip(res, gold):
+        same = st_ == 0 and [d.ids for d in dims] == [r["ids"] for r in g["dims"]]
+        ok_ids += same
+        if same:
+            cerr = max([cerr] + [abs(a - c) / max(abs(c), 1e-300) for d, r in zip(dims, g["dims"])
+                                 for a, c in zip(d.coef, r["coef"])])
+    mean_ms = sum(ms) / len(ms)
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, n, dt, th = oracle_tasks_sample(probs, 5.0, seed=5)
+        cpu = {"value": r, "unit": "tasks/s", "cores": th, "kind": "oracle",
+               "sample": f"{n} randomly drawn tasks fitted by the FP64 oracle ({dt:.1f} s)"}
+    return {"workload": BATCH_NAME.format(n=512), "metric": "tasks/s", "value": 512 / (mean_ms / 1e3),
+            "unit": "tasks/s", "launch_ms": mean_ms, "tune": tune,
+            "latency_ms": {"p50": float(np.percentile(end, 50)), "p99": float(np.percentile(end, 99))},
+            "e2e": {"value": 512 / (sum(tms) / len(tms)), "unit": "tasks/s", "h2d_bytes_per_step": int(in_bytes),
+                    "d2h_bytes_per_step": int(512 * sisso.C.sizeof(sisso.TaskResult))},
+            "gpu_launches": 1, "cpu_baseline": cpu,
+            "parity": {"tasks": len(gold), "descriptors_equal": ok_ids, "coef_max_rel_err": cerr,
+                       "ok": len(gold) == 512 and ok_ids == 512 and cerr <= 1e-6, "tolerance_rel": 1e-6}}
+
+
+def form_learned(args):
+    """The learned proposal: trained on the method's own exhaustive results (2000 problems),
+    then the fit's time to the D = 5 descriptor with and without it on held-out problems,
+    judged by the oracle's stored exhaustive fits."""
+    import numpy as np
+    from paper_2410_01752_gb300 import inputs, proposal, sisso
+    t0 = time.perf_counter()
+    X, t = proposal.training_set(2000, k=60, per_problem=768, top=256, seed=0)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, rel_loss = proposal.train(X, t, seed=0, epochs=10, batch=2048, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    gold = golden_fit("workload4") or []
+    probs = [inputs.workload4(r["p"], held_out=True) for r in gold]
+    proposal.evaluate(net, probs[:1], frac=0.01)
+    res = proposal.evaluate(net, probs, frac=0.01)
+    zero = sisso.MLP(0)
+    zero.set_params(np.zeros(sisso.MLP_PARAMS, dtype=np.float32))
+    res0 = proposal.evaluate(zero, probs, frac=0.01)
+    ok = [(r, g, r0) for r, g, r0 in zip(res, gold, res0) if "recall" in r]
+    match = [r["learned_ids"] == g["dims"][-1]["ids"] for r, g, _ in ok]
+    plain_match = [r["plain_ids"] == g["dims"][-1]["ids"] for r, g, _ in ok]
+    ms_l = float(np.mean([r["fit_learned_ms_device"] for r, _, _ in ok])) if ok else None
+    ms_p = float(np.mean([r["fit_plain_ms_device"] for r, _, _ in ok])) if ok else None
+    cpu = None
+    if not args.no_cpu_baseline and probs:
+        import oracle
+        P = probs[0]
+        c = sisso.Sisso(P.X, P.y, P.op_set, P.rung, 60, 5, grammar=P.grammar)
+        c.fit()
+        S = sum((c.sis(t) for t in range(1, 6)), [])[:60]
+        G, b, syy = c.subspace_gram(S)
+        c.close()
+        t0 = time.perf_counter()
+        _, _, ex = oracle.l0(G, b, syy, P.N, 5, S, nthreads=cores())
+        dt = time.perf_counter() - t0
+        cpu = {"value": ex / dt, "unit": "subsets/s", "cores": cores(), "kind": "oracle",
+               "sample": f"exhaustive D = 5 over the first 60 screened features: C(60,5) = {ex} subsets ({dt:.1f} s)"}
+    return {"workload": "learned proposal: D=5 over 300 features (k=60), held-out problems of the stored oracle fits",
+            "metric": "time-to-descriptor vs plain at equal RMSE", "unit": "ms",
+            "fit_learned_ms": ms_l, "fit_plain_ms": ms_p, "speedup_vs_plain": (ms_p / ms_l) if ok else None,
+            "problems": len(ok), "learned_equals_oracle": sum(match), "plain_equals_oracle": sum(plain_match),
+            "greedy_only_equals_exhaustive": sum(r0["recall"] for _, _, r0 in ok),
+            "trained_equals_exhaustive": sum(r["recall"] for r, _, _ in ok),
+            "training": {"problems": 2000, "examples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
+                         "loss_rel_to_target_var": rel_loss},
+            "gpu_launches": int(round(float(np.mean([r["fit_learned_launches"] for r, _, _ in ok])))) if ok else None,
+            "cpu_baseline": cpu,
+            "parity": {"ok": bool(ok) and all(match), "note": "final D = 5 descriptor of the learned fit vs the oracle"}}
+
+
+def workload2_config(P, n_features: int, world: int = 1):
+    """The default line's config (both arms print the same dict)."""
+    return {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "grammar": "new_x_prev",
+            "sis_size": P.sis_size, "max_dim": P.max_dim, "n_features": int(n_features),
+            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank: int):
     """The oracle as the reference arm: each step a bounded sample of the workload."""
+    import oracle
     from paper_2410_01752_gb300 import inputs
     if rank != 0:
         return
@@ -217,8 +446,7 @@ def run_reference(args, rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "grammar": "new_x_prev",
-                   "sis_size": P.sis_size, "max_dim": P.max_dim},
+        "config": workload2_config(P, oracle.Space(P.d, P.op_set, P.rung, P.grammar).n_features, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
                          "sample": f"{samples[0]} random candidate ids per step scored in FP64 over all {P.N} samples"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -580,7 +808,7 @@ def main():
     value = cand / (total_ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e = None
+    e2e, e2e_step_s = None, None
     if not args.no_e2e:
         Xh = torch.from_numpy(P.X).pin_memory()
         yh = torch.from_numpy(P.y).pin_memory()
@@ -598,6 +826,7 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
             d2h = sum(8 * len(x.ids) + 8 * len(x.coef) + 16 for x in dd)
         tot, (e2e_cand,) = job_totals(sum(e2e_ms), [e2e_cand], dist, "cuda")
+        e2e_step_s = tot / args.steps / 1e3
         e2e = {"value": e2e_cand / (tot / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
                "d2h_bytes_per_step": int(d2h)}
 
@@ -634,16 +863,31 @@ def main():
                "sample": f"{m} random candidate ids of the workload scored in FP64 over all {P.N} samples ({dt:.1f} s)",
                "value_1thread": r1, "sample_1thread": f"{m1} random candidate ids on one thread ({dt1:.1f} s)"}
 
+    # parity of the timed fit with the oracle's stored fit of the same problem
+    parity = None
+    rec = golden_fit("workload2") if (P.N, P.d) == (1000, 10) and rank == 0 else None
+    if rec:
+        parity = compare_fit([s.sis(t) for t in range(1, len(desc) + 1)], desc, rec[0], 1e-6)
+        parity["golden"] = "tests/golden/workload2_oracle.json"
+    l0_roof = l0_roofline(s, len(desc), peak, sms, mhz) if len(desc) >= 3 else None
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = {"mixed_precision": form_mixed(args), "batched": form_batched(args),
+                 "learned_proposal": form_learned(args)}
+
     d_last = desc[-1] if desc else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": P.name, "N": P.N, "d": P.d, "rung": P.rung, "grammar": "new_x_prev",
-                   "sis_size": P.sis_size, "max_dim": P.max_dim, "n_features": n_feat,
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
-        "l0_subsets_fit_per_s": subsets / (total_ms / 1e3),
+        "config": workload2_config(P, n_feat, world),
+        "parity": parity,
+        "l0_subsets_fit_per_s": subsets / (sum(st["ms_l0"] for st in stats) / 1e3),
+        "l0_subsets_fit_per_s_note": "subsets of every step's search / the searches' device time (ms_l0)",
         "time_to_descriptor_s": total_ms / args.steps / 1e3,
+        "time_to_descriptor_e2e_s": e2e_step_s,
+        "time_to_descriptor_e2e_note": "one fit through the C ABI from host buffers, context creation included",
+        "l0_roofline": l0_roof,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -656,6 +900,7 @@ def main():
                        "expr": [s.expr(i) for i in d_last.ids]} if d_last else None,
         "window_grown": sum(st["window_grown"] for st in stats),
         "window_saturated": max(st["window_saturated"] for st in stats),
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
     s.close()

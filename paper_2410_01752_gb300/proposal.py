@@ -98,6 +98,7 @@ def evaluate(net: MLP, problems, frac: float = 0.01, k: int = 60):
             rec["fit_learned_ms_device"] = c.stats()["ms_fit"]
             rec["fit_learned_launches"] = c.stats()["launches"]
             c.set_proposal(None)
+            rec["plain_ids"], rec["learned_ids"] = plain[4].ids, learned[4].ids
             rec["same_descriptor"] = learned[4].ids == plain[4].ids
             rec["rmse_rel_diff"] = abs(learned[4].rmse - plain[4].rmse) / plain[4].rmse
         out.append(rec)
