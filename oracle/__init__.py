@@ -83,6 +83,10 @@ def lib():
                                         C.c_int]
         L.oracle_sis.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p, C.c_int,
                                  C.c_int, i64p, C.c_int]
+        L.oracle_sis_ex.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p, C.c_int,
+                                    C.c_int, C.c_double, i64p, C.c_int]
+        L.oracle_fit_ex.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(_Result)]
         L.oracle_l0.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, i64p, ip, dp, C.c_int]
         L.oracle_l0.restype = C.c_int64
         L.oracle_fit.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int,
@@ -172,13 +176,14 @@ class Space:
             raise ValueError(f"oracle_scores_all failed ({rc})")
         return sc, va.astype(bool)
 
-    def sis(self, X, target, S_prev, k: int, nthreads: int = 0) -> list[int]:
+    def sis(self, X, target, S_prev, k: int, nthreads: int = 0, threshold: float = 0.0) -> list[int]:
+        """One SIS step (§2.2): up to k ids, only scores above `threshold` when it is > 0."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         target = np.ascontiguousarray(target, dtype=np.float64)
         Sp = np.ascontiguousarray(np.asarray(S_prev, dtype=np.int64).reshape(-1))
         acc = np.zeros(k, dtype=np.int64)
-        n = lib().oracle_sis(*self.args, _dp(X), X.shape[0], _dp(target), _i64p(Sp), Sp.size, k,
-                             _i64p(acc), nthreads)
+        n = lib().oracle_sis_ex(*self.args, _dp(X), X.shape[0], _dp(target), _i64p(Sp), Sp.size, k,
+                                float(threshold), _i64p(acc), nthreads)
         if n < 0:
             raise ValueError(f"oracle_sis failed ({n})")
         return [int(v) for v in acc[:n]]
@@ -215,13 +220,17 @@ class FitResult:
     sis: list[list[int]] = field(default_factory=list)   # ids accepted at each step
 
 
-def fit(X, y, space: Space, k: int, max_dim: int, nthreads: int = 0) -> FitResult:
-    """The SISSO iteration of §2.3 (Eq. 8) on the feature space of §2.1."""
+def fit(X, y, space: Space, k: int, max_dim: int, nthreads: int = 0, sis_threshold: float = 0.0,
+        stop_rmse: float = 0.0) -> FitResult:
+    """The SISSO iteration of §2.3 (Eq. 8) on the feature space of §2.1; sis_threshold > 0:
+    the threshold variant of SIS (§2.2), stop_rmse > 0: stop once a step's RMSE is at or
+    below it (§2.3, "low enough error")."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     r = _Result()
-    rc = lib().oracle_fit(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
-                          space.grammar, k, max_dim, nthreads, C.byref(r))
+    rc = lib().oracle_fit_ex(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
+                             space.grammar, k, max_dim, float(sis_threshold), float(stop_rmse), nthreads,
+                             C.byref(r))
     if rc:
         raise ValueError(f"oracle_fit failed ({rc})")
     out = FitResult()

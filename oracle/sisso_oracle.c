@@ -35,7 +35,12 @@
  *  - Winner refit: Householder QR on the raw N x (t+1) matrix [1, Phi_E]; coefficients,
  *    RMSE = |y - yhat| / sqrt(N), R^2 = 1 - RSS/SST come from that fit.
  *  - Stop (§2.3, "low enough error"): after a step whose RMSE <= 1e-10 * std(y) (the fit
- *    is exact to FP64 rounding), or when S holds fewer than t features.
+ *    is exact to FP64 rounding), after a step whose RMSE is at or below the caller's
+ *    tolerance (stop_rmse > 0), or when S holds fewer than t features.
+ *  - Threshold SIS (§2.2, last paragraph: keep the features whose correlation exceeds a
+ *    threshold): the score is the same Pearson |rho| as the ranking; the walk runs as
+ *    above and ends when the best remaining score is at or below the threshold, or at k
+ *    accepted ids (k stays the per-step capacity).
  */
 #include "sisso_oracle.h"
 
@@ -562,7 +567,7 @@ static int cand_cmp(const void* x, const void* y) {
 }
 
 static int sis_step(const space_t* s, const double* X, int N, const double* target,
-                    const int64_t* S_prev, int n_prev, int k, int64_t* acc, int nthreads) {
+                    const int64_t* S_prev, int n_prev, int k, double thr, int64_t* acc, int nthreads) {
     int64_t n_all = s->phi[s->rung];
     double* tc = (double*)malloc(sizeof(double) * (size_t)N);
     double tsd = centre(target, N, tc);
@@ -598,6 +603,9 @@ static int sis_step(const space_t* s, const double* X, int N, const double* targ
         while (p < nc && removed[p]) p++;
         if (p >= nc) break;
         double m = c[p].score;
+        /* threshold variant (§2.2, last paragraph): only features whose correlation
+           exceeds thr; the walk ends when the best remaining score is at or below it */
+        if (thr > 0.0 && m <= thr) break;
         int64_t best = p;
         for (int64_t q = p; q < nc && c[q].score >= m - SCORE_TIE; q++)
             if (!removed[q] && c[q].id < c[best].id) best = q;
@@ -614,12 +622,18 @@ static int sis_step(const space_t* s, const double* X, int N, const double* targ
     return n_acc;
 }
 
+int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+                  const double* target, const int64_t* S_prev, int n_prev, int k, double thr,
+                  int64_t* acc_out, int nthreads) {
+    space_t s;
+    if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1 || thr < 0.0) return -1;
+    return sis_step(&s, X, N, target, S_prev, n_prev, k, thr, acc_out, nthreads);
+}
+
 int oracle_sis(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                const double* target, const int64_t* S_prev, int n_prev, int k,
                int64_t* acc_out, int nthreads) {
-    space_t s;
-    if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1) return -1;
-    return sis_step(&s, X, N, target, S_prev, n_prev, k, acc_out, nthreads);
+    return oracle_sis_ex(d, ops, rung, grammar, X, N, target, S_prev, n_prev, k, 0.0, acc_out, nthreads);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -820,9 +834,16 @@ static int lstsq_qr(const double* A_in, const double* y_in, int N, int p, double
 
 int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
                int grammar, int k, int max_dim, int nthreads, oracle_result* out) {
+    return oracle_fit_ex(X, y, N, d, ops, rung, grammar, k, max_dim, 0.0, 0.0, nthreads, out);
+}
+
+int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
+                  int grammar, int k, int max_dim, double sis_threshold, double stop_rmse,
+                  int nthreads, oracle_result* out) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1 || k > 1024 ||
-        max_dim < 1 || max_dim > ORC_MAX_DIM || N < max_dim + 1) return -1;
+        max_dim < 1 || max_dim > ORC_MAX_DIM || N < max_dim + 1 || sis_threshold < 0.0 ||
+        stop_rmse < 0.0) return -1;
     memset(out, 0, sizeof(*out));
     double ybar = 0.0, sst = 0.0;
     for (int i = 0; i < N; i++) ybar += y[i];
@@ -837,7 +858,7 @@ int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int
     int rc = 0;
     for (int t = 1; t <= max_dim; t++) {
         /* SIS on y (t = 1) or on the best residual of step t-1 */
-        int na = sis_step(&s, X, N, target, S, nS, k, S + nS, nthreads);
+        int na = sis_step(&s, X, N, target, S, nS, k, sis_threshold, S + nS, nthreads);
         if (na < 0) { rc = (t == 1) ? -3 : 0; break; }
         out->n_sis[t - 1] = na;
         nS += na;
@@ -889,6 +910,8 @@ int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int
         out->subsets[di] = ex;
         out->n_dims = t;
         if (out->rmse[di] <= STOP_REL * ysd) break;    /* exact fit: nothing left to screen */
+        /* "low enough error" (§2.3): the caller's RMSE tolerance */
+        if (stop_rmse > 0.0 && out->rmse[di] <= stop_rmse) break;
     }
     free(yc); free(target);
     return rc;

@@ -59,6 +59,11 @@ int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const double* 
 int oracle_sis(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                const double* target, const int64_t* S_prev, int n_prev, int k,
                int64_t* acc_out, int nthreads);
+/* the same with the threshold variant of §2.2: the walk ends when the best remaining
+   score is at or below thr (thr = 0: top k only) */
+int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+                  const double* target, const int64_t* S_prev, int n_prev, int k, double thr,
+                  int64_t* acc_out, int nthreads);
 /* exhaustive l0 over all D-subsets of n standardised features.
  * G (n x n), b (n) are Z^T Z / N and Z^T y~ / N; syy = y~^T y~ / N; gid[n] = global ids used
  * for the tie rule.  Writes the winning positions (ascending) and its RSS; returns the
@@ -80,6 +85,11 @@ typedef struct {
 
 int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
                int grammar, int k, int max_dim, int nthreads, oracle_result* out);
+/* the same with the SIS threshold (0: top k only) and the "low enough error" stop: after a
+   step whose RMSE <= stop_rmse (0: only the exact-fit stop) */
+int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
+                  int grammar, int k, int max_dim, double sis_threshold, double stop_rmse,
+                  int nthreads, oracle_result* out);
 
 #ifdef __cplusplus
 }

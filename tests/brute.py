@@ -100,10 +100,11 @@ def standardise(v: np.ndarray) -> np.ndarray:
 
 
 def sis(values: list[np.ndarray], target: np.ndarray, S_prev: list[int], k: int,
-        ok: list[bool] | None = None) -> list[int]:
+        ok: list[bool] | None = None, thr: float = 0.0) -> list[int]:
     """SIS step (§2.2 Eqs. 5-6) by brute force, with the tie-tolerant walk and the
     duplicate rule (standardised vectors equal up to sign within 1e-8).  ok[i]: validity
-    of feature i (default: the value rules only)."""
+    of feature i (default: the value rules only).  thr > 0: the threshold variant (§2.2,
+    last paragraph), the walk ends once the best remaining |corr| is at or below thr."""
     if ok is None:
         ok = [valid(v) for v in values]
     cand = [(abs_corr(v, target), i) for i, v in enumerate(values)
@@ -113,6 +114,8 @@ def sis(values: list[np.ndarray], target: np.ndarray, S_prev: list[int], k: int,
     acc = []
     while remaining and len(acc) < k:
         m = remaining[0][0]
+        if thr > 0 and m <= thr:
+            break
         window = [c for c in remaining if c[0] >= m - 1e-9]
         pick = min(window, key=lambda c: c[1])
         remaining.remove(pick)
@@ -144,9 +147,10 @@ def best_subset(cols: np.ndarray, y: np.ndarray, D: int, gid: list[int]):
 
 
 def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: int, T: int,
-          new_x_prev: bool = False):
+          new_x_prev: bool = False, thr: float = 0.0, stop_rmse: float = 0.0):
     """The whole iteration of §2.3 (Eq. 8) by brute force: SIS on y, then on the residual
-    of the best t-term lstsq fit; l0 over all t-subsets of S_t."""
+    of the best t-term lstsq fit; l0 over all t-subsets of S_t.  thr: threshold SIS;
+    stop_rmse: stop after a step whose RMSE is at or below it."""
     feats, _ = space(d, ops, rung, new_x_prev)
     values = [evaluate(f, X) for f in feats]
     ok = [valid(v, f, X) for v, f in zip(values, feats)]
@@ -154,7 +158,7 @@ def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: in
     out = []
     target = y.copy()
     for t in range(1, T + 1):
-        S = S + sis(values, target, S, k, ok)
+        S = S + sis(values, target, S, k, ok, thr)
         if len(S) < t:
             break
         cols = np.column_stack([values[i] for i in S])
@@ -164,6 +168,6 @@ def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: in
         target = y - A @ c
         rmse = float(np.sqrt(target @ target / len(y)))
         out.append((list(tup), c, rmse, list(S)))
-        if rmse <= 1e-10 * y.std():
+        if rmse <= 1e-10 * y.std() or (stop_rmse > 0 and rmse <= stop_rmse):
             break
     return out

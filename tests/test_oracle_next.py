@@ -1,0 +1,86 @@
+"""Pins for the oracle's options beyond the plain iteration: the threshold variant of SIS
+(§2.2, last paragraph) and the "low enough error" stop of the iteration (§2.3)."""
+import numpy as np
+import pytest
+
+import brute
+
+NAMES = ["+", "-", "*", "/", "sqrt", "^2"]
+
+
+def _mask(orc, names):
+    return orc.opmask(*[orc.OP_NAMES.index(n) for n in names])
+
+
+def _tiny(seed):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(1, 5, size=(25, 3))
+    y = X[:, 0] * X[:, 1] / X[:, 2] + 0.1 * rng.normal(size=25)
+    feats, _ = brute.space(3, NAMES, 2)
+    values = [brute.evaluate(f, X) for f in feats]
+    ok = [brute.valid(v, f, X) for v, f in zip(values, feats)]
+    return X, y, values, ok
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_threshold_sis_matches_brute_force(orc, seed):
+    """Thresholds between scores, on y and on a residual with a prior S: the oracle's walk
+    equals the brute-force walk that ends at the first maximum at or below the threshold."""
+    X, y, values, ok = _tiny(seed)
+    sp = orc.Space(3, _mask(orc, NAMES), 2)
+    sc = np.sort(np.unique(np.round([brute.abs_corr(v, y) for v, o in zip(values, ok) if o], 12)))[::-1]
+    for thr in (0.5 * (sc[3] + sc[4]), 0.5 * (sc[12] + sc[13]), 0.5 * (sc[30] + sc[31])):
+        acc = sp.sis(X, y, [], 40, threshold=thr)
+        ref = brute.sis(values, y, [], 40, ok, thr)
+        assert acc == ref
+        assert 0 < len(acc) < 40
+        # every accepted feature scores above the threshold
+        assert all(brute.abs_corr(values[i], y) > thr for i in acc)
+    acc1 = sp.sis(X, y, [], 5)
+    v = values[acc1[0]]
+    r = y - np.polyval(np.polyfit(v, y, 1), v)
+    thr = 0.2
+    assert sp.sis(X, r, acc1, 40, threshold=thr) == brute.sis(values, r, acc1, 40, ok, thr)
+
+
+def test_threshold_zero_and_above_all(orc):
+    """Threshold 0 is the plain top-k step; a threshold above every score accepts nothing
+    and a fit with it ends with no descriptor."""
+    X, y, values, ok = _tiny(4)
+    sp = orc.Space(3, _mask(orc, NAMES), 2)
+    assert sp.sis(X, y, [], 12, threshold=0.0) == sp.sis(X, y, [], 12)
+    assert sp.sis(X, y, [], 12, threshold=1.0) == []
+    res = orc.fit(X, y, sp, 5, 2, sis_threshold=1.0)
+    assert res.dims == [] and res.sis in ([], [[]])
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_threshold_fit_matches_brute_force(orc, seed):
+    """The whole iteration with threshold SIS equals the brute-force iteration."""
+    X, y, values, ok = _tiny(seed)
+    sp = orc.Space(3, _mask(orc, NAMES), 2)
+    thr = 0.3
+    ref = brute.sisso(X, y, 3, NAMES, 2, 30, 3, thr=thr)
+    res = orc.fit(X, y, sp, 30, 3, sis_threshold=thr)
+    assert len(res.dims) == len(ref) > 0
+    for t, (tup, c, rmse, S) in enumerate(ref):
+        assert res.dims[t].ids == tup
+        assert np.allclose(res.dims[t].coef, c, rtol=1e-8, atol=1e-10)
+        assert sum(res.sis[: t + 1], []) == S
+
+
+def test_stop_rmse_ends_the_iteration(orc):
+    """With the tolerance set between the RMSE of the 2-term and the 1-term model, the
+    iteration stops after 2 terms with the full iteration's first two models; the
+    brute-force iteration stops at the same place."""
+    X, y, values, ok = _tiny(7)
+    sp = orc.Space(3, _mask(orc, NAMES), 2)
+    full = orc.fit(X, y, sp, 8, 3)
+    assert len(full.dims) == 3 and full.dims[1].rmse < full.dims[0].rmse
+    tol = 0.5 * (full.dims[0].rmse + full.dims[1].rmse)
+    short = orc.fit(X, y, sp, 8, 3, stop_rmse=tol)
+    assert len(short.dims) == 2
+    for a, b in zip(short.dims, full.dims[:2]):
+        assert a.ids == b.ids and a.coef == b.coef and a.rmse == b.rmse
+    ref = brute.sisso(X, y, 3, NAMES, 2, 8, 3, stop_rmse=tol)
+    assert [r[0] for r in ref] == [d.ids for d in short.dims]
