@@ -94,6 +94,15 @@ typedef struct {
     int64_t max_band;       /* l0: capacity of the FP64 refit list (0 = 1<<22) */
     void* cuda_stream;      /* cudaStream_t to run on; NULL = a stream the context owns */
     int device;             /* CUDA device ordinal (default 0) */
+    double sis_threshold;   /* threshold variant of SIS (§2.2, last paragraph: keep the
+                               features whose correlation exceeds a threshold): in [0, 1),
+                               on the Pearson |rho| the walk ranks by; a step ends when the
+                               best remaining score is at or below it, or at sis_size
+                               accepted ids (0 = top sis_size only, the default).  A fit
+                               whose first step accepts nothing ends with no descriptor. */
+    double stop_rmse;       /* "low enough error" stop of the iteration (§2.3): after a step
+                               whose RMSE is at or below this (in units of y), no further
+                               step runs (0 = only the exact-fit stop, the default) */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */
@@ -131,7 +140,8 @@ void sisso_default_opts(sisso_opts* opts);
  * buffer sisso_fit needs.  sis_size is k of §2.2 (features added per step), max_dim the
  * number of terms T of §2.3.  Errors: SISSO_ERR_ARG for N < max_dim+1, d < 1, rung not
  * in 1..SISSO_MAX_RUNG, max_dim not in 1..SISSO_MAX_DIM, sis_size not in
- * 1..SISSO_MAX_SIS, an empty op mask, or non-finite X/y; SISSO_ERR_OOM; SISSO_ERR_CUDA.
+ * 1..SISSO_MAX_SIS, an empty op mask, sis_threshold outside [0, 1), stop_rmse < 0, or
+ * non-finite X/y; SISSO_ERR_OOM; SISSO_ERR_CUDA.
  * On error *out is NULL. */
 sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32_t op_set,
                           int rung, int sis_size, int max_dim, const sisso_opts* opts,
@@ -287,7 +297,8 @@ typedef struct {
 /* Plan every task (feature space, work units, memory), copy the inputs to pinned host
  * and device memory, and allocate all device memory the runs need (one arena).  opts:
  * grammar, max_band (band capacity per task and step, default 16384), cuda_stream and
- * device are used; precision must be SISSO_PREC_FP32 (or default).  Limits: n_tasks <=
+ * device are used; precision must be SISSO_PREC_FP32 (or default), sis_threshold and
+ * stop_rmse 0 (top-k screening, exact-fit stop).  Limits: n_tasks <=
  * 2^20, max_dim <= 4, max_dim * sis_size <= 512, every task N >= max_dim + 1 and d >= 1, finite inputs,
  * non-constant y, and at most 2^18 screening units per task.  Errors: SISSO_ERR_ARG
  * (message names the task), SISSO_ERR_OOM, SISSO_ERR_CUDA.  On error *out is NULL and

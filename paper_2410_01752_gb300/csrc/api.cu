@@ -69,6 +69,8 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if (o.precision < SISSO_PREC_FP64 || o.precision > SISSO_PREC_MIXED_FP16) { why = "bad precision"; return SISSO_ERR_ARG; }
     if (o.grammar != SISSO_GRAMMAR_EQ2 && o.grammar != SISSO_GRAMMAR_NEW_X_PREV) { why = "bad grammar"; return SISSO_ERR_ARG; }
     if ((int64_t)max_dim * k > (max_dim <= 4 ? 65535 : 4095)) { why = "subspace too large"; return SISSO_ERR_ARG; }
+    if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
+    if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
     return SISSO_OK;
 }
 
@@ -241,7 +243,8 @@ sisso_status sisso_fit(sisso_ctx* c) {
         c->n_sis.push_back((int)acc.size());
         const int n = (int)c->S.size();
         if (n < t) {
-            if (t == 1) st = fail(c, SISSO_ERR_NUMERIC, "no valid feature");
+            // nothing valid to screen is an error; nothing above the SIS threshold ends the fit
+            if (t == 1 && !(c->opts.sis_threshold > 0.0)) st = fail(c, SISSO_ERR_NUMERIC, "no valid feature");
             break;
         }
         cudaEvent_t g0, g1;
@@ -270,6 +273,7 @@ sisso_status sisso_fit(sisso_ctx* c) {
         c->n_dims = t;
         target = c->resid;
         if (w.rmse <= kStopRel * std::sqrt(c->syy)) break;   // exact fit
+        if (c->opts.stop_rmse > 0.0 && w.rmse <= c->opts.stop_rmse) break;   // low enough error (§2.3)
     }
     cudaEventRecord(f1, c->stream);
     cudaEventSynchronize(f1);

@@ -321,6 +321,7 @@ struct WalkResult {
     int visited;            // survivors visited
     int dup_checks;         // vector comparisons made
     double last_score;      // FP64 score of the last visited candidate
+    int thr_stop;           // ended at the SIS threshold (best remaining score <= threshold)
     int64_t acc[SISSO_MAX_SIS];
 };
 

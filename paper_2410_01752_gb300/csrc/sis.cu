@@ -598,8 +598,8 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
        const double* __restrict__ sv_mean, const double* __restrict__ sv_sd,
        const double* __restrict__ probe, const double* __restrict__ zc, const double* __restrict__ V,
        const int* __restrict__ dup_list, const int* __restrict__ cnt_g, const unsigned char* __restrict__ dup_ok,
-       int s_off, int nS, int k, unsigned char* __restrict__ removed_g, unsigned char* __restrict__ accepted_g,
-       WalkResult* out) {
+       int s_off, int nS, int k, double thr, unsigned char* __restrict__ removed_g,
+       unsigned char* __restrict__ accepted_g, WalkResult* out) {
     extern __shared__ __align__(16) unsigned char wsm[];
     __shared__ int acc_src[SISSO_MAX_SIS];
     __shared__ int64_t heap_id[kHeapCap];
@@ -634,7 +634,10 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
         for (int q = tid; q < s_off; q += blockDim.x) s_acc[q] = 0;
         sk = s_sk; sid = s_sid; dup_cnt = s_cnt; ssrc = s_src; removed = s_rem; accepted = s_acc;
     }
-    if (tid == 0) { n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0; }
+    if (tid == 0) {
+        n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0;
+        out->thr_stop = 0;
+    }
     // lane 0's state: first remaining entry p, window end e, heap of the window's
     // remaining entries keyed by id (the window only grows as the maximum falls)
     int p = 0, e = 0, hn = 0;
@@ -647,7 +650,9 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
                 int best = -1, stop = 0;
                 if (lane == 0) {
                     while (p < n_sorted && removed[p]) ++p;
-                    if (n_acc >= k || p >= n_sorted || sk[p] < 0.0) {
+                    if (n_acc >= k || p >= n_sorted || sk[p] < 0.0 || (thr > 0.0 && sk[p] <= thr)) {
+                        // threshold variant (§2.2): the best remaining score is at or below it
+                        if (n_acc < k && p < n_sorted && sk[p] >= 0.0) out->thr_stop = 1;
                         done = 1;
                         exhausted = n_acc < k;
                         stop = 1;
@@ -1116,7 +1121,8 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         k_walk<<<1, kWalkThreads, wsm, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,
                                                   n_pad, c->surv_ids, c->surv_score, c->surv_mean, c->surv_sd,
                                                   c->surv_probe, zc, c->opval64, c->dup_list, c->dup_cnt, c->dup_ok,
-                                                  ns, n_prev, k, c->removed, c->accepted, c->walk);
+                                                  ns, n_prev, k, c->opts.sis_threshold, c->removed, c->accepted,
+                                                  c->walk);
         c->stats.launches += 3;
         cudaEventRecord(q[4], c->stream);
         cudaMemcpyAsync(c->walk_h, c->walk, sizeof(WalkResult), cudaMemcpyDeviceToHost, c->stream);
@@ -1130,8 +1136,12 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         c->stats.survivors_rescored += nr;
         const WalkResult& w = *c->walk_h;
         // exact iff every candidate outside the window scores (FP64) below the last
-        // accepted one by more than the tie tolerance
-        const bool safe = all || (w.n_acc == k && w.last_score - kScoreTie > (double)t32 + eps);
+        // accepted one by more than the tie tolerance, or, when the walk ended at the SIS
+        // threshold, below the threshold by more than the tie tolerance (no outside
+        // candidate could be picked above it, nor tie with a pick)
+        const double thr = c->opts.sis_threshold;
+        const bool safe = all || (w.n_acc == k && w.last_score - kScoreTie > (double)t32 + eps) ||
+                          (w.thr_stop && (double)t32 + eps < thr - kScoreTie);
         const bool can_grow = M < c->surv_cap - n_prev;
         if (safe || !can_grow) {
             if (!safe) c->stats.window_saturated = 1;

@@ -1,0 +1,87 @@
+"""GPU parity of the options beyond the plain iteration, against the FP64 oracle: the
+threshold variant of SIS (§2.2, last paragraph) and the "low enough error" stop (§2.3).
+
+Bars: accepted ids and descriptors bit-exact; coefficients and RMSE within 1e-6 relative."""
+import numpy as np
+import pytest
+
+from paper_2410_01752_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2410_01752_gb300 import build, sisso
+    build.build()
+    return sisso
+
+
+def _thresholds(orc, sp, X, y, picks):
+    """Midpoints between consecutive distinct oracle scores at the given ranks."""
+    sc, va = sp.scores_all(X, y)
+    u = np.unique(np.round(sc[va], 9))[::-1]
+    return [0.5 * (u[r] + u[r + 1]) for r in picks if r + 1 < u.size]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", ["rung2", "rung3"])
+def test_threshold_sis_step(S, orc, prec, case):
+    """One SIS step with the threshold variant, thresholds between scores at several ranks
+    (the walk ends inside the first window, after it grew, and at the cap k)."""
+    if case == "rung2":
+        P = inputs.workload1(0)
+    else:
+        P = inputs.workload2(0, N=300, d=5, sis_size=40, max_dim=2)
+    sp = orc.Space(P.d, P.op_set, P.rung, P.grammar)
+    for thr in _thresholds(orc, sp, P.X, P.y, [3, 17, 60]):
+        k = 40
+        ref = sp.sis(P.X, P.y, [], k, threshold=thr)
+        with S.Sisso(P.X, P.y, P.op_set, P.rung, k, 2, precision=prec, grammar=P.grammar, sis_threshold=thr) as c:
+            got = c.sis_step(P.y, [], k)
+        assert got == ref, (thr, len(got), len(ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_threshold_fit(S, orc, prec):
+    """The whole iteration with threshold SIS (the subspace grows by fewer than k ids at some
+    steps) against the oracle's iteration."""
+    P = inputs.workload1(1)
+    sp = orc.Space(P.d, P.op_set, P.rung, P.grammar)
+    thr = _thresholds(orc, sp, P.X, P.y, [12])[0]
+    ref = orc.fit(P.X, P.y, sp, P.sis_size, P.max_dim, sis_threshold=thr)
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, sis_threshold=thr) as c:
+        got = c.fit()
+        assert len(got) == len(ref.dims) > 0
+        for t, (g, r) in enumerate(zip(got, ref.dims)):
+            assert c.sis(t + 1) == ref.sis[t]
+            assert g.ids == r.ids
+            np.testing.assert_allclose(g.coef, r.coef, rtol=1e-6, atol=1e-9 * np.abs(P.y).max())
+            assert abs(g.rmse - r.rmse) <= 1e-6 * r.rmse
+
+
+def test_threshold_above_every_score(S, orc):
+    """Nothing above the threshold: no descriptor, as in the oracle."""
+    P = inputs.workload1(2)
+    sp = orc.Space(P.d, P.op_set, P.rung, P.grammar)
+    assert orc.fit(P.X, P.y, sp, 10, 2, sis_threshold=0.9999999).dims == []
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, 10, 2, sis_threshold=0.9999999) as c:
+        assert c.fit() == []
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stop_rmse(S, orc, prec):
+    """The iteration stops after the first step whose RMSE reaches the tolerance."""
+    P = inputs.workload2(1, N=400, d=5, rung=2, sis_size=20, max_dim=4)
+    sp = orc.Space(P.d, P.op_set, P.rung, P.grammar)
+    full = orc.fit(P.X, P.y, sp, P.sis_size, P.max_dim)
+    assert len(full.dims) == 4
+    tol = 0.5 * (full.dims[1].rmse + full.dims[2].rmse)
+    ref = orc.fit(P.X, P.y, sp, P.sis_size, P.max_dim, stop_rmse=tol)
+    assert len(ref.dims) == 3
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar,
+                 stop_rmse=tol) as c:
+        got = c.fit()
+    assert [g.ids for g in got] == [r.ids for r in ref.dims]
+    for g, r in zip(got, ref.dims):
+        assert abs(g.rmse - r.rmse) <= 1e-6 * r.rmse
