@@ -79,13 +79,14 @@ def lib():
         L.oracle_eval.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, C.c_int64, dp]
         L.oracle_scores.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p,
                                     C.c_int64, dp, ip, C.c_int]
-        L.oracle_scores_all.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, dp, ip,
+        L.oracle_scores_all.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, ip, dp, C.c_int, dp, dp, ip,
                                         C.c_int]
+        L.oracle_units.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, ip, C.c_int64, ip]
         L.oracle_sis.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p, C.c_int,
                                  C.c_int, i64p, C.c_int]
-        L.oracle_sis_ex.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, dp, C.c_int, dp, i64p, C.c_int,
+        L.oracle_sis_ex.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, ip, dp, C.c_int, dp, i64p, C.c_int,
                                     C.c_int, C.c_double, i64p, C.c_int]
-        L.oracle_fit_ex.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int,
+        L.oracle_fit_ex.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, ip, C.c_int,
                                     C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(_Result)]
         L.oracle_l0.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, i64p, ip, dp, C.c_int]
         L.oracle_l0.restype = C.c_int64
@@ -105,15 +106,37 @@ def _i64p(a: np.ndarray):
 
 @dataclass
 class Space:
-    """The expanded feature space phi_rung of §2.1 (Eq. 2)."""
+    """The expanded feature space phi_rung of §2.1 (Eq. 2).  units: one unit label per
+    primary (equal labels share units, -1 dimensionless) for the dimensional analysis of
+    §2.1 / §3.3, or None."""
     d: int
     ops: int
     rung: int
     grammar: int = GRAMMAR_EQ2
+    units: tuple | None = None
 
     @property
     def args(self):
         return (self.d, self.ops, self.rung, self.grammar)
+
+    def _units_ptr(self):
+        if self.units is None:
+            return None, None
+        u = np.ascontiguousarray(np.asarray(self.units, dtype=np.int32))
+        if u.size != self.d or u.min() < -1 or u.max() >= self.d:
+            raise ValueError("units: one label in -1..d-1 per primary")
+        return u.ctypes.data_as(C.POINTER(C.c_int)), u
+
+    def units_of(self, fid: int):
+        """(consistent, exponents over the unit labels in sixteenths) of feature fid."""
+        up, keep = self._units_ptr()
+        if up is None:
+            raise ValueError("space without units")
+        e = np.zeros(self.d, dtype=np.int32)
+        ok = lib().oracle_units(*self.args, up, fid, e.ctypes.data_as(C.POINTER(C.c_int)))
+        if ok < 0:
+            raise ValueError("oracle_units failed")
+        return bool(ok), e
 
     def sizes(self) -> list[int]:
         out = np.zeros(self.rung + 1, dtype=np.int64)
@@ -170,7 +193,8 @@ class Space:
         n = self.n_features
         sc = np.zeros(n, dtype=np.float64)
         va = np.zeros(n, dtype=np.int32)
-        rc = lib().oracle_scores_all(*self.args, _dp(X), X.shape[0], _dp(target), _dp(sc),
+        up, keep = self._units_ptr()
+        rc = lib().oracle_scores_all(*self.args, up, _dp(X), X.shape[0], _dp(target), _dp(sc),
                                      va.ctypes.data_as(C.POINTER(C.c_int)), nthreads)
         if rc:
             raise ValueError(f"oracle_scores_all failed ({rc})")
@@ -182,7 +206,8 @@ class Space:
         target = np.ascontiguousarray(target, dtype=np.float64)
         Sp = np.ascontiguousarray(np.asarray(S_prev, dtype=np.int64).reshape(-1))
         acc = np.zeros(k, dtype=np.int64)
-        n = lib().oracle_sis_ex(*self.args, _dp(X), X.shape[0], _dp(target), _i64p(Sp), Sp.size, k,
+        up, keep = self._units_ptr()
+        n = lib().oracle_sis_ex(*self.args, up, _dp(X), X.shape[0], _dp(target), _i64p(Sp), Sp.size, k,
                                 float(threshold), _i64p(acc), nthreads)
         if n < 0:
             raise ValueError(f"oracle_sis failed ({n})")
@@ -228,8 +253,9 @@ def fit(X, y, space: Space, k: int, max_dim: int, nthreads: int = 0, sis_thresho
     X = np.ascontiguousarray(X, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     r = _Result()
+    up, keep = space._units_ptr()
     rc = lib().oracle_fit_ex(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
-                             space.grammar, k, max_dim, float(sis_threshold), float(stop_rmse), nthreads,
+                             space.grammar, up, k, max_dim, float(sis_threshold), float(stop_rmse), nthreads,
                              C.byref(r))
     if rc:
         raise ValueError(f"oracle_fit failed ({rc})")

@@ -37,6 +37,11 @@
  *  - Stop (§2.3, "low enough error"): after a step whose RMSE <= 1e-10 * std(y) (the fit
  *    is exact to FP64 rounding), after a step whose RMSE is at or below the caller's
  *    tolerance (stop_rmse > 0), or when S holds fewer than t features.
+ *  - Dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality, one unit label per
+ *    primary): units are exponent vectors over the labels; + and - need equal units,
+ *    exp, log, sin and exp(-.) a dimensionless operand, the other operators combine
+ *    units.  A feature that breaks the rule, or is built from one that does, is invalid
+ *    (the enumeration and the ids stay those of the space without units).
  *  - Threshold SIS (§2.2, last paragraph: keep the features whose correlation exceeds a
  *    threshold): the score is the same Pearson |rho| as the ranking; the walk runs as
  *    above and ends when the best remaining score is at or below the threshold, or at k
@@ -69,6 +74,7 @@ typedef struct {
     uint32_t ops;
     int64_t phi[ORC_MAX_RUNG + 1];                 /* |phi_l|, cumulative */
     int64_t sec[ORC_MAX_RUNG + 1][ORC_NOPS];       /* features new at level l by op */
+    const int* units;                              /* unit label per primary (-1: none), or NULL */
 } space_t;
 
 static int op_is_binary(int op) { return op <= ORC_DIV; }
@@ -243,6 +249,78 @@ static double apply_binary(int op, double x, double y) {
     return NAN;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality)                   */
+/* ------------------------------------------------------------------------------------ */
+
+/* Units of feature id as exponents over the primaries' unit labels (label j is base unit
+   j; -1 is dimensionless), in sixteenths so that up to four nested square roots stay
+   exact.  Returns 1 if the feature and every operand is dimensionally consistent: + and -
+   need operands of equal units, exp, log, sin and exp(-.) a dimensionless operand; the
+   other operators combine units (x adds, / subtracts, ^2 ^3 ^-1 sqrt scale the exponents). */
+#define UNIT_SCALE 16
+static int units_rec(const space_t* s, int64_t id, int* e) {
+    int level, op; int64_t a, b;
+    if (decode(s, id, &level, &op, &a, &b)) return 0;
+    int d = s->d;
+    if (level == 0) {
+        for (int j = 0; j < d; j++) e[j] = 0;
+        int lab = s->units[a];
+        if (lab >= 0) e[lab] = UNIT_SCALE;
+        return 1;
+    }
+    int* ea = (int*)malloc(sizeof(int) * (size_t)d);
+    int ok = units_rec(s, a, ea);
+    if (ok && b >= 0) {
+        int* eb = (int*)malloc(sizeof(int) * (size_t)d);
+        ok = units_rec(s, b, eb);
+        for (int j = 0; ok && j < d; j++) {
+            switch (op) {
+                case ORC_ADD: case ORC_SUB:
+                    if (ea[j] != eb[j]) ok = 0;
+                    e[j] = ea[j];
+                    break;
+                case ORC_MUL: e[j] = ea[j] + eb[j]; break;
+                case ORC_DIV: e[j] = ea[j] - eb[j]; break;
+            }
+        }
+        free(eb);
+    } else if (ok) {
+        for (int j = 0; ok && j < d; j++) {
+            switch (op) {
+                case ORC_EXP: case ORC_LOG: case ORC_SIN: case ORC_EXPNEG:
+                    if (ea[j] != 0) ok = 0;
+                    e[j] = 0;
+                    break;
+                case ORC_SQRT:
+                    if (ea[j] % 2) ok = 0;
+                    e[j] = ea[j] / 2;
+                    break;
+                case ORC_SQ: e[j] = 2 * ea[j]; break;
+                case ORC_CUBE: e[j] = 3 * ea[j]; break;
+                case ORC_INV: e[j] = -ea[j]; break;
+            }
+        }
+    }
+    free(ea);
+    return ok;
+}
+
+static int units_ok(const space_t* s, int64_t id) {
+    if (!s->units) return 1;
+    int* e = (int*)malloc(sizeof(int) * (size_t)s->d);
+    int ok = units_rec(s, id, e);
+    free(e);
+    return ok;
+}
+
+int oracle_units(int d, uint32_t ops, int rung, int grammar, const int* units, int64_t id, int* exps_out) {
+    space_t s;
+    if (space_init(&s, d, ops, rung, grammar) || !units) return -1;
+    s.units = units;
+    return units_rec(&s, id, exps_out);
+}
+
 /* values of feature id at all N samples, recursively from the primaries */
 static int eval_rec(const space_t* s, const double* X, int N, int64_t id, double* out) {
     int level, op; int64_t a, b;
@@ -323,6 +401,7 @@ static double pearson(const double* v, int N, double mean, double sd, const doub
 static int valid_rec(const space_t* s, const double* X, int N, int64_t id) {
     int level, op; int64_t a, b;
     if (decode(s, id, &level, &op, &a, &b)) return 0;
+    if (!units_ok(s, id)) return 0;
     double* v = (double*)malloc(sizeof(double) * (size_t)N);
     double m, sd;
     int cancelled;
@@ -350,7 +429,7 @@ static void* score_worker(void* p) {
         int cancelled, level, op;
         int64_t a, b;
         int ok = (eval_checked(j->s, j->X, j->N, id, v, &cancelled) == 0) && !cancelled &&
-                 moments(v, j->N, &m, &sd);
+                 moments(v, j->N, &m, &sd) && units_ok(j->s, id);
         if (ok && decode(j->s, id, &level, &op, &a, &b) == 0 && level > 0)
             ok = valid_rec(j->s, j->X, j->N, a) && (b < 0 || valid_rec(j->s, j->X, j->N, b));
         j->valid[q] = ok;
@@ -408,6 +487,7 @@ typedef struct {
     const double* X;
     const double* vals;   /* phi_{rung-1} values, id-major (P x N) */
     int* vok;             /* recursive validity of phi_{rung-1} */
+    int* uexp;            /* units of phi_{rung-1} (P x d), when the space has units */
     const double* tc; double tsd;
     double* score; int* valid;
     int tid, nthreads;
@@ -420,8 +500,22 @@ static void* level_table_worker(void* p) {
     for (int64_t id = j->tid; id < P; id += j->nthreads) {
         double* v = (double*)j->vals + (size_t)id * (size_t)j->N;
         j->vok[id] = eval_rec(j->s, j->X, j->N, id, v) == 0 && valid_rec(j->s, j->X, j->N, id);
+        if (j->uexp) units_rec(j->s, id, j->uexp + (size_t)id * (size_t)j->s->d);
     }
     return NULL;
+}
+
+/* the units rule of a feature new at the top level, from its operands' stored units */
+static int binary_units_ok(const level_job* j, int op, int64_t a, int64_t b) {
+    if (!j->uexp || (op != ORC_ADD && op != ORC_SUB)) return 1;
+    const int d = j->s->d;
+    return memcmp(j->uexp + (size_t)a * d, j->uexp + (size_t)b * d, sizeof(int) * (size_t)d) == 0;
+}
+static int unary_units_ok(const level_job* j, int op, int64_t a) {
+    if (!j->uexp || !(op == ORC_EXP || op == ORC_LOG || op == ORC_SIN || op == ORC_EXPNEG)) return 1;
+    const int d = j->s->d;
+    for (int q = 0; q < d; q++) if (j->uexp[(size_t)a * d + q]) return 0;
+    return 1;
 }
 
 /* score of the stored feature v (valid flag ok) */
@@ -452,7 +546,7 @@ static void* level_score_worker(void* p) {
                 if (row % j->nthreads != j->tid) continue;
                 const double* va = j->vals + (size_t)a * (size_t)N;
                 for (int q = 0; q < N; q++) v[q] = apply_unary(op, va[q]);
-                score_values(j, v, j->vok[a], id);
+                score_values(j, v, j->vok[a] && unary_units_ok(j, op, a), id);
             }
             id0 += P - Q;
             continue;
@@ -475,7 +569,7 @@ static void* level_score_worker(void* p) {
                             if (fabs(va[e]) + fabs(vb[e]) > mo) mo = fabs(va[e]) + fabs(vb[e]);
                         }
                         int cancelled = (op == ORC_ADD || op == ORC_SUB) && mv <= CANCEL_REL * mo;
-                        score_values(j, v, !cancelled && j->vok[i] && j->vok[b], id);
+                        score_values(j, v, !cancelled && j->vok[i] && j->vok[b] && binary_units_ok(j, op, i, b), id);
                     }
                 }
             }
@@ -495,26 +589,28 @@ static int scores_all_levelwise(const space_t* s, const double* X, int N, const 
     if ((size_t)P * (size_t)N > LEVEL_TABLE_MAX_BYTES / sizeof(double)) return -1;
     double* vals = (double*)malloc(sizeof(double) * (size_t)P * (size_t)N);
     int* vok = (int*)malloc(sizeof(int) * (size_t)P);
-    if (!vals || !vok) { free(vals); free(vok); return -1; }
+    int* uexp = s->units ? (int*)calloc((size_t)P * (size_t)s->d, sizeof(int)) : NULL;
+    if (!vals || !vok || (s->units && !uexp)) { free(vals); free(vok); free(uexp); return -1; }
     nthreads = default_threads(nthreads);
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
     level_job* jobs = (level_job*)malloc(sizeof(level_job) * (size_t)nthreads);
     for (int phase = 0; phase < 2; phase++) {
         for (int t = 0; t < nthreads; t++) {
-            level_job jb = { s, N, X, vals, vok, tc, tsd, score, valid, t, nthreads };
+            level_job jb = { s, N, X, vals, vok, uexp, tc, tsd, score, valid, t, nthreads };
             jobs[t] = jb;
             pthread_create(&th[t], NULL, phase == 0 ? level_table_worker : level_score_worker, &jobs[t]);
         }
         for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     }
-    free(th); free(jobs); free(vals); free(vok);
+    free(th); free(jobs); free(vals); free(vok); free(uexp);
     return 0;
 }
 
-int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const int* units, const double* X, int N,
                       const double* target, double* score_out, int* valid_out, int nthreads) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar) || N < 2) return -1;
+    s.units = units;
     double* tc = (double*)malloc(sizeof(double) * (size_t)N);
     double tsd = centre(target, N, tc);
     if (!(tsd > 0.0)) { free(tc); return -2; }
@@ -622,18 +718,19 @@ static int sis_step(const space_t* s, const double* X, int N, const double* targ
     return n_acc;
 }
 
-int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const int* units, const double* X, int N,
                   const double* target, const int64_t* S_prev, int n_prev, int k, double thr,
                   int64_t* acc_out, int nthreads) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1 || thr < 0.0) return -1;
+    s.units = units;
     return sis_step(&s, X, N, target, S_prev, n_prev, k, thr, acc_out, nthreads);
 }
 
 int oracle_sis(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                const double* target, const int64_t* S_prev, int n_prev, int k,
                int64_t* acc_out, int nthreads) {
-    return oracle_sis_ex(d, ops, rung, grammar, X, N, target, S_prev, n_prev, k, 0.0, acc_out, nthreads);
+    return oracle_sis_ex(d, ops, rung, grammar, NULL, X, N, target, S_prev, n_prev, k, 0.0, acc_out, nthreads);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -834,16 +931,17 @@ static int lstsq_qr(const double* A_in, const double* y_in, int N, int p, double
 
 int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
                int grammar, int k, int max_dim, int nthreads, oracle_result* out) {
-    return oracle_fit_ex(X, y, N, d, ops, rung, grammar, k, max_dim, 0.0, 0.0, nthreads, out);
+    return oracle_fit_ex(X, y, N, d, ops, rung, grammar, NULL, k, max_dim, 0.0, 0.0, nthreads, out);
 }
 
 int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
-                  int grammar, int k, int max_dim, double sis_threshold, double stop_rmse,
+                  int grammar, const int* units, int k, int max_dim, double sis_threshold, double stop_rmse,
                   int nthreads, oracle_result* out) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1 || k > 1024 ||
         max_dim < 1 || max_dim > ORC_MAX_DIM || N < max_dim + 1 || sis_threshold < 0.0 ||
         stop_rmse < 0.0) return -1;
+    s.units = units;
     memset(out, 0, sizeof(*out));
     double ybar = 0.0, sst = 0.0;
     for (int i = 0; i < N; i++) ybar += y[i];

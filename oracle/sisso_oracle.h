@@ -53,15 +53,18 @@ int oracle_scores(int d, uint32_t ops, int rung, int grammar, const double* X, i
                   const double* target, const int64_t* ids, int64_t n_ids,
                   double* score_out, int* valid_out, int nthreads);
 /* the same for every id of phi_rung, evaluated level by level (bit-identical results) */
-int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+int oracle_scores_all(int d, uint32_t ops, int rung, int grammar, const int* units, const double* X, int N,
                       const double* target, double* score_out, int* valid_out, int nthreads);
+/* dimensional analysis: units (d labels, -1 dimensionless; NULL: none) of feature id as
+   exponents over the labels in sixteenths (exps_out: d ints); returns 1 if consistent */
+int oracle_units(int d, uint32_t ops, int rung, int grammar, const int* units, int64_t id, int* exps_out);
 /* one SIS step: accept up to k ids (written to acc_out); returns number accepted or <0 */
 int oracle_sis(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
                const double* target, const int64_t* S_prev, int n_prev, int k,
                int64_t* acc_out, int nthreads);
 /* the same with the threshold variant of §2.2: the walk ends when the best remaining
    score is at or below thr (thr = 0: top k only) */
-int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const double* X, int N,
+int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const int* units, const double* X, int N,
                   const double* target, const int64_t* S_prev, int n_prev, int k, double thr,
                   int64_t* acc_out, int nthreads);
 /* exhaustive l0 over all D-subsets of n standardised features.
@@ -88,7 +91,7 @@ int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int
 /* the same with the SIS threshold (0: top k only) and the "low enough error" stop: after a
    step whose RMSE <= stop_rmse (0: only the exact-fit stop) */
 int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
-                  int grammar, int k, int max_dim, double sis_threshold, double stop_rmse,
+                  int grammar, const int* units, int k, int max_dim, double sis_threshold, double stop_rmse,
                   int nthreads, oracle_result* out);
 
 #ifdef __cplusplus

@@ -171,3 +171,32 @@ def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: in
         if rmse <= 1e-10 * y.std() or (stop_rmse > 0 and rmse <= stop_rmse):
             break
     return out
+
+
+def units(f, labels):
+    """Units of feature tree f as {label: exponent} (Fractions), or None when the tree
+    breaks the dimensional rule: + and - on unequal units, exp, log, sin or exp- of a
+    dimensioned operand.  labels[i]: unit label of primary i, -1 dimensionless."""
+    from fractions import Fraction
+    if f[0] == "x":
+        lab = labels[f[1]]
+        return {} if lab < 0 else {lab: Fraction(1)}
+    a = units(f[1], labels)
+    if a is None:
+        return None
+    op = f[0]
+    if op in BINARY:
+        b = units(f[2], labels)
+        if b is None:
+            return None
+        if op in ("+", "-"):
+            return a if a == b else None
+        sign = 1 if op == "*" else -1
+        out = dict(a)
+        for k, v in b.items():
+            out[k] = out.get(k, 0) + sign * v
+        return {k: v for k, v in out.items() if v != 0}
+    if op in ("exp", "log", "sin", "exp-"):
+        return {} if not a else None
+    scale = {"sqrt": Fraction(1, 2), "^2": 2, "^3": 3, "^-1": -1}[op]
+    return {k: v * scale for k, v in a.items()}

@@ -84,3 +84,76 @@ def test_stop_rmse_ends_the_iteration(orc):
         assert a.ids == b.ids and a.coef == b.coef and a.rmse == b.rmse
     ref = brute.sisso(X, y, 3, NAMES, 2, 8, 3, stop_rmse=tol)
     assert [r[0] for r in ref] == [d.ids for d in short.dims]
+
+
+# ---- dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality) ---------------
+ALL12 = brute.TABLE
+
+
+OPS_R3 = ["+", "-", "*", "/", "exp", "sqrt", "^-1"]
+
+
+@pytest.mark.parametrize("labels,rung,nxp,ops", [((0, 0, 1), 2, False, ALL12), ((0, 1, -1), 2, False, ALL12),
+                                                 ((1, 1), 3, False, OPS_R3), ((0, 1), 3, True, OPS_R3)])
+def test_units_match_brute_force(orc, labels, rung, nxp, ops):
+    """Every feature's unit exponents and consistency flag equal the brute-force units of
+    its expression tree (exact fractions)."""
+    d = len(labels)
+    feats, sizes = brute.space(d, ops, rung, nxp)
+    sp = orc.Space(d, _mask(orc, ops), rung, orc.GRAMMAR_NEW_X_PREV if nxp else orc.GRAMMAR_EQ2, units=labels)
+    assert sp.sizes() == sizes
+    n_bad = 0
+    for i, f in enumerate(feats):
+        u = brute.units(f, labels)
+        ok, e = sp.units_of(i)
+        assert ok == (u is not None), brute.to_str(f)
+        if ok:
+            assert {k: v for k, v in enumerate(e) if v} == {k: int(v * 16) for k, v in u.items()}, brute.to_str(f)
+        n_bad += not ok
+    assert n_bad > 0
+
+
+def test_units_validity_and_sis_match_brute_force(orc):
+    """With units, a feature is valid iff its values are valid and it (with every operand) is
+    dimensionally consistent; the SIS step with units equals the brute-force walk over
+    those features."""
+    rng = np.random.default_rng(21)
+    X = rng.uniform(1, 5, size=(30, 3))
+    y = (X[:, 0] - X[:, 1]) / X[:, 2] + 0.05 * rng.normal(size=30)
+    labels = (0, 0, 1)
+    feats, _ = brute.space(3, ALL12, 2)
+    values = [brute.evaluate(f, X) for f in feats]
+    ok = [brute.valid(v, f, X) and brute.units(f, labels) is not None for v, f in zip(values, feats)]
+    sp = orc.Space(3, _mask(orc, ALL12), 2, units=labels)
+    sc, va = sp.scores_all(X, y)
+    assert list(va) == ok
+    for i in np.flatnonzero(va):
+        assert sc[i] == pytest.approx(brute.abs_corr(values[i], y), abs=1e-12)
+    assert sp.sis(X, y, [], 15) == brute.sis(values, y, [], 15, ok)
+
+
+def test_units_fit_recovers_physical_descriptor(orc):
+    """y = 2 (x1 - x2) / x3 + 1 with x1, x2 lengths and x3 a time: the units-aware fit finds
+    (x1-x2)/x3 as its 1-term descriptor, its whole iteration equals the brute-force one
+    over the consistent features, and no selected feature breaks the units rule."""
+    rng = np.random.default_rng(22)
+    X = rng.uniform(1, 5, size=(40, 3))
+    y = 2.0 * (X[:, 0] - X[:, 1]) / X[:, 2] + 1.0
+    labels = (0, 0, 1)
+    sp = orc.Space(3, _mask(orc, ALL12), 2, units=labels)
+    res = orc.fit(X, y, sp, 10, 2)
+    v = sp.eval(X, res.dims[0].ids[0])                  # (x1-x2)/x3 or a duplicate of it
+    assert abs(np.corrcoef(v, (X[:, 0] - X[:, 1]) / X[:, 2])[0, 1]) > 1 - 1e-12
+    assert res.dims[0].rmse < 1e-9
+    assert all(sp.units_of(i)[0] for s in res.sis for i in s)
+
+
+def test_dimensionless_units_change_nothing(orc):
+    """All primaries dimensionless: every rule is met, so validity and scores equal those of
+    the space without units."""
+    rng = np.random.default_rng(23)
+    X = rng.uniform(0.5, 3, size=(25, 3))
+    y = rng.normal(size=25)
+    a = orc.Space(3, _mask(orc, ALL12), 2).scores_all(X, y)
+    b = orc.Space(3, _mask(orc, ALL12), 2, units=(-1, -1, -1)).scores_all(X, y)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
