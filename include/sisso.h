@@ -103,6 +103,15 @@ typedef struct {
     double stop_rmse;       /* "low enough error" stop of the iteration (§2.3): after a step
                                whose RMSE is at or below this (in units of y), no further
                                step runs (0 = only the exact-fit stop, the default) */
+    const int* units;       /* dimensional analysis (§2.1, closing paragraph; §3.3
+                               dimensionality): d unit labels, HOST memory, copied by
+                               sisso_create; primaries with equal labels share units, -1
+                               is dimensionless (NULL = no units, the default).  Units are
+                               exponent vectors over the labels: + and - need equal units,
+                               exp, log, sin and exp(-.) a dimensionless operand, the other
+                               operators combine units.  A feature that breaks the rule, or
+                               is built from one that does, is invalid (scores -1, never
+                               selected); ids are those of the space without units. */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */
@@ -140,8 +149,8 @@ void sisso_default_opts(sisso_opts* opts);
  * buffer sisso_fit needs.  sis_size is k of §2.2 (features added per step), max_dim the
  * number of terms T of §2.3.  Errors: SISSO_ERR_ARG for N < max_dim+1, d < 1, rung not
  * in 1..SISSO_MAX_RUNG, max_dim not in 1..SISSO_MAX_DIM, sis_size not in
- * 1..SISSO_MAX_SIS, an empty op mask, sis_threshold outside [0, 1), stop_rmse < 0, or
- * non-finite X/y; SISSO_ERR_OOM; SISSO_ERR_CUDA.
+ * 1..SISSO_MAX_SIS, an empty op mask, sis_threshold outside [0, 1), stop_rmse < 0, a unit
+ * label outside -1..d-1, or non-finite X/y; SISSO_ERR_OOM; SISSO_ERR_CUDA.
  * On error *out is NULL. */
 sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32_t op_set,
                           int rung, int sis_size, int max_dim, const sisso_opts* opts,
@@ -298,7 +307,7 @@ typedef struct {
  * and device memory, and allocate all device memory the runs need (one arena).  opts:
  * grammar, max_band (band capacity per task and step, default 16384), cuda_stream and
  * device are used; precision must be SISSO_PREC_FP32 (or default), sis_threshold and
- * stop_rmse 0 (top-k screening, exact-fit stop).  Limits: n_tasks <=
+ * stop_rmse 0 (top-k screening, exact-fit stop), units NULL.  Limits: n_tasks <=
  * 2^20, max_dim <= 4, max_dim * sis_size <= 512, every task N >= max_dim + 1 and d >= 1, finite inputs,
  * non-constant y, and at most 2^18 screening units per task.  Errors: SISSO_ERR_ARG
  * (message names the task), SISSO_ERR_OOM, SISSO_ERR_CUDA.  On error *out is NULL and

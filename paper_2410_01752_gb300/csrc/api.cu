@@ -50,7 +50,8 @@ void free_all(sisso_ctx* c) {
                     c->band, c->band_rss, c->band_count, c->prefixes, c->work, c->win, c->blk_best,
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
                     c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
-                    c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info};
+                    c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info,
+                    c->unit_ok, c->unit_mask};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (c->walk_h) cudaFreeHost(c->walk_h);
@@ -71,6 +72,9 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if ((int64_t)max_dim * k > (max_dim <= 4 ? 65535 : 4095)) { why = "subspace too large"; return SISSO_ERR_ARG; }
     if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
     if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
+    if (o.units)
+        for (int j = 0; j < d; ++j)
+            if (o.units[j] < -1 || o.units[j] >= d) { why = "unit labels must be in -1..d-1"; return SISSO_ERR_ARG; }
     return SISSO_OK;
 }
 
@@ -104,6 +108,8 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     sisso_ctx* c = new (std::nothrow) sisso_ctx();
     if (!c) return SISSO_ERR_OOM;
     c->N = N; c->d = d; c->rung = rung; c->k = sis_size; c->max_dim = max_dim; c->ops = op_set; c->opts = o;
+    if (o.units) c->units.assign(o.units, o.units + d);
+    c->opts.units = nullptr;        // the labels live in the context
     if (!plan_space(d, op_set, rung, o.grammar, c->space)) { delete c; return SISSO_ERR_ARG; }
     c->n_feat = c->space.phi[rung];
     if (c->space.phi[rung - 1] >= (int64_t)1 << 31) { delete c; return SISSO_ERR_ARG; }
@@ -199,6 +205,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     // validity of the operand features (depends on X only), moments of y, y~ = y - mean(y)
     st = fill_val64(c);
+    if (!st) st = build_units(c);
     if (!st) st = compute_subvalid(c);
     if (!st) st = fill_opcache(c);
     if (!st) st = prepare_target(c, c->y64);

@@ -1378,8 +1378,8 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         return SISSO_ERR_ARG;
     }
     if (o.precision != SISSO_PREC_FP32) { set_err("the batched form computes in FP32 (SISSO_PREC_FP32)"); return SISSO_ERR_ARG; }
-    if (o.sis_threshold != 0.0 || o.stop_rmse != 0.0) {
-        set_err("the batched form screens the top sis_size and stops at exact fits (sis_threshold = stop_rmse = 0)");
+    if (o.sis_threshold != 0.0 || o.stop_rmse != 0.0 || o.units) {
+        set_err("the batched form screens the top sis_size without units and stops at exact fits (sis_threshold = stop_rmse = 0, units = NULL)");
         return SISSO_ERR_ARG;
     }
     if (o.grammar != SISSO_GRAMMAR_EQ2 && o.grammar != SISSO_GRAMMAR_NEW_X_PREV) { set_err("bad grammar"); return SISSO_ERR_ARG; }

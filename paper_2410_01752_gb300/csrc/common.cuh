@@ -421,6 +421,11 @@ struct sisso_ctx {
     sg::Winner* win_h = nullptr;       // pinned host
     unsigned long long* blk_best = nullptr;  // per-block tie-break winners
     int blk_cap = 0;
+    // dimensional analysis: unit labels of the primaries, the units rule of every id of
+    // phi_{L-1} (recursive, one byte each) and of every id of phi_L (one bit each)
+    std::vector<int> units;
+    unsigned char* unit_ok = nullptr;
+    unsigned* unit_mask = nullptr;
     // tiled FP32 enumeration: padded FP32 Gram, moments and diagonal (rows x tile_ld), tile list
     float* tile_G = nullptr;
     float* tile_b = nullptr;
@@ -471,6 +476,7 @@ void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles);
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
 sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status ensure_tile_buffers(sisso_ctx* c, int n);
+sisso_status build_units(sisso_ctx* c);
 sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,

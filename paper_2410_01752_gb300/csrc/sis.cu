@@ -16,6 +16,7 @@
 #include "sis_device.cuh"
 
 #include <algorithm>
+#include <map>
 #include <cfloat>
 #include <cstring>
 
@@ -47,7 +48,8 @@ __global__ void k_fill_val64(const Space* __restrict__ sp, const double* __restr
 }
 
 __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t lo,
-                           int64_t hi, const double* __restrict__ V, unsigned char* __restrict__ valid) {
+                           int64_t hi, const double* __restrict__ V, const unsigned char* __restrict__ unit_ok,
+                           unsigned char* __restrict__ valid) {
     const int64_t id = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (id >= hi) return;
@@ -86,7 +88,7 @@ __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restric
     ss = warp_sum(ss);
     if (lane == 0) {
         const bool cancelled = root_is_addsub(p) && mx <= kCancelRel * mo;
-        valid[id] = !bad && !cancelled && sqrt(ss / N) > kConstRel * mx;
+        valid[id] = !bad && !cancelled && sqrt(ss / N) > kConstRel * mx && (!unit_ok || unit_ok[id]);
     }
 }
 
@@ -367,10 +369,12 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
     rescore_one(sp, Xc, N, N, tc, st, ids[w], w, subvalid, V, score, mean_out, sd_out, valid_out, probe, zc);
 }
 
-// sort keys: valid survivors not in S get their FP64 score, others -1; padding -2
+// sort keys: valid survivors not in S (and, with units, dimensionally consistent) get
+// their FP64 score, others -1; padding -2
 __global__ void k_sort_keys(const int64_t* __restrict__ ids, const double* __restrict__ score,
                             const int* __restrict__ valid, int n, const int64_t* __restrict__ S_sorted,
-                            int nS, int n_pad, double* sk, int64_t* sid, int* ssrc) {
+                            int nS, int n_pad, const unsigned* __restrict__ unit_mask, double* sk, int64_t* sid,
+                            int* ssrc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
     if (i >= n) { sk[i] = -2.0; sid[i] = INT64_MAX; ssrc[i] = -1; return; }
@@ -378,7 +382,8 @@ __global__ void k_sort_keys(const int64_t* __restrict__ ids, const double* __res
     int lo = 0, hi = nS;            // binary search in S (ascending)
     while (lo < hi) { const int m = (lo + hi) >> 1; if (S_sorted[m] < id) lo = m + 1; else hi = m; }
     const bool inS = lo < nS && S_sorted[lo] == id;
-    sk[i] = (valid[i] && !inS) ? score[i] : -1.0;
+    const bool units = !unit_mask || ((unit_mask[id >> 5] >> (id & 31)) & 1u);
+    sk[i] = (valid[i] && !inS && units) ? score[i] : -1.0;
     sid[i] = id;
     ssrc[i] = i;
 }
@@ -831,6 +836,107 @@ __global__ void k_eval(const Space* __restrict__ sp, const T* __restrict__ Xc, i
 // ===================================================================================
 
 // validity of every id of phi_{L-1}, level by level (operands before their features)
+// ---------------------------------------------------------------------------------
+// dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality)
+// ---------------------------------------------------------------------------------
+__global__ void k_apply_unit_mask(const unsigned* __restrict__ mask, int64_t n, float* __restrict__ scores) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!((mask[i >> 5] >> (i & 31)) & 1u)) scores[i] = -1.0f;
+}
+
+// one bit per id of phi_L: ids of phi_{L-1} carry their own (recursive) rule; a top-level
+// id is consistent when its operands are and its operator's rule holds on their classes
+// (+ and -: equal units; exp, log, sin, exp(-.): dimensionless operand)
+__global__ void k_unit_mask_build(const Space* __restrict__ sp, int64_t P, int64_t n,
+                                  const unsigned char* __restrict__ unit_ok, const int* __restrict__ cls,
+                                  int dimless, unsigned* __restrict__ mask) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;     // word
+    if (w * 32 >= n) return;
+    unsigned bits = 0;
+    for (int q = 0; q < 32; ++q) {
+        const int64_t id = w * 32 + q;
+        if (id >= n) break;
+        bool ok;
+        if (id < P) {
+            ok = unit_ok[id] != 0;
+        } else {
+            int level, op;
+            int64_t a, b;
+            ok = decode(*sp, id, level, op, a, b) && unit_ok[a] && (b < 0 || unit_ok[b]);
+            if (ok && (op == ADD || op == SUB)) ok = cls[a] == cls[b];
+            if (ok && (op == EXP || op == LOG || op == SIN || op == EXPNEG)) ok = cls[a] == dimless;
+        }
+        bits |= ok ? (1u << q) : 0u;
+    }
+    mask[w] = bits;
+}
+
+// Units of every id of phi_{L-1} on the host (exponent vectors over the labels, in
+// sixteenths, interned as classes; a few hundred thousand ids at most), then the bitmask
+// of phi_L on the device.  No units: nothing to do.
+sisso_status build_units(sisso_ctx* c) {
+    if (c->units.empty()) return SISSO_OK;
+    const Space& sp = c->space;
+    const int64_t P = sp.phi[c->rung - 1], n = c->n_feat;
+    const int d = c->d;
+    std::map<std::vector<int>, int> classes;
+    std::vector<std::vector<int>> vec_of;
+    auto intern = [&](const std::vector<int>& e) {
+        auto it = classes.find(e);
+        if (it != classes.end()) return it->second;
+        const int k = (int)vec_of.size();
+        classes.emplace(e, k);
+        vec_of.push_back(e);
+        return k;
+    };
+    const int dimless = intern(std::vector<int>(d, 0));
+    std::vector<int> cls((size_t)P);
+    std::vector<unsigned char> ok((size_t)P);
+    for (int64_t id = 0; id < P; ++id) {
+        int level, op;
+        int64_t a, b;
+        decode(sp, id, level, op, a, b);
+        std::vector<int> e(d, 0);
+        bool good = true;
+        if (level == 0) {
+            if (c->units[a] >= 0) e[c->units[a]] = 16;
+        } else {
+            const std::vector<int>& ea = vec_of[cls[a]];
+            good = ok[a] && (b < 0 || ok[b]);
+            for (int j = 0; j < d; ++j) {
+                const int x = ea[j], y = b >= 0 ? vec_of[cls[b]][j] : 0;
+                switch (op) {
+                    case ADD: case SUB: if (x != y) good = false; e[j] = x; break;
+                    case MUL: e[j] = x + y; break;
+                    case DIV: e[j] = x - y; break;
+                    case EXP: case LOG: case SIN: case EXPNEG: if (x != 0) good = false; e[j] = 0; break;
+                    case SQRT: if (x % 2) good = false; e[j] = x / 2; break;
+                    case SQ: e[j] = 2 * x; break;
+                    case CUBE: e[j] = 3 * x; break;
+                    default: e[j] = -x; break;      // INV
+                }
+            }
+        }
+        cls[(size_t)id] = intern(e);
+        ok[(size_t)id] = good ? 1 : 0;
+    }
+    int* d_cls = nullptr;
+    sisso_status st;
+    const int64_t words = (n + 31) / 32;
+    if ((st = check_cuda(c, cudaMalloc(&c->unit_ok, (size_t)P), "unit_ok")) ||
+        (st = check_cuda(c, cudaMalloc(&c->unit_mask, sizeof(unsigned) * (size_t)words), "unit_mask")) ||
+        (st = check_cuda(c, cudaMallocAsync(&d_cls, sizeof(int) * (size_t)P, c->stream), "unit classes")))
+        return st;
+    cudaMemcpyAsync(c->unit_ok, ok.data(), (size_t)P, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(d_cls, cls.data(), sizeof(int) * (size_t)P, cudaMemcpyHostToDevice, c->stream);
+    k_unit_mask_build<<<(int)((words + 255) / 256), 256, 0, c->stream>>>(c->space_dev, P, n, c->unit_ok, d_cls,
+                                                                        dimless, c->unit_mask);
+    c->stats.launches++;
+    cudaFreeAsync(d_cls, c->stream);
+    // the host vectors are freed on return: the copies must have left them
+    return check_cuda(c, cudaStreamSynchronize(c->stream), "build_units");
+}
+
 sisso_status compute_subvalid(sisso_ctx* c) {
     const Space& sp = c->space;
     for (int l = 0; l < sp.rung; ++l) {
@@ -838,7 +944,7 @@ sisso_status compute_subvalid(sisso_ctx* c) {
         const int64_t n = hi - lo;
         if (n <= 0) continue;
         k_subvalid<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, lo, hi,
-                                                                       c->opval64, c->subvalid);
+                                                                       c->opval64, c->unit_ok, c->subvalid);
         c->stats.launches++;
     }
     return check_cuda(c, cudaGetLastError(), "subvalid");
@@ -1013,9 +1119,18 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         if (st) return st;
     }
     cudaEventRecord(e2, c->stream);
-    cudaEventSynchronize(e2);
-    c->stats.ms_screen += event_ms(e0, e2);
+    if (c->unit_mask) {     // dimensional analysis: non-physical candidates score -1
+        k_apply_unit_mask<<<std::max(1, std::min(c->sms * 8, (int)((c->n_feat + 255) / 256))), 256, 0, c->stream>>>(
+            c->unit_mask, c->n_feat, c->scores);
+        c->stats.launches++;
+    }
+    cudaEvent_t e3;
+    cudaEventCreate(&e3);
+    cudaEventRecord(e3, c->stream);
+    cudaEventSynchronize(e3);
+    c->stats.ms_screen += event_ms(e0, e3);
     c->stats.ms_screen_pair += event_ms(e1, e2);
+    cudaEventDestroy(e3);
     c->stats.candidates_scored += c->n_feat;
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
     return SISSO_OK;
@@ -1090,8 +1205,8 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         int n_pad = 1;
         while (n_pad < std::max(ns, 1)) n_pad <<= 1;
         k_sort_keys<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->surv_ids, c->surv_score, c->surv_valid, ns,
-                                                                 c->S_sorted, n_prev, n_pad, c->sort_score,
-                                                                 c->sort_id, c->sort_src);
+                                                                 c->S_sorted, n_prev, n_pad, c->unit_mask,
+                                                                 c->sort_score, c->sort_id, c->sort_src);
         c->stats.launches += 2;
         cudaEventRecord(q[2], c->stream);
         if (n_pad <= kSortBlock) {

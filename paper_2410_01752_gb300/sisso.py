@@ -55,7 +55,8 @@ class SissoError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("grammar", C.c_int), ("survivors", C.c_int),
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
-                ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double)]
+                ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
+                ("units", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -257,7 +258,7 @@ class Sisso:
     def __init__(self, X, y, op_set: int, rung: int, sis_size: int, max_dim: int,
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
-                 sis_threshold: float = 0.0, stop_rmse: float = 0.0):
+                 sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -268,6 +269,10 @@ class Sisso:
         o.precision, o.grammar, o.survivors = precision, grammar, survivors
         o.max_band, o.band_rel, o.device = max_band, band_rel, device
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
+        ulab = None
+        if units is not None:        # one label per primary (-1: dimensionless); copied by sisso_create
+            ulab = np.ascontiguousarray(np.asarray(units, dtype=np.int32))
+            o.units = C.c_void_p(ulab.ctypes.data)
         if stream is not None:
             o.cuda_stream = C.c_void_p(getattr(stream, "cuda_stream", stream))
         st = L.sisso_create(xp, yp, N, d, op_set, rung, sis_size, max_dim, C.byref(o), C.byref(self._ctx))

@@ -85,3 +85,53 @@ def test_stop_rmse(S, orc, prec):
     assert [g.ids for g in got] == [r.ids for r in ref.dims]
     for g, r in zip(got, ref.dims):
         assert abs(g.rmse - r.rmse) <= 1e-6 * r.rmse
+
+
+# ---- dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality) ---------------
+def _units_problem(seed, N, d):
+    r = np.random.default_rng(seed)
+    X = r.uniform(1, 5, size=(N, d))
+    y = 2.0 * (X[:, 0] - X[:, 1]) / X[:, 2] + 0.5 * X[:, 3] * X[:, 2] + 0.01 * r.normal(size=N)
+    return X, y
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("labels,rung,g", [((0, 0, 1, 2), 2, 0), ((0, 0, 1, -1, 1), 2, 0), ((0, 0, 1, 2), 3, 1)])
+def test_units_scores(S, orc, prec, labels, rung, g):
+    """With unit labels, the screening rejects every feature that breaks the units rule
+    (itself or through an operand), rejects only what the oracle rejects (the value cap is
+    checked exactly by the FP64 re-score of the window, as without units), and scores the
+    rest as the oracle does."""
+    d = len(labels)
+    X, y = _units_problem(31 + d, 120, d)
+    sp = orc.Space(d, inputs.OPS9, rung, g, units=labels)
+    ref, va = sp.scores_all(X, y)
+    _, va_plain = orc.Space(d, inputs.OPS9, rung, g).scores_all(X, y)
+    by_units = va_plain & ~va
+    with S.Sisso(X, y, inputs.OPS9, rung, 10, 2, precision=prec, grammar=g, units=labels) as c:
+        got = c.score_all(y, prec)
+    assert by_units.sum() > 0
+    assert np.all(got[by_units] < 0)
+    assert np.all(va[got < 0] == False)                                  # noqa: E712
+    tol = 2e-4 if prec == 1 else 1e-7
+    ok = va & (got >= 0)
+    assert np.abs(got[ok] - ref[ok]).max() <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("rung,g", [(2, 0), (3, 1)])
+def test_units_fit(S, orc, prec, rung, g):
+    """The whole iteration with units against the oracle's: SIS selections and descriptors
+    bit-exact, coefficients within 1e-6."""
+    labels = (0, 0, 1, 2)
+    X, y = _units_problem(40 + rung, 200, 4)
+    sp = orc.Space(4, inputs.OPS9, rung, g, units=labels)
+    ref = orc.fit(X, y, sp, 15, 3)
+    with S.Sisso(X, y, inputs.OPS9, rung, 15, 3, precision=prec, grammar=g, units=labels) as c:
+        got = c.fit()
+        assert len(got) == len(ref.dims) > 0
+        for t, (a, r) in enumerate(zip(got, ref.dims)):
+            assert c.sis(t + 1) == ref.sis[t]
+            assert a.ids == r.ids
+            np.testing.assert_allclose(a.coef, r.coef, rtol=1e-6, atol=1e-9 * np.abs(y).max())
+    assert all(sp.units_of(i)[0] for s in ref.sis for i in s)
