@@ -88,6 +88,9 @@ def lib():
                                     C.c_int, C.c_double, i64p, C.c_int]
         L.oracle_fit_ex.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, ip, C.c_int,
                                     C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(_Result)]
+        L.oracle_mi_kde.argtypes = [dp, C.c_int, C.c_int, dp, dp]
+        L.oracle_spearman.argtypes = [dp, C.c_int, C.c_int, dp, dp]
+        L.oracle_prescreen_keep.argtypes = [dp, C.c_int, C.c_double, ip]
         L.oracle_l0.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, i64p, ip, dp, C.c_int]
         L.oracle_l0.restype = C.c_int64
         L.oracle_fit.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int,
@@ -273,3 +276,32 @@ def fit(X, y, space: Space, k: int, max_dim: int, nthreads: int = 0, sis_thresho
                                    rmse=float(r.rmse[t]), r2=float(r.r2[t]),
                                    rss_gram=float(r.rss_gram[t]), subsets=int(r.subsets[t])))
     return out
+
+
+def mi_kde(X, y) -> np.ndarray:
+    """MI(y; x_i) of every primary by Gaussian kernel density estimates (§3.1)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    out = np.zeros(X.shape[1])
+    if lib().oracle_mi_kde(_dp(X), X.shape[0], X.shape[1], _dp(y), _dp(out)):
+        raise ValueError("oracle_mi_kde failed")
+    return out
+
+
+def spearman(X, y) -> np.ndarray:
+    """Spearman rank correlation of every primary with y (§3.3)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    out = np.zeros(X.shape[1])
+    if lib().oracle_spearman(_dp(X), X.shape[0], X.shape[1], _dp(y), _dp(out)):
+        raise ValueError("oracle_spearman failed")
+    return out
+
+
+def prescreen_keep(score, q: float) -> np.ndarray:
+    """Flags of the primaries whose score is in the top quantile q (§3.3)."""
+    score = np.ascontiguousarray(score, dtype=np.float64)
+    keep = np.zeros(score.size, dtype=np.int32)
+    if lib().oracle_prescreen_keep(_dp(score), score.size, float(q), keep.ctypes.data_as(C.POINTER(C.c_int))) < 0:
+        raise ValueError("oracle_prescreen_keep failed")
+    return keep.astype(bool)

@@ -1014,3 +1014,128 @@ int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, 
     free(yc); free(target);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* pre-screening of the primaries (§3.1; §3.3 initial_screening)                          */
+/* ------------------------------------------------------------------------------------ */
+
+#define ORC_PI 3.14159265358979323846
+
+static void mean_var(const double* v, int N, int stride, double* m, double* var) {
+    double s = 0.0;
+    for (int i = 0; i < N; i++) s += v[(size_t)i * stride];
+    double mu = s / N, ss = 0.0;
+    for (int i = 0; i < N; i++) { double e = v[(size_t)i * stride] - mu; ss += e * e; }
+    *m = mu;
+    *var = ss / (N - 1);              /* unbiased, as the KDE bandwidth rule takes it */
+}
+
+/* MI(y; x_i) of Eq. (MI) estimated by resubstitution with Gaussian kernel density
+   estimates: MI = mean_s log( p(x_s, y_s) / (p(x_s) p(y_s)) ).  Reading: the bandwidths
+   follow Scott's rule, the kernel covariance of a d-dimensional estimate being
+   N^(-2/(d+4)) times the sample covariance (the joint density uses the full 2 x 2
+   covariance of (x_i, y)).  X is N x d row-major; mi_out: d values. */
+int oracle_mi_kde(const double* X, int N, int d, const double* y, double* mi_out) {
+    if (N < 3 || d < 1) return -1;
+    double my, vy;
+    mean_var(y, N, 1, &my, &vy);
+    double f1 = pow((double)N, -2.0 / 5.0), f2 = pow((double)N, -2.0 / 6.0);
+    double hy2 = f1 * vy;
+    /* p(y_s) */
+    double* py = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int s = 0; s < N; s++) {
+        double acc = 0.0;
+        for (int t = 0; t < N; t++) { double u = y[s] - y[t]; acc += exp(-0.5 * u * u / hy2); }
+        py[s] = acc / (N * sqrt(2.0 * ORC_PI * hy2));
+    }
+    for (int i = 0; i < d; i++) {
+        double mx, vx;
+        mean_var(X + i, N, d, &mx, &vx);
+        double cxy = 0.0;
+        for (int s = 0; s < N; s++) cxy += (X[(size_t)s * d + i] - mx) * (y[s] - my);
+        cxy /= (N - 1);
+        double hx2 = f1 * vx;
+        /* joint kernel covariance H = f2 * [[vx, cxy], [cxy, vy]] and its inverse */
+        double a = f2 * vx, b = f2 * cxy, c = f2 * vy;
+        double det = a * c - b * b;
+        if (!(vx > 0.0) || !(det > 0.0)) { free(py); return -2; }
+        double ia = c / det, ib = -b / det, ic = a / det;
+        double sum = 0.0;
+        for (int s = 0; s < N; s++) {
+            double xs = X[(size_t)s * d + i], kx = 0.0, kxy = 0.0;
+            for (int t = 0; t < N; t++) {
+                double u = xs - X[(size_t)t * d + i], v = y[s] - y[t];
+                kx += exp(-0.5 * u * u / hx2);
+                kxy += exp(-0.5 * (ia * u * u + 2.0 * ib * u * v + ic * v * v));
+            }
+            double px = kx / (N * sqrt(2.0 * ORC_PI * hx2));
+            double pxy = kxy / (N * 2.0 * ORC_PI * sqrt(det));
+            sum += log(pxy / (px * py[s]));
+        }
+        mi_out[i] = sum / N;
+    }
+    free(py);
+    return 0;
+}
+
+/* average ranks (1-based; ties share the mean of their positions) of v (stride) */
+static void ranks(const double* v, int N, int stride, double* r) {
+    for (int s = 0; s < N; s++) {
+        int less = 0, equal = 0;
+        for (int t = 0; t < N; t++) {
+            double a = v[(size_t)s * stride], b = v[(size_t)t * stride];
+            if (b < a) less++;
+            else if (b == a) equal++;
+        }
+        r[s] = less + (equal + 1) / 2.0;
+    }
+}
+
+/* Spearman rank correlation of x_i and y (the Pearson correlation of average ranks) */
+int oracle_spearman(const double* X, int N, int d, const double* y, double* rho_out) {
+    if (N < 2 || d < 1) return -1;
+    double* ry = (double*)malloc(sizeof(double) * (size_t)N);
+    double* rx = (double*)malloc(sizeof(double) * (size_t)N);
+    ranks(y, N, 1, ry);
+    for (int i = 0; i < d; i++) {
+        ranks(X + i, N, d, rx);
+        double mx = 0.0, my = 0.0;
+        for (int s = 0; s < N; s++) { mx += rx[s]; my += ry[s]; }
+        mx /= N; my /= N;
+        double sxy = 0.0, sxx = 0.0, syy = 0.0;
+        for (int s = 0; s < N; s++) {
+            sxy += (rx[s] - mx) * (ry[s] - my);
+            sxx += (rx[s] - mx) * (rx[s] - mx);
+            syy += (ry[s] - my) * (ry[s] - my);
+        }
+        rho_out[i] = (sxx > 0.0 && syy > 0.0) ? sxy / sqrt(sxx * syy) : 0.0;
+    }
+    free(rx); free(ry);
+    return 0;
+}
+
+static int dbl_cmp(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Keep the primaries whose score lies in the top quantile q (0 < q <= 1): score strictly
+   above the (1 - q)-quantile of the d scores (linear interpolation between order
+   statistics, position (d - 1)(1 - q)); with q = 1 every primary is kept.  Reading of
+   §3.3 ("only features with MI inside of this quantile range").  keep_out: d flags;
+   returns the number kept. */
+int oracle_prescreen_keep(const double* score, int d, double q, int* keep_out) {
+    if (d < 1 || !(q > 0.0 && q <= 1.0)) return -1;
+    if (q >= 1.0) { for (int i = 0; i < d; i++) keep_out[i] = 1; return d; }
+    double* s = (double*)malloc(sizeof(double) * (size_t)d);
+    memcpy(s, score, sizeof(double) * (size_t)d);
+    qsort(s, (size_t)d, sizeof(double), dbl_cmp);
+    double pos = (d - 1) * (1.0 - q);
+    int lo = (int)floor(pos);
+    double fr = pos - lo;
+    double cut = lo + 1 < d ? s[lo] + fr * (s[lo + 1] - s[lo]) : s[lo];
+    int n = 0;
+    for (int i = 0; i < d; i++) { keep_out[i] = score[i] > cut; n += keep_out[i]; }
+    free(s);
+    return n;
+}

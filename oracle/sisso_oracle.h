@@ -74,6 +74,13 @@ int oracle_sis_ex(int d, uint32_t ops, int rung, int grammar, const int* units, 
 int64_t oracle_l0(const double* G, const double* b, double syy, int N, int n, int D,
                   const int64_t* gid, int* best_pos, double* best_rss, int nthreads);
 
+/* pre-screening of the primaries (§3.1; §3.3): MI(y; x_i) by Gaussian kernel density
+   estimates (Scott's rule, resubstitution), Spearman rank correlation, and the top-quantile
+   rule; X N x d row-major */
+int oracle_mi_kde(const double* X, int N, int d, const double* y, double* mi_out);
+int oracle_spearman(const double* X, int N, int d, const double* y, double* rho_out);
+int oracle_prescreen_keep(const double* score, int d, double q, int* keep_out);
+
 typedef struct {
     int n_dims;                         /* descriptors produced (<= max_dim) */
     int n_sis[ORC_MAX_DIM];             /* ids accepted by SIS at step t */

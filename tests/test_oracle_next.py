@@ -157,3 +157,66 @@ def test_dimensionless_units_change_nothing(orc):
     a = orc.Space(3, _mask(orc, ALL12), 2).scores_all(X, y)
     b = orc.Space(3, _mask(orc, ALL12), 2, units=(-1, -1, -1)).scores_all(X, y)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
+
+
+# ---- pre-screening of the primaries (§3.1; §3.3 initial_screening) ----------------------
+def _mi_scipy(a, b):
+    st = pytest.importorskip("scipy.stats")
+    kxy, kx, ky = st.gaussian_kde(np.vstack([a, b])), st.gaussian_kde(a), st.gaussian_kde(b)
+    return float(np.mean(np.log(kxy(np.vstack([a, b])) / (kx(a) * ky(b)))))
+
+
+def test_mi_kde_equals_library_kde(orc):
+    """The oracle's MI is the resubstitution estimate built from scipy's Gaussian KDE
+    (Scott's rule, full joint covariance), for linear, monotone, periodic and independent
+    relations and heavy-tailed inputs."""
+    r = np.random.default_rng(50)
+    N = 400
+    x = r.normal(size=N)
+    y = np.sin(2 * x) + 0.3 * r.normal(size=N)
+    X = np.column_stack([x, np.exp(x), r.standard_t(3, size=N), x ** 2, r.uniform(size=N)])
+    mi = orc.mi_kde(X, y)
+    for i in range(X.shape[1]):
+        assert mi[i] == pytest.approx(_mi_scipy(X[:, i], y), rel=1e-10, abs=1e-12)
+
+
+def test_mi_kde_gaussian_closed_form_and_invariances(orc):
+    """Bivariate normal pairs: within 0.03 of MI = -log(1 - rho^2)/2 at N = 3000 and ordered
+    by rho; the estimate is symmetric in (x, y) and unchanged by an affine map of x."""
+    N = 3000
+    r = np.random.default_rng(51)
+    g = r.normal(size=(N, 3))
+    y = r.normal(size=N)
+    rhos = (0.5, 0.8, 0.95)
+    X = np.column_stack([rho * y + np.sqrt(1 - rho ** 2) * g[:, i] for i, rho in enumerate(rhos)])
+    mi = orc.mi_kde(X, y)
+    for m, rho in zip(mi, rhos):
+        assert abs(m - (-0.5 * np.log(1 - rho ** 2))) <= 0.03
+    assert mi[0] < mi[1] < mi[2]
+    assert orc.mi_kde(y[:, None], X[:, 1])[0] == pytest.approx(mi[1], rel=1e-12)
+    assert orc.mi_kde(3.0 * X[:, 1:2] - 7.0, y)[0] == pytest.approx(mi[1], rel=1e-9)
+
+
+def test_spearman_equals_library(orc):
+    """Spearman rank correlation with average ranks for ties equals scipy's."""
+    st = pytest.importorskip("scipy.stats")
+    r = np.random.default_rng(52)
+    N = 200
+    y = r.normal(size=N)
+    X = np.column_stack([np.exp(y) + 0.1 * r.normal(size=N), r.integers(0, 5, size=N).astype(float),
+                         -y ** 3, r.normal(size=N)])
+    rho = orc.spearman(X, np.round(y, 1))
+    for i in range(X.shape[1]):
+        assert rho[i] == pytest.approx(st.spearmanr(X[:, i], np.round(y, 1)).statistic, rel=1e-12, abs=1e-14)
+
+
+@pytest.mark.parametrize("d,q", [(10, 0.3), (1445, 0.01), (7, 1.0), (50, 0.5)])
+def test_prescreen_keep_is_top_quantile(orc, d, q):
+    """Kept primaries are those scoring strictly above numpy's (1 - q)-quantile."""
+    s = np.random.default_rng(d).uniform(size=d)
+    keep = orc.prescreen_keep(s, q)
+    if q >= 1.0:
+        assert keep.all()
+    else:
+        assert np.array_equal(keep, s > np.quantile(s, 1.0 - q))
+        assert 0 < keep.sum() <= int(np.ceil(q * d))
