@@ -78,6 +78,10 @@ enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1, SISSO_PREC_MIXED_BF16 = 2, SISS
  * features new at level l-1. */
 enum { SISSO_GRAMMAR_EQ2 = 0, SISSO_GRAMMAR_NEW_X_PREV = 1 };
 
+/* Pre-screening of the primaries (§3.1): mutual information with the target, estimated
+ * with Gaussian kernel density estimates, or the Spearman rank correlation. */
+enum { SISSO_PRESCREEN_NONE = 0, SISSO_PRESCREEN_MI = 1, SISSO_PRESCREEN_SPEARMAN = 2 };
+
 #define SISSO_MAX_RUNG 3
 #define SISSO_MAX_DIM 5
 #define SISSO_MAX_SIS 1024
@@ -103,6 +107,12 @@ typedef struct {
     double stop_rmse;       /* "low enough error" stop of the iteration (§2.3): after a step
                                whose RMSE is at or below this (in units of y), no further
                                step runs (0 = only the exact-fit stop, the default) */
+    int prescreen;          /* pre-screening of the primaries (§3.1; §3.3 initial_screening):
+                               SISSO_PRESCREEN_NONE (default), _MI or _SPEARMAN; the context
+                               is then built on the kept primaries only (renumbered x1..;
+                               sisso_get_primaries maps them back) */
+    double prescreen_quantile; /* fraction q in (0, 1] of the primaries kept: those scoring
+                               strictly above the (1 - q)-quantile of the scores */
     const int* units;       /* dimensional analysis (§2.1, closing paragraph; §3.3
                                dimensionality): d unit labels, HOST memory, copied by
                                sisso_create; primaries with equal labels share units, -1
@@ -162,6 +172,24 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
  * (RMSE <= 1e-10 std(y)) or S has fewer than t features.  Synchronous: returns when
  * the results are on the host. */
 sisso_status sisso_fit(sisso_ctx* ctx);
+
+/* Original indices (0-based) of the primaries the context was built on, in the order of
+ * its x1, x2, ...: all d without pre-screening.  idx: HOST, cap entries; *n = count. */
+sisso_status sisso_get_primaries(const sisso_ctx* ctx, int* idx, int cap, int* n);
+
+/* Pre-screening scores of the d primaries of X (N x d row-major FP64, host or device)
+ * against y (§3.1; §3.3): method SISSO_PRESCREEN_MI, MI(y; x_i) = mean over the samples of
+ * log(p(x, y) / (p(x) p(y))) with Gaussian kernel density estimates at the samples (Scott's
+ * rule: kernel covariance N^(-2/(k+4)) times the sample covariance of the k-dimensional
+ * variable, the full 2 x 2 covariance for the joint density; kernel values in FP32,
+ * sums in FP64), or SISSO_PRESCREEN_SPEARMAN, |Spearman rank correlation| (average ranks
+ * for ties).  keep: flags of the primaries in the top quantile q (strictly above the
+ * (1 - q)-quantile of the scores, linear interpolation); scores, keep (may be NULL) and
+ * n_keep (may be NULL) HOST.  Runs on the current device with its own buffers.  Errors:
+ * SISSO_ERR_ARG (sizes, method, q outside (0, 1], a constant primary or target for MI),
+ * SISSO_ERR_OOM, SISSO_ERR_CUDA. */
+sisso_status sisso_prescreen(const double* X, const double* y, int N, int d, int method, double quantile,
+                             double* scores, int* keep, int* n_keep);
 
 /* Number of descriptors produced by the last fit (<= max_dim). */
 sisso_status sisso_get_n_dims(const sisso_ctx* ctx, int* n_dims);

@@ -75,6 +75,11 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if (o.units)
         for (int j = 0; j < d; ++j)
             if (o.units[j] < -1 || o.units[j] >= d) { why = "unit labels must be in -1..d-1"; return SISSO_ERR_ARG; }
+    if (o.prescreen < SISSO_PRESCREEN_NONE || o.prescreen > SISSO_PRESCREEN_SPEARMAN) { why = "bad prescreen"; return SISSO_ERR_ARG; }
+    if (o.prescreen != SISSO_PRESCREEN_NONE && !(o.prescreen_quantile > 0.0 && o.prescreen_quantile <= 1.0)) {
+        why = "prescreen_quantile must be in (0, 1]";
+        return SISSO_ERR_ARG;
+    }
     return SISSO_OK;
 }
 
@@ -105,10 +110,43 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     std::string why;
     sisso_status st = validate(N, d, op_set, rung, sis_size, max_dim, o, why);
     if (st) return st;
+    if (o.prescreen != SISSO_PRESCREEN_NONE) {
+        // pre-screening (§3.1): score the primaries, keep the top quantile and build the
+        // context on those columns only (renumbered; their unit labels renumbered too)
+        if (cudaSetDevice(o.device) != cudaSuccess) return SISSO_ERR_CUDA;
+        std::vector<double> score((size_t)d);
+        std::vector<int> keep((size_t)d);
+        if ((st = prescreen_scores(X, y, N, d, o.prescreen, score.data(), why))) return st;
+        const int dk = prescreen_keep(score.data(), d, o.prescreen_quantile, keep.data());
+        if (dk < 1) return SISSO_ERR_NUMERIC;
+        std::vector<double> Xh((size_t)N * d), Xk((size_t)N * dk);
+        if (cudaMemcpy(Xh.data(), X, sizeof(double) * Xh.size(), cudaMemcpyDefault) != cudaSuccess) return SISSO_ERR_CUDA;
+        std::vector<int> idx, lab, relabel((size_t)d + 1, -2);
+        for (int j = 0; j < d; ++j)
+            if (keep[j]) idx.push_back(j);
+        for (int r = 0; r < N; ++r)
+            for (int q = 0; q < dk; ++q) Xk[(size_t)r * dk + q] = Xh[(size_t)r * d + idx[q]];
+        sisso_opts o2 = o;
+        o2.prescreen = SISSO_PRESCREEN_NONE;
+        if (o.units) {
+            int next = 0;
+            for (int q = 0; q < dk; ++q) {
+                const int u = o.units[idx[q]];
+                if (u < 0) { lab.push_back(-1); continue; }
+                if (relabel[u] == -2) relabel[u] = next++;
+                lab.push_back(relabel[u]);
+            }
+            o2.units = lab.data();
+        }
+        st = sisso_create(Xk.data(), y, N, dk, op_set, rung, sis_size, max_dim, &o2, out);
+        if (!st) (*out)->primaries = idx;
+        return st;
+    }
     sisso_ctx* c = new (std::nothrow) sisso_ctx();
     if (!c) return SISSO_ERR_OOM;
     c->N = N; c->d = d; c->rung = rung; c->k = sis_size; c->max_dim = max_dim; c->ops = op_set; c->opts = o;
     if (o.units) c->units.assign(o.units, o.units + d);
+    for (int j = 0; j < d; ++j) c->primaries.push_back(j);
     c->opts.units = nullptr;        // the labels live in the context
     if (!plan_space(d, op_set, rung, o.grammar, c->space)) { delete c; return SISSO_ERR_ARG; }
     c->n_feat = c->space.phi[rung];
@@ -288,6 +326,16 @@ sisso_status sisso_fit(sisso_ctx* c) {
     cudaEventDestroy(f0); cudaEventDestroy(f1);
     if (st) return st;
     c->fitted = true;
+    return SISSO_OK;
+}
+
+sisso_status sisso_get_primaries(const sisso_ctx* c, int* idx, int cap, int* n) {
+    if (!c || !n) return SISSO_ERR_ARG;
+    *n = (int)c->primaries.size();
+    if (idx) {
+        if (cap < *n) return SISSO_ERR_CAPACITY;
+        std::copy(c->primaries.begin(), c->primaries.end(), idx);
+    }
     return SISSO_OK;
 }
 

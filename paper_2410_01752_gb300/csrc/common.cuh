@@ -424,6 +424,7 @@ struct sisso_ctx {
     // dimensional analysis: unit labels of the primaries, the units rule of every id of
     // phi_{L-1} (recursive, one byte each) and of every id of phi_L (one bit each)
     std::vector<int> units;
+    std::vector<int> primaries;        // original indices of the primaries (pre-screening)
     unsigned char* unit_ok = nullptr;
     unsigned* unit_mask = nullptr;
     // tiled FP32 enumeration: padded FP32 Gram, moments and diagonal (rows x tile_ld), tile list
@@ -477,6 +478,9 @@ sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
 sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status ensure_tile_buffers(sisso_ctx* c, int n);
 sisso_status build_units(sisso_ctx* c);
+int prescreen_keep(const double* score, int d, double q, int* keep);
+sisso_status prescreen_scores(const double* X, const double* y, int N, int d, int method, double* scores,
+                              std::string& why);
 sisso_status winner_model_z(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,
                       int ld, double syy, int n, int D, const int64_t* gid_dev, int precision, Winner& w,

@@ -20,6 +20,7 @@ OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_EXP, OP_LOG, OP_SQRT, OP_SQ, OP_INV, OP_SIN, 
     1 << i for i in range(12))
 PREC_FP64, PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
+PRESCREEN_NONE, PRESCREEN_MI, PRESCREEN_SPEARMAN = 0, 1, 2
 MAX_DIM, MAX_SIS, MAX_RUNG = 5, 1024, 3
 STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
           -4: "SISSO_ERR_NUMERIC", -5: "SISSO_ERR_TIMEOUT", -6: "SISSO_ERR_STATE",
@@ -38,7 +39,7 @@ EXPORTS = [
     "sisso_fit_batch", "sisso_subspace_gram",
     "sisso_mlp_create", "sisso_mlp_destroy", "sisso_mlp_get_params", "sisso_mlp_set_params", "sisso_mlp_forward",
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
-    "sisso_set_proposal",
+    "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -56,7 +57,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("grammar", C.c_int), ("survivors", C.c_int),
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
-                ("units", C.c_void_p)]
+                ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("units", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -125,6 +126,9 @@ def load() -> C.CDLL:
     L.sisso_get_n_dims.argtypes = [vp, C.POINTER(C.c_int)]
     L.sisso_get_descriptor.argtypes = [vp, C.c_int, i64p, dp, dp, dp]
     L.sisso_get_sis.argtypes = [vp, C.c_int, i64p, C.c_int, C.POINTER(C.c_int)]
+    L.sisso_get_primaries.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+    L.sisso_prescreen.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_double, dp, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]
     L.sisso_feature_count.argtypes = [vp, i64p, i64p]
     L.sisso_feature_expr.argtypes = [vp, C.c_int64, C.c_char_p, C.c_size_t]
     L.sisso_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -212,6 +216,23 @@ def space_expr(d: int, op_set: int, rung: int, grammar: int, fid: int) -> str:
     return buf.value.decode()
 
 
+def prescreen(X, y, method: int, quantile: float = 1.0):
+    """(scores, keep flags) of the primaries (§3.1): method PRESCREEN_MI or PRESCREEN_SPEARMAN."""
+    L = load()
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    d = X.shape[1]
+    sc = np.zeros(d)
+    keep = np.zeros(d, dtype=np.int32)
+    n = C.c_int()
+    st = L.sisso_prescreen(C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), X.shape[0], d, int(method),
+                           float(quantile), sc.ctypes.data_as(C.POINTER(C.c_double)),
+                           keep.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n))
+    if st != 0:
+        raise SissoError(st, "sisso_prescreen")
+    return sc, keep.astype(bool)
+
+
 def gram_tc(Z, yc, sdy: float, kind: int = PREC_MIXED_BF16):
     """Z Z^T / N and Z yc / N on the tensor cores from 16-bit operands (sisso_gram_tc)."""
     Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -258,7 +279,7 @@ class Sisso:
     def __init__(self, X, y, op_set: int, rung: int, sis_size: int, max_dim: int,
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
-                 sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None):
+                 sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -269,6 +290,8 @@ class Sisso:
         o.precision, o.grammar, o.survivors = precision, grammar, survivors
         o.max_band, o.band_rel, o.device = max_band, band_rel, device
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
+        if prescreen is not None:    # (SISSO_PRESCREEN_MI or _SPEARMAN, quantile kept)
+            o.prescreen, o.prescreen_quantile = int(prescreen[0]), float(prescreen[1])
         ulab = None
         if units is not None:        # one label per primary (-1: dimensionless); copied by sisso_create
             ulab = np.ascontiguousarray(np.asarray(units, dtype=np.int32))
@@ -303,6 +326,16 @@ class Sisso:
                                                C.byref(rmse), C.byref(r2)), "get_descriptor")
             out.append(Descriptor([int(v) for v in ids], [float(v) for v in coef], rmse.value, r2.value))
         return out
+
+    def primaries(self) -> list[int]:
+        """Original indices of the primaries the context was built on (pre-screening)."""
+        L = load()
+        n = C.c_int()
+        self._check(L.sisso_get_primaries(self._ctx, None, 0, C.byref(n)), "get_primaries")
+        idx = np.zeros(max(n.value, 1), dtype=np.int32)
+        self._check(L.sisso_get_primaries(self._ctx, idx.ctypes.data_as(C.POINTER(C.c_int)), n.value, C.byref(n)),
+                    "get_primaries")
+        return [int(v) for v in idx[: n.value]]
 
     def sis(self, step: int) -> list[int]:
         buf = np.zeros(MAX_SIS, dtype=np.int64)

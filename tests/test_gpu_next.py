@@ -135,3 +135,50 @@ def test_units_fit(S, orc, prec, rung, g):
             assert a.ids == r.ids
             np.testing.assert_allclose(a.coef, r.coef, rtol=1e-6, atol=1e-9 * np.abs(y).max())
     assert all(sp.units_of(i)[0] for s in ref.sis for i in s)
+
+
+# ---- pre-screening of the primaries (§3.1; §3.3 initial_screening) ----------------------
+def _wide_problem(seed, N, d):
+    """A few informative primaries among many noise ones (molecular-descriptor-like width)."""
+    r = np.random.default_rng(seed)
+    X = r.uniform(0.5, 3.0, size=(N, d))
+    X[:, 3 % d] = np.round(X[:, 3 % d], 1)                                # ties for the ranks
+    y = np.log(X[:, 0]) * X[:, 1 % d] + 0.5 * X[:, 2 % d] ** 2 + 0.05 * r.normal(size=N)
+    return X, y
+
+
+@pytest.mark.parametrize("N,d", [(200, 30), (115, 300), (2000, 12), (333, 1)])
+def test_prescreen_scores(S, orc, N, d):
+    """MI within 5e-5 (FP32 kernel values, FP64 sums) and |Spearman| within 1e-12 of the
+    oracle; the kept primaries equal the oracle's wherever no score is within the tolerance
+    of the quantile cut."""
+    X, y = _wide_problem(60 + d, N, d)
+    mi_ref = orc.mi_kde(X, y)
+    sp_ref = np.abs(orc.spearman(X, y))
+    for method, ref, tol in ((S.PRESCREEN_MI, mi_ref, 5e-5), (S.PRESCREEN_SPEARMAN, sp_ref, 1e-12)):
+        q = 0.1 if d > 10 else 1.0
+        got, keep = S.prescreen(X, y, method, q)
+        assert np.abs(got - ref).max() <= tol
+        cut = np.quantile(ref, 1 - q) if q < 1 else -np.inf
+        if np.all(np.abs(ref - cut) > 2 * tol):
+            assert np.array_equal(keep, orc.prescreen_keep(ref, q))
+
+
+@pytest.mark.parametrize("method", ["mi", "spearman"])
+def test_prescreen_fit(S, orc, method):
+    """A context built with pre-screening keeps the oracle's primaries (in their order) and
+    its fit equals the oracle's fit on those columns."""
+    X, y = _wide_problem(70, 300, 16)
+    ref_scores = orc.mi_kde(X, y) if method == "mi" else np.abs(orc.spearman(X, y))
+    keep = orc.prescreen_keep(ref_scores, 0.25)
+    kept = list(np.flatnonzero(keep))
+    Xk = X[:, kept]
+    sp = orc.Space(len(kept), inputs.OPS9, 2)
+    ref = orc.fit(Xk, y, sp, 12, 2)
+    m = S.PRESCREEN_MI if method == "mi" else S.PRESCREEN_SPEARMAN
+    with S.Sisso(X, y, inputs.OPS9, 2, 12, 2, prescreen=(m, 0.25)) as c:
+        assert c.primaries() == kept
+        got = c.fit()
+        assert [g.ids for g in got] == [r.ids for r in ref.dims]
+        for g, r in zip(got, ref.dims):
+            np.testing.assert_allclose(g.coef, r.coef, rtol=1e-6, atol=1e-9 * np.abs(y).max())
