@@ -113,6 +113,9 @@ typedef struct {
                                sisso_get_primaries maps them back) */
     double prescreen_quantile; /* fraction q in (0, 1] of the primaries kept: those scoring
                                strictly above the (1 - q)-quantile of the scores */
+    int64_t wait_limit_ns;  /* batched form: the persistent kernel gives up (SISSO_ERR_TIMEOUT,
+                               every CTA returns) after this long without progress anywhere
+                               on its work queue (0 = 10 s, the default) */
     const int* units;       /* dimensional analysis (§2.1, closing paragraph; §3.3
                                dimensionality): d unit labels, HOST memory, copied by
                                sisso_create; primaries with equal labels share units, -1
@@ -194,9 +197,12 @@ sisso_status sisso_prescreen(const double* X, const double* y, int N, int d, int
 /* Number of descriptors produced by the last fit (<= max_dim). */
 sisso_status sisso_get_n_dims(const sisso_ctx* ctx, int* n_dims);
 
-/* Descriptor of dimension dim (1-based): ids[dim] ascending, coef[dim+1] with coef[0]
- * the intercept and coef[j+1] the coefficient of ids[j] in the original units,
- * rmse = sqrt(RSS/N), r2 = 1 - RSS/SST.  Any output pointer may be NULL. */
+/* Descriptor of dimension dim (1-based), the best dim-term model of §2.3 (Eq. 7: the
+ * least-squares coefficients c_t of the chosen columns, with the constant feature as the
+ * intercept) reported as §3.3's fit outputs (equation, RMSE, R^2): ids[dim] ascending,
+ * coef[dim+1] with coef[0] the intercept and coef[j+1] the coefficient of ids[j] in the
+ * original units, rmse = sqrt(RSS/N), r2 = 1 - RSS/SST.  Any output pointer may be NULL.
+ * Errors: SISSO_ERR_STATE before a fit, SISSO_ERR_ARG for dim outside 1..n_dims. */
 sisso_status sisso_get_descriptor(const sisso_ctx* ctx, int dim, int64_t* ids, double* coef,
                                   double* rmse, double* r2);
 
@@ -206,7 +212,8 @@ sisso_status sisso_get_sis(const sisso_ctx* ctx, int step, int64_t* ids, int cap
 /* |phi_rung| and |phi_l| for l = 0..rung (sizes[rung+1]; may be NULL). */
 sisso_status sisso_feature_count(const sisso_ctx* ctx, int64_t* n_features, int64_t* sizes);
 
-/* Expression of feature id, e.g. "(x1*(x2/x3))": primaries are x1..xd; binary
+/* Expression of feature id of the expanded space (§2.1, Eq. 2: the operator tree that
+ * generated it), e.g. "(x1*(x2/x3))": primaries are x1..xd; binary
  * "(a+b)", "(a-b)", "(a*b)", "(a/b)"; unary "exp(a)", "log(a)", "sqrt(a)", "(a)^2",
  * "(a)^-1", "sin(a)", "(a)^3", "exp(-a)". */
 sisso_status sisso_feature_expr(const sisso_ctx* ctx, int64_t id, char* buf, size_t len);
@@ -348,6 +355,11 @@ const char* sisso_batch_create_error(void);
 sisso_status sisso_batch_set_tune(sisso_batch* b, const sisso_batch_tune* tune);
 sisso_status sisso_batch_get_tune(const sisso_batch* b, sisso_batch_tune* tune);
 
+/* Replace the no-progress limit of the work-queue wait (ns; 0 = 10 s); the graphs are
+ * re-captured.  A run whose wait runs out returns SISSO_ERR_TIMEOUT after every CTA has
+ * returned; the next run starts from a clean state. */
+sisso_status sisso_batch_set_wait_limit(sisso_batch* b, int64_t ns);
+
 /* Autotuner: times candidate launch shapes on this batch (each a full run, reps times,
  * CUDA events) one parameter at a time and keeps the fastest.  cache_path (may be NULL):
  * a text file of earlier choices keyed by the batch's shape signature; a hit skips the
@@ -439,6 +451,14 @@ sisso_status sisso_prefix_features(const double* G, const double* b, double syy,
  * extending it with higher positions (exhaustive; +inf when it has none).  n in 5..1400.
  * out HOST. */
 sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, int N, int n, float* out);
+
+/* Training examples of every 3-prefix (same order as above), computed on the device:
+ * inputs (C(n,3) x SISSO_MLP_IN), labels (as sisso_prefix_labels) and the network's
+ * training target, log10(max(label, 1e-12)) minus the base score log10(RSS/SST) of the
+ * prefix's greedy completion (NaN for a prefix without extensions).  n in 5..1400; all
+ * outputs HOST. */
+sisso_status sisso_prefix_training(const double* G, const double* b, double syy, int N, int n, float* inputs,
+                                   float* labels, float* targets);
 
 /* The learned l0 search at D = 5 on the context's device: network scores of every 3-prefix,
  * prefixes best first up to frac x C(n,5) subsets, their extensions solved exactly (same

@@ -48,7 +48,7 @@ constexpr int kInitIds = 32;                     // ids per LEVEL unit
 constexpr int kLowIds = kBT;                     // lower-level ids per SCORE unit
 constexpr int kMaxSub = 1024;                    // subspace size cap (max_dim * k)
 constexpr int kZRaw = 512;                       // window entries whose FP64 values are kept
-constexpr unsigned long long kIdleNs = 10000000000ull;  // 10 s with no progress anywhere: give up
+constexpr unsigned long long kIdleNs = 10000000000ull;  // default: 10 s with no progress anywhere, give up
 constexpr unsigned long long kExit = ~0ull;
 
 enum : int { WK_NONE = 0, WK_START, WK_LEVEL, WK_SCORE, WK_GRAM, WK_BOUND, WK_BAND, WK_OPSUM = 11 };
@@ -164,6 +164,7 @@ struct BatchArgs {
     int gram_rows;              // new subspace rows per GRAM item
     int win0;                   // first screening window
     int band_cap;
+    unsigned long long idle_ns; // no progress anywhere for this long: give up (error word)
 };
 
 // shared memory of one CTA: one layout per stage
@@ -222,7 +223,7 @@ __device__ unsigned long long acquire(const BatchArgs& B) {
                 while (true) {
                     const unsigned long long v = *slot;
                     if (v) { __threadfence(); return v; }
-                    if (*(volatile int*)(B.ctr + 4) || gtimer() - w0 > kIdleNs) { atomicOr(B.ctr + 4, 1); return kExit; }
+                    if (*(volatile int*)(B.ctr + 4) || gtimer() - w0 > B.idle_ns) { atomicOr(B.ctr + 4, 1); return kExit; }
                 }
             }
             continue;
@@ -232,7 +233,7 @@ __device__ unsigned long long acquire(const BatchArgs& B) {
             if (c < B.n_tasks) return item_word(WK_START, 0, B.order[c], 0);
         }
         if (*(volatile int*)(B.ctr + 3) >= B.n_tasks || *(volatile int*)(B.ctr + 4)) return kExit;
-        if (gtimer() - since > kIdleNs) { atomicOr(B.ctr + 4, 2); return kExit; }
+        if (gtimer() - since > B.idle_ns) { atomicOr(B.ctr + 4, 2); return kExit; }
         __nanosleep(ns);
         if (ns < 2048) ns <<= 1;
     }
@@ -1165,6 +1166,7 @@ __global__ void __launch_bounds__(kBT, MINB) k_batch(BatchArgs B) {
 
 struct sisso_batch {
     int n_tasks = 0, rung = 0, k = 0, max_dim = 0, grammar = 0;
+    unsigned long long idle_ns = 0;     // work-queue no-progress limit (0: the default)
     uint32_t ops = 0;
     int device = 0, sms = 0;
     cudaStream_t stream = nullptr;
@@ -1311,6 +1313,7 @@ sisso_status capture(sisso_batch* b, bool copies, cudaGraphExec_t* out) {
     A.k = b->k; A.max_dim = b->max_dim;
     A.score_units = b->tune.score_units; A.enum_items = b->tune.enum_items; A.gram_rows = b->tune.gram_rows;
     A.win0 = b->tune.window; A.band_cap = b->band_cap;
+    A.idle_ns = b->idle_ns > 0 ? b->idle_ns : kIdleNs;
     if (b->tune.ctas_per_sm == 1) k_batch<1><<<grid, kBT, kBatchSmem, b->stream>>>(A);
     else k_batch<2><<<grid, kBT, kBatchSmem, b->stream>>>(A);
     cudaMemcpyAsync(b->ctr_host, b->ctr, sizeof(int) * 8, cudaMemcpyDeviceToHost, b->stream);
@@ -1378,6 +1381,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
         return SISSO_ERR_ARG;
     }
     if (o.precision != SISSO_PREC_FP32) { set_err("the batched form computes in FP32 (SISSO_PREC_FP32)"); return SISSO_ERR_ARG; }
+    if (o.wait_limit_ns < 0) { set_err("wait_limit_ns must be >= 0"); return SISSO_ERR_ARG; }
     if (o.sis_threshold != 0.0 || o.stop_rmse != 0.0 || o.units) {
         set_err("the batched form screens the top sis_size without units and stops at exact fits (sis_threshold = stop_rmse = 0, units = NULL)");
         return SISSO_ERR_ARG;
@@ -1387,6 +1391,7 @@ sisso_status sisso_batch_create(const sisso_task* tasks, int n_tasks, uint32_t o
     b->n_tasks = n_tasks; b->rung = rung; b->k = sis_size; b->max_dim = max_dim; b->grammar = o.grammar;
     b->ops = op_set; b->device = o.device;
     b->band_cap = o.max_band > 0 ? (int)std::min<int64_t>(o.max_band, 1 << 24) : 16384;
+    b->idle_ns = o.wait_limit_ns > 0 ? (unsigned long long)o.wait_limit_ns : 0;
     b->tune.score_units = 2; b->tune.enum_items = 32; b->tune.gram_rows = 2; b->tune.ctas_per_sm = 2;
     b->tune.window = std::max(256, 4 * sis_size);
     auto bail = [&](sisso_status st, const std::string& m) {
@@ -1628,6 +1633,13 @@ sisso_status sisso_batch_set_tune(sisso_batch* b, const sisso_batch_tune* tune) 
     if (t.score_units < 1 || t.enum_items < 8 || t.gram_rows < 1) return bfail(b, SISSO_ERR_ARG, "work items below the queue's sizing");
     cudaSetDevice(b->device);
     b->tune = t;
+    return rebuild(b);
+}
+
+sisso_status sisso_batch_set_wait_limit(sisso_batch* b, int64_t ns) {
+    if (!b || ns < 0) return SISSO_ERR_ARG;
+    cudaSetDevice(b->device);
+    b->idle_ns = (unsigned long long)ns;
     return rebuild(b);
 }
 

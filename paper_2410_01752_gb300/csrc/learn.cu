@@ -880,9 +880,30 @@ sisso_status sisso_prefix_features(const double* G, const double* b, double syy,
     return st;
 }
 
-sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, int N, int n, float* out) {
-    // the enumeration keeps 5 n FP32 values per warp in shared memory
-    if (!G || !b || !out || n < 5 || n > 1400 || N < 1 || !(syy > 0.0)) return SISSO_ERR_ARG;
+}  // extern "C"
+
+namespace sg {
+namespace {
+// labels of every 3-prefix from the enumeration's ordered keys: the lowest RSS / SST of its
+// extensions (+inf: none); with base (the greedy completion's log10 RSS/SST) also the
+// training target log10(max(label, 1e-12)) - base (NaN for a prefix without extensions)
+__global__ void k_prefix_targets(const unsigned* __restrict__ keys, int64_t np, double sst,
+                                 const float* __restrict__ base, float* __restrict__ label,
+                                 float* __restrict__ target) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < np; r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned k = keys[r];
+        const unsigned u = (k >> 31) ? (k & 0x7FFFFFFFu) : ~k;
+        const float lab = k == 0xFFFFFFFFu ? INFINITY : (float)((double)__uint_as_float(u) / sst);
+        label[r] = lab;
+        if (target) target[r] = isinf(lab) ? NAN : log10f(fmaxf(lab, 1e-12f)) - base[r];
+    }
+}
+}  // namespace
+
+// labels (and, with base_dev, training targets) of every 3-prefix on the current device;
+// outputs HOST
+static sisso_status prefix_labels_dev(const double* G, const double* b, double syy, int N, int n,
+                                      const float* base_dev, float* labels, float* targets) {
     const int64_t np = (int64_t)n * (n - 1) * (n - 2) / 6;
     std::vector<float> G32((size_t)n * n), b32(n);
     std::vector<double> hG((size_t)n * n), hb(n);
@@ -890,12 +911,14 @@ sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, i
     cudaMemcpy(hb.data(), b, sizeof(double) * n, cudaMemcpyDefault);
     for (size_t i = 0; i < hG.size(); ++i) G32[i] = (float)hG[i];
     for (int i = 0; i < n; ++i) b32[i] = (float)hb[i];
-    float *dG = nullptr, *db = nullptr;
+    float *dG = nullptr, *db = nullptr, *dl = nullptr, *dt = nullptr;
     unsigned* lab = nullptr;
     int* ctr = nullptr;
     sisso_status st = SISSO_OK;
     if (cudaMalloc((void**)&dG, sizeof(float) * n * n) != cudaSuccess || cudaMalloc((void**)&db, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc((void**)&lab, sizeof(unsigned) * np) != cudaSuccess || cudaMalloc((void**)&ctr, sizeof(int)) != cudaSuccess)
+        cudaMalloc((void**)&lab, sizeof(unsigned) * np) != cudaSuccess || cudaMalloc((void**)&ctr, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&dl, sizeof(float) * np) != cudaSuccess ||
+        (targets && cudaMalloc((void**)&dt, sizeof(float) * np) != cudaSuccess))
         st = SISSO_ERR_OOM;
     if (!st) {
         cudaMemcpy(dG, G32.data(), sizeof(float) * n * n, cudaMemcpyHostToDevice);
@@ -913,21 +936,52 @@ sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, i
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_prefix_labels<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_prefix_labels<0><<<sms * 2, kWarps * 32, smem>>>(A, lab);
-        std::vector<unsigned> h(np);
-        if (cudaMemcpy(h.data(), lab, sizeof(unsigned) * np, cudaMemcpyDeviceToHost) != cudaSuccess) st = SISSO_ERR_CUDA;
-        // prefixes of [0, n-2) only have extensions; the rest have none (+inf)
-        for (int64_t r = 0; r < np && !st; ++r) {
-            const unsigned k = h[r];
-            const unsigned u = (k >> 31) ? (k & 0x7FFFFFFFu) : ~k;
-            float f;
-            std::memcpy(&f, &u, sizeof f);
-            out[r] = k == 0xFFFFFFFFu ? INFINITY : (float)(f / (syy * N));
-        }
+        // prefixes of [0, n-2) only have extensions; the rest keep the +inf key
+        k_prefix_targets<<<(unsigned)std::min<int64_t>((np + 255) / 256, 4096), 256>>>(lab, np, syy * N, base_dev, dl,
+                                                                                       targets ? dt : nullptr);
+        if (cudaMemcpy(labels, dl, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess) st = SISSO_ERR_CUDA;
+        if (!st && targets && cudaMemcpy(targets, dt, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = SISSO_ERR_CUDA;
     }
     cudaGetLastError();
-    cudaFree(dG); cudaFree(db); cudaFree(lab); cudaFree(ctr);
+    cudaFree(dG); cudaFree(db); cudaFree(lab); cudaFree(ctr); cudaFree(dl); cudaFree(dt);
     return st;
 }
+
+}  // namespace sg
+
+extern "C" {
+
+sisso_status sisso_prefix_labels(const double* G, const double* b, double syy, int N, int n, float* out) {
+    // the enumeration keeps 5 n FP32 values per warp in shared memory
+    if (!G || !b || !out || n < 5 || n > 1400 || N < 1 || !(syy > 0.0)) return SISSO_ERR_ARG;
+    return sg::prefix_labels_dev(G, b, syy, N, n, nullptr, out, nullptr);
+}
+
+sisso_status sisso_prefix_training(const double* G, const double* b, double syy, int N, int n, float* inputs,
+                                   float* labels, float* targets) {
+    if (!G || !b || !inputs || !labels || !targets || n < 5 || n > 1400 || N < 1 || !(syy > 0.0))
+        return SISSO_ERR_ARG;
+    const int64_t np = (int64_t)n * (n - 1) * (n - 2) / 6;
+    double *dG = nullptr, *db = nullptr;
+    float *dX = nullptr, *dB = nullptr;
+    sisso_status st = SISSO_OK;
+    if (cudaMalloc((void**)&dG, sizeof(double) * n * n) != cudaSuccess || cudaMalloc((void**)&db, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc((void**)&dX, sizeof(float) * np * kIn) != cudaSuccess || cudaMalloc((void**)&dB, sizeof(float) * np) != cudaSuccess)
+        st = SISSO_ERR_OOM;
+    if (!st) {
+        cudaMemcpy(dG, G, sizeof(double) * n * n, cudaMemcpyDefault);
+        cudaMemcpy(db, b, sizeof(double) * n, cudaMemcpyDefault);
+        k_prefix_features<<<(unsigned)std::min<int64_t>((np + 255) / 256, 65535), 256>>>(dG, db, 1.0 / std::sqrt(syy), n,
+                                                                                          np, dX, nullptr, dB);
+        if (cudaMemcpy(inputs, dX, sizeof(float) * np * kIn, cudaMemcpyDeviceToHost) != cudaSuccess) st = SISSO_ERR_CUDA;
+        if (!st) st = sg::prefix_labels_dev(G, b, syy, N, n, dB, labels, targets);
+    }
+    cudaGetLastError();
+    cudaFree(dG); cudaFree(db); cudaFree(dX); cudaFree(dB);
+    return st;
+}
+
 
 }  // extern "C"
 

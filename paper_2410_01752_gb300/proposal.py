@@ -14,7 +14,7 @@ import time
 import numpy as np
 
 from . import inputs
-from .sisso import MLP, PREC_FP32, Sisso, prefix_features, prefix_labels
+from .sisso import MLP, PREC_FP32, Sisso, prefix_training
 
 
 def problem_gram(P, k: int):
@@ -36,8 +36,7 @@ def training_set(n_problems: int, k: int = 60, per_problem: int = 1024, top: int
         G, b, syy, N, ids = problem_gram(P, k)
         if len(ids) < 5:
             continue
-        X, _, base = prefix_features(G, b, syy)
-        lab = prefix_labels(G, b, syy, N)
+        X, lab, tgt = prefix_training(G, b, syy, N)
         ok = np.flatnonzero(np.isfinite(lab))
         if ok.size == 0:
             continue
@@ -45,7 +44,7 @@ def training_set(n_problems: int, k: int = 60, per_problem: int = 1024, top: int
         rest = rng.choice(ok, size=min(per_problem, ok.size), replace=False)
         sel = np.unique(np.concatenate([best, rest]))
         Xs.append(X[sel])
-        ts.append((np.log10(np.maximum(lab[sel], 1e-12)) - base[sel]).astype(np.float32))
+        ts.append(tgt[sel])
     return np.concatenate(Xs), np.concatenate(ts)
 
 

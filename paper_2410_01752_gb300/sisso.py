@@ -39,7 +39,8 @@ EXPORTS = [
     "sisso_fit_batch", "sisso_subspace_gram",
     "sisso_mlp_create", "sisso_mlp_destroy", "sisso_mlp_get_params", "sisso_mlp_set_params", "sisso_mlp_forward",
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
-    "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen",
+    "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen", "sisso_prefix_training",
+    "sisso_batch_set_wait_limit",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -57,7 +58,8 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("grammar", C.c_int), ("survivors", C.c_int),
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
-                ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("units", C.c_void_p)]
+                ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("wait_limit_ns", C.c_int64),
+                ("units", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -175,6 +177,8 @@ def load() -> C.CDLL:
                                   C.POINTER(C.c_float)]
     L.sisso_prefix_features.argtypes = [vp, vp, C.c_double, C.c_int, vp, vp, vp]
     L.sisso_prefix_labels.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp]
+    L.sisso_prefix_training.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp, vp, vp]
+    L.sisso_batch_set_wait_limit.argtypes = [vp, C.c_int64]
     L.sisso_l0_learned.argtypes = [vp, vp, vp, C.c_double, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_int), dp,
                                    i64p, i64p]
     L.sisso_set_proposal.argtypes = [vp, vp, C.c_double]
@@ -509,6 +513,10 @@ class Batch:
         self._check(load().sisso_batch_set_tune(self._b, C.byref(t)), "batch_set_tune")
         return self.get_tune()
 
+    def set_wait_limit(self, ns: int):
+        """No-progress limit of the persistent kernel's work-queue wait (0: the default)."""
+        self._check(load().sisso_batch_set_wait_limit(self._b, int(ns)), "batch_set_wait_limit")
+
     def get_tune(self) -> dict:
         t = BatchTune()
         self._check(load().sisso_batch_get_tune(self._b, C.byref(t)), "batch_get_tune")
@@ -650,6 +658,24 @@ def prefix_features(G, b, syy: float):
     if st != 0:
         raise SissoError(st, "prefix_features")
     return X, P, base
+
+
+def prefix_training(G, b, syy: float, N: int):
+    """(inputs C(n,3) x 20, labels C(n,3), targets C(n,3)) of every 3-prefix, colex order: the
+    network's inputs, the lowest RSS/SST of the prefix's extensions and the training target
+    (its log10 minus the greedy completion's), all computed by the library."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = b.size
+    npre = n * (n - 1) * (n - 2) // 6
+    X = np.zeros((npre, MLP_IN), dtype=np.float32)
+    lab = np.zeros(npre, dtype=np.float32)
+    tgt = np.zeros(npre, dtype=np.float32)
+    st = load().sisso_prefix_training(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), int(N), n,
+                                      C.c_void_p(X.ctypes.data), C.c_void_p(lab.ctypes.data), C.c_void_p(tgt.ctypes.data))
+    if st != 0:
+        raise SissoError(st, "prefix_training")
+    return X, lab, tgt
 
 
 def prefix_labels(G, b, syy: float, N: int) -> np.ndarray:

@@ -202,3 +202,23 @@ def test_fit_batch_one_shot(S, orc):
     res = S.fit_batch([(P.X, P.y)], P.op_set, 2, 50, 3)
     ref = orc.fit(P.X, P.y, orc.Space(P.d, P.op_set, 2), 50, 3)
     _check(res[0], ref.dims, P.y)
+
+
+def test_wait_limit_runs_out_and_recovers(S):
+    """The persistent kernel's work-queue wait is bounded: with a 1 ns no-progress limit the
+    CTAs that find no work give up, the run returns SISSO_ERR_TIMEOUT once every CTA has
+    returned, and with the default limit restored the next run is clean and reaches the
+    oracle's stored descriptors."""
+    gold = [json.loads(l) for l in open(GOLDEN)]
+    ids = list(range(24))
+    probs = [inputs.workload5_task(p) for p in ids]
+    with S.Batch([(P.X, P.y) for P in probs], probs[0].op_set, 2, 50, 3) as b:
+        b.set_wait_limit(1)
+        with pytest.raises(S.SissoError) as e:
+            b.run()
+        assert e.value.status == -5
+        b.set_wait_limit(0)
+        b.run()
+        res = b.results()
+    for P, p, r in zip(probs, ids, res):
+        _check(r, gold[p]["dims"], P.y, f"task {p}")

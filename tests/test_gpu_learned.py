@@ -211,3 +211,19 @@ def test_training_gains_over_untrained_network(S):
     assert hits_t >= evaluated - 1
     trained.close()
     untrained.close()
+
+
+def test_prefix_training_targets(S):
+    """The library's training examples: inputs and labels equal those of the separate entry
+    points, and each target is log10(max(label, 1e-12)) minus the greedy completion's base
+    score (NaN where the prefix has no extension)."""
+    G, b, syy, N = _gram_case(7, 24)
+    X, lab, tgt = S.prefix_training(G, b, syy, N)
+    X2, _, base = S.prefix_features(G, b, syy)
+    lab2 = S.prefix_labels(G, b, syy, N)
+    assert np.array_equal(X, X2)
+    assert np.array_equal(lab, lab2)
+    fin = np.isfinite(lab)
+    assert fin.sum() > 0 and (~fin).sum() > 0
+    np.testing.assert_allclose(tgt[fin], np.log10(np.maximum(lab[fin], 1e-12)) - base[fin], rtol=1e-5, atol=1e-5)
+    assert np.all(np.isnan(tgt[~fin]))
