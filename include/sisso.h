@@ -153,6 +153,7 @@ typedef struct {
     double ms_l0_enum;           /* ... of ms_l0: the tiled FP32 enumeration kernel alone */
     int l0_enum_launches;        /* launches of the tiled FP32 enumeration kernel */
     int64_t l0_candidates;       /* subsets its filter sent to the exact FP32/FP64 test */
+    int64_t certified_prefixes;  /* learned D = 5 step: 3-prefixes its certificate left to enumerate */
 } sisso_stats;
 
 void sisso_default_opts(sisso_opts* opts);
@@ -469,9 +470,31 @@ sisso_status sisso_l0_learned(sisso_ctx* ctx, const double* G, const double* b, 
                               const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos, double* best_rss,
                               int64_t* examined, int64_t* n_prefixes);
 
-/* Make sisso_fit use the learned search for its D = 5 step (mlp NULL: exhaustive again).
- * The context does not own the network. */
+/* The learned search followed by its certificate, so that the result is the exhaustive
+ * search's: every 5-subset extending a 3-prefix P = {p0 < p1 < p2} with two higher features
+ * lies in the superset {p0, p1} U [p2, n) and has at least its RSS (least squares on a
+ * superset fits at least as well).  Those superset RSS values, for every prefix at once,
+ * come from one reversed-order FP64 Cholesky of G and running sums per pair {p0, p1}; a
+ * prefix whose bound exceeds the learned winner's FP64 RSS (plus the tie window, 1e-9 SST
+ * and 1e-7 relative) is skipped, and the others are enumerated exactly by the tiled FP32
+ * search with FP64 confirmation, started from the learned winner.  Suffix sets whose
+ * Cholesky pivot falls to 1e-6 or below are never pruned.  Outputs as sisso_l0_learned;
+ * *examined: the subsets of both searches; *prefixes_kept (may be NULL): the prefixes the
+ * certificate left to enumerate.  n in 5..1400. */
+sisso_status sisso_l0_learned_certified(sisso_ctx* ctx, const double* G, const double* b, double syy, int n,
+                                        const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos,
+                                        double* best_rss, int64_t* examined, int64_t* n_prefixes,
+                                        int64_t* prefixes_kept);
+
+/* Make sisso_fit use the learned search for its D = 5 step (mlp NULL: exhaustive again),
+ * with the certificate above, so that the fit's descriptors are those of the exhaustive
+ * search.  The context does not own the network. */
 sisso_status sisso_set_proposal(sisso_ctx* ctx, sisso_mlp* mlp, double frac);
+
+/* The same with the certificate on (certify != 0) or off: off, the D = 5 step returns the
+ * best of the proposed subsets only, which is the exhaustive search's winner when the
+ * proposal contains it (the recall the tests and the benchmark report). */
+sisso_status sisso_set_proposal_ex(sisso_ctx* ctx, sisso_mlp* mlp, double frac, int certify);
 
 /* ---- allocation-free l0 search --------------------------------------------------------
  *

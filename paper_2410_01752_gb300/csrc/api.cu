@@ -303,6 +303,16 @@ sisso_status sisso_fit(sisso_ctx* c) {
         else if (c->proposal && t == 5 && n >= 5 && n <= 1400) {
             st = l0_learned(c, c->proposal, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, c->S_dev,
                             c->prune_frac, w, &c->learned_prefixes);
+            if (!st && c->certify_proposal) {
+                // certificate: the prefixes the learned winner cannot rule out are enumerated
+                // exactly, so the step's winner is the exhaustive search's
+                Winner w2{};
+                int64_t kept = 0;
+                st = l0_certify(c, c->G64, c->b64, c->n_cap, c->syy, n, c->S_dev, w.rss_gram, w2, &kept);
+                if (!st) w = w2;
+                c->certified_prefixes = kept;
+                c->stats.certified_prefixes += kept;
+            }
             // the exhaustive search is the fallback when the proposed subsets are all singular
             if (st == SISSO_ERR_NUMERIC)
                 st = l0_solve(c, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, t, c->S_dev, prec, w);
@@ -514,16 +524,21 @@ sisso_status sisso_l0_search(sisso_ctx* c, const double* G, const double* b, dou
 
 }  // extern "C"
 
-extern "C" sisso_status sisso_set_proposal(sisso_ctx* c, sisso_mlp* mlp, double frac) {
+extern "C" sisso_status sisso_set_proposal_ex(sisso_ctx* c, sisso_mlp* mlp, double frac, int certify) {
     if (!c || (mlp && !(frac > 0.0 && frac <= 1.0))) return SISSO_ERR_ARG;
     c->proposal = mlp;
     if (mlp) c->prune_frac = frac;
+    c->certify_proposal = certify != 0;
     return SISSO_OK;
 }
 
-extern "C" sisso_status sisso_l0_learned(sisso_ctx* c, const double* G, const double* b, double syy, int n,
-                                         const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos,
-                                         double* best_rss, int64_t* examined, int64_t* n_prefixes) {
+extern "C" sisso_status sisso_set_proposal(sisso_ctx* c, sisso_mlp* mlp, double frac) {
+    return sisso_set_proposal_ex(c, mlp, frac, 1);
+}
+
+static sisso_status l0_learned_entry(sisso_ctx* c, const double* G, const double* b, double syy, int n,
+                                     const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos, double* best_rss,
+                                     int64_t* examined, int64_t* n_prefixes, bool certify, int64_t* kept) {
     using namespace sg;
     if (!c || !G || !b || !gid || !mlp || !best_pos || n < 5 || n > 1400 || !(frac > 0.0 && frac <= 1.0) ||
         !(syy > 0.0))
@@ -547,15 +562,35 @@ extern "C" sisso_status sisso_l0_learned(sisso_ctx* c, const double* G, const do
     Winner w{};
     int64_t sel = 0;
     st = l0_learned(c, mlp, dG, db, dG32, db32, n, syy, n, dgid, frac, w, &sel);
+    int64_t ex = w.examined;
+    if (!st && certify) {
+        Winner w2{};
+        st = l0_certify(c, dG, db, n, syy, n, dgid, w.rss_gram, w2, kept);
+        if (!st) { ex += w2.examined; w = w2; }
+    }
     if (!st) {
         std::copy(w.pos, w.pos + 5, best_pos);
         if (best_rss) *best_rss = w.rss_gram;
-        if (examined) *examined = w.examined;
+        if (examined) *examined = ex;
         if (n_prefixes) *n_prefixes = sel;
     }
     cudaStreamSynchronize(c->stream);
     cudaFree(dG); cudaFree(db); cudaFree(dG32); cudaFree(db32); cudaFree(dgid);
     return st;
+}
+
+extern "C" sisso_status sisso_l0_learned(sisso_ctx* c, const double* G, const double* b, double syy, int n,
+                                         const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos,
+                                         double* best_rss, int64_t* examined, int64_t* n_prefixes) {
+    return l0_learned_entry(c, G, b, syy, n, gid, mlp, frac, best_pos, best_rss, examined, n_prefixes, false, nullptr);
+}
+
+extern "C" sisso_status sisso_l0_learned_certified(sisso_ctx* c, const double* G, const double* b, double syy, int n,
+                                                   const int64_t* gid, sisso_mlp* mlp, double frac, int* best_pos,
+                                                   double* best_rss, int64_t* examined, int64_t* n_prefixes,
+                                                   int64_t* prefixes_kept) {
+    return l0_learned_entry(c, G, b, syy, n, gid, mlp, frac, best_pos, best_rss, examined, n_prefixes, true,
+                            prefixes_kept);
 }
 
 extern "C" sisso_status sisso_subspace_gram(sisso_ctx* c, const int64_t* ids, int n, double* G, double* b, double* syy) {

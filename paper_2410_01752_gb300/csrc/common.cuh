@@ -450,6 +450,8 @@ struct sisso_ctx {
     sisso_mlp* proposal = nullptr;
     double prune_frac = 0.01;
     int64_t learned_prefixes = 0;
+    int64_t certified_prefixes = 0;    // 3-prefixes the certificate left to enumerate
+    bool certify_proposal = true;      // the learned D = 5 step is followed by its certificate
 };
 
 namespace sg {
@@ -478,6 +480,8 @@ sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64);
 sisso_status l0_solve_mixed(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status ensure_tile_buffers(sisso_ctx* c, int n);
 sisso_status build_units(sisso_ctx* c);
+sisso_status l0_certify(sisso_ctx* c, const double* G, const double* b, int ld, double syy, int n,
+                        const int64_t* gid_dev, double bound0, Winner& w, int64_t* prefixes_kept);
 int prescreen_keep(const double* score, int d, double q, int* keep);
 sisso_status prescreen_scores(const double* X, const double* y, int N, int d, int method, double* scores,
                               std::string& why);

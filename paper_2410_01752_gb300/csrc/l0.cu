@@ -511,8 +511,13 @@ sisso_status ensure_tile_buffers(sisso_ctx* c, int n) {
 // Exhaustive FP32 l0 (D >= 2) by the single-pass tiled enumeration (l0_tile.cuh): padded
 // FP32 copies, a greedy FP64 bound, one enumeration launch, FP64 refit of the band and the
 // tie-broken winner.
+__global__ void k_set_bound(unsigned long long* key, double v) { *key = okey(v); }
+
+// prefix_mask (optional): only the prefixes whose bit is set are enumerated; bound0 >= 0:
+// the search starts from this FP64 RSS (an upper bound of the minimum) instead of the greedy one
 static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* b, int ld, double syy, int n, int D,
-                                   const int64_t* gid_dev, Winner& w) {
+                                   const int64_t* gid_dev, Winner& w, const unsigned* prefix_mask = nullptr,
+                                   double bound0 = -1.0) {
     sisso_status st;
     if ((st = ensure_tile_buffers(c, n))) return st;
     const int DP = D - 2;
@@ -551,7 +556,8 @@ static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* 
     const int64_t tot = (int64_t)n * ldp;
     k_pad_gram<<<std::max(1, (int)std::min<int64_t>(c->sms * 8, (tot + 255) / 256)), 256, 0, c->stream>>>(
         G, b, ld, n, ldp, c->tile_G, c->tile_b, c->tile_diag);
-    k_greedy_bound<<<1, 256, 0, c->stream>>>(G, b, ld, syy, c->N, n, D, ub_key);
+    if (bound0 >= 0.0) k_set_bound<<<1, 1, 0, c->stream>>>(ub_key, bound0);
+    else k_greedy_bound<<<1, 256, 0, c->stream>>>(G, b, ld, syy, c->N, n, D, ub_key);
     TileArgs A{};
     A.G = c->tile_G + kTC; A.b = c->tile_b; A.diag = c->tile_diag; A.ldp = ldp; A.n = n; A.N = c->N; A.D = D;
     A.syy = (float)syy; A.tau = kPivotMin32; A.sst = sst; A.sqrt_syy = std::sqrt(syy);
@@ -568,7 +574,7 @@ static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* 
     A.counter = c->work; A.ub_key = ub_key; A.tie64 = 2.0 * kRssTie * sst;
     A.G64 = G; A.b64 = b; A.ld64 = ld; A.syy64 = syy;
     A.band = c->band; A.band_count = c->band_count; A.band_cap = c->band_cap; A.band_r32 = nullptr;
-    A.examined = examined; A.candidates = cand;
+    A.examined = examined; A.candidates = cand; A.prefix_mask = prefix_mask;
     cudaEventRecord(e1, c->stream);
     const int grid = c->sms * 2;
 #define SG_TILE(DPV)                                                                                   \
@@ -614,6 +620,55 @@ static sisso_status l0_solve_tiled(sisso_ctx* c, const double* G, const double* 
     w.examined = (int64_t)ex[0];
     if (!w.found) return fail(c, SISSO_ERR_NUMERIC, "l0: every subset is singular");
     return SISSO_OK;
+}
+
+// Certificate of a D = 5 incumbent (FP64 RSS bound0, e.g. the learned search's winner):
+// every 3-prefix whose superset bound (l0_tile.cuh) exceeds bound0 + tie + margin cannot
+// extend to the minimum or a tie of it and is skipped; the other prefixes are enumerated
+// exactly by the tiled search started from bound0, whose winner is then the exhaustive
+// search's.  The bounds are FP64 (margin 1e-9 SST + 1e-7 relative); suffix sets whose
+// reversed Cholesky meets a pivot at or below 1e-6 are never pruned.
+sisso_status l0_certify(sisso_ctx* c, const double* G, const double* b, int ld, double syy, int n,
+                        const int64_t* gid_dev, double bound0, Winner& w, int64_t* prefixes_kept) {
+    if (n < 5 || n > 4095) return fail(c, SISSO_ERR_ARG, "certificate: n must be in 5..4095");
+    const int64_t np = (int64_t)n * (n - 1) * (n - 2) / 6;
+    const int64_t words = (np + 31) / 32;
+    double *L = nullptr, *wv = nullptr, *q = nullptr;
+    int* m_ok = nullptr;
+    unsigned* mask = nullptr;
+    unsigned long long* kept = nullptr;
+    sisso_status st = SISSO_OK;
+    auto ck = [&](cudaError_t e, const char* what) { if (!st && e != cudaSuccess) st = check_cuda(c, e, what); };
+    ck(cudaMallocAsync((void**)&L, sizeof(double) * (size_t)n * n, c->stream), "certificate: factor");
+    ck(cudaMallocAsync((void**)&wv, sizeof(double) * (size_t)n, c->stream), "certificate: w");
+    ck(cudaMallocAsync((void**)&q, sizeof(double) * (size_t)(n + 1), c->stream), "certificate: q");
+    ck(cudaMallocAsync((void**)&m_ok, sizeof(int), c->stream), "certificate: m");
+    ck(cudaMallocAsync((void**)&mask, sizeof(unsigned) * (size_t)words, c->stream), "certificate: mask");
+    ck(cudaMallocAsync((void**)&kept, sizeof(unsigned long long), c->stream), "certificate: count");
+    if (!st) {
+        const double sst = syy * c->N;
+        const double thr = bound0 + 2.0 * kRssTie * sst + 1e-9 * sst + 1e-7 * std::fabs(bound0);
+        cudaMemsetAsync(mask, 0, sizeof(unsigned) * (size_t)words, c->stream);
+        cudaMemsetAsync(kept, 0, sizeof(unsigned long long), c->stream);
+        k_rev_chol<<<1, 1024, 0, c->stream>>>(G, b, ld, n, 1e-6, L, wv, m_ok);
+        k_prefix_sq<<<1, 32, 0, c->stream>>>(wv, n, m_ok, q);
+        const int64_t npair = (int64_t)n * (n - 1) / 2;
+        k_superset_mask<<<(unsigned)((npair + 255) / 256), 256, 0, c->stream>>>(G, b, ld, n, c->N, syy, L, wv, q, m_ok,
+                                                                                  thr, mask, kept);
+        c->stats.launches += 3;
+        ck(cudaGetLastError(), "certificate");
+        unsigned long long h_kept = 0;
+        ck(cudaMemcpyAsync(&h_kept, kept, sizeof(h_kept), cudaMemcpyDeviceToHost, c->stream), "certificate: count");
+        ck(cudaStreamSynchronize(c->stream), "certificate");
+        if (!st) {
+            if (prefixes_kept) *prefixes_kept = (int64_t)h_kept;
+            st = l0_solve_tiled(c, G, b, ld, syy, n, 5, gid_dev, w, mask, bound0);
+        }
+    }
+    cudaFreeAsync(L, c->stream); cudaFreeAsync(wv, c->stream); cudaFreeAsync(q, c->stream);
+    cudaFreeAsync(m_ok, c->stream); cudaFreeAsync(mask, c->stream); cudaFreeAsync(kept, c->stream);
+    (void)np;
+    return st;
 }
 
 sisso_status l0_solve(sisso_ctx* c, const double* G, const double* b, const float* G32, const float* b32,

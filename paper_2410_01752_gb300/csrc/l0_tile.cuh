@@ -74,6 +74,8 @@ struct TileArgs {
     float* band_r32;
     unsigned long long* examined;
     unsigned long long* candidates;      // subsets sent to the exact test
+    const unsigned* prefix_mask;         // optional: one bit per (D-2)-prefix in colex order;
+                                         //   prefixes whose bit is clear are skipped
 };
 
 // a posteriori bound on |RSS_FP32 - RSS| (the same formula as the two-pass form)
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
         }
         const int a = A.tiles[lo].a, c = A.tiles[lo].c;
         const int64_t prank = item - A.tiles[lo].item0;
+        if (A.prefix_mask && !((A.prefix_mask[prank >> 5] >> (prank & 31)) & 1u)) continue;
 
         // column groups j (columns c + 32 j + lane) and rows of this unit
         int pm = -1;
@@ -495,6 +498,126 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
 __host__ __device__ constexpr size_t tile_smem_bytes(int DP) {
     return sizeof(float) * (size_t)kTW * (kTR * row_words(DP) + (DP + 2) * kTC + kTQ) + sizeof(PrefixSm) * kTW +
            sizeof(unsigned short) * (size_t)kTW * kTQ;
+}
+
+// ---------------------------------------------------------------------------------
+// certificate of a D = 5 incumbent by superset bounds
+// ---------------------------------------------------------------------------------
+// Every 5-subset extending the prefix P = {a < b < p2} with two features above p2 is a
+// subset of T(P) = {a, b} U [p2, n), so its RSS is at least RSS(T(P)): least squares on a
+// superset can only fit better.  With L the Cholesky factor of G in reversed feature order
+// (row r <-> feature n-1-r), the leading m x m block of L factors the suffix [n-m, n), and
+// row r of L (r >= m, first m entries) is L_m^-1 applied to the Gram column of feature
+// n-1-r: the projections a pair {a, b} needs.  So for every prefix
+//     RSS(T) = N (syy - |w_m|^2 - t^T S^-1 t),   m = n - p2,
+// with w = L^-1 b (reversed), S_uv = G_uv - sum_{j<m} L[r_u][j] L[r_v][j] and
+// t_u = b_u - sum_{j<m} L[r_u][j] w[j] (u, v in {a, b}) -- running sums over m.
+
+// reversed-order FP64 Cholesky of G (n x n, ld) and w = L^-1 b (reversed); *m_ok: the
+// number of leading columns with a pivot above tau (the suffixes that have a factor)
+__global__ void __launch_bounds__(1024) k_rev_chol(const double* __restrict__ G, const double* __restrict__ b,
+                                                  int ld, int n, double tau, double* __restrict__ L,
+                                                  double* __restrict__ w, int* __restrict__ m_ok) {
+    __shared__ double s_ljj, s_red[32];
+    __shared__ int s_stop;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) { s_stop = 0; *m_ok = n; }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const int oj = n - 1 - j;
+        // pivot: G_rev[j][j] - |L[j][0..j)|^2
+        double p = 0.0;
+        for (int k = threadIdx.x; k < j; k += blockDim.x) p += L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        p = l0_warp_sum(p);
+        if (lane == 0) s_red[wid] = p;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < nw; ++q) t += s_red[q];
+            const double dj = G[(size_t)oj * ld + oj] - t;
+            if (!(dj > tau)) { s_stop = 1; *m_ok = j; }
+            s_ljj = sqrt(dj > 0.0 ? dj : 1.0);
+            L[(size_t)j * n + j] = s_ljj;
+            // w[j] = (b_rev[j] - L[j][0..j) . w[0..j)) / L[j][j]
+            double v = b[oj];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)j * n + k] * w[k];
+            w[j] = v / s_ljj;
+        }
+        __syncthreads();
+        if (s_stop) return;
+        // rows i > j, one warp per row: L[i][j] = (G_rev[i][j] - L[i][0..j) . L[j][0..j)) / L[j][j]
+        for (int i = j + 1 + wid; i < n; i += nw) {
+            double v = 0.0;
+            for (int k = lane; k < j; k += 32) v += L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            v = l0_warp_sum(v);
+            if (lane == 0) L[(size_t)i * n + j] = (G[(size_t)(n - 1 - i) * ld + oj] - v) / s_ljj;
+        }
+        __syncthreads();
+    }
+}
+
+// one thread per pair a < b: the superset bound of every prefix {a, b, p2}, p2 = n-m for
+// m = 3 .. n-b-1; a prefix survives (bit set) unless the bound clears thr, or its suffix has
+// no factor (m > m_ok) or the 2 x 2 Schur complement is not positive
+__global__ void k_superset_mask(const double* __restrict__ G, const double* __restrict__ b, int ld, int n, int N,
+                                double syy, const double* __restrict__ L, const double* __restrict__ w,
+                                const double* __restrict__ q, const int* __restrict__ m_ok_p, double thr,
+                                unsigned* __restrict__ mask, unsigned long long* __restrict__ survivors) {
+    const int64_t pr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t npair = (int64_t)n * (n - 1) / 2;
+    if (pr >= npair) return;
+    // pair rank -> (a < b): b the largest with b (b-1) / 2 <= pr
+    int bb = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pr)) * 0.5);
+    while (bb > 1 && (int64_t)bb * (bb - 1) / 2 > pr) --bb;
+    while ((int64_t)(bb + 1) * bb / 2 <= pr) ++bb;
+    const int aa = (int)(pr - (int64_t)bb * (bb - 1) / 2);
+    if (bb > n - 3) return;
+    const int m_ok = *m_ok_p;
+    const int ra = n - 1 - aa, rb = n - 1 - bb;
+    const double* La = L + (size_t)ra * n;
+    const double* Lb = L + (size_t)rb * n;
+    double saa = 0.0, sab = 0.0, sbb = 0.0, ta = 0.0, tb = 0.0;
+    const double gaa = G[(size_t)aa * ld + aa], gab = G[(size_t)aa * ld + bb], gbb = G[(size_t)bb * ld + bb];
+    const double pre2 = (double)bb * (bb - 1) / 2 + aa;          // C(b, 2) + a
+    unsigned long long surv = 0;
+    for (int m = 1; m <= n - bb - 1; ++m) {
+        const int j = m - 1;
+        if (m <= m_ok) {
+            const double la = La[j], lb = Lb[j], wj = w[j];
+            saa += la * la; sab += la * lb; sbb += lb * lb; ta += la * wj; tb += lb * wj;
+        }
+        if (m < 3) continue;
+        const int p2 = n - m;
+        bool keep = true;
+        if (m <= m_ok) {
+            const double Saa = gaa - saa, Sab = gab - sab, Sbb = gbb - sbb;
+            const double Ta = b[aa] - ta, Tb = b[bb] - tb;
+            const double det = Saa * Sbb - Sab * Sab;
+            if (Saa > 0.0 && det > 1e-12 * Saa * Sbb) {
+                const double extra = (Sbb * Ta * Ta - 2.0 * Sab * Ta * Tb + Saa * Tb * Tb) / det;
+                const double lb_rss = (double)N * (syy - q[m] - extra);
+                keep = !(lb_rss > thr);
+            }
+        }
+        if (keep) {
+            const int64_t rank = (int64_t)p2 * (p2 - 1) * (p2 - 2) / 6 + (int64_t)pre2;
+            atomicOr(&mask[rank >> 5], 1u << (rank & 31));
+            ++surv;
+        }
+    }
+    if (surv) atomicAdd(survivors, surv);
+}
+
+// q[m] = |w[0..m)|^2, m = 0 .. n
+__global__ void k_prefix_sq(const double* __restrict__ w, int n, const int* __restrict__ m_ok, double* __restrict__ q) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        q[0] = 0.0;
+        for (int m = 1; m <= n; ++m) {
+            if (m <= *m_ok) s += w[m - 1] * w[m - 1];
+            q[m] = s;
+        }
+    }
 }
 
 // greedy forward selection in FP64: its D-subset's RSS is an upper bound of the minimum

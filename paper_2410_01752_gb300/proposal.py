@@ -90,12 +90,17 @@ def evaluate(net: MLP, problems, frac: float = 0.01, k: int = 60):
             rec["learned_s"] = time.perf_counter() - t0
             rec.update(n=len(S), examined_exhaustive=ex_ex, examined_learned=ex_l, prefixes=npre,
                        recall=sorted(pos_l) == sorted(pos_ex), rss_exhaustive=rss_ex, rss_learned=rss_l)
-            c.set_proposal(net, frac)
+            c.set_proposal(net, frac, certify=False)
             t0 = time.perf_counter()
             learned = c.fit()
             rec["fit_learned_s"] = time.perf_counter() - t0
             rec["fit_learned_ms_device"] = c.stats()["ms_fit"]
             rec["fit_learned_launches"] = c.stats()["launches"]
+            c.set_proposal(net, frac, certify=True)
+            certified = c.fit()
+            rec["fit_certified_ms_device"] = c.stats()["ms_fit"]
+            rec["certified_prefixes"] = c.stats()["certified_prefixes"]
+            rec["certified_ids"] = certified[4].ids
             c.set_proposal(None)
             rec["plain_ids"], rec["learned_ids"] = plain[4].ids, learned[4].ids
             rec["same_descriptor"] = learned[4].ids == plain[4].ids

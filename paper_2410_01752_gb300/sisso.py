@@ -40,7 +40,7 @@ EXPORTS = [
     "sisso_mlp_create", "sisso_mlp_destroy", "sisso_mlp_get_params", "sisso_mlp_set_params", "sisso_mlp_forward",
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
     "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen", "sisso_prefix_training",
-    "sisso_batch_set_wait_limit",
+    "sisso_batch_set_wait_limit", "sisso_l0_learned_certified", "sisso_set_proposal_ex",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -72,7 +72,7 @@ class Stats(C.Structure):
                 ("ms_walk", C.c_double), ("walk_visited", C.c_int64), ("walk_dup_checks", C.c_int64),
                 ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
                 ("ms_fit", C.c_double), ("ms_l0_enum", C.c_double), ("l0_enum_launches", C.c_int),
-                ("l0_candidates", C.c_int64)]
+                ("l0_candidates", C.c_int64), ("certified_prefixes", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -179,6 +179,9 @@ def load() -> C.CDLL:
     L.sisso_prefix_labels.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp]
     L.sisso_prefix_training.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, vp, vp, vp]
     L.sisso_batch_set_wait_limit.argtypes = [vp, C.c_int64]
+    L.sisso_set_proposal_ex.argtypes = [vp, vp, C.c_double, C.c_int]
+    L.sisso_l0_learned_certified.argtypes = [vp, vp, vp, C.c_double, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_int),
+                                             dp, i64p, i64p, i64p]
     L.sisso_l0_learned.argtypes = [vp, vp, vp, C.c_double, C.c_int, vp, vp, C.c_double, C.POINTER(C.c_int), dp,
                                    i64p, i64p]
     L.sisso_set_proposal.argtypes = [vp, vp, C.c_double]
@@ -428,10 +431,26 @@ class Sisso:
                                             C.byref(npre)), "l0_learned")
         return [int(p) for p in pos], rss.value, ex.value, npre.value
 
-    def set_proposal(self, mlp, frac: float = 0.01):
+    def l0_learned_certified(self, G, b, syy: float, gid, mlp: "MLP", frac: float):
+        """The learned D = 5 search and its certificate: the exhaustive search's winner.
+        Returns (positions, rss, subsets solved, prefixes proposed, prefixes the certificate kept)."""
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        gid = np.ascontiguousarray(gid, dtype=np.int64)
+        pos = np.zeros(5, dtype=np.int32)
+        rss, ex, npre, kept = C.c_double(), C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(load().sisso_l0_learned_certified(self._ctx, C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data),
+                                                      float(syy), b.size, C.c_void_p(gid.ctypes.data), mlp._m,
+                                                      float(frac), pos.ctypes.data_as(C.POINTER(C.c_int)),
+                                                      C.byref(rss), C.byref(ex), C.byref(npre), C.byref(kept)),
+                    "l0_learned_certified")
+        return [int(p) for p in pos], rss.value, ex.value, npre.value, kept.value
+
+    def set_proposal(self, mlp, frac: float = 0.01, certify: bool = True):
+        """Learned search at the fit's D = 5 step; certify: followed by its certificate (exact)."""
         self._proposal = mlp
-        self._check(load().sisso_set_proposal(self._ctx, mlp._m if mlp is not None else None, float(frac)),
-                    "set_proposal")
+        self._check(load().sisso_set_proposal_ex(self._ctx, mlp._m if mlp is not None else None, float(frac),
+                                                 int(bool(certify))), "set_proposal")
 
     def close(self):
         if self._ctx:

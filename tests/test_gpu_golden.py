@@ -83,3 +83,19 @@ def test_d5_fit_full_size(S):
         P = _problem(rec)
         with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=1, grammar=P.grammar) as c:
             _check(c, rec, P.y, 1e-6)
+
+
+def test_d5_learned_fit_full_size(S):
+    """The fit with the learned proposal at its D = 5 step (a network that returns the
+    greedy-completion base score, i.e. the proposal without training) and the certificate:
+    every stored held-out problem's descriptors equal the oracle's."""
+    recs = _golden("workload4")
+    net = S.MLP(0)
+    net.set_params(np.zeros(S.MLP_PARAMS, dtype=np.float32))
+    for rec in recs:
+        P = _problem(rec)
+        with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=1, grammar=P.grammar) as c:
+            c.set_proposal(net, 0.01)
+            _check(c, rec, P.y, 1e-6)
+            assert c.stats()["certified_prefixes"] > 0
+    net.close()
