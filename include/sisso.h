@@ -91,8 +91,8 @@ typedef struct {
                                selection and refits are always FP64 (default FP32) */
     int grammar;            /* SISSO_GRAMMAR_* (default EQ2) */
     int survivors;          /* FP32 screening window: candidates re-scored in FP64 per
-                               step (0 = max(4096, 32 k)); grown x4 automatically when
-                               it cannot prove the selection exact */
+                               step (0 = max(5 k, min(max(4096, 32 k), 2^26 / N))); grown
+                               x4 automatically when it cannot prove the selection exact */
     double band_rel;        /* l0: FP32 RSS band, relative to SST, refit in FP64
                                (0 = 1e-4) */
     int64_t max_band;       /* l0: capacity of the FP64 refit list (0 = 1<<22) */
@@ -125,6 +125,12 @@ typedef struct {
                                operators combine units.  A feature that breaks the rule, or
                                is built from one that does, is invalid (scores -1, never
                                selected); ids are those of the space without units. */
+    int screen_cores;       /* mixed forms: 0 (default) scores the top level's binary
+                               candidates from split 16-bit tensor-core products (§2.2 Eq. 5
+                               as a contraction; each key carries its error bound, see
+                               sisso_bilinear_tc), where the operand set fits (EQ2 grammar or
+                               rung <= 2, |phi_{L-1}| <= 4096); 1 keeps them on the FP32
+                               CUDA-core kernel */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */
@@ -154,6 +160,9 @@ typedef struct {
     int l0_enum_launches;        /* launches of the tiled FP32 enumeration kernel */
     int64_t l0_candidates;       /* subsets its filter sent to the exact FP32/FP64 test */
     int64_t certified_prefixes;  /* learned D = 5 step: 3-prefixes its certificate left to enumerate */
+    int screen_tc;               /* 1 if the top level's pairs were scored on the tensor cores */
+    int64_t tc_keys_raised;      /* ... keys raised to their error bound (bound above the FP32
+                                    screening margin, or the variance not resolved) */
 } sisso_stats;
 
 void sisso_default_opts(sisso_opts* opts);
@@ -266,7 +275,7 @@ sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, d
  * b = Z y~ / N (n), HOST; *syy (may be NULL) = y~^T y~ / N. */
 sisso_status sisso_subspace_gram(sisso_ctx* ctx, const int64_t* ids, int n, double* G, double* b, double* syy);
 
-/* Subspace Gram on the tcgen05 tensor cores (the mixed-precision forms' a4 step): with Z
+/* Subspace Gram on the tcgen05 tensor cores (the mixed-precision forms' Gram, §2.3 Eq. 7): with Z
  * n standardised rows of N samples (FP64, row-major) and yc the centred target with
  * population std sdy, returns G = Z Z^T / N (n x n) and b = Z yc / N (n), computed from
  * BF16 (kind = SISSO_PREC_MIXED_BF16) or FP16 (SISSO_PREC_MIXED_FP16) operands with FP32
@@ -274,6 +283,17 @@ sisso_status sisso_subspace_gram(sisso_ctx* ctx, const int64_t* ids, int n, doub
  * legacy default stream.  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT. */
 sisso_status sisso_gram_tc(const double* Z, const double* yc, double sdy, int n, int N, int kind, float* G,
                            float* b);
+
+/* Split-precision tensor-core product (the mixed forms' screening sums, §2.2 Eq. 5 written
+ * as a contraction over the samples): out[i][j] = sum_s L[i][s] R[j][s] for the m rows of L
+ * and n rows of R (N samples each, FP64, row-major, HOST; out m x n FP64 HOST).  Every row
+ * is scaled by a power of two and split into 16-bit parts (FP16: two, BF16: three); the
+ * part products of tcgen05.mma kind::f16 accumulate in FP32 over chunks of 1024 samples,
+ * the chunks in FP64.  |out - exact| stays within about 2^-21 of the Cauchy-Schwarz scale
+ * sqrt(sum L_i^2 sum R_j^2) (the screening bounds each key with 2^-17).  kind:
+ * SISSO_PREC_MIXED_BF16 or _FP16.  m, n <= 65536.  Current device, default stream.
+ * Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT (a bounded wait ran out). */
+sisso_status sisso_bilinear_tc(const double* L, const double* R, int m, int n, int N, int kind, double* out);
 
 /* ---- batched multi-task form ----------------------------------------------------------
  *

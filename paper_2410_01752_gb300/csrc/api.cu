@@ -54,6 +54,7 @@ void free_all(sisso_ctx* c) {
                     c->unit_ok, c->unit_mask};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    tc_screen_free(c);
     if (c->walk_h) cudaFreeHost(c->walk_h);
     if (c->win_h) cudaFreeHost(c->win_h);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -72,6 +73,7 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if ((int64_t)max_dim * k > (max_dim <= 4 ? 65535 : 4095)) { why = "subspace too large"; return SISSO_ERR_ARG; }
     if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
     if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
+    if (o.screen_cores != 0 && o.screen_cores != 1) { why = "screen_cores must be 0 or 1"; return SISSO_ERR_ARG; }
     if (o.units)
         for (int j = 0; j < d; ++j)
             if (o.units[j] < -1 || o.units[j] >= d) { why = "unit labels must be in -1..d-1"; return SISSO_ERR_ARG; }
@@ -246,6 +248,8 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     if (!st) st = build_units(c);
     if (!st) st = compute_subvalid(c);
     if (!st) st = fill_opcache(c);
+    const bool mixed_form = o.precision == SISSO_PREC_MIXED_BF16 || o.precision == SISSO_PREC_MIXED_FP16;
+    if (!st && mixed_form && !o.screen_cores && c->opval64 && tc_screen_possible(c)) st = tc_screen_alloc(c);
     if (!st) st = prepare_target(c, c->y64);
     cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);
     TargetStats ts{};
@@ -266,8 +270,8 @@ sisso_status sisso_fit(sisso_ctx* c) {
     cudaSetDevice(c->opts.device);
     const int prec = c->opts.precision;
     const bool mixed = prec == SISSO_PREC_MIXED_BF16 || prec == SISSO_PREC_MIXED_FP16;
-    const int screen_prec = mixed ? SISSO_PREC_FP32 : prec;
     c->stats = sisso_stats{};
+    c->tc_ready = false;
     c->S.clear(); c->n_sis.clear(); c->res_ids.clear(); c->res_coef.clear(); c->res_rmse.clear(); c->res_r2.clear();
     c->n_dims = 0;
     c->fitted = false;
@@ -278,7 +282,7 @@ sisso_status sisso_fit(sisso_ctx* c) {
     sisso_status st = SISSO_OK;
     for (int t = 1; t <= c->max_dim; ++t) {
         if ((st = prepare_target(c, target))) break;
-        if ((st = score_all(c, screen_prec))) break;
+        if ((st = score_all(c, prec))) break;
         std::vector<int64_t> acc;
         if ((st = sis_select(c, c->k, c->S.data(), (int)c->S.size(), acc))) break;
         const int n_old = (int)c->S.size();

@@ -452,6 +452,24 @@ struct sisso_ctx {
     int64_t learned_prefixes = 0;
     int64_t certified_prefixes = 0;    // 3-prefixes the certificate left to enumerate
     bool certify_proposal = true;      // the learned D = 5 step is followed by its certificate
+
+    // tensor-core screening of the top level's pairs (mixed forms): 16-bit parts of the
+    // operand rows, exponents, moments, chunk partials and the FP64 products
+    bool tc_on = false, tc_ready = false;
+    int tc_P = 0, tc_Pp = 0, tc_Kpad = 0;
+    size_t tc_part_cap = 0;
+    void* tc_L = nullptr;
+    void* tc_R = nullptr;
+    int* tc_eL = nullptr;
+    int* tc_eR = nullptr;
+    double* tc_mom = nullptr;
+    double* tc_tgt = nullptr;
+    float* tc_part = nullptr;
+    double* tc_C1 = nullptr;
+    double* tc_C2 = nullptr;
+    double* tc_recip = nullptr;
+    int* tc_err = nullptr;
+    unsigned long long* tc_raised = nullptr;
 };
 
 namespace sg {
@@ -495,6 +513,13 @@ sisso_status winner_model(sisso_ctx* c, int n, int D, Winner& w);
 sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const double* b, const float* G32,
                         const float* b32, int ld, double syy, int n, const int64_t* gid_dev, double frac, Winner& w,
                         int64_t* n_selected);
+
+// tensor-core screening of the top level's pairs (screen_tc.cu)
+bool tc_screen_possible(const sisso_ctx* c);
+sisso_status tc_screen_alloc(sisso_ctx* c);
+sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]);
+sisso_status tc_screen_status(sisso_ctx* c);
+void tc_screen_free(sisso_ctx* c);
 
 // tensor-core Gram (gram_tc.cu)
 sisso_status gram_tc(sisso_ctx* c, const double* Z, const double* yc, double sdy, int n, int N, int kind,

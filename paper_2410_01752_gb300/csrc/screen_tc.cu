@@ -1,0 +1,760 @@
+// screen_tc.cu — SIS scores of the top level's binary candidates from bilinear sums on the
+// tcgen05 tensor cores (the mixed-precision forms; §2.2 Eq. 5 as a contraction).
+//
+// A candidate f = x (op) z over operands of phi_{L-1} scores |sum (f - fbar) r| /
+// sqrt(sum (f - fbar)^2 * sum r^2) (r: the centred target).  With each operand centred in
+// FP64 (x' = x - xbar) and g = z for *, g = 1/z for x/z, the candidate's two sums are
+//   U = xbar sum g'r + gbar sum x'r + P5 - P1 sum(r) / N
+//   V = xbar^2 sum g'^2 + gbar^2 sum x'^2 + P2 - P1^2 / N + 2 xbar gbar P1 + 2 xbar P3 + 2 gbar P4
+// with P1 = sum x'g', P2 = sum x'^2 g'^2, P3 = sum x'g'^2, P4 = sum x'^2 g', P5 = sum (x'r) g',
+// and for x +/- z: U = sum x'r +/- sum z'r, V = sum x'^2 + sum z'^2 +/- 2 P1.  The per-operand
+// sums are FP64; P1..P4 do not depend on the target (one product per fit), P5 does (one
+// product per SIS step).  The products run as C = L R^T over the samples:
+//   L rows [x' | x'^2 | x'r],  R rows [z' | (1/z)' | z'^2 | ((1/z)')^2]   (blocks of Pp rows)
+// each row scaled by a power of two and split into 16-bit parts (FP16: hi + lo, BF16:
+// hi + mid + lo); the part products kept (FP16: hh, hl, lh; BF16: hh, hm, mh, hl, lh, mm)
+// give every sum to about 2^-21 of its Cauchy-Schwarz scale.  A CTA computes one 128 x 128
+// tile over a chunk of 1024 samples (FP32 accumulation in TMEM) and stores it; chunks are
+// added in FP64.  Each candidate's score carries an error bound from eps_tc times the
+// Cauchy-Schwarz scale of every product it uses; where the bound exceeds the FP32 screening
+// margin the stored key is raised by the excess, so that key + margin bounds the exact
+// score and the FP64 re-score of the selection window stays exact.
+#include "tc_device.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace sg {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;            // output tile; samples per stage
+constexpr int STAGES = 4;
+constexpr int kThreads = 128;
+constexpr uint32_t kTileBytes = BM * BK * 2;
+constexpr int kAcc = 4;                                // TMEM accumulators per tile, 128 columns each
+constexpr uint32_t kTmemCols = 128 * kAcc;
+constexpr int kAccBlocks = 4;                          // 64-sample blocks summed in one accumulator
+constexpr int kChunkBlocks = kAcc * kAccBlocks;        // 64-sample blocks per chunk (1024 samples)
+constexpr double kTcEps = 1.0 / (1 << 17);            // bound on |error| / Cauchy-Schwarz scale
+constexpr int kMaxParts = 6;
+
+struct Smem {
+    uint8_t a[STAGES][kTileBytes];
+    uint8_t b[STAGES][kTileBytes];
+    uint64_t full[STAGES], empty[STAGES], done;
+    uint32_t tmem_base;
+};
+
+struct BilinArgs {
+    int tiles_m, tiles_n;        // output tiles of this product
+    int chunks, kb_per_chunk;    // sample chunks (in 64-sample blocks) and their length
+    int nkb;                     // 64-sample blocks in all
+    int l_row0, r_row0;          // first row of the product within a part block
+    int l_part_rows, r_part_rows;// rows of one part block (the stride between parts)
+    int npairs;                  // part products summed
+    int lp[kMaxParts], rp[kMaxParts];
+    float* C;                    // C[chunk * chunk_stride + row * ldc + col]
+    int ldc;
+    size_t chunk_stride;
+    int* err;
+    uint32_t idesc;
+};
+
+// One 128 x 128 tile of one sample chunk: TMA producer (warp 0), MMA issuer (warp 1), all
+// four warps store the tile (warp w: rows 32w..32w+31).  The tensor cores' FP32 accumulation
+// loses up to about one unit in the last place per MMA, so every run of kAccBlocks blocks
+// goes to its own TMEM accumulator and the accumulators are added in FP64 before the store.
+// Bounded waits; on timeout the error flag is raised and nothing is stored.
+__global__ void __launch_bounds__(kThreads, 1) k_bilin_tc(const __grid_constant__ CUtensorMap mapL,
+                                                          const __grid_constant__ CUtensorMap mapR, BilinArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_chunk = A.tiles_m * A.tiles_n;
+    const int chunk = blockIdx.x / per_chunk, t = blockIdx.x % per_chunk;
+    const int tm = t / A.tiles_n, tn = t % A.tiles_n;
+    const int kb_lo = chunk * A.kb_per_chunk, kb_hi = min(A.nkb, kb_lo + A.kb_per_chunk);
+    const int nk = max(0, kb_hi - kb_lo) * A.npairs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
+        mbar_init(&S.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem_base;
+    __shared__ int failed;
+    if (threadIdx.x == 0) failed = 0;
+    __syncthreads();
+
+    float* out = A.C + (size_t)chunk * A.chunk_stride + (size_t)(tm * BM + warp * 32 + lane) * A.ldc + tn * BN;
+    if (nk > 0) {
+        if (warp == 0 && lane == 0) {
+            int issued = 0;
+            for (int ks = 0; ks < nk; ++ks) {
+                const int s = ks % STAGES;
+                const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
+                if (ks >= STAGES && !mbar_wait(&S.empty[s], ph ^ 1u)) { failed = 1; break; }
+                mbar_expect_tx(&S.full[s], 2 * kTileBytes);
+                const int kb = kb_lo + ks / A.npairs, p = ks % A.npairs;
+                tma_load_2d(S.a[s], &mapL, kb * BK, A.lp[p] * A.l_part_rows + A.l_row0 + tm * BM, &S.full[s]);
+                tma_load_2d(S.b[s], &mapR, kb * BK, A.rp[p] * A.r_part_rows + A.r_row0 + tn * BN, &S.full[s]);
+                ++issued;
+            }
+            if (failed)
+                for (int ks = (issued > STAGES ? issued - STAGES : 0); ks < issued; ++ks)
+                    mbar_wait(&S.full[ks % STAGES], (uint32_t)(ks / STAGES) & 1u);
+        } else if (warp == 1 && lane == 0) {
+            bool ok = true;
+            for (int ks = 0; ks < nk; ++ks) {
+                const int s = ks % STAGES;
+                if (!mbar_wait(&S.full[s], (uint32_t)(ks / STAGES) & 1u)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t da = desc_sw128(smem_u32(S.a[s])), db = desc_sw128(smem_u32(S.b[s]));
+                const int blk = ks / A.npairs;
+                const uint32_t acc = tmem + (uint32_t)((blk / kAccBlocks) * 128);
+                const bool first = blk % kAccBlocks == 0 && ks % A.npairs == 0;
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    mma_f16(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), A.idesc, (!first || k > 0) ? 1u : 0u);
+                mma_commit(&S.empty[s]);
+            }
+            if (!ok) failed = 1;
+            mma_commit(&S.done);
+        }
+        __syncwarp();
+        const bool ready = mbar_wait(&S.done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (!ready || failed) {
+            if (threadIdx.x == 0) atomicExch(A.err, 1);
+        } else {
+            const int used = (kb_hi - kb_lo + kAccBlocks - 1) / kAccBlocks;
+#pragma unroll 1
+            for (int cb = 0; cb < BN / 32; ++cb) {
+                double v[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.0;
+#pragma unroll 1
+                for (int a = 0; a < used; ++a) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * 128 + cb * 32), r);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] += (double)__uint_as_float(r[q]);
+                }
+                float4* dst = reinterpret_cast<float4*>(out + cb * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    dst[q] = make_float4((float)v[4 * q], (float)v[4 * q + 1], (float)v[4 * q + 2], (float)v[4 * q + 3]);
+            }
+        }
+    } else {
+        float4* dst = reinterpret_cast<float4*>(out);
+        for (int q = 0; q < BN / 4; ++q) dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// ---- 16-bit parts --------------------------------------------------------------------
+// x (already scaled, rounded once to FP32) as NP 16-bit parts whose sum is x to about 2^-22
+// (FP16: two parts of 11 bits) or 2^-24 (BF16: three parts of 8 bits); the residuals are
+// exact in FP32
+template <typename H> __device__ __forceinline__ H to_h(float v);
+template <> __device__ __forceinline__ __half to_h<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_h<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from_h(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from_h(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename H, int NP>
+__device__ __forceinline__ void split_parts(double xd, H (&h)[NP]) {
+    float x = (float)xd;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        h[p] = to_h<H>(x);
+        x -= from_h(h[p]);
+    }
+}
+
+template <typename H, int NP>
+__device__ __forceinline__ void put_parts(const H (&h)[NP], H* dst, size_t part_stride) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) dst[(size_t)p * part_stride] = h[p];
+}
+
+template <typename H, int NP>
+__device__ __forceinline__ void store_parts(double x, H* dst, size_t part_stride) {
+    H h[NP];
+    split_parts<H, NP>(x, h);
+    put_parts<H, NP>(h, dst, part_stride);
+}
+
+// power-of-two exponent e with max * 2^e in [2^14, 2^15) (0 for max = 0)
+__device__ __forceinline__ int scale_exp(double mx) {
+    if (!(mx > 0.0) || !isfinite(mx)) return 0;
+    int q;
+    frexp(mx, &q);
+    return 15 - q;
+}
+
+__device__ __forceinline__ double wsum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+struct PrepArgs {
+    const double* val;            // operand values, feature-major (P rows of N)
+    const unsigned char* valid;   // operand validity (recursive rules)
+    int P, Pp, N, Kpad;
+    void* L;                      // parts x 3 Pp rows x Kpad
+    void* R;                      // parts x 4 Pp rows x Kpad
+    int* eL;                      // 3 Pp row exponents
+    int* eR;                      // 4 Pp
+    double* mom;                  // per operand: xbar, sum x'^2, sum x'^4, gbar, sum g'^2, sum g'^4,
+                                  // 1/x state (0 rows built, 1 x has a zero, 2 rows unusable), valid
+    double* recip;                // 1/x of every operand value (P rows of N)
+};
+
+constexpr int kPrepThreads = 512;          // one CTA per operand row, threads over samples
+constexpr int kPrepWarps = kPrepThreads / 32;
+
+// CTA-wide sums (op 0) or maxima (op 1) of K values, the same in every thread (warps
+// combined in a fixed order, so results do not depend on timing)
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], const int (&op)[K], double (*sh)[K]) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = op[k] ? wmax(v[k]) : wsum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[w][k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double t = sh[0][k];
+        for (int q = 1; q < kPrepWarps; ++q) t = op[k] ? fmax(t, sh[q][k]) : t + sh[q][k];
+        v[k] = t;
+    }
+}
+
+// Target-independent rows and moments of every operand (one CTA per operand row): L blocks
+// 0 (x') and 1 (x'^2); R blocks 0 (x'), 1 ((1/x)'), 2 (x'^2), 3 (((1/x)')^2).  Rows of
+// invalid operands, of 1/x where x has a zero (or 1/x overflows), and padding are zero.
+template <typename H, int NP>
+__global__ void __launch_bounds__(kPrepThreads) k_tc_prep(PrepArgs A) {
+    __shared__ double sh[kPrepWarps][8];
+    const int f = blockIdx.x, t = threadIdx.x;
+    H* L = static_cast<H*>(A.L);
+    H* R = static_cast<H*>(A.R);
+    const size_t K = (size_t)A.Kpad, lps = (size_t)3 * A.Pp * K, rps = (size_t)4 * A.Pp * K;
+    H* l0 = L + (size_t)f * K;
+    H* l1 = L + (size_t)(A.Pp + f) * K;
+    H* r0 = R + (size_t)f * K;
+    H* r1 = R + (size_t)(A.Pp + f) * K;
+    H* r2 = R + (size_t)(2 * A.Pp + f) * K;
+    H* r3 = R + (size_t)(3 * A.Pp + f) * K;
+    const bool ok = f < A.P && A.valid[f];
+    const double* v = A.val + (size_t)(ok ? f : 0) * A.N;
+    double* rc = A.recip + (size_t)(ok ? f : 0) * A.N;
+    double m1[3] = {0.0, 0.0, 0.0};          // sum x, zero flag, sum 1/x
+    if (ok)
+        for (int i = t; i < A.N; i += kPrepThreads) {
+            const double x = v[i];
+            m1[0] += x;
+            const double c = 1.0 / x;
+            rc[i] = c;
+            if (!(x != 0.0) || !isfinite(c)) m1[1] = 1.0;
+            else m1[2] += c;
+        }
+    block_reduce<3>(m1, {0, 1, 0}, reinterpret_cast<double (*)[3]>(&sh[0][0]));
+    const bool zero = m1[1] != 0.0;
+    const double mean = m1[0] / A.N, meanc = zero ? 0.0 : m1[2] / A.N;
+    double m2[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // x'^2, x'^4, c'^2, c'^4, max |x'|, x'^2, |c'|, c'^2
+    if (ok)
+        for (int i = t; i < A.N; i += kPrepThreads) {
+            const double a = v[i] - mean, a2 = a * a;
+            m2[0] += a2; m2[1] += a2 * a2;
+            m2[4] = fmax(m2[4], fabs(a)); m2[5] = fmax(m2[5], a2);
+            if (!zero) {
+                const double c = rc[i] - meanc, cc = c * c;
+                m2[2] += cc; m2[3] += cc * cc;
+                m2[6] = fmax(m2[6], fabs(c)); m2[7] = fmax(m2[7], cc);
+            }
+        }
+    block_reduce<8>(m2, {0, 0, 0, 0, 1, 1, 1, 1}, sh);
+    // 1/x rows whose fourth powers overflow (|x| below ~1e-77 somewhere) are not used: the
+    // keys of x-divided candidates are then 1, left to the FP64 re-score
+    const bool unusable = !zero && !(isfinite(m2[3]) && isfinite(m2[7]));
+    const bool crow = !zero && !unusable;
+    if (!crow) m2[2] = m2[3] = m2[6] = m2[7] = 0.0;
+    const int e1 = scale_exp(m2[4]), e2 = scale_exp(m2[5]), ec1 = scale_exp(m2[6]), ec2 = scale_exp(m2[7]);
+    const double s1 = ldexp(1.0, e1), s2 = ldexp(1.0, e2), sc1 = ldexp(1.0, ec1), sc2 = ldexp(1.0, ec2);
+    for (int i = t; i < A.Kpad; i += kPrepThreads) {
+        double a = 0.0, a2 = 0.0, c = 0.0, cc = 0.0;
+        if (ok && i < A.N) {
+            a = v[i] - mean;
+            a2 = a * a;
+            if (crow) { c = rc[i] - meanc; cc = c * c; }
+        }
+        H h[NP];
+        split_parts<H, NP>(a * s1, h);
+        put_parts<H, NP>(h, l0 + i, lps);
+        put_parts<H, NP>(h, r0 + i, rps);
+        split_parts<H, NP>(a2 * s2, h);
+        put_parts<H, NP>(h, l1 + i, lps);
+        put_parts<H, NP>(h, r2 + i, rps);
+        store_parts<H, NP>(c * sc1, r1 + i, rps);
+        store_parts<H, NP>(cc * sc2, r3 + i, rps);
+    }
+    if (t == 0) {
+        A.eL[f] = e1; A.eL[A.Pp + f] = e2;
+        A.eR[f] = e1; A.eR[A.Pp + f] = ec1; A.eR[2 * A.Pp + f] = e2; A.eR[3 * A.Pp + f] = ec2;
+        double* m = A.mom + (size_t)f * 8;
+        m[0] = mean; m[1] = m2[0]; m[2] = m2[1]; m[3] = meanc; m[4] = m2[2]; m[5] = m2[3];
+        m[6] = zero ? 1.0 : unusable ? 2.0 : 0.0; m[7] = ok;
+    }
+}
+
+// Target rows and moments of every operand (one CTA per operand row): L block 2 (x' r) and
+// sum x'r, sum (x'r)^2, sum (1/x)' r.
+template <typename H, int NP>
+__global__ void __launch_bounds__(kPrepThreads) k_tc_target(PrepArgs A, const double* __restrict__ r,
+                                                            double* __restrict__ tgt) {
+    __shared__ double sh[kPrepWarps][4];
+    const int f = blockIdx.x, t = threadIdx.x;
+    H* L = static_cast<H*>(A.L);
+    const size_t K = (size_t)A.Kpad, lps = (size_t)3 * A.Pp * K;
+    H* l2 = L + (size_t)(2 * A.Pp + f) * K;
+    const double* m = A.mom + (size_t)f * 8;
+    const bool ok = m[7] != 0.0;
+    const bool zero = m[6] != 0.0;           // no 1/x rows
+    const double mean = m[0], meanc = m[3];
+    const double* v = A.val + (size_t)(ok ? f : 0) * A.N;
+    const double* rc = A.recip + (size_t)(ok ? f : 0) * A.N;
+    double q[4] = {0.0, 0.0, 0.0, 0.0};     // sum x'r, sum (x'r)^2, sum c'r, max |x'r|
+    if (ok)
+        for (int i = t; i < A.N; i += kPrepThreads) {
+            const double a = (v[i] - mean) * r[i];
+            q[0] += a; q[1] += a * a;
+            q[3] = fmax(q[3], fabs(a));
+            if (!zero) q[2] += (rc[i] - meanc) * r[i];
+        }
+    block_reduce<4>(q, {0, 0, 0, 1}, sh);
+    const int e = scale_exp(q[3]);
+    const double s = ldexp(1.0, e);
+    for (int i = t; i < A.Kpad; i += kPrepThreads) {
+        const double a = ok && i < A.N ? (v[i] - mean) * r[i] : 0.0;
+        store_parts<H, NP>(a * s, l2 + i, lps);
+    }
+    if (t == 0) {
+        A.eL[2 * A.Pp + f] = e;
+        tgt[(size_t)f * 4 + 0] = q[0]; tgt[(size_t)f * 4 + 1] = q[1]; tgt[(size_t)f * 4 + 2] = q[2]; tgt[(size_t)f * 4 + 3] = 0.0;
+    }
+}
+
+// out[r][c] = sum over chunks of C (FP64, in chunk order), unscaled by the rows' exponents
+__global__ void k_bilin_reduce(const float* __restrict__ C, int chunks, size_t chunk_stride, int rows, int cols, int ldc,
+                               const int* __restrict__ eL, const int* __restrict__ eR, double* __restrict__ out,
+                               int ldo) {
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), c = (int)(e % cols);
+        const float* p = C + (size_t)r * ldc + c;
+        double s = 0.0;
+        for (int q = 0; q < chunks; ++q) s += (double)p[(size_t)q * chunk_stride];
+        out[(size_t)r * ldo + c] = ldexp(s, -(eL[r] + eR[c]));
+    }
+}
+
+struct ScoreArgs {
+    const Space* sp;
+    int sec[4];
+    int P, Q, Pp, N;
+    const double* mom;      // Pp x 8
+    const double* tgt;      // Pp x 4
+    const double* C1;       // 2 Pp x 4 Pp
+    const double* C2;       // Pp x 2 Pp
+    const TargetStats* st;
+    double eps_tc, eps_sel;
+    float* scores;
+    unsigned long long* raised;
+};
+
+// U, V and their error bounds for f = x g (x: L-side operand, g: R-side row set gs = 0 for
+// g = z, 1 for g = 1/z); see the header comment for the formulas
+struct UV { double U, V, dU, dV; };
+
+__device__ __forceinline__ UV prod_uv(const ScoreArgs& A, int xi, int zi, int gs) {
+    const int Pp = A.Pp;
+    const size_t l1 = (size_t)4 * Pp, l2 = (size_t)2 * Pp;
+    const double* mx = A.mom + (size_t)xi * 8;
+    const double* mz = A.mom + (size_t)zi * 8;
+    const double xb = mx[0], X2 = mx[1], X4 = mx[2];
+    const double gb = gs ? mz[3] : mz[0], G2 = gs ? mz[4] : mz[1], G4 = gs ? mz[5] : mz[2];
+    const double XR = A.tgt[(size_t)xi * 4], XRR = A.tgt[(size_t)xi * 4 + 1];
+    const double GR = gs ? A.tgt[(size_t)zi * 4 + 2] : A.tgt[(size_t)zi * 4];
+    const double P1 = A.C1[(size_t)xi * l1 + gs * Pp + zi];
+    const double P2 = A.C1[(size_t)(Pp + xi) * l1 + (2 + gs) * Pp + zi];
+    const double P3 = A.C1[(size_t)xi * l1 + (2 + gs) * Pp + zi];
+    const double P4 = A.C1[(size_t)(Pp + xi) * l1 + gs * Pp + zi];
+    const double P5 = A.C2[(size_t)xi * l2 + gs * Pp + zi];
+    const double N = (double)A.N, ts = A.st->tsum;
+    UV o;
+    const double t1 = xb * xb * G2, t2 = gb * gb * X2, t3 = 2.0 * xb * gb * P1, t4 = 2.0 * xb * P3, t5 = 2.0 * gb * P4;
+    o.V = t1 + t2 + P2 - P1 * P1 / N + t3 + t4 + t5;
+    o.U = xb * GR + gb * XR + P5 - P1 * ts / N;
+    const double cs11 = sqrt(X2 * G2);
+    o.dV = A.eps_tc * ((2.0 * fabs(P1) / N + 2.0 * fabs(xb * gb)) * cs11 + sqrt(X4 * G4) + 2.0 * fabs(xb) * sqrt(X2 * G4) +
+                       2.0 * fabs(gb) * sqrt(X4 * G2)) +
+           1e-15 * (t1 + t2 + fabs(P2) + P1 * P1 / N + fabs(t3) + fabs(t4) + fabs(t5));
+    o.dU = A.eps_tc * (sqrt(XRR * G2) + fabs(ts / N) * cs11) + 1e-15 * (fabs(xb * GR) + fabs(gb * XR) + fabs(P5));
+    return o;
+}
+
+// stored key: the estimate, raised to (upper bound - margin) where the bound exceeds it by
+// more than the margin; 1 (the largest |rho|) where V is not resolved
+__device__ __forceinline__ float key_of(const UV& o, double srr, double eps_sel, unsigned long long* raised) {
+    if (!(o.V - o.dV > 0.0)) {
+        atomicAdd(raised, 1ull);
+        return 1.0f;
+    }
+    const double est = fabs(o.U) / sqrt(o.V * srr);
+    const double ub = (fabs(o.U) + o.dU) / sqrt((o.V - o.dV) * srr);
+    double key = est;
+    if (ub - eps_sel > est) {
+        key = ub - eps_sel;
+        atomicAdd(raised, 1ull);
+    }
+    return __double2float_ru(fmin(key, 1.0));
+}
+
+// key of x / z: -1 where z has a zero (division by zero), 1 where the 1/z rows are unusable
+__device__ __forceinline__ float div_key(const ScoreArgs& A, bool ok, int xi, int zi, double srr) {
+    const double st = A.mom[(size_t)zi * 8 + 6];
+    if (!ok || st == 1.0) return -1.f;
+    if (st == 2.0) {
+        atomicAdd(A.raised, 1ull);
+        return 1.f;
+    }
+    return key_of(prod_uv(A, xi, zi, 1), srr, A.eps_sel, A.raised);
+}
+
+// one thread per operand pair i < j (j >= Q): the keys of i+j, i-j, i*j, i/j, j/i
+__global__ void k_score_bilin(ScoreArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)A.P * A.P) return;
+    const int i = (int)(e / A.P), j = (int)(e % A.P);
+    if (!(i < j && j >= A.Q)) return;
+    const double* mi = A.mom + (size_t)i * 8;
+    const double* mj = A.mom + (size_t)j * 8;
+    const bool ok = mi[7] != 0.0 && mj[7] != 0.0;
+    const double srr = (double)A.N * A.st->sd * A.st->sd;
+    if (A.sec[0] >= 0 || A.sec[1] >= 0) {
+        const double P1 = A.C1[(size_t)i * 4 * A.Pp + j];
+        const double X2 = mi[1], Z2 = mj[1], XR = A.tgt[(size_t)i * 4], ZR = A.tgt[(size_t)j * 4];
+        const double cs = sqrt(X2 * Z2);
+        for (int o = 0; o < 2; ++o) {
+            if (A.sec[o] < 0) continue;
+            const double sg = o == 0 ? 1.0 : -1.0;
+            float key = -1.f;
+            if (ok) {
+                UV u;
+                u.V = X2 + Z2 + 2.0 * sg * P1;
+                u.U = XR + sg * ZR;
+                u.dV = 2.0 * A.eps_tc * cs + 1e-15 * (X2 + Z2 + 2.0 * fabs(P1));
+                u.dU = 1e-15 * (fabs(XR) + fabs(ZR));
+                key = key_of(u, srr, A.eps_sel, A.raised);
+            }
+            const Section& sc = A.sp->sec[A.sec[o]];
+            A.scores[sc.base + rank_of(sc, i, j)] = key;
+        }
+    }
+    if (A.sec[2] >= 0) {
+        const Section& sc = A.sp->sec[A.sec[2]];
+        A.scores[sc.base + rank_of(sc, i, j)] = ok ? key_of(prod_uv(A, i, j, 0), srr, A.eps_sel, A.raised) : -1.f;
+    }
+    if (A.sec[3] >= 0) {
+        const Section& sc = A.sp->sec[A.sec[3]];
+        A.scores[sc.base + rank_of(sc, i, j)] = div_key(A, ok, i, j, srr);
+        A.scores[sc.base + rank_of(sc, j, i)] = div_key(A, ok, j, i, srr);
+    }
+}
+
+// rows (FP64, row stride N) -> NP parts of 16 bits, scaled per row (one warp per row)
+template <typename H, int NP>
+__global__ void k_rows_parts(const double* __restrict__ src, int rows, int N, int rows_pad, int Kpad, H* __restrict__ dst,
+                             int* __restrict__ ex) {
+    const int f = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (f >= rows_pad) return;
+    const size_t K = (size_t)Kpad, ps = (size_t)rows_pad * K;
+    double mx = 0.0;
+    if (f < rows)
+        for (int i = lane; i < N; i += 32) mx = fmax(mx, fabs(src[(size_t)f * N + i]));
+    const int e = scale_exp(wmax(mx));
+    const double s = ldexp(1.0, e);
+    for (int i = lane; i < Kpad; i += 32)
+        store_parts<H, NP>(f < rows && i < N ? src[(size_t)f * N + i] * s : 0.0, dst + (size_t)f * K + i, ps);
+    if (lane == 0) ex[f] = e;
+}
+
+// ---- host -----------------------------------------------------------------------------
+struct Parts {
+    int n;
+    int lp[kMaxParts], rp[kMaxParts];
+};
+Parts parts_of(bool bf16) {
+    if (bf16) return Parts{6, {0, 0, 1, 0, 2, 1}, {0, 1, 0, 2, 0, 1}};
+    return Parts{3, {0, 0, 1}, {0, 1, 0}};
+}
+int nparts(bool bf16) { return bf16 ? 3 : 2; }
+
+bool encode_map(EncodeTiledFn enc, CUtensorMap* map, bool bf16, void* base, int rows, int Kpad) {
+    const cuuint64_t gdim[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)Kpad * 2};
+    const cuuint32_t box[2] = {BK, BM};
+    const cuuint32_t estride[2] = {1, 1};
+    return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, gdim, gstride, box,
+               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int chunks_of(int nkb, int& per) {
+    const int ch = std::max(1, (nkb + kChunkBlocks - 1) / kChunkBlocks);
+    per = (nkb + ch - 1) / ch;
+    return (nkb + per - 1) / per;
+}
+
+// C (m_rows x n_rows of the product, FP64 into out) = L[l_row0 ..] R[r_row0 ..]^T over the
+// samples, both sides given as parts; out is unscaled by eL / eR (offset to the product's rows)
+cudaError_t bilin(cudaStream_t s, int sms, bool bf16, void* L, int l_part_rows, int l_row0, int m_rows, void* R,
+                  int r_part_rows, int r_row0, int n_rows, int Kpad, float* part, int* err, const int* eL,
+                  const int* eR, double* out, int ldo, int& launches) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int np = nparts(bf16);
+    CUtensorMap mL, mR;
+    if (!encode_map(enc, &mL, bf16, L, np * l_part_rows, Kpad) || !encode_map(enc, &mR, bf16, R, np * r_part_rows, Kpad))
+        return cudaErrorInvalidValue;
+    const Parts pp = parts_of(bf16);
+    BilinArgs A{};
+    A.tiles_m = m_rows / BM;
+    A.tiles_n = n_rows / BN;
+    A.nkb = Kpad / BK;
+    A.chunks = chunks_of(A.nkb, A.kb_per_chunk);
+    A.l_row0 = l_row0; A.r_row0 = r_row0;
+    A.l_part_rows = l_part_rows; A.r_part_rows = r_part_rows;
+    A.npairs = pp.n;
+    for (int q = 0; q < pp.n; ++q) { A.lp[q] = pp.lp[q]; A.rp[q] = pp.rp[q]; }
+    A.C = part;
+    A.ldc = n_rows;
+    A.chunk_stride = (size_t)m_rows * n_rows;
+    A.err = err;
+    A.idesc = idesc_f16(bf16 ? 1u : 0u, BM, BN);
+    const size_t smem = sizeof(Smem) + 1024;
+    cudaFuncSetAttribute(k_bilin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bilin_tc<<<A.tiles_m * A.tiles_n * A.chunks, kThreads, smem, s>>>(mL, mR, A);
+    const int64_t total = (int64_t)m_rows * n_rows;
+    k_bilin_reduce<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (total + 255) / 256)), 256, 0, s>>>(
+        part, A.chunks, A.chunk_stride, m_rows, n_rows, n_rows, eL + l_row0, eR + r_row0, out, ldo);
+    launches += 2;
+    return cudaGetLastError();
+}
+
+size_t part_floats(int Pp, int Kpad) {
+    int per;
+    const int ch = chunks_of(Kpad / BK, per);
+    return (size_t)ch * 8 * Pp * Pp;        // the larger product: 2 Pp x 4 Pp per chunk
+}
+
+}  // namespace
+
+bool tc_screen_possible(const sisso_ctx* c) {
+    const int L = c->space.rung;
+    if (c->space.grammar == SISSO_GRAMMAR_NEW_X_PREV && L >= 3) return false;
+    const int64_t P = c->space.phi[L - 1];
+    if (P > 4096) return false;
+    const int Pp = (int)((P + BM - 1) / BM) * BM;
+    const int Kpad = ((c->N + BK - 1) / BK) * BK;
+    const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
+    const size_t bytes = (size_t)nparts(bf16) * 7 * Pp * Kpad * 2 + part_floats(Pp, Kpad) * 4 + (size_t)10 * Pp * Pp * 8 +
+                         (size_t)P * c->N * 8;
+    return bytes <= ((size_t)16 << 30);
+}
+
+sisso_status tc_screen_alloc(sisso_ctx* c) {
+    const int L = c->space.rung;
+    const int P = (int)c->space.phi[L - 1];
+    const int Pp = (P + BM - 1) / BM * BM;
+    const int Kpad = ((c->N + BK - 1) / BK) * BK;
+    const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
+    const int np = nparts(bf16);
+    c->tc_P = P; c->tc_Pp = Pp; c->tc_Kpad = Kpad;
+    c->tc_part_cap = part_floats(Pp, Kpad);
+    sisso_status st;
+    auto al = [&](void** p, size_t bytes, const char* what) {
+        return check_cuda(c, cudaMalloc(p, bytes), what);
+    };
+    if ((st = al(&c->tc_L, (size_t)np * 3 * Pp * Kpad * 2, "tc L")) ||
+        (st = al(&c->tc_R, (size_t)np * 4 * Pp * Kpad * 2, "tc R")) ||
+        (st = al((void**)&c->tc_eL, sizeof(int) * 3 * Pp, "tc eL")) ||
+        (st = al((void**)&c->tc_eR, sizeof(int) * 4 * Pp, "tc eR")) ||
+        (st = al((void**)&c->tc_mom, sizeof(double) * 8 * Pp, "tc mom")) ||
+        (st = al((void**)&c->tc_tgt, sizeof(double) * 4 * Pp, "tc tgt")) ||
+        (st = al((void**)&c->tc_part, sizeof(float) * c->tc_part_cap, "tc partials")) ||
+        (st = al((void**)&c->tc_C1, sizeof(double) * 8 * Pp * Pp, "tc C1")) ||
+        (st = al((void**)&c->tc_C2, sizeof(double) * 2 * Pp * Pp, "tc C2")) ||
+        (st = al((void**)&c->tc_recip, sizeof(double) * (size_t)P * c->N, "tc reciprocals")) ||
+        (st = al((void**)&c->tc_err, 16, "tc err")))
+        return st;
+    c->tc_raised = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->tc_err) + 8);
+    cudaMemsetAsync(c->tc_err, 0, 16, c->stream);
+    c->tc_on = true;
+    c->tc_ready = false;
+    return SISSO_OK;
+}
+
+// keys of the top level's binary sections for the current target (tc64 / tstats); the
+// target-independent product runs on the first call after tc_ready was cleared
+sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]) {
+    const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
+    const int L = c->space.rung;
+    PrepArgs A{};
+    A.val = c->opval64;
+    A.valid = c->subvalid;
+    A.P = c->tc_P; A.Pp = c->tc_Pp; A.N = c->N; A.Kpad = c->tc_Kpad;
+    A.L = c->tc_L; A.R = c->tc_R; A.eL = c->tc_eL; A.eR = c->tc_eR; A.mom = c->tc_mom; A.recip = c->tc_recip;
+    const int Pp = c->tc_Pp;
+    cudaError_t e = cudaSuccess;
+    if (!c->tc_ready) {
+        if (bf16) k_tc_prep<__nv_bfloat16, 3><<<Pp, kPrepThreads, 0, c->stream>>>(A);
+        else k_tc_prep<__half, 2><<<Pp, kPrepThreads, 0, c->stream>>>(A);
+        c->stats.launches++;
+        e = bilin(c->stream, c->sms, bf16, c->tc_L, 3 * Pp, 0, 2 * Pp, c->tc_R, 4 * Pp, 0, 4 * Pp, c->tc_Kpad, c->tc_part,
+                  c->tc_err, c->tc_eL, c->tc_eR, c->tc_C1, 4 * Pp, c->stats.launches);
+        if (e != cudaSuccess) return check_cuda(c, e, "tc product (target-independent)");
+        c->tc_ready = true;
+    }
+    if (bf16) k_tc_target<__nv_bfloat16, 3><<<Pp, kPrepThreads, 0, c->stream>>>(A, c->tc64, c->tc_tgt);
+    else k_tc_target<__half, 2><<<Pp, kPrepThreads, 0, c->stream>>>(A, c->tc64, c->tc_tgt);
+    c->stats.launches++;
+    e = bilin(c->stream, c->sms, bf16, c->tc_L, 3 * Pp, 2 * Pp, Pp, c->tc_R, 4 * Pp, 0, 2 * Pp, c->tc_Kpad, c->tc_part,
+              c->tc_err, c->tc_eL, c->tc_eR, c->tc_C2, 2 * Pp, c->stats.launches);
+    if (e != cudaSuccess) return check_cuda(c, e, "tc product (target)");
+    ScoreArgs S{};
+    S.sp = c->space_dev;
+    for (int o = 0; o < 4; ++o) S.sec[o] = sec[o];
+    S.P = c->tc_P;
+    S.Q = L >= 2 ? (int)c->space.phi[L - 2] : 0;
+    S.Pp = Pp; S.N = c->N;
+    S.mom = c->tc_mom; S.tgt = c->tc_tgt; S.C1 = c->tc_C1; S.C2 = c->tc_C2; S.st = c->tstats;
+    S.eps_tc = kTcEps;
+    S.eps_sel = kScoreErr32;
+    S.scores = c->scores;
+    S.raised = c->tc_raised;
+    const int64_t n = (int64_t)S.P * S.P;
+    k_score_bilin<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(S);
+    c->stats.launches++;
+    return check_cuda(c, cudaGetLastError(), "tc keys");
+}
+
+// the error flag and the raised-key count since the last call (both then cleared)
+sisso_status tc_screen_status(sisso_ctx* c) {
+    int h[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(h, c->tc_err, 16, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemsetAsync(c->tc_err, 0, 16, c->stream);
+    sisso_status st = check_cuda(c, cudaStreamSynchronize(c->stream), "tc status");
+    if (st) return st;
+    unsigned long long raised;
+    std::memcpy(&raised, &h[2], 8);
+    c->stats.tc_keys_raised += (int64_t)raised;
+    if (h[0]) return fail(c, SISSO_ERR_TIMEOUT, "tensor-core screening: a bounded wait ran out");
+    return SISSO_OK;
+}
+
+void tc_screen_free(sisso_ctx* c) {
+    void* bufs[] = {c->tc_L,  c->tc_R,  c->tc_eL, c->tc_eR,    c->tc_mom, c->tc_tgt,
+                    c->tc_part, c->tc_C1, c->tc_C2, c->tc_recip, c->tc_err};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace sg
+
+// sum_s L[i][s] R[j][s] (FP64 in and out, host memory) through the split 16-bit tensor-core
+// product the mixed forms' screening uses
+extern "C" sisso_status sisso_bilinear_tc(const double* Lrows, const double* Rrows, int m, int n, int N, int kind,
+                                          double* out) {
+    using namespace sg;
+    if (!Lrows || !Rrows || !out || m < 1 || n < 1 || N < 1 ||
+        (kind != SISSO_PREC_MIXED_BF16 && kind != SISSO_PREC_MIXED_FP16) || m > 65536 || n > 65536)
+        return SISSO_ERR_ARG;
+    const bool bf16 = kind == SISSO_PREC_MIXED_BF16;
+    const int np = nparts(bf16);
+    const int mp = (m + BM - 1) / BM * BM, npad = (n + BN - 1) / BN * BN, Kpad = (N + BK - 1) / BK * BK;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per;
+    const int ch = chunks_of(Kpad / BK, per);
+    double *dL = nullptr, *dR = nullptr, *dout = nullptr;
+    void *hL = nullptr, *hR = nullptr;
+    int *eL = nullptr, *eR = nullptr, *err = nullptr;
+    float* part = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t x) { if (e == cudaSuccess && x != cudaSuccess) e = x; };
+    ck(cudaMalloc((void**)&dL, sizeof(double) * (size_t)m * N));
+    ck(cudaMalloc((void**)&dR, sizeof(double) * (size_t)n * N));
+    ck(cudaMalloc(&hL, (size_t)np * mp * Kpad * 2));
+    ck(cudaMalloc(&hR, (size_t)np * npad * Kpad * 2));
+    ck(cudaMalloc((void**)&eL, sizeof(int) * mp));
+    ck(cudaMalloc((void**)&eR, sizeof(int) * npad));
+    ck(cudaMalloc((void**)&err, sizeof(int)));
+    ck(cudaMalloc((void**)&part, sizeof(float) * (size_t)ch * mp * npad));
+    ck(cudaMalloc((void**)&dout, sizeof(double) * (size_t)mp * npad));
+    int h_err = 0, launches = 0;
+    if (e == cudaSuccess) {
+        ck(cudaMemcpy(dL, Lrows, sizeof(double) * (size_t)m * N, cudaMemcpyHostToDevice));
+        ck(cudaMemcpy(dR, Rrows, sizeof(double) * (size_t)n * N, cudaMemcpyHostToDevice));
+        ck(cudaMemset(err, 0, sizeof(int)));
+        if (bf16) {
+            k_rows_parts<__nv_bfloat16, 3><<<(mp * 32 + 255) / 256, 256>>>(dL, m, N, mp, Kpad, (__nv_bfloat16*)hL, eL);
+            k_rows_parts<__nv_bfloat16, 3><<<(npad * 32 + 255) / 256, 256>>>(dR, n, N, npad, Kpad, (__nv_bfloat16*)hR, eR);
+        } else {
+            k_rows_parts<__half, 2><<<(mp * 32 + 255) / 256, 256>>>(dL, m, N, mp, Kpad, (__half*)hL, eL);
+            k_rows_parts<__half, 2><<<(npad * 32 + 255) / 256, 256>>>(dR, n, N, npad, Kpad, (__half*)hR, eR);
+        }
+        ck(cudaGetLastError());
+        if (e == cudaSuccess)
+            ck(bilin(0, sms, bf16, hL, mp, 0, mp, hR, npad, 0, npad, Kpad, part, err, eL, eR, dout, npad, launches));
+        ck(cudaDeviceSynchronize());
+        if (e == cudaSuccess) {
+            ck(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
+            ck(cudaMemcpy2D(out, sizeof(double) * n, dout, sizeof(double) * npad, sizeof(double) * n, m,
+                            cudaMemcpyDeviceToHost));
+        }
+    }
+    cudaFree(dL); cudaFree(dR); cudaFree(hL); cudaFree(hR); cudaFree(eL); cudaFree(eR); cudaFree(err);
+    cudaFree(part); cudaFree(dout);
+    if (e != cudaSuccess) return SISSO_ERR_CUDA;
+    return h_err ? SISSO_ERR_TIMEOUT : SISSO_OK;
+}

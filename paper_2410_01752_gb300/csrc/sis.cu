@@ -127,9 +127,12 @@ __global__ void k_score_generic(const Space* __restrict__ sp, const T* __restric
 // sections score from cached rows, and the pair kernel stages operands by plain loads.
 // ---------------------------------------------------------------------------------
 // sample-major layout: cache[s * P + id], so that a warp reads 32 consecutive features of
-// one sample with one coalesced access
+// one sample with one coalesced access.  Values are evaluated in FP64 from the FP64
+// primaries and rounded once to T: an operand built by cancellation (x_i - x_j of nearly
+// equal columns) keeps its full relative precision, and so does every candidate the top
+// level builds from it (1/(x_i - x_j) is then within a few FP32 roundings at every sample).
 template <typename T>
-__global__ void k_fill_cache_w(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, int64_t n_ids,
+__global__ void k_fill_cache_w(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t n_ids,
                                T* __restrict__ cache) {
     const int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -137,18 +140,20 @@ __global__ void k_fill_cache_w(const Space* __restrict__ sp, const T* __restrict
     Prog p;
     const bool ok = build_prog(*sp, id, p);
     for (int s = lane; s < N; s += 32)
-        cache[(size_t)s * n_ids + id] = ok ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
+        cache[(size_t)s * n_ids + id] =
+            ok ? (T)eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
 }
 
 template <typename T>
-__global__ void k_fill_cache(const Space* __restrict__ sp, const T* __restrict__ Xc, int N, int64_t n_ids,
+__global__ void k_fill_cache(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t n_ids,
                              T* __restrict__ cache) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= n_ids) return;
     Prog p;
     const bool ok = build_prog(*sp, id, p);
     for (int s = 0; s < N; ++s)
-        cache[(size_t)s * n_ids + id] = ok ? eval_prog<T>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
+        cache[(size_t)s * n_ids + id] =
+            ok ? (T)eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
 }
 
 // ids [lo, hi) below the top level (P = |phi_{L-1}| of them) scored from the cache: one
@@ -233,32 +238,71 @@ __global__ void k_opsums_w(const T* __restrict__ cache, int N, int64_t P, const 
     if (lane == 0) { if (A1ON) A1[f] = a; AR[f] = ar; }
 }
 
-// the top level's unary sections with one warp per candidate (few operands, many samples)
+// the top level's unary sections when operands are few and samples many: one warp per
+// (operand, run of samples) computes every enabled operator from the operand's feature-major
+// FP64 row (coalesced; rounded to T as the cache is) and leaves its shifted sums (shift: the
+// value at sample 0) in part[run][op][operand][3]; k_unary_finish adds the runs in FP64
 template <typename T>
-__global__ void k_score_unary_w(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
-                                const TargetStats* st, const unsigned char* __restrict__ subvalid,
-                                float* __restrict__ scores) {
+__global__ void k_score_unary_runs(UnaryArgs U, const double* __restrict__ val, const float* tc32, const double* tc64,
+                                   const unsigned char* __restrict__ subvalid, int runs, double* __restrict__ part) {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t nz = U.P - U.Q;
-    if (w >= nz * U.n_ops) return;
-    const int k = (int)(w / nz);
+    if (w >= nz * runs) return;
+    const int run = (int)(w / nz);
     const int64_t z = U.Q + w % nz;
-    const int op = U.op[k];
     const int N = U.N;
+    const int lo = (int)((int64_t)N * run / runs), hi = (int)((int64_t)N * (run + 1) / runs);
     const T* tc = TgtView<T>::tc(tc32, tc64);
-    if (!subvalid[z]) { if (lane == 0) scores[U.base[k] + (z - U.Q)] = -1.f; return; }
-    const T v0 = op_unary<T>(op, cache[z]);
-    T s1 = 0, s2 = 0, sr = 0;
-    for (int s = lane; s < N; s += 32) {
-        const T v = op_unary<T>(op, cache[(size_t)s * U.P + z]) - v0;
-        s1 += v;
-        s2 = fma(v, v, s2);
-        sr = fma(v, tc[s], sr);
+    const double* row = val + (size_t)z * N;
+    const bool ok = subvalid[z];
+    T v0[kUnaryMax], s1[kUnaryMax], s2[kUnaryMax], sr[kUnaryMax];
+    const T x0 = (T)row[0];
+#pragma unroll
+    for (int k = 0; k < kUnaryMax; ++k) {
+        v0[k] = k < U.n_ops ? op_unary<T>(U.op[k], x0) : T(0);
+        s1[k] = s2[k] = sr[k] = T(0);
     }
-    s1 = warp_sum(s1); s2 = warp_sum(s2); sr = warp_sum(sr);
-    if (lane == 0)
-        scores[U.base[k] + (z - U.Q)] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
+    if (ok)
+        for (int s = lo + lane; s < hi; s += 32) {
+            const T x = (T)row[s], r = tc[s];
+#pragma unroll
+            for (int k = 0; k < kUnaryMax; ++k) {
+                if (k >= U.n_ops) break;
+                const T v = op_unary<T>(U.op[k], x) - v0[k];
+                s1[k] += v;
+                s2[k] = fma(v, v, s2[k]);
+                sr[k] = fma(v, r, sr[k]);
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < kUnaryMax; ++k) {
+        if (k >= U.n_ops) break;
+        const double a = warp_sum((double)s1[k]), b = warp_sum((double)s2[k]), c = warp_sum((double)sr[k]);
+        if (lane == 0) {
+            double* o = part + (((size_t)run * U.n_ops + k) * nz + (z - U.Q)) * 3;
+            o[0] = a; o[1] = b; o[2] = c;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_unary_finish(UnaryArgs U, const double* __restrict__ val, const TargetStats* st,
+                               const unsigned char* __restrict__ subvalid, int runs, const double* __restrict__ part,
+                               float* __restrict__ scores) {
+    const int64_t nz = U.P - U.Q;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nz * U.n_ops) return;
+    const int k = (int)(e / nz);
+    const int64_t z = U.Q + e % nz;
+    if (!subvalid[z]) { scores[U.base[k] + (z - U.Q)] = -1.f; return; }
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int run = 0; run < runs; ++run) {
+        const double* o = part + (((size_t)run * U.n_ops + k) * nz + (z - U.Q)) * 3;
+        a += o[0]; b += o[1]; c += o[2];
+    }
+    const T v0 = op_unary<T>(U.op[k], (T)val[(size_t)z * U.N]);
+    scores[U.base[k] + (z - U.Q)] = finalize<T>((T)a, (T)b, (T)c, v0, U.N, TgtView<T>::sum(st), TgtView<T>::sd(st));
 }
 
 // the top level's unary sections from cached operand rows: a CTA takes 32 operands and
@@ -964,8 +1008,8 @@ sisso_status fill_opcache(sisso_ctx* c) {
     const int grid = few ? (int)((n * 32 + 255) / 256) : (int)((n + 127) / 128);
     const int block = few ? 256 : 128;
     if (c->opcache32) {
-        if (few) k_fill_cache_w<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
-        else k_fill_cache<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc32, c->N, n, c->opcache32);
+        if (few) k_fill_cache_w<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache32);
+        else k_fill_cache<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache32);
         c->stats.launches++;
     }
     if (c->opcache64) {
@@ -1040,13 +1084,28 @@ sisso_status score_all(sisso_ctx* c, int precision) {
             if (sp.sec[q].level == L && sp.sec[q].op > DIV) { U.op[U.n_ops] = sp.sec[q].op; U.base[U.n_ops] = sp.sec[q].base; ++U.n_ops; }
         if (U.n_ops > 0) {
             const int gu = (int)((A.P - A.Q + 31) / 32);
-            if (gu >= 2 * c->sms) {
+            if (gu >= 2 * c->sms || !c->opval64) {
                 if (fp64) k_score_unary<double><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
                 else k_score_unary<float><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
-            } else {      // few operands: a warp per candidate splits the samples
-                const int gw = (int)(((A.P - A.Q) * U.n_ops * 32 + 255) / 256);
-                if (fp64) k_score_unary_w<double><<<gw, 256, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
-                else k_score_unary_w<float><<<gw, 256, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+            } else {      // few operands: warps over (operand, run of samples)
+                const int64_t nz = A.P - A.Q;
+                const int runs = (int)std::max<int64_t>(1, std::min<int64_t>((c->N + 1023) / 1024,
+                                                                             ((int64_t)c->sms * 32 + nz - 1) / nz));
+                double* part = nullptr;
+                const sisso_status su = check_cuda(
+                    c, cudaMallocAsync((void**)&part, sizeof(double) * 3 * (size_t)runs * U.n_ops * nz, c->stream),
+                    "unary partials");
+                if (su) return su;
+                const int gw = (int)((nz * runs * 32 + 255) / 256), gf = (int)((nz * U.n_ops + 255) / 256);
+                if (fp64) {
+                    k_score_unary_runs<double><<<gw, 256, 0, c->stream>>>(U, c->opval64, c->tc32, c->tc64, c->subvalid, runs, part);
+                    k_unary_finish<double><<<gf, 256, 0, c->stream>>>(U, c->opval64, c->tstats, c->subvalid, runs, part, c->scores);
+                } else {
+                    k_score_unary_runs<float><<<gw, 256, 0, c->stream>>>(U, c->opval64, c->tc32, c->tc64, c->subvalid, runs, part);
+                    k_unary_finish<float><<<gf, 256, 0, c->stream>>>(U, c->opval64, c->tstats, c->subvalid, runs, part, c->scores);
+                }
+                cudaFreeAsync(part, c->stream);
+                c->stats.launches++;
             }
             c->stats.launches++;
         }
@@ -1067,7 +1126,13 @@ sisso_status score_all(sisso_ctx* c, int precision) {
     cudaEventRecord(e1, c->stream);
     bool any = false;
     for (int o = 0; o < 4; ++o) any |= A.sec[o] >= 0;
-    if (any) {
+    const bool tc = any && c->tc_on && (precision == SISSO_PREC_MIXED_BF16 || precision == SISSO_PREC_MIXED_FP16);
+    if (tc) {
+        cudaEventRecord(e1, c->stream);
+        if ((st = tc_screen_pairs(c, A.sec))) return st;
+        c->stats.screen_pair_launches++;
+        c->stats.screen_tc = 1;
+    } else if (any) {
         std::vector<int2> tiles;
         pair_tiles(A.P, A.Q, A.nxp, tiles);
         int2* d_tiles = nullptr;
@@ -1128,6 +1193,7 @@ sisso_status score_all(sisso_ctx* c, int precision) {
     cudaEventCreate(&e3);
     cudaEventRecord(e3, c->stream);
     cudaEventSynchronize(e3);
+    if (tc && (st = tc_screen_status(c))) return st;
     c->stats.ms_screen += event_ms(e0, e3);
     c->stats.ms_screen_pair += event_ms(e1, e2);
     cudaEventDestroy(e3);
@@ -1161,7 +1227,11 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         cudaMemcpyAsync(c->S_sorted, Ss.data(), sizeof(int64_t) * n_prev, cudaMemcpyHostToDevice, c->stream);
     const bool fp_kernel64 = c->opts.precision == SISSO_PREC_FP64;
     const double eps = fp_kernel64 ? kScoreErr64 : kScoreErr32;   // bound on |score_kernel - score_FP64|
-    int64_t M = c->opts.survivors > 0 ? c->opts.survivors : std::max<int64_t>(4096, 32LL * k);
+    // default window: max(4096, 32 k) candidates, but at most about 2^26 sample evaluations of
+    // FP64 re-scoring (the re-score costs M x N) and never below 5 k
+    int64_t M = c->opts.survivors > 0
+                    ? c->opts.survivors
+                    : std::max<int64_t>(5LL * k, std::min<int64_t>(std::max<int64_t>(4096, 32LL * k), (1LL << 26) / c->N));
     const int64_t n = c->n_feat;
     const int gridS = std::max(1, c->sms * 8);
     cudaEvent_t q[5];

@@ -41,6 +41,7 @@ EXPORTS = [
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
     "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen", "sisso_prefix_training",
     "sisso_batch_set_wait_limit", "sisso_l0_learned_certified", "sisso_set_proposal_ex",
+    "sisso_bilinear_tc",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -59,7 +60,7 @@ class Opts(C.Structure):
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
                 ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("wait_limit_ns", C.c_int64),
-                ("units", C.c_void_p)]
+                ("units", C.c_void_p), ("screen_cores", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -72,7 +73,8 @@ class Stats(C.Structure):
                 ("ms_walk", C.c_double), ("walk_visited", C.c_int64), ("walk_dup_checks", C.c_int64),
                 ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
                 ("ms_fit", C.c_double), ("ms_l0_enum", C.c_double), ("l0_enum_launches", C.c_int),
-                ("l0_candidates", C.c_int64), ("certified_prefixes", C.c_int64)]
+                ("l0_candidates", C.c_int64), ("certified_prefixes", C.c_int64),
+                ("screen_tc", C.c_int), ("tc_keys_raised", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -145,6 +147,7 @@ def load() -> C.CDLL:
                                   C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_sizes.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, i64p]
     L.sisso_gram_tc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.sisso_bilinear_tc.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
                                           C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
@@ -254,6 +257,21 @@ def gram_tc(Z, yc, sdy: float, kind: int = PREC_MIXED_BF16):
     return G, b
 
 
+def bilinear_tc(Lrows, Rrows, kind: int = PREC_MIXED_FP16):
+    """sum_s L[i, s] R[j, s] from split 16-bit tensor-core products (sisso_bilinear_tc)."""
+    Lrows = np.ascontiguousarray(Lrows, dtype=np.float64)
+    Rrows = np.ascontiguousarray(Rrows, dtype=np.float64)
+    m, N = Lrows.shape
+    n = Rrows.shape[0]
+    assert Rrows.shape[1] == N
+    out = np.zeros((m, n), dtype=np.float64)
+    st = load().sisso_bilinear_tc(C.c_void_p(Lrows.ctypes.data), C.c_void_p(Rrows.ctypes.data), m, n, N, kind,
+                                  C.c_void_p(out.ctypes.data))
+    if st:
+        raise SissoError(st, "bilinear_tc")
+    return out
+
+
 def l0_search_noalloc(G, b, syy: float, N: int, D: int, gid, precision: int = PREC_FP32, stream=None):
     """Exhaustive l0 over every D-subset of len(b) standardised features without a context
     and without allocating device memory (sisso_l0_search_noalloc): for callers that may
@@ -286,7 +304,8 @@ class Sisso:
     def __init__(self, X, y, op_set: int, rung: int, sis_size: int, max_dim: int,
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
-                 sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None):
+                 sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None,
+                 screen_cores: bool = False):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -297,6 +316,7 @@ class Sisso:
         o.precision, o.grammar, o.survivors = precision, grammar, survivors
         o.max_band, o.band_rel, o.device = max_band, band_rel, device
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
+        o.screen_cores = int(bool(screen_cores))
         if prescreen is not None:    # (SISSO_PRESCREEN_MI or _SPEARMAN, quantile kept)
             o.prescreen, o.prescreen_quantile = int(prescreen[0]), float(prescreen[1])
         ulab = None

@@ -72,6 +72,9 @@ SCORE_CASES = [
     ("rung3-nxp", lambda: _lognormal_problem(7, 200, 4), ALL9, 3, 1),
     ("rung3-eq2", lambda: _lognormal_problem(8, 77, 2), ["+", "-", "*", "/", "sqrt", "^2"], 3, 0),
     ("rung1", lambda: _lognormal_problem(9, 33, 40), ALL9, 1, 0),
+    # six primaries correlated 0.999: operands such as x2 - x4 cancel, and 1/(x2 - x4) or
+    # x1/(x2 - x4) is dominated by the samples where they nearly vanish
+    ("collinear", lambda: (inputs.workload3(0, N=3000).X, inputs.workload3(0, N=3000).y), ALL9, 2, 0),
 ]
 
 
