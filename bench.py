@@ -230,6 +230,31 @@ L0_FLOP_PER_SUBSET = {1: 3, 2: 11, 3: 26, 4: 50, 5: 85}   # full Cholesky solve 
 L0_FP32_OPS_PER_SUBSET = {3: 8, 4: 9, 5: 10}              # tiled enumeration: FP32 arithmetic per subset (filter included)
 
 
+_ALU_PEAK = {}
+
+
+def alu_peak(sms, mhz):
+    """The FP32 pipe's peak for the ALU-bound kernels' roofline: the larger of the measured
+    FP32 and paired-FP32 FMA rates (sisso_measure_alu_peak, every SM busy, CUDA events),
+    measured once before any timed region; the derived SMs x 128 lanes x 2 x clock if the
+    measurement fails."""
+    if not _ALU_PEAK:
+        from paper_2410_01752_gb300 import sisso
+        derived = sms * 128 * 2 * mhz * 1e6 / 1e12
+        try:
+            f32 = sisso.measure_alu_peak(sisso.ALU_FP32)
+            f32x2 = sisso.measure_alu_peak(sisso.ALU_FP32X2)
+            f64 = sisso.measure_alu_peak(sisso.ALU_FP64)
+            _ALU_PEAK.update(peak=max(f32, f32x2), fp32=f32, fp32x2=f32x2, fp64=f64, derived=derived,
+                             source=f"measured: max of FP32 FMA ({f32:.1f}) and paired FP32 FMA ({f32x2:.1f}) "
+                                    f"TFLOP/s, sisso_measure_alu_peak (derived {sms} SMs x 128 lanes x 2 x "
+                                    f"{mhz:.0f} MHz = {derived:.1f})")
+        except Exception as e:      # noqa: BLE001
+            _ALU_PEAK.update(peak=derived, derived=derived,
+                             source=f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz ({e})")
+    return _ALU_PEAK
+
+
 def l0_roofline(s, D, peak, sms, mhz, reps=3):
     """The tiled l0 enumeration alone, one launch over every D-subset of the fit's final
     subspace (the fit's own last step), timed with CUDA events inside the library."""
@@ -255,7 +280,12 @@ def l0_roofline(s, D, peak, sms, mhz, reps=3):
             "fp32_issue_frac": L0_FP32_OPS_PER_SUBSET.get(D, 0) * n_sub / t / (sms * 128 * mhz * 1e6),
             "fp32_issue_note": f"{L0_FP32_OPS_PER_SUBSET.get(D, 0)} FP32 arithmetic instructions per subset in the "
                                "prefix-reduced form, against SMs x 128 lanes x clock",
-            "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x measured max SM clock"}
+            "peak_source": alu_peak(sms, mhz)["source"]}
+
+
+def sisso_sizes(P):
+    from paper_2410_01752_gb300 import sisso
+    return sisso.space_sizes(P.d, P.op_set, P.rung, P.grammar)
 
 
 def form_mixed(args):
@@ -287,9 +317,24 @@ def form_mixed(args):
                 ms.append(e0.elapsed_time(e1))
             st = s.stats()
             out[name] = {"time_to_descriptor_ms": sum(ms) / len(ms), "descriptor": d[-1].ids, "rmse": d[-1].rmse,
-                         "ms_gram": st["ms_gram"], "ms_screen": st["ms_screen"], "ms_l0": st["ms_l0"],
                          "gpu_launches": st["launches"],
+                         "phase_ms": {k: st[k] for k in ("ms_screen", "ms_screen_pair", "ms_select", "ms_rescore",
+                                                          "ms_walk", "ms_gram", "ms_l0", "ms_refit")},
+                         "screen_tensor_cores": bool(st["screen_tc"]), "tc_keys_raised": st["tc_keys_raised"],
+                         "survivors_rescored": st["survivors_rescored"],
                          "parity": compare_fit([s.sis(t) for t in range(1, len(d) + 1)], d, rec, tol) if rec else None}
+            if st["screen_tc"]:
+                # split 16-bit products of the screening: one target-independent product
+                # (2 Pp x 4 Pp) per fit and one (Pp x 2 Pp) per step, K = padded samples x parts
+                Pp = -(-int(sisso_sizes(P)[1]) // 128) * 128
+                Kp = -(-P.N // 64) * 64
+                parts = 6 if prec == PREC_MIXED_BF16 else 3
+                flop = 2.0 * (8 * Pp * Pp + len(d) * 2 * Pp * Pp) * Kp * parts
+                pk = peaks()
+                out[name]["screen_tc_products"] = {
+                    "flop_per_fit": flop, "tflops_over_pair_stage": flop / (st["ms_screen_pair"] / 1e3) / 1e12,
+                    "note": "over the whole tensor-core pair stage (row preparation, products, chunk sums, keys)",
+                    "bf16_peak_measured": pk.get("bf16_tflops")}
     for k in ("mixed_bf16", "mixed_fp16"):
         out[k]["speedup_vs_plain"] = out["plain_fp32"]["time_to_descriptor_ms"] / out[k]["time_to_descriptor_ms"]
         out[k]["rmse_rel_diff_vs_plain"] = abs(out[k]["rmse"] - out["plain_fp32"]["rmse"]) / out["plain_fp32"]["rmse"]
@@ -646,11 +691,11 @@ def run_batch(args, rank: int):
     pk = peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    peak = alu_peak(sms, mhz)["peak"]
     achieved = flop / (mean_ms / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": "k_batch (persistent, all stages)", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_batch_traffic(tune),
-            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (measured max SM clock)",
+            "peak_source": alu_peak(sms, mhz)["source"],
             "flop_per_launch": flop, "launch_ms": mean_ms,
             "algorithmic_unit": f"{FP32_FLOP_PER_CAND_SAMPLE} flop per candidate-sample of screening, every task and step run",
             "score_stage_frac": None}
@@ -857,11 +902,13 @@ def main():
     pk = peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    apk = alu_peak(sms, mhz)
+    peak = apk["peak"]
     full_size = (P.N, P.d) == (1000, 10)
     roof = {"bound": "alu", "kernel": "k_score_pairs<float>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": captured_traffic() if full_size else None,
-            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz (measured max SM clock)",
+            "peak_source": apk["source"], "peak_fp32_derived": apk["derived"],
+            "frac_of_derived": achieved / apk["derived"], "fp64_measured_tflops": apk.get("fp64"),
             "flop_per_launch": flop_launch, "launch_ms": avg_launch_s * 1e3,
             "algorithmic_unit": f"{FP32_FLOP_PER_CAND_SAMPLE} flop per candidate-sample x {cand_pair} candidates x {P.N} samples"}
 

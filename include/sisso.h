@@ -295,6 +295,12 @@ sisso_status sisso_gram_tc(const double* Z, const double* yc, double sdy, int n,
  * Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT (a bounded wait ran out). */
 sisso_status sisso_bilinear_tc(const double* L, const double* R, int m, int n, int N, int kind, double* out);
 
+/* Measured FMA throughput of the current device in TFLOP/s, the denominator of the ALU-bound
+ * kernels' roofline: kind 0 FP32 (fma.rn.f32, 2 flop), 1 paired FP32 (fma.rn.f32x2, 4 flop),
+ * 2 FP64.  Every SM busy with independent chains; best of three timed launches (about 0.1 s
+ * on the legacy default stream).  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA. */
+sisso_status sisso_measure_alu_peak(int kind, double* tflops);
+
 /* ---- batched multi-task form ----------------------------------------------------------
  *
  * Many independent SISSO problems (each §2.1-2.3: feature space Eq. 2, SIS Eqs. 5-6, l0

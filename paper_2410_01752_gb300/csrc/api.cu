@@ -51,7 +51,7 @@ void free_all(sisso_ctx* c) {
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
                     c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
                     c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info,
-                    c->unit_ok, c->unit_mask};
+                    c->unit_ok, c->unit_mask, c->opinv64};
     for (void* p : bufs)
         if (p) cudaFree(p);
     tc_screen_free(c);
@@ -226,6 +226,10 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         // FP64 operand values (feature-major) for the exact re-score and duplicate checks
         if ((size_t)c->space.phi[rung - 1] * Nn * sizeof(double) <= ((size_t)16 << 30)) {
             if ((st = dalloc(c, c->opval64, (size_t)c->space.phi[rung - 1] * Nn, "opval64"))) return bail(st);
+            // their reciprocals when they fit 8 GB (the FP64 re-score divides by operands)
+            if ((size_t)c->space.phi[rung - 1] * Nn * sizeof(double) <= ((size_t)8 << 30) &&
+                (st = dalloc(c, c->opinv64, (size_t)c->space.phi[rung - 1] * Nn, "opinv64")))
+                return bail(st);
         }
     }
     if ((st = check_cuda(c, cudaMallocHost(&c->walk_h, sizeof(WalkResult)), "walk_h")) ||

@@ -250,6 +250,7 @@ constexpr double kCancelRel = 1e-9;    // root +/- with max|v| <= this * max(|a|
 struct OpRef {
     int64_t a, b;   // rows (b = -1: unary or direct)
     int op;         // -1: row a itself
+    const double* inv = nullptr;   // optional rows of 1/x (same layout as V): a / b as a * (1/b)
 };
 
 __host__ __device__ inline bool make_opref(const Space& sp, int64_t id, OpRef& r) {
@@ -267,6 +268,12 @@ __device__ __forceinline__ double opref_val(const OpRef& r, const double* __rest
     const double x = V[(size_t)r.a * N + s];
     if (r.op < 0) { mag = fabs(x); return x; }
     if (r.b < 0) { const double v = op_unary<double>(r.op, x); mag = fabs(v); return v; }
+    if (r.op == DIV && r.inv) {       // one rounding more than x / y (relative 1.1e-16); x / y where 1/y overflows
+        const double q = r.inv[(size_t)r.b * N + s];
+        const double v = isfinite(q) ? x * q : x / V[(size_t)r.b * N + s];
+        mag = fabs(v);
+        return v;
+    }
     const double y = V[(size_t)r.b * N + s];
     const double v = op_binary<double>(r.op, x, y);
     mag = (r.op == ADD || r.op == SUB) ? fabs(x) + fabs(y) : fabs(v);
@@ -468,6 +475,7 @@ struct sisso_ctx {
     double* tc_C1 = nullptr;
     double* tc_C2 = nullptr;
     double* tc_recip = nullptr;
+    double* opinv64 = nullptr;         // 1/x of every FP64 operand value (division in the FP64 re-score)
     int* tc_err = nullptr;
     unsigned long long* tc_raised = nullptr;
 };

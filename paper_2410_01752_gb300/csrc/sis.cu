@@ -47,6 +47,12 @@ __global__ void k_fill_val64(const Space* __restrict__ sp, const double* __restr
         V[(size_t)id * N + s] = ok ? eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : NAN;
 }
 
+// 1/x of every FP64 operand value (the re-score's divisions become products)
+__global__ void k_fill_inv64(const double* __restrict__ V, int64_t total, double* __restrict__ inv) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        inv[e] = 1.0 / V[e];
+}
+
 __global__ void k_subvalid(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, int64_t lo,
                            int64_t hi, const double* __restrict__ V, const unsigned char* __restrict__ unit_ok,
                            unsigned char* __restrict__ valid) {
@@ -154,6 +160,27 @@ __global__ void k_fill_cache(const Space* __restrict__ sp, const double* __restr
     for (int s = 0; s < N; ++s)
         cache[(size_t)s * n_ids + id] =
             ok ? (T)eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : T(NAN);
+}
+
+// the same cache as the transpose of the feature-major FP64 values (the same evaluation,
+// rounded once to T): 32 x 32 tiles through shared memory, both sides coalesced
+template <typename T>
+__global__ void k_cache_from_val64(const double* __restrict__ V, int N, int64_t n_ids, T* __restrict__ cache) {
+    __shared__ double t[32][33];
+    const int64_t id0 = (int64_t)blockIdx.y * 32;
+    const int s0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t id = id0 + r;
+        const int s = s0 + tx;
+        t[r][tx] = id < n_ids && s < N ? V[(size_t)id * N + s] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int s = s0 + r;
+        const int64_t id = id0 + tx;
+        if (id < n_ids && s < N) cache[(size_t)s * n_ids + id] = (T)t[tx][r];
+    }
 }
 
 // ids [lo, hi) below the top level (P = |phi_{L-1}| of them) scored from the cache: one
@@ -407,10 +434,88 @@ __global__ void k_rescore(const Space* __restrict__ sp, const double* __restrict
                           const double* __restrict__ tc, const TargetStats* __restrict__ st,
                           const int64_t* __restrict__ ids, int n, const unsigned char* __restrict__ subvalid,
                           const double* __restrict__ V, double* score, double* mean_out, double* sd_out,
-                          int* valid_out, double* __restrict__ probe, double* __restrict__ zc) {
+                          int* valid_out, double* __restrict__ probe, double* __restrict__ zc,
+                          const double* __restrict__ Vinv) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n) return;
-    rescore_one(sp, Xc, N, N, tc, st, ids[w], w, subvalid, V, score, mean_out, sd_out, valid_out, probe, zc);
+    rescore_one(sp, Xc, N, N, tc, st, ids[w], w, subvalid, V, score, mean_out, sd_out, valid_out, probe, zc, false,
+                Vinv);
+}
+
+// The same re-score with one CTA of kRescoreThreads per id (many samples): the warp form
+// keeps too few independent FP64 chains per SM to cover the pipe's latency.  Sums are
+// combined warp by warp in a fixed order.
+constexpr int kRescoreThreads = 256;
+__global__ void __launch_bounds__(kRescoreThreads)
+k_rescore_cta(const Space* __restrict__ sp, int N, const double* __restrict__ tc, const TargetStats* __restrict__ st,
+              const int64_t* __restrict__ ids, const unsigned char* __restrict__ subvalid, const double* __restrict__ V,
+              const double* __restrict__ Vinv, double* score, double* mean_out, double* sd_out, int* valid_out,
+              double* __restrict__ probe, double* __restrict__ zc) {
+    constexpr int W = kRescoreThreads / 32;
+    __shared__ double red[W][5];
+    __shared__ int red_bad[W];
+    const int w = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    const int64_t id = ids[w];
+    int level, op; int64_t a, b;
+    const int64_t Pbot = sp->phi[sp->rung - 1];
+    OpRef ref{};
+    bool built = decode(*sp, id, level, op, a, b) && make_opref(*sp, id, ref);
+    ref.inv = Vinv;
+    if (built && id < Pbot && !subvalid[id]) built = false;
+    if (built && id >= Pbot && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;
+    if (!built) {
+        if (t == 0) { score[w] = -1.0; valid_out[w] = 0; mean_out[w] = 0; sd_out[w] = 0; }
+        if (t < kProbes) probe[(size_t)w * kProbes + t] = 0.0;
+        return;
+    }
+    double* z = zc ? zc + (size_t)w * N : nullptr;
+    double mag0;
+    const double v0 = opref_val(ref, V, N, 0, mag0);
+    double s1 = 0.0, s2 = 0.0, sc = 0.0, mx = 0.0, mo = 0.0;
+    int bad = 0;
+    for (int i = t; i < N; i += kRescoreThreads) {
+        double mag;
+        const double v = opref_val(ref, V, N, i, mag);
+        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
+        const double u = v - v0;
+        s1 += u;
+        s2 += u * u;
+        sc += u * tc[i];
+        mx = fmax(mx, fabs(v));
+        mo = fmax(mo, mag);
+        if (z) z[i] = v;
+    }
+    bad = warp_or(bad);
+    s1 = warp_sum(s1); s2 = warp_sum(s2); sc = warp_sum(sc); mx = warp_max(mx); mo = warp_max(mo);
+    if (lane == 0) { red[wp][0] = s1; red[wp][1] = s2; red[wp][2] = sc; red[wp][3] = mx; red[wp][4] = mo; red_bad[wp] = bad; }
+    __syncthreads();
+    s1 = red[0][0]; s2 = red[0][1]; sc = red[0][2]; mx = red[0][3]; mo = red[0][4]; bad = red_bad[0];
+    for (int q = 1; q < W; ++q) {
+        s1 += red[q][0]; s2 += red[q][1]; sc += red[q][2];
+        mx = fmax(mx, red[q][3]); mo = fmax(mo, red[q][4]); bad |= red_bad[q];
+    }
+    const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
+    const bool cancelled = top_addsub && mx <= kCancelRel * mo;
+    const double mean = v0 + s1 / N;
+    const double var = s2 / N - (s1 / N) * (s1 / N);
+    const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
+    const int ok = !bad && !cancelled && sd > kConstRel * mx;
+    const double inv = ok ? 1.0 / sd : 0.0;
+    if (z) {
+        for (int i = t; i < N; i += kRescoreThreads) z[i] = (z[i] - mean) * inv;
+        __syncthreads();
+    }
+    if (t < kProbes) {
+        const int i = (int)(((int64_t)t * N) / kProbes);
+        double mag;
+        probe[(size_t)w * kProbes + t] = z ? z[i] : (opref_val(ref, V, N, i, mag) - mean) * inv;
+    }
+    if (t == 0) {
+        valid_out[w] = ok;
+        mean_out[w] = mean;
+        sd_out[w] = sd;
+        score[w] = ok ? fabs(sc - (s1 / N) * st->tsum) / ((double)N * sd * st->sd) : -1.0;
+    }
 }
 
 // sort keys: valid survivors not in S (and, with units, dimensionally consistent) get
@@ -586,38 +691,50 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
                               const int64_t* __restrict__ sv_ids, const double* __restrict__ sv_mean,
                               const double* __restrict__ sv_sd, const double* __restrict__ zc,
                               const double* __restrict__ V, const int* __restrict__ dup_list,
-                              const int* __restrict__ dup_cnt, unsigned char* __restrict__ dup_ok) {
+                              const int* __restrict__ dup_cnt, unsigned char* __restrict__ dup_ok,
+                              const double* __restrict__ Vinv) {
     const int lane = threadIdx.x & 31;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_sorted; i += (gridDim.x * blockDim.x) >> 5) {
+    // one warp per (sorted entry, listed partner)
+    for (int64_t wi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wi < (int64_t)n_sorted * kDupSlots;
+         wi += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int i = (int)(wi / kDupSlots), q = (int)(wi % kDupSlots);
         const int raw = dup_cnt[i];
         const int cnt = min(raw < 0 ? -raw - 1 : raw, n_confirm(N));
-        if (cnt <= 0) continue;
+        if (q >= cnt) continue;
         const int src = ssrc[i];
         Prog pc;
         OpRef rc{};
         if (!zc) { if (V) make_opref(*sp, sid[i], rc); else build_prog(*sp, sid[i], pc); }
+        rc.inv = Vinv;
         const double mc = sv_mean[src], dc = sv_sd[src];
-        for (int q = 0; q < cnt; ++q) {
+        {
             const int m = dup_list[(size_t)i * kDupSlots + q];
             Prog pm;
             OpRef rm{};
             if (!zc) { if (V) make_opref(*sp, sv_ids[m], rm); else build_prog(*sp, sv_ids[m], pm); }
+            rm.inv = Vinv;
             const double mm = sv_mean[m], dm = sv_sd[m];
             double e1 = 0.0, e2 = 0.0;
-            for (int t = lane; t < N; t += 32) {
-                double za, zb, mg;
-                if (zc) {
-                    za = zc[(size_t)src * N + t];
-                    zb = zc[(size_t)m * N + t];
-                } else if (V) {
-                    za = (opref_val(rc, V, N, t, mg) - mc) / dc;
-                    zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
-                } else {
-                    za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
-                    zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+            // the pair is a duplicate iff max|za - zb| or max|za + zb| stays within kDupTol:
+            // the warp stops as soon as both have exceeded it somewhere (the common case)
+            for (int t0 = 0; t0 < N; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < N) {
+                    double za, zb, mg;
+                    if (zc) {
+                        za = zc[(size_t)src * N + t];
+                        zb = zc[(size_t)m * N + t];
+                    } else if (V) {
+                        za = (opref_val(rc, V, N, t, mg) - mc) / dc;
+                        zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
+                    } else {
+                        za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
+                        zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+                    }
+                    e1 = fmax(e1, fabs(za - zb));
+                    e2 = fmax(e2, fabs(za + zb));
                 }
-                e1 = fmax(e1, fabs(za - zb));
-                e2 = fmax(e2, fabs(za + zb));
+                if (__any_sync(0xffffffffu, e1 > kDupTol) && __any_sync(0xffffffffu, e2 > kDupTol)) break;
             }
             e1 = warp_max(e1);
             e2 = warp_max(e2);
@@ -999,6 +1116,12 @@ sisso_status fill_val64(sisso_ctx* c) {
     const int64_t n = c->space.phi[c->rung - 1];
     k_fill_val64<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opval64);
     c->stats.launches++;
+    if (c->opinv64) {
+        const int64_t total = n * (int64_t)c->N;
+        k_fill_inv64<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sms * 16, (total + 255) / 256)), 256, 0,
+                       c->stream>>>(c->opval64, total, c->opinv64);
+        c->stats.launches++;
+    }
     return check_cuda(c, cudaGetLastError(), "fill_val64");
 }
 
@@ -1007,6 +1130,13 @@ sisso_status fill_opcache(sisso_ctx* c) {
     const bool few = n < 65536;     // few features: a warp per feature splits the samples
     const int grid = few ? (int)((n * 32 + 255) / 256) : (int)((n + 127) / 128);
     const int block = few ? 256 : 128;
+    if (c->opval64 && (c->opcache32 || c->opcache64) && (n + 31) / 32 <= 65535) {   // fill_val64 ran first
+        const dim3 grid2((unsigned)((c->N + 31) / 32), (unsigned)((n + 31) / 32));
+        if (c->opcache32) k_cache_from_val64<float><<<grid2, 256, 0, c->stream>>>(c->opval64, c->N, n, c->opcache32);
+        if (c->opcache64) k_cache_from_val64<double><<<grid2, 256, 0, c->stream>>>(c->opval64, c->N, n, c->opcache64);
+        c->stats.launches++;
+        return check_cuda(c, cudaGetLastError(), "fill_opcache");
+    }
     if (c->opcache32) {
         if (few) k_fill_cache_w<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache32);
         else k_fill_cache<float><<<grid, block, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opcache32);
@@ -1268,10 +1398,16 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         const int nr = ns + n_prev;
         cudaEventRecord(q[1], c->stream);
         double* zc = (int64_t)nr <= c->zcap ? c->zcache : nullptr;   // cache the vectors if they fit
-        k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->tc64, c->tstats,
-                                                                 c->surv_ids, nr, c->subvalid, c->opval64,
-                                                                 c->surv_score, c->surv_mean, c->surv_sd,
-                                                                 c->surv_valid, c->surv_probe, zc);
+        if (c->opval64 && c->N >= 4096 && nr > 0)
+            k_rescore_cta<<<nr, kRescoreThreads, 0, c->stream>>>(c->space_dev, c->N, c->tc64, c->tstats, c->surv_ids,
+                                                                 c->subvalid, c->opval64, c->opinv64, c->surv_score,
+                                                                 c->surv_mean, c->surv_sd, c->surv_valid,
+                                                                 c->surv_probe, zc);
+        else
+            k_rescore<<<(nr * 32 + 255) / 256, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->tc64, c->tstats,
+                                                                     c->surv_ids, nr, c->subvalid, c->opval64,
+                                                                     c->surv_score, c->surv_mean, c->surv_sd,
+                                                                     c->surv_valid, c->surv_probe, zc, c->opinv64);
         int n_pad = 1;
         while (n_pad < std::max(ns, 1)) n_pad <<= 1;
         k_sort_keys<<<(n_pad + 255) / 256, 256, 0, c->stream>>>(c->surv_ids, c->surv_score, c->surv_valid, ns,
@@ -1298,9 +1434,9 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         k_dup_find<<<(int)(((int64_t)n_pad * 32 + 255) / 256), 256, 0, c->stream>>>(c->sort_score, c->sort_src, c->sort_id, n_pad, c->surv_score,
                                                                c->surv_sd, c->surv_probe, ns, n_prev, c->dup_list,
                                                                c->dup_cnt);
-        k_dup_confirm<<<std::max(1, std::min(c->sms * 16, (n_pad * 32 + 255) / 256)), 256, 0, c->stream>>>(
+        k_dup_confirm<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sms * 32, ((int64_t)n_pad * kDupSlots * 32 + 255) / 256)), 256, 0, c->stream>>>(
             c->space_dev, c->Xc64, c->N, c->sort_src, c->sort_id, n_pad, c->surv_ids, c->surv_mean, c->surv_sd, zc,
-            c->opval64, c->dup_list, c->dup_cnt, c->dup_ok);
+            c->opval64, c->dup_list, c->dup_cnt, c->dup_ok, c->opinv64);
         cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmem);
         const size_t wsm = n_pad <= kWalkStage && ns <= kWalkStage ? kWalkSmem : 0;
         k_walk<<<1, kWalkThreads, wsm, c->stream>>>(c->space_dev, c->Xc64, c->N, c->sort_score, c->sort_id, c->sort_src,

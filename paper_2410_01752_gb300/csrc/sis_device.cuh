@@ -318,13 +318,14 @@ __device__ __forceinline__ void rescore_one(const Space* sp, const double* Xc, i
                                             const TargetStats* st, int64_t id, int w,
                                             const unsigned char* subvalid, const double* V, double* score,
                                             double* mean_out, double* sd_out, int* valid_out, double* probe,
-                                            double* zc, bool zc_raw = false) {
+                                            double* zc, bool zc_raw = false, const double* Vinv = nullptr) {
     const int lane = threadIdx.x & 31;
     Prog p;
     int level, op; int64_t a, b;
     const int64_t Pbot = sp->phi[sp->rung - 1];
     OpRef ref{};
     bool built = decode(*sp, id, level, op, a, b) && (V ? make_opref(*sp, id, ref) : build_prog(*sp, id, p));
+    ref.inv = Vinv;
     if (built && id < Pbot && !subvalid[id]) built = false;                                  // exact, recursive
     if (built && id >= Pbot && (!subvalid[a] || (b >= 0 && !subvalid[b]))) built = false;   // invalid operand
     if (!built) {

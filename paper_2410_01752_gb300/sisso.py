@@ -41,7 +41,7 @@ EXPORTS = [
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
     "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen", "sisso_prefix_training",
     "sisso_batch_set_wait_limit", "sisso_l0_learned_certified", "sisso_set_proposal_ex",
-    "sisso_bilinear_tc",
+    "sisso_bilinear_tc", "sisso_measure_alu_peak",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -148,6 +148,7 @@ def load() -> C.CDLL:
     L.sisso_space_sizes.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, i64p]
     L.sisso_gram_tc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp]
     L.sisso_bilinear_tc.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    L.sisso_measure_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
                                           C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
@@ -270,6 +271,18 @@ def bilinear_tc(Lrows, Rrows, kind: int = PREC_MIXED_FP16):
     if st:
         raise SissoError(st, "bilinear_tc")
     return out
+
+
+ALU_FP32, ALU_FP32X2, ALU_FP64 = 0, 1, 2
+
+
+def measure_alu_peak(kind: int = ALU_FP32) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (sisso_measure_alu_peak)."""
+    v = C.c_double()
+    st = load().sisso_measure_alu_peak(int(kind), C.byref(v))
+    if st:
+        raise SissoError(st, "measure_alu_peak")
+    return v.value
 
 
 def l0_search_noalloc(G, b, syy: float, N: int, D: int, gid, precision: int = PREC_FP32, stream=None):
