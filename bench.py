@@ -348,6 +348,64 @@ def form_mixed(args):
             "parity_ok": all(v["parity"] and v["parity"]["ok"] for v in out.values())}
 
 
+def form_ensemble(args):
+    """The paper's ensemble timing workload (§4.5): 30 models, each fitted on a disjoint
+    100-sample subset of the four-term problem (k = 20, D <= 4), as the 30 tasks of one
+    batched launch; every model against the oracle's stored fit of its subset."""
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import ensemble, inputs, sisso
+    P = inputs.ensemble_problem(0)
+    rows = inputs.partition_rows(P.N, 30, 100, 0)
+    probs = [(P.X[r], P.y[r]) for r in rows]
+    stream = torch.cuda.current_stream()
+    with sisso.Batch(probs, P.op_set, P.rung, P.sis_size, P.max_dim, stream=stream) as b:
+        b.run(copies=False)
+        ms = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(copies=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res = b.results()
+    # end to end: row gather on the host, batch creation (plan, arena, graphs), copies, run, results
+    tms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        models = ensemble.fit_rows(P.X, P.y, rows, P.op_set, P.rung, P.sis_size, P.max_dim, stream=stream)
+        tms.append(time.perf_counter() - t0)
+    assert [[d.ids for d in m.dims] for m in models] == [[d.ids for d in dims] for _, dims in res]
+    gold = golden_fit("ensemble") or []
+    parity = None
+    if gold:
+        eq = sum(int([d.ids for d in dims] == [g["ids"] for g in rec["dims"]]) for (_, dims), rec in zip(res, gold))
+        err = max((abs(a - b) / max(abs(b), 1e-300) for (_, dims), rec in zip(res, gold)
+                   for d, g in zip(dims, rec["dims"]) for a, b in zip(d.coef, g["coef"])), default=0.0)
+        parity = {"tasks": len(gold), "descriptors_equal": eq, "coef_max_rel_err": err,
+                  "ok": eq == len(gold) and err <= 1e-6, "tolerance_rel": 1e-6,
+                  "golden": "tests/golden/ensemble_oracle.json"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        sp = oracle.Space(P.d, P.op_set, P.rung, P.grammar)
+        t0 = time.perf_counter()
+        for r in rows:
+            oracle.fit(P.X[r], P.y[r], sp, P.sis_size, P.max_dim)
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt, "unit": "s", "cores": cores(), "kind": "oracle",
+               "sample": "all 30 models fitted by the FP64 oracle, one after another (its l0 threaded)"}
+    return {"workload": P.name + ", 30 disjoint subsets of 100 samples", "metric": "time to train the ensemble",
+            "unit": "ms", "launch_ms": float(np.median(ms)), "e2e_ms": 1e3 * float(np.median(tms)),
+            "e2e_note": "host row gather, batch creation (plan, arena, CUDA graphs), copies, launch, results",
+            "paper_seconds": {"fortran_sisso_1cpu": 182.43, "torchsisso_gpu_a100": 51.32,
+                              "note": "the paper's ensemble timing table (another machine: context, not a target)"},
+            "gpu_launches": 1, "cpu_baseline": cpu, "parity": parity}
+
+
 def form_batched(args):
     """The batched multi-task form: 512 tasks in one persistent launch (CUDA graph), launch
     shape from the autotuner; every task's descriptors against the oracle's stored fits."""
@@ -930,7 +988,7 @@ def main():
     forms = None
     if not args.no_forms and world == 1:
         forms = {"mixed_precision": form_mixed(args), "batched": form_batched(args),
-                 "learned_proposal": form_learned(args)}
+                 "learned_proposal": form_learned(args), "ensemble": form_ensemble(args)}
 
     d_last = desc[-1] if desc else None
     line = {

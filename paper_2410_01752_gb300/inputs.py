@@ -18,6 +18,8 @@ Workloads (x: primary features, N samples x d; y: target):
                                                                                 (rung 2, k=60, D<=5)
   5  one of 512 tasks: N ~ U{20..2000}, d ~ U{4..12}, x ~ U[0.5, 5], 1-3 planted rung-2
      terms from a fixed menu, c ~ U(-5, 5), 0.5% noise                          (rung 2, k=50, D<=3)
+  6  the ensemble timing workload (§4.5): N=3000, d=4, x ~ U[1,5], y = x1^4 + x2^3 + x3^2
+     + x4 + 0.1% noise, cut into 30 subsets of 100 samples                       (rung 2, k=20, D<=4)
   The paper's own workloads are of the same kind: x in [1,5], small N, 3-4 term targets
   (§4.1, §4.5).
 """
@@ -95,6 +97,18 @@ def workload3(p: int = 0, N: int = 65536, sis_size: int = 200, max_dim: int = 3)
                    f"mixed N={N} d=12 collinear rung2 k={sis_size} D<={max_dim}")
 
 
+def ensemble_problem(p: int = 0, N: int = 3000, sis_size: int = 20, max_dim: int = 4) -> Problem:
+    """The ensemble timing workload (§4.5): the first four-term model x1^4 + x2^3 + x3^2 + x4,
+    x ~ U[1, 5], 3000 samples to be cut into 30 subsets of 100, k = 20 (noise 0.1% of the
+    clean signal's std, so that no two descriptors fit exactly)."""
+    r = _rng(6, p)
+    X = r.uniform(1.0, 5.0, size=(N, 4))
+    clean = X[:, 0] ** 4 + X[:, 1] ** 3 + X[:, 2] ** 2 + X[:, 3]
+    y = clean + r.normal(0.0, 1e-3 * clean.std(), size=N)
+    return Problem(X, y, OPS9, 2, sis_size, max_dim, GRAMMAR_EQ2,
+                   f"ensemble four-term N={N} d=4 rung2 k={sis_size} D<={max_dim}")
+
+
 _MENU = [
     lambda x: x[0] * x[1] / x[2],
     lambda x: np.sqrt(x[0]) * x[3],
@@ -136,5 +150,36 @@ def workload4(p: int, held_out: bool = True, sis_size: int = 60, max_dim: int = 
                    f"learned-{'eval' if held_out else 'train'}{p} N={N} d={d} rung2 k={sis_size} D<={max_dim}")
 
 
+# row sets of resampled fits (ensembles, bagging, k-fold; §2.4, §4.5): data selection only
+def partition_rows(N: int, n_models: int, size: int, seed: int) -> list[np.ndarray]:
+    """Disjoint subsets of `size` rows each (one seeded permutation, cut in order)."""
+    if n_models * size > N:
+        raise ValueError("partition needs n_models * size <= N")
+    perm = np.random.default_rng(seed).permutation(N)
+    return [np.sort(perm[m * size:(m + 1) * size]) for m in range(n_models)]
+
+
+def bootstrap_rows(N: int, n_models: int, seed: int, size: int | None = None) -> list[np.ndarray]:
+    """Bootstrap samples: `size` (default N) rows drawn uniformly with replacement."""
+    r = np.random.default_rng(seed)
+    n = N if size is None else size
+    return [np.sort(r.integers(0, N, n)) for _ in range(n_models)]
+
+
+def kfold_rows(N: int, K: int, seed: int) -> list[tuple[np.ndarray, np.ndarray]]:
+    """(training rows, held-out rows) of each of K folds."""
+    if not 2 <= K <= N:
+        raise ValueError("k-fold needs 2 <= K <= N")
+    perm = np.random.default_rng(seed).permutation(N)
+    sizes = [N // K + (1 if f < N % K else 0) for f in range(K)]
+    out, at = [], 0
+    for f in range(K):
+        test = np.sort(perm[at:at + sizes[f]])
+        at += sizes[f]
+        out.append((np.setdiff1d(np.arange(N), test), test))
+    return out
+
+
 def workload(config: int, p: int = 0, **kw) -> Problem:
-    return {1: workload1, 2: workload2, 3: workload3, 4: workload4, 5: workload5_task}[config](p, **kw)
+    return {1: workload1, 2: workload2, 3: workload3, 4: workload4, 5: workload5_task,
+            6: ensemble_problem}[config](p, **kw)
