@@ -1156,7 +1156,9 @@ sisso_status prepare_target(sisso_ctx* c, const double* target_dev) {
     return check_cuda(c, cudaGetLastError(), "prepare_target");
 }
 
-// tiles of the top level's pair set (i tile origin, j tile origin)
+// tiles of the top level's pair set (i tile origin, j tile origin), listed j-major: the
+// CTAs that run at the same time share j tiles, so each j tile of the operand cache is
+// read from DRAM about once (listed i-major, every row of i tiles re-read the whole cache)
 void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
     tiles.clear();
     for (int64_t i0 = 0; i0 < P; i0 += TI) {
@@ -1169,6 +1171,7 @@ void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
             tiles.push_back(make_int2((int)i0, (int)j0));
         }
     }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const int2& a, const int2& b) { return a.y < b.y; });
 }
 
 sisso_status score_all(sisso_ctx* c, int precision) {
