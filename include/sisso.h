@@ -72,6 +72,9 @@ enum {
  * condition estimate exceeds 1e6. */
 enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1, SISSO_PREC_MIXED_BF16 = 2, SISSO_PREC_MIXED_FP16 = 3 };
 
+/* Mixed forms: where the top level's binary candidates are scored (sisso_opts.screen). */
+enum { SISSO_SCREEN_AUTO = 0, SISSO_SCREEN_CORES = 1, SISSO_SCREEN_TENSOR = 2 };
+
 /* Expansion grammar (§2.1 Eq. 2).  EQ2: every pair of phi_{l-1} except pairs already
  * in phi_{l-2}.  NEW_X_PREV: identical up to level 2; from level 3 one operand is new at
  * level l-1 and the other comes from phi_{l-2}.  Unary operators always act on the
@@ -125,12 +128,15 @@ typedef struct {
                                operators combine units.  A feature that breaks the rule, or
                                is built from one that does, is invalid (scores -1, never
                                selected); ids are those of the space without units. */
-    int screen_cores;       /* mixed forms: 0 (default) scores the top level's binary
-                               candidates from split 16-bit tensor-core products (§2.2 Eq. 5
-                               as a contraction; each key carries its error bound, see
-                               sisso_bilinear_tc), where the operand set fits (EQ2 grammar or
-                               rung <= 2, |phi_{L-1}| <= 4096); 1 keeps them on the FP32
-                               CUDA-core kernel */
+    int screen;             /* mixed forms' scoring of the top level's binary candidates:
+                               SISSO_SCREEN_AUTO (default) from split 16-bit tensor-core
+                               products (§2.2 Eq. 5 as a contraction; each key carries its
+                               error bound, see sisso_bilinear_tc) when the pairs lie within
+                               phi_{L-1} (EQ2 grammar, or rung <= 2) and |phi_{L-1}| <= 4096,
+                               else the FP32 CUDA-core kernel; SISSO_SCREEN_CORES always the
+                               CUDA-core kernel; SISSO_SCREEN_TENSOR the tensor cores also for
+                               the NEW_X_PREV pairs phi_{L-2} x new_{L-1} at rung >= 3 (when
+                               |phi_{L-2}| <= 4096 and the products fit 48 GB) */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */

@@ -73,7 +73,7 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if ((int64_t)max_dim * k > (max_dim <= 4 ? 65535 : 4095)) { why = "subspace too large"; return SISSO_ERR_ARG; }
     if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
     if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
-    if (o.screen_cores != 0 && o.screen_cores != 1) { why = "screen_cores must be 0 or 1"; return SISSO_ERR_ARG; }
+    if (o.screen < SISSO_SCREEN_AUTO || o.screen > SISSO_SCREEN_TENSOR) { why = "bad screen option"; return SISSO_ERR_ARG; }
     if (o.units)
         for (int j = 0; j < d; ++j)
             if (o.units[j] < -1 || o.units[j] >= d) { why = "unit labels must be in -1..d-1"; return SISSO_ERR_ARG; }
@@ -253,7 +253,8 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     if (!st) st = compute_subvalid(c);
     if (!st) st = fill_opcache(c);
     const bool mixed_form = o.precision == SISSO_PREC_MIXED_BF16 || o.precision == SISSO_PREC_MIXED_FP16;
-    if (!st && mixed_form && !o.screen_cores && c->opval64 && tc_screen_possible(c)) st = tc_screen_alloc(c);
+    if (!st && mixed_form && o.screen != SISSO_SCREEN_CORES && c->opval64 && tc_screen_possible(c, o.screen))
+        st = tc_screen_alloc(c);
     if (!st) st = prepare_target(c, c->y64);
     cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);
     TargetStats ts{};

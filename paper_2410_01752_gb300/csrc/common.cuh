@@ -523,7 +523,7 @@ sisso_status l0_learned(sisso_ctx* c, sisso_mlp* mlp, const double* G, const dou
                         int64_t* n_selected);
 
 // tensor-core screening of the top level's pairs (screen_tc.cu)
-bool tc_screen_possible(const sisso_ctx* c);
+bool tc_screen_possible(const sisso_ctx* c, int screen);
 sisso_status tc_screen_alloc(sisso_ctx* c);
 sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]);
 sisso_status tc_screen_status(sisso_ctx* c);

@@ -221,20 +221,7 @@ __device__ __forceinline__ double wmax(double v) {
     return v;
 }
 
-struct PrepArgs {
-    const double* val;            // operand values, feature-major (P rows of N)
-    const unsigned char* valid;   // operand validity (recursive rules)
-    int P, Pp, N, Kpad;
-    void* L;                      // parts x 3 Pp rows x Kpad
-    void* R;                      // parts x 4 Pp rows x Kpad
-    int* eL;                      // 3 Pp row exponents
-    int* eR;                      // 4 Pp
-    double* mom;                  // per operand: xbar, sum x'^2, sum x'^4, gbar, sum g'^2, sum g'^4,
-                                  // 1/x state (0 rows built, 1 x has a zero, 2 rows unusable), valid
-    double* recip;                // 1/x of every operand value (P rows of N)
-};
-
-constexpr int kPrepThreads = 512;          // one CTA per operand row, threads over samples
+constexpr int kPrepThreads = 512;          // one CTA per operand or row, threads over samples
 constexpr int kPrepWarps = kPrepThreads / 32;
 
 // CTA-wide sums (op 0) or maxima (op 1) of K values, the same in every thread (warps
@@ -249,127 +236,152 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], const int (&op)[K],
 #pragma unroll
         for (int k = 0; k < K; ++k) sh[w][k] = v[k];
     __syncthreads();
+    const int nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         double t = sh[0][k];
-        for (int q = 1; q < kPrepWarps; ++q) t = op[k] ? fmax(t, sh[q][k]) : t + sh[q][k];
+        for (int q = 1; q < nw; ++q) t = op[k] ? fmax(t, sh[q][k]) : t + sh[q][k];
         v[k] = t;
     }
 }
 
-// Target-independent rows and moments of every operand (one CTA per operand row): L blocks
-// 0 (x') and 1 (x'^2); R blocks 0 (x'), 1 ((1/x)'), 2 (x'^2), 3 (((1/x)')^2).  Rows of
-// invalid operands, of 1/x where x has a zero (or 1/x overflows), and padding are zero.
-template <typename H, int NP>
-__global__ void __launch_bounds__(kPrepThreads) k_tc_prep(PrepArgs A) {
+// threads per CTA of the per-operand and per-row kernels: enough samples per thread to
+// amortise the CTA-wide reductions
+inline int prep_threads(int N) { return N >= 8192 ? kPrepThreads : N >= 2048 ? 256 : 128; }
+
+struct MomArgs {
+    const double* val;            // operand values, feature-major (P rows of N)
+    const unsigned char* valid;   // operand validity (recursive rules)
+    int P, N;
+    double* mom;                  // per operand: xbar, sum x'^2, sum x'^4, gbar, sum g'^2, sum g'^4,
+                                  // 1/x state (0 rows built, 1 x has a zero, 2 rows unusable), valid
+    double* recip;                // 1/x of every operand value (P rows of N)
+    int write_recip;              // 0: recip already holds 1/x
+};
+
+// Target-independent moments of every operand (one CTA per operand), with g = 1/x.  An
+// operand with a zero (or a 1/x that overflows) has no 1/x rows; 1/x rows whose fourth powers
+// overflow (|x| below about 1e-77 somewhere) are not used either: the keys of candidates
+// divided by it are then 1, left to the FP64 re-score.
+__global__ void __launch_bounds__(kPrepThreads) k_tc_moments(MomArgs A) {
     __shared__ double sh[kPrepWarps][8];
     const int f = blockIdx.x, t = threadIdx.x;
-    H* L = static_cast<H*>(A.L);
-    H* R = static_cast<H*>(A.R);
-    const size_t K = (size_t)A.Kpad, lps = (size_t)3 * A.Pp * K, rps = (size_t)4 * A.Pp * K;
-    H* l0 = L + (size_t)f * K;
-    H* l1 = L + (size_t)(A.Pp + f) * K;
-    H* r0 = R + (size_t)f * K;
-    H* r1 = R + (size_t)(A.Pp + f) * K;
-    H* r2 = R + (size_t)(2 * A.Pp + f) * K;
-    H* r3 = R + (size_t)(3 * A.Pp + f) * K;
     const bool ok = f < A.P && A.valid[f];
     const double* v = A.val + (size_t)(ok ? f : 0) * A.N;
     double* rc = A.recip + (size_t)(ok ? f : 0) * A.N;
     double m1[3] = {0.0, 0.0, 0.0};          // sum x, zero flag, sum 1/x
     if (ok)
-        for (int i = t; i < A.N; i += kPrepThreads) {
+        for (int i = t; i < A.N; i += blockDim.x) {
             const double x = v[i];
             m1[0] += x;
             const double c = 1.0 / x;
-            rc[i] = c;
+            if (A.write_recip) rc[i] = c;
             if (!(x != 0.0) || !isfinite(c)) m1[1] = 1.0;
             else m1[2] += c;
         }
     block_reduce<3>(m1, {0, 1, 0}, reinterpret_cast<double (*)[3]>(&sh[0][0]));
     const bool zero = m1[1] != 0.0;
     const double mean = m1[0] / A.N, meanc = zero ? 0.0 : m1[2] / A.N;
-    double m2[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // x'^2, x'^4, c'^2, c'^4, max |x'|, x'^2, |c'|, c'^2
+    double m2[4] = {0.0, 0.0, 0.0, 0.0};     // x'^2, x'^4, c'^2, c'^4
     if (ok)
-        for (int i = t; i < A.N; i += kPrepThreads) {
+        for (int i = t; i < A.N; i += blockDim.x) {
             const double a = v[i] - mean, a2 = a * a;
             m2[0] += a2; m2[1] += a2 * a2;
-            m2[4] = fmax(m2[4], fabs(a)); m2[5] = fmax(m2[5], a2);
             if (!zero) {
-                const double c = rc[i] - meanc, cc = c * c;
+                const double c = (A.write_recip ? 1.0 / v[i] : rc[i]) - meanc, cc = c * c;
                 m2[2] += cc; m2[3] += cc * cc;
-                m2[6] = fmax(m2[6], fabs(c)); m2[7] = fmax(m2[7], cc);
             }
         }
-    block_reduce<8>(m2, {0, 0, 0, 0, 1, 1, 1, 1}, sh);
-    // 1/x rows whose fourth powers overflow (|x| below ~1e-77 somewhere) are not used: the
-    // keys of x-divided candidates are then 1, left to the FP64 re-score
-    const bool unusable = !zero && !(isfinite(m2[3]) && isfinite(m2[7]));
-    const bool crow = !zero && !unusable;
-    if (!crow) m2[2] = m2[3] = m2[6] = m2[7] = 0.0;
-    const int e1 = scale_exp(m2[4]), e2 = scale_exp(m2[5]), ec1 = scale_exp(m2[6]), ec2 = scale_exp(m2[7]);
-    const double s1 = ldexp(1.0, e1), s2 = ldexp(1.0, e2), sc1 = ldexp(1.0, ec1), sc2 = ldexp(1.0, ec2);
-    for (int i = t; i < A.Kpad; i += kPrepThreads) {
-        double a = 0.0, a2 = 0.0, c = 0.0, cc = 0.0;
-        if (ok && i < A.N) {
-            a = v[i] - mean;
-            a2 = a * a;
-            if (crow) { c = rc[i] - meanc; cc = c * c; }
-        }
-        H h[NP];
-        split_parts<H, NP>(a * s1, h);
-        put_parts<H, NP>(h, l0 + i, lps);
-        put_parts<H, NP>(h, r0 + i, rps);
-        split_parts<H, NP>(a2 * s2, h);
-        put_parts<H, NP>(h, l1 + i, lps);
-        put_parts<H, NP>(h, r2 + i, rps);
-        store_parts<H, NP>(c * sc1, r1 + i, rps);
-        store_parts<H, NP>(cc * sc2, r3 + i, rps);
-    }
-    if (t == 0) {
-        A.eL[f] = e1; A.eL[A.Pp + f] = e2;
-        A.eR[f] = e1; A.eR[A.Pp + f] = ec1; A.eR[2 * A.Pp + f] = e2; A.eR[3 * A.Pp + f] = ec2;
+    block_reduce<4>(m2, {0, 0, 0, 0}, reinterpret_cast<double (*)[4]>(&sh[0][0]));
+    const bool unusable = !zero && !(isfinite(m2[2]) && isfinite(m2[3]));
+    if (t == 0 && f < A.P) {
         double* m = A.mom + (size_t)f * 8;
-        m[0] = mean; m[1] = m2[0]; m[2] = m2[1]; m[3] = meanc; m[4] = m2[2]; m[5] = m2[3];
-        m[6] = zero ? 1.0 : unusable ? 2.0 : 0.0; m[7] = ok;
+        m[0] = mean; m[1] = m2[0]; m[2] = m2[1];
+        m[3] = zero || unusable ? 0.0 : meanc;
+        m[4] = zero || unusable ? 0.0 : m2[2];
+        m[5] = zero || unusable ? 0.0 : m2[3];
+        m[6] = zero ? 1.0 : unusable ? 2.0 : 0.0;
+        m[7] = ok;
     }
 }
 
-// Target rows and moments of every operand (one CTA per operand row): L block 2 (x' r) and
-// sum x'r, sum (x'r)^2, sum (1/x)' r.
-template <typename H, int NP>
-__global__ void __launch_bounds__(kPrepThreads) k_tc_target(PrepArgs A, const double* __restrict__ r,
-                                                            double* __restrict__ tgt) {
+// Target moments of every operand (one CTA per operand): sum x'r, sum (x'r)^2, sum g'r,
+// sum (g'r)^2 with g = 1/x
+__global__ void __launch_bounds__(kPrepThreads) k_tc_tmoments(const double* __restrict__ val,
+                                                              const double* __restrict__ recip,
+                                                              const double* __restrict__ mom, int P, int N,
+                                                              const double* __restrict__ r, double* __restrict__ tgt) {
     __shared__ double sh[kPrepWarps][4];
     const int f = blockIdx.x, t = threadIdx.x;
-    H* L = static_cast<H*>(A.L);
-    const size_t K = (size_t)A.Kpad, lps = (size_t)3 * A.Pp * K;
-    H* l2 = L + (size_t)(2 * A.Pp + f) * K;
-    const double* m = A.mom + (size_t)f * 8;
-    const bool ok = m[7] != 0.0;
-    const bool zero = m[6] != 0.0;           // no 1/x rows
-    const double mean = m[0], meanc = m[3];
+    const double* m = mom + (size_t)f * 8;
+    const bool ok = m[7] != 0.0, crow = m[6] == 0.0;
+    const double* v = val + (size_t)(ok ? f : 0) * N;
+    const double* rc = recip + (size_t)(ok ? f : 0) * N;
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    if (ok)
+        for (int i = t; i < N; i += blockDim.x) {
+            const double a = (v[i] - m[0]) * r[i];
+            q[0] += a; q[1] += a * a;
+            if (crow) {
+                const double c = (rc[i] - m[3]) * r[i];
+                q[2] += c; q[3] += c * c;
+            }
+        }
+    block_reduce<4>(q, {0, 0, 0, 0}, sh);
+    if (t == 0)
+        for (int k = 0; k < 4; ++k) tgt[(size_t)f * 4 + k] = q[k];
+}
+
+// row kinds: x', x'^2, (1/x)', ((1/x)')^2, x' r, (1/x)' r
+enum RowKind { RK_X = 0, RK_X2 = 1, RK_C = 2, RK_C2 = 3, RK_XR = 4, RK_CR = 5 };
+
+struct RowArgs {
+    const double* val;
+    const double* recip;
+    const double* mom;
+    const double* r;              // centred target (row kinds 4, 5)
+    int N, Kpad;
+    int set0, nset, setp;         // the operands of this matrix side: set0 .. set0 + nset, padded to setp
+    int nblk;                     // row blocks written by this launch
+    int kind[8];                  // their kinds
+    int row0;                     // matrix row of the first block (kind[0])
+    size_t part_stride;           // elements between part planes
+    void* dst;                    // parts x rows x Kpad
+    int* ex;                      // per matrix row: power-of-two exponent
+};
+
+// one CTA per matrix row (block, operand): the row's values, their power-of-two scale and
+// the 16-bit parts; rows of padding, of invalid operands and of unusable 1/x rows are zero
+template <typename H, int NP>
+__global__ void __launch_bounds__(kPrepThreads) k_tc_rows(RowArgs A) {
+    __shared__ double sh[kPrepWarps][1];
+    const int blk = blockIdx.x / A.setp, fl = blockIdx.x % A.setp, t = threadIdx.x;
+    const int kind = A.kind[blk];
+    const int f = A.set0 + fl;
+    const double* m = A.mom + (size_t)(fl < A.nset ? f : 0) * 8;
+    const bool cuse = kind == RK_C || kind == RK_C2 || kind == RK_CR;
+    const bool ok = fl < A.nset && m[7] != 0.0 && (!cuse || m[6] == 0.0);
     const double* v = A.val + (size_t)(ok ? f : 0) * A.N;
     const double* rc = A.recip + (size_t)(ok ? f : 0) * A.N;
-    double q[4] = {0.0, 0.0, 0.0, 0.0};     // sum x'r, sum (x'r)^2, sum c'r, max |x'r|
-    if (ok)
-        for (int i = t; i < A.N; i += kPrepThreads) {
-            const double a = (v[i] - mean) * r[i];
-            q[0] += a; q[1] += a * a;
-            q[3] = fmax(q[3], fabs(a));
-            if (!zero) q[2] += (rc[i] - meanc) * r[i];
+    auto value = [&](int i) -> double {
+        const double u = cuse ? rc[i] - m[3] : v[i] - m[0];
+        switch (kind) {
+            case RK_X: case RK_C: return u;
+            case RK_X2: case RK_C2: return u * u;
+            default: return u * A.r[i];
         }
-    block_reduce<4>(q, {0, 0, 0, 1}, sh);
-    const int e = scale_exp(q[3]);
-    const double s = ldexp(1.0, e);
-    for (int i = t; i < A.Kpad; i += kPrepThreads) {
-        const double a = ok && i < A.N ? (v[i] - mean) * r[i] : 0.0;
-        store_parts<H, NP>(a * s, l2 + i, lps);
-    }
-    if (t == 0) {
-        A.eL[2 * A.Pp + f] = e;
-        tgt[(size_t)f * 4 + 0] = q[0]; tgt[(size_t)f * 4 + 1] = q[1]; tgt[(size_t)f * 4 + 2] = q[2]; tgt[(size_t)f * 4 + 3] = 0.0;
-    }
+    };
+    double mx[1] = {0.0};
+    if (ok)
+        for (int i = t; i < A.N; i += blockDim.x) mx[0] = fmax(mx[0], fabs(value(i)));
+    block_reduce<1>(mx, {1}, sh);
+    const int e = scale_exp(mx[0]);
+    const double sc = ldexp(1.0, e);
+    const int row = A.row0 + blockIdx.x;
+    H* dst = static_cast<H*>(A.dst) + (size_t)row * A.Kpad;
+    for (int i = t; i < A.Kpad; i += blockDim.x)
+        store_parts<H, NP>(ok && i < A.N ? value(i) * sc : 0.0, dst + i, A.part_stride);
+    if (t == 0) A.ex[row] = e;
 }
 
 // out[r][c] = sum over chunks of C (FP64, in chunk order), unscaled by the rows' exponents
@@ -389,46 +401,55 @@ __global__ void k_bilin_reduce(const float* __restrict__ C, int chunks, size_t c
 struct ScoreArgs {
     const Space* sp;
     int sec[4];
-    int P, Q, Pp, N;
-    const double* mom;      // Pp x 8
-    const double* tgt;      // Pp x 4
-    const double* C1;       // 2 Pp x 4 Pp
-    const double* C2;       // Pp x 2 Pp
+    int P, Q, N;
+    int rect;               // 0: operand pairs i < j of one set (Pp = Ap = Bp); 1: i in [0, Q) x j in [Q, P)
+    int Ap, Bp;             // padded operand counts of the L and R sides
+    const double* mom;      // P x 8
+    const double* tgt;      // P x 4
+    const double* C1;       // target-independent products (ld1 columns)
+    const double* C2;       // per-step products (ld2 columns)
+    size_t ld1, ld2;
     const TargetStats* st;
     double eps_tc, eps_sel;
     float* scores;
     unsigned long long* raised;
 };
 
-// U, V and their error bounds for f = x g (x: L-side operand, g: R-side row set gs = 0 for
-// g = z, 1 for g = 1/z); see the header comment for the formulas
+// U, V and their error bounds for f = x g from the moments of x (mean, sum x'^2, sum x'^4,
+// sum x'r) and of g (mean, sum g'^2, sum g'^4, sum g'r), the products P1..P5 and the
+// Cauchy-Schwarz scale of the P5 product as computed; see the header comment for the formulas
 struct UV { double U, V, dU, dV; };
 
-__device__ __forceinline__ UV prod_uv(const ScoreArgs& A, int xi, int zi, int gs) {
-    const int Pp = A.Pp;
-    const size_t l1 = (size_t)4 * Pp, l2 = (size_t)2 * Pp;
-    const double* mx = A.mom + (size_t)xi * 8;
-    const double* mz = A.mom + (size_t)zi * 8;
-    const double xb = mx[0], X2 = mx[1], X4 = mx[2];
-    const double gb = gs ? mz[3] : mz[0], G2 = gs ? mz[4] : mz[1], G4 = gs ? mz[5] : mz[2];
-    const double XR = A.tgt[(size_t)xi * 4], XRR = A.tgt[(size_t)xi * 4 + 1];
-    const double GR = gs ? A.tgt[(size_t)zi * 4 + 2] : A.tgt[(size_t)zi * 4];
-    const double P1 = A.C1[(size_t)xi * l1 + gs * Pp + zi];
-    const double P2 = A.C1[(size_t)(Pp + xi) * l1 + (2 + gs) * Pp + zi];
-    const double P3 = A.C1[(size_t)xi * l1 + (2 + gs) * Pp + zi];
-    const double P4 = A.C1[(size_t)(Pp + xi) * l1 + gs * Pp + zi];
-    const double P5 = A.C2[(size_t)xi * l2 + gs * Pp + zi];
-    const double N = (double)A.N, ts = A.st->tsum;
+__device__ __forceinline__ UV uv_product(double xb, double X2, double X4, double XR, double gb, double G2, double G4,
+                                         double GR, double P1, double P2, double P3, double P4, double P5, double cs5,
+                                         double N, double ts, double eps) {
     UV o;
     const double t1 = xb * xb * G2, t2 = gb * gb * X2, t3 = 2.0 * xb * gb * P1, t4 = 2.0 * xb * P3, t5 = 2.0 * gb * P4;
     o.V = t1 + t2 + P2 - P1 * P1 / N + t3 + t4 + t5;
     o.U = xb * GR + gb * XR + P5 - P1 * ts / N;
     const double cs11 = sqrt(X2 * G2);
-    o.dV = A.eps_tc * ((2.0 * fabs(P1) / N + 2.0 * fabs(xb * gb)) * cs11 + sqrt(X4 * G4) + 2.0 * fabs(xb) * sqrt(X2 * G4) +
-                       2.0 * fabs(gb) * sqrt(X4 * G2)) +
+    o.dV = eps * ((2.0 * fabs(P1) / N + 2.0 * fabs(xb * gb)) * cs11 + sqrt(X4 * G4) + 2.0 * fabs(xb) * sqrt(X2 * G4) +
+                  2.0 * fabs(gb) * sqrt(X4 * G2)) +
            1e-15 * (t1 + t2 + fabs(P2) + P1 * P1 / N + fabs(t3) + fabs(t4) + fabs(t5));
-    o.dU = A.eps_tc * (sqrt(XRR * G2) + fabs(ts / N) * cs11) + 1e-15 * (fabs(xb * GR) + fabs(gb * XR) + fabs(P5));
+    o.dU = eps * (cs5 + fabs(ts / N) * cs11) + 1e-15 * (fabs(xb * GR) + fabs(gb * XR) + fabs(P5));
     return o;
+}
+
+// one operand pair of one set: x = operand xi, g = operand zi (gs = 0) or its 1/x rows (gs = 1)
+__device__ __forceinline__ UV prod_uv(const ScoreArgs& A, int xi, int zi, int gs) {
+    const int Pp = A.Ap;
+    const double* mx = A.mom + (size_t)xi * 8;
+    const double* mz = A.mom + (size_t)zi * 8;
+    const double* tx = A.tgt + (size_t)xi * 4;
+    const double* tz = A.tgt + (size_t)zi * 4;
+    const double P1 = A.C1[(size_t)xi * A.ld1 + gs * Pp + zi];
+    const double P2 = A.C1[(size_t)(Pp + xi) * A.ld1 + (2 + gs) * Pp + zi];
+    const double P3 = A.C1[(size_t)xi * A.ld1 + (2 + gs) * Pp + zi];
+    const double P4 = A.C1[(size_t)(Pp + xi) * A.ld1 + gs * Pp + zi];
+    const double P5 = A.C2[(size_t)xi * A.ld2 + gs * Pp + zi];
+    const double G2 = gs ? mz[4] : mz[1];
+    return uv_product(mx[0], mx[1], mx[2], tx[0], gs ? mz[3] : mz[0], G2, gs ? mz[5] : mz[2], gs ? tz[2] : tz[0],
+                      P1, P2, P3, P4, P5, sqrt(tx[1] * G2), (double)A.N, A.st->tsum, A.eps_tc);
 }
 
 // stored key: the estimate, raised to (upper bound - margin) where the bound exceeds it by
@@ -449,45 +470,37 @@ __device__ __forceinline__ float key_of(const UV& o, double srr, double eps_sel,
 }
 
 // key of x / z: -1 where z has a zero (division by zero), 1 where the 1/z rows are unusable
-__device__ __forceinline__ float div_key(const ScoreArgs& A, bool ok, int xi, int zi, double srr) {
+__device__ __forceinline__ bool div_state(const ScoreArgs& A, bool ok, int zi, float& key) {
     const double st = A.mom[(size_t)zi * 8 + 6];
-    if (!ok || st == 1.0) return -1.f;
-    if (st == 2.0) {
-        atomicAdd(A.raised, 1ull);
-        return 1.f;
-    }
-    return key_of(prod_uv(A, xi, zi, 1), srr, A.eps_sel, A.raised);
+    if (!ok || st == 1.0) { key = -1.f; return false; }
+    if (st == 2.0) { atomicAdd(A.raised, 1ull); key = 1.f; return false; }
+    return true;
 }
 
-// one thread per operand pair i < j (j >= Q): the keys of i+j, i-j, i*j, i/j, j/i
+__device__ __forceinline__ float key_sum(const ScoreArgs& A, double P1, int xi, int zi, double sg, double srr) {
+    const double X2 = A.mom[(size_t)xi * 8 + 1], Z2 = A.mom[(size_t)zi * 8 + 1];
+    const double XR = A.tgt[(size_t)xi * 4], ZR = A.tgt[(size_t)zi * 4];
+    UV u;
+    u.V = X2 + Z2 + 2.0 * sg * P1;
+    u.U = XR + sg * ZR;
+    u.dV = 2.0 * A.eps_tc * sqrt(X2 * Z2) + 1e-15 * (X2 + Z2 + 2.0 * fabs(P1));
+    u.dU = 1e-15 * (fabs(XR) + fabs(ZR));
+    return key_of(u, srr, A.eps_sel, A.raised);
+}
+
+// one thread per operand pair i < j (j >= Q) of one set: the keys of i+j, i-j, i*j, i/j, j/i
 __global__ void k_score_bilin(ScoreArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)A.P * A.P) return;
     const int i = (int)(e / A.P), j = (int)(e % A.P);
     if (!(i < j && j >= A.Q)) return;
-    const double* mi = A.mom + (size_t)i * 8;
-    const double* mj = A.mom + (size_t)j * 8;
-    const bool ok = mi[7] != 0.0 && mj[7] != 0.0;
+    const bool ok = A.mom[(size_t)i * 8 + 7] != 0.0 && A.mom[(size_t)j * 8 + 7] != 0.0;
     const double srr = (double)A.N * A.st->sd * A.st->sd;
-    if (A.sec[0] >= 0 || A.sec[1] >= 0) {
-        const double P1 = A.C1[(size_t)i * 4 * A.Pp + j];
-        const double X2 = mi[1], Z2 = mj[1], XR = A.tgt[(size_t)i * 4], ZR = A.tgt[(size_t)j * 4];
-        const double cs = sqrt(X2 * Z2);
-        for (int o = 0; o < 2; ++o) {
-            if (A.sec[o] < 0) continue;
-            const double sg = o == 0 ? 1.0 : -1.0;
-            float key = -1.f;
-            if (ok) {
-                UV u;
-                u.V = X2 + Z2 + 2.0 * sg * P1;
-                u.U = XR + sg * ZR;
-                u.dV = 2.0 * A.eps_tc * cs + 1e-15 * (X2 + Z2 + 2.0 * fabs(P1));
-                u.dU = 1e-15 * (fabs(XR) + fabs(ZR));
-                key = key_of(u, srr, A.eps_sel, A.raised);
-            }
-            const Section& sc = A.sp->sec[A.sec[o]];
-            A.scores[sc.base + rank_of(sc, i, j)] = key;
-        }
+    const double P1 = A.C1[(size_t)i * A.ld1 + j];
+    for (int o = 0; o < 2; ++o) {
+        if (A.sec[o] < 0) continue;
+        const Section& sc = A.sp->sec[A.sec[o]];
+        A.scores[sc.base + rank_of(sc, i, j)] = ok ? key_sum(A, P1, i, j, o == 0 ? 1.0 : -1.0, srr) : -1.f;
     }
     if (A.sec[2] >= 0) {
         const Section& sc = A.sp->sec[A.sec[2]];
@@ -495,8 +508,63 @@ __global__ void k_score_bilin(ScoreArgs A) {
     }
     if (A.sec[3] >= 0) {
         const Section& sc = A.sp->sec[A.sec[3]];
-        A.scores[sc.base + rank_of(sc, i, j)] = div_key(A, ok, i, j, srr);
-        A.scores[sc.base + rank_of(sc, j, i)] = div_key(A, ok, j, i, srr);
+        float k1, k2;
+        if (div_state(A, ok, j, k1)) k1 = key_of(prod_uv(A, i, j, 1), srr, A.eps_sel, A.raised);
+        if (div_state(A, ok, i, k2)) k2 = key_of(prod_uv(A, j, i, 1), srr, A.eps_sel, A.raised);
+        A.scores[sc.base + rank_of(sc, i, j)] = k1;
+        A.scores[sc.base + rank_of(sc, j, i)] = k2;
+    }
+}
+
+// One thread per pair i in [0, Q) x j in [Q, P) (the NEW_X_PREV top level): the keys of i+j,
+// i-j, i*j, i/j, j/i.  L side: the operands [0, Q), row blocks x', x'^2, c', c'^2 (products
+// C1, Ap rows each) and x'r, c'r (C2); R side: the operands [Q, P), row blocks z', c_z',
+// z'^2, c_z'^2 (Bp columns each; C2 uses the first two).  j/i = z (1/x) is read as
+// sum z' c_x' = C1[c'][z'], sum z'^2 c_x'^2 = C1[c'^2][z'^2], sum z' c_x'^2 = C1[c'^2][z'],
+// sum z'^2 c_x' = C1[c'][z'^2] and sum (z'r) c_x' = C2[c'r][z'].
+__global__ void k_score_bilin_rect(ScoreArgs A) {
+    const int nB = A.P - A.Q;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)A.Q * nB) return;
+    const int i = (int)(e / nB), jl = (int)(e % nB), j = A.Q + jl;
+    const double* mi = A.mom + (size_t)i * 8;
+    const double* mj = A.mom + (size_t)j * 8;
+    const double* ti = A.tgt + (size_t)i * 4;
+    const double* tj = A.tgt + (size_t)j * 4;
+    const bool ok = mi[7] != 0.0 && mj[7] != 0.0;
+    const double srr = (double)A.N * A.st->sd * A.st->sd;
+    const double N = (double)A.N, ts = A.st->tsum;
+    auto c1 = [&](int rb, int cb) { return A.C1[(size_t)(rb * A.Ap + i) * A.ld1 + (size_t)cb * A.Bp + jl]; };
+    auto c2 = [&](int rb, int cb) { return A.C2[(size_t)(rb * A.Ap + i) * A.ld2 + (size_t)cb * A.Bp + jl]; };
+    const double P1 = c1(0, 0);
+    for (int o = 0; o < 2; ++o) {
+        if (A.sec[o] < 0) continue;
+        const Section& sc = A.sp->sec[A.sec[o]];
+        A.scores[sc.base + rank_of(sc, i, j)] = ok ? key_sum(A, P1, i, j, o == 0 ? 1.0 : -1.0, srr) : -1.f;
+    }
+    // x = operand i, g = operand j (gs = 0) or 1/j (gs = 1)
+    auto uv_ij = [&](int gs) {
+        const double G2 = gs ? mj[4] : mj[1];
+        return uv_product(mi[0], mi[1], mi[2], ti[0], gs ? mj[3] : mj[0], G2, gs ? mj[5] : mj[2], gs ? tj[2] : tj[0],
+                          c1(0, gs), c1(1, 2 + gs), c1(0, 2 + gs), c1(1, gs), c2(0, gs), sqrt(ti[1] * G2), N, ts,
+                          A.eps_tc);
+    };
+    if (A.sec[2] >= 0) {
+        const Section& sc = A.sp->sec[A.sec[2]];
+        A.scores[sc.base + rank_of(sc, i, j)] = ok ? key_of(uv_ij(0), srr, A.eps_sel, A.raised) : -1.f;
+    }
+    if (A.sec[3] >= 0) {
+        const Section& sc = A.sp->sec[A.sec[3]];
+        float k1, k2;
+        if (div_state(A, ok, j, k1)) k1 = key_of(uv_ij(1), srr, A.eps_sel, A.raised);
+        if (div_state(A, ok, i, k2)) {
+            // x = operand j, g = 1/i; P5 computed as sum (c_i' r) z_j'
+            const UV u = uv_product(mj[0], mj[1], mj[2], tj[0], mi[3], mi[4], mi[5], ti[2], c1(2, 0), c1(3, 2),
+                                    c1(3, 0), c1(2, 2), c2(1, 0), sqrt(ti[3] * mj[1]), N, ts, A.eps_tc);
+            k2 = key_of(u, srr, A.eps_sel, A.raised);
+        }
+        A.scores[sc.base + rank_of(sc, i, j)] = k1;
+        A.scores[sc.base + rank_of(sc, j, i)] = k2;
     }
 }
 
@@ -580,51 +648,80 @@ cudaError_t bilin(cudaStream_t s, int sms, bool bf16, void* L, int l_part_rows, 
     return cudaGetLastError();
 }
 
-size_t part_floats(int Pp, int Kpad) {
+// layout of the tensor-core screening for a context: one operand set (pairs i < j) or two
+// (NEW_X_PREV at rung >= 3: [0, Q) x [Q, P)); L and R row blocks, product sizes
+struct TcLayout {
+    bool rect;
+    int P, Q, Ap, Bp, Kpad, chunks;
+    int lblk, rblk;               // row blocks per part plane of L and R
+    int m1, n1, m2, n2;           // the two products' rows and columns
+};
+
+TcLayout tc_layout(const sisso_ctx* c) {
+    TcLayout t{};
+    const int L = c->space.rung;
+    t.P = (int)c->space.phi[L - 1];
+    t.Q = L >= 2 ? (int)c->space.phi[L - 2] : 0;
+    t.rect = c->space.grammar == SISSO_GRAMMAR_NEW_X_PREV && L >= 3;
+    t.Kpad = ((c->N + BK - 1) / BK) * BK;
     int per;
-    const int ch = chunks_of(Kpad / BK, per);
-    return (size_t)ch * 8 * Pp * Pp;        // the larger product: 2 Pp x 4 Pp per chunk
+    t.chunks = chunks_of(t.Kpad / BK, per);
+    if (t.rect) {
+        t.Ap = (t.Q + BM - 1) / BM * BM;
+        t.Bp = (t.P - t.Q + BM - 1) / BM * BM;
+        t.lblk = 6; t.rblk = 4;
+        t.m1 = 4 * t.Ap; t.n1 = 4 * t.Bp; t.m2 = 2 * t.Ap; t.n2 = 2 * t.Bp;
+    } else {
+        t.Ap = t.Bp = (t.P + BM - 1) / BM * BM;
+        t.lblk = 3; t.rblk = 4;
+        t.m1 = 2 * t.Ap; t.n1 = 4 * t.Bp; t.m2 = t.Ap; t.n2 = 2 * t.Bp;
+    }
+    return t;
+}
+
+size_t tc_bytes(const sisso_ctx* c, const TcLayout& t, bool bf16) {
+    const size_t np = nparts(bf16);
+    const size_t part = (size_t)t.chunks * std::max((size_t)t.m1 * t.n1, (size_t)t.m2 * t.n2);
+    return np * ((size_t)t.lblk * t.Ap + (size_t)t.rblk * t.Bp) * t.Kpad * 2 + part * 4 +
+           ((size_t)t.m1 * t.n1 + (size_t)t.m2 * t.n2) * 8 + (c->opinv64 ? 0 : (size_t)t.P * c->N * 8) +
+           (size_t)t.P * 12 * 8;
 }
 
 }  // namespace
 
-bool tc_screen_possible(const sisso_ctx* c) {
-    const int L = c->space.rung;
-    if (c->space.grammar == SISSO_GRAMMAR_NEW_X_PREV && L >= 3) return false;
-    const int64_t P = c->space.phi[L - 1];
-    if (P > 4096) return false;
-    const int Pp = (int)((P + BM - 1) / BM) * BM;
-    const int Kpad = ((c->N + BK - 1) / BK) * BK;
-    const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
-    const size_t bytes = (size_t)nparts(bf16) * 7 * Pp * Kpad * 2 + part_floats(Pp, Kpad) * 4 + (size_t)10 * Pp * Pp * 8 +
-                         (size_t)P * c->N * 8;
-    return bytes <= ((size_t)16 << 30);
+// the rectangular (NEW_X_PREV) layout only on request: on lognormal rung-3 data about 5% of
+// its keys carry bounds above the screening margin, and the windows they open cost more
+// FP64 re-scoring than the products save
+bool tc_screen_possible(const sisso_ctx* c, int screen) {
+    const TcLayout t = tc_layout(c);
+    if (t.rect && screen != SISSO_SCREEN_TENSOR) return false;
+    if (t.rect ? t.Q > 4096 : t.P > 4096) return false;
+    if ((int64_t)t.rblk * t.Bp * 3 > (int64_t)INT32_MAX / 2) return false;
+    return tc_bytes(c, t, c->opts.precision == SISSO_PREC_MIXED_BF16) <= ((size_t)48 << 30);
 }
 
 sisso_status tc_screen_alloc(sisso_ctx* c) {
-    const int L = c->space.rung;
-    const int P = (int)c->space.phi[L - 1];
-    const int Pp = (P + BM - 1) / BM * BM;
-    const int Kpad = ((c->N + BK - 1) / BK) * BK;
+    const TcLayout t = tc_layout(c);
     const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
-    const int np = nparts(bf16);
-    c->tc_P = P; c->tc_Pp = Pp; c->tc_Kpad = Kpad;
-    c->tc_part_cap = part_floats(Pp, Kpad);
+    const size_t np = nparts(bf16);
+    c->tc_P = t.P; c->tc_Pp = t.Ap; c->tc_Kpad = t.Kpad;
+    c->tc_part_cap = (size_t)t.chunks * std::max((size_t)t.m1 * t.n1, (size_t)t.m2 * t.n2);
     sisso_status st;
     auto al = [&](void** p, size_t bytes, const char* what) {
         return check_cuda(c, cudaMalloc(p, bytes), what);
     };
-    if ((st = al(&c->tc_L, (size_t)np * 3 * Pp * Kpad * 2, "tc L")) ||
-        (st = al(&c->tc_R, (size_t)np * 4 * Pp * Kpad * 2, "tc R")) ||
-        (st = al((void**)&c->tc_eL, sizeof(int) * 3 * Pp, "tc eL")) ||
-        (st = al((void**)&c->tc_eR, sizeof(int) * 4 * Pp, "tc eR")) ||
-        (st = al((void**)&c->tc_mom, sizeof(double) * 8 * Pp, "tc mom")) ||
-        (st = al((void**)&c->tc_tgt, sizeof(double) * 4 * Pp, "tc tgt")) ||
+    if ((st = al(&c->tc_L, np * t.lblk * t.Ap * t.Kpad * 2, "tc L")) ||
+        (st = al(&c->tc_R, np * t.rblk * t.Bp * t.Kpad * 2, "tc R")) ||
+        (st = al((void**)&c->tc_eL, sizeof(int) * t.lblk * t.Ap, "tc eL")) ||
+        (st = al((void**)&c->tc_eR, sizeof(int) * t.rblk * t.Bp, "tc eR")) ||
+        (st = al((void**)&c->tc_mom, sizeof(double) * 8 * (size_t)t.P, "tc mom")) ||
+        (st = al((void**)&c->tc_tgt, sizeof(double) * 4 * (size_t)t.P, "tc tgt")) ||
         (st = al((void**)&c->tc_part, sizeof(float) * c->tc_part_cap, "tc partials")) ||
-        (st = al((void**)&c->tc_C1, sizeof(double) * 8 * Pp * Pp, "tc C1")) ||
-        (st = al((void**)&c->tc_C2, sizeof(double) * 2 * Pp * Pp, "tc C2")) ||
-        (st = al((void**)&c->tc_recip, sizeof(double) * (size_t)P * c->N, "tc reciprocals")) ||
+        (st = al((void**)&c->tc_C1, sizeof(double) * t.m1 * (size_t)t.n1, "tc C1")) ||
+        (st = al((void**)&c->tc_C2, sizeof(double) * t.m2 * (size_t)t.n2, "tc C2")) ||
         (st = al((void**)&c->tc_err, 16, "tc err")))
+        return st;
+    if (!c->opinv64 && (st = al((void**)&c->tc_recip, sizeof(double) * (size_t)t.P * c->N, "tc reciprocals")))
         return st;
     c->tc_raised = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c->tc_err) + 8);
     cudaMemsetAsync(c->tc_err, 0, 16, c->stream);
@@ -633,46 +730,80 @@ sisso_status tc_screen_alloc(sisso_ctx* c) {
     return SISSO_OK;
 }
 
+namespace {
+// the rows of one side for the given blocks (one launch)
+void tc_rows(sisso_ctx* c, bool bf16, void* dst, int* ex, int setp, int lblk_total, int set0, int nset, int blk0,
+             std::initializer_list<int> kinds) {
+    RowArgs R{};
+    R.val = c->opval64;
+    R.recip = c->opinv64 ? c->opinv64 : c->tc_recip;
+    R.mom = c->tc_mom;
+    R.r = c->tc64;
+    R.N = c->N; R.Kpad = c->tc_Kpad;
+    R.set0 = set0; R.nset = nset; R.setp = setp;
+    R.nblk = 0;
+    for (int k : kinds) R.kind[R.nblk++] = k;
+    R.row0 = blk0 * setp;
+    R.part_stride = (size_t)lblk_total * setp * c->tc_Kpad;
+    R.dst = dst;
+    R.ex = ex;
+    const int grid = R.nblk * setp;
+    if (bf16) k_tc_rows<__nv_bfloat16, 3><<<grid, prep_threads(c->N), 0, c->stream>>>(R);
+    else k_tc_rows<__half, 2><<<grid, prep_threads(c->N), 0, c->stream>>>(R);
+    c->stats.launches++;
+}
+}  // namespace
+
 // keys of the top level's binary sections for the current target (tc64 / tstats); the
-// target-independent product runs on the first call after tc_ready was cleared
+// target-independent rows, moments and product run on the first call after tc_ready was
+// cleared
 sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]) {
     const bool bf16 = c->opts.precision == SISSO_PREC_MIXED_BF16;
-    const int L = c->space.rung;
-    PrepArgs A{};
-    A.val = c->opval64;
-    A.valid = c->subvalid;
-    A.P = c->tc_P; A.Pp = c->tc_Pp; A.N = c->N; A.Kpad = c->tc_Kpad;
-    A.L = c->tc_L; A.R = c->tc_R; A.eL = c->tc_eL; A.eR = c->tc_eR; A.mom = c->tc_mom; A.recip = c->tc_recip;
-    const int Pp = c->tc_Pp;
+    const TcLayout t = tc_layout(c);
+    const double* recip = c->opinv64 ? c->opinv64 : c->tc_recip;
     cudaError_t e = cudaSuccess;
+    const int nA = t.rect ? t.Q : t.P, nB = t.rect ? t.P - t.Q : t.P, b0 = t.rect ? t.Q : 0;
     if (!c->tc_ready) {
-        if (bf16) k_tc_prep<__nv_bfloat16, 3><<<Pp, kPrepThreads, 0, c->stream>>>(A);
-        else k_tc_prep<__half, 2><<<Pp, kPrepThreads, 0, c->stream>>>(A);
+        MomArgs M{};
+        M.val = c->opval64; M.valid = c->subvalid; M.P = t.P; M.N = c->N; M.mom = c->tc_mom;
+        M.recip = const_cast<double*>(recip); M.write_recip = c->opinv64 ? 0 : 1;
+        k_tc_moments<<<t.P, prep_threads(c->N), 0, c->stream>>>(M);
         c->stats.launches++;
-        e = bilin(c->stream, c->sms, bf16, c->tc_L, 3 * Pp, 0, 2 * Pp, c->tc_R, 4 * Pp, 0, 4 * Pp, c->tc_Kpad, c->tc_part,
-                  c->tc_err, c->tc_eL, c->tc_eR, c->tc_C1, 4 * Pp, c->stats.launches);
+        if (t.rect) tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 0, {RK_X, RK_X2, RK_C, RK_C2});
+        else tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 0, {RK_X, RK_X2});
+        tc_rows(c, bf16, c->tc_R, c->tc_eR, t.Bp, t.rblk, b0, nB, 0, {RK_X, RK_C, RK_X2, RK_C2});
+        e = bilin(c->stream, c->sms, bf16, c->tc_L, t.lblk * t.Ap, 0, t.m1, c->tc_R, t.rblk * t.Bp, 0, t.n1, t.Kpad,
+                  c->tc_part, c->tc_err, c->tc_eL, c->tc_eR, c->tc_C1, t.n1, c->stats.launches);
         if (e != cudaSuccess) return check_cuda(c, e, "tc product (target-independent)");
         c->tc_ready = true;
     }
-    if (bf16) k_tc_target<__nv_bfloat16, 3><<<Pp, kPrepThreads, 0, c->stream>>>(A, c->tc64, c->tc_tgt);
-    else k_tc_target<__half, 2><<<Pp, kPrepThreads, 0, c->stream>>>(A, c->tc64, c->tc_tgt);
+    k_tc_tmoments<<<t.P, prep_threads(c->N), 0, c->stream>>>(c->opval64, recip, c->tc_mom, t.P, c->N, c->tc64, c->tc_tgt);
     c->stats.launches++;
-    e = bilin(c->stream, c->sms, bf16, c->tc_L, 3 * Pp, 2 * Pp, Pp, c->tc_R, 4 * Pp, 0, 2 * Pp, c->tc_Kpad, c->tc_part,
-              c->tc_err, c->tc_eL, c->tc_eR, c->tc_C2, 2 * Pp, c->stats.launches);
+    if (t.rect) tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 4, {RK_XR, RK_CR});
+    else tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 2, {RK_XR});
+    const int l2 = t.rect ? 4 * t.Ap : 2 * t.Ap;
+    e = bilin(c->stream, c->sms, bf16, c->tc_L, t.lblk * t.Ap, l2, t.m2, c->tc_R, t.rblk * t.Bp, 0, t.n2, t.Kpad,
+              c->tc_part, c->tc_err, c->tc_eL, c->tc_eR, c->tc_C2, t.n2, c->stats.launches);
     if (e != cudaSuccess) return check_cuda(c, e, "tc product (target)");
     ScoreArgs S{};
     S.sp = c->space_dev;
     for (int o = 0; o < 4; ++o) S.sec[o] = sec[o];
-    S.P = c->tc_P;
-    S.Q = L >= 2 ? (int)c->space.phi[L - 2] : 0;
-    S.Pp = Pp; S.N = c->N;
-    S.mom = c->tc_mom; S.tgt = c->tc_tgt; S.C1 = c->tc_C1; S.C2 = c->tc_C2; S.st = c->tstats;
+    S.P = t.P; S.Q = t.Q; S.N = c->N;
+    S.rect = t.rect; S.Ap = t.Ap; S.Bp = t.Bp;
+    S.mom = c->tc_mom; S.tgt = c->tc_tgt; S.C1 = c->tc_C1; S.C2 = c->tc_C2;
+    S.ld1 = (size_t)t.n1; S.ld2 = (size_t)t.n2;
+    S.st = c->tstats;
     S.eps_tc = kTcEps;
     S.eps_sel = kScoreErr32;
     S.scores = c->scores;
     S.raised = c->tc_raised;
-    const int64_t n = (int64_t)S.P * S.P;
-    k_score_bilin<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(S);
+    if (t.rect) {
+        const int64_t n = (int64_t)nA * nB;
+        k_score_bilin_rect<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(S);
+    } else {
+        const int64_t n = (int64_t)t.P * t.P;
+        k_score_bilin<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(S);
+    }
     c->stats.launches++;
     return check_cuda(c, cudaGetLastError(), "tc keys");
 }

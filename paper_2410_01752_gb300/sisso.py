@@ -21,6 +21,7 @@ OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_EXP, OP_LOG, OP_SQRT, OP_SQ, OP_INV, OP_SIN, 
 PREC_FP64, PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
 PRESCREEN_NONE, PRESCREEN_MI, PRESCREEN_SPEARMAN = 0, 1, 2
+SCREEN_AUTO, SCREEN_CORES, SCREEN_TENSOR = 0, 1, 2
 MAX_DIM, MAX_SIS, MAX_RUNG = 5, 1024, 3
 STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
           -4: "SISSO_ERR_NUMERIC", -5: "SISSO_ERR_TIMEOUT", -6: "SISSO_ERR_STATE",
@@ -60,7 +61,7 @@ class Opts(C.Structure):
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
                 ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("wait_limit_ns", C.c_int64),
-                ("units", C.c_void_p), ("screen_cores", C.c_int)]
+                ("units", C.c_void_p), ("screen", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -289,13 +290,13 @@ def l0_search_noalloc(G, b, syy: float, N: int, D: int, gid, precision: int = PR
     """Exhaustive l0 over every D-subset of len(b) standardised features without a context
     and without allocating device memory (sisso_l0_search_noalloc): for callers that may
     not allocate.  Returns (positions, RSS, subsets examined)."""
-    G = np.ascontiguousarray(G, dtype=np.float64)
-    b = np.ascontiguousarray(b, dtype=np.float64)
-    gid = np.ascontiguousarray(gid, dtype=np.int64)
+    n = int(b.shape[0])
+    gp, G = _ptr(G, np.float64)          # host arrays or CUDA tensors
+    bp, b = _ptr(b, np.float64)
+    ip, gid = _ptr(gid, np.int64)
     pos = np.zeros(D, dtype=np.int32)
     rss, ex = C.c_double(), C.c_int64()
-    st = load().sisso_l0_search_noalloc(C.c_void_p(G.ctypes.data), C.c_void_p(b.ctypes.data), float(syy), int(N),
-                                        b.size, D, C.c_void_p(gid.ctypes.data), precision,
+    st = load().sisso_l0_search_noalloc(gp, bp, float(syy), int(N), n, D, ip, precision,
                                         C.c_void_p(getattr(stream, "cuda_stream", stream)) if stream else None,
                                         pos.ctypes.data_as(C.POINTER(C.c_int)), C.byref(rss), C.byref(ex))
     if st:
@@ -318,7 +319,7 @@ class Sisso:
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
                  sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None,
-                 screen_cores: bool = False):
+                 screen: int = 0):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -329,7 +330,7 @@ class Sisso:
         o.precision, o.grammar, o.survivors = precision, grammar, survivors
         o.max_band, o.band_rel, o.device = max_band, band_rel, device
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
-        o.screen_cores = int(bool(screen_cores))
+        o.screen = int(screen)          # SCREEN_AUTO, SCREEN_CORES or SCREEN_TENSOR (mixed forms)
         if prescreen is not None:    # (SISSO_PRESCREEN_MI or _SPEARMAN, quantile kept)
             o.prescreen, o.prescreen_quantile = int(prescreen[0]), float(prescreen[1])
         ulab = None

@@ -53,16 +53,22 @@ def _check(c, rec, y, rtol):
     return got
 
 
-@pytest.mark.parametrize("name,prec", [("workload2", 1), ("workload2_d6", 1), ("workload2_d6", 0)])
+@pytest.mark.parametrize("name,prec", [("workload2", 1), ("workload2_d6", 1), ("workload2_d6", 0), ("workload2", 2),
+                                       ("workload2", 3)])
 def test_rung3_fit_full_size(S, name, prec):
-    """The benchmark's plain fit: N=1000, lognormal primaries, rung 3 (2.9e8 candidates at
-    d=10), k=100, D<=4 (C(400,4) = 1.05e9 subsets at the last step)."""
+    """The benchmark's fit: N=1000, lognormal primaries, rung 3 (2.9e8 candidates at d=10),
+    k=100, D<=4 (C(400,4) = 1.05e9 subsets at the last step); plain FP32 and FP64, and the
+    mixed BF16 / FP16 forms (tensor-core screening and Gram, FP64 refits)."""
     rec = _golden(name)[0]
     P = _problem(rec)
-    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar) as c:
-        _check(c, rec, P.y, 1e-6)
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar,
+                 screen=S.SCREEN_TENSOR) as c:
+        _check(c, rec, P.y, 1e-6 if prec < 2 else 1e-4)
         st = c.stats()
-    assert st["subsets_fit"] == sum(d["subsets"] for d in rec["dims"])
+    if prec < 2:
+        assert st["subsets_fit"] == sum(d["subsets"] for d in rec["dims"])
+    else:       # the mixed forms with tensor-core screening of the phi_1 x new_2 pairs (on request)
+        assert st["screen_tc"] == 1
 
 
 @pytest.mark.parametrize("prec,rtol", [(1, 1e-6), (2, 1e-4), (3, 1e-4)])

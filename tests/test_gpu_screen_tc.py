@@ -61,24 +61,27 @@ def _lognormal(seed, N, d):
 
 
 TC_CASES = [
-    ("c1", lambda: (inputs.workload1(0).X, inputs.workload1(0).y), ALL9, 2),
-    ("collinear", lambda: (inputs.workload3(0, N=3000).X, inputs.workload3(0, N=3000).y), ALL9, 2),
-    ("rung3-eq2", lambda: _lognormal(8, 77, 2), ["+", "-", "*", "/", "sqrt", "^2"], 3),
-    ("rung1", lambda: _lognormal(9, 33, 40), ALL9, 1),
+    ("c1", lambda: (inputs.workload1(0).X, inputs.workload1(0).y), ALL9, 2, 0),
+    ("collinear", lambda: (inputs.workload3(0, N=3000).X, inputs.workload3(0, N=3000).y), ALL9, 2, 0),
+    ("rung3-eq2", lambda: _lognormal(8, 77, 2), ["+", "-", "*", "/", "sqrt", "^2"], 3, 0),
+    ("rung1", lambda: _lognormal(9, 33, 40), ALL9, 1, 0),
+    # NEW_X_PREV at rung 3: pairs of phi_1 x new_2 (two operand sets, rectangular products)
+    ("rung3-nxp", lambda: _lognormal(7, 200, 4), ALL9, 3, 1),
+    ("rung3-nxp-d5", lambda: (inputs.workload2(0, N=400, d=5).X, inputs.workload2(0, N=400, d=5).y), ALL9, 3, 1),
 ]
 
 
-@pytest.mark.parametrize("name,make,names,rung", TC_CASES, ids=[c[0] for c in TC_CASES])
+@pytest.mark.parametrize("name,make,names,rung,g", TC_CASES, ids=[c[0] for c in TC_CASES])
 @pytest.mark.parametrize("kind", [2, 3])
-def test_tc_keys_bound_oracle_scores(S, orc, name, make, names, rung, kind):
+def test_tc_keys_bound_oracle_scores(S, orc, name, make, names, rung, g, kind):
     """Every key is an upper bound of the oracle's FP64 score up to the screening margin
     (key + margin >= score), a key rejects only what the oracle rejects, and keys above the
     score by more than the margin are the raised ones the context counts."""
     X, y = make()
     m = _mask(orc, names)
-    sp = orc.Space(X.shape[1], m, rung, 0)
+    sp = orc.Space(X.shape[1], m, rung, g)
     ref, valid = sp.scores(X, y)
-    with S.Sisso(X, y, m, rung, 5, 2, precision=kind) as c:
+    with S.Sisso(X, y, m, rung, 5, 2, precision=kind, grammar=g, screen=S.SCREEN_TENSOR) as c:
         got = c.score_all(y, kind).astype(np.float64)
         st = c.stats()
     assert st["screen_tc"] == 1
@@ -104,7 +107,8 @@ def test_tc_fit_matches_oracle(S, orc, kind, seed, N):
     ref = orc.fit(P.X, P.y, sp, 25, 3)
     out = {}
     for cores in (False, True):
-        with S.Sisso(P.X, P.y, P.op_set, 2, 25, 3, precision=kind, screen_cores=cores) as c:
+        with S.Sisso(P.X, P.y, P.op_set, 2, 25, 3, precision=kind,
+                     screen=S.SCREEN_CORES if cores else S.SCREEN_AUTO) as c:
             got = c.fit()
             assert c.stats()["screen_tc"] == (0 if cores else 1)
             assert len(got) == len(ref.dims)
@@ -131,3 +135,38 @@ def test_tc_fit_with_units(S, orc):
         for t, (a, b) in enumerate(zip(got, ref.dims)):
             assert c.sis(t + 1) == ref.sis[t]
             assert a.ids == b.ids
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_tc_rung3_fit_matches_oracle(S, orc, kind):
+    """NEW_X_PREV rung 3 with tensor-core screening on request (phi_1 x new_2 products): the
+    oracle's selections and descriptors; coefficients within 1e-4 relative.  By default the
+    mixed forms keep these pairs on the CUDA cores."""
+    P = inputs.workload2(0, N=400, d=5, sis_size=20, max_dim=3)
+    sp = orc.Space(P.d, P.op_set, P.rung, P.grammar)
+    ref = orc.fit(P.X, P.y, sp, P.sis_size, P.max_dim)
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=kind, grammar=P.grammar,
+                 screen=S.SCREEN_TENSOR) as c:
+        got = c.fit()
+        assert c.stats()["screen_tc"] == 1
+        assert len(got) == len(ref.dims)
+        for t, (g, r) in enumerate(zip(got, ref.dims)):
+            assert c.sis(t + 1) == ref.sis[t]
+            assert g.ids == r.ids
+            np.testing.assert_allclose(g.coef, r.coef, rtol=1e-4, atol=1e-9 * np.abs(P.y).max())
+
+
+def test_screen_modes(S):
+    """Where the mixed forms score the top level's pairs: automatically on the tensor cores
+    for pairs within phi_{L-1}, on the CUDA cores for NEW_X_PREV rung 3 unless asked."""
+    P = inputs.workload2(0, N=200, d=4, sis_size=5, max_dim=1)
+    for mode, want in ((S.SCREEN_AUTO, 0), (S.SCREEN_CORES, 0), (S.SCREEN_TENSOR, 1)):
+        with S.Sisso(P.X, P.y, P.op_set, P.rung, 5, 1, precision=2, grammar=P.grammar, screen=mode) as c:
+            c.fit()
+            assert c.stats()["screen_tc"] == want
+    Q = inputs.workload1(0)
+    with S.Sisso(Q.X, Q.y, Q.op_set, Q.rung, 5, 1, precision=3) as c:
+        c.fit()
+        assert c.stats()["screen_tc"] == 1
+    with pytest.raises(S.SissoError):
+        S.Sisso(Q.X, Q.y, Q.op_set, Q.rung, 5, 1, precision=3, screen=3)

@@ -50,3 +50,26 @@ def test_noalloc_matches_context_search(prec):
         assert got[0] == ref[0]
         assert got[1] == pytest.approx(ref[1], rel=1e-9, abs=1e-9 * syy * N)
         assert got[2] == ref[2] == math.comb(b.size, D)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("D,n", [(1, 40), (2, 40), (3, 40), (4, 40), (5, 30)])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_noalloc_every_dimension(D, n, where):
+    """D = 1..5 with G, b and gid in host or device memory: the context search's winner, RSS
+    and subset count."""
+    import torch
+    from paper_2410_01752_gb300 import build, sisso
+    build.build()
+    G, b, syy, N, gid = _case(10 + D, n)
+    X = np.random.default_rng(0).uniform(1, 2, size=(N, 2))
+    with sisso.Sisso(X, np.arange(N, dtype=float), sisso.OP_ADD, 1, 2, 1, precision=1) as c:
+        ref = c.l0_search(G, b, syy, D, gid, 1)
+    if where == "device":
+        args = (torch.from_numpy(G).cuda(), torch.from_numpy(b).cuda(), torch.from_numpy(gid.astype(np.int64)).cuda())
+    else:
+        args = (G, b, gid)
+    got = sisso.l0_search_noalloc(args[0], args[1], syy, N, D, args[2], 1)
+    assert got[0] == ref[0]
+    assert got[1] == pytest.approx(ref[1], rel=1e-9, abs=1e-9 * syy * N)
+    assert got[2] == ref[2] == math.comb(n, D)
