@@ -39,6 +39,25 @@
 namespace sg {
 namespace {
 
+// paired FP32 arithmetic (two columns per 64-bit register, one instruction for both)
+using p2 = unsigned long long;
+__device__ __forceinline__ p2 pk2(float a, float b) {
+    p2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(p2 x, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x)); }
+__device__ __forceinline__ p2 fma2(p2 a, p2 b, p2 c) {
+    p2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ p2 mul2(p2 a, p2 b) {
+    p2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 constexpr int kTR = 64;                  // i1 rows per tile
 constexpr int kTC = 256;                 // i2 columns per tile: 8 per lane
 constexpr int kTW = 8;                   // warps per CTA = prefixes per work item
@@ -401,6 +420,16 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
         __syncwarp();
 
         // ---- sweep -------------------------------------------------------------------
+        // the column values in pairs of groups (2 jp, 2 jp + 1): the per-subset arithmetic
+        // runs as paired FP32 instructions, the same roundings as one column at a time
+        p2 rtp[4][DPa], dpp[4], npp[4];
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+#pragma unroll
+            for (int m = 0; m < DP; ++m) rtp[jp][m] = pk2(rt[2 * jp][m], rt[2 * jp + 1][m]);
+            dpp[jp] = pk2(dp2[2 * jp], dp2[2 * jp + 1]);
+            npp[jp] = pk2(np2[2 * jp], np2[2 * jp + 1]);
+        }
         // this lane's columns that belong to the tile: bits j with c <= cb + lane + 32 j < n
         unsigned nmask = 0;
 #pragma unroll
@@ -440,17 +469,45 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
 #pragma unroll
                 for (int j = J; j < 8; ++j) gv[j] = grow[32 * j];
                 unsigned mask = 0;
-#pragma unroll
-                for (int j = J; j < 8; ++j) {
-                    float g = gv[j];
-#pragma unroll
-                    for (int m = 0; m < DP; ++m) g -= rec[m] * rt[j][m];
-                    gv[j] = g;
-                    const float d2 = dp2[j] - g * g * id1;
-                    const float num = np2[j] - g * w1s;
-                    const float f = num * num - cB * d2;
-                    const float e = S1 * fabsf(num) - Rk * d2;
+                // per column: g = G - sum R R, d2 = dp2 - g^2 / d1, num = np2 - g w1 / sqrt(d1),
+                // f = num^2 - cB d2, e = S1 |num| - Rk d2 (as fma(-a, b, c) and fma(a, a, -(c d)))
+                auto decide = [&](int j, float d2, float num, float f) {
+                    const float e = fmaf(S1, fabsf(num), -(Rk * d2));
                     mask |= (f < 0.f && e <= 0.f && d2 > A.tau) ? 0u : (1u << j);
+                };
+                if (J & 1) {           // a first group without its pair partner
+                    float g = gv[J];
+                    float rtJ[DPa], dJ, nJ, u;
+#pragma unroll
+                    for (int m = 0; m < DP; ++m) up2(rtp[J >> 1][m], u, rtJ[m]);
+                    up2(dpp[J >> 1], u, dJ);
+                    up2(npp[J >> 1], u, nJ);
+#pragma unroll
+                    for (int m = 0; m < DP; ++m) g = fmaf(-rec[m], rtJ[m], g);
+                    gv[J] = g;
+                    const float d2 = fmaf(-(g * g), id1, dJ);
+                    const float num = fmaf(-g, w1s, nJ);
+                    decide(J, d2, num, fmaf(num, num, -(cB * d2)));
+                }
+                {
+                    p2 nrec[DPa];
+#pragma unroll
+                    for (int m = 0; m < DP; ++m) nrec[m] = pk2(-rec[m], -rec[m]);
+                    const p2 nid1 = pk2(-id1, -id1), nw1s = pk2(-w1s, -w1s), ncB = pk2(-cB, -cB);
+#pragma unroll
+                    for (int jp = (J + 1) >> 1; jp < 4; ++jp) {
+                        p2 g = pk2(gv[2 * jp], gv[2 * jp + 1]);
+#pragma unroll
+                        for (int m = 0; m < DP; ++m) g = fma2(nrec[m], rtp[jp][m], g);
+                        const p2 d2 = fma2(mul2(g, g), nid1, dpp[jp]);
+                        const p2 num = fma2(g, nw1s, npp[jp]);
+                        const p2 f = fma2(num, num, mul2(ncB, d2));
+                        float ga, gb, da, db, na, nb, fa, fb;
+                        up2(g, ga, gb); up2(d2, da, db); up2(num, na, nb); up2(f, fa, fb);
+                        gv[2 * jp] = ga; gv[2 * jp + 1] = gb;
+                        decide(2 * jp, da, na, fa);
+                        decide(2 * jp + 1, db, nb, fb);
+                    }
                 }
                 mask &= vmask;
                 if (__any_sync(0xffffffffu, mask != 0)) {
