@@ -471,6 +471,7 @@ struct sisso_ctx {
     int* tc_eR = nullptr;
     double* tc_mom = nullptr;
     double* tc_tgt = nullptr;
+    int* tc_mex = nullptr;
     float* tc_part = nullptr;
     double* tc_C1 = nullptr;
     double* tc_C2 = nullptr;

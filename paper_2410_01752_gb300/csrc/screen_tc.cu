@@ -33,7 +33,6 @@ namespace sg {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;            // output tile; samples per stage
-constexpr int STAGES = 4;
 constexpr int kThreads = 128;
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kAcc = 4;                                // TMEM accumulators per tile, 128 columns each
@@ -43,10 +42,15 @@ constexpr int kChunkBlocks = kAcc * kAccBlocks;        // 64-sample blocks per c
 constexpr double kTcEps = 1.0 / (1 << 17);            // bound on |error| / Cauchy-Schwarz scale
 constexpr int kMaxParts = 6;
 
+// one stage = one 64-sample block: every 16-bit part of the L tile and of the R tile
+// (FP16: 2 + 2 tiles, 64 KB, three stages; BF16: 3 + 3 tiles, 96 KB, two stages), so each
+// part is loaded once per block and the block's part products are issued back to back
+template <int NP>
 struct Smem {
-    uint8_t a[STAGES][kTileBytes];
-    uint8_t b[STAGES][kTileBytes];
-    uint64_t full[STAGES], empty[STAGES], done;
+    static constexpr int ST = NP == 2 ? 3 : 2;
+    uint8_t a[ST][NP][kTileBytes];
+    uint8_t b[ST][NP][kTileBytes];
+    uint64_t full[ST], empty[ST], done;
     uint32_t tmem_base;
 };
 
@@ -70,19 +74,22 @@ struct BilinArgs {
 // loses up to about one unit in the last place per MMA, so every run of kAccBlocks blocks
 // goes to its own TMEM accumulator and the accumulators are added in FP64 before the store.
 // Bounded waits; on timeout the error flag is raised and nothing is stored.
+template <int NP>
 __global__ void __launch_bounds__(kThreads, 1) k_bilin_tc(const __grid_constant__ CUtensorMap mapL,
                                                           const __grid_constant__ CUtensorMap mapR, BilinArgs A) {
+    using SM = Smem<NP>;
+    constexpr int ST = SM::ST;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    SM& S = *reinterpret_cast<SM*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per_chunk = A.tiles_m * A.tiles_n;
     const int chunk = blockIdx.x / per_chunk, t = blockIdx.x % per_chunk;
     const int tm = t / A.tiles_n, tn = t % A.tiles_n;
     const int kb_lo = chunk * A.kb_per_chunk, kb_hi = min(A.nkb, kb_lo + A.kb_per_chunk);
-    const int nk = max(0, kb_hi - kb_lo) * A.npairs;
+    const int nk = max(0, kb_hi - kb_lo);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
+        for (int s = 0; s < ST; ++s) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], 1); }
         mbar_init(&S.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -105,31 +112,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_bilin_tc(const __grid_constant_
         if (warp == 0 && lane == 0) {
             int issued = 0;
             for (int ks = 0; ks < nk; ++ks) {
-                const int s = ks % STAGES;
-                const uint32_t ph = (uint32_t)(ks / STAGES) & 1u;
-                if (ks >= STAGES && !mbar_wait(&S.empty[s], ph ^ 1u)) { failed = 1; break; }
-                mbar_expect_tx(&S.full[s], 2 * kTileBytes);
-                const int kb = kb_lo + ks / A.npairs, p = ks % A.npairs;
-                tma_load_2d(S.a[s], &mapL, kb * BK, A.lp[p] * A.l_part_rows + A.l_row0 + tm * BM, &S.full[s]);
-                tma_load_2d(S.b[s], &mapR, kb * BK, A.rp[p] * A.r_part_rows + A.r_row0 + tn * BN, &S.full[s]);
+                const int s = ks % ST;
+                const uint32_t ph = (uint32_t)(ks / ST) & 1u;
+                if (ks >= ST && !mbar_wait(&S.empty[s], ph ^ 1u)) { failed = 1; break; }
+                mbar_expect_tx(&S.full[s], 2 * NP * kTileBytes);
+                const int x = (kb_lo + ks) * BK;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    tma_load_2d(S.a[s][q], &mapL, x, q * A.l_part_rows + A.l_row0 + tm * BM, &S.full[s]);
+                    tma_load_2d(S.b[s][q], &mapR, x, q * A.r_part_rows + A.r_row0 + tn * BN, &S.full[s]);
+                }
                 ++issued;
             }
             if (failed)
-                for (int ks = (issued > STAGES ? issued - STAGES : 0); ks < issued; ++ks)
-                    mbar_wait(&S.full[ks % STAGES], (uint32_t)(ks / STAGES) & 1u);
+                for (int ks = (issued > ST ? issued - ST : 0); ks < issued; ++ks)
+                    mbar_wait(&S.full[ks % ST], (uint32_t)(ks / ST) & 1u);
         } else if (warp == 1 && lane == 0) {
             bool ok = true;
             for (int ks = 0; ks < nk; ++ks) {
-                const int s = ks % STAGES;
-                if (!mbar_wait(&S.full[s], (uint32_t)(ks / STAGES) & 1u)) { ok = false; break; }
+                const int s = ks % ST;
+                if (!mbar_wait(&S.full[s], (uint32_t)(ks / ST) & 1u)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t da = desc_sw128(smem_u32(S.a[s])), db = desc_sw128(smem_u32(S.b[s]));
-                const int blk = ks / A.npairs;
-                const uint32_t acc = tmem + (uint32_t)((blk / kAccBlocks) * 128);
-                const bool first = blk % kAccBlocks == 0 && ks % A.npairs == 0;
+                const uint32_t acc = tmem + (uint32_t)((ks / kAccBlocks) * 128);
+                const bool first = ks % kAccBlocks == 0;
+                for (int p = 0; p < A.npairs; ++p) {
+                    const uint64_t da = desc_sw128(smem_u32(S.a[s][A.lp[p]])), db = desc_sw128(smem_u32(S.b[s][A.rp[p]]));
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    mma_f16(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), A.idesc, (!first || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_f16(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), A.idesc,
+                                (!first || p > 0 || k > 0) ? 1u : 0u);
+                }
                 mma_commit(&S.empty[s]);
             }
             if (!ok) failed = 1;
@@ -249,6 +261,9 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], const int (&op)[K],
 // amortise the CTA-wide reductions
 inline int prep_threads(int N) { return N >= 8192 ? kPrepThreads : N >= 2048 ? 256 : 128; }
 
+// row kinds: x', x'^2, (1/x)', ((1/x)')^2, x' r, (1/x)' r
+enum RowKind { RK_X = 0, RK_X2 = 1, RK_C = 2, RK_C2 = 3, RK_XR = 4, RK_CR = 5 };
+
 struct MomArgs {
     const double* val;            // operand values, feature-major (P rows of N)
     const unsigned char* valid;   // operand validity (recursive rules)
@@ -257,6 +272,7 @@ struct MomArgs {
                                   // 1/x state (0 rows built, 1 x has a zero, 2 rows unusable), valid
     double* recip;                // 1/x of every operand value (P rows of N)
     int write_recip;              // 0: recip already holds 1/x
+    int* mex;                     // per operand and row kind: power-of-two exponent of the row
 };
 
 // Target-independent moments of every operand (one CTA per operand), with g = 1/x.  An
@@ -282,19 +298,25 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_moments(MomArgs A) {
     block_reduce<3>(m1, {0, 1, 0}, reinterpret_cast<double (*)[3]>(&sh[0][0]));
     const bool zero = m1[1] != 0.0;
     const double mean = m1[0] / A.N, meanc = zero ? 0.0 : m1[2] / A.N;
-    double m2[4] = {0.0, 0.0, 0.0, 0.0};     // x'^2, x'^4, c'^2, c'^4
+    double m2[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // x'^2, x'^4, c'^2, c'^4, max |x'|, x'^2, |c'|, c'^2
     if (ok)
         for (int i = t; i < A.N; i += blockDim.x) {
             const double a = v[i] - mean, a2 = a * a;
             m2[0] += a2; m2[1] += a2 * a2;
+            m2[4] = fmax(m2[4], fabs(a)); m2[5] = fmax(m2[5], a2);
             if (!zero) {
                 const double c = (A.write_recip ? 1.0 / v[i] : rc[i]) - meanc, cc = c * c;
                 m2[2] += cc; m2[3] += cc * cc;
+                m2[6] = fmax(m2[6], fabs(c)); m2[7] = fmax(m2[7], cc);
             }
         }
-    block_reduce<4>(m2, {0, 0, 0, 0}, reinterpret_cast<double (*)[4]>(&sh[0][0]));
+    block_reduce<8>(m2, {0, 0, 0, 0, 1, 1, 1, 1}, sh);
     const bool unusable = !zero && !(isfinite(m2[2]) && isfinite(m2[3]));
     if (t == 0 && f < A.P) {
+        int* ex = A.mex + (size_t)f * 6;
+        ex[RK_X] = scale_exp(m2[4]); ex[RK_X2] = scale_exp(m2[5]);
+        ex[RK_C] = zero || unusable ? 0 : scale_exp(m2[6]);
+        ex[RK_C2] = zero || unusable ? 0 : scale_exp(m2[7]);
         double* m = A.mom + (size_t)f * 8;
         m[0] = mean; m[1] = m2[0]; m[2] = m2[1];
         m[3] = zero || unusable ? 0.0 : meanc;
@@ -310,78 +332,96 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_moments(MomArgs A) {
 __global__ void __launch_bounds__(kPrepThreads) k_tc_tmoments(const double* __restrict__ val,
                                                               const double* __restrict__ recip,
                                                               const double* __restrict__ mom, int P, int N,
-                                                              const double* __restrict__ r, double* __restrict__ tgt) {
-    __shared__ double sh[kPrepWarps][4];
+                                                              const double* __restrict__ r, double* __restrict__ tgt,
+                                                              int* __restrict__ mex) {
+    __shared__ double sh[kPrepWarps][6];
     const int f = blockIdx.x, t = threadIdx.x;
     const double* m = mom + (size_t)f * 8;
     const bool ok = m[7] != 0.0, crow = m[6] == 0.0;
     const double* v = val + (size_t)(ok ? f : 0) * N;
     const double* rc = recip + (size_t)(ok ? f : 0) * N;
-    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};      // sums, then max |x'r|, max |c'r|
     if (ok)
         for (int i = t; i < N; i += blockDim.x) {
             const double a = (v[i] - m[0]) * r[i];
             q[0] += a; q[1] += a * a;
+            q[4] = fmax(q[4], fabs(a));
             if (crow) {
                 const double c = (rc[i] - m[3]) * r[i];
                 q[2] += c; q[3] += c * c;
+                q[5] = fmax(q[5], fabs(c));
             }
         }
-    block_reduce<4>(q, {0, 0, 0, 0}, sh);
-    if (t == 0)
+    block_reduce<6>(q, {0, 0, 0, 0, 1, 1}, sh);
+    if (t == 0) {
         for (int k = 0; k < 4; ++k) tgt[(size_t)f * 4 + k] = q[k];
+        mex[(size_t)f * 6 + RK_XR] = scale_exp(q[4]);
+        mex[(size_t)f * 6 + RK_CR] = scale_exp(q[5]);
+    }
 }
-
-// row kinds: x', x'^2, (1/x)', ((1/x)')^2, x' r, (1/x)' r
-enum RowKind { RK_X = 0, RK_X2 = 1, RK_C = 2, RK_C2 = 3, RK_XR = 4, RK_CR = 5 };
 
 struct RowArgs {
     const double* val;
     const double* recip;
     const double* mom;
+    const int* mex;               // per operand and kind: power-of-two exponent
     const double* r;              // centred target (row kinds 4, 5)
     int N, Kpad;
     int set0, nset, setp;         // the operands of this matrix side: set0 .. set0 + nset, padded to setp
     int nblk;                     // row blocks written by this launch
     int kind[8];                  // their kinds
-    int row0;                     // matrix row of the first block (kind[0])
+    int row0;                     // matrix row of the first block's operand 0
     size_t part_stride;           // elements between part planes
     void* dst;                    // parts x rows x Kpad
     int* ex;                      // per matrix row: power-of-two exponent
 };
 
-// one CTA per matrix row (block, operand): the row's values, their power-of-two scale and
-// the 16-bit parts; rows of padding, of invalid operands and of unusable 1/x rows are zero
+// one CTA per operand of the set: its rows of every requested block in one pass over the
+// samples (values scaled by the row's power of two, then split into 16-bit parts); rows of
+// padding, of invalid operands and of unusable 1/x rows are zero
 template <typename H, int NP>
 __global__ void __launch_bounds__(kPrepThreads) k_tc_rows(RowArgs A) {
-    __shared__ double sh[kPrepWarps][1];
-    const int blk = blockIdx.x / A.setp, fl = blockIdx.x % A.setp, t = threadIdx.x;
-    const int kind = A.kind[blk];
+    const int fl = blockIdx.x, t = threadIdx.x;
     const int f = A.set0 + fl;
-    const double* m = A.mom + (size_t)(fl < A.nset ? f : 0) * 8;
-    const bool cuse = kind == RK_C || kind == RK_C2 || kind == RK_CR;
-    const bool ok = fl < A.nset && m[7] != 0.0 && (!cuse || m[6] == 0.0);
-    const double* v = A.val + (size_t)(ok ? f : 0) * A.N;
-    const double* rc = A.recip + (size_t)(ok ? f : 0) * A.N;
-    auto value = [&](int i) -> double {
-        const double u = cuse ? rc[i] - m[3] : v[i] - m[0];
-        switch (kind) {
-            case RK_X: case RK_C: return u;
-            case RK_X2: case RK_C2: return u * u;
-            default: return u * A.r[i];
+    const bool in = fl < A.nset;
+    const double* m = A.mom + (size_t)(in ? f : 0) * 8;
+    const bool okx = in && m[7] != 0.0, okc = okx && m[6] == 0.0;
+    const double* v = A.val + (size_t)(okx ? f : 0) * A.N;
+    const double* rc = A.recip + (size_t)(okx ? f : 0) * A.N;
+    double sc[8];
+    bool ok[8];
+    H* dst[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (b >= A.nblk) break;
+        const int k = A.kind[b];
+        ok[b] = (k == RK_C || k == RK_C2 || k == RK_CR) ? okc : okx;
+        const int e = ok[b] ? A.mex[(size_t)f * 6 + k] : 0;
+        sc[b] = ldexp(1.0, e);
+        const int row = A.row0 + b * A.setp + fl;
+        dst[b] = static_cast<H*>(A.dst) + (size_t)row * A.Kpad;
+        if (t == 0) A.ex[row] = e;
+    }
+    for (int i = t; i < A.Kpad; i += blockDim.x) {
+        const bool live = i < A.N;
+        const double u = okx && live ? v[i] - m[0] : 0.0;
+        const double c = okc && live ? rc[i] - m[3] : 0.0;
+        const double r = live ? A.r[i] : 0.0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if (b >= A.nblk) break;
+            double x;
+            switch (A.kind[b]) {
+                case RK_X: x = u; break;
+                case RK_X2: x = u * u; break;
+                case RK_C: x = c; break;
+                case RK_C2: x = c * c; break;
+                case RK_XR: x = u * r; break;
+                default: x = c * r; break;
+            }
+            store_parts<H, NP>(ok[b] ? x * sc[b] : 0.0, dst[b] + i, A.part_stride);
         }
-    };
-    double mx[1] = {0.0};
-    if (ok)
-        for (int i = t; i < A.N; i += blockDim.x) mx[0] = fmax(mx[0], fabs(value(i)));
-    block_reduce<1>(mx, {1}, sh);
-    const int e = scale_exp(mx[0]);
-    const double sc = ldexp(1.0, e);
-    const int row = A.row0 + blockIdx.x;
-    H* dst = static_cast<H*>(A.dst) + (size_t)row * A.Kpad;
-    for (int i = t; i < A.Kpad; i += blockDim.x)
-        store_parts<H, NP>(ok && i < A.N ? value(i) * sc : 0.0, dst + i, A.part_stride);
-    if (t == 0) A.ex[row] = e;
+    }
 }
 
 // out[r][c] = sum over chunks of C (FP64, in chunk order), unscaled by the rows' exponents
@@ -638,9 +678,16 @@ cudaError_t bilin(cudaStream_t s, int sms, bool bf16, void* L, int l_part_rows, 
     A.chunk_stride = (size_t)m_rows * n_rows;
     A.err = err;
     A.idesc = idesc_f16(bf16 ? 1u : 0u, BM, BN);
-    const size_t smem = sizeof(Smem) + 1024;
-    cudaFuncSetAttribute(k_bilin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bilin_tc<<<A.tiles_m * A.tiles_n * A.chunks, kThreads, smem, s>>>(mL, mR, A);
+    const unsigned grid = (unsigned)A.tiles_m * A.tiles_n * A.chunks;
+    if (bf16) {
+        const size_t smem = sizeof(Smem<3>) + 1024;
+        cudaFuncSetAttribute(k_bilin_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bilin_tc<3><<<grid, kThreads, smem, s>>>(mL, mR, A);
+    } else {
+        const size_t smem = sizeof(Smem<2>) + 1024;
+        cudaFuncSetAttribute(k_bilin_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bilin_tc<2><<<grid, kThreads, smem, s>>>(mL, mR, A);
+    }
     const int64_t total = (int64_t)m_rows * n_rows;
     k_bilin_reduce<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (total + 255) / 256)), 256, 0, s>>>(
         part, A.chunks, A.chunk_stride, m_rows, n_rows, n_rows, eL + l_row0, eR + r_row0, out, ldo);
@@ -716,6 +763,7 @@ sisso_status tc_screen_alloc(sisso_ctx* c) {
         (st = al((void**)&c->tc_eR, sizeof(int) * t.rblk * t.Bp, "tc eR")) ||
         (st = al((void**)&c->tc_mom, sizeof(double) * 8 * (size_t)t.P, "tc mom")) ||
         (st = al((void**)&c->tc_tgt, sizeof(double) * 4 * (size_t)t.P, "tc tgt")) ||
+        (st = al((void**)&c->tc_mex, sizeof(int) * 6 * (size_t)t.P, "tc row exponents")) ||
         (st = al((void**)&c->tc_part, sizeof(float) * c->tc_part_cap, "tc partials")) ||
         (st = al((void**)&c->tc_C1, sizeof(double) * t.m1 * (size_t)t.n1, "tc C1")) ||
         (st = al((void**)&c->tc_C2, sizeof(double) * t.m2 * (size_t)t.n2, "tc C2")) ||
@@ -740,6 +788,7 @@ void tc_rows(sisso_ctx* c, bool bf16, void* dst, int* ex, int setp, int lblk_tot
     R.mom = c->tc_mom;
     R.r = c->tc64;
     R.N = c->N; R.Kpad = c->tc_Kpad;
+    R.mex = c->tc_mex;
     R.set0 = set0; R.nset = nset; R.setp = setp;
     R.nblk = 0;
     for (int k : kinds) R.kind[R.nblk++] = k;
@@ -747,7 +796,7 @@ void tc_rows(sisso_ctx* c, bool bf16, void* dst, int* ex, int setp, int lblk_tot
     R.part_stride = (size_t)lblk_total * setp * c->tc_Kpad;
     R.dst = dst;
     R.ex = ex;
-    const int grid = R.nblk * setp;
+    const int grid = setp;
     if (bf16) k_tc_rows<__nv_bfloat16, 3><<<grid, prep_threads(c->N), 0, c->stream>>>(R);
     else k_tc_rows<__half, 2><<<grid, prep_threads(c->N), 0, c->stream>>>(R);
     c->stats.launches++;
@@ -766,7 +815,7 @@ sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]) {
     if (!c->tc_ready) {
         MomArgs M{};
         M.val = c->opval64; M.valid = c->subvalid; M.P = t.P; M.N = c->N; M.mom = c->tc_mom;
-        M.recip = const_cast<double*>(recip); M.write_recip = c->opinv64 ? 0 : 1;
+        M.recip = const_cast<double*>(recip); M.write_recip = c->opinv64 ? 0 : 1; M.mex = c->tc_mex;
         k_tc_moments<<<t.P, prep_threads(c->N), 0, c->stream>>>(M);
         c->stats.launches++;
         if (t.rect) tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 0, {RK_X, RK_X2, RK_C, RK_C2});
@@ -777,7 +826,8 @@ sisso_status tc_screen_pairs(sisso_ctx* c, const int sec[4]) {
         if (e != cudaSuccess) return check_cuda(c, e, "tc product (target-independent)");
         c->tc_ready = true;
     }
-    k_tc_tmoments<<<t.P, prep_threads(c->N), 0, c->stream>>>(c->opval64, recip, c->tc_mom, t.P, c->N, c->tc64, c->tc_tgt);
+    k_tc_tmoments<<<t.P, prep_threads(c->N), 0, c->stream>>>(c->opval64, recip, c->tc_mom, t.P, c->N, c->tc64, c->tc_tgt,
+                                                                  c->tc_mex);
     c->stats.launches++;
     if (t.rect) tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 4, {RK_XR, RK_CR});
     else tc_rows(c, bf16, c->tc_L, c->tc_eL, t.Ap, t.lblk, 0, nA, 2, {RK_XR});
@@ -823,7 +873,7 @@ sisso_status tc_screen_status(sisso_ctx* c) {
 }
 
 void tc_screen_free(sisso_ctx* c) {
-    void* bufs[] = {c->tc_L,  c->tc_R,  c->tc_eL, c->tc_eR,    c->tc_mom, c->tc_tgt,
+    void* bufs[] = {c->tc_L,  c->tc_R,  c->tc_eL,    c->tc_eR,  c->tc_mom, c->tc_tgt, c->tc_mex,
                     c->tc_part, c->tc_C1, c->tc_C2, c->tc_recip, c->tc_err};
     for (void* p : bufs)
         if (p) cudaFree(p);
