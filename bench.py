@@ -147,7 +147,7 @@ def captured_traffic():
         return None
     vals = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes", "source_sha256")))
     h = hashlib.sha256()
-    for f in ("sis.cu", "sis_device.cuh", "common.cuh"):
+    for f in ("sis.cu", "sis_device.cuh"):        # the kernel, its device code and its tile list
         with open(os.path.join(ROOT, "paper_2410_01752_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     sha = next((v.strip() for k, v in vals.items() if k.startswith("source_sha256")), "")
