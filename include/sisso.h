@@ -303,8 +303,8 @@ sisso_status sisso_bilinear_tc(const double* L, const double* R, int m, int n, i
 
 /* Measured FMA throughput of the current device in TFLOP/s, the denominator of the ALU-bound
  * kernels' roofline: kind 0 FP32 (fma.rn.f32, 2 flop), 1 paired FP32 (fma.rn.f32x2, 4 flop),
- * 2 FP64.  Every SM busy with independent chains; best of three timed launches (about 0.1 s
- * on the legacy default stream).  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA. */
+ * 2 FP64.  Every SM busy with independent chains; best of five timed launches of about
+ * 16 ms each (80 ms FP64), after one (the burst rate; legacy default stream).  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA. */
 sisso_status sisso_measure_alu_peak(int kind, double* tflops);
 
 /* ---- batched multi-task form ----------------------------------------------------------

@@ -471,9 +471,11 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
                 unsigned mask = 0;
                 // per column: g = G - sum R R, d2 = dp2 - g^2 / d1, num = np2 - g w1 / sqrt(d1),
                 // f = num^2 - cB d2, e = S1 |num| - Rk d2 (as fma(-a, b, c) and fma(a, a, -(c d)))
+                // dismissed <=> f < 0 and e <= 0 and d2 > tau, evaluated without branches
                 auto decide = [&](int j, float d2, float num, float f) {
                     const float e = fmaf(S1, fabsf(num), -(Rk * d2));
-                    mask |= (f < 0.f && e <= 0.f && d2 > A.tau) ? 0u : (1u << j);
+                    const bool dismiss = (f < 0.f) & (e <= 0.f) & (d2 > A.tau);
+                    mask |= (unsigned)(!dismiss) << j;
                 };
                 if (J & 1) {           // a first group without its pair partner
                     float g = gv[J];

@@ -2,7 +2,7 @@
 // kernels' roofline (the screening pair kernel and the l0 enumeration run on the FP32 pipe,
 // the FP64 re-score on the FP64 pipe).  Every thread runs 8 independent FMA chains; the
 // grid fills every SM; the loop is unrolled 16 times so that its own instructions cost
-// about 1% of the issue slots; timed with CUDA events, best of three launches.
+// about 1% of the issue slots; timed with CUDA events, best of five launches after one.
 #include "common.cuh"
 
 #include <algorithm>
@@ -79,12 +79,14 @@ extern "C" sisso_status sisso_measure_alu_peak(int kind, double* tflops) {
     float* sink = nullptr;
     if (cudaMalloc((void**)&sink, sizeof(float)) != cudaSuccess) return SISSO_ERR_CUDA;
     const int grid = sms * 8;
-    const int iters = kind == 2 ? 256 : 4096;
+    // about 16 ms per FP32 launch (80 ms FP64): the burst rate of a kernel timed alone (longer
+    // launches run into the power cap, which sets the rate of a kernel inside a long step)
+    const int iters = kind == 2 ? 16 : 256;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best = 0.0;
-    for (int rep = 0; rep < 4; ++rep) {
+    for (int rep = 0; rep < 6; ++rep) {
         cudaEventRecord(e0);
         if (kind == 0) k_peak_f32<<<grid, kPeakThreads>>>(iters, 0.999999f, 1e-7f, sink);
         else if (kind == 1) k_peak_f32x2<<<grid, kPeakThreads>>>(iters, 0.999999f, 1e-7f, sink);
