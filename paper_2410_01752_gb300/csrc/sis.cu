@@ -387,28 +387,64 @@ __global__ void k_hist(const float* __restrict__ scores, int64_t n, int pass,
         if (h[i]) atomicAdd(&hist[pass * 4096 + i], h[i]);
 }
 
-__global__ void k_find(const unsigned* __restrict__ hist, int pass, unsigned* state, unsigned M) {
-    if (threadIdx.x != 0) return;
+// the bin, counted from the top, where the running count of keys first reaches the number
+// still needed: one CTA of 1024 threads, four bins each, a block-wide prefix sum
+constexpr int kFindThreads = 1024;
+__global__ void __launch_bounds__(kFindThreads) k_find(const unsigned* __restrict__ hist, int pass, unsigned* state,
+                                                       unsigned M) {
+    __shared__ unsigned wsum[kFindThreads / 32];
+    __shared__ unsigned total;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int nb = pass == 2 ? 256 : 4096;
-    unsigned need = pass == 0 ? M : state[1];
-    if (pass > 0 && state[3]) return;
-    unsigned cum = 0;
-    for (int b = nb - 1; b >= 0; --b) {
-        const unsigned c = hist[pass * 4096 + b];
-        if (cum + c >= need) {
-            const unsigned prefix = pass == 0 ? (unsigned)b
-                                  : pass == 1 ? ((state[0] << 12) | (unsigned)b)
-                                              : ((state[0] << 8) | (unsigned)b);
-            state[0] = prefix;
-            state[1] = need - cum;
-            if (pass == 2) state[2] = prefix;
-            return;
-        }
-        cum += c;
+    if (pass > 0 && state[3]) return;                  // uniform: every thread returns
+    const unsigned need = pass == 0 ? M : state[1];
+    // positions p = 4 t .. 4 t + 3 from the top: bin nb - 1 - p
+    unsigned c[4], local = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int p = 4 * t + q;
+        c[q] = p < nb ? hist[pass * 4096 + (nb - 1 - p)] : 0u;
+        local += c[q];
     }
-    // fewer than M nonzero keys: take them all
-    state[3] = 1u;
-    state[2] = 1u;
+    // exclusive prefix of local over the threads
+    unsigned incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned x = wsum[lane], y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += v;
+        }
+        wsum[lane] = y - x;                             // exclusive prefix of the warps
+        if (lane == 31) total = y;
+    }
+    __syncthreads();
+    unsigned cum = wsum[w] + incl - local;             // keys above this thread's first position
+    if (cum < need && cum + local >= need) {           // exactly one thread
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (cum + c[q] >= need) {
+                const unsigned b = (unsigned)(nb - 1 - (4 * t + q));
+                const unsigned prefix = pass == 0 ? b : pass == 1 ? ((state[0] << 12) | b) : ((state[0] << 8) | b);
+                state[0] = prefix;
+                state[1] = need - cum;
+                if (pass == 2) state[2] = prefix;
+                return;
+            }
+            cum += c[q];
+        }
+    }
+    if (t == 0 && total < need) {                      // fewer than M nonzero keys: take them all
+        state[3] = 1u;
+        state[2] = 1u;
+    }
 }
 
 __global__ void k_compact(const float* __restrict__ scores, int64_t n, const unsigned* __restrict__ state,
@@ -1377,7 +1413,7 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         cudaMemsetAsync(c->surv_count, 0, sizeof(unsigned), c->stream);
         for (int pass = 0; pass < 3; ++pass) {
             k_hist<<<gridS, kBlock, 0, c->stream>>>(c->scores, n, pass, c->sel_state, c->hist);
-            k_find<<<1, 32, 0, c->stream>>>(c->hist, pass, c->sel_state, (unsigned)M);
+            k_find<<<1, kFindThreads, 0, c->stream>>>(c->hist, pass, c->sel_state, (unsigned)M);
             c->stats.launches += 2;
         }
         k_compact<<<gridS, kBlock, 0, c->stream>>>(c->scores, n, c->sel_state, c->surv_ids, c->surv_count,
