@@ -807,8 +807,7 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
     __shared__ int64_t heap_id[kHeapCap];
     __shared__ int heap_ix[kHeapCap];
     __shared__ int refs[kMaxRefs];
-    __shared__ int cur, n_acc, done, exhausted, visited, checks, slow, n_refs;
-    __shared__ double red[32];
+    __shared__ int cur, n_acc, done, exhausted, visited, checks, n_refs, dup_found;
     __shared__ double cur_score, last_score;
     const int tid = threadIdx.x;
     // staged copies (the flags start cleared) or the global arrays
@@ -837,7 +836,7 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
         sk = s_sk; sid = s_sid; dup_cnt = s_cnt; ssrc = s_src; removed = s_rem; accepted = s_acc;
     }
     if (tid == 0) {
-        n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; slow = 0; last_score = -1.0;
+        n_acc = 0; done = 0; exhausted = 0; visited = 0; checks = 0; last_score = -1.0;
         out->thr_stop = 0;
     }
     // lane 0's state: first remaining entry p, window end e, heap of the window's
@@ -847,7 +846,6 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
     while (true) {
         if (tid < 32) {
             const int lane = tid;
-            if (lane == 0) slow = 0;
             while (true) {
                 int best = -1, stop = 0;
                 if (lane == 0) {
@@ -927,8 +925,7 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
                 const bool unknown = raw < 0 || __ballot_sync(0xffffffffu, ref && lane >= n_confirm(N)) != 0;
                 if (lane == 0) {
                     checks += cnt;
-                    if (!dup && unknown) slow = 1;
-                    else if (!dup) {
+                    if (!dup && !unknown) {
                         const int src = ssrc[best];
                         accepted[src] = 1;
                         acc_src[n_acc] = src;
@@ -944,7 +941,7 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
         __syncthreads();
         if (done) break;
         // slow path: every S member and accepted id that passes the score and probe tests
-        // (gathered in parallel), compared on all samples by the whole CTA
+        // (gathered in parallel), compared on all samples, one warp per reference
         const int c = cur;
         const int csrc = ssrc[c];
         const int64_t cid = sid[c];
@@ -966,34 +963,49 @@ k_walk(const Space* __restrict__ sp, const double* __restrict__ Xc, int N, const
             }
         }
         __syncthreads();
+        // one warp per gathered reference, all of them at once; a warp stops at the first
+        // sample that rules its pair out both ways, and every warp stops once one has found
+        // a duplicate (the outcome is whether any reference is one)
         const int nr = n_refs;
-        for (int q = 0; q < nr; ++q) {
+        if (tid == 0) dup_found = 0;
+        __syncthreads();
+        const int wq = tid >> 5, lq = tid & 31;
+        for (int q = wq; q < nr; q += (int)(blockDim.x >> 5)) {
+            if (__any_sync(0xffffffffu, *(volatile int*)&dup_found)) break;
             const int src = refs[q];
             Prog pm;
             OpRef rm{};
             if (!zc) { if (V) make_opref(*sp, sv_ids[src], rm); else build_prog(*sp, sv_ids[src], pm); }
             const double mm = sv_mean[src], dm = sv_sd[src];
             double e1 = 0.0, e2 = 0.0;
-            for (int t = tid; t < N; t += blockDim.x) {
-                double za, zb, mg;
-                if (zc) {
-                    za = zc[(size_t)csrc * N + t];
-                    zb = zc[(size_t)src * N + t];
-                } else if (V) {
-                    za = (opref_val(rc, V, N, t, mg) - mc) / dc;
-                    zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
-                } else {
-                    za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
-                    zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+            for (int t0 = 0; t0 < N; t0 += 32) {
+                const int t = t0 + lq;
+                if (t < N) {
+                    double za, zb, mg;
+                    if (zc) {
+                        za = zc[(size_t)csrc * N + t];
+                        zb = zc[(size_t)src * N + t];
+                    } else if (V) {
+                        za = (opref_val(rc, V, N, t, mg) - mc) / dc;
+                        zb = (opref_val(rm, V, N, t, mg) - mm) / dm;
+                    } else {
+                        za = (eval_prog<double>(pc, [&](int col) { return Xc[(size_t)col * N + t]; }) - mc) / dc;
+                        zb = (eval_prog<double>(pm, [&](int col) { return Xc[(size_t)col * N + t]; }) - mm) / dm;
+                    }
+                    e1 = fmax(e1, fabs(za - zb));
+                    e2 = fmax(e2, fabs(za + zb));
                 }
-                e1 = fmax(e1, fabs(za - zb));
-                e2 = fmax(e2, fabs(za + zb));
+                if (__any_sync(0xffffffffu, e1 > kDupTol) && __any_sync(0xffffffffu, e2 > kDupTol)) break;
             }
-            e1 = block_max(e1, red);
-            e2 = block_max(e2, red);
-            if (tid == 0) ++checks;
-            if (e1 <= kDupTol || e2 <= kDupTol) { dupf = 1; break; }
+            e1 = warp_max(e1);
+            e2 = warp_max(e2);
+            if (lq == 0) {
+                atomicAdd(&checks, 1);
+                if (e1 <= kDupTol || e2 <= kDupTol) atomicExch(&dup_found, 1);
+            }
         }
+        __syncthreads();
+        dupf = dup_found;
         __syncthreads();
         }
         if (tid == 0 && !dupf) {
