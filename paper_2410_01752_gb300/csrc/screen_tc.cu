@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_moments(MomArgs A) {
         for (int i = t; i < A.N; i += blockDim.x) {
             const double x = v[i];
             m1[0] += x;
-            const double c = 1.0 / x;
+            const double c = A.write_recip ? 1.0 / x : rc[i];       // stored reciprocals when there are
             if (A.write_recip) rc[i] = c;
             if (!(x != 0.0) || !isfinite(c)) m1[1] = 1.0;
             else m1[2] += c;

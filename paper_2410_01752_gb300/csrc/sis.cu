@@ -752,7 +752,27 @@ __global__ void k_dup_confirm(const Space* __restrict__ sp, const double* __rest
             const double mm = sv_mean[m], dm = sv_sd[m];
             double e1 = 0.0, e2 = 0.0;
             // the pair is a duplicate iff max|za - zb| or max|za + zb| stays within kDupTol:
-            // the warp stops as soon as both have exceeded it somewhere (the common case)
+            // the warp stops as soon as both have exceeded it somewhere (the common case).
+            // Cached vectors: four samples per lane per round, so that eight loads are in flight.
+            if (zc) {
+                const double* pa = zc + (size_t)src * N;
+                const double* pb = zc + (size_t)m * N;
+                for (int t0 = 0; t0 < N; t0 += 128) {
+                    double a4[4], b4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int t = t0 + 32 * u + lane;
+                        a4[u] = t < N ? pa[t] : 0.0;
+                        b4[u] = t < N ? pb[t] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        e1 = fmax(e1, fabs(a4[u] - b4[u]));
+                        e2 = fmax(e2, fabs(a4[u] + b4[u]));
+                    }
+                    if (__any_sync(0xffffffffu, e1 > kDupTol) && __any_sync(0xffffffffu, e2 > kDupTol)) break;
+                }
+            } else
             for (int t0 = 0; t0 < N; t0 += 32) {
                 const int t = t0 + lane;
                 if (t < N) {
