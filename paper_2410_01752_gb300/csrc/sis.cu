@@ -509,18 +509,32 @@ k_rescore_cta(const Space* __restrict__ sp, int N, const double* __restrict__ tc
     const double v0 = opref_val(ref, V, N, 0, mag0);
     double s1 = 0.0, s2 = 0.0, sc = 0.0, mx = 0.0, mo = 0.0;
     int bad = 0;
-    for (int i = t; i < N; i += kRescoreThreads) {
-        double mag;
-        const double v = opref_val(ref, V, N, i, mag);
-        if (!isfinite(v) || fabs(v) > kValueCap) bad = 1;
+    // one comparison per sample catches non-finite values and the cap; the operands'
+    // magnitude (the cancellation rule) only for a top-level + or -
+    const bool need_mag = id >= Pbot && (op == ADD || op == SUB);
+    auto body = [&](int i, double v, double mag, bool with_mag) {
+        const double av = fabs(v);
+        if (!(av <= kValueCap)) bad = 1;
         const double u = v - v0;
         s1 += u;
-        s2 += u * u;
-        sc += u * tc[i];
-        mx = fmax(mx, fabs(v));
-        mo = fmax(mo, mag);
+        s2 = fma(u, u, s2);
+        sc = fma(u, tc[i], sc);
+        mx = fmax(mx, av);
+        if (with_mag) mo = fmax(mo, mag);
         if (z) z[i] = v;
-    }
+    };
+    if (need_mag)
+        for (int i = t; i < N; i += kRescoreThreads) {
+            double mag;
+            const double v = opref_val(ref, V, N, i, mag);
+            body(i, v, mag, true);
+        }
+    else
+        for (int i = t; i < N; i += kRescoreThreads) {
+            double mag;
+            const double v = opref_val(ref, V, N, i, mag);
+            body(i, v, 0.0, false);
+        }
     bad = warp_or(bad);
     s1 = warp_sum(s1); s2 = warp_sum(s2); sc = warp_sum(sc); mx = warp_max(mx); mo = warp_max(mo);
     if (lane == 0) { red[wp][0] = s1; red[wp][1] = s2; red[wp][2] = sc; red[wp][3] = mx; red[wp][4] = mo; red_bad[wp] = bad; }
@@ -530,8 +544,7 @@ k_rescore_cta(const Space* __restrict__ sp, int N, const double* __restrict__ tc
         s1 += red[q][0]; s2 += red[q][1]; sc += red[q][2];
         mx = fmax(mx, red[q][3]); mo = fmax(mo, red[q][4]); bad |= red_bad[q];
     }
-    const bool top_addsub = id >= Pbot && (op == ADD || op == SUB);
-    const bool cancelled = top_addsub && mx <= kCancelRel * mo;
+    const bool cancelled = need_mag && mx <= kCancelRel * mo;
     const double mean = v0 + s1 / N;
     const double var = s2 / N - (s1 / N) * (s1 / N);
     const double sd = bad || !(var > 0.0) ? 0.0 : sqrt(var);
