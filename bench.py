@@ -300,10 +300,10 @@ def form_mixed(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     out = {}
-    for name, prec, tol in (("plain_fp32", PREC_FP32, 1e-6), ("mixed_bf16", PREC_MIXED_BF16, 1e-4),
-                            ("mixed_fp16", PREC_MIXED_FP16, 1e-4)):
+    for name, prec, tol, gram in (("plain_fp32", PREC_FP32, 1e-6, 0), ("fp32_tf32x3_gram", PREC_FP32, 1e-6, 2),
+                                  ("mixed_bf16", PREC_MIXED_BF16, 1e-4, 0), ("mixed_fp16", PREC_MIXED_FP16, 1e-4, 0)):
         with Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar,
-                   stream=stream) as s:
+                   stream=stream, gram=gram) as s:
             s.fit()
             ms = []
             for _ in range(2):
@@ -335,7 +335,7 @@ def form_mixed(args):
                     "flop_per_fit": flop, "tflops_over_pair_stage": flop / (st["ms_screen_pair"] / 1e3) / 1e12,
                     "note": "over the whole tensor-core pair stage (row preparation, products, chunk sums, keys)",
                     "bf16_peak_measured": pk.get("bf16_tflops")}
-    for k in ("mixed_bf16", "mixed_fp16"):
+    for k in ("fp32_tf32x3_gram", "mixed_bf16", "mixed_fp16"):
         out[k]["speedup_vs_plain"] = out["plain_fp32"]["time_to_descriptor_ms"] / out[k]["time_to_descriptor_ms"]
         out[k]["rmse_rel_diff_vs_plain"] = abs(out[k]["rmse"] - out["plain_fp32"]["rmse"]) / out["plain_fp32"]["rmse"]
     cpu = None
@@ -577,8 +577,10 @@ def run_mixed(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     res = {}
-    for name, prec in (("plain_fp32", PREC_FP32), ("mixed_bf16", PREC_MIXED_BF16), ("mixed_fp16", PREC_MIXED_FP16)):
-        s = Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar, stream=stream)
+    for name, prec, gram in (("plain_fp32", PREC_FP32, 0), ("fp32_tf32x3_gram", PREC_FP32, 2),
+                             ("mixed_bf16", PREC_MIXED_BF16, 0), ("mixed_fp16", PREC_MIXED_FP16, 0)):
+        s = Sisso(Xd, yd, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar, stream=stream,
+                  gram=gram)
         for _ in range(args.warmup):
             s.fit()
         ms, st = [], None

@@ -75,6 +75,9 @@ enum { SISSO_PREC_FP64 = 0, SISSO_PREC_FP32 = 1, SISSO_PREC_MIXED_BF16 = 2, SISS
 /* Mixed forms: where the top level's binary candidates are scored (sisso_opts.screen). */
 enum { SISSO_SCREEN_AUTO = 0, SISSO_SCREEN_CORES = 1, SISSO_SCREEN_TENSOR = 2 };
 
+/* FP32 precision: how the subspace Gram of §2.3 Eq. 7 is formed (sisso_opts.gram). */
+enum { SISSO_GRAM_AUTO = 0, SISSO_GRAM_FP64 = 1, SISSO_GRAM_TF32X3 = 2 };
+
 /* Expansion grammar (§2.1 Eq. 2).  EQ2: every pair of phi_{l-1} except pairs already
  * in phi_{l-2}.  NEW_X_PREV: identical up to level 2; from level 3 one operand is new at
  * level l-1 and the other comes from phi_{l-2}.  Unary operators always act on the
@@ -137,6 +140,20 @@ typedef struct {
                                CUDA-core kernel; SISSO_SCREEN_TENSOR the tensor cores also for
                                the NEW_X_PREV pairs phi_{L-2} x new_{L-1} at rung >= 3 (when
                                |phi_{L-2}| <= 4096 and the products fit 48 GB) */
+    int gram;               /* FP32 precision's subspace Gram (§2.3 Eq. 7):
+                               SISSO_GRAM_AUTO (default) and SISSO_GRAM_FP64 build it from
+                               FP64 rows on the CUDA cores, and the l0 result is the FP64
+                               search's; SISSO_GRAM_TF32X3 forms it on the tensor cores from
+                               3xTF32 split products (tcgen05.mma kind::tf32, FP32
+                               accumulation over runs of 512 samples, runs added in FP64;
+                               entries within 2.4e-5 of the FP64 Gram; the partial sums
+                               are capped at 512 MB, which lengthens the runs, and the bound
+                               with them, above about 1000 features at 65 536 samples), and
+                               the l0 step then refits in FP64, from the standardised rows,
+                               its 100 best subsets and every subset with a small pivot, as
+                               the mixed forms do (a learned proposal set on the context is
+                               not used).
+                               Other precisions accept AUTO or FP64 only. */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */
@@ -281,12 +298,16 @@ sisso_status sisso_l0_search(sisso_ctx* ctx, const double* G, const double* b, d
  * b = Z y~ / N (n), HOST; *syy (may be NULL) = y~^T y~ / N. */
 sisso_status sisso_subspace_gram(sisso_ctx* ctx, const int64_t* ids, int n, double* G, double* b, double* syy);
 
-/* Subspace Gram on the tcgen05 tensor cores (the mixed-precision forms' Gram, §2.3 Eq. 7): with Z
- * n standardised rows of N samples (FP64, row-major) and yc the centred target with
- * population std sdy, returns G = Z Z^T / N (n x n) and b = Z yc / N (n), computed from
- * BF16 (kind = SISSO_PREC_MIXED_BF16) or FP16 (SISSO_PREC_MIXED_FP16) operands with FP32
- * accumulation.  Inputs host or device; G and b HOST.  Uses the current device and the
- * legacy default stream.  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT. */
+/* Subspace Gram on the tcgen05 tensor cores (§2.3 Eq. 7): with Z n standardised rows of N
+ * samples (FP64, row-major) and yc the centred target with population std sdy, returns
+ * G = Z Z^T / N (n x n) and b = Z yc / N (n), computed from BF16 (kind =
+ * SISSO_PREC_MIXED_BF16) or FP16 (SISSO_PREC_MIXED_FP16) operands with FP32 accumulation
+ * (the mixed forms' Gram), or (kind = SISSO_PREC_FP32) from 3xTF32 split products: each
+ * value is h + l with h = tf32(z), l = tf32(z - h), and z_i z_j is taken as h_i h_j + h_i l_j
+ * + l_i h_j, accumulated in FP32 over runs of 512 samples and the runs added in FP64 (the
+ * FP32 precision's tensor-core Gram, sisso_opts.gram; entries within 3 2^-22 + 192 2^-23 =
+ * 2.4e-5 of the exact Gram, the second term the tensor cores' FP32 accumulation).  Inputs
+ * host or device; G and b HOST.  Uses the current device and the legacy default stream.  Errors: SISSO_ERR_ARG, SISSO_ERR_CUDA, SISSO_ERR_TIMEOUT. */
 sisso_status sisso_gram_tc(const double* Z, const double* yc, double sdy, int n, int N, int kind, float* G,
                            float* b);
 

@@ -74,6 +74,11 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
     if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
     if (o.screen < SISSO_SCREEN_AUTO || o.screen > SISSO_SCREEN_TENSOR) { why = "bad screen option"; return SISSO_ERR_ARG; }
+    if (o.gram < SISSO_GRAM_AUTO || o.gram > SISSO_GRAM_TF32X3 ||
+        (o.gram == SISSO_GRAM_TF32X3 && o.precision != SISSO_PREC_FP32)) {
+        why = "bad gram option (the 3xTF32 Gram is an FP32-precision form)";
+        return SISSO_ERR_ARG;
+    }
     if (o.units)
         for (int j = 0; j < d; ++j)
             if (o.units[j] < -1 || o.units[j] >= d) { why = "unit labels must be in -1..d-1"; return SISSO_ERR_ARG; }
@@ -275,6 +280,9 @@ sisso_status sisso_fit(sisso_ctx* c) {
     cudaSetDevice(c->opts.device);
     const int prec = c->opts.precision;
     const bool mixed = prec == SISSO_PREC_MIXED_BF16 || prec == SISSO_PREC_MIXED_FP16;
+    // tensor-core Gram: the mixed forms' 16-bit one, or FP32 precision's 3xTF32 one on request;
+    // either way the l0 step refits its best subsets in FP64 from the standardised rows
+    const bool tc_gram = mixed || (prec == SISSO_PREC_FP32 && c->opts.gram == SISSO_GRAM_TF32X3);
     c->stats = sisso_stats{};
     c->tc_ready = false;
     c->S.clear(); c->n_sis.clear(); c->res_ids.clear(); c->res_coef.clear(); c->res_rmse.clear(); c->res_r2.clear();
@@ -304,11 +312,11 @@ sisso_status sisso_fit(sisso_ctx* c) {
         cudaEvent_t g0, g1;
         cudaEventCreate(&g0); cudaEventCreate(&g1);
         cudaEventRecord(g0, c->stream);
-        if ((st = append_subspace(c, n_old, (int)acc.size(), !mixed))) break;
-        if (mixed && (st = gram_tc(c, c->Z, c->yc64, std::sqrt(c->syy), n, c->N, prec, c->G32, c->n_cap, c->b32))) break;
+        if ((st = append_subspace(c, n_old, (int)acc.size(), !tc_gram))) break;
+        if (tc_gram && (st = gram_tc(c, c->Z, c->yc64, std::sqrt(c->syy), n, c->N, prec, c->G32, c->n_cap, c->b32))) break;
         cudaEventRecord(g1, c->stream);
         Winner w{};
-        if (mixed) st = l0_solve_mixed(c, n, t, w);
+        if (tc_gram) st = l0_solve_mixed(c, n, t, w);
         else if (c->proposal && t == 5 && n >= 5 && n <= 1400) {
             st = l0_learned(c, c->proposal, c->G64, c->b64, c->G32, c->b32, c->n_cap, c->syy, n, c->S_dev,
                             c->prune_frac, w, &c->learned_prefixes);
@@ -329,7 +337,7 @@ sisso_status sisso_fit(sisso_ctx* c) {
         if (st) break;
         c->stats.ms_gram += event_ms(g0, g1);
         cudaEventDestroy(g0); cudaEventDestroy(g1);
-        if ((st = mixed ? winner_model_z(c, n, t, w) : winner_model(c, n, t, w))) break;
+        if ((st = tc_gram ? winner_model_z(c, n, t, w) : winner_model(c, n, t, w))) break;
         c->res_ids.emplace_back(w.ids, w.ids + t);
         c->res_coef.emplace_back(w.coef, w.coef + t + 1);
         c->res_rmse.push_back(w.rmse);

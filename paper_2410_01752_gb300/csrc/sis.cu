@@ -218,51 +218,56 @@ __global__ void k_score_cached_w(const T* __restrict__ cache, int N, int64_t P, 
     if (lane == 0) scores[id] = finalize<T>(s1, s2, sr, v0, N, TgtView<T>::sum(st), TgtView<T>::sd(st));
 }
 
-// per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) (when A1ON) and AR[f] =
-// sum_s (x_fs - x_f0) r_s, with r the centred target the pair kernel uses.  For + and - the
-// pair kernel's sums of v' = (a - a0) +/- (b - b0) and of v' r follow from these.  Products
-// and runs of 32 samples are summed in T (FP32 for the FP32 screening: the FP32 pipe, not the
-// 64x slower FP64 one), the runs in FP64.  A1 does not depend on the target: computed once.
+// per operand f of phi_{L-1}: A1[f] = sum_s (x_fs - x_f0) and A2[f] = sum_s (x_fs - x_f0)^2
+// (when A1ON) and AR[f] = sum_s (x_fs - x_f0) r_s, with r the centred target the pair kernel
+// uses.  For + and - the pair kernel's sums of v' = (a - a0) +/- (b - b0), of v'^2 and of v' r
+// follow from these and the pair's cross sum sum a' b'.  Products and runs of 32 samples of
+// A1 and AR are summed in T (FP32 for the FP32 screening: the FP32 pipe, not the 64x slower
+// FP64 one), the runs in FP64; A2 is summed in FP64 from the T values the pair kernel sees
+// (the square of an FP32 value is exact in FP64).  A1 and A2 do not depend on the target:
+// computed once.
 template <typename T, bool A1ON>
 __global__ void k_opsums(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
-                         double* __restrict__ A1, double* __restrict__ AR) {
+                         double* __restrict__ A1, double* __restrict__ AR, double* __restrict__ A2) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= P) return;
     const T* tc = TgtView<T>::tc(tc32, tc64);
     const T x0 = cache[f];
-    double a = 0.0, ar = 0.0;
+    double a = 0.0, ar = 0.0, a2 = 0.0;
     for (int s0 = 0; s0 < N; s0 += 32) {
         const int e = s0 + 32 < N ? s0 + 32 : N;
         T pa = T(0), pr = T(0);
         for (int s = s0; s < e; ++s) {
             const T v = cache[(size_t)s * P + f] - x0;
-            if (A1ON) pa += v;
+            if (A1ON) { pa += v; a2 = fma((double)v, (double)v, a2); }
             pr = fma(v, tc[s], pr);
         }
         a += (double)pa;
         ar += (double)pr;
     }
-    if (A1ON) A1[f] = a;
+    if (A1ON) { A1[f] = a; A2[f] = a2; }
     AR[f] = ar;
 }
 
 // the same with one warp per operand
 template <typename T, bool A1ON>
 __global__ void k_opsums_w(const T* __restrict__ cache, int N, int64_t P, const float* tc32, const double* tc64,
-                           double* __restrict__ A1, double* __restrict__ AR) {
+                           double* __restrict__ A1, double* __restrict__ AR, double* __restrict__ A2) {
     const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (f >= P) return;
     const T* tc = TgtView<T>::tc(tc32, tc64);
     const T x0 = cache[f];
     T pa = T(0), pr = T(0);
+    double a2 = 0.0;
     for (int s = lane; s < N; s += 32) {
         const T v = cache[(size_t)s * P + f] - x0;
-        if (A1ON) pa += v;
+        if (A1ON) { pa += v; a2 = fma((double)v, (double)v, a2); }
         pr = fma(v, tc[s], pr);
     }
     const double a = warp_sum((double)pa), ar = warp_sum((double)pr);
-    if (lane == 0) { if (A1ON) A1[f] = a; AR[f] = ar; }
+    if (A1ON) a2 = warp_sum(a2);
+    if (lane == 0) { if (A1ON) { A1[f] = a; A2[f] = a2; } AR[f] = ar; }
 }
 
 // the top level's unary sections when operands are few and samples many: one warp per
@@ -1364,11 +1369,11 @@ sisso_status score_all(sisso_ctx* c, int precision) {
 #define SG_OPSUMS(TT, CACHE)                                                                                   \
     do {                                                                                                       \
         if (few) {                                                                                             \
-            if (a1) k_opsums_w<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
-            else k_opsums_w<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+            if (a1) k_opsums_w<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P, c->opsum + 2 * A.P); \
+            else k_opsums_w<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P, c->opsum + 2 * A.P); \
         } else {                                                                                               \
-            if (a1) k_opsums<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
-            else k_opsums<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P); \
+            if (a1) k_opsums<TT, true><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P, c->opsum + 2 * A.P); \
+            else k_opsums<TT, false><<<go, 256, 0, c->stream>>>(CACHE, c->N, A.P, c->tc32, c->tc64, c->opsum, c->opsum + A.P, c->opsum + 2 * A.P); \
         }                                                                                                      \
     } while (0)
             if (fp64) SG_OPSUMS(double, c->opcache64);

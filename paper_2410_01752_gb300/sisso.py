@@ -22,6 +22,7 @@ PREC_FP64, PREC_FP32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 GRAMMAR_EQ2, GRAMMAR_NEW_X_PREV = 0, 1
 PRESCREEN_NONE, PRESCREEN_MI, PRESCREEN_SPEARMAN = 0, 1, 2
 SCREEN_AUTO, SCREEN_CORES, SCREEN_TENSOR = 0, 1, 2
+GRAM_AUTO, GRAM_FP64, GRAM_TF32X3 = 0, 1, 2
 MAX_DIM, MAX_SIS, MAX_RUNG = 5, 1024, 3
 STATUS = {0: "SISSO_OK", -1: "SISSO_ERR_ARG", -2: "SISSO_ERR_OOM", -3: "SISSO_ERR_CUDA",
           -4: "SISSO_ERR_NUMERIC", -5: "SISSO_ERR_TIMEOUT", -6: "SISSO_ERR_STATE",
@@ -61,7 +62,7 @@ class Opts(C.Structure):
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
                 ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("wait_limit_ns", C.c_int64),
-                ("units", C.c_void_p), ("screen", C.c_int)]
+                ("units", C.c_void_p), ("screen", C.c_int), ("gram", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -246,7 +247,8 @@ def prescreen(X, y, method: int, quantile: float = 1.0):
 
 
 def gram_tc(Z, yc, sdy: float, kind: int = PREC_MIXED_BF16):
-    """Z Z^T / N and Z yc / N on the tensor cores from 16-bit operands (sisso_gram_tc)."""
+    """Z Z^T / N and Z yc / N on the tensor cores (sisso_gram_tc): 16-bit operands for the
+    mixed kinds, 3xTF32 split products for kind PREC_FP32."""
     Z = np.ascontiguousarray(Z, dtype=np.float64)
     yc = np.ascontiguousarray(yc, dtype=np.float64)
     n, N = Z.shape
@@ -319,7 +321,7 @@ class Sisso:
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
                  sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None,
-                 screen: int = 0):
+                 screen: int = 0, gram: int = 0):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -331,6 +333,7 @@ class Sisso:
         o.max_band, o.band_rel, o.device = max_band, band_rel, device
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
         o.screen = int(screen)          # SCREEN_AUTO, SCREEN_CORES or SCREEN_TENSOR (mixed forms)
+        o.gram = int(gram)              # GRAM_AUTO, GRAM_FP64 or GRAM_TF32X3 (FP32 precision)
         if prescreen is not None:    # (SISSO_PRESCREEN_MI or _SPEARMAN, quantile kept)
             o.prescreen, o.prescreen_quantile = int(prescreen[0]), float(prescreen[1])
         ulab = None

@@ -71,14 +71,26 @@ def test_rung3_fit_full_size(S, name, prec):
         assert st["screen_tc"] == 1
 
 
-@pytest.mark.parametrize("prec,rtol", [(1, 1e-6), (2, 1e-4), (3, 1e-4)])
-def test_collinear_fit_full_size(S, prec, rtol):
+@pytest.mark.parametrize("prec,rtol,gram", [(1, 1e-6, 0), (1, 1e-6, 2), (2, 1e-4, 0), (3, 1e-4, 0)])
+def test_collinear_fit_full_size(S, prec, rtol, gram):
     """The mixed-precision workload at full size: N=65536, six primaries correlated 0.999,
-    rung 2, k=200, D<=3 -- plain FP32 and the BF16 / FP16 tensor-core forms."""
+    rung 2, k=200, D<=3 -- plain FP32 (FP64 Gram rows, or the 3xTF32 tensor-core Gram with
+    the FP64 refit of the best subsets) and the BF16 / FP16 tensor-core forms."""
     rec = _golden("workload3")[0]
     P = _problem(rec)
-    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar) as c:
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=prec, grammar=P.grammar,
+                 gram=gram) as c:
         _check(c, rec, P.y, rtol)
+
+
+def test_rung3_fit_full_size_tf32x3_gram(S):
+    """The benchmark's fit (N=1000, d=10, rung 3, k=100, D<=4) in FP32 with the 3xTF32
+    tensor-core Gram: the oracle's stored subspaces and descriptors."""
+    rec = _golden("workload2")[0]
+    P = _problem(rec)
+    with S.Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=1, grammar=P.grammar,
+                 gram=S.GRAM_TF32X3) as c:
+        _check(c, rec, P.y, 1e-6)
 
 
 def test_d5_fit_full_size(S):

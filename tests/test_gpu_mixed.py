@@ -1,4 +1,5 @@
-"""Mixed-precision form: the tensor-core (tcgen05) subspace Gram against an FP64 Gram."""
+"""Tensor-core (tcgen05) subspace Gram against an FP64 Gram: the mixed forms' 16-bit one and
+the FP32 precision's 3xTF32 one; mixed fits against the oracle."""
 import numpy as np
 import pytest
 
@@ -23,19 +24,28 @@ def _rows(seed, n, N, collinear=True):
     return Z, yc, float(yc.std())
 
 
-@pytest.mark.parametrize("kind,rel", [(2, 2.0 ** -7), (3, 2.0 ** -10)])
-@pytest.mark.parametrize("n,N", [(5, 64), (150, 3000), (301, 20000), (129, 130)])
-def test_gram_tc_matches_fp64(S, kind, rel, n, N):
-    """Every entry of Z Z^T / N and Z y~ / N within the 16-bit input rounding of the FP64
-    product (tiles of 128 rows, ragged edges, split over samples)."""
+# 3xTF32: the split's error 3 2^-22 plus the FP32 accumulation of a 512-sample run, at most
+# about one unit in the last place per MMA: 192 MMAs x 2^-23 (scale: sum |z_i z_j| / N <= 1)
+TF32X3_BOUND = 3 * 2.0 ** -22 + 192 * 2.0 ** -23
+
+
+@pytest.mark.parametrize("kind,tol", [(2, 2.0 ** -6), (3, 2.0 ** -9), (1, TF32X3_BOUND)])
+@pytest.mark.parametrize("n,N", [(5, 64), (150, 3000), (301, 20000), (129, 130), (400, 1000)])
+def test_gram_tc_matches_fp64(S, kind, tol, n, N):
+    """Every entry of Z Z^T / N and Z y~ / N within the error bound of its form (tiles of 128
+    rows, ragged edges, split over samples).  BF16 / FP16 operands: twice their unit
+    roundoff.  3xTF32 (kind 1): |z_i z_j - (h_i h_j + h_i l_j + l_i h_j)| <= 3 2^-22 |z_i z_j|
+    and sum |z_i z_j| / N <= 1 for standardised rows (Cauchy-Schwarz), plus the tensor
+    cores' FP32 accumulation over 512-sample runs: 2.4e-5, which a single TF32 product
+    (error up to 2^-11 = 4.9e-4) would miss by far."""
     Z, yc, sdy = _rows(n + N, n, N)
     G, b = S.gram_tc(Z, yc, sdy, kind)
     G64 = Z @ Z.T / N
     b64 = Z @ yc / N
-    assert np.abs(G - G64).max() <= 2 * rel
-    assert np.abs(b - b64).max() <= 2 * rel * sdy
-    # the diagonal of standardised rows is 1 up to the input rounding
-    assert np.abs(np.diag(G) - 1).max() <= 2 * rel
+    assert np.abs(G - G64).max() <= tol
+    assert np.abs(b - b64).max() <= tol * sdy
+    # the diagonal of standardised rows is 1 up to the same error
+    assert np.abs(np.diag(G) - 1).max() <= tol
 
 
 @pytest.mark.parametrize("kind", [2, 3])
@@ -70,3 +80,23 @@ def test_fit_mixed_equals_plain(S):
         assert [d.ids for d in mixed] == [d.ids for d in plain]
         for a, b in zip(mixed, plain):
             assert a.rmse == pytest.approx(b.rmse, rel=1e-5)
+
+
+@pytest.mark.parametrize("seed,N", [(0, 700), (1, 2500)])
+def test_fit_fp32_tf32x3_gram_matches_oracle(S, orc, seed, N):
+    """FP32 precision with the 3xTF32 tensor-core Gram (sisso_opts.gram = TF32X3) on
+    collinear data: the same screened subspaces and descriptors as the FP64 oracle; the
+    winner is refit in FP64 from the standardised rows, so coefficients and RMSE within
+    1e-6 relative."""
+    from paper_2410_01752_gb300 import inputs
+    P = inputs.workload3(seed, N=N, sis_size=25, max_dim=3)
+    sp = orc.Space(12, P.op_set, 2)
+    ref = orc.fit(P.X, P.y, sp, 25, 3)
+    with S.Sisso(P.X, P.y, P.op_set, 2, 25, 3, precision=1, gram=S.GRAM_TF32X3) as c:
+        got = c.fit()
+        for t, (g, r) in enumerate(zip(got, ref.dims)):
+            assert c.sis(t + 1) == ref.sis[t]
+            assert g.ids == r.ids
+            np.testing.assert_allclose(g.coef, r.coef, rtol=1e-6, atol=1e-9 * np.abs(P.y).max())
+            assert g.rmse == pytest.approx(r.rmse, rel=1e-6)
+    assert len(got) == len(ref.dims)
