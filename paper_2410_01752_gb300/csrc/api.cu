@@ -225,7 +225,7 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
         if (bytes <= ((size_t)8 << 30)) {
             if (o.precision == SISSO_PREC_FP64) st = dalloc(c, c->opcache64, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
             else st = dalloc(c, c->opcache32, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
-            if (!st) st = dalloc(c, c->opsum, 2 * (size_t)c->space.phi[rung - 1], "opsum");
+            if (!st) st = dalloc(c, c->opsum, 3 * (size_t)c->space.phi[rung - 1], "opsum");
             if (st) return bail(st);
         }
         // FP64 operand values (feature-major) for the exact re-score and duplicate checks

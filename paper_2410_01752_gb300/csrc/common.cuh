@@ -385,7 +385,7 @@ struct sisso_ctx {
     unsigned char* subvalid = nullptr; // FP64 validity (recursive) of every id of phi_{L-1}
     float* opcache32 = nullptr;        // values of phi_{L-1}, sample-major (N x id), or null
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
-    double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r (2 x |phi_{L-1}|)
+    double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r, sum (x - x0)^2 (3 x |phi_{L-1}|)
     int opsum_prec = -1;               // cache the first half was computed from (0 FP64, 1 FP32)
     double* opval64 = nullptr;         // FP64 values of phi_{L-1}, feature-major (id x N), or null
     int* dup_list = nullptr;           // per sorted entry: partner candidates (kDupSlots)
