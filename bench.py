@@ -1020,6 +1020,7 @@ def main():
                        "expr": [s.expr(i) for i in d_last.ids]} if d_last else None,
         "window_grown": sum(st["window_grown"] for st in stats),
         "window_saturated": max(st["window_saturated"] for st in stats),
+        "pm_keys_direct_per_fit": sum(st["pm_keys_direct"] for st in stats) / args.steps,
         "forms": forms,
     }
     print(json.dumps(line), flush=True)

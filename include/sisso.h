@@ -186,6 +186,9 @@ typedef struct {
     int screen_tc;               /* 1 if the top level's pairs were scored on the tensor cores */
     int64_t tc_keys_raised;      /* ... keys raised to their error bound (bound above the FP32
                                     screening margin, or the variance not resolved) */
+    int64_t pm_keys_direct;      /* FP32 top-level + / - candidates whose cross-sum key was left
+                                    open (operands that nearly cancel) and scored from the
+                                    direct sums instead, all steps */
 } sisso_stats;
 
 void sisso_default_opts(sisso_opts* opts);

@@ -51,7 +51,7 @@ void free_all(sisso_ctx* c) {
                     c->space_dev, c->surv_probe, c->zcache, c->subvalid, c->dup_list, c->dup_ok,
                     c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
                     c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info,
-                    c->unit_ok, c->unit_mask, c->opinv64};
+                    c->unit_ok, c->unit_mask, c->opinv64, c->fix_ids, c->fix_count};
     for (void* p : bufs)
         if (p) cudaFree(p);
     tc_screen_free(c);
@@ -226,6 +226,11 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
             if (o.precision == SISSO_PREC_FP64) st = dalloc(c, c->opcache64, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
             else st = dalloc(c, c->opcache32, (size_t)c->space.phi[rung - 1] * Nn, "opcache");
             if (!st) st = dalloc(c, c->opsum, 3 * (size_t)c->space.phi[rung - 1], "opsum");
+            if (!st && o.precision != SISSO_PREC_FP64) {
+                c->fix_cap = 1 << 20;
+                st = dalloc(c, c->fix_ids, (size_t)c->fix_cap, "fix_ids");
+                if (!st) st = dalloc(c, c->fix_count, 1, "fix_count");
+            }
             if (st) return bail(st);
         }
         // FP64 operand values (feature-major) for the exact re-score and duplicate checks

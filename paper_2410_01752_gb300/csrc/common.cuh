@@ -387,6 +387,9 @@ struct sisso_ctx {
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
     double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r, sum (x - x0)^2 (3 x |phi_{L-1}|)
     int opsum_prec = -1;               // cache the first half was computed from (0 FP64, 1 FP32)
+    unsigned long long* fix_ids = nullptr;  // FP32 pair kernel: + / - candidates left to the direct sums
+    unsigned* fix_count = nullptr;
+    int fix_cap = 0;
     double* opval64 = nullptr;         // FP64 values of phi_{L-1}, feature-major (id x N), or null
     int* dup_list = nullptr;           // per sorted entry: partner candidates (kDupSlots)
     unsigned char* dup_ok = nullptr;   // ... confirmed duplicates

@@ -355,7 +355,7 @@ k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const
 // ---------------------------------------------------------------------------------
 // fused generate-and-score for the top level's binary sections
 // ---------------------------------------------------------------------------------
-template <typename T, bool LIN>
+template <typename T, bool LIN, bool XS = false>
 __global__ void __launch_bounds__(NG * 32, sizeof(T) == 4 ? 2 : 1)
 k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
               const double* __restrict__ tc64, const TargetStats* __restrict__ st,
@@ -364,7 +364,36 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PairSmem<T>& S = *reinterpret_cast<PairSmem<T>*>(smem_raw);
     for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x)
-        pair_tile<T, LIN>(A, Xc, tc32, tc64, st, subvalid, cache, A1, AR, S, A.tiles[tile].x, A.tiles[tile].y);
+        pair_tile<T, LIN, XS>(A, Xc, tc32, tc64, st, subvalid, cache, A1, AR, S, A.tiles[tile].x, A.tiles[tile].y);
+}
+
+// + and - candidates whose key the cross-sum form left open (the pair nearly cancels): the
+// direct shifted sum of ((a - a0) +/- (b - b0))^2 from the FP32 operand cache, the values
+// the pair kernel would stage, one warp per candidate (lanes over samples)
+__global__ void k_fix_pm(PairArgs A, const float* __restrict__ cache, const TargetStats* __restrict__ st,
+                         const double* __restrict__ A1, const double* __restrict__ AR) {
+    const unsigned n = min(*A.fix_count, (unsigned)A.fix_cap);
+    const int lane = threadIdx.x & 31;
+    const float sum_t = TgtView<float>::sum(st), sd_t = TgtView<float>::sd(st);
+    for (unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n; e += (gridDim.x * blockDim.x) >> 5) {
+        const unsigned long long w = A.fix[e];
+        const int o = (int)(w >> 62);
+        const int64_t i = (int64_t)((w >> 31) & 0x7FFFFFFFull), j = (int64_t)(w & 0x7FFFFFFFull);
+        const float a0 = cache[i], b0 = cache[j];
+        float q = 0.f;
+        for (int s = lane; s < A.N; s += 32) {
+            const float at = cache[(size_t)s * A.P + i] - a0, bt = cache[(size_t)s * A.P + j] - b0;
+            const float v = o == 0 ? at + bt : at - bt;
+            q = fmaf(v, v, q);
+        }
+        q = warp_sum(q);
+        if (lane == 0) {
+            const Section& sc = A.sp->sec[A.sec[o]];
+            A.scores[sc.base + rank_of(sc, i, j)] =
+                o == 0 ? finalize_lin<float>(A1[i] + A1[j], q, AR[i] + AR[j], a0 + b0, A.N, sum_t, sd_t)
+                       : finalize_lin<float>(A1[i] - A1[j], q, AR[i] - AR[j], a0 - b0, A.N, sum_t, sd_t);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1386,18 +1415,43 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         }
         cudaEventRecord(e1, c->stream);
         const int grid = std::min<int>(A.n_tiles, c->sms * 16);
-#define SG_PAIRS(TT, LINV, XC, CACHE)                                                                  \
+#define SG_PAIRS(TT, LINV, XSV, XC, CACHE)                                                             \
     do {                                                                                                \
         const size_t sm = sizeof(PairSmem<TT>);                                                         \
-        cudaFuncSetAttribute(k_score_pairs<TT, LINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        k_score_pairs<TT, LINV><<<grid, NG * 32, sm, c->stream>>>(A, XC, c->tc32, c->tc64, c->tstats,        \
-                                                                  c->subvalid, CACHE, A1, AR);          \
+        cudaFuncSetAttribute(k_score_pairs<TT, LINV, XSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_score_pairs<TT, LINV, XSV><<<grid, NG * 32, sm, c->stream>>>(A, XC, c->tc32, c->tc64, c->tstats,  \
+                                                                       c->subvalid, CACHE, A1, AR);     \
     } while (0)
-        if (fp64) { if (cached) SG_PAIRS(double, true, c->Xc64, c->opcache64); else SG_PAIRS(double, false, c->Xc64, c->opcache64); }
-        else { if (cached) SG_PAIRS(float, true, c->Xc32, c->opcache32); else SG_PAIRS(float, false, c->Xc32, c->opcache32); }
-#undef SG_PAIRS
+        // FP32 with the operand cache: + and - from the cross sum, the open keys from the
+        // direct sums (k_fix_pm); if the open list overflows, the direct kernel again
+        const bool cross = !fp64 && cached && c->fix_ids;
+        if (cross) {
+            A.A2 = c->opsum + 2 * A.P;
+            A.fix = c->fix_ids; A.fix_count = c->fix_count; A.fix_cap = c->fix_cap;
+            cudaMemsetAsync(c->fix_count, 0, sizeof(unsigned), c->stream);
+        }
+        if (fp64) { if (cached) SG_PAIRS(double, true, false, c->Xc64, c->opcache64); else SG_PAIRS(double, false, false, c->Xc64, c->opcache64); }
+        else if (cross) SG_PAIRS(float, true, true, c->Xc32, c->opcache32);
+        else { if (cached) SG_PAIRS(float, true, false, c->Xc32, c->opcache32); else SG_PAIRS(float, false, false, c->Xc32, c->opcache32); }
         c->stats.launches++;
         c->stats.screen_pair_launches++;
+        if (cross) {
+            k_fix_pm<<<c->sms * 4, 256, 0, c->stream>>>(A, c->opcache32, c->tstats, A1, AR);
+            c->stats.launches++;
+            unsigned h_fix = 0;
+            cudaMemcpyAsync(&h_fix, c->fix_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+            if ((st = check_cuda(c, cudaStreamSynchronize(c->stream), "score_pairs cross"))) {
+                cudaFreeAsync(d_tiles, c->stream);
+                return st;
+            }
+            c->stats.pm_keys_direct += (int64_t)h_fix;
+            if (h_fix > (unsigned)c->fix_cap) {
+                SG_PAIRS(float, true, false, c->Xc32, c->opcache32);
+                c->stats.launches++;
+                c->stats.screen_pair_launches++;
+            }
+        }
+#undef SG_PAIRS
         st = check_cuda(c, cudaGetLastError(), "score_pairs");
         cudaFreeAsync(d_tiles, c->stream);
         if (st) return st;

@@ -77,6 +77,30 @@ __device__ __forceinline__ float finalize_lin(double s1, T s2, double sr, T v0, 
     return finalize<T>((T)s1, s2, (T)sr, v0, N, sum_t, sd_t);
 }
 
+// + and - from the cross sum (FP32 form): the sum of v'^2 is q2 = A2[a] + A2[b] +/- 2 X with
+// X = sum a'b' accumulated in FP32 and |q2 - the exact sum| <= dq.  Where dq cannot change
+// the key by more than a small share of the FP32 screening margin (dq / N <= kCrossTol var,
+// a relative score change <= 5e-5) the score is final; where it could (a and b nearly
+// cancel) or where it decides the validity tests, kCrossOpen asks for the direct sums.
+constexpr float kCrossTol = 1e-4f;
+constexpr float kCrossOpen = -2.f;
+__device__ __forceinline__ float finalize_x(double s1d, double q2d, float dq, double srd, float v0, int N, float sum_t,
+                                            float sd_t) {
+    const float s1 = (float)s1d, s2 = (float)q2d, sr = (float)srd;
+    const float inv_n = 1.f / (float)N;
+    const float ms = s1 * inv_n;
+    const float var = s2 * inv_n - ms * ms;
+    const float cov = sr * inv_n - ms * (sum_t * inv_n);
+    const float mean = v0 + ms;
+    const bool finite = isfinite(s1) && isfinite(s2) && isfinite(sr) && isfinite(v0) && isfinite(dq);
+    if (!finite || !(fabsf(v0) <= (float)kValueCap)) return -1.f;
+    const float dv = dq * inv_n;
+    const float lim = (float)kConstRel * fmaxf(fabsf(v0), fabsf(mean));
+    if (!(var + dv > 0.f) || !(sqrtf(var + dv) > lim)) return -1.f;       // rejected at either end
+    if (!(dv <= kCrossTol * var) || !(sqrtf(var - dv) > lim)) return kCrossOpen;
+    return fabsf(cov) / (sqrtf(var) * sd_t);
+}
+
 template <typename T> struct TgtView;
 template <> struct TgtView<float> {
     __device__ static const float* tc(const float* t32, const double*) { return t32; }
@@ -104,6 +128,12 @@ struct PairArgs {
     const int2* tiles;
     int n_tiles;
     float* scores;
+    // cross-sum form of + and - (FP32 with the operand cache): per-operand sums of squared
+    // shifted values, and the list of candidates whose key the cross sum leaves open
+    const double* A2;
+    unsigned long long* fix;
+    unsigned* fix_count;
+    int fix_cap;
 };
 
 // four consecutive values from shared memory (16-byte aligned)
@@ -413,7 +443,7 @@ __device__ __forceinline__ f2 f2sub(f2 a, f2 b) {
 // One 32 x 32 tile of operand pairs (i0.., j0..): stage operands chunk by chunk, accumulate
 // the shifted sums of + - * a/b b/a for 4 pairs per thread, write the scores.  Called by
 // every thread of an 8-warp CTA; S is that CTA's shared memory.
-template <typename T, bool LIN>
+template <typename T, bool LIN, bool XS = false>
 __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict__ Xc, const float* __restrict__ tc32,
                                           const double* __restrict__ tc64, const TargetStats* __restrict__ st,
                                           const unsigned char* __restrict__ subvalid, const T* __restrict__ cache,
@@ -464,13 +494,18 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
     // FP32 with per-operand sums: the same sums kept in pairs of i operands (q, q + 1), two FP32
     // lanes per register (fma/add/sub.f32x2: half the FP32 instructions to issue)
     constexpr bool kPair = std::is_same<T, float>::value && LIN;
+    // cross-sum form (XS): + and - keep only X = sum a'b' per pair, in 32-sample runs (XC)
+    // added into XT, so the rounding of X stays within (TS + runs + 2) u sum |a'b'|
+    constexpr bool kX = kPair && XS;
     constexpr int RH = RI / 2;
     f2 Q2[2][RH], L1[2][RH], LR[2][RH], S1[3][RH], S2[3][RH], SR[3][RH], NKM[RH], NKD[RH], NKE[RH];
+    f2 XT[RH], XC[RH];
     if constexpr (kPair) {
 #pragma unroll
         for (int h = 0; h < RH; ++h) {
             const f2 z = f2pk(0.f, 0.f);
             Q2[0][h] = Q2[1][h] = L1[0][h] = L1[1][h] = LR[0][h] = LR[1][h] = z;
+            XT[h] = XC[h] = z;
 #pragma unroll
             for (int o = 0; o < 3; ++o) { S1[o][h] = z; S2[o][h] = z; SR[o][h] = z; }
             NKM[h] = f2pk(-(float)Km[2 * h], -(float)Km[2 * h + 1]);
@@ -501,10 +536,14 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
 #pragma unroll
                 for (int h = 0; h < RH; ++h) {
                     f2 v;
+                    if constexpr (kX) {
+                        XC[h] = f2fma(atp[h], bt2, XC[h]);
+                    } else {
                     v = f2add(atp[h], bt2);           Q2[0][h] = f2fma(v, v, Q2[0][h]);
                     if constexpr (!LIN) { L1[0][h] = f2add(L1[0][h], v); LR[0][h] = f2fma(v, r2, LR[0][h]); }
                     v = f2sub(atp[h], bt2);           Q2[1][h] = f2fma(v, v, Q2[1][h]);
                     if constexpr (!LIN) { L1[1][h] = f2add(L1[1][h], v); LR[1][h] = f2fma(v, r2, LR[1][h]); }
+                    }
                     v = f2fma(avp[h], bv2, NKM[h]);   S1[0][h] = f2add(S1[0][h], v); S2[0][h] = f2fma(v, v, S2[0][h]); SR[0][h] = f2fma(v, r2, SR[0][h]);
                     v = f2fma(avp[h], br2, NKD[h]);   S1[1][h] = f2add(S1[1][h], v); S2[1][h] = f2fma(v, v, S2[1][h]); SR[1][h] = f2fma(v, r2, SR[1][h]);
                     v = f2fma(bv2, arp[h], NKE[h]);   S1[2][h] = f2add(S1[2][h], v); S2[2][h] = f2fma(v, v, S2[2][h]); SR[2][h] = f2fma(v, r2, SR[2][h]);
@@ -535,17 +574,23 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         } else {
             for (int s = 0; s < ns; ++s) step(s);
         }
+        if constexpr (kX) {
+#pragma unroll
+            for (int h = 0; h < RH; ++h) { XT[h] = f2add(XT[h], XC[h]); XC[h] = f2pk(0.f, 0.f); }
+        }
         if (more) stage_store<T>(S, b ^ 1, pf, py, g, lane);
         __syncthreads();
     }
 
+    float xs[RI];     // cross sums (kX)
     if constexpr (kPair) {
 #pragma unroll
         for (int h = 0; h < RH; ++h) {
             float a, b;
+            if constexpr (kX) { f2up(XT[h], a, b); xs[2 * h] = a; xs[2 * h + 1] = b; }
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
-                f2up(Q2[o][h], a, b); q2[o][2 * h] = a; q2[o][2 * h + 1] = b;
+                if constexpr (!kX) { f2up(Q2[o][h], a, b); q2[o][2 * h] = a; q2[o][2 * h + 1] = b; }
                 f2up(L1[o][h], a, b); l1[o][2 * h] = a; l1[o][2 * h + 1] = b;
                 f2up(LR[o][h], a, b); lr[o][2 * h] = a; lr[o][2 * h + 1] = b;
             }
@@ -573,6 +618,34 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
         const T keq = kPair ? b0 * rcp<T>(a0) : Ke[q];
         const bool opv = okj && S.ok[g * RI + q];   // both operands valid
         const double a1i = lin ? A1[i] : 0.0, ari = lin ? AR[i] : 0.0;
+        if constexpr (kX) {
+            if (A.sec[0] >= 0 || A.sec[1] >= 0) {
+                // rounding bound of X: (TS + runs + 2) u per unit of sum |a'b'| <= sqrt(A2[i] A2[j]),
+                // twice in q2 (u = 2^-24; 0.1% for second-order terms)
+                const double a2i = A.A2[i], a2j = A.A2[j];
+                const double a2s = a2i + a2j, x2 = 2.0 * (double)xs[q];
+                const float dq = 2.002f * (float)(TS + (N + TS - 1) / TS + 2) * 5.9604645e-8f *
+                                 sqrtf((float)a2i) * sqrtf((float)a2j);
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    if (A.sec[o] < 0) continue;
+                    const Section& sc = A.sp->sec[A.sec[o]];
+                    float v = -1.f;
+                    if (opv) {
+                        v = o == 0 ? finalize_x(a1i + a1j, a2s + x2, dq, ari + arj, a0 + b0, N, sum_t, sd_t)
+                                   : finalize_x(a1i - a1j, a2s - x2, dq, ari - arj, a0 - b0, N, sum_t, sd_t);
+                        if (v == kCrossOpen) {      // scored by the direct sums afterwards
+                            const unsigned slot = atomicAdd(A.fix_count, 1u);
+                            if (slot < (unsigned)A.fix_cap)
+                                A.fix[slot] = ((unsigned long long)o << 62) | ((unsigned long long)i << 31) |
+                                              (unsigned long long)j;
+                            v = -1.f;
+                        }
+                    }
+                    A.scores[sc.base + rank_of(sc, i, j)] = v;
+                }
+            }
+        } else {
         if (A.sec[0] >= 0) {
             const Section& sc = A.sp->sec[A.sec[0]];
             float v = -1.f;
@@ -586,6 +659,7 @@ __device__ __forceinline__ void pair_tile(const PairArgs& A, const T* __restrict
             if (opv) v = lin ? finalize_lin<T>(a1i - a1j, q2[1][q], ari - arj, a0 - b0, N, sum_t, sd_t)
                              : finalize<T>(l1[1][q], q2[1][q], lr[1][q], a0 - b0, N, sum_t, sd_t);
             A.scores[sc.base + rank_of(sc, i, j)] = v;
+        }
         }
         if (A.sec[2] >= 0) {
             const Section& sc = A.sp->sec[A.sec[2]];

@@ -76,7 +76,7 @@ class Stats(C.Structure):
                 ("ms_gram", C.c_double), ("ms_l0", C.c_double), ("ms_refit", C.c_double),
                 ("ms_fit", C.c_double), ("ms_l0_enum", C.c_double), ("l0_enum_launches", C.c_int),
                 ("l0_candidates", C.c_int64), ("certified_prefixes", C.c_int64),
-                ("screen_tc", C.c_int), ("tc_keys_raised", C.c_int64)]
+                ("screen_tc", C.c_int), ("tc_keys_raised", C.c_int64), ("pm_keys_direct", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

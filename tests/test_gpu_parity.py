@@ -96,6 +96,23 @@ def test_score_all(S, orc, name, make, names, rung, g, prec):
     assert err.max() <= tol, (err.max(), sp.expr(int(np.where(valid)[0][np.argmax(err)])))
 
 
+def test_cross_sum_keys_left_open(S, orc):
+    """FP32 + and - from the cross sum: on six primaries correlated 0.999 the operands x_i - x_j
+    cancel against each other, the cross sum's rounding bound leaves those keys open, and the
+    direct sums score them -- every score within the margin of the oracle's and no valid
+    candidate rejected."""
+    P = inputs.workload3(0, N=3000)
+    m = _mask(orc, ALL9)
+    sp = orc.Space(P.X.shape[1], m, 2, 0)
+    ref, valid = sp.scores(P.X, P.y)
+    with _ctx(S, P.X, P.y, m, 2, 5, 2, 1) as c:
+        got = c.score_all(P.y, 1)
+        opened = c.stats()["pm_keys_direct"]
+    assert opened > 0
+    assert not np.any((got < 0) & valid)
+    assert np.abs(got[valid].astype(np.float64) - ref[valid]).max() <= FP32_SCORE_TOL
+
+
 # ---------------------------------------------------------------------------------
 # one SIS step: device-wide selection, FP64 re-score, walk
 # ---------------------------------------------------------------------------------
