@@ -47,6 +47,25 @@ __global__ void k_fill_val64(const Space* __restrict__ sp, const double* __restr
         V[(size_t)id * N + s] = ok ? eval_prog<double>(p, [&](int c) { return Xc[(size_t)c * N + s]; }) : NAN;
 }
 
+// the FP64 values of the ids [lo, hi) of one level >= 2 from the stored values of the levels
+// below: one operation per sample on the operands' rows, the operation eval_prog applies last
+// (a op b, or op(a)), on the values its sub-programs produce, so the values are bitwise those
+// of the full programs (one warp per id, lanes over samples)
+__global__ void k_fill_val64_level(const Space* __restrict__ sp, int N, int64_t lo, int64_t hi,
+                                   double* __restrict__ V) {
+    const int64_t id = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (id >= hi) return;
+    int level, op;
+    int64_t a, b;
+    const bool ok = decode(*sp, id, level, op, a, b) && a >= 0 && a < lo && b < lo;
+    double* out = V + (size_t)id * N;
+    const double* va = V + (size_t)(ok ? a : 0) * N;
+    const double* vb = V + (size_t)(ok && b >= 0 ? b : 0) * N;
+    for (int s = lane; s < N; s += 32)
+        out[s] = !ok ? NAN : b >= 0 ? op_binary<double>(op, va[s], vb[s]) : op_unary<double>(op, va[s]);
+}
+
 // 1/x of every FP64 operand value (the re-score's divisions become products)
 __global__ void k_fill_inv64(const double* __restrict__ V, int64_t total, double* __restrict__ inv) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
@@ -355,6 +374,8 @@ k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const
 // ---------------------------------------------------------------------------------
 // fused generate-and-score for the top level's binary sections
 // ---------------------------------------------------------------------------------
+constexpr int kCrossMaxN = 4096;      // samples up to which + and - use the cross sum
+
 template <typename T, bool LIN, bool XS = false>
 __global__ void __launch_bounds__(NG * 32, sizeof(T) == 4 ? 2 : 1)
 k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc32,
@@ -368,9 +389,10 @@ k_score_pairs(PairArgs A, const T* __restrict__ Xc, const float* __restrict__ tc
 }
 
 // + and - candidates whose key the cross-sum form left open (the pair nearly cancels): the
-// direct shifted sum of ((a - a0) +/- (b - b0))^2 from the FP32 operand cache, the values
-// the pair kernel would stage, one warp per candidate (lanes over samples)
-__global__ void k_fix_pm(PairArgs A, const float* __restrict__ cache, const TargetStats* __restrict__ st,
+// direct shifted sum of ((a - a0) +/- (b - b0))^2 over the values the pair kernel stages
+// (the FP32 operand cache is the FP64 operand rows rounded once, so the rows are read
+// feature-major and rounded here: coalesced), one warp per candidate, lanes over samples
+__global__ void k_fix_pm(PairArgs A, const double* __restrict__ V, const TargetStats* __restrict__ st,
                          const double* __restrict__ A1, const double* __restrict__ AR) {
     const unsigned n = min(*A.fix_count, (unsigned)A.fix_cap);
     const int lane = threadIdx.x & 31;
@@ -379,10 +401,12 @@ __global__ void k_fix_pm(PairArgs A, const float* __restrict__ cache, const Targ
         const unsigned long long w = A.fix[e];
         const int o = (int)(w >> 62);
         const int64_t i = (int64_t)((w >> 31) & 0x7FFFFFFFull), j = (int64_t)(w & 0x7FFFFFFFull);
-        const float a0 = cache[i], b0 = cache[j];
+        const double* vi = V + (size_t)i * A.N;
+        const double* vj = V + (size_t)j * A.N;
+        const float a0 = (float)vi[0], b0 = (float)vj[0];
         float q = 0.f;
         for (int s = lane; s < A.N; s += 32) {
-            const float at = cache[(size_t)s * A.P + i] - a0, bt = cache[(size_t)s * A.P + j] - b0;
+            const float at = (float)vi[s] - a0, bt = (float)vj[s] - b0;
             const float v = o == 0 ? at + bt : at - bt;
             q = fmaf(v, v, q);
         }
@@ -1229,8 +1253,17 @@ sisso_status compute_subvalid(sisso_ctx* c) {
 sisso_status fill_val64(sisso_ctx* c) {
     if (!c->opval64) return SISSO_OK;
     const int64_t n = c->space.phi[c->rung - 1];
-    k_fill_val64<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n, c->opval64);
+    // levels 0 and 1 from the primaries, every higher level from the one below
+    const int64_t n01 = c->rung - 1 >= 1 ? c->space.phi[1] : n;
+    k_fill_val64<<<(int)((n01 * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, n01, c->opval64);
     c->stats.launches++;
+    for (int l = 2; l <= c->rung - 1; ++l) {
+        const int64_t lo = c->space.phi[l - 1], hi = c->space.phi[l];
+        if (hi <= lo) continue;
+        k_fill_val64_level<<<(int)(((hi - lo) * 32 + 255) / 256), 256, 0, c->stream>>>(c->space_dev, c->N, lo, hi,
+                                                                                         c->opval64);
+        c->stats.launches++;
+    }
     if (c->opinv64) {
         const int64_t total = n * (int64_t)c->N;
         k_fill_inv64<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sms * 16, (total + 255) / 256)), 256, 0,
@@ -1423,8 +1456,11 @@ sisso_status score_all(sisso_ctx* c, int precision) {
                                                                        c->subvalid, CACHE, A1, AR);     \
     } while (0)
         // FP32 with the operand cache: + and - from the cross sum, the open keys from the
-        // direct sums (k_fix_pm); if the open list overflows, the direct kernel again
-        const bool cross = !fp64 && cached && c->fix_ids;
+        // direct sums (k_fix_pm); if the open list overflows, the direct kernel again.  The
+        // cross sum's rounding bound grows with the number of 32-sample runs: up to 4096
+        // samples (128 runs) it leaves open only pairs that nearly cancel, beyond that most
+        // keys, so longer problems keep the direct sums
+        const bool cross = !fp64 && cached && c->fix_ids && c->opval64 && c->N <= kCrossMaxN;
         if (cross) {
             A.A2 = c->opsum + 2 * A.P;
             A.fix = c->fix_ids; A.fix_count = c->fix_count; A.fix_cap = c->fix_cap;
@@ -1436,7 +1472,7 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         c->stats.launches++;
         c->stats.screen_pair_launches++;
         if (cross) {
-            k_fix_pm<<<c->sms * 4, 256, 0, c->stream>>>(A, c->opcache32, c->tstats, A1, AR);
+            k_fix_pm<<<c->sms * 4, 256, 0, c->stream>>>(A, c->opval64, c->tstats, A1, AR);
             c->stats.launches++;
             unsigned h_fix = 0;
             cudaMemcpyAsync(&h_fix, c->fix_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
