@@ -88,6 +88,8 @@ def lib():
                                     C.c_int, C.c_double, i64p, C.c_int]
         L.oracle_fit_ex.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, ip, C.c_int,
                                     C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(_Result)]
+        L.oracle_fit_w.argtypes = [dp, dp, C.c_int, C.c_int, C.c_uint32, C.c_int, C.c_int, ip, dp, C.c_int,
+                                   C.c_int, C.c_double, C.c_double, C.c_int, C.POINTER(_Result)]
         L.oracle_mi_kde.argtypes = [dp, C.c_int, C.c_int, dp, dp]
         L.oracle_spearman.argtypes = [dp, C.c_int, C.c_int, dp, dp]
         L.oracle_prescreen_keep.argtypes = [dp, C.c_int, C.c_double, ip]
@@ -249,17 +251,25 @@ class FitResult:
 
 
 def fit(X, y, space: Space, k: int, max_dim: int, nthreads: int = 0, sis_threshold: float = 0.0,
-        stop_rmse: float = 0.0) -> FitResult:
+        stop_rmse: float = 0.0, W=None) -> FitResult:
     """The SISSO iteration of §2.3 (Eq. 8) on the feature space of §2.1; sis_threshold > 0:
     the threshold variant of SIS (§2.2), stop_rmse > 0: stop once a step's RMSE is at or
-    below it (§2.3, "low enough error")."""
+    below it (§2.3, "low enough error"); W (N x N): SISSO on the whitened data W y, W Phi
+    (§2.4)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     r = _Result()
     up, keep = space._units_ptr()
-    rc = lib().oracle_fit_ex(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
-                             space.grammar, up, k, max_dim, float(sis_threshold), float(stop_rmse), nthreads,
-                             C.byref(r))
+    if W is None:
+        rc = lib().oracle_fit_ex(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
+                                 space.grammar, up, k, max_dim, float(sis_threshold), float(stop_rmse), nthreads,
+                                 C.byref(r))
+    else:
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        assert W.shape == (X.shape[0], X.shape[0])
+        rc = lib().oracle_fit_w(_dp(X), _dp(y), X.shape[0], X.shape[1], space.ops, space.rung,
+                                space.grammar, up, _dp(W), k, max_dim, float(sis_threshold), float(stop_rmse),
+                                nthreads, C.byref(r))
     if rc:
         raise ValueError(f"oracle_fit failed ({rc})")
     out = FitResult()

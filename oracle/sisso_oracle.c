@@ -37,6 +37,13 @@
  *  - Stop (§2.3, "low enough error"): after a step whose RMSE <= 1e-10 * std(y) (the fit
  *    is exact to FP64 rounding), after a step whose RMSE is at or below the caller's
  *    tolerance (stop_rmse > 0), or when S holds fewer than t features.
+ *  - Whitening (§2.4: W = Sigma^-1/2, y~ = W y, Phi~ = W Phi, then SISSO in the transformed
+ *    space): every candidate is evaluated on the samples and checked by the rules above
+ *    on those raw values; its column is then mapped to W v, and that column must pass the
+ *    same finite / cap / near-constant rules.  Scores, standardised vectors, the Gram and
+ *    the refit use the whitened columns and the whitened target W y; the intercept stays
+ *    a constant column in the transformed space (the paper fits SISSO, intercept included,
+ *    to the transformed data), and coefficients, residuals and RMSE are those of that fit.
  *  - Dimensional analysis (§2.1, closing paragraph; §3.3 dimensionality, one unit label per
  *    primary): units are exponent vectors over the labels; + and - need equal units,
  *    exp, log, sin and exp(-.) a dimensionless operand, the other operators combine
@@ -75,7 +82,21 @@ typedef struct {
     int64_t phi[ORC_MAX_RUNG + 1];                 /* |phi_l|, cumulative */
     int64_t sec[ORC_MAX_RUNG + 1][ORC_NOPS];       /* features new at level l by op */
     const int* units;                              /* unit label per primary (-1: none), or NULL */
+    const double* W;                               /* whitening matrix (N x N, row-major), or NULL */
 } space_t;
+
+/* v <- W v (§2.4); a no-op without whitening */
+static void whiten(const space_t* s, int N, double* v) {
+    if (!s->W) return;
+    double* t = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int i = 0; i < N; i++) {
+        double acc = 0.0;
+        for (int k = 0; k < N; k++) acc += s->W[(size_t)i * N + k] * v[k];
+        t[i] = acc;
+    }
+    memcpy(v, t, sizeof(double) * (size_t)N);
+    free(t);
+}
 
 static int op_is_binary(int op) { return op <= ORC_DIV; }
 static int op_enabled(const space_t* s, int op) { return (s->ops >> op) & 1u; }
@@ -121,6 +142,7 @@ static int64_t row_count(const space_t* s, int l, int op, int64_t i) {
 }
 
 static int space_init(space_t* s, int d, uint32_t ops, int rung, int grammar) {
+    s->W = NULL;
     if (d < 1 || rung < 0 || rung > ORC_MAX_RUNG) return -1;
     memset(s, 0, sizeof(*s));
     s->d = d; s->ops = ops; s->rung = rung; s->grammar = grammar;
@@ -432,6 +454,10 @@ static void* score_worker(void* p) {
                  moments(v, j->N, &m, &sd) && units_ok(j->s, id);
         if (ok && decode(j->s, id, &level, &op, &a, &b) == 0 && level > 0)
             ok = valid_rec(j->s, j->X, j->N, a) && (b < 0 || valid_rec(j->s, j->X, j->N, b));
+        if (ok && j->s->W) {             /* the whitened column passes the same rules */
+            whiten(j->s, j->N, v);
+            ok = moments(v, j->N, &m, &sd);
+        }
         j->valid[q] = ok;
         j->score[q] = ok ? pearson(v, j->N, m, sd, j->tc, j->tsd) : 0.0;
     }
@@ -584,7 +610,7 @@ static void* level_score_worker(void* p) {
    written) when the table would not fit in LEVEL_TABLE_MAX_BYTES or rung < 1 */
 static int scores_all_levelwise(const space_t* s, const double* X, int N, const double* tc, double tsd,
                                 double* score, int* valid, int nthreads) {
-    if (s->rung < 1) return -1;
+    if (s->rung < 1 || s->W) return -1;            /* whitened columns: the per-id path */
     int64_t P = s->phi[s->rung - 1];
     if ((size_t)P * (size_t)N > LEVEL_TABLE_MAX_BYTES / sizeof(double)) return -1;
     double* vals = (double*)malloc(sizeof(double) * (size_t)P * (size_t)N);
@@ -638,6 +664,10 @@ static int standardised(const space_t* s, const double* X, int N, int64_t id, do
     double m, sd;
     int cancelled;
     if (eval_checked(s, X, N, id, z, &cancelled) || cancelled || !moments(z, N, &m, &sd)) return -1;
+    if (s->W) {
+        whiten(s, N, z);
+        if (!moments(z, N, &m, &sd)) return -1;
+    }
     for (int i = 0; i < N; i++) z[i] = (z[i] - m) / sd;
     return 0;
 }
@@ -937,11 +967,24 @@ int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int
 int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
                   int grammar, const int* units, int k, int max_dim, double sis_threshold, double stop_rmse,
                   int nthreads, oracle_result* out) {
+    return oracle_fit_w(X, y, N, d, ops, rung, grammar, units, NULL, k, max_dim, sis_threshold, stop_rmse,
+                        nthreads, out);
+}
+
+int oracle_fit_w(const double* X, const double* y_in, int N, int d, uint32_t ops, int rung,
+                 int grammar, const int* units, const double* W, int k, int max_dim, double sis_threshold,
+                 double stop_rmse, int nthreads, oracle_result* out) {
     space_t s;
     if (space_init(&s, d, ops, rung, grammar) || N < 2 || k < 1 || k > 1024 ||
         max_dim < 1 || max_dim > ORC_MAX_DIM || N < max_dim + 1 || sis_threshold < 0.0 ||
         stop_rmse < 0.0) return -1;
     s.units = units;
+    s.W = W;
+    /* whitening (§2.4): SISSO on W y and W Phi */
+    double* yw = (double*)malloc(sizeof(double) * (size_t)N);
+    memcpy(yw, y_in, sizeof(double) * (size_t)N);
+    whiten(&s, N, yw);
+    const double* y = yw;
     memset(out, 0, sizeof(*out));
     double ybar = 0.0, sst = 0.0;
     for (int i = 0; i < N; i++) ybar += y[i];
@@ -988,7 +1031,10 @@ int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, 
             for (int c = a; c > 0 && ids[c - 1] > ids[c]; c--) { int64_t tmp = ids[c]; ids[c] = ids[c - 1]; ids[c - 1] = tmp; }
         double* A = (double*)malloc(sizeof(double) * (size_t)N * (size_t)(t + 1));
         for (int i = 0; i < N; i++) A[i] = 1.0;
-        for (int j = 0; j < t; j++) eval_rec(&s, X, N, ids[j], A + (size_t)(j + 1) * N);
+        for (int j = 0; j < t; j++) {
+            eval_rec(&s, X, N, ids[j], A + (size_t)(j + 1) * N);
+            whiten(&s, N, A + (size_t)(j + 1) * N);
+        }
         double coef[ORC_MAX_DIM + 1];
         if (lstsq_qr(A, y, N, t + 1, coef)) { free(A); rc = -4; break; }
         double rss = 0.0;
@@ -1011,7 +1057,7 @@ int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, 
         /* "low enough error" (§2.3): the caller's RMSE tolerance */
         if (stop_rmse > 0.0 && out->rmse[di] <= stop_rmse) break;
     }
-    free(yc); free(target);
+    free(yc); free(target); free(yw);
     return rc;
 }
 

@@ -100,6 +100,12 @@ int oracle_fit(const double* X, const double* y, int N, int d, uint32_t ops, int
 int oracle_fit_ex(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
                   int grammar, const int* units, int k, int max_dim, double sis_threshold, double stop_rmse,
                   int nthreads, oracle_result* out);
+/* the same on whitened data (§2.4): W (N x N, row-major; NULL = none) maps the target and
+   every candidate column, SISSO then runs on W y and W Phi (the intercept a constant column
+   in the transformed space); coefficients, RMSE and R^2 are those of the transformed fit */
+int oracle_fit_w(const double* X, const double* y, int N, int d, uint32_t ops, int rung,
+                 int grammar, const int* units, const double* W, int k, int max_dim, double sis_threshold,
+                 double stop_rmse, int nthreads, oracle_result* out);
 
 #ifdef __cplusplus
 }

@@ -147,13 +147,19 @@ def best_subset(cols: np.ndarray, y: np.ndarray, D: int, gid: list[int]):
 
 
 def sisso(X: np.ndarray, y: np.ndarray, d: int, ops: list[str], rung: int, k: int, T: int,
-          new_x_prev: bool = False, thr: float = 0.0, stop_rmse: float = 0.0):
+          new_x_prev: bool = False, thr: float = 0.0, stop_rmse: float = 0.0, W=None):
     """The whole iteration of §2.3 (Eq. 8) by brute force: SIS on y, then on the residual
     of the best t-term lstsq fit; l0 over all t-subsets of S_t.  thr: threshold SIS;
-    stop_rmse: stop after a step whose RMSE is at or below it."""
+    stop_rmse: stop after a step whose RMSE is at or below it.  W: whitening (§2.4), every
+    feature valid on the samples is mapped to W v (and must pass the value rules there),
+    the target to W y, and the iteration runs on those."""
     feats, _ = space(d, ops, rung, new_x_prev)
     values = [evaluate(f, X) for f in feats]
     ok = [valid(v, f, X) for v, f in zip(values, feats)]
+    if W is not None:
+        values = [W @ v if o else v for v, o in zip(values, ok)]
+        ok = [o and valid(v) for v, o in zip(values, ok)]
+        y = W @ y
     S: list[int] = []
     out = []
     target = y.copy()
