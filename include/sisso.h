@@ -154,6 +154,19 @@ typedef struct {
                                the mixed forms do (a learned proposal set on the context is
                                not used).
                                Other precisions accept AUTO or FP64 only. */
+    const double* whiten;   /* whitening (§2.4): W = Sigma^-1/2 (N x N, row-major FP64, host
+                               or device, copied by sisso_create) for noise with a known
+                               covariance Sigma; SISSO then runs on W y and W Phi: every
+                               candidate valid on the samples is mapped to W v (which must
+                               pass the same value rules), the intercept stays a constant
+                               column in the transformed space, and coefficients, RMSE and
+                               R^2 are those of the transformed fit.  Needs SISSO_PREC_FP64
+                               and no pre-screening (else SISSO_ERR_ARG); candidates are
+                               scored row by row (an N x N FP64 product per candidate), and
+                               the FP64 operand values and the window's vectors must fit
+                               (else SISSO_ERR_CAPACITY).  Targets passed to
+                               sisso_score_all / sisso_sis_step on such a context are taken
+                               as already whitened.  NULL = none (the default). */
 } sisso_opts;
 
 /* Per-context counters and device timings (CUDA events on the context's stream). */

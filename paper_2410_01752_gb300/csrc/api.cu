@@ -55,6 +55,7 @@ void free_all(sisso_ctx* c) {
     for (void* p : bufs)
         if (p) cudaFree(p);
     tc_screen_free(c);
+    whiten_free(c);
     if (c->walk_h) cudaFreeHost(c->walk_h);
     if (c->win_h) cudaFreeHost(c->win_h);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -74,6 +75,10 @@ sisso_status validate(int N, int d, uint32_t ops, int rung, int k, int max_dim, 
     if (!(o.sis_threshold >= 0.0 && o.sis_threshold < 1.0)) { why = "sis_threshold must be in [0, 1)"; return SISSO_ERR_ARG; }
     if (!(o.stop_rmse >= 0.0)) { why = "stop_rmse must be >= 0"; return SISSO_ERR_ARG; }
     if (o.screen < SISSO_SCREEN_AUTO || o.screen > SISSO_SCREEN_TENSOR) { why = "bad screen option"; return SISSO_ERR_ARG; }
+    if (o.whiten && (o.precision != SISSO_PREC_FP64 || o.prescreen != SISSO_PRESCREEN_NONE)) {
+        why = "whitening needs SISSO_PREC_FP64 and no pre-screening";
+        return SISSO_ERR_ARG;
+    }
     if (o.gram < SISSO_GRAM_AUTO || o.gram > SISSO_GRAM_TF32X3 ||
         (o.gram == SISSO_GRAM_TF32X3 && o.precision != SISSO_PREC_FP32)) {
         why = "bad gram option (the 3xTF32 Gram is an FP32-precision form)";
@@ -265,6 +270,14 @@ sisso_status sisso_create(const double* X, const double* y, int N, int d, uint32
     const bool mixed_form = o.precision == SISSO_PREC_MIXED_BF16 || o.precision == SISSO_PREC_MIXED_FP16;
     if (!st && mixed_form && o.screen != SISSO_SCREEN_CORES && c->opval64 && tc_screen_possible(c, o.screen))
         st = tc_screen_alloc(c);
+    if (!st && o.whiten) {
+        // whitening (§2.4) runs row by row from the FP64 operand values and keeps every
+        // window vector
+        if (!c->opval64 || c->zcap < c->surv_cap)
+            st = fail(c, SISSO_ERR_CAPACITY, "whitening: FP64 operand values or window vectors do not fit");
+        else
+            st = whiten_setup(c, o.whiten);
+    }
     if (!st) st = prepare_target(c, c->y64);
     cudaMemcpyAsync(c->yc64, c->tc64, sizeof(double) * Nn, cudaMemcpyDeviceToDevice, c->stream);
     TargetStats ts{};

@@ -387,6 +387,13 @@ struct sisso_ctx {
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
     double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r, sum (x - x0)^2 (3 x |phi_{L-1}|)
     int opsum_prec = -1;               // cache the first half was computed from (0 FP64, 1 FP32)
+    double* Wm = nullptr;              // whitening matrix W (N x N), or null (§2.4)
+    double* w_raw = nullptr;           // whitened path: raw rows, whitened rows (w_chunk x N each),
+    double* w_u = nullptr;             //   per-row scratch (3 w_chunk), probes, raw validity
+    double* w_scr = nullptr;
+    double* w_probe = nullptr;
+    int* w_ok = nullptr;
+    int w_chunk = 0;
     unsigned long long* fix_ids = nullptr;  // FP32 pair kernel: + / - candidates left to the direct sums
     unsigned* fix_count = nullptr;
     int fix_cap = 0;
@@ -498,6 +505,14 @@ sisso_status fill_opcache(sisso_ctx* c);
 sisso_status fill_val64(sisso_ctx* c);
 sisso_status prepare_target(sisso_ctx* c, const double* target_dev);
 sisso_status score_all(sisso_ctx* c, int precision);
+void apply_unit_mask(sisso_ctx* c);
+// whitened data (whiten.cu)
+sisso_status whiten_setup(sisso_ctx* c, const double* W);
+void whiten_free(sisso_ctx* c);
+sisso_status whiten_score_all(sisso_ctx* c);
+sisso_status whiten_rescore(sisso_ctx* c, const int64_t* ids, int n, double* score, double* mean, double* sd,
+                            int* valid, double* probe, double* zc);
+sisso_status whiten_standardise(sisso_ctx* c, const int64_t* ids, int n, double* Z, double* Zmean, double* Zsd);
 sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_prev,
                         std::vector<int64_t>& acc);
 sisso_status eval_features(sisso_ctx* c, const int64_t* ids_dev, int64_t n, int precision,

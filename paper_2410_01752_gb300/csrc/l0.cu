@@ -444,9 +444,15 @@ __global__ void k_model_z(const double* __restrict__ Z, const double* __restrict
 sisso_status append_subspace(sisso_ctx* c, int n_old, int n_new, bool gram64) {
     if (n_new <= 0) return SISSO_OK;
     const int n = n_old + n_new;
-    k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->opval64, c->Z,
-                                                 c->Zmean, c->Zsd);
-    c->stats.launches++;
+    if (c->Wm) {       // whitened data (§2.4): the standardised rows of W v
+        sisso_status st = whiten_standardise(c, c->S_dev + n_old, n_new, c->Z + (size_t)n_old * c->N,
+                                             c->Zmean + n_old, c->Zsd + n_old);
+        if (st) return st;
+    } else {
+        k_standardise<<<n_new, 256, 0, c->stream>>>(c->space_dev, c->Xc64, c->N, c->S_dev, n_old, c->opval64, c->Z,
+                                                     c->Zmean, c->Zsd);
+        c->stats.launches++;
+    }
     if (gram64) {
         dim3 grid(n_new, std::max(1, std::min(64, (n + 1 + kWarps - 1) / kWarps)));
         k_gram_rows<<<grid, kWarps * 32, 0, c->stream>>>(c->Z, c->yc64, c->N, n_old, n, c->n_cap, c->G64, c->b64,

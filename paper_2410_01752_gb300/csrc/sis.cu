@@ -1322,7 +1322,16 @@ void pair_tiles(int64_t P, int64_t Q, bool nxp, std::vector<int2>& tiles) {
     std::stable_sort(tiles.begin(), tiles.end(), [](const int2& a, const int2& b) { return a.y < b.y; });
 }
 
+// dimensional analysis: non-physical candidates score -1
+void apply_unit_mask(sisso_ctx* c) {
+    if (!c->unit_mask) return;
+    k_apply_unit_mask<<<std::max(1, std::min(c->sms * 8, (int)((c->n_feat + 255) / 256))), 256, 0, c->stream>>>(
+        c->unit_mask, c->n_feat, c->scores);
+    c->stats.launches++;
+}
+
 sisso_status score_all(sisso_ctx* c, int precision) {
+    if (c->Wm) return whiten_score_all(c);       // whitened data (§2.4): scored row by row
     const Space& sp = c->space;
     const int L = sp.rung;
     const bool fp64 = precision == SISSO_PREC_FP64;
@@ -1493,11 +1502,7 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         if (st) return st;
     }
     cudaEventRecord(e2, c->stream);
-    if (c->unit_mask) {     // dimensional analysis: non-physical candidates score -1
-        k_apply_unit_mask<<<std::max(1, std::min(c->sms * 8, (int)((c->n_feat + 255) / 256))), 256, 0, c->stream>>>(
-            c->unit_mask, c->n_feat, c->scores);
-        c->stats.launches++;
-    }
+    apply_unit_mask(c);
     cudaEvent_t e3;
     cudaEventCreate(&e3);
     cudaEventRecord(e3, c->stream);
@@ -1577,7 +1582,12 @@ sisso_status sis_select(sisso_ctx* c, int k, const int64_t* S_prev_host, int n_p
         const int nr = ns + n_prev;
         cudaEventRecord(q[1], c->stream);
         double* zc = (int64_t)nr <= c->zcap ? c->zcache : nullptr;   // cache the vectors if they fit
-        if (c->opval64 && c->N >= 4096 && nr > 0)
+        if (c->Wm) {            // whitened data: every window vector cached (checked at creation)
+            if (!zc) { st = fail(c, SISSO_ERR_CAPACITY, "whitened window exceeds the vector cache"); break; }
+            if ((st = whiten_rescore(c, c->surv_ids, nr, c->surv_score, c->surv_mean, c->surv_sd, c->surv_valid,
+                                     c->surv_probe, zc)))
+                break;
+        } else if (c->opval64 && c->N >= 4096 && nr > 0)
             k_rescore_cta<<<nr, kRescoreThreads, 0, c->stream>>>(c->space_dev, c->N, c->tc64, c->tstats, c->surv_ids,
                                                                  c->subvalid, c->opval64, c->opinv64, c->surv_score,
                                                                  c->surv_mean, c->surv_sd, c->surv_valid,

@@ -62,7 +62,7 @@ class Opts(C.Structure):
                 ("band_rel", C.c_double), ("max_band", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("device", C.c_int), ("sis_threshold", C.c_double), ("stop_rmse", C.c_double),
                 ("prescreen", C.c_int), ("prescreen_quantile", C.c_double), ("wait_limit_ns", C.c_int64),
-                ("units", C.c_void_p), ("screen", C.c_int), ("gram", C.c_int)]
+                ("units", C.c_void_p), ("screen", C.c_int), ("gram", C.c_int), ("whiten", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -321,7 +321,7 @@ class Sisso:
                  precision: int = PREC_FP32, grammar: int = GRAMMAR_EQ2, survivors: int = 0,
                  max_band: int = 0, band_rel: float = 0.0, stream=None, device: int = 0,
                  sis_threshold: float = 0.0, stop_rmse: float = 0.0, units=None, prescreen=None,
-                 screen: int = 0, gram: int = 0):
+                 screen: int = 0, gram: int = 0, whiten=None):
         L = load()
         self._ctx = C.c_void_p()
         N, d = int(X.shape[0]), int(X.shape[1])
@@ -334,6 +334,12 @@ class Sisso:
         o.sis_threshold, o.stop_rmse = sis_threshold, stop_rmse
         o.screen = int(screen)          # SCREEN_AUTO, SCREEN_CORES or SCREEN_TENSOR (mixed forms)
         o.gram = int(gram)              # GRAM_AUTO, GRAM_FP64 or GRAM_TF32X3 (FP32 precision)
+        wmat = None
+        if whiten is not None:          # W (N x N): SISSO on W y and W Phi (FP64 precision)
+            wmat = np.ascontiguousarray(np.asarray(whiten, dtype=np.float64))
+            if wmat.shape != (N, N):
+                raise ValueError("whiten: W must be N x N")
+            o.whiten = C.c_void_p(wmat.ctypes.data)
         if prescreen is not None:    # (SISSO_PRESCREEN_MI or _SPEARMAN, quantile kept)
             o.prescreen, o.prescreen_quantile = int(prescreen[0]), float(prescreen[1])
         ulab = None

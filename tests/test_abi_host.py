@@ -85,10 +85,11 @@ def test_eq2_rung3_triangle_unranking(orc, lib):
     (dict(max_dim=6), "max_dim > 5"), (dict(sis_size=0), "k = 0"), (dict(sis_size=2000), "k > 1024"),
     (dict(N=3), "N < max_dim + 1"), (dict(precision=7), "precision"), (dict(grammar=3), "grammar"),
     (dict(gram=3), "gram option"), (dict(gram=2, precision=0), "3xTF32 Gram with FP64 precision"),
-    (dict(gram=2, precision=2), "3xTF32 Gram with a mixed form")])
+    (dict(gram=2, precision=2), "3xTF32 Gram with a mixed form"),
+    (dict(whiten=True, precision=1), "whitening needs FP64 precision")])
 def test_argument_errors(lib, kw, bad):
     args = dict(N=20, d=3, op_set=lib.OP_ADD | lib.OP_MUL, rung=2, sis_size=5, max_dim=3, precision=1, grammar=0,
-                gram=0)
+                gram=0, whiten=False)
     args.update(kw)
     L = lib.load()
     X = np.ones((max(args["N"], 1), args["d"]))
@@ -96,6 +97,9 @@ def test_argument_errors(lib, kw, bad):
     o = lib.Opts()
     L.sisso_default_opts(C.byref(o))
     o.precision, o.grammar, o.gram = args["precision"], args["grammar"], args["gram"]
+    W = np.eye(max(args["N"], 1))
+    if args["whiten"]:
+        o.whiten = C.c_void_p(W.ctypes.data)
     ctx = C.c_void_p()
     st = L.sisso_create(C.c_void_p(X.ctypes.data), C.c_void_p(y.ctypes.data), args["N"], args["d"],
                         args["op_set"], args["rung"], args["sis_size"], args["max_dim"], C.byref(o),
