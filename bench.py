@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="default line: skip the bounded runs of the mixed, batched and learned forms")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
-                    help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples")
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5, 7],
+                    help="2: rung-3 screening + l0 (default); 3: mixed precision vs plain, 65 536 samples; "
+                         "7: whitened fit (AR(1) noise, 500 samples)")
     ap.add_argument("--tasks", type=int, default=512, help="batched workload: number of tasks")
     ap.add_argument("--train-problems", type=int, default=2000, help="learned workload: training problems")
     ap.add_argument("--eval-problems", type=int, default=100, help="learned workload: held-out problems")
@@ -404,6 +405,66 @@ def form_ensemble(args):
             "paper_seconds": {"fortran_sisso_1cpu": 182.43, "torchsisso_gpu_a100": 51.32,
                               "note": "the paper's ensemble timing table (another machine: context, not a target)"},
             "gpu_launches": 1, "cpu_baseline": cpu, "parity": parity}
+
+
+def form_whitened(args):
+    """Whitening (§2.4) on the workload-7 problem: N = 500, AR(1) noise and its whitening
+    matrix, rung 2 (16 205 candidates), k = 10, D <= 3, FP64: time to the final descriptor,
+    the whitened scoring's FP64 rate (the N x N product per candidate and step against the
+    measured FP64 FMA peak), and parity with the oracle's whitened fit of the same data (the
+    CPU-baseline leg)."""
+    import numpy as np
+    import torch
+    from paper_2410_01752_gb300 import PREC_FP64, Sisso, inputs, sisso
+    P = inputs.whitened_problem(0)
+    stream = torch.cuda.current_stream()
+    with Sisso(P.X, P.y, P.op_set, P.rung, P.sis_size, P.max_dim, precision=PREC_FP64, stream=stream,
+               whiten=P.W) as s:
+        s.fit()
+        ms = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d = s.fit()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = s.stats()
+        sis_ids = [s.sis(t) for t in range(1, len(d) + 1)]
+        n_feat = s.feature_count()[0]
+    steps = len(d)
+    flop = 2.0 * P.N * P.N * n_feat * steps           # W applied to every candidate, every step
+    fp64_peak = None
+    try:
+        fp64_peak = sisso.measure_alu_peak(2)
+    except Exception:
+        pass
+    rate = flop / (st["ms_screen"] / 1e3) / 1e12
+    out = {"workload": P.name, "metric": "time-to-descriptor", "unit": "ms", "time_to_descriptor_ms": float(np.median(ms)),
+           "descriptor": d[-1].ids, "rmse": d[-1].rmse, "gpu_launches": st["launches"],
+           "whitened_scoring": {"ms_per_fit": st["ms_screen"], "flop_per_fit": flop, "tflops": rate,
+                                "fp64_peak_measured_tflops": fp64_peak,
+                                "frac_of_measured": rate / fp64_peak if fp64_peak else None,
+                                "fp64_peak_nominal_tflops": 1.25, "frac_of_nominal": rate / 1.25,
+                                "note": "2 N^2 flop per candidate and step over the whole scoring phase (raw rows, "
+                                        "the FP64 product with W, whitened moments)"},
+           "phase_ms": {k: st[k] for k in ("ms_screen", "ms_select", "ms_gram", "ms_l0", "ms_refit")}}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.fit(P.X, P.y, oracle.Space(P.d, P.op_set, P.rung, P.grammar), P.sis_size, P.max_dim, W=P.W)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 1e3 * dt, "unit": "ms", "cores": cores(), "kind": "oracle",
+                               "sample": "the whole whitened fit by the FP64 oracle (its scoring threaded)"}
+        err = max((abs(a - b) / max(abs(b), 1e-300) for g, r in zip(d, ref.dims) for a, b in zip(g.coef, r.coef)),
+                  default=0.0)
+        out["parity"] = {"sis_steps_equal": sis_ids == ref.sis[:len(sis_ids)],
+                         "descriptors_equal": [g.ids for g in d] == [r.ids for r in ref.dims],
+                         "coef_max_rel_err": err, "tolerance_rel": 1e-6,
+                         "ok": sis_ids == ref.sis[:len(sis_ids)] and [g.ids for g in d] == [r.ids for r in ref.dims]
+                         and err <= 1e-6}
+    return out
 
 
 def form_batched(args):
@@ -864,6 +925,13 @@ def main():
     if args.workload == 5:
         run_batch(args, int(os.environ.get("RANK", "0")))
         return
+    if args.workload == 7:         # whitening (§2.4): the form on its own line
+        import torch
+        from paper_2410_01752_gb300 import build
+        build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(form_whitened(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -993,7 +1061,8 @@ def main():
     forms = None
     if not args.no_forms and world == 1:
         forms = {"mixed_precision": form_mixed(args), "batched": form_batched(args),
-                 "learned_proposal": form_learned(args), "ensemble": form_ensemble(args)}
+                 "learned_proposal": form_learned(args), "ensemble": form_ensemble(args),
+                 "whitened": form_whitened(args)}
 
     d_last = desc[-1] if desc else None
     line = {

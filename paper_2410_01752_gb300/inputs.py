@@ -20,6 +20,9 @@ Workloads (x: primary features, N samples x d; y: target):
      terms from a fixed menu, c ~ U(-5, 5), 0.5% noise                          (rung 2, k=50, D<=3)
   6  the ensemble timing workload (§4.5): N=3000, d=4, x ~ U[1,5], y = x1^4 + x2^3 + x3^2
      + x4 + 0.1% noise, cut into 30 subsets of 100 samples                       (rung 2, k=20, D<=4)
+  7  whitening (§2.4): N=500, d=5, x ~ U[1,5]; y = 2 x1 x2 / x3 + sqrt(x5) + AR(1) noise
+     (coefficient 0.6, innovations sd 0.05), with the whitening matrix of that covariance
+     (the Prais-Winsten transform, lower bidiagonal)                           (rung 2, k=10, D<=3)
   The paper's own workloads are of the same kind: x in [1,5], small N, 3-4 term targets
   (§4.1, §4.5).
 """
@@ -107,6 +110,38 @@ def ensemble_problem(p: int = 0, N: int = 3000, sis_size: int = 20, max_dim: int
     y = clean + r.normal(0.0, 1e-3 * clean.std(), size=N)
     return Problem(X, y, OPS9, 2, sis_size, max_dim, GRAMMAR_EQ2,
                    f"ensemble four-term N={N} d=4 rung2 k={sis_size} D<={max_dim}")
+
+
+@dataclass
+class WhitenedProblem(Problem):
+    W: np.ndarray = None   # N x N whitening matrix of the noise covariance (W Sigma W^T = I)
+
+
+def ar1_whitener(N: int, rho: float, sd: float) -> np.ndarray:
+    """The whitening matrix of AR(1) noise e_t = rho e_{t-1} + u_t, u ~ N(0, sd^2), stationary
+    start (the Prais-Winsten transform): row 0 = sqrt(1 - rho^2) e_0 / sd, row t = (e_t - rho
+    e_{t-1}) / sd, so that W e has independent unit-variance entries."""
+    W = np.zeros((N, N))
+    W[0, 0] = np.sqrt(1.0 - rho * rho) / sd
+    i = np.arange(1, N)
+    W[i, i] = 1.0 / sd
+    W[i, i - 1] = -rho / sd
+    return W
+
+
+def whitened_problem(p: int = 0, N: int = 500, sis_size: int = 10, max_dim: int = 3,
+                     rho: float = 0.6, sd: float = 0.05) -> WhitenedProblem:
+    """Workload 7: a planted rung-2 target with AR(1) noise and its whitening matrix."""
+    r = _rng(7, p)
+    X = r.uniform(1.0, 5.0, size=(N, 5))
+    e = np.empty(N)
+    e[0] = r.normal(0.0, sd / np.sqrt(1.0 - rho * rho))
+    u = r.normal(0.0, sd, size=N)
+    for t in range(1, N):
+        e[t] = rho * e[t - 1] + u[t]
+    y = 2.0 * X[:, 0] * X[:, 1] / X[:, 2] + np.sqrt(X[:, 4]) + e
+    return WhitenedProblem(X, y, OPS9, 2, sis_size, max_dim, GRAMMAR_EQ2,
+                           f"whitened AR(1) N={N} d=5 rung2 k={sis_size} D<={max_dim}", ar1_whitener(N, rho, sd))
 
 
 _MENU = [

@@ -89,3 +89,14 @@ def test_whitening_changes_the_fit(orc):
     a = orc.fit(X, y, sp, 4, 1)
     b = orc.fit(X, y, sp, 4, 1, W=W)
     assert not np.allclose(a.dims[0].coef, b.dims[0].coef, rtol=1e-6)
+
+
+def test_ar1_whitener_whitens_its_covariance():
+    """The benchmark's whitening matrix (inputs.ar1_whitener, the Prais-Winsten transform)
+    satisfies W Sigma W^T = I for the stationary AR(1) covariance it is built for."""
+    from paper_2410_01752_gb300 import inputs
+    N, rho, sd = 200, 0.6, 0.05
+    i = np.arange(N)
+    Sig = sd ** 2 / (1 - rho ** 2) * rho ** np.abs(i[:, None] - i[None, :])
+    W = inputs.ar1_whitener(N, rho, sd)
+    assert np.abs(W @ Sig @ W.T - np.eye(N)).max() < 1e-12
