@@ -362,13 +362,53 @@ __global__ void k_unary_finish(UnaryArgs U, const double* __restrict__ val, cons
 
 
 
-template <typename T>
-__global__ void __launch_bounds__(kUnaryMax * 32)
-k_score_unary(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
-              const TargetStats* st, const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
-    __shared__ T xs[32][33];
-    __shared__ T r[32];
-    unary_block<T>(U, cache, tc32, tc64, st, subvalid, scores, blockIdx.x, xs, r);
+// the top level's unary sections: one warp per 32 operands (lane = operand) and every
+// enabled operator, reading the sample-major cache directly (coalesced, no staging, no block
+// barrier: no warp waits for the slowest operator of another).  Each (operand, operator)
+// accumulates its shifted sums over the samples in order, the arithmetic of unary_block.
+// STD5: the operators are exp, log, sqrt, ^2, ^-1 in that order, unrolled at compile time.
+template <typename T, bool STD5>
+__global__ void __launch_bounds__(256)
+k_score_unary_w(UnaryArgs U, const T* __restrict__ cache, const float* tc32, const double* tc64,
+                const TargetStats* st, const unsigned char* __restrict__ subvalid, float* __restrict__ scores) {
+    const int lane = threadIdx.x & 31;
+    const int64_t z0 = U.Q + ((((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5);
+    if (z0 >= U.P) return;
+    const int64_t z = z0 + lane;
+    const bool active = z < U.P;
+    const T* tc = TgtView<T>::tc(tc32, tc64);
+    const int N = U.N;
+    constexpr int K = STD5 ? 5 : kUnaryMax;
+    constexpr int kStd[5] = {EXP, LOG, SQRT, SQ, INV};
+    T v0[K], s1[K], s2[K], sr[K];
+    const T x0 = active ? cache[z] : T(1);
+#pragma unroll
+    for (int o = 0; o < K; ++o) {
+        const int op = STD5 ? kStd[o] : (o < U.n_ops ? U.op[o] : EXP);
+        v0[o] = op_unary<T>(op, x0);
+        s1[o] = s2[o] = sr[o] = T(0);
+    }
+#pragma unroll 4
+    for (int s = 0; s < N; ++s) {
+        const T x = active ? cache[(size_t)s * U.P + z] : T(1);
+        const T r = tc[s];
+#pragma unroll
+        for (int o = 0; o < K; ++o) {
+            if (!STD5 && o >= U.n_ops) continue;
+            const T v = op_unary<T>(STD5 ? kStd[o] : U.op[o], x) - v0[o];
+            s1[o] += v;
+            s2[o] = fma(v, v, s2[o]);
+            sr[o] = fma(v, r, sr[o]);
+        }
+    }
+    if (!active) return;
+    const bool ok = subvalid[z];
+#pragma unroll
+    for (int o = 0; o < K; ++o) {
+        if (!STD5 && o >= U.n_ops) continue;
+        scores[U.base[o] + (z - U.Q)] = ok ? finalize<T>(s1[o], s2[o], sr[o], v0[o], N, TgtView<T>::sum(st), TgtView<T>::sd(st))
+                                           : -1.f;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1375,8 +1415,16 @@ sisso_status score_all(sisso_ctx* c, int precision) {
         if (U.n_ops > 0) {
             const int gu = (int)((A.P - A.Q + 31) / 32);
             if (gu >= 2 * c->sms || !c->opval64) {
-                if (fp64) k_score_unary<double><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
-                else k_score_unary<float><<<gu, kUnaryMax * 32, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                const bool std5 = U.n_ops == 5 && U.op[0] == EXP && U.op[1] == LOG && U.op[2] == SQRT &&
+                                  U.op[3] == SQ && U.op[4] == INV;
+                const int gb = (gu + 7) / 8;           // eight warps per block, a warp per 32 operands
+                if (fp64) {
+                    if (std5) k_score_unary_w<double, true><<<gb, 256, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                    else k_score_unary_w<double, false><<<gb, 256, 0, c->stream>>>(U, c->opcache64, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                } else {
+                    if (std5) k_score_unary_w<float, true><<<gb, 256, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                    else k_score_unary_w<float, false><<<gb, 256, 0, c->stream>>>(U, c->opcache32, c->tc32, c->tc64, c->tstats, c->subvalid, c->scores);
+                }
             } else {      // few operands: warps over (operand, run of samples)
                 const int64_t nz = A.P - A.Q;
                 const int runs = (int)std::max<int64_t>(1, std::min<int64_t>((c->N + 1023) / 1024,
