@@ -83,3 +83,18 @@ def test_identity_whitening_is_the_plain_fit(S, orc):
     assert [g.ids for g in white] == [g.ids for g in plain]
     for a, b in zip(white, plain):
         np.testing.assert_allclose(a.coef, b.coef, rtol=1e-10)
+
+
+def test_whitened_fit_with_units_threshold_and_nxp(S, orc):
+    """Whitening together with dimensional analysis (x1, x2 one unit, x3 dimensionless),
+    the threshold variant of SIS and the NEW_X_PREV grammar at rung 3."""
+    X, y = _problem(9, 50, 3)
+    W, _ = _whitener(50, "tri")
+    labels = [0, 0, -1]
+    m = _mask(orc, ALL9)
+    sp = orc.Space(3, m, 3, orc.GRAMMAR_NEW_X_PREV, units=labels)
+    ref = orc.fit(X, y, sp, 8, 2, sis_threshold=0.3, W=W)
+    with S.Sisso(X, y, m, 3, 8, 2, precision=PREC_FP64, grammar=S.GRAMMAR_NEW_X_PREV, units=labels,
+                 sis_threshold=0.3, whiten=W) as c:
+        got = c.fit()
+        _compare(c, got, ref, y)
