@@ -1,5 +1,6 @@
-// gram_tc.cu — the subspace Gram G = Z Z^T / N on the tcgen05 tensor cores.
+// gram_tc.cu — the subspace Gram G = Z Z^T / N on the tcgen05 tensor cores (§2.3 Eq. 7).
 //
+// 16-bit form (mixed precision; the 3xTF32 form of FP32 precision follows further down).
 // Z (rows of standardised features, plus the centred target scaled to unit variance as the
 // last row) is rounded to BF16 or FP16 and stored K-major (rows of samples), zero-padded to
 // multiples of 128 rows and 64 samples.  A CTA computes one 128 x 128 output tile over a

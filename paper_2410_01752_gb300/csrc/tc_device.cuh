@@ -58,8 +58,8 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B of the same
-// 16-bit type (0 FP16, 1 BF16), both K-major, tile M x N
+// instruction descriptor of tcgen05.mma kind::f16 / kind::tf32: FP32 accumulator, A and B of
+// the same type (kind::f16: 0 FP16, 1 BF16; kind::tf32: 2 TF32), both K-major, tile M x N
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type, int M = 128, int N = 128) {
     return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
