@@ -303,15 +303,18 @@ __global__ void __launch_bounds__(kTW * 32, 2) k_l0_tile(TileArgs A) {
 
     // work units (tile, prefix) are claimed kClaim at a time from the global counter: one
     // same-address atomic per kClaim units instead of one per unit (about 3e5 units per
-    // launch at C(400, 4)), and the warp waits for the counter once per claim
+    // launch at C(400, 4)); the claim after the current one is requested when the current
+    // one starts, so the atomic's round trip overlaps the current units (claims are handed
+    // out in increasing order, so a warp that runs past the end holds no unit below it)
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(A.counter);
+    int64_t ahead = 0;
+    if (lane == 0) ahead = (int64_t)atomicAdd(ctr, (unsigned long long)kClaim);
     int64_t next = 0, end = 0;
     while (true) {
         if (next == end) {
-            int64_t base = 0;
-            if (lane == 0) base = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(A.counter), (unsigned long long)kClaim);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            next = base;
-            end = base + kClaim;
+            next = __shfl_sync(0xffffffffu, ahead, 0);
+            end = next + kClaim;
+            if (lane == 0) ahead = (int64_t)atomicAdd(ctr, (unsigned long long)kClaim);
         }
         const int64_t item = next++;
         if (item >= A.n_items) break;
