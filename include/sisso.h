@@ -269,7 +269,16 @@ sisso_status sisso_feature_expr(const sisso_ctx* ctx, int64_t id, char* buf, siz
 
 sisso_status sisso_get_stats(const sisso_ctx* ctx, sisso_stats* out);
 const char* sisso_last_error(const sisso_ctx* ctx);
+/* Destroy a context: its device buffers go back to a memory pool per device that the library
+ * keeps (up to 32 GB of freed memory) for the next context, so that creating contexts one
+ * after another does not map and unmap gigabytes each time; sisso_release_memory returns
+ * that memory to the device. */
 void sisso_destroy(sisso_ctx* ctx);
+
+/* Release the device memory the library's pool keeps for device `device` after its contexts
+ * were destroyed (memory of live contexts stays).  Synchronises the device.  Errors:
+ * SISSO_ERR_ARG (no such device), SISSO_ERR_CUDA. */
+sisso_status sisso_release_memory(int device);
 
 /* ---- feature space without a context (host only, no GPU needed) ------------------- */
 

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 using namespace sg;
@@ -35,11 +37,41 @@ __global__ void k_cast(const double* __restrict__ a, float* __restrict__ b, int6
         b[i] = (float)a[i];
 }
 
+// A context's buffers (several GB at rung 3) come from a stream-ordered pool per device that
+// is private to the library and keeps up to kPoolKeep bytes of freed memory for the next
+// context: mapping and unmapping them at every create / destroy took a large share of a
+// create-fit-destroy cycle.  sisso_release_memory hands the kept memory back.
+constexpr uint64_t kPoolKeep = (uint64_t)32 << 30;
+std::mutex g_pool_mutex;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t ctx_pool(int dev, bool create) {
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    if (!create) return nullptr;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = kPoolKeep;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    return pool;
+}
+
 template <typename T>
 sisso_status dalloc(sisso_ctx* c, T*& p, size_t count, const char* what) {
     p = nullptr;
     if (count == 0) count = 1;
-    return check_cuda(c, cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * count), what);
+    cudaMemPool_t pool = ctx_pool(c->opts.device, true);
+    if (!pool) return check_cuda(c, cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * count), what);
+    const sisso_status st = check_cuda(
+        c, cudaMallocFromPoolAsync(reinterpret_cast<void**>(&p), sizeof(T) * count, pool, c->stream), what);
+    if (!st) c->pooled.insert(p);
+    return st;
 }
 
 void free_all(sisso_ctx* c) {
@@ -52,12 +84,17 @@ void free_all(sisso_ctx* c) {
                     c->dup_cnt, c->accepted, c->opcache32, c->opcache64, c->opsum, c->opval64,
                     c->band_r32, c->band_sel, c->tile_G, c->tile_b, c->tile_diag, c->tile_info,
                     c->unit_ok, c->unit_mask, c->opinv64, c->fix_ids, c->fix_count};
-    for (void* p : bufs)
-        if (p) cudaFree(p);
+    for (void* p : bufs) {
+        if (!p) continue;
+        if (c->pooled.count(p)) cudaFreeAsync(p, c->stream);    // back to the library's pool
+        else cudaFree(p);
+    }
+    c->pooled.clear();
     tc_screen_free(c);
     whiten_free(c);
     if (c->walk_h) cudaFreeHost(c->walk_h);
     if (c->win_h) cudaFreeHost(c->win_h);
+    if (c->stream) cudaStreamSynchronize(c->stream);          // the frees done before the stream goes
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -445,6 +482,17 @@ void sisso_destroy(sisso_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_all(c);
     delete c;
+}
+
+sisso_status sisso_release_memory(int device) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return SISSO_ERR_ARG;
+    cudaMemPool_t pool = ctx_pool(device, false);
+    if (!pool) return SISSO_OK;
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemPoolTrimTo(pool, 0) != cudaSuccess)
+        return SISSO_ERR_CUDA;
+    return SISSO_OK;
 }
 
 // ---- feature space without a context -----------------------------------------------------

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdint>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/sisso.h"
@@ -387,6 +388,7 @@ struct sisso_ctx {
     double* opcache64 = nullptr;       // ... FP64 copy (FP64 screening only)
     double* opsum = nullptr;           // per operand: sum (x - x0), sum (x - x0) r, sum (x - x0)^2 (3 x |phi_{L-1}|)
     int opsum_prec = -1;               // cache the first half was computed from (0 FP64, 1 FP32)
+    std::unordered_set<const void*> pooled;  // buffers from the library's device pool (api.cu)
     double* Wm = nullptr;              // whitening matrix W (N x N), or null (§2.4)
     double* w_raw = nullptr;           // whitened path: raw rows, whitened rows (w_chunk x N each),
     double* w_u = nullptr;             //   per-row scratch (3 w_chunk), probes, raw validity

@@ -43,7 +43,7 @@ EXPORTS = [
     "sisso_mlp_gradients", "sisso_mlp_train", "sisso_prefix_features", "sisso_prefix_labels", "sisso_l0_learned",
     "sisso_set_proposal", "sisso_get_primaries", "sisso_prescreen", "sisso_prefix_training",
     "sisso_batch_set_wait_limit", "sisso_l0_learned_certified", "sisso_set_proposal_ex",
-    "sisso_bilinear_tc", "sisso_measure_alu_peak",
+    "sisso_bilinear_tc", "sisso_measure_alu_peak", "sisso_release_memory",
 ]
 MLP_IN, MLP_HIDDEN = 20, 256
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
@@ -151,6 +151,7 @@ def load() -> C.CDLL:
     L.sisso_gram_tc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, vp]
     L.sisso_bilinear_tc.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.sisso_measure_alu_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    L.sisso_release_memory.argtypes = [C.c_int]
     L.sisso_l0_search_noalloc.argtypes = [vp, vp, C.c_double, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp,
                                           C.POINTER(C.c_int), dp, i64p]
     L.sisso_space_expr.argtypes = [C.c_int, C.c_uint32, C.c_int, C.c_int, C.c_int64, C.c_char_p, C.c_size_t]
@@ -277,6 +278,14 @@ def bilinear_tc(Lrows, Rrows, kind: int = PREC_MIXED_FP16):
 
 
 ALU_FP32, ALU_FP32X2, ALU_FP64 = 0, 1, 2
+
+
+def release_memory(device: int = 0) -> None:
+    """Hand the device memory the library keeps for later contexts back to the device
+    (sisso_release_memory)."""
+    st = load().sisso_release_memory(int(device))
+    if st:
+        raise SissoError(st, "release_memory")
 
 
 def measure_alu_peak(kind: int = ALU_FP32) -> float:

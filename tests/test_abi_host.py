@@ -111,6 +111,7 @@ def test_argument_errors(lib, kw, bad):
 def test_null_and_state_errors(lib):
     L = lib.load()
     assert L.sisso_fit(None) == -1
+    assert L.sisso_release_memory(-1) == -1
     n = C.c_int()
     assert L.sisso_get_n_dims(None, C.byref(n)) == -1
     assert L.sisso_space_sizes(3, 0, 2, 0, None) == -1
